@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Throughput of the SPH terrain step on B300: active SPH particle-steps per second.
+
+Workload: the single grousered wheel on a soil bin -- 120,000 SPH particles on a
+2.0 x 0.4 x 0.15 m bin at d0 = 0.01 m (h = 1.2 d0), 3-layer BCE walls, a rigid
+wheel (r = 0.2 m, width 0.15 m, 12 grousers 0.01 m tall) with prescribed spin and
+slip 0.3 and a free vertical DOF under a 100 N load, friction 33 deg, cohesion
+500 Pa, dt = 5e-5 s, neighbour lists rebuilt every step.  Synthetic, seeded
+inputs (scenes.wheel_bin).
+
+One step = the whole per-step path: rebuild (keys, scan, scatter, reorder,
+neighbour lists), BCE extrapolation and pair sums for both RK2 stages, return
+map, FP64 wrench and body update.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl crm|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload ("replicas only": the method has no exchange step on
+one terrain here), so value = all ranks' particle-steps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "active SPH particle-steps/sec on 1 B300"
+UNIT = "particle-steps/s"
+WORKLOAD = ("wheel_bin: 120,000 SPH particles, 2.0x0.4x0.15 m bin at d0=0.01 m, h=1.2 d0, "
+            "3-layer BCE walls + grousered wheel (r=0.2 m, 12 grousers), slip 0.3, 100 N, "
+            "phi=33 deg, c=500 Pa, dt=5e-5 s, ps_freq=1")
+# Arithmetic of one fluid-fluid or fluid-marker pair in the pair kernel, counted
+# from its source (FMA = 2): offsets 6, r^2 5, rsqrt/scale 3, dW/dr 5, grad 3,
+# V_j 1, u_ji 3, continuity 7, stress sums 6, momentum 21, V_j u_ji 3, velocity
+# gradient 18, artificial viscosity 18 => 99; per particle: stress rate,
+# update and return map ~100.
+FLOP_PER_PAIR = 99
+FLOP_PER_PARTICLE = 100
+SM_FP32_LANES = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        self.f.close()
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(budget_s: float = 15.0) -> dict:
+    """The FP64 oracle as it stands, on this host's cores, on a bounded sample of
+    the same workload: as many whole steps as fit in ~budget_s (at least 2)."""
+    import oracle
+    import scenes
+    sc = scenes.wheel_bin()
+    st = oracle.State(sc)
+    t0 = time.perf_counter()
+    n = 0
+    while n < 2 or time.perf_counter() - t0 < budget_s:
+        st.step()
+        n += 1
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": sc.n_fluid * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"wheel_bin workload, first {n} whole steps ({el:.1f} s, FP64, OpenMP), "
+                      f"cpu={_cpu_model()}"}
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, one whole step of the workload per step."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import scenes
+    sc = scenes.wheel_bin()
+    st = oracle.State(sc)
+    for _ in range(args.warmup):
+        st.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.step()
+    el = time.perf_counter() - t0
+    value = sc.n_fluid * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_sph": sc.n_fluid, "n_bce": sc.n_markers,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"wheel_bin workload, {args.steps} whole steps after "
+                                       f"{args.warmup} warm-up, cpu={_cpu_model()}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2507_05643_b300", "csrc", "crm_step.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = rec.get(kernel)
+    if not e or e.get("source_sha") != h:
+        return None
+    return e.get("bytes_per_launch")
+
+
+def _workload(args):
+    """The benchmark workload; --bin-scale S > 1 widens the bin S-fold in x and y
+    (a profiling case larger than L2, not a bench line)."""
+    import scenes
+    if args.bin_scale == 1:
+        return scenes.wheel_bin()
+    s = args.bin_scale
+    return scenes.wheel_bin(nx=200 * s, ny=40 * s, wheel_x=0.4 * s)
+
+
+def run_crm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2507_05643_b300 as crm
+    import scenes
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sc = _workload(args)
+    t = crm.from_scene(sc, stream=stream)
+    dt = sc.dt
+    with torch.cuda.stream(stream):
+        t.step(dt, args.warmup)
+        t.sync()
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        t.profile_reset(timing=True)
+        sampler = ClockSampler(local)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            t.step(dt, 1)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        clocks = sampler.stop()
+        t.sync()
+        prof = t.profile()
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    n_active, _, n_bce = t.counts()
+    # the neighbour pairs of the fluid rows at the end of the timed region
+    off, _ = t.neighbors()
+    fluid_pairs = int(off[sc.n_fluid] - off[0])
+
+    # end to end through the public API: per step the co-simulation exchange of
+    # Sec. 2.4 -- body pose/twist host->device, step, wrench + body state
+    # device->host (pinned host buffers, synchronous read of the result)
+    pose, twist = t.body_state(0)
+    hbuf = torch.empty(13, dtype=torch.float64, pin_memory=True)
+    hbuf[:7] = torch.from_numpy(pose)
+    hbuf[7:] = torch.from_numpy(twist)
+    e2e_steps = max(args.steps, 1)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hb = hbuf.numpy()
+        t.set_body_motion(0, hb[:7], hb[7:])
+        t.step(dt, 1)
+        F, T = t.body_wrench(0)
+        p, tw = t.body_state(0)
+        hbuf[:7] = torch.from_numpy(p)
+        hbuf[7:] = torch.from_numpy(tw)
+    e2e_s = time.perf_counter() - w0
+    t.sync()
+
+    # max over ranks
+    times = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(times[0]), float(times[1])
+    if rank == 0:
+        peaks, kind = _peaks()
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        launches = sum(prof["launches"].values())
+        # dominant kernel = largest share of the event-timed step
+        kern = max(prof["ms"], key=lambda k: prof["ms"][k])
+        avg_ms = prof["ms"][kern] / max(prof["launches"][kern], 1)
+        if kern.startswith("pair"):
+            flop = fluid_pairs * FLOP_PER_PAIR + sc.n_fluid * FLOP_PER_PARTICLE
+            achieved = flop / (avg_ms * 1e-3) / 1e12
+            peak = nsm * SM_FP32_LANES * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": f"{nsm} SMs x {SM_FP32_LANES} FP32 lanes x 2 x "
+                                   f"{peaks['sm_max_mhz']:.0f} MHz ({kind} max clock)",
+                    "traffic": _traffic(kern),
+                    "flop_per_launch": flop, "ms_per_launch": avg_ms,
+                    "hbm_frac_of_measured": None}
+        else:
+            roof = {"bound": "hbm", "kernel": kern, "achieved": None, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": None, "traffic": _traffic(kern)}
+        line = {
+            "metric": METRIC,
+            "value": world * sc.n_fluid * args.steps / (ms_max * 1e-3),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_sph": sc.n_fluid, "n_active": n_active,
+                       "n_bce": n_bce, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write outside the events)"},
+            "e2e": {"value": world * sc.n_fluid * e2e_steps / e2e_max, "unit": UNIT,
+                    "h2d_bytes_per_step": 13 * 8, "d2h_bytes_per_step": 6 * 8 + 13 * 8 + 4,
+                    "loop": "set_body_motion -> step -> body_wrench + body_state (sync)"},
+            "gpu_launches": launches,
+            "kernel_ms": {k: v for k, v in prof["ms"].items() if prof["launches"][k]},
+            "roofline": roof,
+            "clocks": clocks,
+        }
+        if args.bin_scale != 1:
+            line["config"]["workload"] = f"profiling case: wheel_bin widened {args.bin_scale}x in x and y"
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["crm", "reference"], default="crm")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bin-scale", type=int, default=1,
+                    help="profiling only: widen the bin S-fold in x and y")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_crm(args)
+
+
+if __name__ == "__main__":
+    main()

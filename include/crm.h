@@ -1,0 +1,249 @@
+/*
+ * crm.h -- C ABI of the B300 (sm_103a) SPH continuum terrain library.
+ *
+ * The library advances the per-step particle loop of the continuum
+ * representation model of "A Physics-Based Continuum Model for Versatile,
+ * Scalable, and Fast Terramechanics Simulation" (arXiv 2507.05643):
+ *   - cell binning of SPH particles and boundary (BCE) markers by key sort and
+ *     the neighbour sets of Sec. 3.1 / Alg. 1,
+ *   - the pairwise continuity, momentum (stress divergence + artificial
+ *     viscosity) and Jaumann stress-rate sums of Sec. 2.1-2.2,
+ *   - the explicit-midpoint (RK2) update of Sec. 2.2 and the cohesive return
+ *     map of Sec. 2.3, restricted to the active-domain particles of Sec. 3.2,
+ *   - the BCE extrapolation and body force/torque of Sec. 2.4.
+ *
+ * Conventions
+ *   - Every call returns an int status: CRM_OK (0) or a negative CRM_E* code.
+ *     No C++ exception crosses the ABI.  crm_last_error() gives a message.
+ *   - A terrain handle is opaque, owns all of its device memory, and is bound
+ *     to one CUDA stream given at creation (NULL = the legacy default
+ *     stream).  A handle is not thread-safe; use one handle per host thread.
+ *   - Host arrays passed in are copied before the call returns; host arrays
+ *     passed out are written before the call returns (such calls synchronise
+ *     the stream).  crm_step() only enqueues work; device-side failures
+ *     (capacity, escaped particle, non-finite state, device wait timeout) are
+ *     latched on the device and reported by the next synchronising call
+ *     (crm_sync, crm_get_*).
+ *   - Units are SI.  Stresses are 6-vectors (xx, yy, zz, xy, xz, yz),
+ *     compression negative.  Poses are (x, y, z, qw, qx, qy, qz); twists are
+ *     (vx, vy, vz, wx, wy, wz) with the angular velocity in the world frame.
+ *   - Particle indices in the query calls are the order of insertion: SPH
+ *     particles in crm_add_sph order, markers in crm_add_fixed_bce /
+ *     crm_add_rigid_body order (fixed markers and body markers share one
+ *     marker index space, in call order).
+ */
+#ifndef CRM_H
+#define CRM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CRM_OK          0
+#define CRM_EINVAL     -1   /* bad argument (null pointer, size, value range) */
+#define CRM_ENOMEM     -2   /* a device or host allocation failed */
+#define CRM_ECAPACITY  -3   /* a neighbour list exceeded max_neighbors */
+#define CRM_EESCAPED   -4   /* a particle or marker left the grid domain */
+#define CRM_ENONFINITE -5   /* the state became non-finite */
+#define CRM_ETIMEOUT   -6   /* a bounded device-side wait gave up */
+#define CRM_ECUDA      -7   /* a CUDA runtime call failed */
+#define CRM_ESTATE     -8   /* call made in the wrong state (e.g. add after step) */
+
+#define CRM_AV_NONE        0
+#define CRM_AV_BILATERAL   1  /* Eq. artificial_viscosity_bilateral */
+#define CRM_AV_UNILATERAL  2  /* Eq. artificial_viscosity_unilateral */
+
+#define CRM_KERNEL_CUBIC   0  /* cubic spline, support 2h (Sec. 3.1) */
+
+#define CRM_DOF_X 1
+#define CRM_DOF_Y 2
+#define CRM_DOF_Z 4
+
+/* Material and numerical parameters (Sec. 2.1-2.3, Table tab:sph_params,
+ * Sec. 3.1-3.2).  Fill with crm_default_params() and override. */
+typedef struct crm_params {
+    double rho0;           /* reference (bulk) density, kg/m^3, > 0 */
+    double E, nu;          /* Young's modulus (Pa, > 0), Poisson ratio in (-1, 0.5):
+                              G = E / (2(1+nu)), K = E / (3(1-2nu)) */
+    double mu_s, mu_2;     /* static and limiting friction coefficients of mu(I);
+                              mu_s = tan(friction angle) (Sec. 4.4); mu_2 = mu_s
+                              gives the rate-independent cohesive cone */
+    double I0, grain_d;    /* mu(I) constants: I0 and particle diameter d (m) */
+    double cohesion;       /* cohesive intercept c of the yield cone, Pa, >= 0 */
+    double d0, h;          /* initial spacing and smoothing length (m); cells are 2h */
+    int32_t kernel;        /* CRM_KERNEL_CUBIC */
+    int32_t av_mode;       /* CRM_AV_* */
+    double av_gamma;       /* gamma_a of the artificial viscosity */
+    double av_xi2_over_h2; /* xi^2 / h^2 in the viscosity denominator (default 0.01) */
+    double gravity[3];     /* body force per unit mass, m/s^2 */
+    int32_t ps_freq;       /* neighbour lists rebuilt every ps_freq steps (Alg. 2), >= 1 */
+    int32_t max_neighbors; /* per-particle neighbour list capacity, 8..1024 */
+    double domain_min[3];  /* axis-aligned grid extent; every particle and marker */
+    double domain_max[3];  /* must stay inside it (else CRM_EESCAPED) */
+    double growth;         /* active-set capacity growth factor G (Sec. 3.2), >= 1 */
+    double shrink_ratio;   /* shrink threshold S (Sec. 3.2), in (0, 1] */
+    int32_t shrink_interval; /* shrink check interval S_I in steps (Sec. 3.2), >= 1 */
+    int32_t reserved;
+} crm_params;
+
+typedef struct crm_terrain crm_terrain;
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int crm_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *crm_status_string(int status);
+
+/* Defaults: rho0 1700, E 1e6, nu 0.3, mu_s = mu_2 = tan 30 deg, I0 0.08,
+ * grain_d 0.002, c 0, d0 0.01, h 0.012, cubic kernel, unilateral AV 0.02,
+ * xi^2 = 0.01 h^2, g = (0, 0, -9.81), ps_freq 1, max_neighbors 96, domain
+ * [0,1]^3, G 1.2, S 0.75, S_I 50 (Sec. 3.2). */
+void crm_default_params(crm_params *p);
+
+/* Create a terrain.  `cuda_stream` is a cudaStream_t (NULL for the default
+ * stream); all work is ordered on it.  Validates the parameters (CRM_EINVAL).
+ * On success *out receives the handle; on failure *out is NULL. */
+int crm_create(const crm_params *p, void *cuda_stream, crm_terrain **out);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+int crm_destroy(crm_terrain *t);
+
+/* Message of the last error on this handle ("" if none).  Valid until the
+ * next call on the handle. */
+const char *crm_last_error(const crm_terrain *t);
+
+/* Add n SPH particles (Sec. 2.2).  xyz: n*3 positions (required); vel: n*3
+ * velocities, stress6: n*6 stresses, rho: n densities -- each nullable
+ * (zero velocity, zero stress, rho0).  Host arrays, copied.  Only before the
+ * first crm_step / crm_eval_rates (else CRM_ESTATE). */
+int crm_add_sph(crm_terrain *t, int64_t n, const double *xyz, const double *vel,
+                const double *stress6, const double *rho);
+
+/* Add n fixed BCE wall markers at world positions xyz (n*3), Sec. 2.4. */
+int crm_add_fixed_bce(crm_terrain *t, int64_t n, const double *xyz);
+
+/* Add a rigid body carrying n_markers BCE markers given in the body frame
+ * (marker_xyz_local, n*3), with pose[7], twist[6], mass (kg, > 0) and a DOF
+ * mask: bit k of CRM_DOF_X/Y/Z set = that linear velocity component is
+ * integrated from the soil force and gravity (symplectic Euler); otherwise it
+ * is prescribed.  Angular velocity is always prescribed.  *body_id receives
+ * the body index (0, 1, ... in call order). */
+int crm_add_rigid_body(crm_terrain *t, int64_t n_markers, const double *marker_xyz_local,
+                       const double pose[7], const double twist[6], double mass,
+                       int32_t dof_mask, int32_t *body_id);
+
+/* Prescribe a body's pose and twist (the FSI exchange of Sec. 2.4): takes
+ * effect at the next step.  Host arrays, copied (enqueued on the stream). */
+int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7],
+                        const double twist[6]);
+
+/* Current pose and twist of a body (synchronises the stream). */
+int crm_get_body_state(crm_terrain *t, int32_t body, double pose[7], double twist[6]);
+
+/* Attach an active box (Sec. 3.2) to `body`: an oriented box with the given
+ * half extents and centre offset in the body frame.  Once any box exists the
+ * terrain runs in active-domain mode: after t_delay (the largest delay of any
+ * box) only SPH particles inside a box are integrated, particles within 2h of
+ * a box are read-only neighbours and the rest are frozen. */
+int crm_add_active_box(crm_terrain *t, int32_t body, const double half_extents[3],
+                       const double offset[3], double t_delay);
+
+/* Advance n_steps steps of size dt (Sec. 2.2 RK2 with the return map of
+ * Sec. 2.3 at the end of each step).  Enqueues on the stream and returns. */
+int crm_step(crm_terrain *t, double dt, int32_t n_steps);
+
+/* Wait for the stream and report any latched device-side failure. */
+int crm_sync(crm_terrain *t);
+
+/* Copy the SPH state out in insertion order: xyz (double, n*3), vel (n*3),
+ * stress6 (n*6), rho (n); each nullable.  cap = room in particles; fewer
+ * than n particles of room is CRM_EINVAL.  *n_out (nullable) receives n. */
+int crm_get_particles(crm_terrain *t, int64_t cap, double *xyz, float *vel, float *stress6,
+                      float *rho, int64_t *n_out);
+
+/* Body force and torque (about the body centre) of the last step, FP64. */
+int crm_get_body_wrench(crm_terrain *t, int32_t body, double force[3], double torque[3]);
+
+/* Active / extended-active SPH particles and BCE markers processed in the
+ * last step (without active boxes every SPH particle is active). */
+int crm_get_counts(crm_terrain *t, int64_t *n_active, int64_t *n_extended, int64_t *n_bce);
+
+/* Evaluate the rates f(y) at the current state without advancing it (the
+ * first RK2 stage: rebuilds the lists, extrapolates the BCE state and sums the
+ * pairs).  Outputs in insertion order, each nullable: drho (n_sph),
+ * dvel (n_sph*3), dstress (n_sph*6), marker_acc (n_markers*3; every marker),
+ * marker_vel (n_markers*3) and marker_stress (n_markers*6): the extrapolated
+ * marker state.  cap_sph / cap_markers = room in elements of each kind. */
+int crm_eval_rates(crm_terrain *t, int64_t cap_sph, float *drho, float *dvel, float *dstress,
+                   int64_t cap_markers, float *marker_acc, float *marker_vel,
+                   float *marker_stress);
+
+/* The neighbour lists of the last rebuild in CSR form over insertion indices
+ * (SPH particles 0..n_sph-1, then markers n_sph..): offset[n_sph+n_markers+1],
+ * list[nnz] (ascending within a row).  cap = room in list; *nnz receives the
+ * total.  Rows of inactive particles are empty. */
+int crm_get_neighbors(crm_terrain *t, int64_t cap, int64_t *offset, int32_t *list,
+                      int64_t *nnz);
+
+/* Bytes needed by crm_save_state. */
+int crm_state_bytes(crm_terrain *t, size_t *bytes);
+
+/* Checkpoint: copy the complete dynamic state (particles, bodies, step
+ * counter) into a caller device buffer of `cap` bytes; *used receives the
+ * size.  crm_load_state restores it into a terrain built from the same
+ * inputs. */
+int crm_save_state(crm_terrain *t, void *dev_buf, size_t cap, size_t *used);
+int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
+
+/* Per-kernel launch counts and CUDA-event timings of one handle (for
+ * measurement).  Kernel ids 0..CRM_NUM_KERNELS-1, names from crm_kernel_name:
+ * keys, scan, scatter, reorder, neighbors, bce, pair_stage1, pair_stage2,
+ * wrench_partial, body_update, export. */
+#define CRM_NUM_KERNELS 11
+typedef struct crm_profile {
+    int64_t launches[CRM_NUM_KERNELS]; /* kernels enqueued since the last reset */
+    double ms[CRM_NUM_KERNELS];        /* summed event-timed durations (timing on) */
+    int64_t steps;                     /* steps enqueued since the last reset */
+    int64_t rebuilds;                  /* neighbour-list rebuilds since the last reset */
+} crm_profile;
+
+/* Name of kernel id k (static string; "" when out of range). */
+const char *crm_kernel_name(int32_t k);
+
+/* Zero the counters.  timing != 0: from now on every kernel launch is
+ * bracketed by two CUDA events recorded on the handle's stream. */
+int crm_profile_reset(crm_terrain *t, int32_t timing);
+
+/* Synchronise the stream and return the counters (and the summed event
+ * durations of the launches timed since the reset). */
+int crm_profile_read(crm_terrain *t, crm_profile *out);
+
+/* Stateless cell binning of n points (Sec. 3.1 steps 1-3: hash, sort,
+ * cellStart/cellEnd).  All pointers are device pointers.
+ *   xyz        n*3 floats, coordinates relative to the grid origin (m)
+ *   cell_size  edge of a cubic cell (2h in the method), > 0
+ *   dims       grid size in cells (X, Y, Z), each >= 1, product < 2^31
+ *   cell_out   n uint32: c = z (Y X) + y X + x of each point's cell; points
+ *              outside the grid are clamped into the nearest boundary cell
+ *   perm_out   n uint32: the point stored at sorted slot s is perm_out[s];
+ *              the sort is stable (equal cells keep ascending input order)
+ *   cell_start_out  X*Y*Z + 1 uint32: the points of cell c occupy sorted
+ *              slots [cell_start[c], cell_start[c+1]) (cellStart/cellEnd of
+ *              the paper folded into one array)
+ *   scratch    caller buffer of at least crm_bin_scratch_bytes(n, X*Y*Z)
+ *              bytes, 256-byte aligned; its contents are overwritten
+ * Enqueues on `cuda_stream` (NULL = default stream) and returns without
+ * synchronising.  CRM_EINVAL for null pointers, n < 0, n >= 2^31, a
+ * non-positive cell size, a bad grid, or too small a scratch buffer. */
+size_t crm_bin_scratch_bytes(int64_t n, int64_t ncell);
+int crm_bin_points(const float *xyz, int64_t n, float cell_size, const int32_t dims[3],
+                   uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out,
+                   void *scratch, size_t scratch_bytes, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRM_H */

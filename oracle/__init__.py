@@ -81,7 +81,8 @@ def lib():
             L.orc_bce.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, d, d, d, d, d, d, d,
                                   i64, i32, vp, d, d]
             L.orc_rates.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, d, d, d, d, d, d, d,
-                                    i64, i32, vp, d, d, d, d, vp]
+                                    i64, i32, vp, d, d, d, d, vp, vp]
+            L.orc_set_scale_conditioning.argtypes = [C.c_int]
             L.orc_return_map.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, d, d, d]
             L.orc_activity.argtypes = [C.POINTER(Params), C.c_int64, d, C.c_int64, i32, d, d, d, u8]
             L.orc_capacity_policy.restype = C.c_int64
@@ -179,19 +180,27 @@ def bce(params: dict, x, u, sig, rho, xm, umb, amb, off, lst, include=None):
 
 def rates(params: dict, x, u, sig, rho, xm, um, sm, off, lst, integrate=None,
           want_scale: bool = False):
-    """Fluid rates (drho, du, dsig), marker accelerations and optional |term| sums."""
+    """Fluid rates (drho, du, dsig), marker accelerations and optional |term| sums
+    (fluid: 10 per particle; markers: 3 per marker, returned as ``mscale``)."""
     nf, nm = x.shape[0], xm.shape[0]
     drho, du, dsig = np.zeros(nf), np.zeros((nf, 3)), np.zeros((nf, 6))
     macc = np.zeros((max(nm, 1), 3))
     scale = np.zeros((nf, 10)) if want_scale else None
+    mscale = np.zeros((max(nm, 1), 3)) if want_scale else None
     ig = None if integrate is None else _c(integrate, np.uint8)
     P = make_params(params)
     z3 = np.zeros((1, 3))
     lib().orc_rates(C.byref(P), nf, nm, _c(x), _c(u), _c(sig), _c(rho),
                     _c(xm) if nm else z3, _c(um) if nm else z3, _c(sm) if nm else np.zeros((1, 6)),
                     _c(off, np.int64), _c(lst, np.int32) if lst.size else np.zeros(1, np.int32),
-                    _ptr(ig), drho, du, dsig, macc, _ptr(scale))
-    return drho, du, dsig, macc[:nm], scale
+                    _ptr(ig), drho, du, dsig, macc, _ptr(scale), _ptr(mscale))
+    return drho, du, dsig, macc[:nm], scale, (None if mscale is None else mscale[:nm])
+
+
+def set_scale_conditioning(on: bool):
+    """Weight the |term| sums returned with the rates by 1 + kappa(q) (kernel-edge
+    conditioning); affects only the scale outputs, never a rate."""
+    lib().orc_set_scale_conditioning(int(bool(on)))
 
 
 def return_map(params: dict, dt: float, sig_star: np.ndarray, sig_n: Optional[np.ndarray] = None):
@@ -298,8 +307,11 @@ class State:
         xm, umb, amb = self.markers_now()
         um, sm = bce(self.params, self.x, self.u, self.sig, self.rho, xm, umb, amb,
                      self.off, self.lst, self.include)
-        return rates(self.params, self.x, self.u, self.sig, self.rho, xm, um, sm, self.off,
-                     self.lst, self.integrate, want_scale) + (um, sm)
+        drho, du, dsig, macc, scale, mscale = rates(
+            self.params, self.x, self.u, self.sig, self.rho, xm, um, sm, self.off, self.lst,
+            self.integrate, want_scale)
+        self.mscale = mscale   # |term| sums of the marker accelerations (want_scale only)
+        return drho, du, dsig, macc, scale, um, sm
 
 
 def run(scene, n_steps: Optional[int] = None, mode: str = "cells") -> State:

@@ -408,6 +408,22 @@ static int av_factor(const orc_params *p, double cs, double m, const double vij[
     return 1;
 }
 
+/* Scale conditioning for parity tolerances (test helper, no effect on any
+ * rate): when on, every |term_ij| entering `scale` / `mscale` is weighted by
+ * 1 + kappa(q), kappa = |q W''(q) / W'(q)| the condition number of the kernel
+ * derivative, so a term near the 2h edge (kappa = 2q/(2-q)) carries the
+ * amplification a relative perturbation of r (rounding) suffers there. */
+static int g_scale_conditioning = 0;
+void orc_set_scale_conditioning(int on) { g_scale_conditioning = on; }
+
+static double kernel_dw_condition(double r, double h)
+{
+    const double q = r / h;
+    if (q <= 0.0 || q >= 2.0) return 0.0;
+    if (q < 1.0) return fabs((-3.0 + 4.5 * q) / (-3.0 + 2.25 * q));
+    return 2.0 * q / (2.0 - q);
+}
+
 /* Rates of every included fluid particle (Eqs. continuity_dis, momentum_dis and
  * the stress rate above; F2 for continuity and the velocity gradient, F3 for
  * momentum; Sec. 2.2), and the accelerations of the markers (Sec. 2.4: marker
@@ -421,12 +437,14 @@ static int av_factor(const orc_params *p, double cs, double m, const double vij[
  * Markers use their extrapolated velocity and stress (orc_bce).
  * `scale` (nullable; 10 per fluid particle: rho, u x3, sigma x6) receives the
  * absolute sums sum_j |term_ij| of each component, the size against which a
- * single-precision evaluation is judged. */
+ * single-precision evaluation is judged; `mscale` (nullable; 3 per marker) the
+ * same for the marker accelerations. */
 void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
                const double *xf, const double *uf, const double *sf, const double *rf,
                const double *xm, const double *um, const double *sm,
                const int64_t *offset, const int32_t *list, const uint8_t *integrate,
-               double *drho, double *du, double *dsig, double *macc, double *scale)
+               double *drho, double *du, double *dsig, double *macc, double *scale,
+               double *mscale)
 {
     const double h = p->h, m = particle_mass(p), G = shear_modulus(p), K = bulk_modulus(p);
     const double cs = sqrt(K / p->rho0);
@@ -461,6 +479,9 @@ void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
             }
             kernel_grad(rij, h, g);
             const double Vj = m / rhoj;
+            const double cw = g_scale_conditioning
+                ? 1.0 + kernel_dw_condition(sqrt(rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2]), h)
+                : 1.0;
             sym_to_full(si, si3);
             sym_to_full(sj, sj3);
             for (int a = 0; a < 3; ++a)
@@ -474,7 +495,8 @@ void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
                 for (int b = 0; b < 3; ++b) t += Ssum[a][b] * g[b];
                 mom[a] += Vj * t;
                 if (has_av) av[a] += fac * g[a];
-                if (scale) sc[1 + a] += fabs(Vj * t / rhoi) + (has_av ? fabs(fac * g[a]) : 0.0);
+                if (scale || mscale)
+                    sc[1 + a] += cw * (fabs(Vj * t / rhoi) + (has_av ? fabs(fac * g[a]) : 0.0));
             }
             if (is_fluid) {
                 double Lj[3][3], dsj[6];
@@ -484,9 +506,9 @@ void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
                         L[a][b] += Lj[a][b];
                     }
                 if (scale) {
-                    sc[0] += fabs(rhoi * Vj * ug);
+                    sc[0] += cw * fabs(rhoi * Vj * ug);
                     stress_rate(Lj, si, G, K, dsj);
-                    for (int c = 0; c < 6; ++c) sc[4 + c] += fabs(dsj[c]);
+                    for (int c = 0; c < 6; ++c) sc[4 + c] += cw * fabs(dsj[c]);
                 }
             }
         }
@@ -500,6 +522,8 @@ void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
             }
         } else {
             for (int a = 0; a < 3; ++a) macc[3 * (i - nf) + a] = mom[a] / rhoi + av[a];
+            if (mscale)
+                for (int a = 0; a < 3; ++a) mscale[3 * (i - nf) + a] = sc[1 + a];
         }
     }
 }
@@ -645,7 +669,7 @@ void orc_step(const orc_params *p, double dt, int64_t nf, double *x, double *u,
     orc_marker_kinematics(nm, mbody, mxloc, pose, twist, bacc, 0.0, xm, umb, amb);
     orc_bce(p, nf, nm, x, u, sig, rho, xm, umb, amb, offset, list, include, um, sm);
     orc_rates(p, nf, nm, x, u, sig, rho, xm, um, sm, offset, list, integrate, d1, du1, ds1,
-              macc, NULL);
+              macc, NULL, NULL);
     for (int64_t i = 0; i < nf; ++i) {
         const int adv = !integrate || integrate[i];
         const double hd = adv ? 0.5 * dt : 0.0;
@@ -660,7 +684,7 @@ void orc_step(const orc_params *p, double dt, int64_t nf, double *x, double *u,
     orc_marker_kinematics(nm, mbody, mxloc, pose, twist, bacc, 0.5 * dt, xm, umb, amb);
     orc_bce(p, nf, nm, xh, uh, sh, rh, xm, umb, amb, offset, list, include, um, sm);
     orc_rates(p, nf, nm, xh, uh, sh, rh, xm, um, sm, offset, list, integrate, d1, du1, ds1,
-              macc, NULL);
+              macc, NULL, NULL);
     for (int64_t i = 0; i < nf; ++i) {
         const int adv = !integrate || integrate[i];
         if (!adv) { for (int c = 0; c < 6; ++c) sstar[6 * i + c] = sig[6 * i + c]; continue; }

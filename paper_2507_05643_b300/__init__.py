@@ -1,0 +1,330 @@
+"""Python binding of the sm_103a SPH continuum terrain library (libcrm.so).
+
+Argument marshalling only: every step of the particle loop runs in the CUDA
+kernels behind the C ABI of ``include/crm.h``.  If the compiled library is
+missing, importing this package raises ImportError -- there is no fallback.
+
+Names follow the C ABI: :class:`Terrain` wraps ``crm_terrain``;
+:func:`bin_points` wraps the stateless ``crm_bin_points``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcrm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2507_05643_b300.build` "
+                      "(the CUDA library is required; there is no CPU path)")
+
+_lib = C.CDLL(LIB_PATH)
+
+CRM_OK = 0
+STATUS = {0: "CRM_OK", -1: "CRM_EINVAL", -2: "CRM_ENOMEM", -3: "CRM_ECAPACITY",
+          -4: "CRM_EESCAPED", -5: "CRM_ENONFINITE", -6: "CRM_ETIMEOUT", -7: "CRM_ECUDA",
+          -8: "CRM_ESTATE"}
+AV_NONE, AV_BILATERAL, AV_UNILATERAL = 0, 1, 2
+
+
+class CrmError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{STATUS.get(code, code)}: {message}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("rho0", C.c_double), ("E", C.c_double), ("nu", C.c_double),
+                ("mu_s", C.c_double), ("mu_2", C.c_double), ("I0", C.c_double),
+                ("grain_d", C.c_double), ("cohesion", C.c_double),
+                ("d0", C.c_double), ("h", C.c_double),
+                ("kernel", C.c_int32), ("av_mode", C.c_int32),
+                ("av_gamma", C.c_double), ("av_xi2_over_h2", C.c_double),
+                ("gravity", C.c_double * 3),
+                ("ps_freq", C.c_int32), ("max_neighbors", C.c_int32),
+                ("domain_min", C.c_double * 3), ("domain_max", C.c_double * 3),
+                ("growth", C.c_double), ("shrink_ratio", C.c_double),
+                ("shrink_interval", C.c_int32), ("reserved", C.c_int32)]
+
+
+_d = np.ctypeslib.ndpointer(np.float64, flags="C")
+_f = np.ctypeslib.ndpointer(np.float32, flags="C")
+_vp, _i64, _i32 = C.c_void_p, C.c_int64, C.c_int32
+_P = C.POINTER(Params)
+_T = C.c_void_p
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("crm_version", C.c_int, [])
+_sig("crm_status_string", C.c_char_p, [C.c_int])
+_sig("crm_default_params", None, [_P])
+_sig("crm_create", C.c_int, [_P, _vp, C.POINTER(_T)])
+_sig("crm_destroy", C.c_int, [_T])
+_sig("crm_last_error", C.c_char_p, [_T])
+_sig("crm_add_sph", C.c_int, [_T, _i64, _vp, _vp, _vp, _vp])
+_sig("crm_add_fixed_bce", C.c_int, [_T, _i64, _vp])
+_sig("crm_add_rigid_body", C.c_int, [_T, _i64, _vp, _vp, _vp, C.c_double, _i32,
+                                     C.POINTER(_i32)])
+_sig("crm_set_body_motion", C.c_int, [_T, _i32, _vp, _vp])
+_sig("crm_get_body_state", C.c_int, [_T, _i32, _vp, _vp])
+_sig("crm_add_active_box", C.c_int, [_T, _i32, _vp, _vp, C.c_double])
+_sig("crm_step", C.c_int, [_T, C.c_double, _i32])
+_sig("crm_sync", C.c_int, [_T])
+_sig("crm_get_particles", C.c_int, [_T, _i64, _vp, _vp, _vp, _vp, C.POINTER(_i64)])
+_sig("crm_get_body_wrench", C.c_int, [_T, _i32, _vp, _vp])
+_sig("crm_get_counts", C.c_int, [_T, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)])
+_sig("crm_eval_rates", C.c_int, [_T, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp])
+_sig("crm_get_neighbors", C.c_int, [_T, _i64, _vp, _vp, C.POINTER(_i64)])
+_sig("crm_state_bytes", C.c_int, [_T, C.POINTER(C.c_size_t)])
+_sig("crm_save_state", C.c_int, [_T, _vp, C.c_size_t, C.POINTER(C.c_size_t)])
+_sig("crm_load_state", C.c_int, [_T, _vp, C.c_size_t])
+_sig("crm_bin_scratch_bytes", C.c_size_t, [_i64, _i64])
+_sig("crm_bin_points", C.c_int, [_vp, _i64, C.c_float, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp])
+
+NUM_KERNELS = 11
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * NUM_KERNELS), ("ms", C.c_double * NUM_KERNELS),
+                ("steps", C.c_int64), ("rebuilds", C.c_int64)]
+
+
+_sig("crm_kernel_name", C.c_char_p, [_i32])
+_sig("crm_profile_reset", C.c_int, [_T, _i32])
+_sig("crm_profile_read", C.c_int, [_T, C.POINTER(Profile)])
+KERNEL_NAMES = tuple(_lib.crm_kernel_name(k).decode() for k in range(NUM_KERNELS))
+
+# Every symbol include/crm.h declares.
+EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create", "crm_destroy",
+           "crm_last_error", "crm_add_sph", "crm_add_fixed_bce", "crm_add_rigid_body",
+           "crm_set_body_motion", "crm_get_body_state", "crm_add_active_box", "crm_step",
+           "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_counts",
+           "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
+           "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
+           "crm_profile_reset", "crm_profile_read")
+
+
+def lib():
+    return _lib
+
+
+def version() -> int:
+    return int(_lib.crm_version())
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def default_params() -> Params:
+    p = Params()
+    _lib.crm_default_params(C.byref(p))
+    return p
+
+
+def params_from_dict(d: dict, domain_min, domain_max) -> Params:
+    """crm_params from a scene's parameter dictionary and grid extent."""
+    p = default_params()
+    for k in ("rho0", "E", "nu", "mu_s", "mu_2", "I0", "grain_d", "cohesion", "d0", "h",
+              "av_gamma", "av_xi2_over_h2"):
+        if k in d and d[k] is not None:
+            setattr(p, k, float(d[k]))
+    for k in ("av_mode", "ps_freq", "max_neighbors"):
+        if k in d:
+            setattr(p, k, int(d[k]))
+    for k in range(3):
+        p.gravity[k] = float(d["gravity"][k])
+        p.domain_min[k] = float(domain_min[k])
+        p.domain_max[k] = float(domain_max[k])
+    return p
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+class Terrain:
+    """Owner of one ``crm_terrain`` handle."""
+
+    def __init__(self, params: Params, stream=None):
+        self._h = _T()
+        self._stream = stream
+        rc = _lib.crm_create(C.byref(params), _stream_handle(stream), C.byref(self._h))
+        if rc != CRM_OK:
+            raise CrmError(rc, "crm_create rejected the parameters")
+        self.params = params
+        self.n_sph = 0
+        self.n_markers = 0
+        self.n_bodies = 0
+
+    # ------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != CRM_OK:
+            msg = _lib.crm_last_error(self._h)
+            raise CrmError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if self._h:
+            _lib.crm_destroy(self._h)
+            self._h = _T()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def add_sph(self, xyz, vel=None, stress6=None, rho=None):
+        xyz = _c(xyz).reshape(-1, 3)
+        n = xyz.shape[0]
+        arrs = [None if a is None else _c(a) for a in (vel, stress6, rho)]
+        self._check(_lib.crm_add_sph(self._h, n, _ptr(xyz), *[_ptr(a) for a in arrs]))
+        self.n_sph += n
+
+    def add_fixed_bce(self, xyz):
+        xyz = _c(xyz).reshape(-1, 3)
+        self._check(_lib.crm_add_fixed_bce(self._h, xyz.shape[0], _ptr(xyz)))
+        self.n_markers += xyz.shape[0]
+
+    def add_rigid_body(self, markers_local, pose, twist, mass: float, dof_mask: int) -> int:
+        ml = _c(markers_local).reshape(-1, 3)
+        bid = _i32()
+        self._check(_lib.crm_add_rigid_body(self._h, ml.shape[0], _ptr(ml), _ptr(_c(pose)),
+                                            _ptr(_c(twist)), float(mass), int(dof_mask),
+                                            C.byref(bid)))
+        self.n_markers += ml.shape[0]
+        self.n_bodies += 1
+        return int(bid.value)
+
+    def add_active_box(self, body: int, half_extents, offset, t_delay: float = 0.0):
+        self._check(_lib.crm_add_active_box(self._h, int(body), _ptr(_c(half_extents)),
+                                            _ptr(_c(offset)), float(t_delay)))
+
+    def set_body_motion(self, body: int, pose, twist):
+        self._check(_lib.crm_set_body_motion(self._h, int(body), _ptr(_c(pose)), _ptr(_c(twist))))
+
+    def body_state(self, body: int) -> Tuple[np.ndarray, np.ndarray]:
+        pose, twist = np.zeros(7), np.zeros(6)
+        self._check(_lib.crm_get_body_state(self._h, int(body), _ptr(pose), _ptr(twist)))
+        return pose, twist
+
+    # ------------------------------------------------------------------
+    def step(self, dt: float, n_steps: int = 1):
+        self._check(_lib.crm_step(self._h, float(dt), int(n_steps)))
+
+    def sync(self):
+        self._check(_lib.crm_sync(self._h))
+
+    def particles(self):
+        n = self.n_sph
+        xyz, vel = np.zeros((n, 3)), np.zeros((n, 3), np.float32)
+        sig, rho = np.zeros((n, 6), np.float32), np.zeros(n, np.float32)
+        nout = _i64()
+        self._check(_lib.crm_get_particles(self._h, n, _ptr(xyz), _ptr(vel), _ptr(sig), _ptr(rho),
+                                           C.byref(nout)))
+        return xyz, vel, sig, rho
+
+    def body_wrench(self, body: int) -> Tuple[np.ndarray, np.ndarray]:
+        f, t = np.zeros(3), np.zeros(3)
+        self._check(_lib.crm_get_body_wrench(self._h, int(body), _ptr(f), _ptr(t)))
+        return f, t
+
+    def counts(self) -> Tuple[int, int, int]:
+        a, e, b = _i64(), _i64(), _i64()
+        self._check(_lib.crm_get_counts(self._h, C.byref(a), C.byref(e), C.byref(b)))
+        return int(a.value), int(e.value), int(b.value)
+
+    def eval_rates(self):
+        """(drho, du, dsig, marker_acc, marker_vel, marker_sig) at the current state."""
+        n, m = self.n_sph, self.n_markers
+        drho, du, ds = np.zeros(n, np.float32), np.zeros((n, 3), np.float32), np.zeros((n, 6), np.float32)
+        ma, mv, ms = (np.zeros((m, 3), np.float32), np.zeros((m, 3), np.float32),
+                      np.zeros((m, 6), np.float32))
+        self._check(_lib.crm_eval_rates(self._h, n, _ptr(drho), _ptr(du), _ptr(ds), m, _ptr(ma),
+                                        _ptr(mv), _ptr(ms)))
+        return drho, du, ds, ma, mv, ms
+
+    def neighbors(self) -> Tuple[np.ndarray, np.ndarray]:
+        n = self.n_sph + self.n_markers
+        off = np.zeros(n + 1, np.int64)
+        nnz = _i64()
+        self._check(_lib.crm_get_neighbors(self._h, 0, _ptr(off), None, C.byref(nnz)))
+        lst = np.zeros(max(int(nnz.value), 1), np.int32)
+        self._check(_lib.crm_get_neighbors(self._h, lst.size, _ptr(off), _ptr(lst), C.byref(nnz)))
+        return off, lst[:int(nnz.value)]
+
+    def profile_reset(self, timing: bool = False):
+        self._check(_lib.crm_profile_reset(self._h, int(bool(timing))))
+
+    def profile(self) -> dict:
+        """{'launches': {name: n}, 'ms': {name: ms}, 'steps': n, 'rebuilds': n}."""
+        pr = Profile()
+        self._check(_lib.crm_profile_read(self._h, C.byref(pr)))
+        return {"launches": {KERNEL_NAMES[k]: int(pr.launches[k]) for k in range(NUM_KERNELS)},
+                "ms": {KERNEL_NAMES[k]: float(pr.ms[k]) for k in range(NUM_KERNELS)},
+                "steps": int(pr.steps), "rebuilds": int(pr.rebuilds)}
+
+    def state_bytes(self) -> int:
+        b = C.c_size_t()
+        self._check(_lib.crm_state_bytes(self._h, C.byref(b)))
+        return int(b.value)
+
+    def save_state(self, dev_ptr: int, cap: int) -> int:
+        used = C.c_size_t()
+        self._check(_lib.crm_save_state(self._h, C.c_void_p(dev_ptr), cap, C.byref(used)))
+        return int(used.value)
+
+    def load_state(self, dev_ptr: int, used: int):
+        self._check(_lib.crm_load_state(self._h, C.c_void_p(dev_ptr), used))
+
+
+def from_scene(scene, stream=None, **param_over) -> Terrain:
+    """Terrain holding a ``scenes.Scene``: its SPH particles, fixed walls, bodies
+    and active boxes, with the scene's constants (overridable by keyword)."""
+    d = dict(scene.params)
+    d.update(param_over)
+    t = Terrain(params_from_dict(d, scene.domain_min, scene.domain_max), stream)
+    t.add_sph(scene.x, scene.u, scene.sig, scene.rho)
+    if scene.fixed.shape[0]:
+        t.add_fixed_bce(scene.fixed)
+    for b in scene.bodies:
+        t.add_rigid_body(b.markers_local, b.pose, b.twist, b.mass, b.dof_mask)
+    for bx in scene.boxes:
+        t.add_active_box(bx.body, bx.half_extents, bx.offset, scene.t_delay)
+    return t
+
+
+def bin_points(xyz_ptr: int, n: int, cell_size: float, dims, cell_ptr: int, perm_ptr: int,
+               start_ptr: int, scratch_ptr: int, scratch_bytes: int, stream=None):
+    """crm_bin_points on device pointers (e.g. torch tensors' data_ptr())."""
+    d = (C.c_int32 * 3)(*[int(v) for v in dims])
+    rc = _lib.crm_bin_points(C.c_void_p(xyz_ptr), int(n), float(cell_size), d,
+                             C.c_void_p(cell_ptr), C.c_void_p(perm_ptr), C.c_void_p(start_ptr),
+                             C.c_void_p(scratch_ptr), int(scratch_bytes),
+                             _stream_handle(stream))
+    if rc != CRM_OK:
+        raise CrmError(rc, "crm_bin_points rejected its arguments")
+
+
+def bin_scratch_bytes(n: int, ncell: int) -> int:
+    return int(_lib.crm_bin_scratch_bytes(int(n), int(ncell)))

@@ -1,0 +1,434 @@
+// crm_bin.cu -- cell binning and neighbour lists (Sec. 3.1, Alg. 1).
+//
+// Binning is a counting sort over cells rather than a comparison or radix
+// sort: the keys are cell ids, so one pass of per-key arrival ranks (atomic),
+// one exclusive scan and one scatter sort the particles, and the scan of the
+// per-cell counts IS the cellStart array (cellEnd[c] = cellStart[c + 1]).
+// The atomic ranks make the arrival order within a cell nondeterministic; a
+// fix-up pass re-ranks every element by its input index inside its cell, so
+// the result equals a stable sort by (cell, input index) on every run.
+#include "crm_internal.cuh"
+
+namespace crm {
+
+// ---------------------------------------------------------------------------
+// Exclusive scan, single pass with decoupled look-back.  Tile status words:
+// high half = (epoch << 2) | state, low half = value; state 1 = tile
+// aggregate, 2 = inclusive prefix.  Tiles are numbered in launch order by a
+// ticket, so every tile waits only on tiles that are already running; each
+// wait is bounded and sets ERR_TIMEOUT instead of spinning forever.  The last
+// tile to finish resets the ticket and advances the epoch, so the status
+// words never need clearing (a zeroed word has state 0 and is never valid).
+namespace {
+constexpr uint32_t kAgg = 1u, kIncl = 2u;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ int pad(int k) { return k + (k >> 5); }
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(uint32_t *__restrict__ count, uint32_t *__restrict__ start, int64_t n,
+       unsigned long long *status, uint32_t *ctr, int64_t n_tiles, int *err)
+{
+    __shared__ uint32_t s_items[kScanTile + kScanTile / 32];
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_tile, s_epoch, s_prefix;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
+        s_tile = atomicAdd(&ctr[0], 1u);
+        s_epoch = (((volatile uint32_t *)ctr)[1] + 1u) & 0x3FFFFFFFu;
+    }
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const uint32_t epoch = s_epoch;
+    const int64_t base = tile * kScanTile;
+    for (int k = t; k < kScanTile; k += kScanThreads) {
+        const int64_t g = base + k;
+        s_items[pad(k)] = g < n ? count[g] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = s_items[pad(t * kScanItems + i)];
+        sum += v[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = incl - sum + (warp > 0 ? s_warp[warp - 1] : 0u);
+    const uint32_t agg = s_warp[kScanThreads / 32 - 1];
+    if (t == 0) {
+        uint32_t prefix = 0;
+        if (tile > 0) {
+            atomicExch(&status[tile],
+                       ((unsigned long long)((epoch << 2) | kAgg) << 32) | agg);
+            int64_t j = tile - 1;
+            int spins = 0;
+            while (true) {
+                const unsigned long long w = ((volatile unsigned long long *)status)[j];
+                const uint32_t hi = (uint32_t)(w >> 32);
+                const uint32_t st = hi & 3u;
+                if (st != 0u && (hi >> 2) == epoch) {
+                    prefix += (uint32_t)w;
+                    if (st == kIncl) break;
+                    --j;
+                    spins = 0;
+                } else if (++spins > kSpinLimit) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    break;
+                } else {
+                    __nanosleep(32);
+                }
+            }
+        }
+        atomicExch(&status[tile],
+                   ((unsigned long long)((epoch << 2) | kIncl) << 32) | (prefix + agg));
+        s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t run = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        s_items[pad(t * kScanItems + i)] = run;
+        run += v[i];
+    }
+    __syncthreads();
+    for (int k = t; k < kScanTile; k += kScanThreads) {
+        const int64_t g = base + k;
+        if (g < n) {
+            start[g] = s_items[pad(k)];
+            count[g] = 0u;
+        }
+    }
+    if (t == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr[2], 1u) == (uint32_t)(n_tiles - 1)) {
+            ctr[0] = 0u;
+            ctr[2] = 0u;
+            __threadfence();
+            atomicAdd(&ctr[1], 1u);
+        }
+    }
+}
+}  // namespace
+
+void launch_scan_reset(uint32_t *count, uint32_t *start, int64_t n, const SortScratch &s,
+                       int *err, cudaStream_t st)
+{
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    k_scan<<<(unsigned)tiles, kScanThreads, 0, st>>>(count, start, n, s.tile_status, s.ctr,
+                                                     tiles, err);
+}
+
+// ---------------------------------------------------------------------------
+// Counting-sort passes shared by the terrain and the stateless entry point.
+namespace {
+
+// slot of element i in the cell-sorted order before the stable fix-up
+__global__ void k_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ rank,
+                          const uint32_t *__restrict__ start, uint32_t *__restrict__ tmp,
+                          int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tmp[start[keys[i]] + rank[i]] = (uint32_t)i;
+}
+
+// Final slot of the element that k_scatter put at slot s: its rank by input
+// index among the elements of the same key.
+__device__ __forceinline__ uint32_t stable_slot(const uint32_t *__restrict__ keys,
+                                                const uint32_t *__restrict__ start,
+                                                const uint32_t *__restrict__ tmp, uint32_t i)
+{
+    const uint32_t key = keys[i];
+    const uint32_t b = start[key], e = start[key + 1];
+    uint32_t r = 0;
+    for (uint32_t u = b; u < e; ++u) r += tmp[u] < i ? 1u : 0u;
+    return b + r;
+}
+
+__global__ void k_perm(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ start,
+                       const uint32_t *__restrict__ tmp, uint32_t *__restrict__ perm, int64_t n)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t i = tmp[s];
+    perm[stable_slot(keys, start, tmp, i)] = i;
+}
+
+// H3 of the stateless call: cell of each point (clamped into the grid) and its
+// arrival rank within the cell.
+__global__ void k_hash_points(const float *__restrict__ xyz, int64_t n, float inv_cell, int X,
+                              int Y, int Z, uint32_t *__restrict__ cell,
+                              uint32_t *__restrict__ rank, uint32_t *__restrict__ count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    int ix = (int)floorf(x * inv_cell), iy = (int)floorf(y * inv_cell),
+        iz = (int)floorf(z * inv_cell);
+    ix = min(max(ix, 0), X - 1);
+    iy = min(max(iy, 0), Y - 1);
+    iz = min(max(iz, 0), Z - 1);
+    const uint32_t c = ((uint32_t)iz * (uint32_t)Y + (uint32_t)iy) * (uint32_t)X + (uint32_t)ix;
+    cell[i] = c;
+    rank[i] = atomicAdd(&count[c], 1u);
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Terrain rebuild kernels.
+
+// Key generation (Sec. 3.1 step 1, calcGridPos / calcGridID).  Fluid particles
+// are re-homed into the cell their offset now lies in; markers get their
+// kinematic position at the start of the step.  The key is the cell index
+// inside the working window, offset by M for markers, so one counting sort
+// yields fluid slots [0, nF) then marker slots [nF, N), each cell-sorted.
+__global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__restrict__ pid,
+                       const double *__restrict__ mloc, const int *__restrict__ mbody,
+                       const BodyDev *__restrict__ bodies, uint32_t *__restrict__ keys,
+                       uint32_t *__restrict__ rank, uint32_t *__restrict__ count,
+                       int *__restrict__ err, int n_fluid_total)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    float4 ps = pos[i];
+    int ix, iy, iz;
+    uint32_t seg;
+    bool bad = false;
+    if (i < p.nF) {
+        seg = 0;
+        decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
+        if (!(isfinite(ps.x) && isfinite(ps.y) && isfinite(ps.z))) {
+            atomicOr(err, ERR_NONFINITE);
+            ps.x = ps.y = ps.z = 0.0f;
+        }
+        const float inv = 1.0f / p.cell;
+        const int fx = (int)floorf(ps.x * inv), fy = (int)floorf(ps.y * inv),
+                  fz = (int)floorf(ps.z * inv);
+        if (fx | fy | fz) {
+            ix += fx; iy += fy; iz += fz;
+            ps.x -= (float)fx * p.cell;
+            ps.y -= (float)fy * p.cell;
+            ps.z -= (float)fz * p.cell;
+        }
+    } else {
+        seg = 1;
+        const int mi = (int)pid[i] - n_fluid_total;
+        double x[3];
+        float u[3], a[3], arm[3];
+        marker_state(bodies, mbody[mi], mloc + 3 * (int64_t)mi, 0.0, x, u, a, arm);
+        const double fx = floor((x[0] - p.dmin_x) / p.cell_d);
+        const double fy = floor((x[1] - p.dmin_y) / p.cell_d);
+        const double fz = floor((x[2] - p.dmin_z) / p.cell_d);
+        ix = (int)fmin(fmax(fx, -1.0), (double)p.GX);
+        iy = (int)fmin(fmax(fy, -1.0), (double)p.GY);
+        iz = (int)fmin(fmax(fz, -1.0), (double)p.GZ);
+        ps.x = (float)(x[0] - (p.dmin_x + ix * p.cell_d));
+        ps.y = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
+        ps.z = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
+    }
+    int lx = ix - p.wx0, ly = iy - p.wy0, lz = iz - p.wz0;
+    if (lx < 0 || ly < 0 || lz < 0 || lx >= p.WX || ly >= p.WY || lz >= p.WZ) {
+        bad = true;
+        lx = min(max(lx, 0), p.WX - 1);
+        ly = min(max(ly, 0), p.WY - 1);
+        lz = min(max(lz, 0), p.WZ - 1);
+        ix = lx + p.wx0; iy = ly + p.wy0; iz = lz + p.wz0;
+    }
+    if (bad) atomicOr(err, ERR_ESCAPED);
+    const uint32_t key = seg * p.M + ((uint32_t)lz * (uint32_t)p.WY + (uint32_t)ly) * (uint32_t)p.WX
+                         + (uint32_t)lx;
+    keys[i] = key;
+    rank[i] = atomicAdd(&count[key], 1u);
+    ps.w = __uint_as_float(encode_cell(ix, iy, iz, p));
+    pos[i] = ps;
+}
+
+// Stable fix-up + gather of every particle array into sorted order (H4).
+__global__ void k_reorder(int n, const uint32_t *__restrict__ keys,
+                          const uint32_t *__restrict__ start, const uint32_t *__restrict__ tmp,
+                          StageArrays src, const uint32_t *__restrict__ pid_src, StageArrays dst,
+                          uint32_t *__restrict__ pid_dst)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t i = tmp[s];
+    const uint32_t d = stable_slot(keys, start, tmp, i);
+    dst.pos[d] = src.pos[i];
+    dst.vel[d] = src.vel[i];
+    dst.sA[d] = src.sA[i];
+    dst.sB[d] = src.sB[i];
+    pid_dst[d] = pid_src[i];
+}
+
+// Neighbour lists (Alg. 1): for particle s scan the 27 cells around its home
+// cell -- 9 runs of 3 consecutive cells in x, which are contiguous in the
+// sorted order -- and keep j when |x_s - x_j| < 2h (strict).  Fluid particles
+// take fluid and marker neighbours, markers take fluid neighbours only.  The
+// list is an ELL table nbr[k * ell + s] (coalesced across a warp); each entry
+// is j | code << 26 with code = (dx+1) | (dy+1) << 2 | (dz+1) << 4, the cell
+// offset of j relative to s, so the pair kernels rebuild x_s - x_j from the
+// cell-relative offsets without decoding cell ids.
+__global__ void __launch_bounds__(kBlock)
+k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restrict__ start,
+            uint32_t *__restrict__ nbr, uint32_t *__restrict__ nnb, int *__restrict__ err)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.N) return;
+    const float4 ps = pos[s];
+    int ix, iy, iz;
+    decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
+    const int lx = ix - p.wx0, ly = iy - p.wy0, lz = iz - p.wz0;
+    const int nseg = s < p.nF ? 2 : 1;
+    const int xa = max(lx - 1, 0), xb = min(lx + 1, p.WX - 1);
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int lz2 = lz + dz;
+        if (lz2 < 0 || lz2 >= p.WZ) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int ly2 = ly + dy;
+            if (ly2 < 0 || ly2 >= p.WY) continue;
+            const uint32_t rowkey = ((uint32_t)lz2 * (uint32_t)p.WY + (uint32_t)ly2) * (uint32_t)p.WX;
+            const uint32_t rowg = ((uint32_t)(iz + dz) * (uint32_t)p.GY + (uint32_t)(iy + dy))
+                                  * (uint32_t)p.GX;
+            const float sy = ps.y - (float)dy * p.cell, sz = ps.z - (float)dz * p.cell;
+            const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
+            for (int seg = 0; seg < nseg; ++seg) {
+                const uint32_t kb = seg * p.M + rowkey;
+                const uint32_t jb = start[kb + xa], je = start[kb + xb + 1];
+                for (uint32_t j = jb; j < je; ++j) {
+                    const float4 pj = pos[j];
+                    const int dxc = (int)(__float_as_uint(pj.w) - rowg) - ix;
+                    const float rx = ps.x - pj.x - (float)dxc * p.cell;
+                    const float ry = sy - pj.y, rz = sz - pj.z;
+                    const float r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 < p.four_h2 && j != (uint32_t)s) {
+                        if (cnt < p.maxnb)
+                            nbr[(size_t)cnt * p.ell + s] = j | (((uint32_t)(dxc + 1) | codeyz) << kIndexBits);
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    if (cnt > p.maxnb) atomicOr(err, ERR_CAPACITY);
+    nnb[s] = (uint32_t)min(cnt, p.maxnb);
+}
+
+// Host launchers of the terrain rebuild, one kernel each.
+void launch_keys(const DevParams &p, StageArrays cur, const uint32_t *pid_cur, const double *mloc,
+                 const int *mbody, const BodyDev *bodies, const SortScratch &s, int *err,
+                 int n_fluid_total, cudaStream_t st)
+{
+    k_keys<<<grid_for(p.N), kBlock, 0, st>>>(p, cur.pos, pid_cur, mloc, mbody, bodies, s.keys,
+                                             s.rank, s.count, err, n_fluid_total);
+}
+
+void launch_scatter(const DevParams &p, const SortScratch &s, const uint32_t *start,
+                    cudaStream_t st)
+{
+    k_scatter<<<grid_for(p.N), kBlock, 0, st>>>(s.keys, s.rank, start, s.tmp, p.N);
+}
+
+void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *start,
+                    StageArrays cur, const uint32_t *pid_cur, StageArrays nxt, uint32_t *pid_nxt,
+                    cudaStream_t st)
+{
+    k_reorder<<<grid_for(p.N), kBlock, 0, st>>>(p.N, s.keys, start, s.tmp, cur, pid_cur, nxt,
+                                                pid_nxt);
+}
+
+void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
+                      uint32_t *nnb, int *err, cudaStream_t st)
+{
+    k_neighbors<<<grid_for(p.N), kBlock, 0, st>>>(p, pos, start, nbr, nnb, err);
+}
+
+}  // namespace crm
+
+// ---------------------------------------------------------------------------
+// Stateless binning entry point (include/crm.h).
+namespace {
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct BinLayout {
+    size_t rank, tmp, count, status, ctr, total;
+};
+
+BinLayout bin_layout(int64_t n, int64_t ncell)
+{
+    BinLayout L;
+    const int64_t nk = ncell + 1;
+    const int64_t tiles = (nk + crm::kScanTile - 1) / crm::kScanTile;
+    size_t o = 0;
+    L.rank = o;   o += align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    L.tmp = o;    o += align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    L.count = o;  o += align256(sizeof(uint32_t) * (size_t)nk);
+    L.status = o; o += align256(sizeof(unsigned long long) * (size_t)tiles);
+    L.ctr = o;    o += align256(sizeof(uint32_t) * 4);
+    L.total = o;
+    return L;
+}
+}  // namespace
+
+extern "C" size_t crm_bin_scratch_bytes(int64_t n, int64_t ncell)
+{
+    if (n < 0 || ncell < 1) return 0;
+    return bin_layout(n, ncell).total;
+}
+
+extern "C" int crm_bin_points(const float *xyz, int64_t n, float cell_size, const int32_t dims[3],
+                              uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out,
+                              void *scratch, size_t scratch_bytes, void *cuda_stream)
+{
+    if (!dims || !cell_start_out || !scratch || n < 0 || n >= (int64_t(1) << 31)) return CRM_EINVAL;
+    if (n > 0 && (!xyz || !cell_out || !perm_out)) return CRM_EINVAL;
+    if (!(cell_size > 0.0f) || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return CRM_EINVAL;
+    const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
+    if (ncell >= (int64_t(1) << 31)) return CRM_EINVAL;
+    if (((uintptr_t)scratch & 255u) != 0) return CRM_EINVAL;
+    const BinLayout L = bin_layout(n, ncell);
+    if (scratch_bytes < L.total) return CRM_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    char *base = (char *)scratch;
+    crm::SortScratch s;
+    s.keys = cell_out;
+    s.rank = (uint32_t *)(base + L.rank);
+    s.tmp = (uint32_t *)(base + L.tmp);
+    s.count = (uint32_t *)(base + L.count);
+    s.tile_status = (unsigned long long *)(base + L.status);
+    s.ctr = (uint32_t *)(base + L.ctr);
+    s.n_tiles = (ncell + 1 + crm::kScanTile - 1) / crm::kScanTile;
+    // counts, look-back words and counters start from zero on every call (the
+    // scratch content is the caller's); ctr[3] collects device-side failures
+    if (cudaMemsetAsync(base + L.count, 0, L.total - L.count, st) != cudaSuccess) return CRM_ECUDA;
+    int *err = (int *)(s.ctr + 3);
+    if (n > 0)
+        crm::k_hash_points<<<crm::grid_for(n), crm::kBlock, 0, st>>>(
+            xyz, n, 1.0f / cell_size, dims[0], dims[1], dims[2], s.keys, s.rank, s.count);
+    crm::launch_scan_reset(s.count, cell_start_out, ncell + 1, s, err, st);
+    if (n > 0) {
+        crm::k_scatter<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, s.rank, cell_start_out,
+                                                                 s.tmp, n);
+        crm::k_perm<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, cell_start_out, s.tmp,
+                                                              perm_out, n);
+    }
+    return cudaGetLastError() == cudaSuccess ? CRM_OK : CRM_ECUDA;
+}

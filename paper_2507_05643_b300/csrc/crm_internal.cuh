@@ -1,0 +1,244 @@
+// crm_internal.cuh -- internal types and device helpers of the sm_103a SPH
+// terrain library.  Everything here is private to the library; the public
+// surface is include/crm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/crm.h"
+
+namespace crm {
+
+// Device-side failure bits, latched with atomicOr into one word per handle.
+enum : int {
+    ERR_CAPACITY = 1,   // a neighbour list overflowed max_neighbors
+    ERR_ESCAPED = 2,    // a particle left the grid window
+    ERR_NONFINITE = 4,  // non-finite state after an update
+    ERR_TIMEOUT = 8,    // a bounded spin-wait gave up
+};
+
+constexpr int kMaxBodies = 16;
+constexpr uint32_t kIndexBits = 26;                 // neighbour entry: j | code << 26
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+constexpr int kBlock = 256;
+
+// Constants of one terrain, passed by value to every kernel.  Single
+// precision for the particle arithmetic, double for the grid origin and the
+// rigid-body kinematics.
+struct DevParams {
+    // kernel and material (Sec. 2.1-2.3)
+    float h, inv_h, four_h2, cell;        // cell = 2h (Sec. 3.1)
+    float kw, kdw;                        // 1/(pi h^3), 1/(pi h^4)
+    float m, rho0, G, K;                  // particle mass rho0 d0^3, moduli
+    float av_c, xi2;                      // gamma_a h c_s m, xi^2
+    int av_mode;
+    float gx, gy, gz;
+    float mu_s, mu_2, I0, grain_d, cohesion;
+    // global grid: cell coordinates (ix, iy, iz), c = (iz GY + iy) GX + ix
+    int GX, GY, GZ;
+    // working window of the sort, in global cell coordinates
+    int wx0, wy0, wz0, WX, WY, WZ;
+    uint32_t M;                           // WX * WY * WZ
+    double dmin_x, dmin_y, dmin_z, cell_d;
+    // particle set (sorted order: fluid slots [0, nF), markers [nF, N))
+    int nF, nM, N;
+    int maxnb;
+    uint32_t ell;                         // stride of the neighbour table (>= N)
+    int n_bodies;
+};
+
+// Rigid body state on the device (FP64, Sec. 2.4 FSI exchange).
+struct BodyDev {
+    double pose[7];     // x, y, z, qw, qx, qy, qz
+    double twist[6];    // v (world), w (world)
+    double acc[3];      // linear acceleration of the centre at the last update
+    double wrench[6];   // force, torque about the centre (last step)
+    double mass;
+    int dof;
+    int pad;
+};
+
+// Stage arrays: the state every pair kernel gathers neighbours from.
+struct StageArrays {
+    float4 *pos;   // offset from the home cell corner (x, y, z), home cell id bits
+    float4 *vel;   // u (x, y, z), rho
+    float4 *sA;    // sigma xx, yy, zz, xy
+    float2 *sB;    // sigma xz, yz
+};
+
+// ---------------------------------------------------------------------------
+// Cubic spline (Monaghan M4), 3-D normalisation 1/(pi h^3), support 2h.
+__device__ __forceinline__ float kernel_w(float q, const DevParams &p)
+{
+    if (q < 1.0f) return p.kw * (1.0f + q * q * (0.75f * q - 1.5f));
+    const float t = 2.0f - q;
+    return q < 2.0f ? 0.25f * p.kw * t * t * t : 0.0f;
+}
+
+// (dW/dr) / r; q < 2 is the caller's guarantee.
+__device__ __forceinline__ float kernel_dw_over_r(float q, float rinv, const DevParams &p)
+{
+    float d;
+    if (q < 1.0f) {
+        d = p.kdw * q * (2.25f * q - 3.0f);
+    } else {
+        const float t = 2.0f - q;
+        d = -0.75f * p.kdw * t * t;
+    }
+    return d * rinv;
+}
+
+__device__ __forceinline__ void decode_cell(uint32_t c, const DevParams &p, int &ix, int &iy,
+                                            int &iz)
+{
+    ix = (int)(c % (uint32_t)p.GX);
+    const uint32_t t = c / (uint32_t)p.GX;
+    iy = (int)(t % (uint32_t)p.GY);
+    iz = (int)(t / (uint32_t)p.GY);
+}
+
+__device__ __forceinline__ uint32_t encode_cell(int ix, int iy, int iz, const DevParams &p)
+{
+    return ((uint32_t)iz * (uint32_t)p.GY + (uint32_t)iy) * (uint32_t)p.GX + (uint32_t)ix;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 rigid-body kinematics.  The pose at stage offset tau is the pose
+// advanced by the current twist held constant.
+__device__ __forceinline__ void qmul(const double a[4], const double b[4], double o[4])
+{
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+__device__ __forceinline__ void qrot(const double q[4], const double v[3], double o[3])
+{
+    // o = v + 2 qv x (qv x v + w v)
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double tx = y * v[2] - z * v[1] + w * v[0];
+    const double ty = z * v[0] - x * v[2] + w * v[1];
+    const double tz = x * v[1] - y * v[0] + w * v[2];
+    o[0] = v[0] + 2.0 * (y * tz - z * ty);
+    o[1] = v[1] + 2.0 * (z * tx - x * tz);
+    o[2] = v[2] + 2.0 * (x * ty - y * tx);
+}
+
+__device__ __forceinline__ void qadvance(const double q[4], const double w[3], double tau,
+                                         double o[4])
+{
+    const double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double dq[4] = {1.0, 0.0, 0.0, 0.0};
+    if (wn > 0.0) {
+        double s, c;
+        sincos(0.5 * wn * tau, &s, &c);
+        s /= wn;
+        dq[0] = c; dq[1] = s * w[0]; dq[2] = s * w[1]; dq[3] = s * w[2];
+    }
+    qmul(dq, q, o);
+    const double n = rsqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2] + o[3] * o[3]);
+    o[0] *= n; o[1] *= n; o[2] *= n; o[3] *= n;
+}
+
+// World position, rigid velocity and rigid acceleration of a marker, and its
+// arm from the body centre.  body < 0: fixed marker, xloc is its world position.
+__device__ __forceinline__ void marker_state(const BodyDev *bodies, int body, const double *xloc,
+                                             double tau, double x[3], float u[3], float a[3],
+                                             float arm[3])
+{
+    if (body < 0) {
+        x[0] = xloc[0]; x[1] = xloc[1]; x[2] = xloc[2];
+        u[0] = u[1] = u[2] = 0.0f;
+        a[0] = a[1] = a[2] = 0.0f;
+        arm[0] = arm[1] = arm[2] = 0.0f;
+        return;
+    }
+    const BodyDev &b = bodies[body];
+    double q[4], r[3];
+    qadvance(b.pose + 3, b.twist + 3, tau, q);
+    qrot(q, xloc, r);
+    const double *w = b.twist + 3;
+    const double wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2],
+                          w[0] * r[1] - w[1] * r[0]};
+    const double wwr[3] = {w[1] * wr[2] - w[2] * wr[1], w[2] * wr[0] - w[0] * wr[2],
+                           w[0] * wr[1] - w[1] * wr[0]};
+    for (int k = 0; k < 3; ++k) {
+        x[k] = b.pose[k] + tau * b.twist[k] + r[k];
+        u[k] = (float)(b.twist[k] + wr[k]);
+        a[k] = (float)(b.acc[k] + wwr[k]);
+        arm[k] = (float)r[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers shared by the translation units.
+inline unsigned grid_for(int64_t n, int block = kBlock)
+{
+    const int64_t g = (n + block - 1) / block;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+// Scratch of one counting sort (Sec. 3.1 steps 2-3).
+struct SortScratch {
+    uint32_t *keys;         // n
+    uint32_t *rank;         // n: arrival rank within the key (atomic)
+    uint32_t *tmp;          // n: slot -> input index before the stable fix-up
+    uint32_t *count;        // nkeys + 1, zero between uses
+    unsigned long long *tile_status;  // scan look-back words
+    uint32_t *ctr;          // [0] ticket, [1] epoch, [2] done
+    int64_t n_tiles;
+};
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Exclusive scan of count[0..n) into start[0..n), resetting count to zero.
+// Single pass, decoupled look-back; every wait is bounded (ERR_TIMEOUT).
+void launch_scan_reset(uint32_t *count, uint32_t *start, int64_t n, const SortScratch &s,
+                       int *err, cudaStream_t st);
+
+// Rebuild (Alg. 2 "PreprocessNeighborList" + Alg. 1), one kernel per launcher:
+// keys + arrival ranks, exclusive scan of the counts (cell ranges, 2M + 1
+// entries), scatter, stable reorder of every particle array from `cur` into
+// `nxt`, and the neighbour table.
+void launch_keys(const DevParams &p, StageArrays cur, const uint32_t *pid_cur, const double *mloc,
+                 const int *mbody, const BodyDev *bodies, const SortScratch &s, int *err,
+                 int n_fluid_total, cudaStream_t st);
+void launch_scatter(const DevParams &p, const SortScratch &s, const uint32_t *start,
+                    cudaStream_t st);
+void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *start,
+                    StageArrays cur, const uint32_t *pid_cur, StageArrays nxt, uint32_t *pid_nxt,
+                    cudaStream_t st);
+void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
+                      uint32_t *nnb, int *err, cudaStream_t st);
+
+struct RateOut {
+    float *drho;    // [slot]
+    float4 *du;     // [slot] (x, y, z, 0)
+    float4 *dsA;    // [slot] xx, yy, zz, xy
+    float2 *dsB;    // [slot] xz, yz
+};
+
+enum { kStage1 = 0, kStage2 = 1, kEval = 2 };
+
+void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, StageArrays MID,
+                 const uint32_t *nbr, const uint32_t *nnb, const uint8_t *integrate, float dt,
+                 RateOut out, int *err, cudaStream_t st);
+void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
+                const double *mloc, const int *mbody, const BodyDev *bodies, const uint32_t *nbr,
+                const uint32_t *nnb, double tau, int accel, int n_fluid_total, float4 *mforce,
+                float4 *mtorque, cudaStream_t st);
+void launch_wrench_partial(const DevParams &p, const float4 *mforce, const float4 *mtorque,
+                           double *partial, cudaStream_t st);
+void launch_body_update(const DevParams &p, const double *partial, BodyDev *bodies, double dt,
+                        int integrate, cudaStream_t st);
+void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
+                   float *sig, float *rho, cudaStream_t st);
+void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, StageArrays S,
+                         const float4 *mforce, int n_fluid_total, float *drho, float *du,
+                         float *ds, float *macc, float *mvel, float *msig, cudaStream_t st);
+
+}  // namespace crm

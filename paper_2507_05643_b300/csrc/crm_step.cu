@@ -1,0 +1,519 @@
+// crm_step.cu -- per-stage kernels of the SPH continuum step (Sec. 2.1-2.4).
+//
+// One step (explicit midpoint, Sec. 2.2) runs
+//   k_bce(tau = 0)          marker velocity / stress from the fluid at y_n
+//   k_pair<kStage1>         rates f(y_n) of every fluid particle, fused with
+//                           y_mid = y_n + dt/2 f(y_n)
+//   k_bce(tau = dt/2)       markers at the midpoint, plus their accelerations
+//   k_pair<kStage2>         rates f(y_mid), fused with y_{n+1} = y_n + dt f(y_mid)
+//                           and the return map of Sec. 2.3
+//   k_wrench_partial        FP64 per-block sums of marker force and torque
+//   k_body_update           FP64 wrench + body update (one warp per body)
+// Every particle owns its outputs (gather form): no float atomics, so a step
+// is bitwise reproducible.
+#include "crm_internal.cuh"
+
+namespace crm {
+
+// Cell offsets of the neighbour codes (dx, dy, dz in {-1, 0, 1}) times the cell
+// size, built once per block in shared memory.
+__device__ __forceinline__ void fill_shift_table(float4 *lut, float cell)
+{
+    const int t = threadIdx.x;
+    if (t < 64) {
+        const int dx = (t & 3) - 1, dy = ((t >> 2) & 3) - 1, dz = (t >> 4) - 1;
+        lut[t] = make_float4((float)dx * cell, (float)dy * cell, (float)dz * cell, 0.0f);
+    }
+}
+
+// Stress rate from the velocity gradient L (L_ab = du_a/dx_b), Eqs.
+// stress_rate_hypoelastic / stress_rate_jaumann / stress_rate:
+//   dsigma = Omega sigma - sigma Omega + 2G (eps - tr(eps)/3 I) + K tr(eps) I,
+//   eps = (L + L^T)/2, Omega = (L - L^T)/2.
+// s and out are (xx, yy, zz, xy, xz, yz).
+__device__ __forceinline__ void stress_rate(const float L[9], const float s[6], float G, float K,
+                                            float out[6])
+{
+    const float a = 0.5f * (L[1] - L[3]);   // Omega_xy
+    const float b = 0.5f * (L[2] - L[6]);   // Omega_xz
+    const float c = 0.5f * (L[5] - L[7]);   // Omega_yz
+    const float exx = L[0], eyy = L[4], ezz = L[8];
+    const float exy = 0.5f * (L[1] + L[3]), exz = 0.5f * (L[2] + L[6]), eyz = 0.5f * (L[5] + L[7]);
+    const float tr = exx + eyy + ezz;
+    const float iso = (K - 2.0f * G / 3.0f) * tr;
+    const float G2 = 2.0f * G;
+    out[0] = 2.0f * (a * s[3] + b * s[4]) + G2 * exx + iso;
+    out[1] = 2.0f * (c * s[5] - a * s[3]) + G2 * eyy + iso;
+    out[2] = -2.0f * (b * s[4] + c * s[5]) + G2 * ezz + iso;
+    out[3] = a * (s[1] - s[0]) + b * s[5] + c * s[4] + G2 * exy;
+    out[4] = b * (s[2] - s[0]) + a * s[5] - c * s[3] + G2 * exz;
+    out[5] = c * (s[2] - s[1]) - a * s[4] - b * s[3] + G2 * eyz;
+}
+
+__device__ __forceinline__ float taubar(const float s[6])
+{
+    const float p = -(s[0] + s[1] + s[2]) * (1.0f / 3.0f);
+    const float t0 = s[0] + p, t1 = s[1] + p, t2 = s[2] + p;
+    return sqrtf(0.5f * (t0 * t0 + t1 * t1 + t2 * t2)
+                 + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]));
+}
+
+// Return map of Sec. 2.3 on the trial stress s (in place); sn = stress at t_n
+// (for the mu(I) shear rate).
+__device__ __forceinline__ void return_map(float s[6], const float sn[6], const DevParams &p,
+                                           float dt)
+{
+    const float ps = -(s[0] + s[1] + s[2]) * (1.0f / 3.0f);
+    // Step 1: tension cut-off at p_cri = -c / mu_s
+    if (p.mu_s > 0.0f && ps < -p.cohesion / p.mu_s) {
+        for (int k = 0; k < 6; ++k) s[k] = 0.0f;
+        return;
+    }
+    const float tb = taubar(s);
+    // Step 2: mu(I); with mu_2 = mu_s the rate term vanishes
+    float mu = p.mu_s;
+    if (p.mu_2 != p.mu_s) {
+        const float gdot = (tb - taubar(sn)) / (p.G * dt);
+        if (gdot > 0.0f && ps > 0.0f) {
+            const float I = gdot * p.grain_d * sqrtf(p.rho0 / ps);
+            mu = p.mu_s + (p.mu_2 - p.mu_s) / (1.0f + p.I0 / I);
+        }
+    }
+    // Step 3: admissible trial stress is kept
+    const float tmax = mu * ps + p.cohesion;
+    if (tb <= tmax) return;
+    // Step 4: radial return in deviatoric space, pressure kept
+    const float f = tmax / tb;
+    s[0] = -ps + f * (s[0] + ps);
+    s[1] = -ps + f * (s[1] + ps);
+    s[2] = -ps + f * (s[2] + ps);
+    s[3] *= f; s[4] *= f; s[5] *= f;
+}
+
+// Pair sums of fluid particle i (Eqs. continuity_dis, momentum_dis, the
+// artificial viscosity of Sec. 2.2 and the F2 velocity gradient), then the
+// stage epilogue.  Neighbours j are fluid particles and BCE markers, whose
+// velocity/stress slots hold the extrapolated marker state and whose density
+// slot holds rho0.  V_j = m / rho_j.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
+       const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ nnb,
+       const uint8_t *__restrict__ integrate, float dt, RateOut out, int *__restrict__ err)
+{
+    __shared__ float4 lut[64];
+    fill_shift_table(lut, p.cell);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.nF) return;
+    const bool adv = integrate == nullptr || integrate[i] != 0;
+    if (!adv) {
+        if (MODE == kStage1) {
+            MID.pos[i] = S.pos[i];
+            MID.vel[i] = S.vel[i];
+            MID.sA[i] = S.sA[i];
+            MID.sB[i] = S.sB[i];
+        } else if (MODE == kEval) {
+            out.drho[i] = 0.0f;
+            out.du[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            out.dsA[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            out.dsB[i] = make_float2(0.f, 0.f);
+        }
+        return;
+    }
+    const float4 pi = S.pos[i];
+    const float4 vi = S.vel[i];
+    const float4 ai = S.sA[i];
+    const float2 bi = S.sB[i];
+    float cont = 0.f, mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
+    float L[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) L[k] = 0.f;
+    const int nn = (int)nnb[i];
+    const uint32_t *row = nbr + i;
+    for (int k = 0; k < nn; ++k) {
+        const uint32_t e = __ldg(row + (size_t)k * p.ell);
+        const uint32_t j = e & kIndexMask;
+        const float4 sh = lut[e >> kIndexBits];
+        const float4 pj = __ldg(&S.pos[j]);
+        const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+        const float4 vj = __ldg(&S.vel[j]);
+        const float4 aj = __ldg(&S.sA[j]);
+        const float2 bj = __ldg(&S.sB[j]);
+        const float rinv = rsqrtf(r2);
+        const float q = r2 * rinv * p.inv_h;
+        const float f = kernel_dw_over_r(q, rinv, p);
+        const float gx = f * rx, gy = f * ry, gz = f * rz;          // grad_i W_ij
+        const float Vj = p.m / vj.w;
+        const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;   // u_ji
+        // continuity (F2)
+        cont = fmaf(Vj, ux * gx + uy * gy + uz * gz, cont);
+        // momentum (F3): (sigma_i + sigma_j) . grad W
+        const float sxx = ai.x + aj.x, syy = ai.y + aj.y, szz = ai.z + aj.z;
+        const float sxy = ai.w + aj.w, sxz = bi.x + bj.x, syz = bi.y + bj.y;
+        mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, mx);
+        my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, my);
+        mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, mz);
+        // velocity gradient (F2): L += V_j u_ji (x) grad W
+        const float vx = Vj * ux, vy = Vj * uy, vz = Vj * uz;
+        L[0] = fmaf(vx, gx, L[0]); L[1] = fmaf(vx, gy, L[1]); L[2] = fmaf(vx, gz, L[2]);
+        L[3] = fmaf(vy, gx, L[3]); L[4] = fmaf(vy, gy, L[4]); L[5] = fmaf(vy, gz, L[5]);
+        L[6] = fmaf(vz, gx, L[6]); L[7] = fmaf(vz, gy, L[7]); L[8] = fmaf(vz, gz, L[8]);
+        // artificial viscosity: v_ij . r_ij = -(u_ji . r_ij)
+        if (p.av_mode != CRM_AV_NONE) {
+            const float vr = -(ux * rx + uy * ry + uz * rz);
+            if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+                const float fac = 2.0f * p.av_c * vr / ((vi.w + vj.w) * (r2 + p.xi2));
+                avx = fmaf(fac, gx, avx);
+                avy = fmaf(fac, gy, avy);
+                avz = fmaf(fac, gz, avz);
+            }
+        }
+    }
+    const float rinv_i = 1.0f / vi.w;
+    const float drho = -vi.w * cont;
+    const float dux = mx * rinv_i + p.gx + avx;
+    const float duy = my * rinv_i + p.gy + avy;
+    const float duz = mz * rinv_i + p.gz + avz;
+    const float si[6] = {ai.x, ai.y, ai.z, ai.w, bi.x, bi.y};
+    float ds[6];
+    stress_rate(L, si, p.G, p.K, ds);
+    if (MODE == kEval) {
+        out.drho[i] = drho;
+        out.du[i] = make_float4(dux, duy, duz, 0.f);
+        out.dsA[i] = make_float4(ds[0], ds[1], ds[2], ds[3]);
+        out.dsB[i] = make_float2(ds[4], ds[5]);
+    } else if (MODE == kStage1) {
+        const float h = 0.5f * dt;
+        MID.pos[i] = make_float4(fmaf(h, vi.x, pi.x), fmaf(h, vi.y, pi.y), fmaf(h, vi.z, pi.z), pi.w);
+        MID.vel[i] = make_float4(fmaf(h, dux, vi.x), fmaf(h, duy, vi.y), fmaf(h, duz, vi.z),
+                                 fmaf(h, drho, vi.w));
+        MID.sA[i] = make_float4(fmaf(h, ds[0], si[0]), fmaf(h, ds[1], si[1]), fmaf(h, ds[2], si[2]),
+                                fmaf(h, ds[3], si[3]));
+        MID.sB[i] = make_float2(fmaf(h, ds[4], si[4]), fmaf(h, ds[5], si[5]));
+    } else {
+        // y_{n+1} = y_n + dt f(y_mid); S holds y_mid, Y holds y_n of particle i
+        const float4 p0 = Y.pos[i];
+        const float4 v0 = Y.vel[i];
+        const float4 a0 = Y.sA[i];
+        const float2 b0 = Y.sB[i];
+        const float sn[6] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y};
+        float s1[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s1[k] = fmaf(dt, ds[k], sn[k]);
+        return_map(s1, sn, p, dt);
+        const float4 np = make_float4(fmaf(dt, vi.x, p0.x), fmaf(dt, vi.y, p0.y),
+                                      fmaf(dt, vi.z, p0.z), p0.w);
+        const float4 nv = make_float4(fmaf(dt, dux, v0.x), fmaf(dt, duy, v0.y),
+                                      fmaf(dt, duz, v0.z), fmaf(dt, drho, v0.w));
+        const float chk = np.x + np.y + np.z + nv.x + nv.y + nv.z + nv.w + s1[0] + s1[1] + s1[2]
+                          + s1[3] + s1[4] + s1[5];
+        if (!isfinite(chk)) atomicOr(err, ERR_NONFINITE);
+        Y.pos[i] = np;
+        Y.vel[i] = nv;
+        Y.sA[i] = make_float4(s1[0], s1[1], s1[2], s1[3]);
+        Y.sB[i] = make_float2(s1[4], s1[5]);
+    }
+}
+
+// BCE marker state (Sec. 2.4) at stage offset tau, written into the marker
+// slots of S.  The home cell of each slot is read from `home_pos` -- the main
+// arrays, whose cell ids the last rebuild set -- so that the marker offset is
+// relative to the cell its neighbour codes were built against.  Velocity (Adami): u_a = 2 u_body - sum_f u_f W / sum_f W.
+// Stress: sigma_a = [sum_f sigma_f W - ((g - a_body) . sum_f rho_f (x_a - x_f) W) I]
+// / sum_f W (the pressure extrapolation of the cited scheme in stress form);
+// without fluid in reach u_a = u_body and sigma_a = 0.
+// accel: 0 = none, 1 = body markers, 2 = every marker.  The acceleration is
+// a_a = (1/rho0) sum_f V_f (sigma_a + sigma_f) . grad_a W_af + AV (no gravity);
+// force m a_a and torque arm x m a_a go to mforce / mtorque[slot - nF].
+__global__ void __launch_bounds__(kBlock)
+k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
+      const uint32_t *__restrict__ pid,
+      const double *__restrict__ mloc, const int *__restrict__ mbody,
+      const BodyDev *__restrict__ bodies, const uint32_t *__restrict__ nbr,
+      const uint32_t *__restrict__ nnb, double tau, int accel, int n_fluid_total,
+      float4 *__restrict__ mforce, float4 *__restrict__ mtorque)
+{
+    __shared__ float4 lut[64];
+    fill_shift_table(lut, p.cell);
+    __syncthreads();
+    const int s = p.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.N) return;
+    const int mi = (int)pid[s] - n_fluid_total;
+    const int body = mbody[mi];
+    double x[3];
+    float ub[3], ab[3], arm[3];
+    marker_state(bodies, body, mloc + 3 * (int64_t)mi, tau, x, ub, ab, arm);
+    const float4 home = home_pos[s];
+    int ix, iy, iz;
+    decode_cell(__float_as_uint(home.w), p, ix, iy, iz);
+    const float ox = (float)(x[0] - (p.dmin_x + ix * p.cell_d));
+    const float oy = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
+    const float oz = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
+    float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
+    float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int nn = (int)nnb[s];
+    const uint32_t *row = nbr + s;
+    for (int k = 0; k < nn; ++k) {
+        const uint32_t e = __ldg(row + (size_t)k * p.ell);
+        const uint32_t j = e & kIndexMask;
+        const float4 sh = lut[e >> kIndexBits];
+        const float4 pj = __ldg(&S.pos[j]);
+        const float rx = ox - pj.x - sh.x, ry = oy - pj.y - sh.y, rz = oz - pj.z - sh.z;
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        if (!(r2 < p.four_h2)) continue;
+        const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
+        const float4 vj = __ldg(&S.vel[j]);
+        const float4 aj = __ldg(&S.sA[j]);
+        const float2 bj = __ldg(&S.sB[j]);
+        w += W;
+        sux = fmaf(vj.x, W, sux); suy = fmaf(vj.y, W, suy); suz = fmaf(vj.z, W, suz);
+        ss[0] = fmaf(aj.x, W, ss[0]); ss[1] = fmaf(aj.y, W, ss[1]); ss[2] = fmaf(aj.z, W, ss[2]);
+        ss[3] = fmaf(aj.w, W, ss[3]); ss[4] = fmaf(bj.x, W, ss[4]); ss[5] = fmaf(bj.y, W, ss[5]);
+        const float rw = vj.w * W;
+        sr[0] = fmaf(rw, rx, sr[0]); sr[1] = fmaf(rw, ry, sr[1]); sr[2] = fmaf(rw, rz, sr[2]);
+    }
+    float ua[3], sa[6];
+    if (w > 0.f) {
+        const float iw = 1.0f / w;
+        ua[0] = 2.f * ub[0] - sux * iw;
+        ua[1] = 2.f * ub[1] - suy * iw;
+        ua[2] = 2.f * ub[2] - suz * iw;
+        const float gp = (p.gx - ab[0]) * sr[0] + (p.gy - ab[1]) * sr[1] + (p.gz - ab[2]) * sr[2];
+        sa[0] = (ss[0] - gp) * iw; sa[1] = (ss[1] - gp) * iw; sa[2] = (ss[2] - gp) * iw;
+        sa[3] = ss[3] * iw; sa[4] = ss[4] * iw; sa[5] = ss[5] * iw;
+    } else {
+        ua[0] = ub[0]; ua[1] = ub[1]; ua[2] = ub[2];
+        for (int k = 0; k < 6; ++k) sa[k] = 0.f;
+    }
+    S.pos[s] = make_float4(ox, oy, oz, home.w);
+    S.vel[s] = make_float4(ua[0], ua[1], ua[2], p.rho0);
+    S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
+    S.sB[s] = make_float2(sa[4], sa[5]);
+    if (accel == 0) return;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (accel == 2 || body >= 0) {
+        float mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
+        for (int k = 0; k < nn; ++k) {
+            const uint32_t e = __ldg(row + (size_t)k * p.ell);
+            const uint32_t j = e & kIndexMask;
+            const float4 sh = lut[e >> kIndexBits];
+            const float4 pj = __ldg(&S.pos[j]);
+            const float rx = ox - pj.x - sh.x, ry = oy - pj.y - sh.y, rz = oz - pj.z - sh.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+            const float4 vj = __ldg(&S.vel[j]);
+            const float4 aj = __ldg(&S.sA[j]);
+            const float2 bj = __ldg(&S.sB[j]);
+            const float rinv = rsqrtf(r2);
+            const float f = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
+            const float gx = f * rx, gy = f * ry, gz = f * rz;
+            const float Vj = p.m / vj.w;
+            const float sxx = sa[0] + aj.x, syy = sa[1] + aj.y, szz = sa[2] + aj.z;
+            const float sxy = sa[3] + aj.w, sxz = sa[4] + bj.x, syz = sa[5] + bj.y;
+            mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, mx);
+            my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, my);
+            mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, mz);
+            if (p.av_mode != CRM_AV_NONE) {
+                const float vr = (ua[0] - vj.x) * rx + (ua[1] - vj.y) * ry + (ua[2] - vj.z) * rz;
+                if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+                    const float fac = 2.0f * p.av_c * vr / ((p.rho0 + vj.w) * (r2 + p.xi2));
+                    avx = fmaf(fac, gx, avx);
+                    avy = fmaf(fac, gy, avy);
+                    avz = fmaf(fac, gz, avz);
+                }
+            }
+        }
+        const float ir = 1.0f / p.rho0;
+        fx = p.m * (mx * ir + avx);
+        fy = p.m * (my * ir + avy);
+        fz = p.m * (mz * ir + avz);
+    }
+    mforce[s - p.nF] = make_float4(fx, fy, fz, __int_as_float(body));
+    mtorque[s - p.nF] = make_float4(arm[1] * fz - arm[2] * fy, arm[2] * fx - arm[0] * fz,
+                                    arm[0] * fy - arm[1] * fx, 0.f);
+}
+
+// FP64 per-block partial wrench of every body (deterministic: fixed block
+// partition, fixed reduction tree).
+__global__ void __launch_bounds__(kBlock)
+k_wrench_partial(int nM, int n_bodies, const float4 *__restrict__ mforce,
+                 const float4 *__restrict__ mtorque, double *__restrict__ partial)
+{
+    __shared__ double red[kBlock / 32][6];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 f = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a < nM) {
+        f = mforce[a];
+        t = mtorque[a];
+    }
+    const int body = __float_as_int(f.w);
+    for (int b = 0; b < n_bodies; ++b) {
+        const bool mine = body == b;
+        double v[6] = {mine ? (double)f.x : 0.0, mine ? (double)f.y : 0.0, mine ? (double)f.z : 0.0,
+                       mine ? (double)t.x : 0.0, mine ? (double)t.y : 0.0, mine ? (double)t.z : 0.0};
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane == 0)
+            for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double acc = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) acc += red[w][threadIdx.x];
+            partial[((size_t)blockIdx.x * n_bodies + b) * 6 + threadIdx.x] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Wrench of each body from the partials (FP64, fixed order), then the body
+// update (Sec. 2.4 FSI step, reading: symplectic Euler on the free linear
+// DOFs, v += dt (F/m + g), x += dt v; prescribed DOFs move with their
+// velocity; the orientation turns by dt w).
+__global__ void k_body_update(int n_bodies, int n_partials, const double *__restrict__ partial,
+                              BodyDev *__restrict__ bodies, double gx, double gy, double gz,
+                              double dt, int integrate)
+{
+    const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (b >= n_bodies) return;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = lane; q < n_partials; q += 32)
+        for (int k = 0; k < 6; ++k) v[k] += partial[((size_t)q * n_bodies + b) * 6 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane != 0) return;
+    BodyDev &B = bodies[b];
+    for (int k = 0; k < 6; ++k) B.wrench[k] = v[k];
+    if (!integrate) return;
+    const double g[3] = {gx, gy, gz};
+    for (int k = 0; k < 3; ++k) {
+        if (B.dof & (1 << k)) {
+            const double acc = v[k] / B.mass + g[k];
+            B.twist[k] += dt * acc;
+            B.acc[k] = acc;
+        } else {
+            B.acc[k] = 0.0;
+        }
+        B.pose[k] += dt * B.twist[k];
+    }
+    double q[4];
+    qadvance(B.pose + 3, B.twist + 3, dt, q);
+    for (int k = 0; k < 4; ++k) B.pose[3 + k] = q[k];
+}
+
+// Sorted fluid slots -> insertion order (absolute FP64 positions).
+__global__ void k_export(DevParams p, StageArrays S, const uint32_t *__restrict__ pid,
+                         double *__restrict__ xyz, float *__restrict__ vel,
+                         float *__restrict__ sig, float *__restrict__ rho)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.nF) return;
+    const uint32_t id = pid[s];
+    const float4 ps = S.pos[s];
+    int ix, iy, iz;
+    decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
+    xyz[3 * (size_t)id + 0] = p.dmin_x + ix * p.cell_d + (double)ps.x;
+    xyz[3 * (size_t)id + 1] = p.dmin_y + iy * p.cell_d + (double)ps.y;
+    xyz[3 * (size_t)id + 2] = p.dmin_z + iz * p.cell_d + (double)ps.z;
+    const float4 v = S.vel[s];
+    vel[3 * (size_t)id + 0] = v.x; vel[3 * (size_t)id + 1] = v.y; vel[3 * (size_t)id + 2] = v.z;
+    rho[id] = v.w;
+    const float4 a = S.sA[s];
+    const float2 b = S.sB[s];
+    float *o = sig + 6 * (size_t)id;
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+}
+
+// Rates and marker state of an evaluation, sorted slots -> insertion order.
+__global__ void k_export_rates(DevParams p, const uint32_t *__restrict__ pid, RateOut r,
+                               StageArrays S, const float4 *__restrict__ mforce,
+                               int n_fluid_total, float *__restrict__ drho,
+                               float *__restrict__ du, float *__restrict__ ds,
+                               float *__restrict__ macc, float *__restrict__ mvel,
+                               float *__restrict__ msig)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.N) return;
+    const uint32_t id = pid[s];
+    if (s < p.nF) {
+        drho[id] = r.drho[s];
+        const float4 a = r.du[s];
+        du[3 * (size_t)id] = a.x; du[3 * (size_t)id + 1] = a.y; du[3 * (size_t)id + 2] = a.z;
+        const float4 b = r.dsA[s];
+        const float2 c = r.dsB[s];
+        float *o = ds + 6 * (size_t)id;
+        o[0] = b.x; o[1] = b.y; o[2] = b.z; o[3] = b.w; o[4] = c.x; o[5] = c.y;
+    } else {
+        const size_t m = (size_t)id - (size_t)n_fluid_total;
+        const float4 f = mforce[s - p.nF];
+        const float im = 1.0f / p.m;
+        macc[3 * m] = f.x * im; macc[3 * m + 1] = f.y * im; macc[3 * m + 2] = f.z * im;
+        const float4 v = S.vel[s];
+        mvel[3 * m] = v.x; mvel[3 * m + 1] = v.y; mvel[3 * m + 2] = v.z;
+        const float4 a = S.sA[s];
+        const float2 b = S.sB[s];
+        float *o = msig + 6 * m;
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers used by the API translation unit.
+void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, StageArrays MID,
+                 const uint32_t *nbr, const uint32_t *nnb, const uint8_t *integrate, float dt,
+                 RateOut out, int *err, cudaStream_t st)
+{
+    const unsigned g = grid_for(p.nF);
+    if (mode == kStage1)
+        k_pair<kStage1><<<g, kBlock, 0, st>>>(p, S, Y, MID, nbr, nnb, integrate, dt, out, err);
+    else if (mode == kStage2)
+        k_pair<kStage2><<<g, kBlock, 0, st>>>(p, S, Y, MID, nbr, nnb, integrate, dt, out, err);
+    else
+        k_pair<kEval><<<g, kBlock, 0, st>>>(p, S, Y, MID, nbr, nnb, integrate, dt, out, err);
+}
+
+void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
+                const double *mloc, const int *mbody, const BodyDev *bodies, const uint32_t *nbr,
+                const uint32_t *nnb, double tau, int accel, int n_fluid_total, float4 *mforce,
+                float4 *mtorque, cudaStream_t st)
+{
+    k_bce<<<grid_for(p.nM), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, mbody, bodies, nbr, nnb,
+                                             tau, accel, n_fluid_total, mforce, mtorque);
+}
+
+void launch_wrench_partial(const DevParams &p, const float4 *mforce, const float4 *mtorque,
+                           double *partial, cudaStream_t st)
+{
+    k_wrench_partial<<<grid_for(p.nM), kBlock, 0, st>>>(p.nM, p.n_bodies, mforce, mtorque, partial);
+}
+
+void launch_body_update(const DevParams &p, const double *partial, BodyDev *bodies, double dt,
+                        int integrate, cudaStream_t st)
+{
+    k_body_update<<<1, 32 * p.n_bodies, 0, st>>>(p.n_bodies, p.nM > 0 ? (int)grid_for(p.nM) : 0,
+                                                 partial, bodies, p.gx, p.gy, p.gz, dt, integrate);
+}
+
+void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
+                   float *sig, float *rho, cudaStream_t st)
+{
+    k_export<<<grid_for(p.nF), kBlock, 0, st>>>(p, S, pid, xyz, vel, sig, rho);
+}
+
+void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, StageArrays S,
+                         const float4 *mforce, int n_fluid_total, float *drho, float *du,
+                         float *ds, float *macc, float *mvel, float *msig, cudaStream_t st)
+{
+    k_export_rates<<<grid_for(p.N), kBlock, 0, st>>>(p, pid, r, S, mforce, n_fluid_total, drho, du,
+                                                     ds, macc, mvel, msig);
+}
+
+}  // namespace crm

@@ -1,0 +1,76 @@
+"""The C-ABI library loads and exports every symbol include/crm.h declares, and its
+host-side argument checks behave (no device work is issued by these calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "crm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(crm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2507_05643_b300 as crm
+    names = _declared()
+    assert len(names) >= 20
+    lib = C.CDLL(crm.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) == set(crm.EXPORTS)
+
+
+def test_version_and_status_strings():
+    import paper_2507_05643_b300 as crm
+    assert crm.version() >= 100
+    assert crm.lib().crm_status_string(-3) == b"CRM_ECAPACITY"
+
+
+def test_default_params_match_paper_constants():
+    import paper_2507_05643_b300 as crm
+    p = crm.default_params()
+    assert p.growth == pytest.approx(1.2) and p.shrink_ratio == pytest.approx(0.75)
+    assert p.shrink_interval == 50
+    assert p.ps_freq == 1 and p.av_mode == crm.AV_UNILATERAL
+
+
+@pytest.mark.parametrize("field, value", [("rho0", 0.0), ("nu", 0.5), ("ps_freq", 0),
+                                          ("max_neighbors", 4), ("h", -1.0), ("av_mode", 3)])
+def test_create_rejects_bad_params(field, value):
+    import paper_2507_05643_b300 as crm
+    p = crm.default_params()
+    setattr(p, field, value)
+    with pytest.raises(crm.CrmError) as e:
+        crm.Terrain(p)
+    assert e.value.code == -1
+
+
+def test_add_rejects_out_of_domain_and_nonfinite():
+    import paper_2507_05643_b300 as crm
+    t = crm.Terrain(crm.default_params())
+    with pytest.raises(crm.CrmError):
+        t.add_sph(np.array([[0.5, 0.5, 1.5]]))
+    with pytest.raises(crm.CrmError):
+        t.add_sph(np.array([[0.5, np.nan, 0.5]]))
+    with pytest.raises(crm.CrmError):
+        t.add_rigid_body(np.zeros((1, 3)), [0.5, 0.5, 0.5, 1, 0, 0, 0], np.zeros(6), -1.0, 4)
+    t.add_sph(np.array([[0.5, 0.5, 0.5]]))
+    assert t.n_sph == 1
+    with pytest.raises(crm.CrmError):
+        t.step(-1.0, 1)
+    t.close()
+
+
+def test_bin_points_rejects_bad_arguments():
+    import paper_2507_05643_b300 as crm
+    with pytest.raises(crm.CrmError):
+        crm.bin_points(0, 10, 0.1, (4, 4, 4), 0, 0, 0, 0, 0)
+    with pytest.raises(crm.CrmError):
+        crm.bin_points(256, 10, -0.1, (4, 4, 4), 256, 256, 256, 256, 1 << 20)
+    assert crm.bin_scratch_bytes(1000, 64) >= 2 * 4 * 1000 + 4 * 65
