@@ -243,6 +243,29 @@ int crm_bin_points(const float *xyz, int64_t n, float cell_size, const int32_t d
                    uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out,
                    void *scratch, size_t scratch_bytes, void *cuda_stream);
 
+/* crm_bin_points without a scratch argument, for callers that cannot
+ * allocate device memory when they bin (code in a host callback or a
+ * real-time loop where cudaMalloc would block or is not allowed, or a caller
+ * whose device memory is entirely owned by its own allocator).  The paper has
+ * no counterpart: this is a packaging of the same binning.
+ *   Arguments, outputs and results are those of crm_bin_points.
+ *   Limits: n <= 1,048,576 points and X*Y*Z <= 1,048,575 cells; larger
+ *   inputs return CRM_EINVAL (with a message on stderr) -- use
+ *   crm_bin_points with a caller buffer instead.
+ *   Scratch: one built-in device array of about 12.6 MB, shared by every
+ *   call on a device and held by every GPU that loads the library until the
+ *   process exits.  Each call clears the parts that must start at zero, so
+ *   results never depend on the previous call; but calls whose work can
+ *   overlap on a GPU (different streams, or host threads) race on that array:
+ *   serialise them.
+ *   Set-up: the first call on each device looks up the array's device
+ *   address with that device current (cudaGetSymbolAddress); make that first
+ *   call before any stream capture.
+ *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+int crm_bin_points_noalloc(const float *xyz, int64_t n, float cell_size, const int32_t dims[3],
+                           uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out,
+                           void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

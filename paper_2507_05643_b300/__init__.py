@@ -112,7 +112,7 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
-           "crm_profile_reset", "crm_profile_read")
+           "crm_profile_reset", "crm_profile_read", "crm_bin_points_noalloc")
 
 
 def lib():
@@ -324,6 +324,21 @@ def bin_points(xyz_ptr: int, n: int, cell_size: float, dims, cell_ptr: int, perm
                              _stream_handle(stream))
     if rc != CRM_OK:
         raise CrmError(rc, "crm_bin_points rejected its arguments")
+
+
+_sig("crm_bin_points_noalloc", C.c_int, [_vp, _i64, C.c_float, _vp, _vp, _vp, _vp, _vp])
+
+
+def bin_points_noalloc(xyz_ptr: int, n: int, cell_size: float, dims, cell_ptr: int,
+                       perm_ptr: int, start_ptr: int, stream=None):
+    """crm_bin_points_noalloc on device pointers: the same binning with the
+    library's built-in scratch array (for callers that cannot allocate)."""
+    d = (C.c_int32 * 3)(*[int(v) for v in dims])
+    rc = _lib.crm_bin_points_noalloc(C.c_void_p(xyz_ptr), int(n), float(cell_size), d,
+                                     C.c_void_p(cell_ptr), C.c_void_p(perm_ptr),
+                                     C.c_void_p(start_ptr), _stream_handle(stream))
+    if rc != CRM_OK:
+        raise CrmError(rc, "crm_bin_points_noalloc rejected its arguments")
 
 
 def bin_scratch_bytes(n: int, ncell: int) -> int:

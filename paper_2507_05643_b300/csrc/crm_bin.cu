@@ -7,6 +7,9 @@
 // The atomic ranks make the arrival order within a cell nondeterministic; a
 // fix-up pass re-ranks every element by its input index inside its cell, so
 // the result equals a stable sort by (cell, input index) on every run.
+#include <cstdio>
+#include <mutex>
+
 #include "crm_internal.cuh"
 
 namespace crm {
@@ -419,6 +422,108 @@ extern "C" int crm_bin_points(const float *xyz, int64_t n, float cell_size, cons
     // counts, look-back words and counters start from zero on every call (the
     // scratch content is the caller's); ctr[3] collects device-side failures
     if (cudaMemsetAsync(base + L.count, 0, L.total - L.count, st) != cudaSuccess) return CRM_ECUDA;
+    int *err = (int *)(s.ctr + 3);
+    if (n > 0)
+        crm::k_hash_points<<<crm::grid_for(n), crm::kBlock, 0, st>>>(
+            xyz, n, 1.0f / cell_size, dims[0], dims[1], dims[2], s.keys, s.rank, s.count);
+    crm::launch_scan_reset(s.count, cell_start_out, ncell + 1, s, err, st);
+    if (n > 0) {
+        crm::k_scatter<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, s.rank, cell_start_out,
+                                                                 s.tmp, n);
+        crm::k_perm<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, cell_start_out, s.tmp,
+                                                              perm_out, n);
+    }
+    return cudaGetLastError() == cudaSuccess ? CRM_OK : CRM_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of crm_bin_points (include/crm.h).
+//
+// For callers that cannot allocate device memory at the time they bin --
+// for example code running inside a host callback or a real-time loop where
+// cudaMalloc would stall or is forbidden, or a caller whose device memory is
+// fully reserved by its own allocator -- the scratch of the counting sort
+// lives in one file-scope device array instead of a caller buffer.  That array
+// is part of the library image: every GPU that loads the library holds
+// kNoAllocScratchBytes of it until the process exits.
+namespace {
+constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 20;   // 1,048,576 points
+constexpr int64_t kNoAllocMaxCells = (int64_t(1) << 20) - 1;   // 1,048,575 cells
+constexpr size_t kNoAllocRank = 0;
+constexpr size_t kNoAllocTmp = kNoAllocRank + sizeof(uint32_t) * kNoAllocMaxPoints;
+constexpr size_t kNoAllocCount = kNoAllocTmp + sizeof(uint32_t) * kNoAllocMaxPoints;
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxCells + 1 + crm::kScanTile - 1) / crm::kScanTile;
+constexpr size_t kNoAllocStatus = kNoAllocCount + sizeof(uint32_t) * (kNoAllocMaxCells + 1);
+constexpr size_t kNoAllocCtr = kNoAllocStatus + sizeof(unsigned long long) * kNoAllocTiles;
+constexpr size_t kNoAllocScratchBytes = kNoAllocCtr + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device (host code
+// must not use the symbol itself: on the host it is only a stand-in).
+constexpr int kMaxDevices = 64;
+void *g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(void **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return CRM_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return CRM_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return CRM_OK;
+}
+}  // namespace
+
+extern "C" int crm_bin_points_noalloc(const float *xyz, int64_t n, float cell_size,
+                                      const int32_t dims[3], uint32_t *cell_out,
+                                      uint32_t *perm_out, uint32_t *cell_start_out,
+                                      void *cuda_stream)
+{
+    if (!dims || !cell_start_out || n < 0) return CRM_EINVAL;
+    if (n > 0 && (!xyz || !cell_out || !perm_out)) return CRM_EINVAL;
+    if (!(cell_size > 0.0f) || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return CRM_EINVAL;
+    const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
+    if (n > kNoAllocMaxPoints || ncell > kNoAllocMaxCells) {
+        std::fprintf(stderr,
+                     "crm_bin_points_noalloc: %lld points / %lld cells exceed the built-in "
+                     "scratch limits of %lld points and %lld cells; use crm_bin_points with a "
+                     "caller scratch buffer\n",
+                     (long long)n, (long long)ncell, (long long)kNoAllocMaxPoints,
+                     (long long)kNoAllocMaxCells);
+        return CRM_EINVAL;
+    }
+    void *addr = nullptr;
+    const int rc = noalloc_scratch(&addr);
+    if (rc != CRM_OK) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    char *base = (char *)addr;
+    crm::SortScratch s;
+    s.keys = cell_out;
+    s.rank = (uint32_t *)(base + kNoAllocRank);
+    s.tmp = (uint32_t *)(base + kNoAllocTmp);
+    s.count = (uint32_t *)(base + kNoAllocCount);
+    s.tile_status = (unsigned long long *)(base + kNoAllocStatus);
+    s.ctr = (uint32_t *)(base + kNoAllocCtr);
+    s.n_tiles = (ncell + 1 + crm::kScanTile - 1) / crm::kScanTile;
+    // the array keeps whatever the previous call left: the counts, the look-back
+    // words and the counters must start from zero
+    if (cudaMemsetAsync(base + kNoAllocCount, 0, sizeof(uint32_t) * (size_t)(ncell + 1), st)
+            != cudaSuccess
+        || cudaMemsetAsync(base + kNoAllocStatus, 0, kNoAllocScratchBytes - kNoAllocStatus, st)
+               != cudaSuccess)
+        return CRM_ECUDA;
     int *err = (int *)(s.ctr + 3);
     if (n > 0)
         crm::k_hash_points<<<crm::grid_for(n), crm::kBlock, 0, st>>>(
