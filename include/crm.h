@@ -198,6 +198,15 @@ int crm_state_bytes(crm_terrain *t, size_t *bytes);
 int crm_save_state(crm_terrain *t, void *dev_buf, size_t cap, size_t *used);
 int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
 
+/* Array-capacity policy of ManageArrayMemory (Sec. 3.2): the capacity that
+ * follows `cap` when `need` elements are required at step `step`: grown to
+ * ceil(need * growth) when need > cap; shrunk to need when step is a multiple
+ * of shrink_interval and need / cap < shrink_ratio; else unchanged.  Pure
+ * host function (the active-domain stepper applies it to the working set).
+ * CRM_EINVAL on a null output or out-of-range argument. */
+int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
+                        double shrink_ratio, int32_t shrink_interval, int64_t *new_cap);
+
 /* Per-kernel launch counts and CUDA-event timings of one handle (for
  * measurement).  Kernel ids 0..CRM_NUM_KERNELS-1, names from crm_kernel_name:
  * keys, scan, scatter, reorder, neighbors, bce, pair_stage1, pair_stage2,

@@ -244,6 +244,7 @@ class State:
         self.mbody, self.mxloc = marker_arrays(scene)
         self.bodies = Bodies(scene)
         self.step_index = 0
+        self.time = 0.0          # accumulated step by step, as a time integrator does
         self.off = None
         self.lst = None
         self.include = None
@@ -266,12 +267,15 @@ class State:
         """Alg. 3 items 1-4 at the current time: activity flags (past t_delay, when
         the scene has active boxes) and the neighbour lists."""
         sc = self.scene
-        t = self.step_index * sc.dt
+        t = self.time
         xm, _, _ = self.markers_now()
         if sc.boxes and t > sc.t_delay:
+            # Sec. 3.2 reading for markers: a body's markers always take part;
+            # fixed markers take part when inside a box grown by 2h.
             self.flags = activity(self.params, self.x, sc.boxes, self.bodies.pose)
             self.marker_flags = activity(self.params, xm, sc.boxes, self.bodies.pose)
-            self.include = np.concatenate([self.flags > 0, self.marker_flags > 0]).astype(np.uint8)
+            mk = (self.marker_flags > 0) | (self.mbody >= 0)
+            self.include = np.concatenate([self.flags > 0, mk]).astype(np.uint8)
             self.integrate = (self.flags == 2).astype(np.uint8)
         else:
             self.flags = None
@@ -295,6 +299,7 @@ class State:
                        b.mass, b.dof, b.acc, b.wrench, self.off, lst,
                        _ptr(self.integrate), _ptr(self.include))
         self.step_index += 1
+        self.time += dt
 
     def run(self, n_steps: int, dt: Optional[float] = None, mode: str = "cells"):
         for _ in range(n_steps):

@@ -112,7 +112,23 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
-           "crm_profile_reset", "crm_profile_read", "crm_bin_points_noalloc")
+           "crm_profile_reset", "crm_profile_read", "crm_bin_points_noalloc",
+           "crm_capacity_policy")
+
+
+_sig("crm_capacity_policy", C.c_int, [_i64, _i64, _i64, C.c_double, C.c_double, _i32,
+                                      C.POINTER(_i64)])
+
+
+def capacity_policy(need: int, cap: int, step: int, growth: float = 1.2,
+                    shrink_ratio: float = 0.75, shrink_interval: int = 50) -> int:
+    """crm_capacity_policy: the active-set capacity after one ManageArrayMemory call."""
+    out = _i64()
+    rc = _lib.crm_capacity_policy(int(need), int(cap), int(step), float(growth),
+                                  float(shrink_ratio), int(shrink_interval), C.byref(out))
+    if rc != CRM_OK:
+        raise CrmError(rc, "crm_capacity_policy rejected its arguments")
+    return int(out.value)
 
 
 def lib():

@@ -1,0 +1,434 @@
+// crm_active.cu -- active domains (Sec. 3.2, Alg. 3): activity flags against
+// oriented boxes attached to bodies, counts of Active / Extended-Active
+// particles, and the compaction of those particles into the working set that
+// the rest of the step processes.
+//
+// Layout.  Every SPH particle lives in a master store sorted once, at commit,
+// by global cell with x slowest; colStart[x] is the first master slot of
+// x-column x.  Particles are never re-sorted in the master: an Active particle
+// is gathered into the working set, advanced there, and written back to its
+// master slot, so its cell can drift away from the column it is filed under.
+// The largest such drift (in columns) is tracked with atomicMax at write-back,
+// so a box covering columns [xa, xb] finds every particle it can contain in
+// the master slots of columns [xa - drift, xb + drift] -- one contiguous
+// range.  Fixed wall markers get the same column index (they never move).
+// The scan over a step is therefore proportional to the boxes' slabs, not to
+// the terrain.
+#include <algorithm>
+
+#include "crm_internal.cuh"
+
+namespace crm {
+
+// Oriented box of one step: centre, rotation (body frame -> world), half
+// extents, and the same grown by 2h.
+struct BoxFrame {
+    double c[3];
+    double R[9];
+    double e[3];
+    double eg[3];
+};
+
+// ---------------------------------------------------------------------------
+// k_box_prep: one block.  Box frames at the start of the step, the working
+// window (union of the grown boxes' cell ranges, plus one cell), and the
+// candidate master ranges: for fluid and for fixed markers, the union of the
+// column ranges [xa - drift, xb + drift] of every box.  `all_active` (t <=
+// t_delay, Alg. 3) takes the whole master and the whole grid instead.
+//   ranges[2 * r], ranges[2 * r + 1]: master slot range r (fluid ranges first)
+//   rinfo[0] = number of fluid ranges, [1] = number of marker ranges,
+//   rinfo[2] = fluid candidates, [3] = all candidates, rinfo[4 + r] = prefix
+//   offset of range r in the flattened candidate index.
+__global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_body,
+                           const double *__restrict__ box_half, const double *__restrict__ box_off,
+                           const BodyDev *__restrict__ bodies, const int *__restrict__ colF,
+                           const int *__restrict__ colM, const int *__restrict__ drift,
+                           int all_active, int n_fluid_master, int n_fixed_master,
+                           int64_t cand_cap, BoxFrame *__restrict__ frames, int *__restrict__ win,
+                           int *__restrict__ ranges, int *__restrict__ rinfo,
+                           int *__restrict__ counts, int *__restrict__ abort_flag,
+                           int64_t step_tag)
+{
+    if (threadIdx.x != 0) return;
+    if (*abort_flag) return;
+    counts[3] = 0;
+    counts[4] = 0;
+    const int G[3] = {p.GX, p.GY, p.GZ};
+    const double dmin[3] = {p.dmin_x, p.dmin_y, p.dmin_z};
+    int lo[3] = {G[0], G[1], G[2]}, hi[3] = {-1, -1, -1};
+    int xa[kMaxBodies], xb[kMaxBodies];
+    const double grow = 2.0 * (double)p.h;
+    for (int b = 0; b < nbox; ++b) {
+        const BodyDev &B = bodies[box_body[b]];
+        BoxFrame &F = frames[b];
+        const double *q = B.pose + 3;
+        const double w = q[0], x = q[1], y = q[2], z = q[3];
+        const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                             2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                             2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+        for (int k = 0; k < 9; ++k) F.R[k] = R[k];
+        for (int k = 0; k < 3; ++k) {
+            F.c[k] = B.pose[k] + R[3 * k] * box_off[3 * b] + R[3 * k + 1] * box_off[3 * b + 1]
+                     + R[3 * k + 2] * box_off[3 * b + 2];
+            F.e[k] = box_half[3 * b + k];
+            F.eg[k] = box_half[3 * b + k] + grow;
+        }
+        for (int k = 0; k < 3; ++k) {
+            const double ext = fabs(R[3 * k]) * F.eg[0] + fabs(R[3 * k + 1]) * F.eg[1]
+                               + fabs(R[3 * k + 2]) * F.eg[2];
+            int a = (int)floor((F.c[k] - ext - dmin[k]) / p.cell_d) - 1;
+            int c = (int)floor((F.c[k] + ext - dmin[k]) / p.cell_d) + 1;
+            a = max(a, 0);
+            c = min(c, G[k] - 1);
+            lo[k] = min(lo[k], a);
+            hi[k] = max(hi[k], c);
+            if (k == 0) { xa[b] = a; xb[b] = c; }
+        }
+    }
+    if (all_active || nbox == 0) {
+        for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = G[k] - 1; }
+    }
+    const int64_t cells = (int64_t)max(hi[0] - lo[0] + 1, 1) * max(hi[1] - lo[1] + 1, 1)
+                          * max(hi[2] - lo[2] + 1, 1);
+    if (hi[0] < lo[0] || hi[1] < lo[1] || hi[2] < lo[2]) {   // boxes outside the grid
+        for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; }
+    }
+    if (cells > (int64_t)p.M) {
+        counts[7] = (int)min(cells, (int64_t)0x7fffffff);
+        atomicCAS(abort_flag, 0, (int)(step_tag + 1));
+        return;
+    }
+    for (int k = 0; k < 3; ++k) {
+        win[k] = lo[k];
+        win[3 + k] = max(hi[k] - lo[k] + 1, 1);
+    }
+    // candidate master ranges (merged; fluid first, then fixed markers)
+    const int d = *drift;
+    int nr = 0;
+    int64_t total = 0;
+    int nrange[2] = {0, 0};
+    rinfo[2] = 0;
+    for (int kind = 0; kind < 2; ++kind) {
+        const int *col = kind == 0 ? colF : colM;
+        const int nmaster = kind == 0 ? n_fluid_master : n_fixed_master;
+        if (nmaster == 0) continue;
+        int a0[kMaxBodies], b0[kMaxBodies], m = 0;
+        if (all_active) {
+            a0[0] = 0; b0[0] = G[0] - 1; m = 1;
+        } else {
+            for (int b = 0; b < nbox; ++b) {
+                a0[m] = max(xa[b] - d, 0);
+                b0[m] = min(xb[b] + d, G[0] - 1);
+                ++m;
+            }
+        }
+        // insertion sort by start, then merge overlapping / touching column ranges
+        for (int i = 1; i < m; ++i)
+            for (int j = i; j > 0 && a0[j] < a0[j - 1]; --j) {
+                int t = a0[j]; a0[j] = a0[j - 1]; a0[j - 1] = t;
+                t = b0[j]; b0[j] = b0[j - 1]; b0[j - 1] = t;
+            }
+        int i = 0;
+        while (i < m) {
+            int ca = a0[i], cb = b0[i];
+            int j = i + 1;
+            while (j < m && a0[j] <= cb + 1) { cb = max(cb, b0[j]); ++j; }
+            const int s0 = col[ca], s1 = col[cb + 1];
+            if (s1 > s0) {
+                ranges[2 * nr] = s0;
+                ranges[2 * nr + 1] = s1;
+                rinfo[4 + nr] = (int)total;
+                total += s1 - s0;
+                ++nr;
+                ++nrange[kind];
+            }
+            i = j;
+        }
+        if (kind == 0) rinfo[2] = (int)total;
+    }
+    rinfo[0] = nrange[0];
+    rinfo[1] = nrange[1];
+    rinfo[3] = (int)min(total, (int64_t)0x7fffffff);
+    rinfo[4 + nr] = (int)total;
+    if (total > cand_cap) {
+        counts[8] = (int)min(total, (int64_t)0x7fffffff);
+        atomicCAS(abort_flag, 0, (int)(step_tag + 1));
+    }
+}
+
+// Position of a master fluid particle in FP64 (cell corner + offset).
+__device__ __forceinline__ void abs_pos(const DevParams &p, float4 ps, double x[3])
+{
+    int ix, iy, iz;
+    decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
+    x[0] = p.dmin_x + ix * p.cell_d + (double)ps.x;
+    x[1] = p.dmin_y + iy * p.cell_d + (double)ps.y;
+    x[2] = p.dmin_z + iz * p.cell_d + (double)ps.z;
+}
+
+// Activity of a point against the step's boxes: 2 inside a box (Active), 1
+// inside a box grown by 2h (Extended-Active), else 0 -- the box-frame test of
+// UpdateActivity, in FP64.
+__device__ __forceinline__ int activity(const double x[3], int nbox, const BoxFrame *F)
+{
+    int best = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const double d[3] = {x[0] - F[b].c[0], x[1] - F[b].c[1], x[2] - F[b].c[2]};
+        int in = 1, ext = 1;
+        for (int k = 0; k < 3; ++k) {
+            const double l = F[b].R[k] * d[0] + F[b].R[3 + k] * d[1] + F[b].R[6 + k] * d[2];
+            if (fabs(l) > F[b].e[k]) in = 0;
+            if (fabs(l) > F[b].eg[k]) ext = 0;
+        }
+        if (in) return 2;
+        if (ext) best = 1;
+    }
+    return best;
+}
+
+__device__ __forceinline__ int range_of(const int *rinfo, int nr, int c)
+{
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rinfo[4 + mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// UpdateActivity (Alg. 3): flag every candidate; include[c] = 1 for Active and
+// Extended-Active fluid and for fixed markers within a grown box.  Counts of
+// Active and Extended fluid go to counts[3], counts[4] (integer atomics).
+__global__ void k_activity(DevParams p, int nbox, const BoxFrame *__restrict__ frames,
+                           const int *__restrict__ ranges, const int *__restrict__ rinfo,
+                           const float4 *__restrict__ mpos, const double *__restrict__ mloc,
+                           const int *__restrict__ fixed_order, int all_active, int64_t cand_cap,
+                           uint32_t *__restrict__ include, uint8_t *__restrict__ kind,
+                           int *__restrict__ counts, const int *__restrict__ abort_flag)
+{
+    if (*abort_flag) return;
+    __shared__ BoxFrame F[kMaxBodies];
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x) F[b] = frames[b];
+    __syncthreads();
+    const int nr = rinfo[0] + rinfo[1];
+    const int nfc = rinfo[2], total = rinfo[3];
+    int na = 0, ne = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cand_cap;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t inc = 0;
+        uint8_t k = 0;
+        if (c < total) {
+            const int r = range_of(rinfo, nr, (int)c);
+            const int m = ranges[2 * r] + ((int)c - rinfo[4 + r]);
+            double x[3];
+            if (c < nfc) {
+                abs_pos(p, mpos[m], x);
+            } else {
+                const int a = fixed_order[m];
+                x[0] = mloc[3 * (int64_t)a]; x[1] = mloc[3 * (int64_t)a + 1]; x[2] = mloc[3 * (int64_t)a + 2];
+            }
+            const int f = all_active ? 2 : activity(x, nbox, F);
+            inc = f > 0 ? 1u : 0u;
+            k = (uint8_t)f;
+            if (c < nfc) {
+                na += f == 2;
+                ne += f == 1;
+            }
+        }
+        include[c] = inc;
+        kind[c] = k;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        na += __shfl_down_sync(0xffffffffu, na, o);
+        ne += __shfl_down_sync(0xffffffffu, ne, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (na | ne)) {
+        atomicAdd(&counts[3], na);
+        atomicAdd(&counts[4], ne);
+    }
+}
+
+// ComputeActiveCount / ManageArrayMemory, device half: sizes of the working
+// set from the exclusive scan of the include flags; overflow of a capacity
+// aborts the step (every later kernel of the step sees the flag and returns).
+__global__ void k_active_sizes(DevParams p, const int *__restrict__ rinfo,
+                               const uint32_t *__restrict__ slot, int n_body_markers,
+                               int *__restrict__ counts, int *__restrict__ abort_flag,
+                               int64_t step_tag)
+{
+    if (threadIdx.x != 0 || *abort_flag) return;
+    const int nfc = rinfo[2], total = rinfo[3];
+    const int nF = (int)slot[nfc];
+    const int nfix = (int)slot[total] - nF;
+    const int nM = nfix + n_body_markers;
+    counts[5] = nF;
+    counts[6] = nM;
+    if (nF > p.capF || nM > p.capM) {
+        atomicCAS(abort_flag, 0, (int)(step_tag + 1));
+        return;
+    }
+    counts[0] = nF;
+    counts[1] = nM;
+    counts[2] = nF + nM;
+}
+
+// Gather the included candidates (and every body marker) into the unsorted
+// working arrays; Extended-Active fluid carries kExtendedBit in its pid.
+__global__ void k_gather(DevParams p, const int *__restrict__ ranges, const int *__restrict__ rinfo,
+                         const uint8_t *__restrict__ kind,
+                         const uint32_t *__restrict__ slot, StageArrays M,
+                         const uint32_t *__restrict__ mpid, const int *__restrict__ fixed_order,
+                         const int *__restrict__ body_markers, int n_body_markers,
+                         int n_fluid_total, int64_t cand_cap, StageArrays W,
+                         uint32_t *__restrict__ wpid, const int *__restrict__ counts,
+                         const int *__restrict__ abort_flag)
+{
+    if (*abort_flag) return;
+    const int nr = rinfo[0] + rinfo[1];
+    const int nfc = rinfo[2], total = rinfo[3];
+    const int nF = counts[0];
+    const int64_t span = (int64_t)max(total, 0) + n_body_markers;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < span;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (c < total) {
+            if (kind[c] == 0) continue;   // (the scan has consumed `include`)
+            const int r = range_of(rinfo, nr, (int)c);
+            const int m = ranges[2 * r] + ((int)c - rinfo[4 + r]);
+            const uint32_t w = slot[c];
+            if (c < nfc) {
+                W.pos[w] = M.pos[m];
+                W.vel[w] = M.vel[m];
+                W.sA[w] = M.sA[m];
+                W.sB[w] = M.sB[m];
+                wpid[w] = mpid[m] | (kind[c] == 1 ? kExtendedBit : 0u);
+            } else {
+                W.pos[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+                W.vel[w] = make_float4(0.f, 0.f, 0.f, p.rho0);
+                W.sA[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+                W.sB[w] = make_float2(0.f, 0.f);
+                wpid[w] = (uint32_t)(n_fluid_total + fixed_order[m]);
+            }
+        } else {
+            const int k = (int)(c - total);
+            const uint32_t w = (uint32_t)((int64_t)slot[total] + k);
+            W.pos[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+            W.vel[w] = make_float4(0.f, 0.f, 0.f, p.rho0);
+            W.sA[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+            W.sB[w] = make_float2(0.f, 0.f);
+            wpid[w] = (uint32_t)(n_fluid_total + body_markers[k]);
+        }
+    }
+    (void)cand_cap;
+    (void)nF;
+}
+
+// Write the Active particles of the (sorted) working set back to their master
+// slots and track how far, in x-columns, any of them has drifted from the
+// column its master slot is filed under.
+__global__ void k_scatter_back(DevParams p, StageArrays W, const uint32_t *__restrict__ wpid,
+                               const uint32_t *__restrict__ mslot_of_pid,
+                               const int *__restrict__ mcol, StageArrays M, int *__restrict__ drift)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int dmax = 0;
+    if (*p.abort) return;
+    if (s < __ldg(p.sizes)) {
+        const uint32_t id = wpid[s];
+        if (!(id & kExtendedBit)) {
+            const uint32_t m = mslot_of_pid[id];
+            const float4 ps = W.pos[s];
+            M.pos[m] = ps;
+            M.vel[m] = W.vel[s];
+            M.sA[m] = W.sA[s];
+            M.sB[m] = W.sB[s];
+            int ix, iy, iz;
+            decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
+            // an offset may have left its home cell since the last re-homing
+            ix += (int)floorf(ps.x / p.cell);
+            dmax = abs(ix - mcol[m]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax > 0) atomicMax(drift, dmax);
+}
+
+// Master store -> insertion order (absolute FP64 positions).
+__global__ void k_export_master(DevParams p, StageArrays M, const uint32_t *__restrict__ mpid,
+                                int n, double *__restrict__ xyz, float *__restrict__ vel,
+                                float *__restrict__ sig, float *__restrict__ rho)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const uint32_t id = mpid[m];
+    double x[3];
+    abs_pos(p, M.pos[m], x);
+    for (int k = 0; k < 3; ++k) xyz[3 * (size_t)id + k] = x[k];
+    const float4 v = M.vel[m];
+    vel[3 * (size_t)id] = v.x; vel[3 * (size_t)id + 1] = v.y; vel[3 * (size_t)id + 2] = v.z;
+    rho[id] = v.w;
+    const float4 a = M.sA[m];
+    const float2 b = M.sB[m];
+    float *o = sig + 6 * (size_t)id;
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+}
+
+// ---------------------------------------------------------------------------
+void launch_box_prep(const DevParams &p, int nbox, const int *box_body, const double *box_half,
+                     const double *box_off, const BodyDev *bodies, const int *colF,
+                     const int *colM, const int *drift, int all_active, int n_fluid_master,
+                     int n_fixed_master, int64_t cand_cap, void *frames, int *win, int *ranges,
+                     int *rinfo, int *counts, int *abort_flag, int64_t step_tag, cudaStream_t st)
+{
+    k_box_prep<<<1, 32, 0, st>>>(p, nbox, box_body, box_half, box_off, bodies, colF, colM, drift,
+                                 all_active, n_fluid_master, n_fixed_master, cand_cap,
+                                 (BoxFrame *)frames, win, ranges, rinfo, counts, abort_flag,
+                                 step_tag);
+}
+
+void launch_activity(const DevParams &p, int nbox, const void *frames, const int *ranges,
+                     const int *rinfo, const float4 *mpos, const double *mloc,
+                     const int *fixed_order, int all_active, int64_t cand_cap, uint32_t *include,
+                     uint8_t *kind, int *counts, const int *abort_flag, cudaStream_t st)
+{
+    const unsigned g = (unsigned)std::min<int64_t>(grid_for(cand_cap), 148 * 16);
+    k_activity<<<g, kBlock, 0, st>>>(p, nbox, (const BoxFrame *)frames, ranges, rinfo, mpos, mloc,
+                                     fixed_order, all_active, cand_cap, include, kind, counts,
+                                     abort_flag);
+}
+
+void launch_active_sizes(const DevParams &p, const int *rinfo, const uint32_t *slot,
+                         int n_body_markers, int *counts, int *abort_flag, int64_t step_tag,
+                         cudaStream_t st)
+{
+    k_active_sizes<<<1, 32, 0, st>>>(p, rinfo, slot, n_body_markers, counts, abort_flag, step_tag);
+}
+
+void launch_gather(const DevParams &p, const int *ranges, const int *rinfo,
+                   const uint8_t *kind, const uint32_t *slot,
+                   StageArrays M, const uint32_t *mpid, const int *fixed_order,
+                   const int *body_markers, int n_body_markers, int n_fluid_total,
+                   int64_t cand_cap, StageArrays W, uint32_t *wpid, const int *counts,
+                   const int *abort_flag, cudaStream_t st)
+{
+    const unsigned g = (unsigned)std::min<int64_t>(grid_for(cand_cap + n_body_markers), 148 * 16);
+    k_gather<<<g, kBlock, 0, st>>>(p, ranges, rinfo, kind, slot, M, mpid, fixed_order,
+                                   body_markers, n_body_markers, n_fluid_total, cand_cap, W, wpid,
+                                   counts, abort_flag);
+}
+
+void launch_scatter_back(const DevParams &p, StageArrays W, const uint32_t *wpid,
+                         const uint32_t *mslot_of_pid, const int *mcol, StageArrays M, int *drift,
+                         cudaStream_t st)
+{
+    k_scatter_back<<<grid_for(p.capF), kBlock, 0, st>>>(p, W, wpid, mslot_of_pid, mcol, M, drift);
+}
+
+void launch_export_master(const DevParams &p, StageArrays M, const uint32_t *mpid, int n,
+                          double *xyz, float *vel, float *sig, float *rho, cudaStream_t st)
+{
+    k_export_master<<<grid_for(n), kBlock, 0, st>>>(p, M, mpid, n, xyz, vel, sig, rho);
+}
+
+size_t box_frame_bytes() { return sizeof(BoxFrame); }
+
+}  // namespace crm

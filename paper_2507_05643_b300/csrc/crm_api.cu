@@ -1,20 +1,36 @@
 // crm_api.cu -- host side of the C ABI declared in include/crm.h.
 //
 // The handle keeps the inputs on the host until the first step, then
-// "commits": sizes the grid, allocates every device array once and uploads
-// the particles in insertion order; the first rebuild sorts them by cell.
-// Each step enqueues the kernels of Alg. 2 (rebuild every ps_freq steps) and
-// the two RK2 stages on the handle's stream.
+// "commits": sizes the grid, allocates the device arrays and uploads the
+// particles.  Each step enqueues the kernels of Alg. 2 / Alg. 3 on the
+// handle's stream: a rebuild every ps_freq steps (in active-domain runs the
+// rebuild first refreshes the activity flags and regathers the working set),
+// then the two RK2 stages.
+//
+// Without active boxes the working set is every particle and nothing is
+// synchronised inside crm_step.  With active boxes the working-set size is
+// decided on the device; when it outgrows a capacity the step is abandoned on
+// the device (an abort word every later kernel checks), and the host, which
+// runs the steps in chunks of at most S_I steps, grows the arrays by G and
+// resumes from that step.  Every S_I steps it shrinks them to the current size
+// when they are less than S full (ManageArrayMemory, Sec. 3.2).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
 #include "crm_internal.cuh"
 
 using namespace crm;
+
+namespace {
+enum { G_STATIC, G_WORK, G_WIN, G_CAND, G_COUNT };
+// device counters word layout
+enum { C_NF, C_NM, C_N, C_NA, C_NE, C_NEED_F, C_NEED_M, C_NEED_CELLS, C_NEED_CAND, C_WORDS = 16 };
+}  // namespace
 
 struct crm_terrain {
     crm_params P{};
@@ -26,29 +42,51 @@ struct crm_terrain {
     std::vector<double> hmloc;                   // marker body-frame / world coordinates
     std::vector<int> hmbody;                     // body of each marker, -1 fixed
     std::vector<BodyDev> hbodies;
-    struct Box { int body; double half[3], off[3], t_delay; };
-    std::vector<Box> boxes;
+    std::vector<int> box_body_h;
+    std::vector<double> box_half_h, box_off_h;
+    double t_delay = 0.0;
 
     bool committed = false;
     bool lists_valid = false;
+    bool active = false;          // any active box
+    bool have_working = false;    // working set holds state not yet written back
     int64_t step_index = 0;
     double time = 0.0;
     int64_t nFtot = 0, nMtot = 0;
     DevParams dp{};
 
-    // device state
+    // capacities
+    int64_t capF = 0, capM = 0, Mcap = 0, cand_cap = 0;
+
+    // device state: working set
     int cur = 0;
     StageArrays A[2]{}, MID{};
     uint32_t *pid[2]{};
     SortScratch ss{};
     uint32_t *start = nullptr, *nbr = nullptr, *nnb = nullptr;
+    float4 *mforce = nullptr, *mtorque = nullptr;
+    double *partial = nullptr;
+    // static
     double *mloc = nullptr;
     int *mbody = nullptr;
     BodyDev *bodies = nullptr;
-    float4 *mforce = nullptr, *mtorque = nullptr;
-    double *partial = nullptr;
-    int *err = nullptr;
-    std::vector<void *> allocs;
+    int *err = nullptr, *counts = nullptr, *win = nullptr, *abort_flag = nullptr;
+    int *h_counts = nullptr;      // pinned mirror: counters + abort word
+    // active domains: master store and candidates
+    StageArrays Mst{};
+    uint32_t *mpid = nullptr, *mslot_of_pid = nullptr;
+    int *mcol = nullptr, *colF = nullptr, *colM = nullptr, *fixed_order = nullptr,
+        *body_markers = nullptr, *drift = nullptr;
+    int n_fixed = 0, n_bodym = 0;
+    int *box_body = nullptr;
+    double *box_half = nullptr, *box_off = nullptr;
+    void *frames = nullptr;
+    int *ranges = nullptr, *rinfo = nullptr;
+    uint32_t *cinc = nullptr, *cslot = nullptr;
+    uint8_t *ckind = nullptr;
+    SortScratch cscan{};
+
+    std::vector<void *> allocs[G_COUNT];
     bool oom = false;
 
     // measurement: launch counters and optional per-launch CUDA events
@@ -63,7 +101,7 @@ struct crm_terrain {
         msg = m;
         return code;
     }
-    template <class T> T *dalloc(size_t count)
+    template <class T> T *dalloc(int group, size_t count)
     {
         void *p = nullptr;
         if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
@@ -71,8 +109,14 @@ struct crm_terrain {
             oom = true;
             return nullptr;
         }
-        allocs.push_back(p);
+        allocs[group].push_back(p);
         return (T *)p;
+    }
+    void free_group(int group)
+    {
+        for (void *p : allocs[group])
+            if (p) cudaFree(p);
+        allocs[group].clear();
     }
 };
 
@@ -134,9 +178,6 @@ int make_devparams(crm_terrain *t)
     }
     if ((double)G[0] * (double)G[1] * (double)G[2] >= 4294967295.0)
         return t->fail(CRM_EINVAL, "grid of 2h cells over the domain exceeds 2^32 cells");
-    const double Mw = (double)G[0] * G[1] * G[2];
-    if (2.0 * Mw + 1.0 >= 2147483647.0)
-        return t->fail(CRM_EINVAL, "grid too large for the cell sort (2M + 1 >= 2^31)");
     const double pi = 3.14159265358979323846;
     const double Gm = P.E / (2.0 * (1.0 + P.nu)), Km = P.E / (3.0 * (1.0 - 2.0 * P.nu));
     const double m = P.rho0 * P.d0 * P.d0 * P.d0;
@@ -162,9 +203,6 @@ int make_devparams(crm_terrain *t)
     d.grain_d = (float)P.grain_d;
     d.cohesion = (float)P.cohesion;
     d.GX = (int)G[0]; d.GY = (int)G[1]; d.GZ = (int)G[2];
-    d.wx0 = d.wy0 = d.wz0 = 0;
-    d.WX = d.GX; d.WY = d.GY; d.WZ = d.GZ;
-    d.M = (uint32_t)(G[0] * G[1] * G[2]);
     d.dmin_x = P.domain_min[0];
     d.dmin_y = P.domain_min[1];
     d.dmin_z = P.domain_min[2];
@@ -178,6 +216,24 @@ bool inside_domain(const crm_params &P, const double *x)
     for (int k = 0; k < 3; ++k)
         if (!(x[k] >= P.domain_min[k] && x[k] < P.domain_max[k])) return false;
     return true;
+}
+
+void cell_of(const DevParams &d, const double *x, int c[3], float o[3])
+{
+    const double dm[3] = {d.dmin_x, d.dmin_y, d.dmin_z};
+    for (int k = 0; k < 3; ++k) {
+        c[k] = (int)std::floor((x[k] - dm[k]) / d.cell_d);
+        o[k] = (float)(x[k] - (dm[k] + c[k] * d.cell_d));
+    }
+}
+
+float cell_bits(const DevParams &d, const int c[3])
+{
+    const uint32_t g = ((uint32_t)c[2] * (uint32_t)d.GY + (uint32_t)c[1]) * (uint32_t)d.GX
+                       + (uint32_t)c[0];
+    float f;
+    std::memcpy(&f, &g, 4);
+    return f;
 }
 
 int latched_error(crm_terrain *t)
@@ -194,6 +250,130 @@ int latched_error(crm_terrain *t)
     return t->fail(CRM_ETIMEOUT, "a bounded device-side wait gave up");
 }
 
+// Working-set arrays for capF fluid + capM marker slots.
+int alloc_working(crm_terrain *t)
+{
+    t->free_group(G_WORK);
+    DevParams &d = t->dp;
+    const int64_t N = t->capF + t->capM;
+    d.capF = (int)t->capF;
+    d.capM = (int)t->capM;
+    d.capN = (int)N;
+    d.ell = (uint32_t)std::max<int64_t>(N, 1);
+    for (int b = 0; b < 2; ++b) {
+        t->A[b].pos = t->dalloc<float4>(G_WORK, N);
+        t->A[b].vel = t->dalloc<float4>(G_WORK, N);
+        t->A[b].sA = t->dalloc<float4>(G_WORK, N);
+        t->A[b].sB = t->dalloc<float2>(G_WORK, N);
+        t->pid[b] = t->dalloc<uint32_t>(G_WORK, N);
+    }
+    t->MID.pos = t->dalloc<float4>(G_WORK, N);
+    t->MID.vel = t->dalloc<float4>(G_WORK, N);
+    t->MID.sA = t->dalloc<float4>(G_WORK, N);
+    t->MID.sB = t->dalloc<float2>(G_WORK, N);
+    t->ss.keys = t->dalloc<uint32_t>(G_WORK, N);
+    t->ss.rank = t->dalloc<uint32_t>(G_WORK, N);
+    t->ss.tmp = t->dalloc<uint32_t>(G_WORK, N);
+    t->nbr = t->dalloc<uint32_t>(G_WORK, (size_t)d.maxnb * d.ell);
+    t->nnb = t->dalloc<uint32_t>(G_WORK, N);
+    t->mforce = t->dalloc<float4>(G_WORK, t->capM);
+    t->mtorque = t->dalloc<float4>(G_WORK, t->capM);
+    t->partial = t->dalloc<double>(G_WORK, (size_t)grid_for(t->capM)
+                                               * std::max<size_t>(t->hbodies.size(), 1) * 6);
+    if (t->oom) return t->fail(CRM_ENOMEM, "device allocation of the working set failed");
+    CRM_CUDA(t, cudaMemsetAsync(t->nnb, 0, N * sizeof(uint32_t), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->mforce, 0, std::max<int64_t>(t->capM, 1) * sizeof(float4), t->st));
+    t->cur = 0;
+    t->lists_valid = false;
+    return CRM_OK;
+}
+
+// Counting-sort key space: 2 Mcap + 1 cell counters and ranges.
+int alloc_window(crm_terrain *t)
+{
+    t->free_group(G_WIN);
+    t->dp.M = (uint32_t)t->Mcap;
+    const size_t nk = 2 * (size_t)t->Mcap + 1;
+    t->ss.count = t->dalloc<uint32_t>(G_WIN, nk);
+    t->ss.n_tiles = ((int64_t)nk + kScanTile - 1) / kScanTile;
+    t->ss.tile_status = t->dalloc<unsigned long long>(G_WIN, t->ss.n_tiles);
+    t->ss.ctr = t->dalloc<uint32_t>(G_WIN, 4);
+    t->start = t->dalloc<uint32_t>(G_WIN, nk);
+    if (t->oom) return t->fail(CRM_ENOMEM, "device allocation of the cell arrays failed");
+    CRM_CUDA(t, cudaMemsetAsync(t->ss.count, 0, nk * sizeof(uint32_t), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->ss.tile_status, 0, t->ss.n_tiles * sizeof(unsigned long long), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->ss.ctr, 0, 4 * sizeof(uint32_t), t->st));
+    return CRM_OK;
+}
+
+// Candidate arrays of the activity pass (active domains).
+int alloc_cand(crm_terrain *t)
+{
+    t->free_group(G_CAND);
+    const size_t n = (size_t)t->cand_cap + 1;
+    t->cinc = t->dalloc<uint32_t>(G_CAND, n);
+    t->cslot = t->dalloc<uint32_t>(G_CAND, n);
+    t->ckind = t->dalloc<uint8_t>(G_CAND, n);
+    t->cscan.n_tiles = ((int64_t)n + kScanTile - 1) / kScanTile;
+    t->cscan.tile_status = t->dalloc<unsigned long long>(G_CAND, t->cscan.n_tiles);
+    t->cscan.ctr = t->dalloc<uint32_t>(G_CAND, 4);
+    if (t->oom) return t->fail(CRM_ENOMEM, "device allocation of the activity arrays failed");
+    CRM_CUDA(t, cudaMemsetAsync(t->cinc, 0, n * sizeof(uint32_t), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->cscan.tile_status, 0, t->cscan.n_tiles * sizeof(unsigned long long), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->cscan.ctr, 0, 4 * sizeof(uint32_t), t->st));
+    return CRM_OK;
+}
+
+template <class T> int upload(crm_terrain *t, T *dev, const T *host, size_t n)
+{
+    if (n == 0) return CRM_OK;
+    CRM_CUDA(t, cudaMemcpyAsync(dev, host, n * sizeof(T), cudaMemcpyHostToDevice, t->st));
+    return CRM_OK;
+}
+
+// Host estimate of the window cells and candidate count of the boxes at the
+// bodies' current poses (initial capacities of an active-domain run).
+void estimate_active(crm_terrain *t, const std::vector<int> &colF_h, const std::vector<int> &colM_h,
+                     int64_t &cells, int64_t &cand, int64_t &fluid)
+{
+    const DevParams &d = t->dp;
+    const int G[3] = {d.GX, d.GY, d.GZ};
+    const double dm[3] = {d.dmin_x, d.dmin_y, d.dmin_z};
+    int lo[3] = {G[0], G[1], G[2]}, hi[3] = {-1, -1, -1};
+    cand = 0;
+    fluid = 0;
+    for (size_t b = 0; b < t->box_body_h.size(); ++b) {
+        const BodyDev &B = t->hbodies[t->box_body_h[b]];
+        const double *q = B.pose + 3;
+        const double w = q[0], x = q[1], y = q[2], z = q[3];
+        const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                             2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                             2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+        double eg[3], c[3], vol = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            eg[k] = t->box_half_h[3 * b + k] + 2.0 * t->P.h;
+            vol *= 2.0 * eg[k];
+        }
+        for (int k = 0; k < 3; ++k)
+            c[k] = B.pose[k] + R[3 * k] * t->box_off_h[3 * b] + R[3 * k + 1] * t->box_off_h[3 * b + 1]
+                   + R[3 * k + 2] * t->box_off_h[3 * b + 2];
+        int xa = 0, xb = -1;
+        for (int k = 0; k < 3; ++k) {
+            const double ext = std::fabs(R[3 * k]) * eg[0] + std::fabs(R[3 * k + 1]) * eg[1]
+                               + std::fabs(R[3 * k + 2]) * eg[2];
+            int a = std::max((int)std::floor((c[k] - ext - dm[k]) / d.cell_d) - 1, 0);
+            int e = std::min((int)std::floor((c[k] + ext - dm[k]) / d.cell_d) + 1, G[k] - 1);
+            lo[k] = std::min(lo[k], a);
+            hi[k] = std::max(hi[k], e);
+            if (k == 0) { xa = a; xb = e; }
+        }
+        if (xb >= xa) cand += colF_h[xb + 1] - colF_h[xa] + colM_h[xb + 1] - colM_h[xa];
+        fluid += (int64_t)(vol / (t->P.d0 * t->P.d0 * t->P.d0));
+    }
+    cells = 1;
+    for (int k = 0; k < 3; ++k) cells *= std::max(hi[k] - lo[k] + 1, 1);
+}
+
 int commit(crm_terrain *t)
 {
     if (t->committed) return CRM_OK;
@@ -203,104 +383,209 @@ int commit(crm_terrain *t)
     int rc = make_devparams(t);
     if (rc) return rc;
     DevParams &d = t->dp;
-    d.nF = (int)nF;
-    d.nM = (int)nM;
-    d.N = (int)N;
-    d.ell = (uint32_t)std::max<int64_t>(N, 1);
     d.n_bodies = (int)t->hbodies.size();
-    const size_t nk = 2 * (size_t)d.M + 1;
+    t->active = !t->box_body_h.empty();
+    const int64_t full_cells = (int64_t)d.GX * d.GY * d.GZ;
+    cudaStream_t st = t->st;
 
-    for (int b = 0; b < 2; ++b) {
-        t->A[b].pos = t->dalloc<float4>(N);
-        t->A[b].vel = t->dalloc<float4>(N);
-        t->A[b].sA = t->dalloc<float4>(N);
-        t->A[b].sB = t->dalloc<float2>(N);
-        t->pid[b] = t->dalloc<uint32_t>(N);
-    }
-    t->MID.pos = t->dalloc<float4>(N);
-    t->MID.vel = t->dalloc<float4>(N);
-    t->MID.sA = t->dalloc<float4>(N);
-    t->MID.sB = t->dalloc<float2>(N);
-    t->ss.keys = t->dalloc<uint32_t>(N);
-    t->ss.rank = t->dalloc<uint32_t>(N);
-    t->ss.tmp = t->dalloc<uint32_t>(N);
-    t->ss.count = t->dalloc<uint32_t>(nk);
-    t->ss.n_tiles = ((int64_t)nk + kScanTile - 1) / kScanTile;
-    t->ss.tile_status = t->dalloc<unsigned long long>(t->ss.n_tiles);
-    t->ss.ctr = t->dalloc<uint32_t>(4);
-    t->start = t->dalloc<uint32_t>(nk);
-    t->nbr = t->dalloc<uint32_t>((size_t)d.maxnb * d.ell);
-    t->nnb = t->dalloc<uint32_t>(N);
-    t->mloc = t->dalloc<double>(3 * nM);
-    t->mbody = t->dalloc<int>(nM);
-    t->bodies = t->dalloc<BodyDev>(t->hbodies.size());
-    t->mforce = t->dalloc<float4>(nM);
-    t->mtorque = t->dalloc<float4>(nM);
-    t->partial = t->dalloc<double>((size_t)grid_for(nM) * std::max<size_t>(t->hbodies.size(), 1) * 6);
-    t->err = t->dalloc<int>(1);
+    // static device state
+    t->mloc = t->dalloc<double>(G_STATIC, 3 * nM);
+    t->mbody = t->dalloc<int>(G_STATIC, nM);
+    t->bodies = t->dalloc<BodyDev>(G_STATIC, t->hbodies.size());
+    t->err = t->dalloc<int>(G_STATIC, 1);
+    t->counts = t->dalloc<int>(G_STATIC, C_WORDS);
+    t->win = t->dalloc<int>(G_STATIC, 8);
+    t->abort_flag = t->dalloc<int>(G_STATIC, 1);
     if (t->oom) return t->fail(CRM_ENOMEM, "device allocation failed");
+    if (!t->h_counts && cudaMallocHost(&t->h_counts, (C_WORDS + 2) * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        t->h_counts = nullptr;
+        return t->fail(CRM_ENOMEM, "pinned host allocation failed");
+    }
+    d.sizes = t->counts;
+    d.win = t->win;
+    d.abort = t->abort_flag;
+    CRM_CUDA(t, cudaMemsetAsync(t->err, 0, sizeof(int), st));
+    CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), st));
+    CRM_CUDA(t, cudaMemsetAsync(t->counts, 0, C_WORDS * sizeof(int), st));
+    if (nM) {
+        rc = upload(t, t->mloc, t->hmloc.data(), 3 * nM);
+        if (!rc) rc = upload(t, t->mbody, t->hmbody.data(), nM);
+        if (rc) return rc;
+    }
+    if (!t->hbodies.empty()) {
+        rc = upload(t, t->bodies, t->hbodies.data(), t->hbodies.size());
+        if (rc) return rc;
+    }
 
-    // initial state in insertion order: SPH first, then markers
-    std::vector<float4> pos(N), vel(N), sA(N);
-    std::vector<float2> sB(N);
-    std::vector<uint32_t> pid(N);
-    const double cell = d.cell_d;
+    // initial state, converted to cell-relative form on the host
+    std::vector<float4> pos(nF), vel(nF), sA(nF);
+    std::vector<float2> sB(nF);
+    std::vector<int> cx(nF);
     for (int64_t i = 0; i < nF; ++i) {
-        const double *x = &t->hx[3 * i];
         int c[3];
         float o[3];
-        const double dm[3] = {d.dmin_x, d.dmin_y, d.dmin_z};
-        for (int k = 0; k < 3; ++k) {
-            c[k] = (int)std::floor((x[k] - dm[k]) / cell);
-            o[k] = (float)(x[k] - (dm[k] + c[k] * cell));
-        }
-        const uint32_t g = ((uint32_t)c[2] * (uint32_t)d.GY + (uint32_t)c[1]) * (uint32_t)d.GX
-                           + (uint32_t)c[0];
-        uint32_t gb;
-        std::memcpy(&gb, &g, 4);
-        float gf;
-        std::memcpy(&gf, &gb, 4);
-        pos[i] = make_float4(o[0], o[1], o[2], gf);
+        cell_of(d, &t->hx[3 * i], c, o);
+        cx[i] = c[0];
+        pos[i] = make_float4(o[0], o[1], o[2], cell_bits(d, c));
         vel[i] = make_float4((float)t->hu[3 * i], (float)t->hu[3 * i + 1], (float)t->hu[3 * i + 2],
                              (float)t->hr[i]);
         const double *s = &t->hs[6 * i];
         sA[i] = make_float4((float)s[0], (float)s[1], (float)s[2], (float)s[3]);
         sB[i] = make_float2((float)s[4], (float)s[5]);
-        pid[i] = (uint32_t)i;
     }
+
+    if (!t->active) {
+        // every particle is in the working set for good
+        t->capF = nF;
+        t->capM = nM;
+        t->Mcap = full_cells;
+        if (2.0 * (double)t->Mcap + 1.0 >= 2147483647.0)
+            return t->fail(CRM_EINVAL, "grid too large for the cell sort (2M + 1 >= 2^31)");
+        rc = alloc_working(t);
+        if (!rc) rc = alloc_window(t);
+        if (rc) return rc;
+        std::vector<float4> p4(N), v4(N), a4(N);
+        std::vector<float2> b2(N);
+        std::vector<uint32_t> pid(N);
+        for (int64_t i = 0; i < N; ++i) {
+            if (i < nF) {
+                p4[i] = pos[i]; v4[i] = vel[i]; a4[i] = sA[i]; b2[i] = sB[i];
+            } else {
+                p4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                v4[i] = make_float4(0.f, 0.f, 0.f, (float)t->P.rho0);
+                a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                b2[i] = make_float2(0.f, 0.f);
+            }
+            pid[i] = (uint32_t)i;
+        }
+        const int c = t->cur;
+        rc = upload(t, t->A[c].pos, p4.data(), N);
+        if (!rc) rc = upload(t, t->A[c].vel, v4.data(), N);
+        if (!rc) rc = upload(t, t->A[c].sA, a4.data(), N);
+        if (!rc) rc = upload(t, t->A[c].sB, b2.data(), N);
+        if (!rc) rc = upload(t, t->pid[c], pid.data(), N);
+        if (rc) return rc;
+        const int sizes[5] = {(int)nF, (int)nM, (int)N, (int)nF, 0};
+        const int win[6] = {0, 0, 0, d.GX, d.GY, d.GZ};
+        rc = upload(t, t->counts, sizes, 5);
+        if (!rc) rc = upload(t, t->win, win, 6);
+        if (rc) return rc;
+        CRM_CUDA(t, cudaStreamSynchronize(st));
+        t->committed = true;
+        return CRM_OK;
+    }
+
+    // ---- active domains: master store sorted by cell, x slowest --------------
+    std::vector<int64_t> key(nF);
+    std::vector<int> order(nF);
+    for (int64_t i = 0; i < nF; ++i) {
+        int c[3];
+        float o[3];
+        cell_of(d, &t->hx[3 * i], c, o);
+        key[i] = ((int64_t)c[0] * d.GY + c[1]) * d.GZ + c[2];
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::vector<float4> mp(nF), mv(nF), ma(nF);
+    std::vector<float2> mb(nF);
+    std::vector<uint32_t> mpid(nF), mslot(nF);
+    std::vector<int> mcol(nF), colF(d.GX + 1, 0), colM(d.GX + 1, 0);
+    for (int64_t m = 0; m < nF; ++m) {
+        const int i = order[m];
+        mp[m] = pos[i]; mv[m] = vel[i]; ma[m] = sA[i]; mb[m] = sB[i];
+        mpid[m] = (uint32_t)i;
+        mslot[i] = (uint32_t)m;
+        mcol[m] = cx[i];
+        colF[cx[i] + 1] += 1;
+    }
+    for (int x = 0; x < d.GX; ++x) colF[x + 1] += colF[x];
+    std::vector<int> fixed, bodym;
     for (int64_t a = 0; a < nM; ++a) {
-        pos[nF + a] = make_float4(0.f, 0.f, 0.f, 0.f);
-        vel[nF + a] = make_float4(0.f, 0.f, 0.f, (float)t->P.rho0);
-        sA[nF + a] = make_float4(0.f, 0.f, 0.f, 0.f);
-        sB[nF + a] = make_float2(0.f, 0.f);
-        pid[nF + a] = (uint32_t)(nF + a);
+        if (t->hmbody[a] < 0) fixed.push_back((int)a);
+        else bodym.push_back((int)a);
     }
-    cudaStream_t st = t->st;
-    const int c = t->cur;
-    CRM_CUDA(t, cudaMemcpyAsync(t->A[c].pos, pos.data(), N * sizeof(float4), cudaMemcpyHostToDevice, st));
-    CRM_CUDA(t, cudaMemcpyAsync(t->A[c].vel, vel.data(), N * sizeof(float4), cudaMemcpyHostToDevice, st));
-    CRM_CUDA(t, cudaMemcpyAsync(t->A[c].sA, sA.data(), N * sizeof(float4), cudaMemcpyHostToDevice, st));
-    CRM_CUDA(t, cudaMemcpyAsync(t->A[c].sB, sB.data(), N * sizeof(float2), cudaMemcpyHostToDevice, st));
-    CRM_CUDA(t, cudaMemcpyAsync(t->pid[c], pid.data(), N * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    if (nM) {
-        CRM_CUDA(t, cudaMemcpyAsync(t->mloc, t->hmloc.data(), 3 * nM * sizeof(double),
-                                    cudaMemcpyHostToDevice, st));
-        CRM_CUDA(t, cudaMemcpyAsync(t->mbody, t->hmbody.data(), nM * sizeof(int),
-                                    cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> fkey(fixed.size());
+    for (size_t k = 0; k < fixed.size(); ++k) {
+        int c[3];
+        float o[3];
+        cell_of(d, &t->hmloc[3 * (size_t)fixed[k]], c, o);
+        fkey[k] = ((int64_t)c[0] * d.GY + c[1]) * d.GZ + c[2];
     }
-    if (!t->hbodies.empty())
-        CRM_CUDA(t, cudaMemcpyAsync(t->bodies, t->hbodies.data(), t->hbodies.size() * sizeof(BodyDev),
-                                    cudaMemcpyHostToDevice, st));
-    CRM_CUDA(t, cudaMemsetAsync(t->ss.count, 0, nk * sizeof(uint32_t), st));
-    CRM_CUDA(t, cudaMemsetAsync(t->ss.tile_status, 0, t->ss.n_tiles * sizeof(unsigned long long), st));
-    CRM_CUDA(t, cudaMemsetAsync(t->ss.ctr, 0, 4 * sizeof(uint32_t), st));
-    CRM_CUDA(t, cudaMemsetAsync(t->nnb, 0, N * sizeof(uint32_t), st));
-    CRM_CUDA(t, cudaMemsetAsync(t->err, 0, sizeof(int), st));
-    CRM_CUDA(t, cudaMemsetAsync(t->mforce, 0, std::max<int64_t>(nM, 1) * sizeof(float4), st));
-    // the host staging vectors die at return: wait for the copies
+    std::vector<int> forder(fixed.size());
+    std::iota(forder.begin(), forder.end(), 0);
+    std::stable_sort(forder.begin(), forder.end(), [&](int a, int b) { return fkey[a] < fkey[b]; });
+    std::vector<int> fixed_sorted(fixed.size());
+    for (size_t k = 0; k < fixed.size(); ++k) {
+        fixed_sorted[k] = fixed[forder[k]];
+        const int x = (int)(fkey[forder[k]] / ((int64_t)d.GY * d.GZ));
+        colM[x + 1] += 1;
+    }
+    for (int x = 0; x < d.GX; ++x) colM[x + 1] += colM[x];
+    t->n_fixed = (int)fixed.size();
+    t->n_bodym = (int)bodym.size();
+
+    t->Mst.pos = t->dalloc<float4>(G_STATIC, nF);
+    t->Mst.vel = t->dalloc<float4>(G_STATIC, nF);
+    t->Mst.sA = t->dalloc<float4>(G_STATIC, nF);
+    t->Mst.sB = t->dalloc<float2>(G_STATIC, nF);
+    t->mpid = t->dalloc<uint32_t>(G_STATIC, nF);
+    t->mslot_of_pid = t->dalloc<uint32_t>(G_STATIC, nF);
+    t->mcol = t->dalloc<int>(G_STATIC, nF);
+    t->colF = t->dalloc<int>(G_STATIC, d.GX + 1);
+    t->colM = t->dalloc<int>(G_STATIC, d.GX + 1);
+    t->fixed_order = t->dalloc<int>(G_STATIC, fixed.size());
+    t->body_markers = t->dalloc<int>(G_STATIC, bodym.size());
+    t->drift = t->dalloc<int>(G_STATIC, 1);
+    const size_t nbox = t->box_body_h.size();
+    t->box_body = t->dalloc<int>(G_STATIC, nbox);
+    t->box_half = t->dalloc<double>(G_STATIC, 3 * nbox);
+    t->box_off = t->dalloc<double>(G_STATIC, 3 * nbox);
+    t->frames = t->dalloc<char>(G_STATIC, box_frame_bytes() * kMaxBodies);
+    t->ranges = t->dalloc<int>(G_STATIC, 4 * kMaxBodies + 4);
+    t->rinfo = t->dalloc<int>(G_STATIC, 4 * kMaxBodies + 8);
+    if (t->oom) return t->fail(CRM_ENOMEM, "device allocation of the master store failed");
+    rc = upload(t, t->Mst.pos, mp.data(), nF);
+    if (!rc) rc = upload(t, t->Mst.vel, mv.data(), nF);
+    if (!rc) rc = upload(t, t->Mst.sA, ma.data(), nF);
+    if (!rc) rc = upload(t, t->Mst.sB, mb.data(), nF);
+    if (!rc) rc = upload(t, t->mpid, mpid.data(), nF);
+    if (!rc) rc = upload(t, t->mslot_of_pid, mslot.data(), nF);
+    if (!rc) rc = upload(t, t->mcol, mcol.data(), nF);
+    if (!rc) rc = upload(t, t->colF, colF.data(), colF.size());
+    if (!rc) rc = upload(t, t->colM, colM.data(), colM.size());
+    if (!rc) rc = upload(t, t->fixed_order, fixed_sorted.data(), fixed_sorted.size());
+    if (!rc) rc = upload(t, t->body_markers, bodym.data(), bodym.size());
+    if (!rc) rc = upload(t, t->box_body, t->box_body_h.data(), nbox);
+    if (!rc) rc = upload(t, t->box_half, t->box_half_h.data(), 3 * nbox);
+    if (!rc) rc = upload(t, t->box_off, t->box_off_h.data(), 3 * nbox);
+    if (rc) return rc;
+    CRM_CUDA(t, cudaMemsetAsync(t->drift, 0, sizeof(int), st));
+
+    // initial capacities: everything when the first step is before t_delay
+    // (Alg. 3 processes all particles then), else the boxes' estimate
+    if (!(0.0 > t->t_delay)) {
+        t->capF = std::max<int64_t>(nF, 1);
+        t->capM = std::max<int64_t>(nM, 1);
+        t->Mcap = full_cells;
+        t->cand_cap = std::max<int64_t>(nF + t->n_fixed, 1);
+    } else {
+        int64_t cells = 0, cand = 0, fl = 0;
+        estimate_active(t, colF, colM, cells, cand, fl);
+        t->capF = std::max<int64_t>(std::min<int64_t>(nF, (int64_t)(t->P.growth * fl) + 256), 1);
+        t->capM = std::max<int64_t>(std::min<int64_t>(nM, t->n_bodym + t->capF), 1);
+        t->Mcap = std::min<int64_t>(full_cells, (int64_t)(cells * 1.5) + 64);
+        t->cand_cap = std::max<int64_t>((int64_t)(cand * t->P.growth) + 256, 1);
+    }
+    if (2.0 * (double)t->Mcap + 1.0 >= 2147483647.0)
+        return t->fail(CRM_EINVAL, "grid too large for the cell sort (2M + 1 >= 2^31)");
+    rc = alloc_working(t);
+    if (!rc) rc = alloc_window(t);
+    if (!rc) rc = alloc_cand(t);
+    if (rc) return rc;
     CRM_CUDA(t, cudaStreamSynchronize(st));
     t->committed = true;
-    t->lists_valid = false;
+    t->have_working = false;
     return CRM_OK;
 }
 
@@ -311,7 +596,9 @@ const char *const kKernelNames[CRM_NUM_KERNELS] = {
     "wrench_partial", "body_update", "export"};
 
 // Enqueue one kernel through `launch`, counting it and, when timing is on,
-// bracketing it with two events on the handle's stream.
+// bracketing it with two events on the handle's stream.  The active-domain
+// kernels are counted under "keys" (flags, compaction, gather), "scan" and
+// "export" (write-back to the master store).
 template <class F> void launch(crm_terrain *t, int k, F &&f)
 {
     t->prof.launches[k] += 1;
@@ -337,11 +624,48 @@ template <class F> void launch(crm_terrain *t, int k, F &&f)
     }
 }
 
+// Write the Active particles of the working set back to the master store.
+void scatter_back(crm_terrain *t)
+{
+    if (!t->active || !t->have_working) return;
+    const int c = t->cur;
+    launch(t, K_EXPORT, [&] { launch_scatter_back(t->dp, t->A[c], t->pid[c], t->mslot_of_pid,
+                                                  t->mcol, t->Mst, t->drift, t->st); });
+}
+
+// Activity flags, counts and the gather of the working set (Alg. 3 items 1-3).
+void activity_pass(crm_terrain *t)
+{
+    const DevParams &d = t->dp;
+    const int all = !(t->time > t->t_delay);
+    const int c = t->cur;
+    scatter_back(t);
+    const int nbox = (int)t->box_body_h.size();
+    launch(t, K_KEYS, [&] { launch_box_prep(d, nbox, t->box_body, t->box_half, t->box_off,
+                                            t->bodies, t->colF, t->colM, t->drift, all,
+                                            (int)t->nFtot, t->n_fixed, t->cand_cap, t->frames,
+                                            t->win, t->ranges, t->rinfo, t->counts, t->abort_flag,
+                                            t->step_index, t->st); });
+    launch(t, K_KEYS, [&] { launch_activity(d, nbox, t->frames, t->ranges, t->rinfo, t->Mst.pos,
+                                            t->mloc, t->fixed_order, all, t->cand_cap, t->cinc,
+                                            t->ckind, t->counts, t->abort_flag, t->st); });
+    launch(t, K_SCAN, [&] { launch_scan_reset(t->cinc, t->cslot, t->cand_cap + 1, t->cscan, t->err,
+                                              t->st); });
+    launch(t, K_KEYS, [&] { launch_active_sizes(d, t->rinfo, t->cslot, t->n_bodym, t->counts,
+                                                t->abort_flag, t->step_index, t->st); });
+    launch(t, K_KEYS, [&] { launch_gather(d, t->ranges, t->rinfo, t->ckind, t->cslot, t->Mst,
+                                          t->mpid, t->fixed_order, t->body_markers, t->n_bodym,
+                                          (int)t->nFtot, t->cand_cap, t->A[c], t->pid[c],
+                                          t->counts, t->abort_flag, t->st); });
+    t->have_working = true;
+}
+
 void rebuild(crm_terrain *t)
 {
+    if (t->active) activity_pass(t);
     const int c = t->cur, n = 1 - c;
     const DevParams &d = t->dp;
-    if (d.N > 0) {
+    if (d.capN > 0) {
         launch(t, K_KEYS, [&] { launch_keys(d, t->A[c], t->pid[c], t->mloc, t->mbody, t->bodies,
                                             t->ss, t->err, (int)t->nFtot, t->st); });
         launch(t, K_SCAN, [&] { launch_scan_reset(t->ss.count, t->start, 2 * (int64_t)d.M + 1,
@@ -360,7 +684,7 @@ void rebuild(crm_terrain *t)
 void bce(crm_terrain *t, StageArrays S, double tau, int accel)
 {
     const DevParams &d = t->dp;
-    if (d.nM == 0) return;
+    if (d.capM == 0) return;
     const int c = t->cur;
     launch(t, K_BCE, [&] { launch_bce(d, S, t->A[c].pos, t->pid[c], t->mloc, t->mbody, t->bodies,
                                       t->nbr, t->nnb, tau, accel, (int)t->nFtot, t->mforce,
@@ -370,9 +694,10 @@ void bce(crm_terrain *t, StageArrays S, double tau, int accel)
 void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, RateOut out)
 {
     const DevParams &d = t->dp;
-    if (d.nF == 0) return;
+    if (d.capF == 0) return;
     const int k = mode == kStage2 ? K_PAIR2 : K_PAIR1;
-    launch(t, k, [&] { launch_pair(mode, d, S, Y, t->MID, t->nbr, t->nnb, nullptr, dt, out, t->err,
+    const uint32_t *flags = t->active ? t->pid[t->cur] : nullptr;
+    launch(t, k, [&] { launch_pair(mode, d, S, Y, t->MID, t->nbr, t->nnb, flags, dt, out, t->err,
                                    t->st); });
 }
 
@@ -380,7 +705,7 @@ void wrench(crm_terrain *t, double dt, int integrate)
 {
     const DevParams &d = t->dp;
     if (d.n_bodies == 0) return;
-    if (d.nM > 0)
+    if (d.capM > 0)
         launch(t, K_WRENCH, [&] { launch_wrench_partial(d, t->mforce, t->mtorque, t->partial, t->st); });
     launch(t, K_BODY, [&] { launch_body_update(d, t->partial, t->bodies, dt, integrate, t->st); });
 }
@@ -399,6 +724,82 @@ void one_step(crm_terrain *t, double dt)
     t->step_index += 1;
     t->time += dt;
     t->prof.steps += 1;
+}
+
+int read_counts(crm_terrain *t)
+{
+    CRM_CUDA(t, cudaMemcpyAsync(t->h_counts, t->counts, C_WORDS * sizeof(int), cudaMemcpyDeviceToHost,
+                                t->st));
+    CRM_CUDA(t, cudaMemcpyAsync(t->h_counts + C_WORDS, t->abort_flag, sizeof(int),
+                                cudaMemcpyDeviceToHost, t->st));
+    CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    return CRM_OK;
+}
+
+int64_t grown(int64_t need, double G) { return (int64_t)std::ceil((double)need * G) + 64; }
+
+// Active-domain stepping: chunks of at most S_I steps, then a sync to handle a
+// capacity overflow (grow by G and resume at the abandoned step) and, at S_I
+// boundaries, the shrink test of ManageArrayMemory (Sec. 3.2).
+int step_active(crm_terrain *t, double dt, int n_steps)
+{
+    const int SI = t->P.shrink_interval;
+    int remaining = n_steps;
+    int guard = 0;
+    while (remaining > 0) {
+        const int64_t s0 = t->step_index;
+        const double t0 = t->time;
+        const int chunk = (int)std::min<int64_t>(remaining, SI - (s0 % SI));
+        for (int s = 0; s < chunk; ++s) one_step(t, dt);
+        CRM_CUDA(t, cudaGetLastError());
+        int rc = read_counts(t);
+        if (rc) return rc;
+        const int ab = t->h_counts[C_WORDS];
+        if (ab != 0) {
+            if (++guard > 64) return t->fail(CRM_ENOMEM, "active-set capacity kept overflowing");
+            const int64_t failed = (int64_t)ab - 1;
+            const int64_t done = failed - s0;
+            t->step_index = failed;
+            t->time = t0 + (double)done * dt;
+            remaining -= (int)done;
+            t->prof.steps -= (chunk - done);
+            const int *h = t->h_counts;
+            const double G = t->P.growth;
+            bool work = false, win = false, cand = false;
+            if (h[C_NEED_F] > t->capF) { t->capF = grown(h[C_NEED_F], G); work = true; }
+            if (h[C_NEED_M] > t->capM) { t->capM = grown(h[C_NEED_M], G); work = true; }
+            if (h[C_NEED_CELLS] > t->Mcap) { t->Mcap = grown(h[C_NEED_CELLS], G); win = true; }
+            if (h[C_NEED_CAND] > t->cand_cap) { t->cand_cap = grown(h[C_NEED_CAND], G); cand = true; }
+            if (2.0 * (double)t->Mcap + 1.0 >= 2147483647.0)
+                return t->fail(CRM_EINVAL, "active window too large for the cell sort");
+            // the abandoned rebuild already wrote the working set back to the master
+            t->have_working = false;
+            if (work) { rc = alloc_working(t); if (rc) return rc; }
+            if (win) { rc = alloc_window(t); if (rc) return rc; }
+            if (cand) { rc = alloc_cand(t); if (rc) return rc; }
+            t->lists_valid = false;
+            CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), t->st));
+            CRM_CUDA(t, cudaMemsetAsync(t->counts + C_NEED_F, 0, 4 * sizeof(int), t->st));
+            continue;
+        }
+        remaining -= chunk;
+        if (t->step_index % SI == 0) {
+            // shrink the working arrays to the current size when under S full
+            const int64_t nF = t->h_counts[C_NF], nM = t->h_counts[C_NM];
+            const double S = t->P.shrink_ratio;
+            const bool shrink = (t->capF > 0 && (double)nF / (double)t->capF < S)
+                                || (t->capM > 0 && (double)nM / (double)t->capM < S);
+            if (shrink) {
+                scatter_back(t);
+                t->have_working = false;
+                t->capF = std::max<int64_t>(nF, 1);
+                t->capM = std::max<int64_t>(nM, 1);
+                rc = alloc_working(t);
+                if (rc) return rc;
+            }
+        }
+    }
+    return CRM_OK;
 }
 
 template <class T> int download(crm_terrain *t, T *host, const T *dev, size_t n)
@@ -460,6 +861,20 @@ void crm_default_params(crm_params *p)
     p->shrink_interval = 50;
 }
 
+int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
+                        double shrink_ratio, int32_t shrink_interval, int64_t *new_cap)
+{
+    if (!new_cap || need < 0 || cap < 0 || !(growth >= 1.0) || !(shrink_ratio > 0)
+        || shrink_interval < 1)
+        return CRM_EINVAL;
+    int64_t c = cap;
+    if (need > cap) c = (int64_t)std::ceil((double)need * growth);
+    else if (step % shrink_interval == 0 && cap > 0 && (double)need / (double)cap < shrink_ratio)
+        c = need;
+    *new_cap = c;
+    return CRM_OK;
+}
+
 int crm_create(const crm_params *p, void *cuda_stream, crm_terrain **out)
 {
     if (!out) return CRM_EINVAL;
@@ -487,8 +902,8 @@ int crm_destroy(crm_terrain *t)
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : t->ev_pool) cudaEventDestroy(e);
-    for (void *p : t->allocs)
-        if (p) cudaFree(p);
+    for (int g = 0; g < G_COUNT; ++g) t->free_group(g);
+    if (t->h_counts) cudaFreeHost(t->h_counts);
     delete t;
     return CRM_OK;
 }
@@ -599,7 +1014,16 @@ int crm_add_active_box(crm_terrain *t, int32_t body, const double half[3], const
     if (t->committed) return t->fail(CRM_ESTATE, "crm_add_active_box after the first step");
     if (body < 0 || body >= (int)t->hbodies.size() || !half || !off)
         return t->fail(CRM_EINVAL, "crm_add_active_box: bad body or null array");
-    return t->fail(CRM_EINVAL, "crm_add_active_box: active domains are not available in this build");
+    if (!finite_all(half, 3) || !finite_all(off, 3) || !std::isfinite(t_delay))
+        return t->fail(CRM_EINVAL, "crm_add_active_box: non-finite input");
+    if (!(half[0] > 0 && half[1] > 0 && half[2] > 0))
+        return t->fail(CRM_EINVAL, "crm_add_active_box: half extents must be > 0");
+    if ((int)t->box_body_h.size() >= kMaxBodies) return t->fail(CRM_EINVAL, "at most 16 active boxes");
+    t->box_body_h.push_back(body);
+    t->box_half_h.insert(t->box_half_h.end(), half, half + 3);
+    t->box_off_h.insert(t->box_off_h.end(), off, off + 3);
+    t->t_delay = t->box_body_h.size() == 1 ? t_delay : std::max(t->t_delay, t_delay);
+    return CRM_OK;
 }
 
 int crm_step(crm_terrain *t, double dt, int32_t n_steps)
@@ -608,6 +1032,7 @@ int crm_step(crm_terrain *t, double dt, int32_t n_steps)
     if (!(dt > 0) || !std::isfinite(dt) || n_steps < 0) return t->fail(CRM_EINVAL, "crm_step: dt > 0, n_steps >= 0");
     int rc = commit(t);
     if (rc) return rc;
+    if (t->active) return step_active(t, dt, n_steps);
     for (int s = 0; s < n_steps; ++s) one_step(t, dt);
     CRM_CUDA(t, cudaGetLastError());
     return CRM_OK;
@@ -636,18 +1061,21 @@ int crm_get_particles(crm_terrain *t, int64_t cap, double *xyz, float *vel, floa
         }
         return CRM_OK;
     }
-    double *dx = nullptr;
-    float *dv = nullptr, *ds = nullptr, *dr = nullptr;
     const size_t bytes = n * (3 * sizeof(double) + 10 * sizeof(float));
     void *buf = nullptr;
     CRM_CUDA(t, cudaMallocAsync(&buf, std::max<size_t>(bytes, 16), t->st));
-    dx = (double *)buf;
-    dv = (float *)(dx + 3 * n);
-    ds = dv + 3 * n;
-    dr = ds + 6 * n;
-    if (n > 0)
-        launch(t, K_EXPORT, [&] { launch_export(t->dp, t->A[t->cur], t->pid[t->cur], dx, dv, ds, dr,
-                                                t->st); });
+    double *dx = (double *)buf;
+    float *dv = (float *)(dx + 3 * n), *ds = dv + 3 * n, *dr = ds + 6 * n;
+    if (n > 0) {
+        if (t->active) {
+            scatter_back(t);
+            launch(t, K_EXPORT, [&] { launch_export_master(t->dp, t->Mst, t->mpid, (int)n, dx, dv,
+                                                           ds, dr, t->st); });
+        } else {
+            launch(t, K_EXPORT, [&] { launch_export(t->dp, t->A[t->cur], t->pid[t->cur], dx, dv, ds,
+                                                    dr, t->st); });
+        }
+    }
     int rc = download(t, xyz, dx, 3 * n);
     if (!rc) rc = download(t, vel, dv, 3 * n);
     if (!rc) rc = download(t, stress6, ds, 6 * n);
@@ -675,9 +1103,17 @@ int crm_get_body_wrench(crm_terrain *t, int32_t body, double force[3], double to
 int crm_get_counts(crm_terrain *t, int64_t *n_active, int64_t *n_extended, int64_t *n_bce)
 {
     if (!t) return CRM_EINVAL;
-    if (n_active) *n_active = t->nFtot;
-    if (n_extended) *n_extended = 0;
-    if (n_bce) *n_bce = t->nMtot;
+    int64_t a = t->nFtot, e = 0, b = t->nMtot;
+    if (t->committed && t->active) {
+        int rc = read_counts(t);
+        if (rc) return rc;
+        a = t->h_counts[C_NA];
+        e = t->h_counts[C_NE];
+        b = t->h_counts[C_NM];
+    }
+    if (n_active) *n_active = a;
+    if (n_extended) *n_extended = e;
+    if (n_bce) *n_bce = b;
     return CRM_OK;
 }
 
@@ -690,26 +1126,36 @@ int crm_eval_rates(crm_terrain *t, int64_t cap_sph, float *drho, float *dvel, fl
     int rc = commit(t);
     if (rc) return rc;
     rebuild(t);
+    if (t->active) {
+        rc = read_counts(t);
+        if (rc) return rc;
+        if (t->h_counts[C_WORDS] != 0) {
+            CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), t->st));
+            t->lists_valid = false;
+            return t->fail(CRM_ENOMEM, "crm_eval_rates: active set exceeds its capacity; step once first");
+        }
+    }
     const int c = t->cur;
     const DevParams &d = t->dp;
     const int64_t nF = t->nFtot, nM = t->nMtot;
-    // rates in slot order, then insertion-order outputs, in one device block
-    const size_t rate_bytes = nF * (sizeof(float) + 2 * sizeof(float4) + sizeof(float2));
+    const int64_t wF = d.capF;
+    const size_t rate_bytes = wF * (sizeof(float) + 2 * sizeof(float4) + sizeof(float2));
     const size_t out_bytes = (nF * 10 + nM * 12) * sizeof(float);
     void *buf = nullptr;
     CRM_CUDA(t, cudaMallocAsync(&buf, std::max<size_t>(rate_bytes + out_bytes + 64, 64), t->st));
     char *b = (char *)buf;
     RateOut r;
     r.du = (float4 *)b;
-    r.dsA = r.du + nF;
-    r.dsB = (float2 *)(r.dsA + nF);
-    r.drho = (float *)(r.dsB + nF);
-    float *o = r.drho + nF;
+    r.dsA = r.du + wF;
+    r.dsB = (float2 *)(r.dsA + wF);
+    r.drho = (float *)(r.dsB + wF);
+    float *o = r.drho + wF;
     float *odrho = o, *odu = o + nF, *ods = odu + 3 * nF, *omacc = ods + 6 * nF,
           *omvel = omacc + 3 * nM, *omsig = omvel + 3 * nM;
+    CRM_CUDA(t, cudaMemsetAsync(o, 0, out_bytes, t->st));
     bce(t, t->A[c], 0.0, 2);
     pair(t, kEval, t->A[c], t->A[c], 0.0f, r);
-    if (d.N > 0)
+    if (d.capN > 0)
         launch(t, K_EXPORT, [&] { launch_export_rates(d, t->pid[c], r, t->A[c], t->mforce,
                                                       (int)t->nFtot, odrho, odu, ods, omacc, omvel,
                                                       omsig, t->st); });
@@ -729,25 +1175,28 @@ int crm_get_neighbors(crm_terrain *t, int64_t cap, int64_t *offset, int32_t *lis
     if (!t) return CRM_EINVAL;
     if (!t->committed || !t->lists_valid) return t->fail(CRM_ESTATE, "crm_get_neighbors: no lists built yet");
     const DevParams &d = t->dp;
-    const int64_t N = d.N;
-    std::vector<uint32_t> nnb(N), pid(N), tab((size_t)d.maxnb * d.ell);
-    int rc = download(t, nnb.data(), t->nnb, N);
-    if (!rc) rc = download(t, pid.data(), t->pid[t->cur], N);
+    const int64_t W = d.capN, Ntot = t->nFtot + t->nMtot;
+    int hs[3] = {0, 0, 0};
+    std::vector<uint32_t> nnb(W), pid(W), tab((size_t)d.maxnb * d.ell);
+    int rc = download(t, hs, (const int *)t->counts, 3);
+    if (!rc) rc = download(t, nnb.data(), t->nnb, W);
+    if (!rc) rc = download(t, pid.data(), t->pid[t->cur], W);
     if (!rc) rc = download(t, tab.data(), t->nbr, tab.size());
     if (rc) return rc;
     rc = latched_error(t);
     if (rc) return rc;
-    std::vector<int64_t> cnt(N + 1, 0);
-    for (int64_t s = 0; s < N; ++s) cnt[pid[s] + 1] = nnb[s];
-    for (int64_t i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
-    if (nnz) *nnz = cnt[N];
-    if (offset) std::memcpy(offset, cnt.data(), (N + 1) * sizeof(int64_t));
+    const int64_t N = hs[2];
+    std::vector<int64_t> cnt(Ntot + 1, 0);
+    for (int64_t s = 0; s < N; ++s) cnt[(pid[s] & ~kExtendedBit) + 1] = nnb[s];
+    for (int64_t i = 0; i < Ntot; ++i) cnt[i + 1] += cnt[i];
+    if (nnz) *nnz = cnt[Ntot];
+    if (offset) std::memcpy(offset, cnt.data(), (Ntot + 1) * sizeof(int64_t));
     if (!list) return CRM_OK;
-    if (cap < cnt[N]) return t->fail(CRM_EINVAL, "crm_get_neighbors: list capacity too small");
+    if (cap < cnt[Ntot]) return t->fail(CRM_EINVAL, "crm_get_neighbors: list capacity too small");
     for (int64_t s = 0; s < N; ++s) {
-        const int64_t o = cnt[pid[s]];
+        const int64_t o = cnt[pid[s] & ~kExtendedBit];
         for (uint32_t k = 0; k < nnb[s]; ++k)
-            list[o + k] = (int32_t)pid[tab[(size_t)k * d.ell + s] & kIndexMask];
+            list[o + k] = (int32_t)(pid[tab[(size_t)k * d.ell + s] & kIndexMask] & ~kExtendedBit);
         std::sort(list + o, list + o + nnb[s]);
     }
     return CRM_OK;
@@ -790,11 +1239,14 @@ int crm_profile_read(crm_terrain *t, crm_profile *out)
     return CRM_OK;
 }
 
+// Checkpoint layout: 64-byte header (step, time, particle count, bodies,
+// active flag, drift), then the state arrays (the working set without active
+// boxes, the master store with them) and the bodies.
 int crm_state_bytes(crm_terrain *t, size_t *bytes)
 {
     if (!t || !bytes) return CRM_EINVAL;
-    const int64_t N = t->nFtot + t->nMtot;
-    *bytes = 64 + N * (3 * sizeof(float4) + sizeof(float2) + sizeof(uint32_t))
+    const int64_t n = t->box_body_h.empty() ? t->nFtot + t->nMtot : t->nFtot;
+    *bytes = 64 + n * (3 * sizeof(float4) + sizeof(float2) + sizeof(uint32_t))
              + t->hbodies.size() * sizeof(BodyDev);
     return CRM_OK;
 }
@@ -808,23 +1260,28 @@ int crm_save_state(crm_terrain *t, void *dev_buf, size_t cap, size_t *used)
     crm_state_bytes(t, &need);
     if (used) *used = need;
     if (cap < need) return t->fail(CRM_EINVAL, "crm_save_state: buffer too small");
-    const int64_t N = t->dp.N;
+    scatter_back(t);
+    const bool act = t->active;
+    const int64_t n = act ? t->nFtot : t->nFtot + t->nMtot;
     const int c = t->cur;
+    const StageArrays S = act ? t->Mst : t->A[c];
+    const uint32_t *P = act ? t->mpid : t->pid[c];
     char *b = (char *)dev_buf;
-    int64_t hdr[4] = {t->step_index, 0, N, (int64_t)t->hbodies.size()};
+    int64_t hdr[6] = {t->step_index, 0, n, (int64_t)t->hbodies.size(), act ? 1 : 0, 0};
     std::memcpy(&hdr[1], &t->time, sizeof(double));
-    CRM_CUDA(t, cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, t->st));
+    CRM_CUDA(t, cudaMemcpyAsync(b, hdr, 48, cudaMemcpyHostToDevice, t->st));
+    if (act) CRM_CUDA(t, cudaMemcpyAsync(b + 48, t->drift, sizeof(int), cudaMemcpyDeviceToDevice, t->st));
     size_t o = 64;
-    auto put = [&](const void *src, size_t n) {
-        cudaError_t e = cudaMemcpyAsync(b + o, src, n, cudaMemcpyDeviceToDevice, t->st);
-        o += n;
+    auto put = [&](const void *src, size_t nb) {
+        cudaError_t e = cudaMemcpyAsync(b + o, src, nb, cudaMemcpyDeviceToDevice, t->st);
+        o += nb;
         return e;
     };
-    CRM_CUDA(t, put(t->A[c].pos, N * sizeof(float4)));
-    CRM_CUDA(t, put(t->A[c].vel, N * sizeof(float4)));
-    CRM_CUDA(t, put(t->A[c].sA, N * sizeof(float4)));
-    CRM_CUDA(t, put(t->A[c].sB, N * sizeof(float2)));
-    CRM_CUDA(t, put(t->pid[c], N * sizeof(uint32_t)));
+    CRM_CUDA(t, put(S.pos, n * sizeof(float4)));
+    CRM_CUDA(t, put(S.vel, n * sizeof(float4)));
+    CRM_CUDA(t, put(S.sA, n * sizeof(float4)));
+    CRM_CUDA(t, put(S.sB, n * sizeof(float2)));
+    CRM_CUDA(t, put(P, n * sizeof(uint32_t)));
     if (!t->hbodies.empty()) CRM_CUDA(t, put(t->bodies, t->hbodies.size() * sizeof(BodyDev)));
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     return CRM_OK;
@@ -838,29 +1295,34 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used)
     size_t need = 0;
     crm_state_bytes(t, &need);
     if (used != need) return t->fail(CRM_EINVAL, "crm_load_state: size does not match this terrain");
-    int64_t hdr[4];
-    CRM_CUDA(t, cudaMemcpyAsync(hdr, dev_buf, sizeof(hdr), cudaMemcpyDeviceToHost, t->st));
+    int64_t hdr[6];
+    CRM_CUDA(t, cudaMemcpyAsync(hdr, dev_buf, 48, cudaMemcpyDeviceToHost, t->st));
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
-    if (hdr[2] != t->dp.N || hdr[3] != (int64_t)t->hbodies.size())
+    const bool act = t->active;
+    const int64_t n = act ? t->nFtot : t->nFtot + t->nMtot;
+    if (hdr[2] != n || hdr[3] != (int64_t)t->hbodies.size() || hdr[4] != (act ? 1 : 0))
         return t->fail(CRM_EINVAL, "crm_load_state: checkpoint of a different terrain");
-    const int64_t N = t->dp.N;
     const int c = t->cur;
+    const StageArrays S = act ? t->Mst : t->A[c];
+    uint32_t *P = act ? t->mpid : t->pid[c];
     const char *b = (const char *)dev_buf;
+    if (act) CRM_CUDA(t, cudaMemcpyAsync(t->drift, b + 48, sizeof(int), cudaMemcpyDeviceToDevice, t->st));
     size_t o = 64;
-    auto get = [&](void *dst, size_t n) {
-        cudaError_t e = cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToDevice, t->st);
-        o += n;
+    auto get = [&](void *dst, size_t nb) {
+        cudaError_t e = cudaMemcpyAsync(dst, b + o, nb, cudaMemcpyDeviceToDevice, t->st);
+        o += nb;
         return e;
     };
-    CRM_CUDA(t, get(t->A[c].pos, N * sizeof(float4)));
-    CRM_CUDA(t, get(t->A[c].vel, N * sizeof(float4)));
-    CRM_CUDA(t, get(t->A[c].sA, N * sizeof(float4)));
-    CRM_CUDA(t, get(t->A[c].sB, N * sizeof(float2)));
-    CRM_CUDA(t, get(t->pid[c], N * sizeof(uint32_t)));
+    CRM_CUDA(t, get(S.pos, n * sizeof(float4)));
+    CRM_CUDA(t, get(S.vel, n * sizeof(float4)));
+    CRM_CUDA(t, get(S.sA, n * sizeof(float4)));
+    CRM_CUDA(t, get(S.sB, n * sizeof(float2)));
+    CRM_CUDA(t, get(P, n * sizeof(uint32_t)));
     if (!t->hbodies.empty()) CRM_CUDA(t, get(t->bodies, t->hbodies.size() * sizeof(BodyDev)));
     t->step_index = hdr[0];
     std::memcpy(&t->time, &hdr[1], sizeof(double));
     t->lists_valid = false;
+    t->have_working = false;
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     return CRM_OK;
 }

@@ -146,10 +146,12 @@ namespace {
 // slot of element i in the cell-sorted order before the stable fix-up
 __global__ void k_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ rank,
                           const uint32_t *__restrict__ start, uint32_t *__restrict__ tmp,
-                          int64_t n)
+                          int64_t n, const int *__restrict__ n_dev,
+                          const int *__restrict__ abort_flag)
 {
+    if (abort_flag && *abort_flag) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= (n_dev ? (int64_t)__ldg(n_dev) : n)) return;
     tmp[start[keys[i]] + rank[i]] = (uint32_t)i;
 }
 
@@ -209,13 +211,16 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
                        uint32_t *__restrict__ rank, uint32_t *__restrict__ count,
                        int *__restrict__ err, int n_fluid_total)
 {
+    if (*p.abort) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.N) return;
+    const Sizes z = load_sizes(p);
+    if (i >= z.N) return;
+    const Window W = load_window(p);
     float4 ps = pos[i];
     int ix, iy, iz;
     uint32_t seg;
     bool bad = false;
-    if (i < p.nF) {
+    if (i < z.nF) {
         seg = 0;
         decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
         if (!(isfinite(ps.x) && isfinite(ps.y) && isfinite(ps.z))) {
@@ -233,7 +238,7 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
         }
     } else {
         seg = 1;
-        const int mi = (int)pid[i] - n_fluid_total;
+        const int mi = (int)(pid[i] & ~kExtendedBit) - n_fluid_total;
         double x[3];
         float u[3], a[3], arm[3];
         marker_state(bodies, mbody[mi], mloc + 3 * (int64_t)mi, 0.0, x, u, a, arm);
@@ -247,16 +252,16 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
         ps.y = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
         ps.z = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
     }
-    int lx = ix - p.wx0, ly = iy - p.wy0, lz = iz - p.wz0;
-    if (lx < 0 || ly < 0 || lz < 0 || lx >= p.WX || ly >= p.WY || lz >= p.WZ) {
+    int lx = ix - W.x0, ly = iy - W.y0, lz = iz - W.z0;
+    if (lx < 0 || ly < 0 || lz < 0 || lx >= W.X || ly >= W.Y || lz >= W.Z) {
         bad = true;
-        lx = min(max(lx, 0), p.WX - 1);
-        ly = min(max(ly, 0), p.WY - 1);
-        lz = min(max(lz, 0), p.WZ - 1);
-        ix = lx + p.wx0; iy = ly + p.wy0; iz = lz + p.wz0;
+        lx = min(max(lx, 0), W.X - 1);
+        ly = min(max(ly, 0), W.Y - 1);
+        lz = min(max(lz, 0), W.Z - 1);
+        ix = lx + W.x0; iy = ly + W.y0; iz = lz + W.z0;
     }
     if (bad) atomicOr(err, ERR_ESCAPED);
-    const uint32_t key = seg * p.M + ((uint32_t)lz * (uint32_t)p.WY + (uint32_t)ly) * (uint32_t)p.WX
+    const uint32_t key = seg * p.M + ((uint32_t)lz * (uint32_t)W.Y + (uint32_t)ly) * (uint32_t)W.X
                          + (uint32_t)lx;
     keys[i] = key;
     rank[i] = atomicAdd(&count[key], 1u);
@@ -264,16 +269,38 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
     pos[i] = ps;
 }
 
+// Final slot of the element k_scatter put at slot s, for the terrain: inside a
+// cell the particles are ordered by their x offset (ties by input index), so
+// the cells of an x-row are sorted by x and the neighbour search can stop a
+// scan once the x-gap alone exceeds the cut-off.
+__device__ __forceinline__ uint32_t xsorted_slot(const uint32_t *__restrict__ keys,
+                                                 const uint32_t *__restrict__ start,
+                                                 const uint32_t *__restrict__ tmp,
+                                                 const float4 *__restrict__ pos, uint32_t i)
+{
+    const uint32_t key = keys[i];
+    const uint32_t b = start[key], e = start[key + 1];
+    const float xi = pos[i].x;
+    uint32_t r = 0;
+    for (uint32_t u = b; u < e; ++u) {
+        const uint32_t k = tmp[u];
+        const float xk = pos[k].x;
+        r += (xk < xi || (xk == xi && k < i)) ? 1u : 0u;
+    }
+    return b + r;
+}
+
 // Stable fix-up + gather of every particle array into sorted order (H4).
-__global__ void k_reorder(int n, const uint32_t *__restrict__ keys,
+__global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restrict__ keys,
                           const uint32_t *__restrict__ start, const uint32_t *__restrict__ tmp,
                           StageArrays src, const uint32_t *__restrict__ pid_src, StageArrays dst,
-                          uint32_t *__restrict__ pid_dst)
+                          uint32_t *__restrict__ pid_dst, const int *__restrict__ abort_flag)
 {
+    if (*abort_flag) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    if (s >= __ldg(n_dev)) return;
     const uint32_t i = tmp[s];
-    const uint32_t d = stable_slot(keys, start, tmp, i);
+    const uint32_t d = xsorted_slot(keys, start, tmp, src.pos, i);
     dst.pos[d] = src.pos[i];
     dst.vel[d] = src.vel[i];
     dst.sA[d] = src.sA[i];
@@ -282,50 +309,72 @@ __global__ void k_reorder(int n, const uint32_t *__restrict__ keys,
 }
 
 // Neighbour lists (Alg. 1): for particle s scan the 27 cells around its home
-// cell -- 9 runs of 3 consecutive cells in x, which are contiguous in the
-// sorted order -- and keep j when |x_s - x_j| < 2h (strict).  Fluid particles
-// take fluid and marker neighbours, markers take fluid neighbours only.  The
-// list is an ELL table nbr[k * ell + s] (coalesced across a warp); each entry
-// is j | code << 26 with code = (dx+1) | (dy+1) << 2 | (dz+1) << 4, the cell
-// offset of j relative to s, so the pair kernels rebuild x_s - x_j from the
-// cell-relative offsets without decoding cell ids.
+// cell and keep j when |x_s - x_j| < 2h (strict).  Fluid particles take fluid
+// and marker neighbours, markers take fluid neighbours only.  The scan is cell
+// by cell, so the cell offset (dx, dy, dz) of j is a loop constant; a row
+// (dy, dz) whose nearest face is already 2h away is skipped, and because every
+// cell is sorted by x the left cell is read from its right end and the right
+// cell from its left end, each stopping once the x-gap alone reaches the
+// remaining radius.  (Both cut-offs carry a 1e-5 relative margin, so they
+// never drop a pair the full test would keep.)  The list is an ELL table
+// nbr[k * ell + s] (coalesced across a warp); each entry is j | code << 26 with
+// code = (dx+1) | (dy+1) << 2 | (dz+1) << 4, which the pair kernels use to
+// rebuild x_s - x_j from the cell-relative offsets.
 __global__ void __launch_bounds__(kBlock)
 k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restrict__ start,
             uint32_t *__restrict__ nbr, uint32_t *__restrict__ nnb, int *__restrict__ err)
 {
+    if (*p.abort) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= p.N) return;
+    const Sizes z = load_sizes(p);
+    if (s >= z.N) return;
+    const Window W = load_window(p);
     const float4 ps = pos[s];
     int ix, iy, iz;
     decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
-    const int lx = ix - p.wx0, ly = iy - p.wy0, lz = iz - p.wz0;
-    const int nseg = s < p.nF ? 2 : 1;
-    const int xa = max(lx - 1, 0), xb = min(lx + 1, p.WX - 1);
+    const int lx = ix - W.x0, ly = iy - W.y0, lz = iz - W.z0;
+    const int nseg = s < z.nF ? 2 : 1;
+    const float cell = p.cell;
+    const float lim2 = p.four_h2 * (1.0f + 1e-5f);
     int cnt = 0;
     for (int dz = -1; dz <= 1; ++dz) {
         const int lz2 = lz + dz;
-        if (lz2 < 0 || lz2 >= p.WZ) continue;
+        if (lz2 < 0 || lz2 >= W.Z) continue;
+        const float gz = dz < 0 ? fmaxf(ps.z, 0.f) : (dz > 0 ? fmaxf(cell - ps.z, 0.f) : 0.f);
+        const float sz = ps.z - (float)dz * cell;
         for (int dy = -1; dy <= 1; ++dy) {
             const int ly2 = ly + dy;
-            if (ly2 < 0 || ly2 >= p.WY) continue;
-            const uint32_t rowkey = ((uint32_t)lz2 * (uint32_t)p.WY + (uint32_t)ly2) * (uint32_t)p.WX;
-            const uint32_t rowg = ((uint32_t)(iz + dz) * (uint32_t)p.GY + (uint32_t)(iy + dy))
-                                  * (uint32_t)p.GX;
-            const float sy = ps.y - (float)dy * p.cell, sz = ps.z - (float)dz * p.cell;
+            if (ly2 < 0 || ly2 >= W.Y) continue;
+            const float gy = dy < 0 ? fmaxf(ps.y, 0.f) : (dy > 0 ? fmaxf(cell - ps.y, 0.f) : 0.f);
+            const float d2 = gy * gy + gz * gz;
+            if (d2 >= lim2) continue;
+            const float R = sqrtf(lim2 - d2);
+            const float sy = ps.y - (float)dy * cell;
+            const uint32_t rowkey = ((uint32_t)lz2 * (uint32_t)W.Y + (uint32_t)ly2) * (uint32_t)W.X;
             const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
             for (int seg = 0; seg < nseg; ++seg) {
                 const uint32_t kb = seg * p.M + rowkey;
-                const uint32_t jb = start[kb + xa], je = start[kb + xb + 1];
-                for (uint32_t j = jb; j < je; ++j) {
-                    const float4 pj = pos[j];
-                    const int dxc = (int)(__float_as_uint(pj.w) - rowg) - ix;
-                    const float rx = ps.x - pj.x - (float)dxc * p.cell;
-                    const float ry = sy - pj.y, rz = sz - pj.z;
-                    const float r2 = rx * rx + ry * ry + rz * rz;
-                    if (r2 < p.four_h2 && j != (uint32_t)s) {
-                        if (cnt < p.maxnb)
-                            nbr[(size_t)cnt * p.ell + s] = j | (((uint32_t)(dxc + 1) | codeyz) << kIndexBits);
-                        ++cnt;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int lx2 = lx + dx;
+                    if (lx2 < 0 || lx2 >= W.X) continue;
+                    const uint32_t jb = start[kb + lx2], je = start[kb + lx2 + 1];
+                    const float sx = ps.x - (float)dx * cell;
+                    const uint32_t tag = ((uint32_t)(dx + 1) | codeyz) << kIndexBits;
+                    // left cell: scan down from the largest x; right cell: up from the smallest
+                    const int step = dx < 0 ? -1 : 1;
+                    const int first = dx < 0 ? (int)je - 1 : (int)jb;
+                    const int count = (int)(je - jb);
+                    for (int q = 0, j = first; q < count; ++q, j += step) {
+                        const float4 pj = pos[j];
+                        const float rx = sx - pj.x;
+                        if (dx != 0 && fabsf(rx) >= R) break;
+                        const float ry = sy - pj.y, rz = sz - pj.z;
+                        const float r2 = rx * rx + ry * ry + rz * rz;
+                        if (r2 < p.four_h2 && j != s) {
+                            if (cnt < p.maxnb) nbr[(size_t)cnt * p.ell + s] = (uint32_t)j | tag;
+                            ++cnt;
+                        }
                     }
                 }
             }
@@ -340,28 +389,29 @@ void launch_keys(const DevParams &p, StageArrays cur, const uint32_t *pid_cur, c
                  const int *mbody, const BodyDev *bodies, const SortScratch &s, int *err,
                  int n_fluid_total, cudaStream_t st)
 {
-    k_keys<<<grid_for(p.N), kBlock, 0, st>>>(p, cur.pos, pid_cur, mloc, mbody, bodies, s.keys,
+    k_keys<<<grid_for(p.capN), kBlock, 0, st>>>(p, cur.pos, pid_cur, mloc, mbody, bodies, s.keys,
                                              s.rank, s.count, err, n_fluid_total);
 }
 
 void launch_scatter(const DevParams &p, const SortScratch &s, const uint32_t *start,
                     cudaStream_t st)
 {
-    k_scatter<<<grid_for(p.N), kBlock, 0, st>>>(s.keys, s.rank, start, s.tmp, p.N);
+    k_scatter<<<grid_for(p.capN), kBlock, 0, st>>>(s.keys, s.rank, start, s.tmp, p.capN,
+                                                   p.sizes + 2, p.abort);
 }
 
 void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *start,
                     StageArrays cur, const uint32_t *pid_cur, StageArrays nxt, uint32_t *pid_nxt,
                     cudaStream_t st)
 {
-    k_reorder<<<grid_for(p.N), kBlock, 0, st>>>(p.N, s.keys, start, s.tmp, cur, pid_cur, nxt,
-                                                pid_nxt);
+    k_reorder<<<grid_for(p.capN), kBlock, 0, st>>>(p.sizes + 2, s.keys, start, s.tmp, cur, pid_cur,
+                                                   nxt, pid_nxt, p.abort);
 }
 
 void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
                       uint32_t *nnb, int *err, cudaStream_t st)
 {
-    k_neighbors<<<grid_for(p.N), kBlock, 0, st>>>(p, pos, start, nbr, nnb, err);
+    k_neighbors<<<grid_for(p.capN), kBlock, 0, st>>>(p, pos, start, nbr, nnb, err);
 }
 
 }  // namespace crm
@@ -429,7 +479,7 @@ extern "C" int crm_bin_points(const float *xyz, int64_t n, float cell_size, cons
     crm::launch_scan_reset(s.count, cell_start_out, ncell + 1, s, err, st);
     if (n > 0) {
         crm::k_scatter<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, s.rank, cell_start_out,
-                                                                 s.tmp, n);
+                                                                 s.tmp, n, nullptr, nullptr);
         crm::k_perm<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, cell_start_out, s.tmp,
                                                               perm_out, n);
     }
@@ -531,7 +581,7 @@ extern "C" int crm_bin_points_noalloc(const float *xyz, int64_t n, float cell_si
     crm::launch_scan_reset(s.count, cell_start_out, ncell + 1, s, err, st);
     if (n > 0) {
         crm::k_scatter<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, s.rank, cell_start_out,
-                                                                 s.tmp, n);
+                                                                 s.tmp, n, nullptr, nullptr);
         crm::k_perm<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, cell_start_out, s.tmp,
                                                               perm_out, n);
     }

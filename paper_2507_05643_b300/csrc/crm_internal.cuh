@@ -19,6 +19,7 @@ enum : int {
 };
 
 constexpr int kMaxBodies = 16;
+constexpr uint32_t kExtendedBit = 0x80000000u;   // pid flag: Extended-Active (read-only)
 constexpr uint32_t kIndexBits = 26;                 // neighbour entry: j | code << 26
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int kBlock = 256;
@@ -37,16 +38,37 @@ struct DevParams {
     float mu_s, mu_2, I0, grain_d, cohesion;
     // global grid: cell coordinates (ix, iy, iz), c = (iz GY + iy) GX + ix
     int GX, GY, GZ;
-    // working window of the sort, in global cell coordinates
-    int wx0, wy0, wz0, WX, WY, WZ;
-    uint32_t M;                           // WX * WY * WZ
+    uint32_t M;                           // cells reserved for the working window
     double dmin_x, dmin_y, dmin_z, cell_d;
-    // particle set (sorted order: fluid slots [0, nF), markers [nF, N))
-    int nF, nM, N;
+    // capacities of the working set (grid sizes; the sorted working arrays
+    // hold fluid slots [0, nF) then markers [nF, N), nF <= capF, N <= capN)
+    int capF, capM, capN;
     int maxnb;
-    uint32_t ell;                         // stride of the neighbour table (>= N)
+    uint32_t ell;                         // stride of the neighbour table (>= capN)
     int n_bodies;
+    // device-resident sizes of the current working set: nF, nM, N, and the
+    // window of the cell sort: x0, y0, z0 (global cells) and X, Y, Z
+    // (X Y Z <= M).  Kept on the device so that a step needs no host sync.
+    const int *sizes;
+    const int *win;
+    // nonzero once a step of an active-domain run has overflowed a capacity:
+    // every later kernel of the enqueued steps returns at once
+    const int *abort;
 };
+
+struct Sizes { int nF, nM, N; };
+struct Window { int x0, y0, z0, X, Y, Z; };
+
+__device__ __forceinline__ Sizes load_sizes(const DevParams &p)
+{
+    return Sizes{__ldg(p.sizes), __ldg(p.sizes + 1), __ldg(p.sizes + 2)};
+}
+
+__device__ __forceinline__ Window load_window(const DevParams &p)
+{
+    return Window{__ldg(p.win), __ldg(p.win + 1), __ldg(p.win + 2),
+                  __ldg(p.win + 3), __ldg(p.win + 4), __ldg(p.win + 5)};
+}
 
 // Rigid body state on the device (FP64, Sec. 2.4 FSI exchange).
 struct BodyDev {
@@ -225,7 +247,7 @@ struct RateOut {
 enum { kStage1 = 0, kStage2 = 1, kEval = 2 };
 
 void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, StageArrays MID,
-                 const uint32_t *nbr, const uint32_t *nnb, const uint8_t *integrate, float dt,
+                 const uint32_t *nbr, const uint32_t *nnb, const uint32_t *pid, float dt,
                  RateOut out, int *err, cudaStream_t st);
 void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
                 const double *mloc, const int *mbody, const BodyDev *bodies, const uint32_t *nbr,
@@ -240,5 +262,31 @@ void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, doubl
 void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, StageArrays S,
                          const float4 *mforce, int n_fluid_total, float *drho, float *du,
                          float *ds, float *macc, float *mvel, float *msig, cudaStream_t st);
+
+// Active domains (Sec. 3.2, Alg. 3), crm_active.cu.
+size_t box_frame_bytes();
+void launch_box_prep(const DevParams &p, int nbox, const int *box_body, const double *box_half,
+                     const double *box_off, const BodyDev *bodies, const int *colF,
+                     const int *colM, const int *drift, int all_active, int n_fluid_master,
+                     int n_fixed_master, int64_t cand_cap, void *frames, int *win, int *ranges,
+                     int *rinfo, int *counts, int *abort_flag, int64_t step_tag, cudaStream_t st);
+void launch_activity(const DevParams &p, int nbox, const void *frames, const int *ranges,
+                     const int *rinfo, const float4 *mpos, const double *mloc,
+                     const int *fixed_order, int all_active, int64_t cand_cap, uint32_t *include,
+                     uint8_t *kind, int *counts, const int *abort_flag, cudaStream_t st);
+void launch_active_sizes(const DevParams &p, const int *rinfo, const uint32_t *slot,
+                         int n_body_markers, int *counts, int *abort_flag, int64_t step_tag,
+                         cudaStream_t st);
+void launch_gather(const DevParams &p, const int *ranges, const int *rinfo,
+                   const uint8_t *kind, const uint32_t *slot,
+                   StageArrays M, const uint32_t *mpid, const int *fixed_order,
+                   const int *body_markers, int n_body_markers, int n_fluid_total,
+                   int64_t cand_cap, StageArrays W, uint32_t *wpid, const int *counts,
+                   const int *abort_flag, cudaStream_t st);
+void launch_scatter_back(const DevParams &p, StageArrays W, const uint32_t *wpid,
+                         const uint32_t *mslot_of_pid, const int *mcol, StageArrays M, int *drift,
+                         cudaStream_t st);
+void launch_export_master(const DevParams &p, StageArrays M, const uint32_t *mpid, int n,
+                          double *xyz, float *vel, float *sig, float *rho, cudaStream_t st);
 
 }  // namespace crm

@@ -99,14 +99,16 @@ template <int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
        const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ nnb,
-       const uint8_t *__restrict__ integrate, float dt, RateOut out, int *__restrict__ err)
+       const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err)
 {
+    if (*p.abort) return;
     __shared__ float4 lut[64];
     fill_shift_table(lut, p.cell);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.nF) return;
-    const bool adv = integrate == nullptr || integrate[i] != 0;
+    if (i >= __ldg(p.sizes)) return;
+    // Extended-Active particles (active domains) are read-only neighbours
+    const bool adv = pid == nullptr || !(pid[i] & kExtendedBit);
     if (!adv) {
         if (MODE == kStage1) {
             MID.pos[i] = S.pos[i];
@@ -236,12 +238,14 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
       const uint32_t *__restrict__ nnb, double tau, int accel, int n_fluid_total,
       float4 *__restrict__ mforce, float4 *__restrict__ mtorque)
 {
+    if (*p.abort) return;
     __shared__ float4 lut[64];
     fill_shift_table(lut, p.cell);
     __syncthreads();
-    const int s = p.nF + blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= p.N) return;
-    const int mi = (int)pid[s] - n_fluid_total;
+    const Sizes z = load_sizes(p);
+    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= z.N) return;
+    const int mi = (int)(pid[s] & ~kExtendedBit) - n_fluid_total;
     const int body = mbody[mi];
     double x[3];
     float ub[3], ab[3], arm[3];
@@ -331,17 +335,20 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
         fy = p.m * (my * ir + avy);
         fz = p.m * (mz * ir + avz);
     }
-    mforce[s - p.nF] = make_float4(fx, fy, fz, __int_as_float(body));
-    mtorque[s - p.nF] = make_float4(arm[1] * fz - arm[2] * fy, arm[2] * fx - arm[0] * fz,
+    mforce[s - z.nF] = make_float4(fx, fy, fz, __int_as_float(body));
+    mtorque[s - z.nF] = make_float4(arm[1] * fz - arm[2] * fy, arm[2] * fx - arm[0] * fz,
                                     arm[0] * fy - arm[1] * fx, 0.f);
 }
 
 // FP64 per-block partial wrench of every body (deterministic: fixed block
 // partition, fixed reduction tree).
 __global__ void __launch_bounds__(kBlock)
-k_wrench_partial(int nM, int n_bodies, const float4 *__restrict__ mforce,
-                 const float4 *__restrict__ mtorque, double *__restrict__ partial)
+k_wrench_partial(const int *__restrict__ nM_dev, int n_bodies, const float4 *__restrict__ mforce,
+                 const float4 *__restrict__ mtorque, double *__restrict__ partial,
+                 const int *__restrict__ abort_flag)
 {
+    if (*abort_flag) return;
+    const int nM = __ldg(nM_dev);
     __shared__ double red[kBlock / 32][6];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -378,8 +385,9 @@ k_wrench_partial(int nM, int n_bodies, const float4 *__restrict__ mforce,
 // velocity; the orientation turns by dt w).
 __global__ void k_body_update(int n_bodies, int n_partials, const double *__restrict__ partial,
                               BodyDev *__restrict__ bodies, double gx, double gy, double gz,
-                              double dt, int integrate)
+                              double dt, int integrate, const int *__restrict__ abort_flag)
 {
+    if (*abort_flag) return;
     const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (b >= n_bodies) return;
     double v[6] = {0, 0, 0, 0, 0, 0};
@@ -415,7 +423,7 @@ __global__ void k_export(DevParams p, StageArrays S, const uint32_t *__restrict_
                          float *__restrict__ sig, float *__restrict__ rho)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= p.nF) return;
+    if (s >= __ldg(p.sizes)) return;
     const uint32_t id = pid[s];
     const float4 ps = S.pos[s];
     int ix, iy, iz;
@@ -441,9 +449,10 @@ __global__ void k_export_rates(DevParams p, const uint32_t *__restrict__ pid, Ra
                                float *__restrict__ msig)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= p.N) return;
-    const uint32_t id = pid[s];
-    if (s < p.nF) {
+    const Sizes z = load_sizes(p);
+    if (s >= z.N) return;
+    const uint32_t id = pid[s] & ~kExtendedBit;
+    if (s < z.nF) {
         drho[id] = r.drho[s];
         const float4 a = r.du[s];
         du[3 * (size_t)id] = a.x; du[3 * (size_t)id + 1] = a.y; du[3 * (size_t)id + 2] = a.z;
@@ -453,7 +462,7 @@ __global__ void k_export_rates(DevParams p, const uint32_t *__restrict__ pid, Ra
         o[0] = b.x; o[1] = b.y; o[2] = b.z; o[3] = b.w; o[4] = c.x; o[5] = c.y;
     } else {
         const size_t m = (size_t)id - (size_t)n_fluid_total;
-        const float4 f = mforce[s - p.nF];
+        const float4 f = mforce[s - z.nF];
         const float im = 1.0f / p.m;
         macc[3 * m] = f.x * im; macc[3 * m + 1] = f.y * im; macc[3 * m + 2] = f.z * im;
         const float4 v = S.vel[s];
@@ -468,10 +477,10 @@ __global__ void k_export_rates(DevParams p, const uint32_t *__restrict__ pid, Ra
 // ---------------------------------------------------------------------------
 // Host-side launchers used by the API translation unit.
 void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, StageArrays MID,
-                 const uint32_t *nbr, const uint32_t *nnb, const uint8_t *integrate, float dt,
+                 const uint32_t *nbr, const uint32_t *nnb, const uint32_t *integrate, float dt,
                  RateOut out, int *err, cudaStream_t st)
 {
-    const unsigned g = grid_for(p.nF);
+    const unsigned g = grid_for(p.capF);
     if (mode == kStage1)
         k_pair<kStage1><<<g, kBlock, 0, st>>>(p, S, Y, MID, nbr, nnb, integrate, dt, out, err);
     else if (mode == kStage2)
@@ -485,34 +494,36 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
                 const uint32_t *nnb, double tau, int accel, int n_fluid_total, float4 *mforce,
                 float4 *mtorque, cudaStream_t st)
 {
-    k_bce<<<grid_for(p.nM), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, mbody, bodies, nbr, nnb,
+    k_bce<<<grid_for(p.capM), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, mbody, bodies, nbr, nnb,
                                              tau, accel, n_fluid_total, mforce, mtorque);
 }
 
 void launch_wrench_partial(const DevParams &p, const float4 *mforce, const float4 *mtorque,
                            double *partial, cudaStream_t st)
 {
-    k_wrench_partial<<<grid_for(p.nM), kBlock, 0, st>>>(p.nM, p.n_bodies, mforce, mtorque, partial);
+    k_wrench_partial<<<grid_for(p.capM), kBlock, 0, st>>>(p.sizes + 1, p.n_bodies, mforce, mtorque,
+                                                          partial, p.abort);
 }
 
 void launch_body_update(const DevParams &p, const double *partial, BodyDev *bodies, double dt,
                         int integrate, cudaStream_t st)
 {
-    k_body_update<<<1, 32 * p.n_bodies, 0, st>>>(p.n_bodies, p.nM > 0 ? (int)grid_for(p.nM) : 0,
-                                                 partial, bodies, p.gx, p.gy, p.gz, dt, integrate);
+    k_body_update<<<1, 32 * p.n_bodies, 0, st>>>(p.n_bodies, p.capM > 0 ? (int)grid_for(p.capM) : 0,
+                                                 partial, bodies, p.gx, p.gy, p.gz, dt, integrate,
+                                                 p.abort);
 }
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
                    float *sig, float *rho, cudaStream_t st)
 {
-    k_export<<<grid_for(p.nF), kBlock, 0, st>>>(p, S, pid, xyz, vel, sig, rho);
+    k_export<<<grid_for(p.capF), kBlock, 0, st>>>(p, S, pid, xyz, vel, sig, rho);
 }
 
 void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, StageArrays S,
                          const float4 *mforce, int n_fluid_total, float *drho, float *du,
                          float *ds, float *macc, float *mvel, float *msig, cudaStream_t st)
 {
-    k_export_rates<<<grid_for(p.N), kBlock, 0, st>>>(p, pid, r, S, mforce, n_fluid_total, drho, du,
+    k_export_rates<<<grid_for(p.capN), kBlock, 0, st>>>(p, pid, r, S, mforce, n_fluid_total, drho, du,
                                                      ds, macc, mvel, msig);
 }
 

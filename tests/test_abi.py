@@ -74,3 +74,20 @@ def test_bin_points_rejects_bad_arguments():
     with pytest.raises(crm.CrmError):
         crm.bin_points(256, 10, -0.1, (4, 4, 4), 256, 256, 256, 256, 1 << 20)
     assert crm.bin_scratch_bytes(1000, 64) >= 2 * 4 * 1000 + 4 * 65
+
+
+def test_capacity_policy_matches_oracle():
+    """ManageArrayMemory (Sec. 3.2): the library's capacity rule equals the oracle's
+    on random need sequences, for the paper's G = 1.2, S = 0.75, S_I = 50 and others."""
+    import numpy as np
+    import oracle
+    import paper_2507_05643_b300 as crm
+    rng = np.random.default_rng(5)
+    for G, S, SI in ((1.2, 0.75, 50), (1.5, 0.5, 7), (1.0, 1.0, 1)):
+        cap_a = cap_b = 0
+        for step in range(1, 400):
+            need = int(rng.integers(0, 5000))
+            cap_a = crm.capacity_policy(need, cap_a, step, G, S, SI)
+            cap_b = oracle.capacity_policy(need, cap_b, step, G, S, SI)
+            assert cap_a == cap_b
+            assert cap_a >= need or step % SI == 0
