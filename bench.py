@@ -216,7 +216,7 @@ def run_crm(args):
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        t.profile_reset(timing=True)
+        t.profile_reset(timing=False)
         sampler = ClockSampler(local)
         if world > 1:
             dist.barrier()
@@ -231,12 +231,22 @@ def run_crm(args):
             dist.barrier()
         clocks = sampler.stop()
         t.sync()
-        prof = t.profile()
+        launches = t.profile()
         ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        # kernel-level breakdown: the same steps with every launch bracketed by
+        # CUDA events on the library's stream (direct launches, not the graph)
+        prof_steps = min(args.steps, 50)
+        t.profile_reset(timing=True)
+        for k in range(prof_steps):
+            flush.fill_(k & 0xFF)
+            t.step(dt, 1)
+        prof = t.profile()
+        t.profile_reset(timing=False)
     n_active, _, n_bce = t.counts()
-    # the neighbour pairs of the fluid rows at the end of the timed region
+    # neighbour pairs of the current exact lists (fluid rows, then all rows)
     off, _ = t.neighbors()
     fluid_pairs = int(off[sc.n_fluid] - off[0])
+    all_pairs = int(off[-1])
 
     # end to end through the public API: per step the co-simulation exchange of
     # Sec. 2.4 -- body pose/twist host->device, step, wrench + body state
@@ -269,24 +279,39 @@ def run_crm(args):
     if rank == 0:
         peaks, kind = _peaks()
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        launches = sum(prof["launches"].values())
+        n_all = sc.n_fluid + sc.n_markers
+        per = {k: prof["ms"][k] / max(prof["launches"][k], 1) for k in prof["ms"]
+               if prof["launches"][k]}
         # dominant kernel = largest share of the event-timed step
         kern = max(prof["ms"], key=lambda k: prof["ms"][k])
-        avg_ms = prof["ms"][kern] / max(prof["launches"][kern], 1)
+        avg_ms = per[kern]
+        fp32_peak = nsm * SM_FP32_LANES * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        alg_bytes = {   # algorithmic DRAM bytes per launch (state read / written once)
+            "keys": 40 * n_all, "scan": 8 * (2 * 60000 + 1), "scatter": 12 * n_all,
+            "reorder": 2 * 60 * n_all, "neighbors": 20 * n_all + 4 * all_pairs * 1.33,
+            "skin": 60 * n_all,
+            "bce": 56 * 2 * sc.n_markers + 4 * (all_pairs - fluid_pairs),
+            "pair_stage1": 56 * 2 * sc.n_fluid + 56 * sc.n_markers + 4 * fluid_pairs,
+            "pair_stage2": 56 * 3 * sc.n_fluid + 56 * sc.n_markers + 4 * fluid_pairs,
+            "export": 88 * sc.n_fluid}
         if kern.startswith("pair"):
             flop = fluid_pairs * FLOP_PER_PAIR + sc.n_fluid * FLOP_PER_PARTICLE
             achieved = flop / (avg_ms * 1e-3) / 1e12
-            peak = nsm * SM_FP32_LANES * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-            roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak,
+            roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                     "peak_source": f"{nsm} SMs x {SM_FP32_LANES} FP32 lanes x 2 x "
                                    f"{peaks['sm_max_mhz']:.0f} MHz ({kind} max clock)",
-                    "traffic": _traffic(kern),
-                    "flop_per_launch": flop, "ms_per_launch": avg_ms,
-                    "hbm_frac_of_measured": None}
+                    "traffic": _traffic(kern), "flop_per_launch": flop, "ms_per_launch": avg_ms}
         else:
-            roof = {"bound": "hbm", "kernel": kern, "achieved": None, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": None, "traffic": _traffic(kern)}
+            b = alg_bytes.get(kern, 0.0)
+            achieved = b / (avg_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": kern, "achieved": achieved,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "peak_source": f"hbm_gbs ({kind})",
+                    "traffic": _traffic(kern), "bytes_per_launch": b, "ms_per_launch": avg_ms}
+        pair_ms = per.get("pair_stage2", 0.0)
+        pair_fp32 = ((fluid_pairs * FLOP_PER_PAIR + sc.n_fluid * FLOP_PER_PARTICLE)
+                     / (pair_ms * 1e-3) / 1e12 / fp32_peak) if pair_ms else None
         line = {
             "metric": METRIC,
             "value": world * sc.n_fluid * args.steps / (ms_max * 1e-3),
@@ -299,8 +324,13 @@ def run_crm(args):
             "e2e": {"value": world * sc.n_fluid * e2e_steps / e2e_max, "unit": UNIT,
                     "h2d_bytes_per_step": 13 * 8, "d2h_bytes_per_step": 6 * 8 + 13 * 8 + 4,
                     "loop": "set_body_motion -> step -> body_wrench + body_state (sync)"},
-            "gpu_launches": launches,
-            "kernel_ms": {k: v for k, v in prof["ms"].items() if prof["launches"][k]},
+            "gpu_launches": sum(launches["launches"].values()),
+            "kernels_us_per_step": {k: 1e3 * prof["ms"][k] / max(prof["steps"], 1)
+                                    for k in per},
+            "kernel_launches_per_step": {k: prof["launches"][k] / max(prof["steps"], 1)
+                                         for k in per},
+            "cell_searches": launches["launches"]["neighbors"],
+            "pair_stage2_fp32_frac": pair_fp32,
             "roofline": roof,
             "clocks": clocks,
         }

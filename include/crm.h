@@ -87,6 +87,14 @@ typedef struct crm_params {
     double shrink_ratio;   /* shrink threshold S (Sec. 3.2), in (0, 1] */
     int32_t shrink_interval; /* shrink check interval S_I in steps (Sec. 3.2), >= 1 */
     int32_t reserved;
+    double skin;           /* Verlet skin as a fraction of 2h, in [0, 1): with skin > 0
+                              the cell sort and the 27-cell search run with radius
+                              2h (1 + skin) only when some particle has moved skin * h
+                              since the last search, and at every Alg. 2 rebuild the
+                              first-stage kernels filter those lists down to the exact
+                              2h sets (the same sets a fresh search gives) while they
+                              compute the stage.  0 = a fresh 2h search every rebuild.
+                              Ignored with active boxes. */
 } crm_params;
 
 typedef struct crm_terrain crm_terrain;
@@ -100,7 +108,7 @@ const char *crm_status_string(int status);
 /* Defaults: rho0 1700, E 1e6, nu 0.3, mu_s = mu_2 = tan 30 deg, I0 0.08,
  * grain_d 0.002, c 0, d0 0.01, h 0.012, cubic kernel, unilateral AV 0.02,
  * xi^2 = 0.01 h^2, g = (0, 0, -9.81), ps_freq 1, max_neighbors 96, domain
- * [0,1]^3, G 1.2, S 0.75, S_I 50 (Sec. 3.2). */
+ * [0,1]^3, G 1.2, S 0.75, S_I 50 (Sec. 3.2), skin 0.1. */
 void crm_default_params(crm_params *p);
 
 /* Create a terrain.  `cuda_stream` is a cudaStream_t (NULL for the default
@@ -209,9 +217,11 @@ int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
 
 /* Per-kernel launch counts and CUDA-event timings of one handle (for
  * measurement).  Kernel ids 0..CRM_NUM_KERNELS-1, names from crm_kernel_name:
- * keys, scan, scatter, reorder, neighbors, bce, pair_stage1, pair_stage2,
- * wrench_partial, body_update, export. */
-#define CRM_NUM_KERNELS 11
+ * keys, scan, scatter, reorder, neighbors (cell search), bce (with the body
+ * wrench and update), pair_stage1, pair_stage2 (with a skin, the first-stage
+ * kernels after a rebuild also filter the exact lists), skin (search decision
+ * and copy-back), export. */
+#define CRM_NUM_KERNELS 10
 typedef struct crm_profile {
     int64_t launches[CRM_NUM_KERNELS]; /* kernels enqueued since the last reset */
     double ms[CRM_NUM_KERNELS];        /* summed event-timed durations (timing on) */

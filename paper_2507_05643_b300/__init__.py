@@ -49,7 +49,8 @@ class Params(C.Structure):
                 ("ps_freq", C.c_int32), ("max_neighbors", C.c_int32),
                 ("domain_min", C.c_double * 3), ("domain_max", C.c_double * 3),
                 ("growth", C.c_double), ("shrink_ratio", C.c_double),
-                ("shrink_interval", C.c_int32), ("reserved", C.c_int32)]
+                ("shrink_interval", C.c_int32), ("reserved", C.c_int32),
+                ("skin", C.c_double)]
 
 
 _d = np.ctypeslib.ndpointer(np.float64, flags="C")
@@ -92,7 +93,7 @@ _sig("crm_load_state", C.c_int, [_T, _vp, C.c_size_t])
 _sig("crm_bin_scratch_bytes", C.c_size_t, [_i64, _i64])
 _sig("crm_bin_points", C.c_int, [_vp, _i64, C.c_float, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp])
 
-NUM_KERNELS = 11
+NUM_KERNELS = 10
 
 
 class Profile(C.Structure):
@@ -157,7 +158,7 @@ def params_from_dict(d: dict, domain_min, domain_max) -> Params:
     """crm_params from a scene's parameter dictionary and grid extent."""
     p = default_params()
     for k in ("rho0", "E", "nu", "mu_s", "mu_2", "I0", "grain_d", "cohesion", "d0", "h",
-              "av_gamma", "av_xi2_over_h2"):
+              "av_gamma", "av_xi2_over_h2", "skin"):
         if k in d and d[k] is not None:
             setattr(p, k, float(d[k]))
     for k in ("av_mode", "ps_freq", "max_neighbors"):

@@ -315,7 +315,7 @@ __global__ void k_gather(DevParams p, const int *__restrict__ ranges, const int 
             W.vel[w] = make_float4(0.f, 0.f, 0.f, p.rho0);
             W.sA[w] = make_float4(0.f, 0.f, 0.f, 0.f);
             W.sB[w] = make_float2(0.f, 0.f);
-            wpid[w] = (uint32_t)(n_fluid_total + body_markers[k]);
+            wpid[w] = (uint32_t)body_markers[k];   // encoded marker pid (index | body)
         }
     }
     (void)cand_cap;

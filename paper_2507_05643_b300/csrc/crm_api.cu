@@ -64,11 +64,27 @@ struct crm_terrain {
     uint32_t *pid[2]{};
     SortScratch ss{};
     uint32_t *start = nullptr, *nbr = nullptr, *nnb = nullptr;
-    float4 *mforce = nullptr, *mtorque = nullptr;
+    float4 *mforce = nullptr;
     double *partial = nullptr;
+    unsigned *ticket = nullptr;
+    // CUDA graphs of whole steps (runs without active boxes, timing off)
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        double dt = 0.0;
+    };
+    // a step with / without the Alg. 2 rebuild, one per current buffer (a graph
+    // bakes in the buffer pointers; a search without a skin swaps the buffers)
+    StepGraph g_search[2], g_plain[2];
+    cudaStream_t cap_st = nullptr;   // private stream the graphs are captured on
+    bool graphs = true;
+    // Verlet skin (non-active runs with skin > 0)
+    bool skin_on = false;
+    uint32_t *sk_nbr = nullptr, *sk_nnb = nullptr;
+    float4 *xref = nullptr;
+    int *gate = nullptr;
+    int64_t searches_at_reset = 0, searched = 0;
     // static
     double *mloc = nullptr;
-    int *mbody = nullptr;
     BodyDev *bodies = nullptr;
     int *err = nullptr, *counts = nullptr, *win = nullptr, *abort_flag = nullptr;
     int *h_counts = nullptr;      // pinned mirror: counters + abort word
@@ -162,6 +178,7 @@ int validate(const crm_params *p, std::string &why)
             return bad("domain_max must exceed domain_min on every axis");
     if (!(p->growth >= 1.0) || !(p->shrink_ratio > 0 && p->shrink_ratio <= 1.0) || p->shrink_interval < 1)
         return bad("growth >= 1, shrink_ratio in (0, 1], shrink_interval >= 1");
+    if (!(p->skin >= 0.0 && p->skin < 1.0)) return bad("skin must lie in [0, 1)");
     return CRM_OK;
 }
 
@@ -170,7 +187,8 @@ int make_devparams(crm_terrain *t)
 {
     const crm_params &P = t->P;
     DevParams &d = t->dp;
-    const double cell = 2.0 * P.h;
+    const double skin = t->skin_on ? P.skin : 0.0;
+    const double cell = 2.0 * P.h * (1.0 + skin);
     int64_t G[3];
     for (int k = 0; k < 3; ++k) {
         G[k] = (int64_t)std::ceil((P.domain_max[k] - P.domain_min[k]) / cell);
@@ -197,6 +215,7 @@ int make_devparams(crm_terrain *t)
     d.gx = (float)P.gravity[0];
     d.gy = (float)P.gravity[1];
     d.gz = (float)P.gravity[2];
+    for (int k = 0; k < 3; ++k) d.g64[k] = P.gravity[k];
     d.mu_s = (float)P.mu_s;
     d.mu_2 = (float)P.mu_2;
     d.I0 = (float)P.I0;
@@ -208,6 +227,11 @@ int make_devparams(crm_terrain *t)
     d.dmin_z = P.domain_min[2];
     d.cell_d = cell;
     d.maxnb = P.max_neighbors;
+    d.sk_r2 = (float)(cell * cell);
+    d.disp_thr2 = (float)(0.95 * skin * P.h * 0.95 * skin * P.h);
+    const double grow3 = (1.0 + skin) * (1.0 + skin) * (1.0 + skin);
+    d.skin_cap = (int)std::ceil(P.max_neighbors * grow3 * 1.05) + 8;
+    d.gate = nullptr;
     return CRM_OK;
 }
 
@@ -277,12 +301,24 @@ int alloc_working(crm_terrain *t)
     t->nbr = t->dalloc<uint32_t>(G_WORK, (size_t)d.maxnb * d.ell);
     t->nnb = t->dalloc<uint32_t>(G_WORK, N);
     t->mforce = t->dalloc<float4>(G_WORK, t->capM);
-    t->mtorque = t->dalloc<float4>(G_WORK, t->capM);
-    t->partial = t->dalloc<double>(G_WORK, (size_t)grid_for(t->capM)
+    t->partial = t->dalloc<double>(G_WORK, (size_t)bce_blocks(d)
                                                * std::max<size_t>(t->hbodies.size(), 1) * 6);
+    t->ticket = t->dalloc<unsigned>(G_WORK, 1);
+    if (t->skin_on) {
+        t->sk_nbr = t->dalloc<uint32_t>(G_WORK, (size_t)d.skin_cap * d.ell);
+        t->sk_nnb = t->dalloc<uint32_t>(G_WORK, N);
+        t->xref = t->dalloc<float4>(G_WORK, N);
+    }
     if (t->oom) return t->fail(CRM_ENOMEM, "device allocation of the working set failed");
+    if (t->skin_on) {
+        CRM_CUDA(t, cudaMemsetAsync(t->sk_nnb, 0, N * sizeof(uint32_t), t->st));
+        const int g0[GATE_WORDS] = {1, 0, 1, 0};   // the first rebuild searches
+        CRM_CUDA(t, cudaMemcpyAsync(t->gate, g0, sizeof(g0), cudaMemcpyHostToDevice, t->st));
+        CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    }
     CRM_CUDA(t, cudaMemsetAsync(t->nnb, 0, N * sizeof(uint32_t), t->st));
     CRM_CUDA(t, cudaMemsetAsync(t->mforce, 0, std::max<int64_t>(t->capM, 1) * sizeof(float4), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->ticket, 0, sizeof(unsigned), t->st));
     t->cur = 0;
     t->lists_valid = false;
     return CRM_OK;
@@ -380,23 +416,37 @@ int commit(crm_terrain *t)
     const int64_t nF = t->nFtot, nM = t->nMtot, N = nF + nM;
     if (N >= (int64_t)kIndexMask)
         return t->fail(CRM_EINVAL, "more than 2^26 particles and markers in one terrain");
+    t->active = !t->box_body_h.empty();
+    t->skin_on = !t->active && t->P.skin > 0.0;
     int rc = make_devparams(t);
     if (rc) return rc;
     DevParams &d = t->dp;
     d.n_bodies = (int)t->hbodies.size();
-    t->active = !t->box_body_h.empty();
+    // largest marker arm of each body, and the reference pose of the skin bound
+    for (size_t b = 0; b < t->hbodies.size(); ++b) {
+        BodyDev &B = t->hbodies[b];
+        B.rmax = 0.0;
+        for (int k = 0; k < 7; ++k) B.ref_pose[k] = B.pose[k];
+    }
+    for (int64_t a = 0; a < nM; ++a) {
+        const int b = t->hmbody[a];
+        if (b < 0) continue;
+        const double *x = &t->hmloc[3 * a];
+        t->hbodies[b].rmax = std::max(t->hbodies[b].rmax, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+    }
     const int64_t full_cells = (int64_t)d.GX * d.GY * d.GZ;
     cudaStream_t st = t->st;
 
     // static device state
     t->mloc = t->dalloc<double>(G_STATIC, 3 * nM);
-    t->mbody = t->dalloc<int>(G_STATIC, nM);
     t->bodies = t->dalloc<BodyDev>(G_STATIC, t->hbodies.size());
     t->err = t->dalloc<int>(G_STATIC, 1);
     t->counts = t->dalloc<int>(G_STATIC, C_WORDS);
     t->win = t->dalloc<int>(G_STATIC, 8);
     t->abort_flag = t->dalloc<int>(G_STATIC, 1);
+    t->gate = t->dalloc<int>(G_STATIC, GATE_WORDS);
     if (t->oom) return t->fail(CRM_ENOMEM, "device allocation failed");
+    if (t->skin_on) d.gate = t->gate;
     if (!t->h_counts && cudaMallocHost(&t->h_counts, (C_WORDS + 2) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         t->h_counts = nullptr;
@@ -410,7 +460,6 @@ int commit(crm_terrain *t)
     CRM_CUDA(t, cudaMemsetAsync(t->counts, 0, C_WORDS * sizeof(int), st));
     if (nM) {
         rc = upload(t, t->mloc, t->hmloc.data(), 3 * nM);
-        if (!rc) rc = upload(t, t->mbody, t->hmbody.data(), nM);
         if (rc) return rc;
     }
     if (!t->hbodies.empty()) {
@@ -457,7 +506,7 @@ int commit(crm_terrain *t)
                 a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 b2[i] = make_float2(0.f, 0.f);
             }
-            pid[i] = (uint32_t)i;
+            pid[i] = i < nF ? (uint32_t)i : marker_pid(i, t->hmbody[i - nF]);
         }
         const int c = t->cur;
         rc = upload(t, t->A[c].pos, p4.data(), N);
@@ -472,6 +521,10 @@ int commit(crm_terrain *t)
         if (!rc) rc = upload(t, t->win, win, 6);
         if (rc) return rc;
         CRM_CUDA(t, cudaStreamSynchronize(st));
+        if (cudaStreamCreateWithFlags(&t->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            t->cap_st = nullptr;   // direct launches only
+        }
         t->committed = true;
         return CRM_OK;
     }
@@ -503,7 +556,7 @@ int commit(crm_terrain *t)
     std::vector<int> fixed, bodym;
     for (int64_t a = 0; a < nM; ++a) {
         if (t->hmbody[a] < 0) fixed.push_back((int)a);
-        else bodym.push_back((int)a);
+        else bodym.push_back((int)marker_pid(nF + a, t->hmbody[a]));
     }
     std::vector<int64_t> fkey(fixed.size());
     for (size_t k = 0; k < fixed.size(); ++k) {
@@ -590,10 +643,10 @@ int commit(crm_terrain *t)
 }
 
 enum KernelId { K_KEYS, K_SCAN, K_SCATTER, K_REORDER, K_NEIGHBORS, K_BCE, K_PAIR1, K_PAIR2,
-                K_WRENCH, K_BODY, K_EXPORT };
+                K_SKIN, K_EXPORT };
 const char *const kKernelNames[CRM_NUM_KERNELS] = {
     "keys", "scan", "scatter", "reorder", "neighbors", "bce", "pair_stage1", "pair_stage2",
-    "wrench_partial", "body_update", "export"};
+    "skin", "export"};
 
 // Enqueue one kernel through `launch`, counting it and, when timing is on,
 // bracketing it with two events on the handle's stream.  The active-domain
@@ -660,70 +713,216 @@ void activity_pass(crm_terrain *t)
     t->have_working = true;
 }
 
+// Alg. 2 "PreprocessNeighborList" + Alg. 1.  Without a skin: keys, counting
+// sort, reorder into the other buffer, 2h search.  With a skin: a device-side
+// decision gates the sort and the skin-radius search (written back into the
+// current buffer); the stage-1 kernels then filter the exact lists from the
+// skin lists.
+void enqueue_search(crm_terrain *t)
+{
+    const int c = t->cur, n = 1 - c;
+    const DevParams &d = t->dp;
+    launch(t, K_KEYS, [&] { launch_keys(d, t->A[c], t->pid[c], t->mloc, t->bodies,
+                                        t->ss, t->err, (int)t->nFtot, t->st); });
+    launch(t, K_SCAN, [&] { launch_scan_reset(t->ss.count, t->start, 2 * (int64_t)d.M + 1, t->ss,
+                                              t->err, t->st, d.gate); });
+    launch(t, K_SCATTER, [&] { launch_scatter(d, t->ss, t->start, t->st); });
+    launch(t, K_REORDER, [&] { launch_reorder(d, t->ss, t->start, t->A[c], t->pid[c], t->A[n],
+                                              t->pid[n], t->st); });
+    if (t->skin_on) {
+        launch(t, K_NEIGHBORS, [&] { launch_neighbors(d, t->A[n].pos, t->start, t->sk_nbr,
+                                                      t->sk_nnb, d.skin_cap, d.sk_r2, t->err,
+                                                      t->st); });
+        launch(t, K_SKIN, [&] { launch_copyback(d, t->A[n], t->pid[n], t->A[c], t->pid[c], t->xref,
+                                                t->bodies, t->st); });
+    } else {
+        launch(t, K_NEIGHBORS, [&] { launch_neighbors(d, t->A[n].pos, t->start, t->nbr, t->nnb,
+                                                      d.maxnb, d.four_h2, t->err, t->st); });
+    }
+}
+
 void rebuild(crm_terrain *t)
 {
     if (t->active) activity_pass(t);
-    const int c = t->cur, n = 1 - c;
     const DevParams &d = t->dp;
     if (d.capN > 0) {
-        launch(t, K_KEYS, [&] { launch_keys(d, t->A[c], t->pid[c], t->mloc, t->mbody, t->bodies,
-                                            t->ss, t->err, (int)t->nFtot, t->st); });
-        launch(t, K_SCAN, [&] { launch_scan_reset(t->ss.count, t->start, 2 * (int64_t)d.M + 1,
-                                                  t->ss, t->err, t->st); });
-        launch(t, K_SCATTER, [&] { launch_scatter(d, t->ss, t->start, t->st); });
-        launch(t, K_REORDER, [&] { launch_reorder(d, t->ss, t->start, t->A[c], t->pid[c], t->A[n],
-                                                  t->pid[n], t->st); });
-        launch(t, K_NEIGHBORS,
-               [&] { launch_neighbors(d, t->A[n].pos, t->start, t->nbr, t->nnb, t->err, t->st); });
+        if (t->skin_on) launch(t, K_SKIN, [&] { launch_decide(d, t->gate, 0ull, 0, t->st); });
+        enqueue_search(t);
     }
-    t->cur = n;
+    if (!t->skin_on) t->cur = 1 - t->cur;
     t->lists_valid = true;
     t->prof.rebuilds += 1;
 }
 
-void bce(crm_terrain *t, StageArrays S, double tau, int accel)
+// BCE state at stage offset tau; accel 1 (stage 2) also reduces the wrench
+// and advances the bodies by dt when `integrate`.
+// `filter` (stage 1 right after a rebuild with the skin): the kernel walks the
+// skin lists and writes the exact lists for the rest of the step.
+void bce(crm_terrain *t, StageArrays S, double tau, int accel, double dt = 0.0, int integrate = 0,
+         bool filter = false)
 {
     const DevParams &d = t->dp;
     if (d.capM == 0) return;
+    if (accel == 1 && d.n_bodies == 0) accel = 0;
     const int c = t->cur;
-    launch(t, K_BCE, [&] { launch_bce(d, S, t->A[c].pos, t->pid[c], t->mloc, t->mbody, t->bodies,
-                                      t->nbr, t->nnb, tau, accel, (int)t->nFtot, t->mforce,
-                                      t->mtorque, t->st); });
+    int *gate = t->skin_on ? t->gate : nullptr;
+    const uint32_t *skl = filter ? t->sk_nbr : nullptr, *skn = filter ? t->sk_nnb : nullptr;
+    launch(t, K_BCE, [&] { launch_bce(d, S, t->A[c].pos, t->pid[c], t->mloc, t->bodies, t->nbr,
+                                      t->nnb, tau, accel, (int)t->nFtot, t->mforce, t->partial,
+                                      t->ticket, dt, integrate, gate, t->st, skl, skn, t->err); });
 }
 
-void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, RateOut out)
+void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, RateOut out,
+          bool filter = false)
 {
     const DevParams &d = t->dp;
     if (d.capF == 0) return;
     const int k = mode == kStage2 ? K_PAIR2 : K_PAIR1;
     const uint32_t *flags = t->active ? t->pid[t->cur] : nullptr;
+    const float4 *xref = t->skin_on ? t->xref : nullptr;
+    int *gate = t->skin_on ? t->gate : nullptr;
+    const uint32_t *skl = filter ? t->sk_nbr : nullptr, *skn = filter ? t->sk_nnb : nullptr;
     launch(t, k, [&] { launch_pair(mode, d, S, Y, t->MID, t->nbr, t->nnb, flags, dt, out, t->err,
-                                   t->st); });
+                                   xref, gate, t->st, skl, skn); });
 }
 
-void wrench(crm_terrain *t, double dt, int integrate)
+void enqueue_stages(crm_terrain *t, double dt, bool filter)
 {
-    const DevParams &d = t->dp;
-    if (d.n_bodies == 0) return;
-    if (d.capM > 0)
-        launch(t, K_WRENCH, [&] { launch_wrench_partial(d, t->mforce, t->mtorque, t->partial, t->st); });
-    launch(t, K_BODY, [&] { launch_body_update(d, t->partial, t->bodies, dt, integrate, t->st); });
+    const int c = t->cur;
+    RateOut none{};
+    bce(t, t->A[c], 0.0, 0, 0.0, 0, filter);
+    pair(t, kStage1, t->A[c], t->A[c], (float)dt, none, filter);
+    bce(t, t->MID, 0.5 * dt, 1, dt, 1);
+    pair(t, kStage2, t->MID, t->A[c], (float)dt, none);
 }
 
 void one_step(crm_terrain *t, double dt)
 {
     const int ps = t->P.ps_freq;
-    if (!t->lists_valid || t->step_index % ps == 0) rebuild(t);
-    const int c = t->cur;
-    RateOut none{};
-    bce(t, t->A[c], 0.0, 0);
-    pair(t, kStage1, t->A[c], t->A[c], (float)dt, none);
-    bce(t, t->MID, 0.5 * dt, 1);
-    pair(t, kStage2, t->MID, t->A[c], (float)dt, none);
-    wrench(t, dt, 1);
+    const bool search = !t->lists_valid || t->step_index % ps == 0;
+    if (search) rebuild(t);
+    enqueue_stages(t, dt, search && t->skin_on);
     t->step_index += 1;
     t->time += dt;
     t->prof.steps += 1;
+}
+
+// Capture one step into an executable graph: with the skin, the decision
+// kernel switches a conditional node around the cell sort and search.
+int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph &G)
+{
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    cudaStream_t user = t->st;
+    const bool timing = t->timing;
+    const crm_profile saved = t->prof;
+    const int cur = t->cur;
+    t->st = t->cap_st;
+    t->timing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    const DevParams &d = t->dp;
+    if (e == cudaSuccess && search && t->skin_on) {
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(t->st, g, nullptr, nullptr, 0, mode);
+        if (e == cudaSuccess) {
+            launch_decide(d, t->gate, (unsigned long long)h, 1, t->st);
+            e = cudaStreamEndCapture(t->st, &g);
+        }
+        cudaGraphNode_t dec = nullptr, cn = nullptr;
+        size_t nn = 1;
+        if (e == cudaSuccess) e = cudaGraphGetNodes(g, &dec, &nn);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&cn, g, &dec, nullptr, 1, &cp);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(t->st, body, nullptr, nullptr, 0, mode);
+            if (e == cudaSuccess) {
+                enqueue_search(t);
+                e = cudaStreamEndCapture(t->st, &body);
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(t->st, g, &cn, nullptr, 1, mode);
+        if (e == cudaSuccess) {
+            enqueue_stages(t, dt, true);
+            e = cudaStreamEndCapture(t->st, &g);
+        }
+    } else if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(t->st, g, nullptr, nullptr, 0, mode);
+        if (e == cudaSuccess) {
+            if (search) {
+                enqueue_search(t);
+                t->cur = 1 - t->cur;
+            }
+            enqueue_stages(t, dt, false);
+            e = cudaStreamEndCapture(t->st, &g);
+        }
+    }
+    t->cur = cur;
+    t->st = user;
+    t->timing = timing;
+    t->prof = saved;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        G.exec = nullptr;
+        return t->fail(CRM_ECUDA, std::string("step graph capture failed: ") + cudaGetErrorString(e));
+    }
+    G.dt = dt;
+    return CRM_OK;
+}
+
+// One step by graph replay (same kernels as one_step).
+int graph_step(crm_terrain *t, double dt)
+{
+    const bool search = !t->lists_valid || t->step_index % t->P.ps_freq == 0;
+    crm_terrain::StepGraph &G = search ? t->g_search[t->cur] : t->g_plain[t->cur];
+    if (!G.exec || G.dt != dt) {
+        if (capture_step(t, dt, search, G) != CRM_OK) {
+            // no graph on this device / driver: direct launches from now on
+            t->graphs = false;
+            t->msg.clear();
+            one_step(t, dt);
+            CRM_CUDA(t, cudaGetLastError());
+            return CRM_OK;
+        }
+    }
+    CRM_CUDA(t, cudaGraphLaunch(G.exec, t->st));
+    const DevParams &d = t->dp;
+    // launch bookkeeping of the replayed kernels (the searches that the skin
+    // decision actually ran are read back from the device at profile_read)
+    if (search) {
+        if (t->skin_on) {
+            t->prof.launches[K_SKIN] += 1;
+        } else {
+            t->prof.launches[K_KEYS] += 1;
+            t->prof.launches[K_SCAN] += 1;
+            t->prof.launches[K_SCATTER] += 1;
+            t->prof.launches[K_REORDER] += 1;
+            t->prof.launches[K_NEIGHBORS] += 1;
+            t->cur = 1 - t->cur;
+        }
+        t->prof.rebuilds += 1;
+        t->lists_valid = true;
+    }
+    if (d.capM > 0) t->prof.launches[K_BCE] += 2;
+    if (d.capF > 0) {
+        t->prof.launches[K_PAIR1] += 1;
+        t->prof.launches[K_PAIR2] += 1;
+    }
+    t->step_index += 1;
+    t->time += dt;
+    t->prof.steps += 1;
+    return CRM_OK;
 }
 
 int read_counts(crm_terrain *t)
@@ -859,6 +1058,7 @@ void crm_default_params(crm_params *p)
     p->growth = 1.2;
     p->shrink_ratio = 0.75;
     p->shrink_interval = 50;
+    p->skin = 0.1;
 }
 
 int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
@@ -902,6 +1102,11 @@ int crm_destroy(crm_terrain *t)
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : t->ev_pool) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b) {
+        if (t->g_search[b].exec) cudaGraphExecDestroy(t->g_search[b].exec);
+        if (t->g_plain[b].exec) cudaGraphExecDestroy(t->g_plain[b].exec);
+    }
+    if (t->cap_st) cudaStreamDestroy(t->cap_st);
     for (int g = 0; g < G_COUNT; ++g) t->free_group(g);
     if (t->h_counts) cudaFreeHost(t->h_counts);
     delete t;
@@ -1033,6 +1238,13 @@ int crm_step(crm_terrain *t, double dt, int32_t n_steps)
     int rc = commit(t);
     if (rc) return rc;
     if (t->active) return step_active(t, dt, n_steps);
+    if (t->graphs && !t->timing && t->cap_st && t->dp.capN > 0) {
+        for (int s = 0; s < n_steps; ++s) {
+            rc = graph_step(t, dt);
+            if (rc) return rc;
+        }
+        return CRM_OK;
+    }
     for (int s = 0; s < n_steps; ++s) one_step(t, dt);
     CRM_CUDA(t, cudaGetLastError());
     return CRM_OK;
@@ -1153,8 +1365,15 @@ int crm_eval_rates(crm_terrain *t, int64_t cap_sph, float *drho, float *dvel, fl
     float *odrho = o, *odu = o + nF, *ods = odu + 3 * nF, *omacc = ods + 6 * nF,
           *omvel = omacc + 3 * nM, *omsig = omvel + 3 * nM;
     CRM_CUDA(t, cudaMemsetAsync(o, 0, out_bytes, t->st));
-    bce(t, t->A[c], 0.0, 2);
-    pair(t, kEval, t->A[c], t->A[c], 0.0f, r);
+    if (t->skin_on) {
+        // exact lists from the skin lists first (marker and fluid rows)
+        bce(t, t->A[c], 0.0, 0, 0.0, 0, true);
+        pair(t, kEval, t->A[c], t->A[c], 0.0f, r, true);
+        bce(t, t->A[c], 0.0, 2);
+    } else {
+        bce(t, t->A[c], 0.0, 2);
+        pair(t, kEval, t->A[c], t->A[c], 0.0f, r);
+    }
     if (d.capN > 0)
         launch(t, K_EXPORT, [&] { launch_export_rates(d, t->pid[c], r, t->A[c], t->mforce,
                                                       (int)t->nFtot, odrho, odu, ods, omacc, omvel,
@@ -1187,16 +1406,16 @@ int crm_get_neighbors(crm_terrain *t, int64_t cap, int64_t *offset, int32_t *lis
     if (rc) return rc;
     const int64_t N = hs[2];
     std::vector<int64_t> cnt(Ntot + 1, 0);
-    for (int64_t s = 0; s < N; ++s) cnt[(pid[s] & ~kExtendedBit) + 1] = nnb[s];
+    for (int64_t s = 0; s < N; ++s) cnt[pid_index(pid[s]) + 1] = nnb[s];
     for (int64_t i = 0; i < Ntot; ++i) cnt[i + 1] += cnt[i];
     if (nnz) *nnz = cnt[Ntot];
     if (offset) std::memcpy(offset, cnt.data(), (Ntot + 1) * sizeof(int64_t));
     if (!list) return CRM_OK;
     if (cap < cnt[Ntot]) return t->fail(CRM_EINVAL, "crm_get_neighbors: list capacity too small");
     for (int64_t s = 0; s < N; ++s) {
-        const int64_t o = cnt[pid[s] & ~kExtendedBit];
+        const int64_t o = cnt[pid_index(pid[s])];
         for (uint32_t k = 0; k < nnb[s]; ++k)
-            list[o + k] = (int32_t)(pid[tab[(size_t)k * d.ell + s] & kIndexMask] & ~kExtendedBit);
+            list[o + k] = (int32_t)pid_index(pid[tab[(size_t)k * d.ell + s] & kIndexMask]);
         std::sort(list + o, list + o + nnb[s]);
     }
     return CRM_OK;
@@ -1220,6 +1439,12 @@ int crm_profile_reset(crm_terrain *t, int32_t timing)
     }
     std::memset(&t->prof, 0, sizeof(t->prof));
     t->timing = timing != 0;
+    t->searched = 0;
+    if (t->committed && t->skin_on) {
+        int g[GATE_WORDS];
+        CRM_CUDA(t, cudaMemcpy(g, t->gate, sizeof(g), cudaMemcpyDeviceToHost));
+        t->searches_at_reset = g[GATE_SEARCHES];
+    }
     return CRM_OK;
 }
 
@@ -1227,6 +1452,27 @@ int crm_profile_read(crm_terrain *t, crm_profile *out)
 {
     if (!t || !out) return CRM_EINVAL;
     if (t->committed) CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    if (t->committed && t->skin_on) {
+        // cell searches the skin decision ran since the reset (each is keys,
+        // scan, scatter, reorder, search and copy-back)
+        int g[GATE_WORDS];
+        CRM_CUDA(t, cudaMemcpy(g, t->gate, sizeof(g), cudaMemcpyDeviceToHost));
+        const int64_t n = g[GATE_SEARCHES] - t->searches_at_reset;
+        t->searches_at_reset = g[GATE_SEARCHES];
+        if (!t->timing) {
+            t->prof.launches[K_KEYS] = t->prof.launches[K_SCAN] = t->prof.launches[K_SCATTER] = 0;
+            t->prof.launches[K_REORDER] = t->prof.launches[K_NEIGHBORS] = 0;
+        }
+        t->searched += n;
+        if (!t->timing) {
+            t->prof.launches[K_KEYS] += t->searched;
+            t->prof.launches[K_SCAN] += t->searched;
+            t->prof.launches[K_SCATTER] += t->searched;
+            t->prof.launches[K_REORDER] += t->searched;
+            t->prof.launches[K_NEIGHBORS] += t->searched;
+            t->prof.launches[K_SKIN] += t->searched;
+        }
+    }
     for (auto &r : t->pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) t->prof.ms[r.k] += ms;
@@ -1323,6 +1569,10 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used)
     std::memcpy(&t->time, &hdr[1], sizeof(double));
     t->lists_valid = false;
     t->have_working = false;
+    if (t->skin_on) {
+        const int g0[GATE_WORDS] = {1, 0, 1, 0};
+        CRM_CUDA(t, cudaMemcpyAsync(t->gate, g0, sizeof(g0), cudaMemcpyHostToDevice, t->st));
+    }
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     return CRM_OK;
 }

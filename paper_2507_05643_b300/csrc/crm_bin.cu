@@ -30,8 +30,10 @@ __device__ __forceinline__ int pad(int k) { return k + (k >> 5); }
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(uint32_t *__restrict__ count, uint32_t *__restrict__ start, int64_t n,
-       unsigned long long *status, uint32_t *ctr, int64_t n_tiles, int *err)
+       unsigned long long *status, uint32_t *ctr, int64_t n_tiles, int *err,
+       const int *__restrict__ gate)
 {
+    if (gate != nullptr && __ldg(gate) == 0) return;   // every block: uniform
     __shared__ uint32_t s_items[kScanTile + kScanTile / 32];
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_tile, s_epoch, s_prefix;
@@ -132,11 +134,11 @@ k_scan(uint32_t *__restrict__ count, uint32_t *__restrict__ start, int64_t n,
 }  // namespace
 
 void launch_scan_reset(uint32_t *count, uint32_t *start, int64_t n, const SortScratch &s,
-                       int *err, cudaStream_t st)
+                       int *err, cudaStream_t st, const int *gate)
 {
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     k_scan<<<(unsigned)tiles, kScanThreads, 0, st>>>(count, start, n, s.tile_status, s.ctr,
-                                                     tiles, err);
+                                                     tiles, err, gate);
 }
 
 // ---------------------------------------------------------------------------
@@ -147,9 +149,9 @@ namespace {
 __global__ void k_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ rank,
                           const uint32_t *__restrict__ start, uint32_t *__restrict__ tmp,
                           int64_t n, const int *__restrict__ n_dev,
-                          const int *__restrict__ abort_flag)
+                          const int *__restrict__ abort_flag, const int *__restrict__ gate = nullptr)
 {
-    if (abort_flag && *abort_flag) return;
+    if ((abort_flag && *abort_flag) || (gate != nullptr && __ldg(gate) == 0)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (n_dev ? (int64_t)__ldg(n_dev) : n)) return;
     tmp[start[keys[i]] + rank[i]] = (uint32_t)i;
@@ -206,12 +208,12 @@ __global__ void k_hash_points(const float *__restrict__ xyz, int64_t n, float in
 // inside the working window, offset by M for markers, so one counting sort
 // yields fluid slots [0, nF) then marker slots [nF, N), each cell-sorted.
 __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__restrict__ pid,
-                       const double *__restrict__ mloc, const int *__restrict__ mbody,
+                       const double *__restrict__ mloc,
                        const BodyDev *__restrict__ bodies, uint32_t *__restrict__ keys,
                        uint32_t *__restrict__ rank, uint32_t *__restrict__ count,
                        int *__restrict__ err, int n_fluid_total)
 {
-    if (*p.abort) return;
+    if (*p.abort || gated_off(p)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const Sizes z = load_sizes(p);
     if (i >= z.N) return;
@@ -238,10 +240,11 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
         }
     } else {
         seg = 1;
-        const int mi = (int)(pid[i] & ~kExtendedBit) - n_fluid_total;
+        const uint32_t id = pid[i];
+        const int mi = (int)pid_index(id) - n_fluid_total;
         double x[3];
         float u[3], a[3], arm[3];
-        marker_state(bodies, mbody[mi], mloc + 3 * (int64_t)mi, 0.0, x, u, a, arm);
+        marker_state(bodies, pid_body(id), mloc + 3 * (int64_t)mi, 0.0, x, u, a, arm);
         const double fx = floor((x[0] - p.dmin_x) / p.cell_d);
         const double fy = floor((x[1] - p.dmin_y) / p.cell_d);
         const double fz = floor((x[2] - p.dmin_z) / p.cell_d);
@@ -294,9 +297,10 @@ __device__ __forceinline__ uint32_t xsorted_slot(const uint32_t *__restrict__ ke
 __global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restrict__ keys,
                           const uint32_t *__restrict__ start, const uint32_t *__restrict__ tmp,
                           StageArrays src, const uint32_t *__restrict__ pid_src, StageArrays dst,
-                          uint32_t *__restrict__ pid_dst, const int *__restrict__ abort_flag)
+                          uint32_t *__restrict__ pid_dst, const int *__restrict__ abort_flag,
+                          const int *__restrict__ gate)
 {
-    if (*abort_flag) return;
+    if (*abort_flag || (gate != nullptr && __ldg(gate) == 0)) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= __ldg(n_dev)) return;
     const uint32_t i = tmp[s];
@@ -322,9 +326,10 @@ __global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restr
 // rebuild x_s - x_j from the cell-relative offsets.
 __global__ void __launch_bounds__(kBlock)
 k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restrict__ start,
-            uint32_t *__restrict__ nbr, uint32_t *__restrict__ nnb, int *__restrict__ err)
+            uint32_t *__restrict__ nbr, uint32_t *__restrict__ nnb, int cap, float r2cut,
+            int *__restrict__ err)
 {
-    if (*p.abort) return;
+    if (*p.abort || gated_off(p)) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const Sizes z = load_sizes(p);
     if (s >= z.N) return;
@@ -335,7 +340,7 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
     const int lx = ix - W.x0, ly = iy - W.y0, lz = iz - W.z0;
     const int nseg = s < z.nF ? 2 : 1;
     const float cell = p.cell;
-    const float lim2 = p.four_h2 * (1.0f + 1e-5f);
+    const float lim2 = r2cut * (1.0f + 1e-5f);
     int cnt = 0;
     for (int dz = -1; dz <= 1; ++dz) {
         const int lz2 = lz + dz;
@@ -371,8 +376,8 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
                         if (dx != 0 && fabsf(rx) >= R) break;
                         const float ry = sy - pj.y, rz = sz - pj.z;
                         const float r2 = rx * rx + ry * ry + rz * rz;
-                        if (r2 < p.four_h2 && j != s) {
-                            if (cnt < p.maxnb) nbr[(size_t)cnt * p.ell + s] = (uint32_t)j | tag;
+                        if (r2 < r2cut && j != s) {
+                            if (cnt < cap) nbr[(size_t)cnt * p.ell + s] = (uint32_t)j | tag;
                             ++cnt;
                         }
                     }
@@ -380,16 +385,16 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
             }
         }
     }
-    if (cnt > p.maxnb) atomicOr(err, ERR_CAPACITY);
-    nnb[s] = (uint32_t)min(cnt, p.maxnb);
+    if (cnt > cap) atomicOr(err, ERR_CAPACITY);
+    nnb[s] = (uint32_t)min(cnt, cap);
 }
 
 // Host launchers of the terrain rebuild, one kernel each.
 void launch_keys(const DevParams &p, StageArrays cur, const uint32_t *pid_cur, const double *mloc,
-                 const int *mbody, const BodyDev *bodies, const SortScratch &s, int *err,
+                 const BodyDev *bodies, const SortScratch &s, int *err,
                  int n_fluid_total, cudaStream_t st)
 {
-    k_keys<<<grid_for(p.capN), kBlock, 0, st>>>(p, cur.pos, pid_cur, mloc, mbody, bodies, s.keys,
+    k_keys<<<grid_for(p.capN), kBlock, 0, st>>>(p, cur.pos, pid_cur, mloc, bodies, s.keys,
                                              s.rank, s.count, err, n_fluid_total);
 }
 
@@ -397,7 +402,7 @@ void launch_scatter(const DevParams &p, const SortScratch &s, const uint32_t *st
                     cudaStream_t st)
 {
     k_scatter<<<grid_for(p.capN), kBlock, 0, st>>>(s.keys, s.rank, start, s.tmp, p.capN,
-                                                   p.sizes + 2, p.abort);
+                                                   p.sizes + 2, p.abort, p.gate);
 }
 
 void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *start,
@@ -405,13 +410,75 @@ void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *st
                     cudaStream_t st)
 {
     k_reorder<<<grid_for(p.capN), kBlock, 0, st>>>(p.sizes + 2, s.keys, start, s.tmp, cur, pid_cur,
-                                                   nxt, pid_nxt, p.abort);
+                                                   nxt, pid_nxt, p.abort, p.gate);
 }
 
 void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
-                      uint32_t *nnb, int *err, cudaStream_t st)
+                      uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st)
 {
-    k_neighbors<<<grid_for(p.capN), kBlock, 0, st>>>(p, pos, start, nbr, nnb, err);
+    k_neighbors<<<grid_for(p.capN), kBlock, 0, st>>>(p, pos, start, nbr, nnb, cap, r2cut, err);
+}
+
+// ---------------------------------------------------------------------------
+// Verlet skin.  Alg. 2 asks for the exact 2h neighbour sets of the positions at
+// each rebuild step.  With a skin s the cell search keeps every pair closer
+// than R = 2h (1 + s); as long as no particle has moved more than s h since that
+// search, every pair now closer than 2h is in those lists, so filtering them
+// gives exactly the sets a fresh search would.  The search (and the cell sort
+// before it) is redone only when the largest displacement reaches s h.
+
+// k_decide: the cell search is due when forced or when the largest squared
+// displacement since the last search reached disp_thr2.  With a graph
+// conditional handle, it also switches the graph's rebuild branch.
+__global__ void k_decide(DevParams p, int *__restrict__ gate,
+                         cudaGraphConditionalHandle h, int use_handle)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int due = 0;
+    if (!*p.abort) {
+        const float d2 = __int_as_float(gate[GATE_DISP]);
+        due = (gate[GATE_FORCE] != 0 || !(d2 < p.disp_thr2)) ? 1 : 0;
+    }
+    gate[GATE_REBUILD] = due;
+    if (due) {
+        gate[GATE_DISP] = 0;
+        gate[GATE_FORCE] = 0;
+        gate[GATE_SEARCHES] += 1;
+    }
+    if (use_handle) cudaGraphSetConditional(h, (unsigned)due);
+}
+
+// After a search: the re-sorted arrays become the current ones, the searched
+// positions become the displacement reference, and so do the body poses.
+__global__ void k_copyback(DevParams p, StageArrays src, const uint32_t *__restrict__ pid_src,
+                           StageArrays dst, uint32_t *__restrict__ pid_dst,
+                           float4 *__restrict__ xref, BodyDev *__restrict__ bodies)
+{
+    if (*p.abort || gated_off(p)) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0)
+        for (int b = 0; b < p.n_bodies; ++b)
+            for (int k = 0; k < 7; ++k) bodies[b].ref_pose[k] = bodies[b].pose[k];
+    if (s >= __ldg(p.sizes + 2)) return;
+    const float4 ps = src.pos[s];
+    dst.pos[s] = ps;
+    dst.vel[s] = src.vel[s];
+    dst.sA[s] = src.sA[s];
+    dst.sB[s] = src.sB[s];
+    pid_dst[s] = pid_src[s];
+    xref[s] = ps;
+}
+
+void launch_decide(const DevParams &p, int *gate, unsigned long long cond_handle, int use_handle,
+                   cudaStream_t st)
+{
+    k_decide<<<1, 32, 0, st>>>(p, gate, (cudaGraphConditionalHandle)cond_handle, use_handle);
+}
+
+void launch_copyback(const DevParams &p, StageArrays src, const uint32_t *pid_src, StageArrays dst,
+                     uint32_t *pid_dst, float4 *xref, BodyDev *bodies, cudaStream_t st)
+{
+    k_copyback<<<grid_for(p.capN), kBlock, 0, st>>>(p, src, pid_src, dst, pid_dst, xref, bodies);
 }
 
 }  // namespace crm

@@ -20,6 +20,15 @@ enum : int {
 
 constexpr int kMaxBodies = 16;
 constexpr uint32_t kExtendedBit = 0x80000000u;   // pid flag: Extended-Active (read-only)
+// particle id: insertion index in bits 0..25; for a marker, bits 26..30 hold
+// its body + 1 (0 = fixed wall marker); bit 31 = Extended-Active
+constexpr uint32_t kPidIndexMask = (1u << 26) - 1u;
+__host__ __device__ __forceinline__ uint32_t pid_index(uint32_t id) { return id & kPidIndexMask; }
+__host__ __device__ __forceinline__ int pid_body(uint32_t id) { return (int)((id >> 26) & 31u) - 1; }
+__host__ __device__ __forceinline__ uint32_t marker_pid(int64_t index, int body)
+{
+    return (uint32_t)index | ((uint32_t)(body + 1) << 26);
+}
 constexpr uint32_t kIndexBits = 26;                 // neighbour entry: j | code << 26
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int kBlock = 256;
@@ -35,6 +44,7 @@ struct DevParams {
     float av_c, xi2;                      // gamma_a h c_s m, xi^2
     int av_mode;
     float gx, gy, gz;
+    double g64[3];                        // gravity in FP64 for the body update
     float mu_s, mu_2, I0, grain_d, cohesion;
     // global grid: cell coordinates (ix, iy, iz), c = (iz GY + iy) GX + ix
     int GX, GY, GZ;
@@ -54,7 +64,24 @@ struct DevParams {
     // nonzero once a step of an active-domain run has overflowed a capacity:
     // every later kernel of the enqueued steps returns at once
     const int *abort;
+    // Verlet skin: the cell search runs with radius^2 sk_r2 and writes lists of
+    // up to skin_cap entries; it is due (gate[0]) once some particle has moved
+    // disp_thr2 (squared) since the last search.  gate == nullptr: no skin,
+    // every rebuild searches the cells for the exact 2h sets.
+    float sk_r2, disp_thr2;
+    int skin_cap;
+    const int *gate;
 };
+
+// gate word layout: [0] rebuild due this step, [1] max squared displacement
+// since the last search (float bits, compared as int), [2] forced rebuild
+// [3] cell searches done (counter, for the launch bookkeeping)
+enum { GATE_REBUILD = 0, GATE_DISP = 1, GATE_FORCE = 2, GATE_SEARCHES = 3, GATE_WORDS = 4 };
+
+__device__ __forceinline__ bool gated_off(const DevParams &p)
+{
+    return p.gate != nullptr && __ldg(p.gate + GATE_REBUILD) == 0;
+}
 
 struct Sizes { int nF, nM, N; };
 struct Window { int x0, y0, z0, X, Y, Z; };
@@ -79,6 +106,8 @@ struct BodyDev {
     double mass;
     int dof;
     int pad;
+    double ref_pose[7]; // pose at the last cell search (skin bookkeeping)
+    double rmax;        // largest marker distance from the centre
 };
 
 // Stage arrays: the state every pair kernel gathers neighbours from.
@@ -220,14 +249,14 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 // Exclusive scan of count[0..n) into start[0..n), resetting count to zero.
 // Single pass, decoupled look-back; every wait is bounded (ERR_TIMEOUT).
 void launch_scan_reset(uint32_t *count, uint32_t *start, int64_t n, const SortScratch &s,
-                       int *err, cudaStream_t st);
+                       int *err, cudaStream_t st, const int *gate = nullptr);
 
 // Rebuild (Alg. 2 "PreprocessNeighborList" + Alg. 1), one kernel per launcher:
 // keys + arrival ranks, exclusive scan of the counts (cell ranges, 2M + 1
 // entries), scatter, stable reorder of every particle array from `cur` into
 // `nxt`, and the neighbour table.
 void launch_keys(const DevParams &p, StageArrays cur, const uint32_t *pid_cur, const double *mloc,
-                 const int *mbody, const BodyDev *bodies, const SortScratch &s, int *err,
+                 const BodyDev *bodies, const SortScratch &s, int *err,
                  int n_fluid_total, cudaStream_t st);
 void launch_scatter(const DevParams &p, const SortScratch &s, const uint32_t *start,
                     cudaStream_t st);
@@ -235,7 +264,15 @@ void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *st
                     StageArrays cur, const uint32_t *pid_cur, StageArrays nxt, uint32_t *pid_nxt,
                     cudaStream_t st);
 void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
-                      uint32_t *nnb, int *err, cudaStream_t st);
+                      uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st);
+// Verlet skin (Alg. 2 with a skin): decide whether the cell search is due and
+// copy the re-sorted arrays back (the stage-1 kernels filter the skin lists
+// down to the exact 2h lists).
+void launch_decide(const DevParams &p, int *gate, unsigned long long cond_handle, int use_handle,
+                   cudaStream_t st);
+void launch_copyback(const DevParams &p, StageArrays src, const uint32_t *pid_src, StageArrays dst,
+                     uint32_t *pid_dst, float4 *xref, BodyDev *bodies, cudaStream_t st);
+
 
 struct RateOut {
     float *drho;    // [slot]
@@ -246,17 +283,24 @@ struct RateOut {
 
 enum { kStage1 = 0, kStage2 = 1, kEval = 2 };
 
+// Pair sums of the fluid particles; with sk_nbr (stage 1 with a skin) the
+// particles walk their skin lists and write their exact lists to nbr / nnb.
 void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, StageArrays MID,
                  const uint32_t *nbr, const uint32_t *nnb, const uint32_t *pid, float dt,
-                 RateOut out, int *err, cudaStream_t st);
+                 RateOut out, int *err, const float4 *xref, int *gate, cudaStream_t st,
+                 const uint32_t *sk_nbr = nullptr, const uint32_t *sk_nnb = nullptr);
+// BCE state of every marker slot of S at stage offset tau; accel 1 also sums
+// the body wrench (FP64) and, in the last block, advances the bodies by dt
+// (integrate != 0); accel 2 writes every marker's force to mforce.  With
+// sk_nbr (stage 1 with a skin) the markers walk their skin lists and write
+// their exact lists to nbr / nnb.
 void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
-                const double *mloc, const int *mbody, const BodyDev *bodies, const uint32_t *nbr,
-                const uint32_t *nnb, double tau, int accel, int n_fluid_total, float4 *mforce,
-                float4 *mtorque, cudaStream_t st);
-void launch_wrench_partial(const DevParams &p, const float4 *mforce, const float4 *mtorque,
-                           double *partial, cudaStream_t st);
-void launch_body_update(const DevParams &p, const double *partial, BodyDev *bodies, double dt,
-                        int integrate, cudaStream_t st);
+                const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
+                double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
+                unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
+                const uint32_t *sk_nbr = nullptr, const uint32_t *sk_nnb = nullptr,
+                int *err = nullptr);
+unsigned bce_blocks(const DevParams &p);
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
                    float *sig, float *rho, cudaStream_t st);
 void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, StageArrays S,

@@ -4,11 +4,11 @@
 //   k_bce(tau = 0)          marker velocity / stress from the fluid at y_n
 //   k_pair<kStage1>         rates f(y_n) of every fluid particle, fused with
 //                           y_mid = y_n + dt/2 f(y_n)
-//   k_bce(tau = dt/2)       markers at the midpoint, plus their accelerations
+//   k_bce(tau = dt/2)       markers at the midpoint, their accelerations, the
+//                           per-block FP64 force / torque partials
 //   k_pair<kStage2>         rates f(y_mid), fused with y_{n+1} = y_n + dt f(y_mid)
 //                           and the return map of Sec. 2.3
-//   k_wrench_partial        FP64 per-block sums of marker force and torque
-//   k_body_update           FP64 wrench + body update (one warp per body)
+//                           (the last block sums the FP64 wrench and moves the bodies)
 // Every particle owns its outputs (gather form): no float atomics, so a step
 // is bitwise reproducible.
 #include "crm_internal.cuh"
@@ -95,11 +95,20 @@ __device__ __forceinline__ void return_map(float s[6], const float sn[6], const 
 // stage epilogue.  Neighbours j are fluid particles and BCE markers, whose
 // velocity/stress slots hold the extrapolated marker state and whose density
 // slot holds rho0.  V_j = m / rho_j.
-template <int MODE>
-__global__ void __launch_bounds__(kBlock)
-k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
-       const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ nnb,
-       const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err)
+// Neighbour lists a kernel walks (and, when filtering, writes).
+struct ListIO {
+    const uint32_t *in;   // list walked (the skin list when filtering)
+    const uint32_t *in_n;
+    uint32_t *out;        // exact list written when filtering
+    uint32_t *out_n;
+    int *err;
+};
+
+template <int MODE, bool FILTER>
+__global__ void __launch_bounds__(kBlock, 4)
+k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
+       const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err,
+       const float4 *__restrict__ xref, int *__restrict__ gate)
 {
     if (*p.abort) return;
     __shared__ float4 lut[64];
@@ -110,6 +119,7 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
     // Extended-Active particles (active domains) are read-only neighbours
     const bool adv = pid == nullptr || !(pid[i] & kExtendedBit);
     if (!adv) {
+        if (FILTER) io.out_n[i] = 0u;
         if (MODE == kStage1) {
             MID.pos[i] = S.pos[i];
             MID.vel[i] = S.vel[i];
@@ -131,8 +141,9 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
     float L[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) L[k] = 0.f;
-    const int nn = (int)nnb[i];
-    const uint32_t *row = nbr + i;
+    const int nn = (int)io.in_n[i];
+    const uint32_t *row = io.in + i;
+    int cnt = 0;
     for (int k = 0; k < nn; ++k) {
         const uint32_t e = __ldg(row + (size_t)k * p.ell);
         const uint32_t j = e & kIndexMask;
@@ -140,7 +151,13 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
         const float4 pj = __ldg(&S.pos[j]);
         const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
         const float r2 = rx * rx + ry * ry + rz * rz;
-        if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+        if (!(r2 < p.four_h2)) continue;
+        if (FILTER) {
+            // stage 1 with a skin: the pairs closer than 2h now are the exact list
+            if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
+            ++cnt;
+        }
+        if (r2 == 0.0f) continue;
         const float4 vj = __ldg(&S.vel[j]);
         const float4 aj = __ldg(&S.sA[j]);
         const float2 bj = __ldg(&S.sB[j]);
@@ -173,6 +190,10 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
                 avz = fmaf(fac, gz, avz);
             }
         }
+    }
+    if (FILTER) {
+        if (cnt > p.maxnb) atomicOr(err, ERR_CAPACITY);
+        io.out_n[i] = (uint32_t)min(cnt, p.maxnb);
     }
     const float rinv_i = 1.0f / vi.w;
     const float drho = -vi.w * cont;
@@ -213,6 +234,16 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
         const float chk = np.x + np.y + np.z + nv.x + nv.y + nv.z + nv.w + s1[0] + s1[1] + s1[2]
                           + s1[3] + s1[4] + s1[5];
         if (!isfinite(chk)) atomicOr(err, ERR_NONFINITE);
+        if (xref != nullptr) {
+            // largest squared displacement since the last cell search (skin); a
+            // max over the lanes that are here, then one atomic per group
+            const float4 r0 = xref[i];
+            const float ddx = np.x - r0.x, ddy = np.y - r0.y, ddz = np.z - r0.z;
+            const int d2 = __float_as_int(ddx * ddx + ddy * ddy + ddz * ddz);
+            const unsigned am = __activemask();
+            const int mx = __reduce_max_sync(am, d2);
+            if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMax(gate + GATE_DISP, mx);
+        }
         Y.pos[i] = np;
         Y.vel[i] = nv;
         Y.sA[i] = make_float4(s1[0], s1[1], s1[2], s1[3]);
@@ -223,198 +254,263 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID,
 // BCE marker state (Sec. 2.4) at stage offset tau, written into the marker
 // slots of S.  The home cell of each slot is read from `home_pos` -- the main
 // arrays, whose cell ids the last rebuild set -- so that the marker offset is
-// relative to the cell its neighbour codes were built against.  Velocity (Adami): u_a = 2 u_body - sum_f u_f W / sum_f W.
-// Stress: sigma_a = [sum_f sigma_f W - ((g - a_body) . sum_f rho_f (x_a - x_f) W) I]
-// / sum_f W (the pressure extrapolation of the cited scheme in stress form);
-// without fluid in reach u_a = u_body and sigma_a = 0.
-// accel: 0 = none, 1 = body markers, 2 = every marker.  The acceleration is
-// a_a = (1/rho0) sum_f V_f (sigma_a + sigma_f) . grad_a W_af + AV (no gravity);
-// force m a_a and torque arm x m a_a go to mforce / mtorque[slot - nF].
+// relative to the cell its neighbour codes were built against.
+//   Velocity (Adami): u_a = 2 u_body - sum_f u_f W / sum_f W.
+//   Stress: sigma_a = [sum_f sigma_f W - ((g - a_body) . sum_f rho_f (x_a - x_f) W) I]
+//   / sum_f W (the pressure extrapolation of the cited scheme in stress form);
+//   without fluid in reach u_a = u_body and sigma_a = 0.
+// ACCEL: 0 = state only; 1 = also the accelerations of body markers, reduced
+// per block into FP64 force / torque partials, after which the last block to
+// finish sums the partials in a fixed order and advances the bodies (the wrench
+// and body update of Sec. 2.4); 2 = the accelerations of every marker, written
+// to mforce (rate evaluation).  Acceleration: a_a = (1/rho0) sum_f V_f
+// (sigma_a + sigma_f) . grad_a W_af + AV, no gravity.
+// FILTER (stage 1 with a Verlet skin): the marker walks its skin list and keeps
+// the fluid particles closer than 2h as its exact list for the rest of the step.
+// A marker without fluid neighbours is not read by anyone (the relation is
+// symmetric), so its thread only takes part in the block reductions.
+struct BodyStep {
+    double *partial;      // [block][body][6]
+    unsigned *ticket;     // last-block counter (reset by the last block)
+    BodyDev *bodies;      // advanced by the last block
+    double dt;
+    int integrate;
+    int *gate;            // skin bookkeeping (nullable): marker displacement bound
+};
+
+
+// ACCEL == 1 tail of k_bce: FP64 per-block partial wrench of every body, then
+// the last block sums the partials in a fixed order and advances the bodies.
+__device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float f[3],
+                                                 const float arm[3], int body, bool mine,
+                                                 const BodyStep &bs, unsigned &s_bodies,
+                                                 unsigned &s_last, double (*red)[6])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (mine) atomicOr(&s_bodies, 1u << body);
+    __syncthreads();
+    const int nb = p.n_bodies;
+    for (int b = 0; b < nb; ++b) {
+        const bool present = (s_bodies >> b) & 1u;
+        if (present) {
+            double v[6] = {0, 0, 0, 0, 0, 0};
+            if (mine && body == b) {
+                v[0] = f[0]; v[1] = f[1]; v[2] = f[2];
+                v[3] = (double)arm[1] * f[2] - (double)arm[2] * f[1];
+                v[4] = (double)arm[2] * f[0] - (double)arm[0] * f[2];
+                v[5] = (double)arm[0] * f[1] - (double)arm[1] * f[0];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double a = 0.0;
+            if (present)
+                for (int w = 0; w < kBlock / 32; ++w) a += red[w][threadIdx.x];
+            bs.partial[((size_t)blockIdx.x * nb + b) * 6 + threadIdx.x] = a;
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    if (threadIdx.x == 0) s_last = atomicAdd(bs.ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int b = 0; b < nb; ++b) {
+        double v[6] = {0, 0, 0, 0, 0, 0};
+        for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                v[k] += ((volatile double *)bs.partial)[((size_t)q * nb + b) * 6 + k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double W[6] = {0, 0, 0, 0, 0, 0};
+            for (int w = 0; w < kBlock / 32; ++w)
+                for (int k = 0; k < 6; ++k) W[k] += red[w][k];
+            BodyDev &B = bs.bodies[b];
+            for (int k = 0; k < 6; ++k) B.wrench[k] = W[k];
+            if (bs.integrate) {
+                // symplectic Euler on the free linear DOFs: v += dt (F/m + g), x += dt v;
+                // prescribed DOFs move with their velocity; the orientation turns by dt w
+                for (int k = 0; k < 3; ++k) {
+                    if (B.dof & (1 << k)) {
+                        const double a = W[k] / B.mass + p.g64[k];
+                        B.twist[k] += bs.dt * a;
+                        B.acc[k] = a;
+                    } else {
+                        B.acc[k] = 0.0;
+                    }
+                    B.pose[k] += bs.dt * B.twist[k];
+                }
+                double q[4];
+                qadvance(B.pose + 3, B.twist + 3, bs.dt, q);
+                for (int k = 0; k < 4; ++k) B.pose[3 + k] = q[k];
+                if (bs.gate != nullptr) {
+                    // every marker of the body has moved at most |dc| + 2 sin(theta/2) rmax
+                    // since the last cell search (theta: rotation since then)
+                    double dc2 = 0.0, w = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double d = B.pose[k] - B.ref_pose[k];
+                        dc2 += d * d;
+                    }
+                    for (int k = 0; k < 4; ++k) w += B.pose[3 + k] * B.ref_pose[3 + k];
+                    const double sh = sqrt(fmax(0.0, 1.0 - w * w));
+                    const double d = sqrt(dc2) + 2.0 * sh * B.rmax;
+                    atomicMax(bs.gate + GATE_DISP, __float_as_int((float)(d * d) * 1.0001f));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *bs.ticket = 0u;
+}
+
+template <int ACCEL, bool FILTER>
 __global__ void __launch_bounds__(kBlock)
 k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
-      const uint32_t *__restrict__ pid,
-      const double *__restrict__ mloc, const int *__restrict__ mbody,
-      const BodyDev *__restrict__ bodies, const uint32_t *__restrict__ nbr,
-      const uint32_t *__restrict__ nnb, double tau, int accel, int n_fluid_total,
-      float4 *__restrict__ mforce, float4 *__restrict__ mtorque)
+      const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
+      const BodyDev *bodies, ListIO L, double tau, int n_fluid_total,
+      float4 *__restrict__ mforce, BodyStep bs)
 {
+    static_assert(!(FILTER && ACCEL != 0), "filtering runs in stage 1 only (no accelerations)");
     if (*p.abort) return;
     __shared__ float4 lut[64];
+    __shared__ double red[kBlock / 32][6];
+    __shared__ unsigned s_bodies, s_last;
     fill_shift_table(lut, p.cell);
+    if (threadIdx.x == 0) s_bodies = 0u;
     __syncthreads();
     const Sizes z = load_sizes(p);
     const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= z.N) return;
-    const int mi = (int)(pid[s] & ~kExtendedBit) - n_fluid_total;
-    const int body = mbody[mi];
-    double x[3];
-    float ub[3], ab[3], arm[3];
-    marker_state(bodies, body, mloc + 3 * (int64_t)mi, tau, x, ub, ab, arm);
-    const float4 home = home_pos[s];
-    int ix, iy, iz;
-    decode_cell(__float_as_uint(home.w), p, ix, iy, iz);
-    const float ox = (float)(x[0] - (p.dmin_x + ix * p.cell_d));
-    const float oy = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
-    const float oz = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
-    float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
-    float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const int nn = (int)nnb[s];
-    const uint32_t *row = nbr + s;
-    for (int k = 0; k < nn; ++k) {
-        const uint32_t e = __ldg(row + (size_t)k * p.ell);
-        const uint32_t j = e & kIndexMask;
-        const float4 sh = lut[e >> kIndexBits];
-        const float4 pj = __ldg(&S.pos[j]);
-        const float rx = ox - pj.x - sh.x, ry = oy - pj.y - sh.y, rz = oz - pj.z - sh.z;
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        if (!(r2 < p.four_h2)) continue;
-        const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
-        const float4 vj = __ldg(&S.vel[j]);
-        const float4 aj = __ldg(&S.sA[j]);
-        const float2 bj = __ldg(&S.sB[j]);
-        w += W;
-        sux = fmaf(vj.x, W, sux); suy = fmaf(vj.y, W, suy); suz = fmaf(vj.z, W, suz);
-        ss[0] = fmaf(aj.x, W, ss[0]); ss[1] = fmaf(aj.y, W, ss[1]); ss[2] = fmaf(aj.z, W, ss[2]);
-        ss[3] = fmaf(aj.w, W, ss[3]); ss[4] = fmaf(bj.x, W, ss[4]); ss[5] = fmaf(bj.y, W, ss[5]);
-        const float rw = vj.w * W;
-        sr[0] = fmaf(rw, rx, sr[0]); sr[1] = fmaf(rw, ry, sr[1]); sr[2] = fmaf(rw, rz, sr[2]);
-    }
-    float ua[3], sa[6];
-    if (w > 0.f) {
-        const float iw = 1.0f / w;
-        ua[0] = 2.f * ub[0] - sux * iw;
-        ua[1] = 2.f * ub[1] - suy * iw;
-        ua[2] = 2.f * ub[2] - suz * iw;
-        const float gp = (p.gx - ab[0]) * sr[0] + (p.gy - ab[1]) * sr[1] + (p.gz - ab[2]) * sr[2];
-        sa[0] = (ss[0] - gp) * iw; sa[1] = (ss[1] - gp) * iw; sa[2] = (ss[2] - gp) * iw;
-        sa[3] = ss[3] * iw; sa[4] = ss[4] * iw; sa[5] = ss[5] * iw;
-    } else {
-        ua[0] = ub[0]; ua[1] = ub[1]; ua[2] = ub[2];
-        for (int k = 0; k < 6; ++k) sa[k] = 0.f;
-    }
-    S.pos[s] = make_float4(ox, oy, oz, home.w);
-    S.vel[s] = make_float4(ua[0], ua[1], ua[2], p.rho0);
-    S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
-    S.sB[s] = make_float2(sa[4], sa[5]);
-    if (accel == 0) return;
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (accel == 2 || body >= 0) {
-        float mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
+    const int nn = s < z.N ? (int)L.in_n[s] : 0;
+    int body = -1;
+    float f[3] = {0.f, 0.f, 0.f}, arm[3] = {0.f, 0.f, 0.f};
+    if (nn > 0 || (ACCEL == 2 && s < z.N)) {
+        const uint32_t id = pid[s];
+        body = pid_body(id);
+        float o[3], ub[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
+        const float4 home = home_pos[s];
+        if (body >= 0) {
+            const int mi = (int)pid_index(id) - n_fluid_total;
+            double x[3];
+            marker_state(bodies, body, mloc + 3 * (int64_t)mi, tau, x, ub, ab, arm);
+            int ix, iy, iz;
+            decode_cell(__float_as_uint(home.w), p, ix, iy, iz);
+            o[0] = (float)(x[0] - (p.dmin_x + ix * p.cell_d));
+            o[1] = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
+            o[2] = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
+        } else {
+            o[0] = home.x; o[1] = home.y; o[2] = home.z;   // fixed: the searched offset
+        }
+        const uint32_t *row = L.in + s;
+        float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
+        float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int cnt = 0;
         for (int k = 0; k < nn; ++k) {
             const uint32_t e = __ldg(row + (size_t)k * p.ell);
             const uint32_t j = e & kIndexMask;
             const float4 sh = lut[e >> kIndexBits];
             const float4 pj = __ldg(&S.pos[j]);
-            const float rx = ox - pj.x - sh.x, ry = oy - pj.y - sh.y, rz = oz - pj.z - sh.z;
+            const float rx = o[0] - pj.x - sh.x, ry = o[1] - pj.y - sh.y, rz = o[2] - pj.z - sh.z;
             const float r2 = rx * rx + ry * ry + rz * rz;
-            if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+            if (!(r2 < p.four_h2)) continue;
+            if (FILTER) {
+                if (cnt < p.maxnb) L.out[(size_t)cnt * p.ell + s] = e;
+                ++cnt;
+            }
+            const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
             const float4 vj = __ldg(&S.vel[j]);
             const float4 aj = __ldg(&S.sA[j]);
             const float2 bj = __ldg(&S.sB[j]);
-            const float rinv = rsqrtf(r2);
-            const float f = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
-            const float gx = f * rx, gy = f * ry, gz = f * rz;
-            const float Vj = p.m / vj.w;
-            const float sxx = sa[0] + aj.x, syy = sa[1] + aj.y, szz = sa[2] + aj.z;
-            const float sxy = sa[3] + aj.w, sxz = sa[4] + bj.x, syz = sa[5] + bj.y;
-            mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, mx);
-            my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, my);
-            mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, mz);
-            if (p.av_mode != CRM_AV_NONE) {
-                const float vr = (ua[0] - vj.x) * rx + (ua[1] - vj.y) * ry + (ua[2] - vj.z) * rz;
-                if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-                    const float fac = 2.0f * p.av_c * vr / ((p.rho0 + vj.w) * (r2 + p.xi2));
-                    avx = fmaf(fac, gx, avx);
-                    avy = fmaf(fac, gy, avy);
-                    avz = fmaf(fac, gz, avz);
+            w += W;
+            sux = fmaf(vj.x, W, sux); suy = fmaf(vj.y, W, suy); suz = fmaf(vj.z, W, suz);
+            ss[0] = fmaf(aj.x, W, ss[0]); ss[1] = fmaf(aj.y, W, ss[1]); ss[2] = fmaf(aj.z, W, ss[2]);
+            ss[3] = fmaf(aj.w, W, ss[3]); ss[4] = fmaf(bj.x, W, ss[4]); ss[5] = fmaf(bj.y, W, ss[5]);
+            const float rw = vj.w * W;
+            sr[0] = fmaf(rw, rx, sr[0]); sr[1] = fmaf(rw, ry, sr[1]); sr[2] = fmaf(rw, rz, sr[2]);
+        }
+        if (FILTER) {
+            if (cnt > p.maxnb) atomicOr(L.err, ERR_CAPACITY);
+            L.out_n[s] = (uint32_t)min(cnt, p.maxnb);
+        }
+        float ua[3], sa[6];
+        if (w > 0.f) {
+            const float iw = 1.0f / w;
+            ua[0] = 2.f * ub[0] - sux * iw;
+            ua[1] = 2.f * ub[1] - suy * iw;
+            ua[2] = 2.f * ub[2] - suz * iw;
+            const float gp = (p.gx - ab[0]) * sr[0] + (p.gy - ab[1]) * sr[1] + (p.gz - ab[2]) * sr[2];
+            sa[0] = (ss[0] - gp) * iw; sa[1] = (ss[1] - gp) * iw; sa[2] = (ss[2] - gp) * iw;
+            sa[3] = ss[3] * iw; sa[4] = ss[4] * iw; sa[5] = ss[5] * iw;
+        } else {
+            ua[0] = ub[0]; ua[1] = ub[1]; ua[2] = ub[2];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sa[k] = 0.f;
+        }
+        S.pos[s] = make_float4(o[0], o[1], o[2], home.w);
+        S.vel[s] = make_float4(ua[0], ua[1], ua[2], p.rho0);
+        S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
+        S.sB[s] = make_float2(sa[4], sa[5]);
+        if (ACCEL == 2 || (ACCEL == 1 && body >= 0)) {
+            const int na = nn;
+            const uint32_t *arow = L.in + s;
+            float mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
+            for (int k = 0; k < na; ++k) {
+                const uint32_t e = __ldg(arow + (size_t)k * p.ell);
+                const uint32_t j = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pj = __ldg(&S.pos[j]);
+                const float rx = o[0] - pj.x - sh.x, ry = o[1] - pj.y - sh.y, rz = o[2] - pj.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+                const float4 vj = __ldg(&S.vel[j]);
+                const float4 aj = __ldg(&S.sA[j]);
+                const float2 bj = __ldg(&S.sB[j]);
+                const float rinv = rsqrtf(r2);
+                const float fk = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
+                const float gx = fk * rx, gy = fk * ry, gz = fk * rz;
+                const float Vj = p.m / vj.w;
+                const float sxx = sa[0] + aj.x, syy = sa[1] + aj.y, szz = sa[2] + aj.z;
+                const float sxy = sa[3] + aj.w, sxz = sa[4] + bj.x, syz = sa[5] + bj.y;
+                mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, mx);
+                my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, my);
+                mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, mz);
+                if (p.av_mode != CRM_AV_NONE) {
+                    const float vr = (ua[0] - vj.x) * rx + (ua[1] - vj.y) * ry + (ua[2] - vj.z) * rz;
+                    if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+                        const float fac = 2.0f * p.av_c * vr / ((p.rho0 + vj.w) * (r2 + p.xi2));
+                        avx = fmaf(fac, gx, avx);
+                        avy = fmaf(fac, gy, avy);
+                        avz = fmaf(fac, gz, avz);
+                    }
                 }
             }
+            const float ir = 1.0f / p.rho0;
+            f[0] = p.m * (mx * ir + avx);
+            f[1] = p.m * (my * ir + avy);
+            f[2] = p.m * (mz * ir + avz);
         }
-        const float ir = 1.0f / p.rho0;
-        fx = p.m * (mx * ir + avx);
-        fy = p.m * (my * ir + avy);
-        fz = p.m * (mz * ir + avz);
+    } else if (FILTER && s < z.N) {
+        L.out_n[s] = 0u;
     }
-    mforce[s - z.nF] = make_float4(fx, fy, fz, __int_as_float(body));
-    mtorque[s - z.nF] = make_float4(arm[1] * fz - arm[2] * fy, arm[2] * fx - arm[0] * fz,
-                                    arm[0] * fy - arm[1] * fx, 0.f);
-}
-
-// FP64 per-block partial wrench of every body (deterministic: fixed block
-// partition, fixed reduction tree).
-__global__ void __launch_bounds__(kBlock)
-k_wrench_partial(const int *__restrict__ nM_dev, int n_bodies, const float4 *__restrict__ mforce,
-                 const float4 *__restrict__ mtorque, double *__restrict__ partial,
-                 const int *__restrict__ abort_flag)
-{
-    if (*abort_flag) return;
-    const int nM = __ldg(nM_dev);
-    __shared__ double red[kBlock / 32][6];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float4 f = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (a < nM) {
-        f = mforce[a];
-        t = mtorque[a];
+    if constexpr (ACCEL == 2) {
+        if (s < z.N) mforce[s - z.nF] = make_float4(f[0], f[1], f[2], __int_as_float(body));
+    } else if constexpr (ACCEL == 1) {
+        body_wrench_tail(p, f, arm, body, nn > 0 && body >= 0, bs, s_bodies, s_last, red);
     }
-    const int body = __float_as_int(f.w);
-    for (int b = 0; b < n_bodies; ++b) {
-        const bool mine = body == b;
-        double v[6] = {mine ? (double)f.x : 0.0, mine ? (double)f.y : 0.0, mine ? (double)f.z : 0.0,
-                       mine ? (double)t.x : 0.0, mine ? (double)t.y : 0.0, mine ? (double)t.z : 0.0};
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        if (lane == 0)
-            for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            double acc = 0.0;
-            for (int w = 0; w < kBlock / 32; ++w) acc += red[w][threadIdx.x];
-            partial[((size_t)blockIdx.x * n_bodies + b) * 6 + threadIdx.x] = acc;
-        }
-        __syncthreads();
-    }
-}
-
-// Wrench of each body from the partials (FP64, fixed order), then the body
-// update (Sec. 2.4 FSI step, reading: symplectic Euler on the free linear
-// DOFs, v += dt (F/m + g), x += dt v; prescribed DOFs move with their
-// velocity; the orientation turns by dt w).
-__global__ void k_body_update(int n_bodies, int n_partials, const double *__restrict__ partial,
-                              BodyDev *__restrict__ bodies, double gx, double gy, double gz,
-                              double dt, int integrate, const int *__restrict__ abort_flag)
-{
-    if (*abort_flag) return;
-    const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (b >= n_bodies) return;
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int q = lane; q < n_partials; q += 32)
-        for (int k = 0; k < 6; ++k) v[k] += partial[((size_t)q * n_bodies + b) * 6 + k];
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane != 0) return;
-    BodyDev &B = bodies[b];
-    for (int k = 0; k < 6; ++k) B.wrench[k] = v[k];
-    if (!integrate) return;
-    const double g[3] = {gx, gy, gz};
-    for (int k = 0; k < 3; ++k) {
-        if (B.dof & (1 << k)) {
-            const double acc = v[k] / B.mass + g[k];
-            B.twist[k] += dt * acc;
-            B.acc[k] = acc;
-        } else {
-            B.acc[k] = 0.0;
-        }
-        B.pose[k] += dt * B.twist[k];
-    }
-    double q[4];
-    qadvance(B.pose + 3, B.twist + 3, dt, q);
-    for (int k = 0; k < 4; ++k) B.pose[3 + k] = q[k];
 }
 
 // Sorted fluid slots -> insertion order (absolute FP64 positions).
@@ -451,7 +547,7 @@ __global__ void k_export_rates(DevParams p, const uint32_t *__restrict__ pid, Ra
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const Sizes z = load_sizes(p);
     if (s >= z.N) return;
-    const uint32_t id = pid[s] & ~kExtendedBit;
+    const uint32_t id = pid_index(pid[s]);
     if (s < z.nF) {
         drho[id] = r.drho[s];
         const float4 a = r.du[s];
@@ -478,40 +574,62 @@ __global__ void k_export_rates(DevParams p, const uint32_t *__restrict__ pid, Ra
 // Host-side launchers used by the API translation unit.
 void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, StageArrays MID,
                  const uint32_t *nbr, const uint32_t *nnb, const uint32_t *integrate, float dt,
-                 RateOut out, int *err, cudaStream_t st)
+                 RateOut out, int *err, const float4 *xref, int *gate, cudaStream_t st,
+                 const uint32_t *sk_nbr, const uint32_t *sk_nnb)
 {
     const unsigned g = grid_for(p.capF);
+    if (mode == kStage1 && sk_nbr != nullptr) {
+        const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
+        k_pair<kStage1, true><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                     nullptr, nullptr);
+        return;
+    }
+    if (mode == kEval && sk_nbr != nullptr) {
+        const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
+        k_pair<kEval, true><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                   nullptr, nullptr);
+        return;
+    }
+    const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (mode == kStage1)
-        k_pair<kStage1><<<g, kBlock, 0, st>>>(p, S, Y, MID, nbr, nnb, integrate, dt, out, err);
+        k_pair<kStage1, false><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                      nullptr, nullptr);
     else if (mode == kStage2)
-        k_pair<kStage2><<<g, kBlock, 0, st>>>(p, S, Y, MID, nbr, nnb, integrate, dt, out, err);
+        k_pair<kStage2, false><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                      xref, gate);
     else
-        k_pair<kEval><<<g, kBlock, 0, st>>>(p, S, Y, MID, nbr, nnb, integrate, dt, out, err);
+        k_pair<kEval, false><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                    nullptr, nullptr);
 }
 
 void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
-                const double *mloc, const int *mbody, const BodyDev *bodies, const uint32_t *nbr,
-                const uint32_t *nnb, double tau, int accel, int n_fluid_total, float4 *mforce,
-                float4 *mtorque, cudaStream_t st)
+                const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
+                double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
+                unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
+                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err)
 {
-    k_bce<<<grid_for(p.capM), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, mbody, bodies, nbr, nnb,
-                                             tau, accel, n_fluid_total, mforce, mtorque);
+    const unsigned g = bce_blocks(p);
+    BodyStep bs{partial, ticket, bodies, dt, integrate, gate};
+    if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
+        const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
+        k_bce<0, true><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+                                             n_fluid_total, mforce, bs);
+        return;
+    }
+    const ListIO L{nbr, nnb, nullptr, nullptr, err};
+    if (accel == 0)
+        k_bce<0, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+                                              n_fluid_total, mforce, bs);
+    else if (accel == 1)
+        k_bce<1, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+                                              n_fluid_total, mforce, bs);
+    else
+        k_bce<2, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+                                              n_fluid_total, mforce, bs);
 }
 
-void launch_wrench_partial(const DevParams &p, const float4 *mforce, const float4 *mtorque,
-                           double *partial, cudaStream_t st)
-{
-    k_wrench_partial<<<grid_for(p.capM), kBlock, 0, st>>>(p.sizes + 1, p.n_bodies, mforce, mtorque,
-                                                          partial, p.abort);
-}
+unsigned bce_blocks(const DevParams &p) { return grid_for(p.capM); }
 
-void launch_body_update(const DevParams &p, const double *partial, BodyDev *bodies, double dt,
-                        int integrate, cudaStream_t st)
-{
-    k_body_update<<<1, 32 * p.n_bodies, 0, st>>>(p.n_bodies, p.capM > 0 ? (int)grid_for(p.capM) : 0,
-                                                 partial, bodies, p.gx, p.gy, p.gz, dt, integrate,
-                                                 p.abort);
-}
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
                    float *sig, float *rho, cudaStream_t st)

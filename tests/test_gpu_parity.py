@@ -350,3 +350,51 @@ def test_bin_points_exact(n, dims):
     assert np.array_equal(cells.cpu().numpy()[:n].astype(np.int64), c_ref)
     assert np.array_equal(perm.cpu().numpy()[:n].astype(np.int64), perm_ref)
     assert np.array_equal(start.cpu().numpy().astype(np.int64), start_ref)
+
+
+# --------------------------------------------------------------------------
+# Verlet skin: the exact 2h lists filtered from skin lists equal a fresh search
+
+@pytest.mark.parametrize("skin", [0.0, 0.1, 0.3])
+def test_skin_lists_stay_exact_over_many_steps(skin):
+    sc = _rand_state(scenes.settling_block(seed=61, n=12, box=0.18), 61, u_amp=0.6)
+    t = crm.from_scene(sc, skin=skin)
+    t.profile_reset()
+    n = 45
+    t.step(sc.dt, n)
+    t.eval_rates()                      # a rebuild at the current positions
+    prof = t.profile()
+    off_g, lst_g = t.neighbors()
+    xyz, *_ = t.particles()
+    st = oracle.State(sc)
+    xm, _, _ = st.markers_now()
+    x = np.concatenate([xyz, xm], axis=0)
+    off_o, lst_o = oracle.neighbors(x, sc.n_fluid, sc.params["h"], "cells")
+    h = sc.params["h"]
+    bad = 0
+    for i in range(x.shape[0]):
+        for j in set(lst_g[off_g[i]:off_g[i + 1]].tolist()) ^ set(lst_o[off_o[i]:off_o[i + 1]].tolist()):
+            if abs(np.linalg.norm(x[i] - x[j]) - 2 * h) >= BAND * h:
+                bad += 1
+    assert bad == 0
+    searches = prof["launches"]["neighbors"]
+    if skin > 0:
+        assert 2 <= searches < prof["rebuilds"], prof   # the skin saves searches but does some
+    else:
+        assert searches == prof["rebuilds"], prof
+
+
+@pytest.mark.parametrize("skin", [0.0, 0.1])
+def test_settling_block_skin_variants_agree(skin):
+    """Same trajectory with and without the skin (identical neighbour sets; only
+    the summation order of the pairs differs)."""
+    sc = scenes.settling_block(seed=62, n=14, box=0.2)
+    a = crm.from_scene(sc, skin=skin)
+    a.step(sc.dt, 60)
+    b = crm.from_scene(sc, skin=0.0)
+    b.step(sc.dt, 60)
+    xa, _, sa, _ = a.particles()
+    xb, _, sb, _ = b.particles()
+    # FP32 rounding only: offsets from cells of 2h (1 + skin) vs 2h, other pair order
+    assert np.max(np.abs(xa - xb)) < 1e-5 * sc.params["d0"]
+    assert np.sqrt(np.mean((sa - sb) ** 2)) < 1e-5 * sc.params["rho0"] * 9.81 * 0.14
