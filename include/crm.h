@@ -144,7 +144,9 @@ int crm_add_rigid_body(crm_terrain *t, int64_t n_markers, const double *marker_x
                        int32_t dof_mask, int32_t *body_id);
 
 /* Prescribe a body's pose and twist (the FSI exchange of Sec. 2.4): takes
- * effect at the next step.  Host arrays, copied (enqueued on the stream). */
+ * effect at the next step.  Host arrays, copied (enqueued on the stream).  The
+ * quaternion is normalised; CRM_EINVAL if its norm is outside (0.5, 2) or an
+ * entry is not finite. */
 int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7],
                         const double twist[6]);
 

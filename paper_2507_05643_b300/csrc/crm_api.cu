@@ -86,6 +86,7 @@ struct crm_terrain {
     // static
     double *mloc = nullptr;
     BodyDev *bodies = nullptr;
+    BodyFrame *mid_frames = nullptr;             // bodies at the step midpoint
     int *err = nullptr, *counts = nullptr, *win = nullptr, *abort_flag = nullptr;
     int *h_counts = nullptr;      // pinned mirror: counters + abort word
     // active domains: master store and candidates
@@ -440,6 +441,7 @@ int commit(crm_terrain *t)
     // static device state
     t->mloc = t->dalloc<double>(G_STATIC, 3 * nM);
     t->bodies = t->dalloc<BodyDev>(G_STATIC, t->hbodies.size());
+    t->mid_frames = t->dalloc<BodyFrame>(G_STATIC, kMaxBodies);
     t->err = t->dalloc<int>(G_STATIC, 1);
     t->counts = t->dalloc<int>(G_STATIC, C_WORDS);
     t->win = t->dalloc<int>(G_STATIC, 8);
@@ -769,7 +771,8 @@ void bce(crm_terrain *t, StageArrays S, double tau, int accel, double dt = 0.0, 
     const uint32_t *skl = filter ? t->sk_nbr : nullptr, *skn = filter ? t->sk_nnb : nullptr;
     launch(t, K_BCE, [&] { launch_bce(d, S, t->A[c].pos, t->pid[c], t->mloc, t->bodies, t->nbr,
                                       t->nnb, tau, accel, (int)t->nFtot, t->mforce, t->partial,
-                                      t->ticket, dt, integrate, gate, t->st, skl, skn, t->err); });
+                                      t->ticket, dt, integrate, gate, t->st, skl, skn, t->err,
+                                      t->mid_frames); });
 }
 
 void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, RateOut out,
@@ -790,7 +793,7 @@ void enqueue_stages(crm_terrain *t, double dt, bool filter)
 {
     const int c = t->cur;
     RateOut none{};
-    bce(t, t->A[c], 0.0, 0, 0.0, 0, filter);
+    bce(t, t->A[c], 0.0, 0, dt, 0, filter);   // also the bodies' midpoint frames
     pair(t, kStage1, t->A[c], t->A[c], (float)dt, none, filter);
     bce(t, t->MID, 0.5 * dt, 1, dt, 1);
     pair(t, kStage2, t->MID, t->A[c], (float)dt, none);
@@ -1189,8 +1192,11 @@ int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7], cons
     if (body < 0 || body >= (int)t->hbodies.size() || !pose || !twist)
         return t->fail(CRM_EINVAL, "crm_set_body_motion: bad body or null array");
     if (!finite_all(pose, 7) || !finite_all(twist, 6)) return t->fail(CRM_EINVAL, "non-finite motion");
+    const double qn = std::sqrt(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6]);
+    if (!(qn > 0.5 && qn < 2.0)) return t->fail(CRM_EINVAL, "crm_set_body_motion: quaternion not normalised");
     BodyDev &b = t->hbodies[body];
-    for (int k = 0; k < 7; ++k) b.pose[k] = pose[k];
+    for (int k = 0; k < 3; ++k) b.pose[k] = pose[k];
+    for (int k = 3; k < 7; ++k) b.pose[k] = pose[k] / qn;
     for (int k = 0; k < 6; ++k) b.twist[k] = twist[k];
     if (t->committed)
         CRM_CUDA(t, cudaMemcpyAsync(&t->bodies[body], &b, 13 * sizeof(double),

@@ -242,9 +242,13 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
         seg = 1;
         const uint32_t id = pid[i];
         const int mi = (int)pid_index(id) - n_fluid_total;
-        double x[3];
-        float u[3], a[3], arm[3];
-        marker_state(bodies, pid_body(id), mloc + 3 * (int64_t)mi, 0.0, x, u, a, arm);
+        const int body = pid_body(id);
+        const double *xl = mloc + 3 * (int64_t)mi;
+        double x[3] = {xl[0], xl[1], xl[2]};   // fixed marker: its world position
+        if (body >= 0) {
+            float u[3], a[3], arm[3];
+            marker_now(bodies[body], xl, x, u, a, arm);
+        }
         const double fx = floor((x[0] - p.dmin_x) / p.cell_d);
         const double fy = floor((x[1] - p.dmin_y) / p.cell_d);
         const double fz = floor((x[2] - p.dmin_z) / p.cell_d);

@@ -193,34 +193,72 @@ __device__ __forceinline__ void qadvance(const double q[4], const double w[3], d
     o[0] *= n; o[1] *= n; o[2] *= n; o[3] *= n;
 }
 
-// World position, rigid velocity and rigid acceleration of a marker, and its
-// arm from the body centre.  body < 0: fixed marker, xloc is its world position.
-__device__ __forceinline__ void marker_state(const BodyDev *bodies, int body, const double *xloc,
-                                             double tau, double x[3], float u[3], float a[3],
-                                             float arm[3])
+// A body's frame at one stage offset: centre and rotation in FP64 (computed
+// once per body and block, so the per-marker work is one FP64 matrix product),
+// twist and linear acceleration in FP32.
+struct BodyFrame {
+    double c[3];
+    double R[9];   // row-major rotation of the body-local marker positions
+    float v[3], w[3], acc[3];
+};
+
+__device__ __forceinline__ void body_frame(const BodyDev &b, double tau, BodyFrame &F)
 {
-    if (body < 0) {
-        x[0] = xloc[0]; x[1] = xloc[1]; x[2] = xloc[2];
-        u[0] = u[1] = u[2] = 0.0f;
-        a[0] = a[1] = a[2] = 0.0f;
-        arm[0] = arm[1] = arm[2] = 0.0f;
-        return;
-    }
-    const BodyDev &b = bodies[body];
-    double q[4], r[3];
+    double q[4];
     qadvance(b.pose + 3, b.twist + 3, tau, q);
-    qrot(q, xloc, r);
-    const double *w = b.twist + 3;
-    const double wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2],
-                          w[0] * r[1] - w[1] * r[0]};
-    const double wwr[3] = {w[1] * wr[2] - w[2] * wr[1], w[2] * wr[0] - w[0] * wr[2],
-                           w[0] * wr[1] - w[1] * wr[0]};
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    F.R[0] = 1.0 - 2.0 * (y * y + z * z); F.R[1] = 2.0 * (x * y - w * z); F.R[2] = 2.0 * (x * z + w * y);
+    F.R[3] = 2.0 * (x * y + w * z); F.R[4] = 1.0 - 2.0 * (x * x + z * z); F.R[5] = 2.0 * (y * z - w * x);
+    F.R[6] = 2.0 * (x * z - w * y); F.R[7] = 2.0 * (y * z + w * x); F.R[8] = 1.0 - 2.0 * (x * x + y * y);
     for (int k = 0; k < 3; ++k) {
-        x[k] = b.pose[k] + tau * b.twist[k] + r[k];
-        u[k] = (float)(b.twist[k] + wr[k]);
-        a[k] = (float)(b.acc[k] + wwr[k]);
-        arm[k] = (float)r[k];
+        F.c[k] = b.pose[k] + tau * b.twist[k];
+        F.v[k] = (float)b.twist[k];
+        F.w[k] = (float)b.twist[3 + k];
+        F.acc[k] = (float)b.acc[k];
     }
+}
+
+// Rigid velocity and acceleration of a body marker with arm r (FP32 is enough:
+// they enter the FP32 rates), and the FP64 world position c + r.
+__device__ __forceinline__ void marker_kin(const double c[3], const double r[3], const float v[3],
+                                           const float w[3], const float acc[3], double x[3],
+                                           float u[3], float a[3], float arm[3])
+{
+    const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
+    const float wr[3] = {w[1] * rf[2] - w[2] * rf[1], w[2] * rf[0] - w[0] * rf[2],
+                         w[0] * rf[1] - w[1] * rf[0]};
+    const float wwr[3] = {w[1] * wr[2] - w[2] * wr[1], w[2] * wr[0] - w[0] * wr[2],
+                          w[0] * wr[1] - w[1] * wr[0]};
+    for (int k = 0; k < 3; ++k) {
+        x[k] = c[k] + r[k];
+        u[k] = v[k] + wr[k];
+        a[k] = acc[k] + wwr[k];
+        arm[k] = rf[k];
+    }
+}
+
+// A body marker at stage offset tau from a precomputed frame.
+__device__ __forceinline__ void marker_at(const BodyFrame &F, const double *xloc, double x[3],
+                                          float u[3], float a[3], float arm[3])
+{
+    const double l0 = xloc[0], l1 = xloc[1], l2 = xloc[2];
+    const double r[3] = {fma(F.R[0], l0, fma(F.R[1], l1, F.R[2] * l2)),
+                         fma(F.R[3], l0, fma(F.R[4], l1, F.R[5] * l2)),
+                         fma(F.R[6], l0, fma(F.R[7], l1, F.R[8] * l2))};
+    marker_kin(F.c, r, F.v, F.w, F.acc, x, u, a, arm);
+}
+
+// A body marker at the current pose (stage offset 0): one quaternion rotation,
+// no trigonometry (the stored quaternion is kept normalised).
+__device__ __forceinline__ void marker_now(const BodyDev &b, const double *xloc, double x[3],
+                                           float u[3], float a[3], float arm[3])
+{
+    double r[3];
+    qrot(b.pose + 3, xloc, r);
+    const float v[3] = {(float)b.twist[0], (float)b.twist[1], (float)b.twist[2]};
+    const float w[3] = {(float)b.twist[3], (float)b.twist[4], (float)b.twist[5]};
+    const float acc[3] = {(float)b.acc[0], (float)b.acc[1], (float)b.acc[2]};
+    marker_kin(b.pose, r, v, w, acc, x, u, a, arm);
 }
 
 // ---------------------------------------------------------------------------
@@ -293,13 +331,14 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
 // the body wrench (FP64) and, in the last block, advances the bodies by dt
 // (integrate != 0); accel 2 writes every marker's force to mforce.  With
 // sk_nbr (stage 1 with a skin) the markers walk their skin lists and write
-// their exact lists to nbr / nnb.
+// their exact lists to nbr / nnb.  frames (kMaxBodies entries): a launch at
+// tau = 0 with dt > 0 writes the bodies' frames at dt / 2 there, and a launch
+// at tau != 0 takes its marker kinematics from them.
 void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
                 const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
                 unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
-                const uint32_t *sk_nbr = nullptr, const uint32_t *sk_nnb = nullptr,
-                int *err = nullptr);
+                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames);
 unsigned bce_blocks(const DevParams &p);
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
                    float *sig, float *rho, cudaStream_t st);

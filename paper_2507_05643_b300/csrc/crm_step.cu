@@ -104,8 +104,10 @@ struct ListIO {
     int *err;
 };
 
+constexpr int kPairBlock = 128;   // pair kernels: 7 blocks of 128 per SM (72 registers)
+
 template <int MODE, bool FILTER>
-__global__ void __launch_bounds__(kBlock, 4)
+__global__ void __launch_bounds__(kPairBlock, 7)
 k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
        const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err,
        const float4 *__restrict__ xref, int *__restrict__ gate)
@@ -144,11 +146,23 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
     const int nn = (int)io.in_n[i];
     const uint32_t *row = io.in + i;
     int cnt = 0;
+    // the next list entry is fetched one iteration ahead; on an exact list the
+    // neighbour's whole state is gathered at once (one load round per
+    // iteration), on a skin list only after the distance test
+    uint32_t e_nx = nn > 0 ? __ldg(row) : 0u;
     for (int k = 0; k < nn; ++k) {
-        const uint32_t e = __ldg(row + (size_t)k * p.ell);
+        const uint32_t e = e_nx;
+        if (k + 1 < nn) e_nx = __ldg(row + (size_t)(k + 1) * p.ell);
         const uint32_t j = e & kIndexMask;
         const float4 sh = lut[e >> kIndexBits];
         const float4 pj = __ldg(&S.pos[j]);
+        float4 vj, aj;
+        float2 bj;
+        if (!FILTER) {
+            vj = __ldg(&S.vel[j]);
+            aj = __ldg(&S.sA[j]);
+            bj = __ldg(&S.sB[j]);
+        }
         const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
         const float r2 = rx * rx + ry * ry + rz * rz;
         if (!(r2 < p.four_h2)) continue;
@@ -156,11 +170,11 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
             // stage 1 with a skin: the pairs closer than 2h now are the exact list
             if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
             ++cnt;
+            vj = __ldg(&S.vel[j]);
+            aj = __ldg(&S.sA[j]);
+            bj = __ldg(&S.sB[j]);
         }
         if (r2 == 0.0f) continue;
-        const float4 vj = __ldg(&S.vel[j]);
-        const float4 aj = __ldg(&S.sA[j]);
-        const float2 bj = __ldg(&S.sB[j]);
         const float rinv = rsqrtf(r2);
         const float q = r2 * rinv * p.inv_h;
         const float f = kernel_dw_over_r(q, rinv, p);
@@ -267,8 +281,9 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
 // (sigma_a + sigma_f) . grad_a W_af + AV, no gravity.
 // FILTER (stage 1 with a Verlet skin): the marker walks its skin list and keeps
 // the fluid particles closer than 2h as its exact list for the rest of the step.
-// A marker without fluid neighbours is not read by anyone (the relation is
-// symmetric), so its thread only takes part in the block reductions.
+// Each marker is served by kBceLanes lanes that stride over its list; a marker
+// without fluid neighbours is not read by anyone (the relation is symmetric),
+// so its lanes only take part in the warp and block reductions.
 struct BodyStep {
     double *partial;      // [block][body][6]
     unsigned *ticket;     // last-block counter (reset by the last block)
@@ -278,6 +293,16 @@ struct BodyStep {
     int *gate;            // skin bookkeeping (nullable): marker displacement bound
 };
 
+
+constexpr int kBceLanes = 4;   // lanes sharing one marker's neighbour list
+
+// Sum over the kBceLanes lanes of a marker's group (every lane of the warp calls it).
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = 1; o < kBceLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // ACCEL == 1 tail of k_bce: FP64 per-block partial wrench of every body, then
 // the last block sums the partials in a fixed order and advances the bodies.
@@ -382,7 +407,7 @@ template <int ACCEL, bool FILTER>
 __global__ void __launch_bounds__(kBlock)
 k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
       const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
-      const BodyDev *bodies, ListIO L, double tau, int n_fluid_total,
+      const BodyDev *bodies, BodyFrame *frames, ListIO L, double tau, int n_fluid_total,
       float4 *__restrict__ mforce, BodyStep bs)
 {
     static_assert(!(FILTER && ACCEL != 0), "filtering runs in stage 1 only (no accelerations)");
@@ -390,51 +415,81 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     __shared__ float4 lut[64];
     __shared__ double red[kBlock / 32][6];
     __shared__ unsigned s_bodies, s_last;
+    if (tau == 0.0 && frames != nullptr && bs.dt > 0.0 && blockIdx.x == 0
+        && (int)threadIdx.x < p.n_bodies) {
+        // the midpoint frames of the following stage-2 launch, once per step
+        body_frame(bodies[threadIdx.x], 0.5 * bs.dt, frames[threadIdx.x]);
+    }
     fill_shift_table(lut, p.cell);
     if (threadIdx.x == 0) s_bodies = 0u;
     __syncthreads();
     const Sizes z = load_sizes(p);
-    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
-    const int nn = s < z.N ? (int)L.in_n[s] : 0;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = t & (kBceLanes - 1);           // lane within the marker's group
+    const int s = z.nF + t / kBceLanes;
+    const bool valid = s < z.N;
+    const int nn = valid ? (int)L.in_n[s] : 0;
+    const bool work = nn > 0 || (ACCEL == 2 && valid);
     int body = -1;
     float f[3] = {0.f, 0.f, 0.f}, arm[3] = {0.f, 0.f, 0.f};
-    if (nn > 0 || (ACCEL == 2 && s < z.N)) {
-        const uint32_t id = pid[s];
-        body = pid_body(id);
-        float o[3], ub[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
-        const float4 home = home_pos[s];
-        if (body >= 0) {
-            const int mi = (int)pid_index(id) - n_fluid_total;
-            double x[3];
-            marker_state(bodies, body, mloc + 3 * (int64_t)mi, tau, x, ub, ab, arm);
-            int ix, iy, iz;
-            decode_cell(__float_as_uint(home.w), p, ix, iy, iz);
-            o[0] = (float)(x[0] - (p.dmin_x + ix * p.cell_d));
-            o[1] = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
-            o[2] = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
-        } else {
-            o[0] = home.x; o[1] = home.y; o[2] = home.z;   // fixed: the searched offset
+    if (__any_sync(0xffffffffu, work)) {
+        float o[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
+        float4 home = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (work) {
+            const uint32_t id = pid[s];
+            body = pid_body(id);
+            home = home_pos[s];
+            if (body >= 0) {
+                const int mi = (int)pid_index(id) - n_fluid_total;
+                double x[3];
+                if (tau == 0.0) marker_now(bodies[body], mloc + 3 * (int64_t)mi, x, ub, ab, arm);
+                else marker_at(frames[body], mloc + 3 * (int64_t)mi, x, ub, ab, arm);
+                int ix, iy, iz;
+                decode_cell(__float_as_uint(home.w), p, ix, iy, iz);
+                o[0] = (float)(x[0] - (p.dmin_x + ix * p.cell_d));
+                o[1] = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
+                o[2] = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
+            } else {
+                o[0] = home.x; o[1] = home.y; o[2] = home.z;   // fixed: the searched offset
+            }
         }
+        // pass 1: extrapolation sums, the list strided over the group's lanes
+        // (warp-uniform round count; the next entry is fetched one round ahead)
         const uint32_t *row = L.in + s;
+        const int rounds = __reduce_max_sync(0xffffffffu, (nn + kBceLanes - 1) / kBceLanes);
         float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
         float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
-        for (int k = 0; k < nn; ++k) {
-            const uint32_t e = __ldg(row + (size_t)k * p.ell);
-            const uint32_t j = e & kIndexMask;
-            const float4 sh = lut[e >> kIndexBits];
-            const float4 pj = __ldg(&S.pos[j]);
-            const float rx = o[0] - pj.x - sh.x, ry = o[1] - pj.y - sh.y, rz = o[2] - pj.z - sh.z;
-            const float r2 = rx * rx + ry * ry + rz * rz;
-            if (!(r2 < p.four_h2)) continue;
-            if (FILTER) {
-                if (cnt < p.maxnb) L.out[(size_t)cnt * p.ell + s] = e;
-                ++cnt;
+        uint32_t e_nx = q < nn ? __ldg(row + (size_t)q * p.ell) : 0u;
+        for (int r = 0; r < rounds; ++r) {
+            const int k = r * kBceLanes + q;
+            const uint32_t e = e_nx;
+            if (k + kBceLanes < nn) e_nx = __ldg(row + (size_t)(k + kBceLanes) * p.ell);
+            bool keep = false;
+            float W = 0.f;
+            float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), aj = vj;
+            float2 bj = make_float2(0.f, 0.f);
+            float rx = 0.f, ry = 0.f, rz = 0.f;
+            if (k < nn) {
+                const uint32_t j = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pj = __ldg(&S.pos[j]);
+                vj = __ldg(&S.vel[j]);
+                aj = __ldg(&S.sA[j]);
+                bj = __ldg(&S.sB[j]);
+                rx = o[0] - pj.x - sh.x; ry = o[1] - pj.y - sh.y; rz = o[2] - pj.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                keep = r2 < p.four_h2;
+                if (keep) W = kernel_w(sqrtf(r2) * p.inv_h, p);
             }
-            const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
-            const float4 vj = __ldg(&S.vel[j]);
-            const float4 aj = __ldg(&S.sA[j]);
-            const float2 bj = __ldg(&S.sB[j]);
+            if (FILTER) {
+                // the kept entries, in list order, become the exact list
+                const unsigned b = __ballot_sync(0xffffffffu, keep);
+                const unsigned g = (b >> ((threadIdx.x & 31) & ~(kBceLanes - 1))) & ((1u << kBceLanes) - 1u);
+                const int at = cnt + __popc(g & ((1u << q) - 1u));
+                if (keep && at < p.maxnb) L.out[(size_t)at * p.ell + s] = e;
+                cnt += __popc(g);
+            }
             w += W;
             sux = fmaf(vj.x, W, sux); suy = fmaf(vj.y, W, suy); suz = fmaf(vj.z, W, suz);
             ss[0] = fmaf(aj.x, W, ss[0]); ss[1] = fmaf(aj.y, W, ss[1]); ss[2] = fmaf(aj.z, W, ss[2]);
@@ -442,7 +497,13 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
             const float rw = vj.w * W;
             sr[0] = fmaf(rw, rx, sr[0]); sr[1] = fmaf(rw, ry, sr[1]); sr[2] = fmaf(rw, rz, sr[2]);
         }
-        if (FILTER) {
+        w = group_sum(w);
+        sux = group_sum(sux); suy = group_sum(suy); suz = group_sum(suz);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ss[k] = group_sum(ss[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sr[k] = group_sum(sr[k]);
+        if (FILTER && q == 0 && valid) {
             if (cnt > p.maxnb) atomicOr(L.err, ERR_CAPACITY);
             L.out_n[s] = (uint32_t)min(cnt, p.maxnb);
         }
@@ -460,25 +521,33 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
 #pragma unroll
             for (int k = 0; k < 6; ++k) sa[k] = 0.f;
         }
-        S.pos[s] = make_float4(o[0], o[1], o[2], home.w);
-        S.vel[s] = make_float4(ua[0], ua[1], ua[2], p.rho0);
-        S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
-        S.sB[s] = make_float2(sa[4], sa[5]);
-        if (ACCEL == 2 || (ACCEL == 1 && body >= 0)) {
-            const int na = nn;
-            const uint32_t *arow = L.in + s;
+        if (work && q == 0) {
+            S.pos[s] = make_float4(o[0], o[1], o[2], home.w);
+            S.vel[s] = make_float4(ua[0], ua[1], ua[2], p.rho0);
+            S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
+            S.sB[s] = make_float2(sa[4], sa[5]);
+        }
+        if constexpr (ACCEL != 0) {
+            // pass 2: marker accelerations (body markers for the wrench; every
+            // marker for the rate evaluation)
+            const int n2 = (ACCEL == 2 || body >= 0) ? nn : 0;
+            const int rounds2 = __reduce_max_sync(0xffffffffu, (n2 + kBceLanes - 1) / kBceLanes);
             float mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
-            for (int k = 0; k < na; ++k) {
-                const uint32_t e = __ldg(arow + (size_t)k * p.ell);
+            e_nx = q < n2 ? __ldg(row + (size_t)q * p.ell) : 0u;
+            for (int r = 0; r < rounds2; ++r) {
+                const int k = r * kBceLanes + q;
+                const uint32_t e = e_nx;
+                if (k + kBceLanes < n2) e_nx = __ldg(row + (size_t)(k + kBceLanes) * p.ell);
+                if (k >= n2) continue;
                 const uint32_t j = e & kIndexMask;
                 const float4 sh = lut[e >> kIndexBits];
                 const float4 pj = __ldg(&S.pos[j]);
-                const float rx = o[0] - pj.x - sh.x, ry = o[1] - pj.y - sh.y, rz = o[2] - pj.z - sh.z;
-                const float r2 = rx * rx + ry * ry + rz * rz;
-                if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
                 const float4 vj = __ldg(&S.vel[j]);
                 const float4 aj = __ldg(&S.sA[j]);
                 const float2 bj = __ldg(&S.sB[j]);
+                const float rx = o[0] - pj.x - sh.x, ry = o[1] - pj.y - sh.y, rz = o[2] - pj.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
                 const float rinv = rsqrtf(r2);
                 const float fk = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
                 const float gx = fk * rx, gy = fk * ry, gz = fk * rz;
@@ -498,18 +567,22 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
                     }
                 }
             }
+            if (rounds2 > 0) {
+                mx = group_sum(mx); my = group_sum(my); mz = group_sum(mz);
+                avx = group_sum(avx); avy = group_sum(avy); avz = group_sum(avz);
+            }
             const float ir = 1.0f / p.rho0;
             f[0] = p.m * (mx * ir + avx);
             f[1] = p.m * (my * ir + avy);
             f[2] = p.m * (mz * ir + avz);
         }
-    } else if (FILTER && s < z.N) {
+    } else if (FILTER && valid && q == 0) {
         L.out_n[s] = 0u;
     }
     if constexpr (ACCEL == 2) {
-        if (s < z.N) mforce[s - z.nF] = make_float4(f[0], f[1], f[2], __int_as_float(body));
+        if (valid && q == 0) mforce[s - z.nF] = make_float4(f[0], f[1], f[2], __int_as_float(body));
     } else if constexpr (ACCEL == 1) {
-        body_wrench_tail(p, f, arm, body, nn > 0 && body >= 0, bs, s_bodies, s_last, red);
+        body_wrench_tail(p, f, arm, body, q == 0 && nn > 0 && body >= 0, bs, s_bodies, s_last, red);
     }
 }
 
@@ -577,28 +650,28 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
                  RateOut out, int *err, const float4 *xref, int *gate, cudaStream_t st,
                  const uint32_t *sk_nbr, const uint32_t *sk_nnb)
 {
-    const unsigned g = grid_for(p.capF);
+    const unsigned g = grid_for(p.capF, kPairBlock);
     if (mode == kStage1 && sk_nbr != nullptr) {
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_pair<kStage1, true><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+        k_pair<kStage1, true><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
                                                      nullptr, nullptr);
         return;
     }
     if (mode == kEval && sk_nbr != nullptr) {
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_pair<kEval, true><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+        k_pair<kEval, true><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
                                                    nullptr, nullptr);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (mode == kStage1)
-        k_pair<kStage1, false><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+        k_pair<kStage1, false><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
                                                       nullptr, nullptr);
     else if (mode == kStage2)
-        k_pair<kStage2, false><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+        k_pair<kStage2, false><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
                                                       xref, gate);
     else
-        k_pair<kEval, false><<<g, kBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+        k_pair<kEval, false><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
                                                     nullptr, nullptr);
 }
 
@@ -606,29 +679,29 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
                 const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
                 unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
-                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err)
+                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames)
 {
     const unsigned g = bce_blocks(p);
     BodyStep bs{partial, ticket, bodies, dt, integrate, gate};
     if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_bce<0, true><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+        k_bce<0, true><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
                                              n_fluid_total, mforce, bs);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (accel == 0)
-        k_bce<0, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+        k_bce<0, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
                                               n_fluid_total, mforce, bs);
     else if (accel == 1)
-        k_bce<1, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+        k_bce<1, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
                                               n_fluid_total, mforce, bs);
     else
-        k_bce<2, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, L, tau,
+        k_bce<2, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
                                               n_fluid_total, mforce, bs);
 }
 
-unsigned bce_blocks(const DevParams &p) { return grid_for(p.capM); }
+unsigned bce_blocks(const DevParams &p) { return grid_for((int64_t)p.capM * kBceLanes); }
 
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
