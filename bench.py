@@ -289,7 +289,7 @@ def run_crm(args):
         alg_bytes = {   # algorithmic DRAM bytes per launch (state read / written once)
             "keys": 40 * n_all, "scan": 8 * (2 * 60000 + 1), "scatter": 12 * n_all,
             "reorder": 2 * 60 * n_all, "neighbors": 20 * n_all + 4 * all_pairs * 1.33,
-            "skin": 60 * n_all,
+            "skin": 60 * n_all, "compact": 12 * sc.n_markers,
             "bce": 56 * 2 * sc.n_markers + 4 * (all_pairs - fluid_pairs),
             "pair_stage1": 56 * 2 * sc.n_fluid + 56 * sc.n_markers + 4 * fluid_pairs,
             "pair_stage2": 56 * 3 * sc.n_fluid + 56 * sc.n_markers + 4 * fluid_pairs,

@@ -219,11 +219,11 @@ int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
 
 /* Per-kernel launch counts and CUDA-event timings of one handle (for
  * measurement).  Kernel ids 0..CRM_NUM_KERNELS-1, names from crm_kernel_name:
- * keys, scan, scatter, reorder, neighbors (cell search), bce (with the body
- * wrench and update), pair_stage1, pair_stage2 (with a skin, the first-stage
- * kernels after a rebuild also filter the exact lists), skin (search decision
- * and copy-back), export. */
-#define CRM_NUM_KERNELS 10
+ * keys, scan, scatter, reorder, neighbors (cell search), compact (markers with
+ * fluid in reach), bce (with the body wrench and update), pair_stage1,
+ * pair_stage2 (with a skin, the first-stage kernels after a rebuild also filter
+ * the exact lists), skin (search decision and copy-back), export. */
+#define CRM_NUM_KERNELS 11
 typedef struct crm_profile {
     int64_t launches[CRM_NUM_KERNELS]; /* kernels enqueued since the last reset */
     double ms[CRM_NUM_KERNELS];        /* summed event-timed durations (timing on) */

@@ -93,7 +93,7 @@ _sig("crm_load_state", C.c_int, [_T, _vp, C.c_size_t])
 _sig("crm_bin_scratch_bytes", C.c_size_t, [_i64, _i64])
 _sig("crm_bin_points", C.c_int, [_vp, _i64, C.c_float, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp])
 
-NUM_KERNELS = 10
+NUM_KERNELS = 11
 
 
 class Profile(C.Structure):

@@ -87,6 +87,8 @@ struct crm_terrain {
     double *mloc = nullptr;
     BodyDev *bodies = nullptr;
     BodyFrame *mid_frames = nullptr;             // bodies at the step midpoint
+    uint32_t *act = nullptr, *act_bcount = nullptr;   // markers with fluid in reach
+    int *n_act = nullptr;
     int *err = nullptr, *counts = nullptr, *win = nullptr, *abort_flag = nullptr;
     int *h_counts = nullptr;      // pinned mirror: counters + abort word
     // active domains: master store and candidates
@@ -305,6 +307,9 @@ int alloc_working(crm_terrain *t)
     t->partial = t->dalloc<double>(G_WORK, (size_t)bce_blocks(d)
                                                * std::max<size_t>(t->hbodies.size(), 1) * 6);
     t->ticket = t->dalloc<unsigned>(G_WORK, 1);
+    t->act = t->dalloc<uint32_t>(G_WORK, t->capM);
+    t->act_bcount = t->dalloc<uint32_t>(G_WORK, compact_blocks(d));
+    t->n_act = t->dalloc<int>(G_WORK, 1);
     if (t->skin_on) {
         t->sk_nbr = t->dalloc<uint32_t>(G_WORK, (size_t)d.skin_cap * d.ell);
         t->sk_nnb = t->dalloc<uint32_t>(G_WORK, N);
@@ -320,6 +325,7 @@ int alloc_working(crm_terrain *t)
     CRM_CUDA(t, cudaMemsetAsync(t->nnb, 0, N * sizeof(uint32_t), t->st));
     CRM_CUDA(t, cudaMemsetAsync(t->mforce, 0, std::max<int64_t>(t->capM, 1) * sizeof(float4), t->st));
     CRM_CUDA(t, cudaMemsetAsync(t->ticket, 0, sizeof(unsigned), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->n_act, 0, sizeof(int), t->st));
     t->cur = 0;
     t->lists_valid = false;
     return CRM_OK;
@@ -644,19 +650,19 @@ int commit(crm_terrain *t)
     return CRM_OK;
 }
 
-enum KernelId { K_KEYS, K_SCAN, K_SCATTER, K_REORDER, K_NEIGHBORS, K_BCE, K_PAIR1, K_PAIR2,
-                K_SKIN, K_EXPORT };
+enum KernelId { K_KEYS, K_SCAN, K_SCATTER, K_REORDER, K_NEIGHBORS, K_COMPACT, K_BCE, K_PAIR1,
+                K_PAIR2, K_SKIN, K_EXPORT };
 const char *const kKernelNames[CRM_NUM_KERNELS] = {
-    "keys", "scan", "scatter", "reorder", "neighbors", "bce", "pair_stage1", "pair_stage2",
-    "skin", "export"};
+    "keys", "scan", "scatter", "reorder", "neighbors", "compact", "bce", "pair_stage1",
+    "pair_stage2", "skin", "export"};
 
 // Enqueue one kernel through `launch`, counting it and, when timing is on,
 // bracketing it with two events on the handle's stream.  The active-domain
 // kernels are counted under "keys" (flags, compaction, gather), "scan" and
 // "export" (write-back to the master store).
-template <class F> void launch(crm_terrain *t, int k, F &&f)
+template <class F> void launch(crm_terrain *t, int k, F &&f, int kernels = 1)
 {
-    t->prof.launches[k] += 1;
+    t->prof.launches[k] += kernels;
     if (!t->timing) {
         f();
         return;
@@ -737,9 +743,15 @@ void enqueue_search(crm_terrain *t)
                                                       t->st); });
         launch(t, K_SKIN, [&] { launch_copyback(d, t->A[n], t->pid[n], t->A[c], t->pid[c], t->xref,
                                                 t->bodies, t->st); });
+        if (d.capM > 0)
+            launch(t, K_COMPACT, [&] { launch_compact_markers(d, t->sk_nnb, t->nnb, t->act_bcount,
+                                                              t->act, t->n_act, t->st); }, 2);
     } else {
         launch(t, K_NEIGHBORS, [&] { launch_neighbors(d, t->A[n].pos, t->start, t->nbr, t->nnb,
                                                       d.maxnb, d.four_h2, t->err, t->st); });
+        if (d.capM > 0)
+            launch(t, K_COMPACT, [&] { launch_compact_markers(d, t->nnb, nullptr, t->act_bcount,
+                                                              t->act, t->n_act, t->st); }, 2);
     }
 }
 
@@ -772,7 +784,7 @@ void bce(crm_terrain *t, StageArrays S, double tau, int accel, double dt = 0.0, 
     launch(t, K_BCE, [&] { launch_bce(d, S, t->A[c].pos, t->pid[c], t->mloc, t->bodies, t->nbr,
                                       t->nnb, tau, accel, (int)t->nFtot, t->mforce, t->partial,
                                       t->ticket, dt, integrate, gate, t->st, skl, skn, t->err,
-                                      t->mid_frames); });
+                                      t->mid_frames, accel == 2 ? nullptr : t->act, t->n_act); });
 }
 
 void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, RateOut out,
@@ -912,6 +924,7 @@ int graph_step(crm_terrain *t, double dt)
             t->prof.launches[K_SCATTER] += 1;
             t->prof.launches[K_REORDER] += 1;
             t->prof.launches[K_NEIGHBORS] += 1;
+            if (d.capM > 0) t->prof.launches[K_COMPACT] += 2;
             t->cur = 1 - t->cur;
         }
         t->prof.rebuilds += 1;
@@ -1468,6 +1481,7 @@ int crm_profile_read(crm_terrain *t, crm_profile *out)
         if (!t->timing) {
             t->prof.launches[K_KEYS] = t->prof.launches[K_SCAN] = t->prof.launches[K_SCATTER] = 0;
             t->prof.launches[K_REORDER] = t->prof.launches[K_NEIGHBORS] = 0;
+            t->prof.launches[K_COMPACT] = 0;
         }
         t->searched += n;
         if (!t->timing) {
@@ -1477,6 +1491,7 @@ int crm_profile_read(crm_terrain *t, crm_profile *out)
             t->prof.launches[K_REORDER] += t->searched;
             t->prof.launches[K_NEIGHBORS] += t->searched;
             t->prof.launches[K_SKIN] += t->searched;
+            if (t->dp.capM > 0) t->prof.launches[K_COMPACT] += 2 * t->searched;
         }
     }
     for (auto &r : t->pending) {

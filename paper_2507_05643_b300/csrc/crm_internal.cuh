@@ -338,8 +338,15 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
                 const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
                 unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
-                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames);
+                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames,
+                const uint32_t *act, const int *n_act);
 unsigned bce_blocks(const DevParams &p);
+// Marker slots whose list (nnb: the skin lists with a skin) is non-empty, in
+// slot order, into act[0 .. *n_act); with nnb_exact the exact counts of the
+// others are zeroed.  bcount: compact_blocks(p) words.  Gated like the search.
+unsigned compact_blocks(const DevParams &p);
+void launch_compact_markers(const DevParams &p, const uint32_t *nnb, uint32_t *nnb_exact,
+                            uint32_t *bcount, uint32_t *act, int *n_act, cudaStream_t st);
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
                    float *sig, float *rho, cudaStream_t st);
 void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, StageArrays S,

@@ -179,7 +179,7 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
         const float q = r2 * rinv * p.inv_h;
         const float f = kernel_dw_over_r(q, rinv, p);
         const float gx = f * rx, gy = f * ry, gz = f * rz;          // grad_i W_ij
-        const float Vj = p.m / vj.w;
+        const float Vj = __fdividef(p.m, vj.w);   // MUFU reciprocal: ~2 ulp
         const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;   // u_ji
         // continuity (F2)
         cont = fmaf(Vj, ux * gx + uy * gy + uz * gz, cont);
@@ -198,7 +198,7 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
         if (p.av_mode != CRM_AV_NONE) {
             const float vr = -(ux * rx + uy * ry + uz * rz);
             if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-                const float fac = 2.0f * p.av_c * vr / ((vi.w + vj.w) * (r2 + p.xi2));
+                const float fac = __fdividef(2.0f * p.av_c * vr, (vi.w + vj.w) * (r2 + p.xi2));
                 avx = fmaf(fac, gx, avx);
                 avy = fmaf(fac, gy, avy);
                 avz = fmaf(fac, gz, avz);
@@ -407,8 +407,9 @@ template <int ACCEL, bool FILTER>
 __global__ void __launch_bounds__(kBlock)
 k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
       const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
-      const BodyDev *bodies, BodyFrame *frames, ListIO L, double tau, int n_fluid_total,
-      float4 *__restrict__ mforce, BodyStep bs)
+      const BodyDev *bodies, BodyFrame *frames, ListIO L, const uint32_t *__restrict__ act,
+      const int *__restrict__ n_act, double tau, int n_fluid_total, float4 *__restrict__ mforce,
+      BodyStep bs)
 {
     static_assert(!(FILTER && ACCEL != 0), "filtering runs in stage 1 only (no accelerations)");
     if (*p.abort) return;
@@ -426,8 +427,16 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     const Sizes z = load_sizes(p);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int q = t & (kBceLanes - 1);           // lane within the marker's group
-    const int s = z.nF + t / kBceLanes;
-    const bool valid = s < z.N;
+    int s;
+    bool valid;
+    if (act != nullptr) {                        // the markers with fluid in reach
+        const int mk = t / kBceLanes;
+        valid = mk < __ldg(n_act);
+        s = valid ? (int)__ldg(&act[mk]) : z.N;
+    } else {                                     // every marker slot
+        s = z.nF + t / kBceLanes;
+        valid = s < z.N;
+    }
     const int nn = valid ? (int)L.in_n[s] : 0;
     const bool work = nn > 0 || (ACCEL == 2 && valid);
     int body = -1;
@@ -551,7 +560,7 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
                 const float rinv = rsqrtf(r2);
                 const float fk = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
                 const float gx = fk * rx, gy = fk * ry, gz = fk * rz;
-                const float Vj = p.m / vj.w;
+                const float Vj = __fdividef(p.m, vj.w);   // MUFU reciprocal: ~2 ulp
                 const float sxx = sa[0] + aj.x, syy = sa[1] + aj.y, szz = sa[2] + aj.z;
                 const float sxy = sa[3] + aj.w, sxz = sa[4] + bj.x, syz = sa[5] + bj.y;
                 mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, mx);
@@ -560,7 +569,7 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
                 if (p.av_mode != CRM_AV_NONE) {
                     const float vr = (ua[0] - vj.x) * rx + (ua[1] - vj.y) * ry + (ua[2] - vj.z) * rz;
                     if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-                        const float fac = 2.0f * p.av_c * vr / ((p.rho0 + vj.w) * (r2 + p.xi2));
+                        const float fac = __fdividef(2.0f * p.av_c * vr, (p.rho0 + vj.w) * (r2 + p.xi2));
                         avx = fmaf(fac, gx, avx);
                         avy = fmaf(fac, gy, avy);
                         avz = fmaf(fac, gz, avz);
@@ -584,6 +593,51 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     } else if constexpr (ACCEL == 1) {
         body_wrench_tail(p, f, arm, body, q == 0 && nn > 0 && body >= 0, bs, s_bodies, s_last, red);
     }
+}
+
+// Markers with a non-empty list, compacted in slot order at each list rebuild
+// (most wall markers have no fluid in reach; the BCE kernels then run over the
+// active ones only).  Two passes without inter-block waits: per-block counts,
+// then each block sums the counts before it and places its markers by ballot.
+constexpr int kCompactBlock = 256;
+
+__global__ void __launch_bounds__(kCompactBlock)
+k_marker_counts(DevParams p, const uint32_t *__restrict__ nnb, uint32_t *__restrict__ bcount)
+{
+    if (*p.abort || gated_off(p)) return;
+    const Sizes z = load_sizes(p);
+    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = __syncthreads_count(s < z.N && nnb[s] > 0u);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = (uint32_t)c;
+}
+
+__global__ void __launch_bounds__(kCompactBlock)
+k_marker_compact(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *__restrict__ bcount,
+                 uint32_t *__restrict__ act, int *__restrict__ n_act, uint32_t *__restrict__ nnb_exact)
+{
+    if (*p.abort || gated_off(p)) return;
+    __shared__ uint32_t s_sum[kCompactBlock / 32], s_cnt[kCompactBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t acc = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) acc += bcount[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const Sizes z = load_sizes(p);
+    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = s < z.N;
+    const bool a = valid && nnb[s] > 0u;
+    const unsigned bits = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) {
+        s_sum[warp] = acc;
+        s_cnt[warp] = (uint32_t)__popc(bits);
+    }
+    __syncthreads();
+    uint32_t off = 0;
+    for (int w = 0; w < kCompactBlock / 32; ++w) off += s_sum[w] + (w < warp ? s_cnt[w] : 0u);
+    if (a) act[off + __popc(bits & ((1u << lane) - 1u))] = (uint32_t)s;
+    else if (valid && nnb_exact != nullptr) nnb_exact[s] = 0u;   // no skin neighbours: none within 2h
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kCompactBlock - 1)
+        *n_act = (int)(off + __popc(bits & ((1u << lane) - 1u)) + (a ? 1u : 0u));
 }
 
 // Sorted fluid slots -> insertion order (absolute FP64 positions).
@@ -679,29 +733,40 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
                 const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
                 unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
-                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames)
+                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames,
+                const uint32_t *act, const int *n_act)
 {
     const unsigned g = bce_blocks(p);
     BodyStep bs{partial, ticket, bodies, dt, integrate, gate};
     if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_bce<0, true><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
+        k_bce<0, true><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
                                              n_fluid_total, mforce, bs);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (accel == 0)
-        k_bce<0, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
+        k_bce<0, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
                                               n_fluid_total, mforce, bs);
     else if (accel == 1)
-        k_bce<1, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
+        k_bce<1, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
                                               n_fluid_total, mforce, bs);
     else
-        k_bce<2, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, tau,
+        k_bce<2, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
                                               n_fluid_total, mforce, bs);
 }
 
 unsigned bce_blocks(const DevParams &p) { return grid_for((int64_t)p.capM * kBceLanes); }
+
+unsigned compact_blocks(const DevParams &p) { return grid_for(p.capM, kCompactBlock); }
+
+void launch_compact_markers(const DevParams &p, const uint32_t *nnb, uint32_t *nnb_exact,
+                            uint32_t *bcount, uint32_t *act, int *n_act, cudaStream_t st)
+{
+    const unsigned g = compact_blocks(p);
+    k_marker_counts<<<g, kCompactBlock, 0, st>>>(p, nnb, bcount);
+    k_marker_compact<<<g, kCompactBlock, 0, st>>>(p, nnb, bcount, act, n_act, nnb_exact);
+}
 
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
