@@ -166,21 +166,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+KERNEL_SOURCE = {"pair_stage1": "crm_step.cu", "pair_stage2": "crm_step.cu", "bce": "crm_bce.cu",
+                 "compact": "crm_bce.cu", "skin": "crm_bin.cu", "keys": "crm_bin.cu",
+                 "scan": "crm_bin.cu", "scatter": "crm_bin.cu", "reorder": "crm_bin.cu",
+                 "neighbors": "crm_bin.cu", "export": "crm_step.cu"}
+
+
 def _traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as f:
-            rec = json.load(f)
-    except (OSError, ValueError):
-        return None
-    src = os.path.join(ROOT, "paper_2507_05643_b300", "csrc", "crm_step.cu")
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.txt: kernel, bytes per launch, sha256[:16] of the source
+    file the kernel lives in when it was captured), if it was taken on the
+    current source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2507_05643_b300", "csrc", KERNEL_SOURCE.get(kernel, "crm_step.cu"))
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    e = rec.get(kernel)
-    if not e or e.get("source_sha") != h:
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
         return None
-    return e.get("bytes_per_launch")
+    for ln in lines:
+        f = ln.split()
+        if len(f) >= 3 and not ln.startswith("#") and f[0] == kernel and f[2] == h:
+            return float(f[1])
+    return None
 
 
 def _workload(args):

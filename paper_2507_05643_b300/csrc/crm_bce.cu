@@ -1,0 +1,426 @@
+// crm_bce.cu -- BCE boundary markers (Sec. 2.4): marker state extrapolated from
+// the fluid, marker accelerations, the FP64 body wrench and the body update,
+// and the compaction of the markers that have fluid in reach.
+#include "crm_internal.cuh"
+
+namespace crm {
+
+// BCE marker state (Sec. 2.4) at stage offset tau, written into the marker
+// slots of S.  The home cell of each slot is read from `home_pos` -- the main
+// arrays, whose cell ids the last rebuild set -- so that the marker offset is
+// relative to the cell its neighbour codes were built against.
+//   Velocity (Adami): u_a = 2 u_body - sum_f u_f W / sum_f W.
+//   Stress: sigma_a = [sum_f sigma_f W - ((g - a_body) . sum_f rho_f (x_a - x_f) W) I]
+//   / sum_f W (the pressure extrapolation of the cited scheme in stress form);
+//   without fluid in reach u_a = u_body and sigma_a = 0.
+// ACCEL: 0 = state only; 1 = also the accelerations of body markers, reduced
+// per block into FP64 force / torque partials, after which the last block to
+// finish sums the partials in a fixed order and advances the bodies (the wrench
+// and body update of Sec. 2.4); 2 = the accelerations of every marker, written
+// to mforce (rate evaluation).  Acceleration: a_a = (1/rho0) sum_f V_f
+// (sigma_a + sigma_f) . grad_a W_af + AV, no gravity.
+// FILTER (stage 1 with a Verlet skin): the marker walks its skin list and keeps
+// the fluid particles closer than 2h as its exact list for the rest of the step.
+// Each marker is served by kBceLanes lanes that stride over its list; a marker
+// without fluid neighbours is not read by anyone (the relation is symmetric),
+// so its lanes only take part in the warp and block reductions.
+struct BodyStep {
+    double *partial;      // [block][body][6]
+    unsigned *ticket;     // last-block counter (reset by the last block)
+    BodyDev *bodies;      // advanced by the last block
+    double dt;
+    int integrate;
+    int *gate;            // skin bookkeeping (nullable): marker displacement bound
+};
+
+
+constexpr int kBceLanes = 4;   // lanes sharing one marker's neighbour list
+
+// Sum over the kBceLanes lanes of a marker's group (every lane of the warp calls it).
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = 1; o < kBceLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ACCEL == 1 tail of k_bce: FP64 per-block partial wrench of every body, then
+// the last block sums the partials in a fixed order and advances the bodies.
+__device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float f[3],
+                                                 const float arm[3], int body, bool mine,
+                                                 const BodyStep &bs, unsigned &s_bodies,
+                                                 unsigned &s_last, double (*red)[6])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (mine) atomicOr(&s_bodies, 1u << body);
+    __syncthreads();
+    const int nb = p.n_bodies;
+    for (int b = 0; b < nb; ++b) {
+        const bool present = (s_bodies >> b) & 1u;
+        if (present) {
+            double v[6] = {0, 0, 0, 0, 0, 0};
+            if (mine && body == b) {
+                v[0] = f[0]; v[1] = f[1]; v[2] = f[2];
+                v[3] = (double)arm[1] * f[2] - (double)arm[2] * f[1];
+                v[4] = (double)arm[2] * f[0] - (double)arm[0] * f[2];
+                v[5] = (double)arm[0] * f[1] - (double)arm[1] * f[0];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double a = 0.0;
+            if (present)
+                for (int w = 0; w < kBlock / 32; ++w) a += red[w][threadIdx.x];
+            bs.partial[((size_t)blockIdx.x * nb + b) * 6 + threadIdx.x] = a;
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    if (threadIdx.x == 0) s_last = atomicAdd(bs.ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int b = 0; b < nb; ++b) {
+        // L2 loads (the partials were published before the ticket): issued
+        // together, not one round trip each
+        double v[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+        for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] += __ldcg(&bs.partial[((size_t)q * nb + b) * 6 + k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double W[6] = {0, 0, 0, 0, 0, 0};
+            for (int w = 0; w < kBlock / 32; ++w)
+                for (int k = 0; k < 6; ++k) W[k] += red[w][k];
+            BodyDev &B = bs.bodies[b];
+            for (int k = 0; k < 6; ++k) B.wrench[k] = W[k];
+            if (bs.integrate) {
+                // symplectic Euler on the free linear DOFs: v += dt (F/m + g), x += dt v;
+                // prescribed DOFs move with their velocity; the orientation turns by dt w
+                for (int k = 0; k < 3; ++k) {
+                    if (B.dof & (1 << k)) {
+                        const double a = W[k] / B.mass + p.g64[k];
+                        B.twist[k] += bs.dt * a;
+                        B.acc[k] = a;
+                    } else {
+                        B.acc[k] = 0.0;
+                    }
+                    B.pose[k] += bs.dt * B.twist[k];
+                }
+                double q[4];
+                qadvance(B.pose + 3, B.twist + 3, bs.dt, q);
+                for (int k = 0; k < 4; ++k) B.pose[3 + k] = q[k];
+                if (bs.gate != nullptr) {
+                    // every marker of the body has moved at most |dc| + 2 sin(theta/2) rmax
+                    // since the last cell search (theta: rotation since then)
+                    double dc2 = 0.0, w = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double d = B.pose[k] - B.ref_pose[k];
+                        dc2 += d * d;
+                    }
+                    for (int k = 0; k < 4; ++k) w += B.pose[3 + k] * B.ref_pose[3 + k];
+                    const double sh = sqrt(fmax(0.0, 1.0 - w * w));
+                    const double d = sqrt(dc2) + 2.0 * sh * B.rmax;
+                    atomicMax(bs.gate + GATE_DISP, __float_as_int((float)(d * d) * 1.0001f));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *bs.ticket = 0u;
+}
+
+template <int ACCEL, bool FILTER>
+__global__ void __launch_bounds__(kBlock)
+k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
+      const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
+      const BodyDev *bodies, BodyFrame *frames, ListIO L, const uint32_t *__restrict__ act,
+      const int *__restrict__ n_act, double tau, int n_fluid_total, float4 *__restrict__ mforce,
+      BodyStep bs)
+{
+    static_assert(!(FILTER && ACCEL != 0), "filtering runs in stage 1 only (no accelerations)");
+    if (*p.abort) return;
+    __shared__ float4 lut[64];
+    __shared__ double red[kBlock / 32][6];
+    __shared__ unsigned s_bodies, s_last;
+    if (tau == 0.0 && frames != nullptr && bs.dt > 0.0 && blockIdx.x == 0
+        && (int)threadIdx.x < p.n_bodies) {
+        // the midpoint frames of the following stage-2 launch, once per step
+        body_frame(bodies[threadIdx.x], 0.5 * bs.dt, frames[threadIdx.x]);
+    }
+    fill_shift_table(lut, p.cell);
+    if (threadIdx.x == 0) s_bodies = 0u;
+    __syncthreads();
+    const Sizes z = load_sizes(p);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = t & (kBceLanes - 1);           // lane within the marker's group
+    int s;
+    bool valid;
+    if (act != nullptr) {                        // the markers with fluid in reach
+        const int mk = t / kBceLanes;
+        valid = mk < __ldg(n_act);
+        s = valid ? (int)__ldg(&act[mk]) : z.N;
+    } else {                                     // every marker slot
+        s = z.nF + t / kBceLanes;
+        valid = s < z.N;
+    }
+    const int nn = valid ? (int)L.in_n[s] : 0;
+    const bool work = nn > 0 || (ACCEL == 2 && valid);
+    int body = -1;
+    float f[3] = {0.f, 0.f, 0.f}, arm[3] = {0.f, 0.f, 0.f};
+    if (__any_sync(0xffffffffu, work)) {
+        float o[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
+        float4 home = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (work) {
+            const uint32_t id = pid[s];
+            body = pid_body(id);
+            home = home_pos[s];
+            if (body >= 0) {
+                const int mi = (int)pid_index(id) - n_fluid_total;
+                double x[3];
+                if (tau == 0.0) marker_now(bodies[body], mloc + 3 * (int64_t)mi, x, ub, ab, arm);
+                else marker_at(frames[body], mloc + 3 * (int64_t)mi, x, ub, ab, arm);
+                int ix, iy, iz;
+                decode_cell(__float_as_uint(home.w), p, ix, iy, iz);
+                o[0] = (float)(x[0] - (p.dmin_x + ix * p.cell_d));
+                o[1] = (float)(x[1] - (p.dmin_y + iy * p.cell_d));
+                o[2] = (float)(x[2] - (p.dmin_z + iz * p.cell_d));
+            } else {
+                o[0] = home.x; o[1] = home.y; o[2] = home.z;   // fixed: the searched offset
+            }
+        }
+        // pass 1: extrapolation sums, the list strided over the group's lanes
+        // (warp-uniform round count; the next entry is fetched one round ahead)
+        const uint32_t *row = L.in + s;
+        const int rounds = __reduce_max_sync(0xffffffffu, (nn + kBceLanes - 1) / kBceLanes);
+        float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
+        float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int cnt = 0;
+        uint32_t e_nx = q < nn ? __ldg(row + (size_t)q * p.ell) : 0u;
+        for (int r = 0; r < rounds; ++r) {
+            const int k = r * kBceLanes + q;
+            const uint32_t e = e_nx;
+            if (k + kBceLanes < nn) e_nx = __ldg(row + (size_t)(k + kBceLanes) * p.ell);
+            bool keep = false;
+            float W = 0.f;
+            float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), aj = vj;
+            float2 bj = make_float2(0.f, 0.f);
+            float rx = 0.f, ry = 0.f, rz = 0.f;
+            if (k < nn) {
+                const uint32_t j = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pj = __ldg(&S.pos[j]);
+                vj = __ldg(&S.vel[j]);
+                aj = __ldg(&S.sA[j]);
+                bj = __ldg(&S.sB[j]);
+                rx = o[0] - pj.x - sh.x; ry = o[1] - pj.y - sh.y; rz = o[2] - pj.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                keep = r2 < p.four_h2;
+                if (keep) W = kernel_w(sqrtf(r2) * p.inv_h, p);
+            }
+            if (FILTER) {
+                // the kept entries, in list order, become the exact list
+                const unsigned b = __ballot_sync(0xffffffffu, keep);
+                const unsigned g = (b >> ((threadIdx.x & 31) & ~(kBceLanes - 1))) & ((1u << kBceLanes) - 1u);
+                const int at = cnt + __popc(g & ((1u << q) - 1u));
+                if (keep && at < p.maxnb) L.out[(size_t)at * p.ell + s] = e;
+                cnt += __popc(g);
+            }
+            w += W;
+            sux = fmaf(vj.x, W, sux); suy = fmaf(vj.y, W, suy); suz = fmaf(vj.z, W, suz);
+            ss[0] = fmaf(aj.x, W, ss[0]); ss[1] = fmaf(aj.y, W, ss[1]); ss[2] = fmaf(aj.z, W, ss[2]);
+            ss[3] = fmaf(aj.w, W, ss[3]); ss[4] = fmaf(bj.x, W, ss[4]); ss[5] = fmaf(bj.y, W, ss[5]);
+            const float rw = vj.w * W;
+            sr[0] = fmaf(rw, rx, sr[0]); sr[1] = fmaf(rw, ry, sr[1]); sr[2] = fmaf(rw, rz, sr[2]);
+        }
+        w = group_sum(w);
+        sux = group_sum(sux); suy = group_sum(suy); suz = group_sum(suz);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ss[k] = group_sum(ss[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sr[k] = group_sum(sr[k]);
+        if (FILTER && q == 0 && valid) {
+            if (cnt > p.maxnb) atomicOr(L.err, ERR_CAPACITY);
+            L.out_n[s] = (uint32_t)min(cnt, p.maxnb);
+        }
+        float ua[3], sa[6];
+        if (w > 0.f) {
+            const float iw = 1.0f / w;
+            ua[0] = 2.f * ub[0] - sux * iw;
+            ua[1] = 2.f * ub[1] - suy * iw;
+            ua[2] = 2.f * ub[2] - suz * iw;
+            const float gp = (p.gx - ab[0]) * sr[0] + (p.gy - ab[1]) * sr[1] + (p.gz - ab[2]) * sr[2];
+            sa[0] = (ss[0] - gp) * iw; sa[1] = (ss[1] - gp) * iw; sa[2] = (ss[2] - gp) * iw;
+            sa[3] = ss[3] * iw; sa[4] = ss[4] * iw; sa[5] = ss[5] * iw;
+        } else {
+            ua[0] = ub[0]; ua[1] = ub[1]; ua[2] = ub[2];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sa[k] = 0.f;
+        }
+        if (work && q == 0) {
+            S.pos[s] = make_float4(o[0], o[1], o[2], home.w);
+            S.vel[s] = make_float4(ua[0], ua[1], ua[2], p.rho0);
+            S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
+            S.sB[s] = make_float2(sa[4], sa[5]);
+        }
+        if constexpr (ACCEL != 0) {
+            // pass 2: marker accelerations (body markers for the wrench; every
+            // marker for the rate evaluation)
+            const int n2 = (ACCEL == 2 || body >= 0) ? nn : 0;
+            const int rounds2 = __reduce_max_sync(0xffffffffu, (n2 + kBceLanes - 1) / kBceLanes);
+            float mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
+            e_nx = q < n2 ? __ldg(row + (size_t)q * p.ell) : 0u;
+            for (int r = 0; r < rounds2; ++r) {
+                const int k = r * kBceLanes + q;
+                const uint32_t e = e_nx;
+                if (k + kBceLanes < n2) e_nx = __ldg(row + (size_t)(k + kBceLanes) * p.ell);
+                if (k >= n2) continue;
+                const uint32_t j = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pj = __ldg(&S.pos[j]);
+                const float4 vj = __ldg(&S.vel[j]);
+                const float4 aj = __ldg(&S.sA[j]);
+                const float2 bj = __ldg(&S.sB[j]);
+                const float rx = o[0] - pj.x - sh.x, ry = o[1] - pj.y - sh.y, rz = o[2] - pj.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+                const float rinv = rsqrtf(r2);
+                const float fk = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
+                const float gx = fk * rx, gy = fk * ry, gz = fk * rz;
+                const float Vj = __fdividef(p.m, vj.w);   // MUFU reciprocal: ~2 ulp
+                const float sxx = sa[0] + aj.x, syy = sa[1] + aj.y, szz = sa[2] + aj.z;
+                const float sxy = sa[3] + aj.w, sxz = sa[4] + bj.x, syz = sa[5] + bj.y;
+                mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, mx);
+                my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, my);
+                mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, mz);
+                if (p.av_mode != CRM_AV_NONE) {
+                    const float vr = (ua[0] - vj.x) * rx + (ua[1] - vj.y) * ry + (ua[2] - vj.z) * rz;
+                    if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+                        const float fac = __fdividef(2.0f * p.av_c * vr, (p.rho0 + vj.w) * (r2 + p.xi2));
+                        avx = fmaf(fac, gx, avx);
+                        avy = fmaf(fac, gy, avy);
+                        avz = fmaf(fac, gz, avz);
+                    }
+                }
+            }
+            if (rounds2 > 0) {
+                mx = group_sum(mx); my = group_sum(my); mz = group_sum(mz);
+                avx = group_sum(avx); avy = group_sum(avy); avz = group_sum(avz);
+            }
+            const float ir = 1.0f / p.rho0;
+            f[0] = p.m * (mx * ir + avx);
+            f[1] = p.m * (my * ir + avy);
+            f[2] = p.m * (mz * ir + avz);
+        }
+    } else if (FILTER && valid && q == 0) {
+        L.out_n[s] = 0u;
+    }
+    if constexpr (ACCEL == 2) {
+        if (valid && q == 0) mforce[s - z.nF] = make_float4(f[0], f[1], f[2], __int_as_float(body));
+    } else if constexpr (ACCEL == 1) {
+        body_wrench_tail(p, f, arm, body, q == 0 && nn > 0 && body >= 0, bs, s_bodies, s_last, red);
+    }
+}
+
+// Markers with a non-empty list, compacted in slot order at each list rebuild
+// (most wall markers have no fluid in reach; the BCE kernels then run over the
+// active ones only).  Two passes without inter-block waits: per-block counts,
+// then each block sums the counts before it and places its markers by ballot.
+constexpr int kCompactBlock = 256;
+
+__global__ void __launch_bounds__(kCompactBlock)
+k_marker_counts(DevParams p, const uint32_t *__restrict__ nnb, uint32_t *__restrict__ bcount)
+{
+    if (*p.abort || gated_off(p)) return;
+    const Sizes z = load_sizes(p);
+    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = __syncthreads_count(s < z.N && nnb[s] > 0u);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = (uint32_t)c;
+}
+
+__global__ void __launch_bounds__(kCompactBlock)
+k_marker_compact(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *__restrict__ bcount,
+                 uint32_t *__restrict__ act, int *__restrict__ n_act, uint32_t *__restrict__ nnb_exact)
+{
+    if (*p.abort || gated_off(p)) return;
+    __shared__ uint32_t s_sum[kCompactBlock / 32], s_cnt[kCompactBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t acc = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) acc += bcount[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const Sizes z = load_sizes(p);
+    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = s < z.N;
+    const bool a = valid && nnb[s] > 0u;
+    const unsigned bits = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) {
+        s_sum[warp] = acc;
+        s_cnt[warp] = (uint32_t)__popc(bits);
+    }
+    __syncthreads();
+    uint32_t off = 0;
+    for (int w = 0; w < kCompactBlock / 32; ++w) off += s_sum[w] + (w < warp ? s_cnt[w] : 0u);
+    if (a) act[off + __popc(bits & ((1u << lane) - 1u))] = (uint32_t)s;
+    else if (valid && nnb_exact != nullptr) nnb_exact[s] = 0u;   // no skin neighbours: none within 2h
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kCompactBlock - 1)
+        *n_act = (int)(off + __popc(bits & ((1u << lane) - 1u)) + (a ? 1u : 0u));
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers used by the API translation unit.
+void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
+                const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
+                double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
+                unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
+                const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames,
+                const uint32_t *act, const int *n_act)
+{
+    const unsigned g = bce_blocks(p);
+    BodyStep bs{partial, ticket, bodies, dt, integrate, gate};
+    if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
+        const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
+        k_bce<0, true><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
+                                             n_fluid_total, mforce, bs);
+        return;
+    }
+    const ListIO L{nbr, nnb, nullptr, nullptr, err};
+    if (accel == 0)
+        k_bce<0, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
+                                              n_fluid_total, mforce, bs);
+    else if (accel == 1)
+        k_bce<1, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
+                                              n_fluid_total, mforce, bs);
+    else
+        k_bce<2, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
+                                              n_fluid_total, mforce, bs);
+}
+
+unsigned bce_blocks(const DevParams &p) { return grid_for((int64_t)p.capM * kBceLanes); }
+
+unsigned compact_blocks(const DevParams &p) { return grid_for(p.capM, kCompactBlock); }
+
+void launch_compact_markers(const DevParams &p, const uint32_t *nnb, uint32_t *nnb_exact,
+                            uint32_t *bcount, uint32_t *act, int *n_act, cudaStream_t st)
+{
+    const unsigned g = compact_blocks(p);
+    k_marker_counts<<<g, kCompactBlock, 0, st>>>(p, nnb, bcount);
+    k_marker_compact<<<g, kCompactBlock, 0, st>>>(p, nnb, bcount, act, n_act, nnb_exact);
+}
+
+}  // namespace crm

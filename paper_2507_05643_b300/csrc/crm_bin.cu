@@ -321,10 +321,11 @@ __global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restr
 // and marker neighbours, markers take fluid neighbours only.  The scan is cell
 // by cell, so the cell offset (dx, dy, dz) of j is a loop constant; a row
 // (dy, dz) whose nearest face is already 2h away is skipped, and because every
-// cell is sorted by x the left cell is read from its right end and the right
-// cell from its left end, each stopping once the x-gap alone reaches the
-// remaining radius.  (Both cut-offs carry a 1e-5 relative margin, so they
-// never drop a pair the full test would keep.)  The list is an ELL table
+// cell is sorted by x only a top run of the left cell (found walking down from
+// its right end) and a bottom run of the right cell (read until the x-gap alone
+// reaches the remaining radius) can hold neighbours.  (Both cut-offs carry a
+// 1e-5 relative margin, so they never drop a pair the full test would keep.)
+// The list is an ELL table
 // nbr[k * ell + s] (coalesced across a warp); each entry is j | code << 26 with
 // code = (dx+1) | (dy+1) << 2 | (dz+1) << 4, which the pair kernels use to
 // rebuild x_s - x_j from the cell-relative offsets.
@@ -345,39 +346,45 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
     const int nseg = s < z.nF ? 2 : 1;
     const float cell = p.cell;
     const float lim2 = r2cut * (1.0f + 1e-5f);
+    // Entries come out in ascending slot order (fluid segment first, cells in
+    // key order, each cell upwards), so the k-th entries of neighbouring
+    // particles -- neighbouring lanes of the pair kernels -- are close in
+    // memory and their gathers share cache lines.
     int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int lz2 = lz + dz;
-        if (lz2 < 0 || lz2 >= W.Z) continue;
-        const float gz = dz < 0 ? fmaxf(ps.z, 0.f) : (dz > 0 ? fmaxf(cell - ps.z, 0.f) : 0.f);
-        const float sz = ps.z - (float)dz * cell;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int ly2 = ly + dy;
-            if (ly2 < 0 || ly2 >= W.Y) continue;
-            const float gy = dy < 0 ? fmaxf(ps.y, 0.f) : (dy > 0 ? fmaxf(cell - ps.y, 0.f) : 0.f);
-            const float d2 = gy * gy + gz * gz;
-            if (d2 >= lim2) continue;
-            const float R = sqrtf(lim2 - d2);
-            const float sy = ps.y - (float)dy * cell;
-            const uint32_t rowkey = ((uint32_t)lz2 * (uint32_t)W.Y + (uint32_t)ly2) * (uint32_t)W.X;
-            const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
-            for (int seg = 0; seg < nseg; ++seg) {
-                const uint32_t kb = seg * p.M + rowkey;
+    for (int seg = 0; seg < nseg; ++seg) {
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int lz2 = lz + dz;
+            if (lz2 < 0 || lz2 >= W.Z) continue;
+            const float gz = dz < 0 ? fmaxf(ps.z, 0.f) : (dz > 0 ? fmaxf(cell - ps.z, 0.f) : 0.f);
+            const float sz = ps.z - (float)dz * cell;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int ly2 = ly + dy;
+                if (ly2 < 0 || ly2 >= W.Y) continue;
+                const float gy = dy < 0 ? fmaxf(ps.y, 0.f) : (dy > 0 ? fmaxf(cell - ps.y, 0.f) : 0.f);
+                const float d2 = gy * gy + gz * gz;
+                if (d2 >= lim2) continue;
+                const float R = sqrtf(lim2 - d2);
+                const float sy = ps.y - (float)dy * cell;
+                const uint32_t kb = seg * p.M + ((uint32_t)lz2 * (uint32_t)W.Y + (uint32_t)ly2) * (uint32_t)W.X;
+                const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
 #pragma unroll
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int lx2 = lx + dx;
                     if (lx2 < 0 || lx2 >= W.X) continue;
-                    const uint32_t jb = start[kb + lx2], je = start[kb + lx2 + 1];
+                    const int jb = (int)start[kb + lx2], je = (int)start[kb + lx2 + 1];
                     const float sx = ps.x - (float)dx * cell;
                     const uint32_t tag = ((uint32_t)(dx + 1) | codeyz) << kIndexBits;
-                    // left cell: scan down from the largest x; right cell: up from the smallest
-                    const int step = dx < 0 ? -1 : 1;
-                    const int first = dx < 0 ? (int)je - 1 : (int)jb;
-                    const int count = (int)(je - jb);
-                    for (int q = 0, j = first; q < count; ++q, j += step) {
+                    // cells are x-sorted: in the left cell only a top run is within R in
+                    // x (found walking down), in the right cell only a bottom run
+                    int j0 = jb;
+                    if (dx < 0) {
+                        j0 = je;
+                        while (j0 > jb && fabsf(sx - pos[j0 - 1].x) < R) --j0;
+                    }
+                    for (int j = j0; j < je; ++j) {
                         const float4 pj = pos[j];
                         const float rx = sx - pj.x;
-                        if (dx != 0 && fabsf(rx) >= R) break;
+                        if (dx > 0 && fabsf(rx) >= R) break;
                         const float ry = sy - pj.y, rz = sz - pj.z;
                         const float r2 = rx * rx + ry * ry + rz * rz;
                         if (r2 < r2cut && j != s) {

@@ -261,6 +261,26 @@ __device__ __forceinline__ void marker_now(const BodyDev &b, const double *xloc,
     marker_kin(b.pose, r, v, w, acc, x, u, a, arm);
 }
 
+// Cell offsets of the neighbour codes (dx, dy, dz in {-1, 0, 1}) times the cell
+// size, built once per block in shared memory.
+__device__ __forceinline__ void fill_shift_table(float4 *lut, float cell)
+{
+    const int t = threadIdx.x;
+    if (t < 64) {
+        const int dx = (t & 3) - 1, dy = ((t >> 2) & 3) - 1, dz = (t >> 4) - 1;
+        lut[t] = make_float4((float)dx * cell, (float)dy * cell, (float)dz * cell, 0.0f);
+    }
+}
+
+// Neighbour lists a kernel walks (and, when filtering, writes).
+struct ListIO {
+    const uint32_t *in;   // list walked (the skin list when filtering)
+    const uint32_t *in_n;
+    uint32_t *out;        // exact list written when filtering
+    uint32_t *out_n;
+    int *err;
+};
+
 // ---------------------------------------------------------------------------
 // Launch helpers shared by the translation units.
 inline unsigned grid_for(int64_t n, int block = kBlock)
