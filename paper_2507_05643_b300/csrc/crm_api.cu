@@ -87,8 +87,11 @@ struct crm_terrain {
     double *mloc = nullptr;
     BodyDev *bodies = nullptr;
     BodyFrame *mid_frames = nullptr;             // bodies at the step midpoint
-    uint32_t *act = nullptr, *act_bcount = nullptr;   // markers with fluid in reach
-    int *n_act = nullptr;
+    uint32_t *act = nullptr, *act_body = nullptr;   // markers with fluid in reach (all, on bodies)
+    uint32_t *act_bcount = nullptr;
+    int *n_act = nullptr;                          // [2]: sizes of act, act_body
+    cudaStream_t side = nullptr;                   // the wrench pass beside pair stage 2
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int *err = nullptr, *counts = nullptr, *win = nullptr, *abort_flag = nullptr;
     int *h_counts = nullptr;      // pinned mirror: counters + abort word
     // active domains: master store and candidates
@@ -304,12 +307,13 @@ int alloc_working(crm_terrain *t)
     t->nbr = t->dalloc<uint32_t>(G_WORK, (size_t)d.maxnb * d.ell);
     t->nnb = t->dalloc<uint32_t>(G_WORK, N);
     t->mforce = t->dalloc<float4>(G_WORK, t->capM);
-    t->partial = t->dalloc<double>(G_WORK, (size_t)bce_blocks(d)
+    t->partial = t->dalloc<double>(G_WORK, (size_t)wrench_blocks(t->n_bodym)
                                                * std::max<size_t>(t->hbodies.size(), 1) * 6);
     t->ticket = t->dalloc<unsigned>(G_WORK, 1);
     t->act = t->dalloc<uint32_t>(G_WORK, t->capM);
-    t->act_bcount = t->dalloc<uint32_t>(G_WORK, compact_blocks(d));
-    t->n_act = t->dalloc<int>(G_WORK, 1);
+    t->act_body = t->dalloc<uint32_t>(G_WORK, std::max(t->n_bodym, 1));
+    t->act_bcount = t->dalloc<uint32_t>(G_WORK, 2 * (size_t)compact_blocks(d));
+    t->n_act = t->dalloc<int>(G_WORK, 2);
     if (t->skin_on) {
         t->sk_nbr = t->dalloc<uint32_t>(G_WORK, (size_t)d.skin_cap * d.ell);
         t->sk_nnb = t->dalloc<uint32_t>(G_WORK, N);
@@ -325,7 +329,7 @@ int alloc_working(crm_terrain *t)
     CRM_CUDA(t, cudaMemsetAsync(t->nnb, 0, N * sizeof(uint32_t), t->st));
     CRM_CUDA(t, cudaMemsetAsync(t->mforce, 0, std::max<int64_t>(t->capM, 1) * sizeof(float4), t->st));
     CRM_CUDA(t, cudaMemsetAsync(t->ticket, 0, sizeof(unsigned), t->st));
-    CRM_CUDA(t, cudaMemsetAsync(t->n_act, 0, sizeof(int), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->n_act, 0, 2 * sizeof(int), t->st));
     t->cur = 0;
     t->lists_valid = false;
     return CRM_OK;
@@ -443,6 +447,7 @@ int commit(crm_terrain *t)
     }
     const int64_t full_cells = (int64_t)d.GX * d.GY * d.GZ;
     cudaStream_t st = t->st;
+    t->n_bodym = (int)std::count_if(t->hmbody.begin(), t->hmbody.end(), [](int b) { return b >= 0; });
 
     // static device state
     t->mloc = t->dalloc<double>(G_STATIC, 3 * nM);
@@ -463,6 +468,18 @@ int commit(crm_terrain *t)
     d.sizes = t->counts;
     d.win = t->win;
     d.abort = t->abort_flag;
+    if (!t->side) {
+        // side stream of the wrench pass; without it everything stays on the handle's stream
+        if (cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking) != cudaSuccess
+            || cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess
+            || cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (t->side) cudaStreamDestroy(t->side);
+            if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+            t->side = nullptr;
+            t->ev_fork = t->ev_join = nullptr;
+        }
+    }
     CRM_CUDA(t, cudaMemsetAsync(t->err, 0, sizeof(int), st));
     CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), st));
     CRM_CUDA(t, cudaMemsetAsync(t->counts, 0, C_WORDS * sizeof(int), st));
@@ -744,14 +761,16 @@ void enqueue_search(crm_terrain *t)
         launch(t, K_SKIN, [&] { launch_copyback(d, t->A[n], t->pid[n], t->A[c], t->pid[c], t->xref,
                                                 t->bodies, t->st); });
         if (d.capM > 0)
-            launch(t, K_COMPACT, [&] { launch_compact_markers(d, t->sk_nnb, t->nnb, t->act_bcount,
-                                                              t->act, t->n_act, t->st); }, 2);
+            launch(t, K_COMPACT, [&] { launch_compact_markers(d, t->sk_nnb, t->pid[c], t->nnb,
+                                                              t->act_bcount, t->act, t->act_body,
+                                                              t->n_act, t->st); }, 2);
     } else {
         launch(t, K_NEIGHBORS, [&] { launch_neighbors(d, t->A[n].pos, t->start, t->nbr, t->nnb,
                                                       d.maxnb, d.four_h2, t->err, t->st); });
         if (d.capM > 0)
-            launch(t, K_COMPACT, [&] { launch_compact_markers(d, t->nnb, nullptr, t->act_bcount,
-                                                              t->act, t->n_act, t->st); }, 2);
+            launch(t, K_COMPACT, [&] { launch_compact_markers(d, t->nnb, t->pid[n], nullptr,
+                                                              t->act_bcount, t->act, t->act_body,
+                                                              t->n_act, t->st); }, 2);
     }
 }
 
@@ -773,18 +792,19 @@ void rebuild(crm_terrain *t)
 // `filter` (stage 1 right after a rebuild with the skin): the kernel walks the
 // skin lists and writes the exact lists for the rest of the step.
 void bce(crm_terrain *t, StageArrays S, double tau, int accel, double dt = 0.0, int integrate = 0,
-         bool filter = false)
+         bool filter = false, cudaStream_t st = nullptr)
 {
     const DevParams &d = t->dp;
     if (d.capM == 0) return;
-    if (accel == 1 && d.n_bodies == 0) accel = 0;
     const int c = t->cur;
     int *gate = t->skin_on ? t->gate : nullptr;
     const uint32_t *skl = filter ? t->sk_nbr : nullptr, *skn = filter ? t->sk_nnb : nullptr;
+    const uint32_t *act = accel == 2 ? nullptr : (accel == 1 ? t->act_body : t->act);
+    const int *n_act = accel == 1 ? t->n_act + 1 : t->n_act;
     launch(t, K_BCE, [&] { launch_bce(d, S, t->A[c].pos, t->pid[c], t->mloc, t->bodies, t->nbr,
                                       t->nnb, tau, accel, (int)t->nFtot, t->mforce, t->partial,
-                                      t->ticket, dt, integrate, gate, t->st, skl, skn, t->err,
-                                      t->mid_frames, accel == 2 ? nullptr : t->act, t->n_act); });
+                                      t->ticket, dt, integrate, gate, st ? st : t->st, skl, skn,
+                                      t->err, t->mid_frames, act, n_act, t->n_bodym); });
 }
 
 void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, RateOut out,
@@ -801,14 +821,28 @@ void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, Rate
                                    xref, gate, t->st, skl, skn); });
 }
 
+// One RK2 step.  The body markers' accelerations, the FP64 wrench and the body
+// update only feed the next step, so they run on a side stream beside pair
+// stage 2 (a parallel branch of the step graph); the step ends after both.
 void enqueue_stages(crm_terrain *t, double dt, bool filter)
 {
     const int c = t->cur;
     RateOut none{};
     bce(t, t->A[c], 0.0, 0, dt, 0, filter);   // also the bodies' midpoint frames
     pair(t, kStage1, t->A[c], t->A[c], (float)dt, none, filter);
-    bce(t, t->MID, 0.5 * dt, 1, dt, 1);
+    bce(t, t->MID, 0.5 * dt, 0);               // marker state at the midpoint
+    const bool wrench = t->dp.capM > 0 && t->dp.n_bodies > 0;
+    const bool fork = wrench && t->side != nullptr && !t->timing;
+    if (fork) {
+        cudaEventRecord(t->ev_fork, t->st);
+        cudaStreamWaitEvent(t->side, t->ev_fork, 0);
+    }
+    if (wrench) bce(t, t->MID, 0.5 * dt, 1, dt, 1, false, fork ? t->side : nullptr);
     pair(t, kStage2, t->MID, t->A[c], (float)dt, none);
+    if (fork) {
+        cudaEventRecord(t->ev_join, t->side);
+        cudaStreamWaitEvent(t->st, t->ev_join, 0);
+    }
 }
 
 void one_step(crm_terrain *t, double dt)
@@ -930,7 +964,7 @@ int graph_step(crm_terrain *t, double dt)
         t->prof.rebuilds += 1;
         t->lists_valid = true;
     }
-    if (d.capM > 0) t->prof.launches[K_BCE] += 2;
+    if (d.capM > 0) t->prof.launches[K_BCE] += d.n_bodies > 0 ? 3 : 2;
     if (d.capF > 0) {
         t->prof.launches[K_PAIR1] += 1;
         t->prof.launches[K_PAIR2] += 1;
@@ -1123,6 +1157,12 @@ int crm_destroy(crm_terrain *t)
         if (t->g_plain[b].exec) cudaGraphExecDestroy(t->g_plain[b].exec);
     }
     if (t->cap_st) cudaStreamDestroy(t->cap_st);
+    if (t->side) {
+        cudaStreamSynchronize(t->side);
+        cudaStreamDestroy(t->side);
+        cudaEventDestroy(t->ev_fork);
+        cudaEventDestroy(t->ev_join);
+    }
     for (int g = 0; g < G_COUNT; ++g) t->free_group(g);
     if (t->h_counts) cudaFreeHost(t->h_counts);
     delete t;

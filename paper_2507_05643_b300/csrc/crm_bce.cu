@@ -13,11 +13,12 @@ namespace crm {
 //   Stress: sigma_a = [sum_f sigma_f W - ((g - a_body) . sum_f rho_f (x_a - x_f) W) I]
 //   / sum_f W (the pressure extrapolation of the cited scheme in stress form);
 //   without fluid in reach u_a = u_body and sigma_a = 0.
-// ACCEL: 0 = state only; 1 = also the accelerations of body markers, reduced
-// per block into FP64 force / torque partials, after which the last block to
+// ACCEL: 0 = state only; 1 = the accelerations of the body markers (their
+// state already written by a state launch on the same arrays), reduced per
+// block into FP64 force / torque partials, after which the last block to
 // finish sums the partials in a fixed order and advances the bodies (the wrench
-// and body update of Sec. 2.4); 2 = the accelerations of every marker, written
-// to mforce (rate evaluation).  Acceleration: a_a = (1/rho0) sum_f V_f
+// and body update of Sec. 2.4); 2 = state and accelerations of every marker,
+// the accelerations written to mforce (rate evaluation).  Acceleration: a_a = (1/rho0) sum_f V_f
 // (sigma_a + sigma_f) . grad_a W_af + AV, no gravity.
 // FILTER (stage 1 with a Verlet skin): the marker walks its skin list and keeps
 // the fluid particles closer than 2h as its exact list for the rest of the step.
@@ -204,14 +205,24 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
                 o[0] = home.x; o[1] = home.y; o[2] = home.z;   // fixed: the searched offset
             }
         }
+        const uint32_t *row = L.in + s;
+        float ua[3], sa[6];
+        uint32_t e_nx;
+        if constexpr (ACCEL == 1) {
+            // the wrench pass follows a state pass over the same arrays: the
+            // marker's extrapolated velocity and stress are in its slot
+            const float4 vs = S.vel[s], as = S.sA[s];
+            const float2 bs2 = S.sB[s];
+            ua[0] = vs.x; ua[1] = vs.y; ua[2] = vs.z;
+            sa[0] = as.x; sa[1] = as.y; sa[2] = as.z; sa[3] = as.w; sa[4] = bs2.x; sa[5] = bs2.y;
+        } else {
         // pass 1: extrapolation sums, the list strided over the group's lanes
         // (warp-uniform round count; the next entry is fetched one round ahead)
-        const uint32_t *row = L.in + s;
         const int rounds = __reduce_max_sync(0xffffffffu, (nn + kBceLanes - 1) / kBceLanes);
         float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
         float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
-        uint32_t e_nx = q < nn ? __ldg(row + (size_t)q * p.ell) : 0u;
+        e_nx = q < nn ? __ldg(row + (size_t)q * p.ell) : 0u;
         for (int r = 0; r < rounds; ++r) {
             const int k = r * kBceLanes + q;
             const uint32_t e = e_nx;
@@ -258,7 +269,6 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
             if (cnt > p.maxnb) atomicOr(L.err, ERR_CAPACITY);
             L.out_n[s] = (uint32_t)min(cnt, p.maxnb);
         }
-        float ua[3], sa[6];
         if (w > 0.f) {
             const float iw = 1.0f / w;
             ua[0] = 2.f * ub[0] - sux * iw;
@@ -278,6 +288,7 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
             S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
             S.sB[s] = make_float2(sa[4], sa[5]);
         }
+        }   // pass 1
         if constexpr (ACCEL != 0) {
             // pass 2: marker accelerations (body markers for the wrench; every
             // marker for the rate evaluation)
@@ -343,43 +354,74 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
 // then each block sums the counts before it and places its markers by ballot.
 constexpr int kCompactBlock = 256;
 
-__global__ void __launch_bounds__(kCompactBlock)
-k_marker_counts(DevParams p, const uint32_t *__restrict__ nnb, uint32_t *__restrict__ bcount)
+// list 0: every marker with a non-empty list; list 1: those of them on a body.
+__device__ __forceinline__ void marker_activity(const Sizes &z, const uint32_t *nnb,
+                                                const uint32_t *pid, int s, bool &valid,
+                                                bool a[2])
 {
-    if (*p.abort || gated_off(p)) return;
-    const Sizes z = load_sizes(p);
-    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = __syncthreads_count(s < z.N && nnb[s] > 0u);
-    if (threadIdx.x == 0) bcount[blockIdx.x] = (uint32_t)c;
+    valid = s < z.N;
+    a[0] = valid && nnb[s] > 0u;
+    a[1] = a[0] && pid_body(pid[s]) >= 0;
 }
 
 __global__ void __launch_bounds__(kCompactBlock)
-k_marker_compact(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *__restrict__ bcount,
-                 uint32_t *__restrict__ act, int *__restrict__ n_act, uint32_t *__restrict__ nnb_exact)
+k_marker_counts(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *__restrict__ pid,
+                uint32_t *__restrict__ bcount)
 {
     if (*p.abort || gated_off(p)) return;
-    __shared__ uint32_t s_sum[kCompactBlock / 32], s_cnt[kCompactBlock / 32];
+    const Sizes z = load_sizes(p);
+    bool valid, a[2];
+    marker_activity(z, nnb, pid, z.nF + blockIdx.x * blockDim.x + threadIdx.x, valid, a);
+    const int c0 = __syncthreads_count(a[0]);
+    const int c1 = __syncthreads_count(a[1]);
+    if (threadIdx.x == 0) {
+        bcount[2 * blockIdx.x] = (uint32_t)c0;
+        bcount[2 * blockIdx.x + 1] = (uint32_t)c1;
+    }
+}
+
+__global__ void __launch_bounds__(kCompactBlock)
+k_marker_compact(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *__restrict__ pid,
+                 const uint32_t *__restrict__ bcount, uint32_t *__restrict__ act,
+                 uint32_t *__restrict__ act_body, int *__restrict__ n_act,
+                 uint32_t *__restrict__ nnb_exact)
+{
+    if (*p.abort || gated_off(p)) return;
+    __shared__ uint32_t s_sum[2][kCompactBlock / 32], s_cnt[2][kCompactBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t acc = 0;
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) acc += bcount[b];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    uint32_t acc[2] = {0u, 0u};
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) {
+        acc[0] += bcount[2 * b];
+        acc[1] += bcount[2 * b + 1];
+    }
     const Sizes z = load_sizes(p);
     const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = s < z.N;
-    const bool a = valid && nnb[s] > 0u;
-    const unsigned bits = __ballot_sync(0xffffffffu, a);
-    if (lane == 0) {
-        s_sum[warp] = acc;
-        s_cnt[warp] = (uint32_t)__popc(bits);
+    bool valid, a[2];
+    marker_activity(z, nnb, pid, s, valid, a);
+    unsigned bits[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[l] += __shfl_xor_sync(0xffffffffu, acc[l], o);
+        bits[l] = __ballot_sync(0xffffffffu, a[l]);
+        if (lane == 0) {
+            s_sum[l][warp] = acc[l];
+            s_cnt[l][warp] = (uint32_t)__popc(bits[l]);
+        }
     }
     __syncthreads();
-    uint32_t off = 0;
-    for (int w = 0; w < kCompactBlock / 32; ++w) off += s_sum[w] + (w < warp ? s_cnt[w] : 0u);
-    if (a) act[off + __popc(bits & ((1u << lane) - 1u))] = (uint32_t)s;
-    else if (valid && nnb_exact != nullptr) nnb_exact[s] = 0u;   // no skin neighbours: none within 2h
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kCompactBlock - 1)
-        *n_act = (int)(off + __popc(bits & ((1u << lane) - 1u)) + (a ? 1u : 0u));
+    const unsigned below = (1u << lane) - 1u;
+    uint32_t *const out[2] = {act, act_body};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        uint32_t off = 0;
+        for (int w = 0; w < kCompactBlock / 32; ++w) off += s_sum[l][w] + (w < warp ? s_cnt[l][w] : 0u);
+        const uint32_t at = off + __popc(bits[l] & below);
+        if (a[l]) out[l][at] = (uint32_t)s;
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kCompactBlock - 1)
+            n_act[l] = (int)(at + (a[l] ? 1u : 0u));
+    }
+    if (valid && !a[0] && nnb_exact != nullptr) nnb_exact[s] = 0u;   // no skin neighbours: none within 2h
 }
 
 // ---------------------------------------------------------------------------
@@ -389,38 +431,41 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
                 unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
                 const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames,
-                const uint32_t *act, const int *n_act)
+                const uint32_t *act, const int *n_act, int64_t body_markers)
 {
-    const unsigned g = bce_blocks(p);
     BodyStep bs{partial, ticket, bodies, dt, integrate, gate};
     if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_bce<0, true><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
-                                             n_fluid_total, mforce, bs);
+        k_bce<0, true><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
+                                                         act, n_act, tau, n_fluid_total, mforce, bs);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (accel == 0)
-        k_bce<0, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
-                                              n_fluid_total, mforce, bs);
+        k_bce<0, false><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
+                                                          act, n_act, tau, n_fluid_total, mforce, bs);
     else if (accel == 1)
-        k_bce<1, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
-                                              n_fluid_total, mforce, bs);
+        k_bce<1, false><<<wrench_blocks(body_markers), kBlock, 0, st>>>(
+            p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
     else
-        k_bce<2, false><<<g, kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
-                                              n_fluid_total, mforce, bs);
+        k_bce<2, false><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
+                                                          act, n_act, tau, n_fluid_total, mforce, bs);
 }
 
 unsigned bce_blocks(const DevParams &p) { return grid_for((int64_t)p.capM * kBceLanes); }
 
+unsigned wrench_blocks(int64_t body_markers) { return grid_for(body_markers * kBceLanes); }
+
 unsigned compact_blocks(const DevParams &p) { return grid_for(p.capM, kCompactBlock); }
 
-void launch_compact_markers(const DevParams &p, const uint32_t *nnb, uint32_t *nnb_exact,
-                            uint32_t *bcount, uint32_t *act, int *n_act, cudaStream_t st)
+void launch_compact_markers(const DevParams &p, const uint32_t *nnb, const uint32_t *pid,
+                            uint32_t *nnb_exact, uint32_t *bcount, uint32_t *act,
+                            uint32_t *act_body, int *n_act, cudaStream_t st)
 {
     const unsigned g = compact_blocks(p);
-    k_marker_counts<<<g, kCompactBlock, 0, st>>>(p, nnb, bcount);
-    k_marker_compact<<<g, kCompactBlock, 0, st>>>(p, nnb, bcount, act, n_act, nnb_exact);
+    k_marker_counts<<<g, kCompactBlock, 0, st>>>(p, nnb, pid, bcount);
+    k_marker_compact<<<g, kCompactBlock, 0, st>>>(p, nnb, pid, bcount, act, act_body, n_act,
+                                                  nnb_exact);
 }
 
 }  // namespace crm

@@ -353,20 +353,25 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
 // sk_nbr (stage 1 with a skin) the markers walk their skin lists and write
 // their exact lists to nbr / nnb.  frames (kMaxBodies entries): a launch at
 // tau = 0 with dt > 0 writes the bodies' frames at dt / 2 there, and a launch
-// at tau != 0 takes its marker kinematics from them.
+// at tau != 0 takes its marker kinematics from them.  act / n_act: the marker
+// slots to process (nullptr: every marker slot); accel 1 takes the active body
+// markers (at most body_markers of them) and reads their state from S.
 void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
                 const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
                 unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
                 const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames,
-                const uint32_t *act, const int *n_act);
+                const uint32_t *act, const int *n_act, int64_t body_markers);
 unsigned bce_blocks(const DevParams &p);
+unsigned wrench_blocks(int64_t body_markers);
 // Marker slots whose list (nnb: the skin lists with a skin) is non-empty, in
-// slot order, into act[0 .. *n_act); with nnb_exact the exact counts of the
-// others are zeroed.  bcount: compact_blocks(p) words.  Gated like the search.
+// slot order, into act[0 .. n_act[0]), and those of them on a body into
+// act_body[0 .. n_act[1]); with nnb_exact the exact counts of the others are
+// zeroed.  bcount: 2 compact_blocks(p) words.  Gated like the search.
 unsigned compact_blocks(const DevParams &p);
-void launch_compact_markers(const DevParams &p, const uint32_t *nnb, uint32_t *nnb_exact,
-                            uint32_t *bcount, uint32_t *act, int *n_act, cudaStream_t st);
+void launch_compact_markers(const DevParams &p, const uint32_t *nnb, const uint32_t *pid,
+                            uint32_t *nnb_exact, uint32_t *bcount, uint32_t *act,
+                            uint32_t *act_body, int *n_act, cudaStream_t st);
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
                    float *sig, float *rho, cudaStream_t st);
 void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, StageArrays S,
