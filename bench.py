@@ -216,7 +216,12 @@ def run_crm(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     sc = _workload(args)
-    t = crm.from_scene(sc, stream=stream)
+    over = {}
+    if args.skin is not None:
+        over["skin"] = args.skin
+    if args.ps_freq != 1:
+        over["ps_freq"] = args.ps_freq
+    t = crm.from_scene(sc, stream=stream, **over)
     dt = sc.dt
     with torch.cuda.stream(stream):
         t.step(dt, args.warmup)
@@ -344,6 +349,9 @@ def run_crm(args):
         }
         if args.bin_scale != 1:
             line["config"]["workload"] = f"profiling case: wheel_bin widened {args.bin_scale}x in x and y"
+        if args.ps_freq != 1:
+            line["config"]["workload"] = WORKLOAD.replace("ps_freq=1", f"ps_freq={args.ps_freq}")
+        line["config"]["skin"] = args.skin if args.skin is not None else 0.1
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -359,6 +367,10 @@ def main():
     ap.add_argument("--impl", choices=["crm", "reference"], default="crm")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skin", type=float, default=None,
+                    help="Verlet skin as a fraction of 2h (default: the library's 0.1)")
+    ap.add_argument("--ps-freq", type=int, default=1,
+                    help="neighbour-list rebuild period (Alg. 2); the workload is quoted at 1")
     ap.add_argument("--bin-scale", type=int, default=1,
                     help="profiling only: widen the bin S-fold in x and y")
     args = ap.parse_args()

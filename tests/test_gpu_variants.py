@@ -1,0 +1,120 @@
+"""Variants of the CUDA path against the FP64 oracle: the mu(I) rheology of the
+return map, and the cell-relative positions far from the origin.
+
+Bars as in test_gpu_parity.py (per particle and component, against the oracle's
+absolute-sum scale S of the rates, carried through one step).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+crm = pytest.importorskip("paper_2507_05643_b300")
+RATE_TOL = 1e-5
+
+
+def _sheared(seed, u_amp=0.5):
+    sc = scenes.lattice_only(seed=seed, n=12, mu_s=0.5, cohesion=200.0, av_mode=1,
+                             av_gamma=0.02, random_state=False)
+    rng = np.random.default_rng(seed)
+    sc.u = rng.uniform(-u_amp, u_amp, size=sc.u.shape)
+    sc.sig = rng.uniform(-3000.0, 300.0, size=sc.sig.shape)
+    sc.sig[:, 3:] *= 0.3
+    sc.rho = sc.params["rho0"] * (1 + rng.uniform(-0.01, 0.01, size=sc.rho.shape))
+    sc.params["gravity"] = (0.0, 0.0, 0.0)
+    return sc
+
+
+def _one_step(sc):
+    t = crm.from_scene(sc)
+    t.step(sc.dt, 1)
+    st = oracle.State(sc)
+    st.step()
+    return t.particles(), st
+
+
+def test_mu_i_return_map_one_step():
+    """mu(I) (Sec. 2.3, mu_2 > mu_s): one step of a sheared, yielding lattice.
+    The rheology branch is live (the mu(I) result differs from the constant-
+    friction one by far more than the bar) and the CUDA path follows the oracle
+    on every particle away from the tension cut-off, where sigma jumps to 0."""
+    sc = _sheared(71)
+    sc.params["mu_2"] = 0.8
+    sc.params["I0"] = 0.08
+    sc.params["grain_d"] = 0.002
+    st0 = oracle.State(sc)
+    oracle.set_scale_conditioning(True)
+    try:
+        *_, scale, _, _ = st0.eval_rates(want_scale=True)
+    finally:
+        oracle.set_scale_conditioning(False)
+    (xyz, vel, sig, rho), st = _one_step(sc)
+    dp = sc.copy()
+    dp.params["mu_2"] = dp.params["mu_s"]
+    st_dp = oracle.State(dp)
+    st_dp.step()
+
+    eps = np.finfo(np.float32).eps
+    tol_s = sc.dt * 2 * RATE_TOL * scale[:, 4:10] + 8 * eps * np.abs(st.sig) + 1e-3
+    zero_o = np.all(st.sig == 0, axis=1)
+    zero_g = np.all(sig == 0, axis=1)
+    flips = zero_o != zero_g
+    assert flips.sum() <= max(3, 0.002 * sig.shape[0]), flips.sum()
+    both = ~zero_o & ~zero_g
+    err = np.abs(sig - st.sig)[both] / tol_s[both]
+    assert np.all(err <= 1.0), float(err.max())
+    # the rate-dependent friction changed the outcome of many particles
+    moved = np.max(np.abs(st.sig - st_dp.sig), axis=1) > 100 * tol_s.max(axis=1)
+    assert moved.sum() > 0.1 * sig.shape[0], moved.sum()
+    # and every particle sits inside the widest cone mu(I) allows, mu in [mu_s, mu_2]
+    # (mu = mu_s in tension, where I is not formed), or at the apex
+    p = -(sig[:, 0] + sig[:, 1] + sig[:, 2]) / 3
+    tau = sig.copy()
+    tau[:, :3] += p[:, None]
+    tb = np.sqrt(0.5 * (np.sum(tau[:, :3] ** 2, axis=1) + 2 * np.sum(tau[:, 3:] ** 2, axis=1)))
+    assert np.all(tb <= (np.maximum(0.5 * p, 0.8 * p) + 200.0) * (1 + 1e-5) + 1e-3)
+
+
+def _shift(sc, dx):
+    s = sc.copy()
+    v = np.array([dx, 0.0, 0.0])
+    s.x = s.x + v
+    s.fixed = s.fixed + v
+    for b in s.bodies:
+        b.pose[:3] = b.pose[:3] + v
+    s.domain_min = np.asarray(s.domain_min, float) + v
+    s.domain_max = np.asarray(s.domain_max, float) + v
+    return s
+
+
+def test_far_from_origin_keeps_precision():
+    """Cell-relative FP32 positions: the wheel bin moved 5 km along x follows the
+    same trajectory as at the origin.  An absolute FP32 coordinate at 5 km has a
+    spacing of 4.9e-4 m (0.05 d0); here the two runs agree to 1e-4 d0 after 50
+    steps, and the far run matches the oracle's FP64 step like the near one."""
+    base = scenes.wheel_bin(seed=73, nx=40, ny=24, nz=10, wheel_radius=0.08, wheel_width=0.08,
+                            n_grousers=8, wheel_x=0.2)
+    base.bodies[0].pose[2] -= 0.004
+    far = _shift(base, 5000.0)
+    a = crm.from_scene(base)
+    b = crm.from_scene(far)
+    a.step(base.dt, 1)
+    b.step(base.dt, 1)
+    st = oracle.State(far)
+    st.step()
+    xb, vb, sb, rb = b.particles()
+    assert np.max(np.abs(xb - st.x)) <= 1e-8   # absolute (FP64) positions of the far run
+    assert np.sqrt(np.mean((sb - st.sig) ** 2)) <= 1e-5 * base.params["rho0"] * 9.81 * 0.1
+    a.step(base.dt, 49)
+    b.step(base.dt, 49)
+    xa, va, sa, ra = a.particles()
+    xb, vb, sb, rb = b.particles()
+    d0 = base.params["d0"]
+    assert np.max(np.abs((xb - 5000.0 * np.array([1.0, 0.0, 0.0])) - xa)) <= 1e-4 * d0
+    assert np.sqrt(np.mean((sb - sa) ** 2)) <= 1e-4 * base.params["rho0"] * 9.81 * 0.1
+    Fa, _ = a.body_wrench(0)
+    Fb, _ = b.body_wrench(0)
+    assert np.linalg.norm(Fb - Fa) <= 1e-3 * np.linalg.norm(Fa)
