@@ -105,6 +105,20 @@ def _dist():
     return world, rank, local
 
 
+def aggregate(world: int, times, units: float, device=None):
+    """Cross-rank reduction of one run: each timing is the maximum over ranks (the
+    job lasts as long as its slowest replica) and the units (particle-steps) are
+    summed over ranks.  Returns (times, total units)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in times], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t], float(u[0])
+
+
 def cpu_baseline(budget_s: float = 15.0) -> dict:
     """The FP64 oracle as it stands, on this host's cores, on a bounded sample of
     the same workload: as many whole steps as fit in ~budget_s (at least 2)."""
@@ -284,11 +298,8 @@ def run_crm(args):
     e2e_s = time.perf_counter() - w0
     t.sync()
 
-    # max over ranks
-    times = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    ms_max, e2e_max = float(times[0]), float(times[1])
+    # max over ranks of the timings, sum of the active particle-steps
+    (ms_max, e2e_max), units = aggregate(world, [ms, e2e_s], n_active * args.steps, dev)
     if rank == 0:
         peaks, kind = _peaks()
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -327,14 +338,14 @@ def run_crm(args):
                      / (pair_ms * 1e-3) / 1e12 / fp32_peak) if pair_ms else None
         line = {
             "metric": METRIC,
-            "value": world * sc.n_fluid * args.steps / (ms_max * 1e-3),
+            "value": units / (ms_max * 1e-3),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_sph": sc.n_fluid, "n_active": n_active,
                        "n_bce": n_bce, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write outside the events)"},
-            "e2e": {"value": world * sc.n_fluid * e2e_steps / e2e_max, "unit": UNIT,
+            "e2e": {"value": units * e2e_steps / args.steps / e2e_max, "unit": UNIT,
                     "h2d_bytes_per_step": 13 * 8, "d2h_bytes_per_step": 6 * 8 + 13 * 8 + 4,
                     "loop": "set_body_motion -> step -> body_wrench + body_state (sync)"},
             "gpu_launches": sum(launches["launches"].values()),
