@@ -86,10 +86,59 @@ __device__ __forceinline__ void return_map(float s[6], const float sn[6], const 
 // velocity/stress slots hold the extrapolated marker state and whose density
 // slot holds rho0.  V_j = m / rho_j.
 
-constexpr int kPairBlock = 128;   // pair kernels: 7 blocks of 128 per SM (72 registers)
+constexpr int kPairBlock = 128;   // pair kernels: blocks of 128 threads
+constexpr int kPairLanes = 2;     // lanes per fluid particle in the pair kernels
 
-template <int MODE, bool FILTER>
-__global__ void __launch_bounds__(kPairBlock, 7)
+// Running sums of one particle's pairs.
+struct PairAcc {
+    float cont, mx, my, mz, avx, avy, avz;
+    float L[9];
+};
+
+// One pair (i, j) with r = x_i - x_j, 0 < |r| < 2h, added to the sums of i.
+__device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi, const float4 &ai,
+                                           const float2 &bi, const float4 &vj, const float4 &aj,
+                                           const float2 &bj, float rx, float ry, float rz,
+                                           float r2, PairAcc &A)
+{
+    const float rinv = rsqrtf(r2);
+    const float q = r2 * rinv * p.inv_h;
+    const float f = kernel_dw_over_r(q, rinv, p);
+    const float gx = f * rx, gy = f * ry, gz = f * rz;          // grad_i W_ij
+    const float Vj = __fdividef(p.m, vj.w);   // MUFU reciprocal: ~2 ulp
+    const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;   // u_ji
+    // continuity (F2)
+    A.cont = fmaf(Vj, ux * gx + uy * gy + uz * gz, A.cont);
+    // momentum (F3): (sigma_i + sigma_j) . grad W
+    const float sxx = ai.x + aj.x, syy = ai.y + aj.y, szz = ai.z + aj.z;
+    const float sxy = ai.w + aj.w, sxz = bi.x + bj.x, syz = bi.y + bj.y;
+    A.mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, A.mx);
+    A.my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, A.my);
+    A.mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, A.mz);
+    // velocity gradient (F2): L += V_j u_ji (x) grad W
+    const float vx = Vj * ux, vy = Vj * uy, vz = Vj * uz;
+    A.L[0] = fmaf(vx, gx, A.L[0]); A.L[1] = fmaf(vx, gy, A.L[1]); A.L[2] = fmaf(vx, gz, A.L[2]);
+    A.L[3] = fmaf(vy, gx, A.L[3]); A.L[4] = fmaf(vy, gy, A.L[4]); A.L[5] = fmaf(vy, gz, A.L[5]);
+    A.L[6] = fmaf(vz, gx, A.L[6]); A.L[7] = fmaf(vz, gy, A.L[7]); A.L[8] = fmaf(vz, gz, A.L[8]);
+    // artificial viscosity: v_ij . r_ij = -(u_ji . r_ij)
+    if (p.av_mode != CRM_AV_NONE) {
+        const float vr = -(ux * rx + uy * ry + uz * rz);
+        if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+            const float fac = __fdividef(2.0f * p.av_c * vr, (vi.w + vj.w) * (r2 + p.xi2));
+            A.avx = fmaf(fac, gx, A.avx);
+            A.avy = fmaf(fac, gy, A.avy);
+            A.avz = fmaf(fac, gz, A.avz);
+        }
+    }
+}
+
+// LANES lanes share particle i: each walks every LANES-th entry of its list and
+// the sums are combined by shuffles (more warps in flight for the gathers of a
+// grid that would otherwise fill each SM only partly).  FILTER (stage 1 with a
+// skin): the list walked is the skin list, and the pairs closer than 2h at y_n
+// are written, in list order, as the exact list for the rest of the step.
+template <int MODE, bool FILTER, int LANES>
+__global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
 k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
        const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err,
        const float4 *__restrict__ xref, int *__restrict__ gate)
@@ -98,11 +147,12 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
     __shared__ float4 lut[64];
     fill_shift_table(lut, p.cell);
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= __ldg(p.sizes)) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LANES, q = t % LANES;
+    const bool valid = i < __ldg(p.sizes);
     // Extended-Active particles (active domains) are read-only neighbours
-    const bool adv = pid == nullptr || !(pid[i] & kExtendedBit);
-    if (!adv) {
+    const bool adv = valid && (pid == nullptr || !(pid[i] & kExtendedBit));
+    if (valid && !adv && q == 0) {
         if (FILTER) io.out_n[i] = 0u;
         if (MODE == kStage1) {
             MID.pos[i] = S.pos[i];
@@ -115,90 +165,110 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
             out.dsA[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             out.dsB[i] = make_float2(0.f, 0.f);
         }
-        return;
     }
-    const float4 pi = S.pos[i];
-    const float4 vi = S.vel[i];
-    const float4 ai = S.sA[i];
-    const float2 bi = S.sB[i];
-    float cont = 0.f, mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
-    float L[9];
+    if (LANES == 1 && !adv) return;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pi = adv ? S.pos[i] : z4;
+    const float4 vi = adv ? S.vel[i] : z4;
+    const float4 ai = adv ? S.sA[i] : z4;
+    const float2 bi = adv ? S.sB[i] : make_float2(0.f, 0.f);
+    PairAcc A;
+    A.cont = A.mx = A.my = A.mz = A.avx = A.avy = A.avz = 0.f;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) L[k] = 0.f;
-    const int nn = (int)io.in_n[i];
-    const uint32_t *row = io.in + i;
+    for (int k = 0; k < 9; ++k) A.L[k] = 0.f;
+    const int nn = adv ? (int)io.in_n[i] : 0;
+    const uint32_t *row = io.in + (adv ? i : 0);
     int cnt = 0;
-    // the next list entry is fetched one iteration ahead; on an exact list the
-    // neighbour's whole state is gathered at once (one load round per
-    // iteration), on a skin list only after the distance test
-    uint32_t e_nx = nn > 0 ? __ldg(row) : 0u;
-    for (int k = 0; k < nn; ++k) {
-        const uint32_t e = e_nx;
-        if (k + 1 < nn) e_nx = __ldg(row + (size_t)(k + 1) * p.ell);
-        const uint32_t j = e & kIndexMask;
-        const float4 sh = lut[e >> kIndexBits];
-        const float4 pj = __ldg(&S.pos[j]);
-        float4 vj, aj;
-        float2 bj;
-        if (!FILTER) {
-            vj = __ldg(&S.vel[j]);
-            aj = __ldg(&S.sA[j]);
-            bj = __ldg(&S.sB[j]);
-        }
-        const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        if (!(r2 < p.four_h2)) continue;
-        if (FILTER) {
-            // stage 1 with a skin: the pairs closer than 2h now are the exact list
-            if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
-            ++cnt;
-            vj = __ldg(&S.vel[j]);
-            aj = __ldg(&S.sA[j]);
-            bj = __ldg(&S.sB[j]);
-        }
-        if (r2 == 0.0f) continue;
-        const float rinv = rsqrtf(r2);
-        const float q = r2 * rinv * p.inv_h;
-        const float f = kernel_dw_over_r(q, rinv, p);
-        const float gx = f * rx, gy = f * ry, gz = f * rz;          // grad_i W_ij
-        const float Vj = __fdividef(p.m, vj.w);   // MUFU reciprocal: ~2 ulp
-        const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;   // u_ji
-        // continuity (F2)
-        cont = fmaf(Vj, ux * gx + uy * gy + uz * gz, cont);
-        // momentum (F3): (sigma_i + sigma_j) . grad W
-        const float sxx = ai.x + aj.x, syy = ai.y + aj.y, szz = ai.z + aj.z;
-        const float sxy = ai.w + aj.w, sxz = bi.x + bj.x, syz = bi.y + bj.y;
-        mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, mx);
-        my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, my);
-        mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, mz);
-        // velocity gradient (F2): L += V_j u_ji (x) grad W
-        const float vx = Vj * ux, vy = Vj * uy, vz = Vj * uz;
-        L[0] = fmaf(vx, gx, L[0]); L[1] = fmaf(vx, gy, L[1]); L[2] = fmaf(vx, gz, L[2]);
-        L[3] = fmaf(vy, gx, L[3]); L[4] = fmaf(vy, gy, L[4]); L[5] = fmaf(vy, gz, L[5]);
-        L[6] = fmaf(vz, gx, L[6]); L[7] = fmaf(vz, gy, L[7]); L[8] = fmaf(vz, gz, L[8]);
-        // artificial viscosity: v_ij . r_ij = -(u_ji . r_ij)
-        if (p.av_mode != CRM_AV_NONE) {
-            const float vr = -(ux * rx + uy * ry + uz * rz);
-            if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-                const float fac = __fdividef(2.0f * p.av_c * vr, (vi.w + vj.w) * (r2 + p.xi2));
-                avx = fmaf(fac, gx, avx);
-                avy = fmaf(fac, gy, avy);
-                avz = fmaf(fac, gz, avz);
+    // the lane's next list entry is fetched one iteration ahead
+    uint32_t e_nx = q < nn ? __ldg(row + (size_t)q * p.ell) : 0u;
+    if (!FILTER || LANES == 1) {
+        // on an exact list the neighbour's whole state is gathered at once (one
+        // load round per iteration); on a skin list the rest follows the distance test
+        for (int k = q; k < nn; k += LANES) {
+            const uint32_t e = e_nx;
+            if (k + LANES < nn) e_nx = __ldg(row + (size_t)(k + LANES) * p.ell);
+            const uint32_t j = e & kIndexMask;
+            const float4 sh = lut[e >> kIndexBits];
+            const float4 pj = __ldg(&S.pos[j]);
+            float4 vj, aj;
+            float2 bj;
+            if (!FILTER) {
+                vj = __ldg(&S.vel[j]);
+                aj = __ldg(&S.sA[j]);
+                bj = __ldg(&S.sB[j]);
             }
+            const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < p.four_h2)) continue;
+            if (FILTER) {
+                if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
+                ++cnt;
+                vj = __ldg(&S.vel[j]);
+                aj = __ldg(&S.sA[j]);
+                bj = __ldg(&S.sB[j]);
+            }
+            if (r2 == 0.0f) continue;
+            pair_terms(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
         }
+    } else {
+        // filtering with a lane group: warp-uniform rounds, in each of which the
+        // group's lanes test consecutive candidates and place the kept ones by ballot
+        const int rounds = __reduce_max_sync(0xffffffffu, (nn + LANES - 1) / LANES);
+        const int lane = threadIdx.x & 31;
+        for (int r = 0; r < rounds; ++r) {
+            const int k = r * LANES + q;
+            const uint32_t e = e_nx;
+            if (k + LANES < nn) e_nx = __ldg(row + (size_t)(k + LANES) * p.ell);
+            bool keep = false;
+            float rx = 0.f, ry = 0.f, rz = 0.f, r2 = 0.f;
+            uint32_t j = 0;
+            if (k < nn) {
+                j = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pj = __ldg(&S.pos[j]);
+                rx = pi.x - pj.x - sh.x; ry = pi.y - pj.y - sh.y; rz = pi.z - pj.z - sh.z;
+                r2 = rx * rx + ry * ry + rz * rz;
+                keep = r2 < p.four_h2;
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, keep);
+            const unsigned g = (b >> (lane & ~(LANES - 1))) & ((1u << LANES) - 1u);
+            const int at = cnt + __popc(g & ((1u << q) - 1u));
+            if (keep && at < p.maxnb) io.out[(size_t)at * p.ell + i] = e;
+            cnt += __popc(g);
+            if (!keep || r2 == 0.0f) continue;
+            const float4 vj = __ldg(&S.vel[j]);
+            const float4 aj = __ldg(&S.sA[j]);
+            const float2 bj = __ldg(&S.sB[j]);
+            pair_terms(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
+        }
+    }
+    if (LANES > 1) {
+#pragma unroll
+        for (int o = 1; o < LANES; o <<= 1) {
+            A.cont += __shfl_xor_sync(0xffffffffu, A.cont, o);
+            A.mx += __shfl_xor_sync(0xffffffffu, A.mx, o);
+            A.my += __shfl_xor_sync(0xffffffffu, A.my, o);
+            A.mz += __shfl_xor_sync(0xffffffffu, A.mz, o);
+            A.avx += __shfl_xor_sync(0xffffffffu, A.avx, o);
+            A.avy += __shfl_xor_sync(0xffffffffu, A.avy, o);
+            A.avz += __shfl_xor_sync(0xffffffffu, A.avz, o);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) A.L[k] += __shfl_xor_sync(0xffffffffu, A.L[k], o);
+        }
+        if (!adv || q != 0) return;
     }
     if (FILTER) {
         if (cnt > p.maxnb) atomicOr(err, ERR_CAPACITY);
         io.out_n[i] = (uint32_t)min(cnt, p.maxnb);
     }
     const float rinv_i = 1.0f / vi.w;
-    const float drho = -vi.w * cont;
-    const float dux = mx * rinv_i + p.gx + avx;
-    const float duy = my * rinv_i + p.gy + avy;
-    const float duz = mz * rinv_i + p.gz + avz;
+    const float drho = -vi.w * A.cont;
+    const float dux = A.mx * rinv_i + p.gx + A.avx;
+    const float duy = A.my * rinv_i + p.gy + A.avy;
+    const float duz = A.mz * rinv_i + p.gz + A.avz;
     const float si[6] = {ai.x, ai.y, ai.z, ai.w, bi.x, bi.y};
     float ds[6];
-    stress_rate(L, si, p.G, p.K, ds);
+    stress_rate(A.L, si, p.G, p.K, ds);
     if (MODE == kEval) {
         out.drho[i] = drho;
         out.du[i] = make_float4(dux, duy, duz, 0.f);
@@ -311,29 +381,33 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
                  RateOut out, int *err, const float4 *xref, int *gate, cudaStream_t st,
                  const uint32_t *sk_nbr, const uint32_t *sk_nnb)
 {
-    const unsigned g = grid_for(p.capF, kPairBlock);
+    // filtering kernels keep one lane per particle (the lane group's ballot per
+    // candidate costs more than the extra warps gain); the others take kPairLanes
+    constexpr int LN = kPairLanes;
+    const unsigned g = grid_for((int64_t)p.capF * LN, kPairBlock);
+    const unsigned g1 = grid_for(p.capF, kPairBlock);
     if (mode == kStage1 && sk_nbr != nullptr) {
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_pair<kStage1, true><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                     nullptr, nullptr);
+        k_pair<kStage1, true, 1><<<g1, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                            err, nullptr, nullptr);
         return;
     }
     if (mode == kEval && sk_nbr != nullptr) {
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_pair<kEval, true><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                   nullptr, nullptr);
+        k_pair<kEval, true, 1><<<g1, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                          nullptr, nullptr);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (mode == kStage1)
-        k_pair<kStage1, false><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                      nullptr, nullptr);
+        k_pair<kStage1, false, LN><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                             err, nullptr, nullptr);
     else if (mode == kStage2)
-        k_pair<kStage2, false><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                      xref, gate);
+        k_pair<kStage2, false, LN><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                             err, xref, gate);
     else
-        k_pair<kEval, false><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                    nullptr, nullptr);
+        k_pair<kEval, false, LN><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                           nullptr, nullptr);
 }
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
