@@ -56,7 +56,9 @@ extern "C" {
 #define CRM_AV_BILATERAL   1  /* Eq. artificial_viscosity_bilateral */
 #define CRM_AV_UNILATERAL  2  /* Eq. artificial_viscosity_unilateral */
 
-#define CRM_KERNEL_CUBIC   0  /* cubic spline, support 2h (Sec. 3.1) */
+#define CRM_KERNEL_CUBIC    0  /* cubic spline, support 2h (Sec. 3.1) */
+#define CRM_KERNEL_WENDLAND 1  /* quintic Wendland, support 2h (Sec. 3.1):
+                                  W = 21/(16 pi h^3) (1 - q/2)^4 (2q + 1) */
 
 #define CRM_DOF_X 1
 #define CRM_DOF_Y 2
@@ -74,7 +76,7 @@ typedef struct crm_params {
     double I0, grain_d;    /* mu(I) constants: I0 and particle diameter d (m) */
     double cohesion;       /* cohesive intercept c of the yield cone, Pa, >= 0 */
     double d0, h;          /* initial spacing and smoothing length (m); cells are 2h */
-    int32_t kernel;        /* CRM_KERNEL_CUBIC */
+    int32_t kernel;        /* CRM_KERNEL_CUBIC or CRM_KERNEL_WENDLAND */
     int32_t av_mode;       /* CRM_AV_* */
     double av_gamma;       /* gamma_a of the artificial viscosity */
     double av_xi2_over_h2; /* xi^2 / h^2 in the viscosity denominator (default 0.01) */

@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("grain_d", C.c_double), ("cohesion", C.c_double),
                 ("d0", C.c_double), ("h", C.c_double),
                 ("av_mode", C.c_int), ("av_gamma", C.c_double), ("av_xi2_over_h2", C.c_double),
-                ("gravity", C.c_double * 3)]
+                ("gravity", C.c_double * 3), ("kernel", C.c_int)]
 
 
 def make_params(p: dict) -> Params:
@@ -56,6 +56,7 @@ def make_params(p: dict) -> Params:
     q.av_mode = int(p["av_mode"])
     for k in range(3):
         q.gravity[k] = float(p["gravity"][k])
+    q.kernel = int(p.get("kernel", 0))
     return q
 
 
@@ -73,6 +74,7 @@ def lib():
             L.orc_kernel_w.argtypes = [C.c_double, C.c_double]
             L.orc_kernel_dwdr.restype = C.c_double
             L.orc_kernel_dwdr.argtypes = [C.c_double, C.c_double]
+            L.orc_kernel_eval.argtypes = [C.c_int, C.c_double, C.c_double, d]
             L.orc_marker_kinematics.argtypes = [C.c_int64, i32, d, d, d, d, C.c_double, d, d, d]
             for nm in ("orc_neighbors_brute", "orc_neighbors_cells"):
                 f = getattr(L, nm)
@@ -109,6 +111,16 @@ def kernel_w(r: float, h: float) -> float:
 
 def kernel_dwdr(r: float, h: float) -> float:
     return lib().orc_kernel_dwdr(float(r), float(h))
+
+
+KERNEL_CUBIC, KERNEL_WENDLAND = 0, 1
+
+
+def kernel_eval(kind: int, r: float, h: float):
+    """(W, dW/dr) of kernel `kind` (0 cubic spline, 1 quintic Wendland)."""
+    out = np.zeros(2)
+    lib().orc_kernel_eval(int(kind), float(r), float(h), out)
+    return float(out[0]), float(out[1])
 
 
 def neighbors(x_all: np.ndarray, nf: int, h: float, mode: str = "cells",

@@ -41,6 +41,7 @@ typedef struct {
     int av_mode; /* 0 none, 1 bilateral (Eq. artificial_viscosity_bilateral), 2 unilateral */
     double av_gamma, av_xi2_over_h2;
     double gravity[3];
+    int kernel; /* 0 cubic spline, 1 quintic Wendland */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -79,12 +80,50 @@ double orc_kernel_dwdr(double r, double h)
     return 0.0;
 }
 
+/* Quintic Wendland kernel (the paper's second kernel choice, Sec. 3.1; support
+ * 2h like the spline).  Reading: the 3-D Wendland C2 function of radius 2h,
+ * W = 21/(16 pi h^3) (1 - q/2)^4 (2q + 1), whose derivative is
+ * dW/dq = -5 (21/(16 pi h^3)) q (1 - q/2)^3. */
+static double wendland_w(double r, double h)
+{
+    const double q = r / h;
+    if (q >= 2.0) return 0.0;
+    const double t = 1.0 - 0.5 * q;
+    return 21.0 / (16.0 * M_PI * h * h * h) * t * t * t * t * (2.0 * q + 1.0);
+}
+
+static double wendland_dwdr(double r, double h)
+{
+    const double q = r / h;
+    if (q >= 2.0) return 0.0;
+    const double t = 1.0 - 0.5 * q;
+    return -5.0 * 21.0 / (16.0 * M_PI * h * h * h * h) * q * t * t * t;
+}
+
+/* Kernel of the run: W(r) and dW/dr for p->kernel. */
+static double kernel_w(const orc_params *p, double r)
+{
+    return p->kernel == 1 ? wendland_w(r, p->h) : orc_kernel_w(r, p->h);
+}
+
+static double kernel_dwdr(const orc_params *p, double r)
+{
+    return p->kernel == 1 ? wendland_dwdr(r, p->h) : orc_kernel_dwdr(r, p->h);
+}
+
+/* W and dW/dr of kernel `kind` (0 cubic, 1 Wendland) at r, for the tests. */
+void orc_kernel_eval(int kind, double r, double h, double out[2])
+{
+    out[0] = kind == 1 ? wendland_w(r, h) : orc_kernel_w(r, h);
+    out[1] = kind == 1 ? wendland_dwdr(r, h) : orc_kernel_dwdr(r, h);
+}
+
 /* grad_i W_ij = W'(r) (x_i - x_j) / r, zero when r = 0. */
-static void kernel_grad(const double rij[3], double h, double g[3])
+static void kernel_grad(const orc_params *p, const double rij[3], double g[3])
 {
     const double r = sqrt(rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2]);
     if (r == 0.0) { g[0] = g[1] = g[2] = 0.0; return; }
-    const double f = orc_kernel_dwdr(r, h) / r;
+    const double f = kernel_dwdr(p, r) / r;
     g[0] = f * rij[0]; g[1] = f * rij[1]; g[2] = f * rij[2];
 }
 
@@ -331,7 +370,7 @@ void orc_bce(const orc_params *p, int64_t nf, int64_t nm, const double *xf,
                 const int64_t f = list[k];
                 double d[3];
                 for (int c = 0; c < 3; ++c) d[c] = xm[3 * a + c] - xf[3 * f + c];
-                const double W = orc_kernel_w(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), h);
+                const double W = kernel_w(p, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
                 w += W;
                 for (int c = 0; c < 3; ++c) su[c] += uf[3 * f + c] * W;
                 for (int c = 0; c < 6; ++c) ss[c] += sf[6 * f + c] * W;
@@ -416,10 +455,11 @@ static int av_factor(const orc_params *p, double cs, double m, const double vij[
 static int g_scale_conditioning = 0;
 void orc_set_scale_conditioning(int on) { g_scale_conditioning = on; }
 
-static double kernel_dw_condition(double r, double h)
+static double kernel_dw_condition(const orc_params *p, double r)
 {
-    const double q = r / h;
+    const double q = r / p->h;
     if (q <= 0.0 || q >= 2.0) return 0.0;
+    if (p->kernel == 1) return fabs(2.0 * (1.0 - 2.0 * q) / (2.0 - q));
     if (q < 1.0) return fabs((-3.0 + 4.5 * q) / (-3.0 + 2.25 * q));
     return 2.0 * q / (2.0 - q);
 }
@@ -477,10 +517,10 @@ void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
                 uji[c] = uj[c] - ui[c];
                 vij[c] = ui[c] - uj[c];
             }
-            kernel_grad(rij, h, g);
+            kernel_grad(p, rij, g);
             const double Vj = m / rhoj;
             const double cw = g_scale_conditioning
-                ? 1.0 + kernel_dw_condition(sqrt(rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2]), h)
+                ? 1.0 + kernel_dw_condition(p, sqrt(rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2]))
                 : 1.0;
             sym_to_full(si, si3);
             sym_to_full(sj, sj3);

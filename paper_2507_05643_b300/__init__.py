@@ -30,6 +30,7 @@ STATUS = {0: "CRM_OK", -1: "CRM_EINVAL", -2: "CRM_ENOMEM", -3: "CRM_ECAPACITY",
           -4: "CRM_EESCAPED", -5: "CRM_ENONFINITE", -6: "CRM_ETIMEOUT", -7: "CRM_ECUDA",
           -8: "CRM_ESTATE"}
 AV_NONE, AV_BILATERAL, AV_UNILATERAL = 0, 1, 2
+KERNEL_CUBIC, KERNEL_WENDLAND = 0, 1
 
 
 class CrmError(RuntimeError):
@@ -161,7 +162,7 @@ def params_from_dict(d: dict, domain_min, domain_max) -> Params:
               "av_gamma", "av_xi2_over_h2", "skin"):
         if k in d and d[k] is not None:
             setattr(p, k, float(d[k]))
-    for k in ("av_mode", "ps_freq", "max_neighbors"):
+    for k in ("av_mode", "ps_freq", "max_neighbors", "kernel"):
         if k in d:
             setattr(p, k, int(d[k]))
     for k in range(3):

@@ -172,7 +172,8 @@ int validate(const crm_params *p, std::string &why)
     if (!(p->cohesion >= 0)) return bad("cohesion must be >= 0");
     if (!(p->I0 > 0) || !(p->grain_d > 0)) return bad("I0, grain_d must be > 0");
     if (!(p->d0 > 0) || !(p->h > 0)) return bad("d0, h must be > 0");
-    if (p->kernel != CRM_KERNEL_CUBIC) return bad("kernel must be CRM_KERNEL_CUBIC");
+    if (p->kernel != CRM_KERNEL_CUBIC && p->kernel != CRM_KERNEL_WENDLAND)
+        return bad("kernel must be CRM_KERNEL_CUBIC or CRM_KERNEL_WENDLAND");
     if (p->av_mode < 0 || p->av_mode > 2) return bad("av_mode must be 0, 1 or 2");
     if (!(p->av_gamma >= 0) || !(p->av_xi2_over_h2 > 0)) return bad("av_gamma >= 0, av_xi2_over_h2 > 0");
     if (!finite_all(p->gravity, 3)) return bad("gravity must be finite");
@@ -209,8 +210,15 @@ int make_devparams(crm_terrain *t)
     d.inv_h = (float)(1.0 / P.h);
     d.four_h2 = (float)(4.0 * P.h * P.h);
     d.cell = (float)cell;
-    d.kw = (float)(1.0 / (pi * P.h * P.h * P.h));
-    d.kdw = (float)(1.0 / (pi * P.h * P.h * P.h * P.h));
+    d.kernel = P.kernel;
+    if (P.kernel == CRM_KERNEL_WENDLAND) {
+        const double a = 21.0 / (16.0 * pi * P.h * P.h * P.h);
+        d.kw = (float)a;
+        d.kdw = (float)(-5.0 * a / (P.h * P.h));   // (dW/dr) / r = kdw (1 - q/2)^3
+    } else {
+        d.kw = (float)(1.0 / (pi * P.h * P.h * P.h));
+        d.kdw = (float)(1.0 / (pi * P.h * P.h * P.h * P.h));
+    }
     d.m = (float)m;
     d.rho0 = (float)P.rho0;
     d.G = (float)Gm;

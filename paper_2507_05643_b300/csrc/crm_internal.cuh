@@ -39,7 +39,9 @@ constexpr int kBlock = 256;
 struct DevParams {
     // kernel and material (Sec. 2.1-2.3)
     float h, inv_h, four_h2, cell;        // cell = 2h (Sec. 3.1)
-    float kw, kdw;                        // 1/(pi h^3), 1/(pi h^4)
+    int kernel;                           // CRM_KERNEL_CUBIC / CRM_KERNEL_WENDLAND
+    float kw, kdw;                        // cubic: 1/(pi h^3), 1/(pi h^4); Wendland:
+                                          // a = 21/(16 pi h^3), -5 a / h^2
     float m, rho0, G, K;                  // particle mass rho0 d0^3, moduli
     float av_c, xi2;                      // gamma_a h c_s m, xi^2
     int av_mode;
@@ -122,6 +124,11 @@ struct StageArrays {
 // Cubic spline (Monaghan M4), 3-D normalisation 1/(pi h^3), support 2h.
 __device__ __forceinline__ float kernel_w(float q, const DevParams &p)
 {
+    if (p.kernel == CRM_KERNEL_WENDLAND) {
+        // quintic Wendland: a (1 - q/2)^4 (2q + 1)
+        const float t = fmaxf(1.0f - 0.5f * q, 0.0f), t2 = t * t;
+        return p.kw * t2 * t2 * fmaf(2.0f, q, 1.0f);
+    }
     if (q < 1.0f) return p.kw * (1.0f + q * q * (0.75f * q - 1.5f));
     const float t = 2.0f - q;
     return q < 2.0f ? 0.25f * p.kw * t * t * t : 0.0f;
@@ -130,6 +137,11 @@ __device__ __forceinline__ float kernel_w(float q, const DevParams &p)
 // (dW/dr) / r; q < 2 is the caller's guarantee.
 __device__ __forceinline__ float kernel_dw_over_r(float q, float rinv, const DevParams &p)
 {
+    if (p.kernel == CRM_KERNEL_WENDLAND) {
+        // dW/dr = -5 a q (1 - q/2)^3 / h, so (dW/dr) / r = -5 a (1 - q/2)^3 / h^2
+        const float t = 1.0f - 0.5f * q;
+        return p.kdw * t * t * t;
+    }
     float d;
     if (q < 1.0f) {
         d = p.kdw * q * (2.25f * q - 3.0f);

@@ -93,7 +93,7 @@ def default_params(d0: float = 0.01, **over) -> Dict[str, object]:
         d0=d0, h=1.2 * d0,
         av_mode=2, av_gamma=0.02, av_xi2_over_h2=0.01,
         gravity=(0.0, 0.0, -G_EARTH),
-        ps_freq=1, max_neighbors=96,
+        ps_freq=1, max_neighbors=96, kernel=0,
     )
     p.update(over)
     if p["mu_2"] is None:

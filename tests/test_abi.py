@@ -41,7 +41,8 @@ def test_default_params_match_paper_constants():
 
 
 @pytest.mark.parametrize("field, value", [("rho0", 0.0), ("nu", 0.5), ("ps_freq", 0),
-                                          ("max_neighbors", 4), ("h", -1.0), ("av_mode", 3)])
+                                          ("max_neighbors", 4), ("h", -1.0), ("av_mode", 3),
+                                          ("kernel", 2)])
 def test_create_rejects_bad_params(field, value):
     import paper_2507_05643_b300 as crm
     p = crm.default_params()

@@ -63,6 +63,57 @@ def test_kernel_gradient_moment_identity():
     assert val == pytest.approx(-1.0, abs=1e-10)
 
 
+# Quintic Wendland kernel (the paper's second kernel, Sec. 3.1), pinned against
+# Wendland's own construction: psi_{3,1}(s) = int_s^1 t psi_{3,0}(t) dt with
+# psi_{3,0}(t) = (1 - t)^3, s = r / (2h), evaluated by quadrature.
+def _wendland_shape(q):
+    s = q / 2.0
+    if s >= 1.0:
+        return 0.0
+    val, _ = integrate.quad(lambda t: t * (1.0 - t) ** 3, s, 1.0, epsabs=1e-16, epsrel=1e-13)
+    return val
+
+
+def test_wendland_equals_its_defining_integral():
+    w0 = oracle.kernel_eval(oracle.KERNEL_WENDLAND, 0.0, H)[0]
+    s0 = _wendland_shape(0.0)
+    for q in np.linspace(0.0, 2.4, 121):
+        w = oracle.kernel_eval(oracle.KERNEL_WENDLAND, q * H, H)[0]
+        assert w == pytest.approx(w0 * _wendland_shape(q) / s0, rel=1e-10, abs=1e-9)
+
+
+def test_wendland_normalised_compact_and_smooth():
+    W = lambda r: oracle.kernel_eval(oracle.KERNEL_WENDLAND, r, H)
+    val, _ = integrate.quad(lambda r: 4 * math.pi * r * r * W(r)[0], 0, 2 * H,
+                            epsabs=1e-14, epsrel=1e-13)
+    assert val == pytest.approx(1.0, abs=1e-10)
+    mom, _ = integrate.quad(lambda r: 4 * math.pi / 3 * r ** 3 * W(r)[1], 0, 2 * H,
+                            epsabs=1e-14, epsrel=1e-13)
+    assert mom == pytest.approx(-1.0, abs=1e-10)
+    assert W(2 * H) == (0.0, 0.0) and W(3 * H) == (0.0, 0.0)
+    assert W(0.0)[1] == 0.0                       # C2 at the origin: no slope
+    eps = 1e-7 * H
+    for q in (0.05, 0.3, 0.77, 1.0, 1.4, 1.9):
+        r = q * H
+        fd = (W(r + eps)[0] - W(r - eps)[0]) / (2 * eps)
+        assert W(r)[1] == pytest.approx(fd, rel=1e-6)
+    # the cubic spline is what kernel 0 selects
+    for q in (0.2, 1.3):
+        assert oracle.kernel_eval(oracle.KERNEL_CUBIC, q * H, H) == (
+            oracle.kernel_w(q * H, H), oracle.kernel_dwdr(q * H, H))
+
+
+def test_wendland_rates_conserve_momentum():
+    sc = scenes.lattice_only(seed=17, n=10, av_mode=1, av_gamma=0.5, kernel=1)
+    sc.params["gravity"] = (0.0, 0.0, 0.0)
+    st = oracle.State(sc)
+    _, du, _, _, _, _, _ = st.eval_rates()
+    assert np.all(np.abs(du.sum(axis=0)) <= 1e-13 * np.abs(du).sum(axis=0))
+    st_c = oracle.State(scenes.lattice_only(seed=17, n=10, av_mode=1, av_gamma=0.5))
+    _, du_c, _, _, _, _, _ = st_c.eval_rates()
+    assert np.max(np.abs(du - du_c)) > 1e-3 * np.max(np.abs(du_c))   # the kernel switch is live
+
+
 def _lattice_constants(h_over_d0=1.2):
     """Interior lattice sums with V = d0^3 from the B-spline form:
     sum_j V W_ij (partition of unity) and M = sum_j V (x_j - x_i) (x) grad_i W_ij."""
