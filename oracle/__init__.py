@@ -92,7 +92,7 @@ def lib():
                                               C.c_double, C.c_int64]
             L.orc_step.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, d, d, d, d,
                                    C.c_int64, i32, d, C.c_int64, d, d, d, i32, d, d, i64, i32,
-                                   vp, vp]
+                                   vp, vp, d, d]
             _lib = L
     return _lib
 
@@ -150,13 +150,19 @@ class Bodies:
         self.twist = np.zeros((max(nb, 1), 6))
         self.mass = np.ones(max(nb, 1))
         self.dof = np.zeros(max(nb, 1), np.int32)
-        self.acc = np.zeros((max(nb, 1), 3))
+        self.acc = np.zeros((max(nb, 1), 6))       # linear, angular acceleration
         self.wrench = np.zeros((max(nb, 1), 6))
+        self.inertia = np.ones((max(nb, 1), 3))     # principal moments, body frame
+        self.load = np.zeros((max(nb, 1), 6))       # external force, torque
         for b, body in enumerate(scene.bodies):
             self.pose[b] = body.pose
             self.twist[b] = body.twist
             self.mass[b] = body.mass
             self.dof[b] = body.dof_mask
+            if getattr(body, "inertia", None) is not None:
+                self.inertia[b] = body.inertia
+            if getattr(body, "load", None) is not None:
+                self.load[b] = body.load
 
 
 def marker_arrays(scene) -> Tuple[np.ndarray, np.ndarray]:
@@ -309,7 +315,7 @@ class State:
                        self.nm, self.mbody if self.nm else np.zeros(1, np.int32),
                        self.mxloc if self.nm else np.zeros((1, 3)), b.n, b.pose, b.twist,
                        b.mass, b.dof, b.acc, b.wrench, self.off, lst,
-                       _ptr(self.integrate), _ptr(self.include))
+                       _ptr(self.integrate), _ptr(self.include), b.inertia, b.load)
         self.step_index += 1
         self.time += dt
 

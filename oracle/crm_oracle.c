@@ -180,8 +180,10 @@ static void cross(const double a[3], const double b[3], double o[3])
 }
 
 /* Marker position, rigid velocity u_body = v + w x (x_a - x_c) and rigid
- * acceleration a_body = a_c + w x (w x (x_a - x_c)) at stage offset tau.
- * body[a] < 0 marks a fixed wall marker (xloc is then its world position). */
+ * acceleration a_body = a_c + alpha x (x_a - x_c) + w x (w x (x_a - x_c)) at
+ * stage offset tau (bacc: 6 per body, a_c then alpha, the accelerations of the
+ * last body update).  body[a] < 0 marks a fixed wall marker (xloc is then its
+ * world position). */
 void orc_marker_kinematics(int64_t nm, const int32_t *body, const double *xloc,
                            const double *pose, const double *twist, const double *bacc,
                            double tau, double *xm, double *um, double *am)
@@ -196,16 +198,20 @@ void orc_marker_kinematics(int64_t nm, const int32_t *body, const double *xloc,
             }
             continue;
         }
-        double xc[3], q[4], rl[3], w[3], wr[3], wwr[3];
+        double xc[3], q[4], rl[3], w[3], al[3], wr[3], wwr[3], ar[3];
         body_pose_at(pose + 7 * b, twist + 6 * b, tau, xc, q);
         quat_rotate(q, xloc + 3 * a, rl);
-        for (int k = 0; k < 3; ++k) w[k] = twist[6 * b + 3 + k];
+        for (int k = 0; k < 3; ++k) {
+            w[k] = twist[6 * b + 3 + k];
+            al[k] = bacc[6 * b + 3 + k];
+        }
         cross(w, rl, wr);
         cross(w, wr, wwr);
+        cross(al, rl, ar);
         for (int k = 0; k < 3; ++k) {
             xm[3 * a + k] = xc[k] + rl[k];
             um[3 * a + k] = twist[6 * b + k] + wr[k];
-            am[3 * a + k] = bacc[3 * b + k] + wwr[k];
+            am[3 * a + k] = bacc[6 * b + k] + ar[k] + wwr[k];
         }
     }
 }
@@ -676,9 +682,13 @@ int64_t orc_capacity_policy(int64_t need, int64_t cap, int64_t step, double G, d
  *   4. x += dt u_mid, u += dt du_mid, rho += dt drho_mid, sigma* = sigma + dt dsigma_mid
  *   5. return map on sigma* (Sec. 2.3: only at the end of the step)
  *   6. body wrench F = sum m a_a, T = sum (x_a - x_c) x m a_a at the midpoint
- *   7. body update, symplectic Euler on the free linear DOFs:
- *      v += dt (F/m + g), x_c += dt v; prescribed DOFs move with their velocity;
- *      orientation advanced by dt w.
+ *   7. body update, symplectic Euler on the free DOFs (reading: the paper leaves
+ *      the rigid-body side to the multibody solver; here the centre is the
+ *      centre of mass and the load is the soil wrench plus an external one):
+ *      v += dt (F/m + g), x_c += dt v;
+ *      w += dt I_w^-1 (T - w x I_w w), I_w = R diag(I) R^T (principal moments I
+ *      in the body frame, R the orientation at t_n), only the free components;
+ *      prescribed DOFs keep their velocity; orientation advanced by dt w.
  * `integrate` (nullable, per fluid particle) marks the particles whose state is
  * advanced (Active); the others only serve as neighbours (Extended-Active) or
  * are absent from the lists (Inactive). */
@@ -687,7 +697,7 @@ void orc_step(const orc_params *p, double dt, int64_t nf, double *x, double *u,
               const double *mxloc, int64_t nb, double *pose, double *twist,
               const double *mass, const int32_t *dof, double *bacc, double *wrench,
               const int64_t *offset, const int32_t *list, const uint8_t *integrate,
-              const uint8_t *include)
+              const uint8_t *include, const double *inertia, const double *load)
 {
     const double m = particle_mass(p);
     double *xm = (double *)calloc(3 * nm + 1, sizeof(double));
@@ -761,13 +771,46 @@ void orc_step(const orc_params *p, double dt, int64_t nf, double *x, double *u,
     }
     /* body update */
     for (int64_t b = 0; b < nb; ++b) {
+        double F[3], T[3];
+        for (int c = 0; c < 3; ++c) {
+            F[c] = wrench[6 * b + c] + (load ? load[6 * b + c] : 0.0);
+            T[c] = wrench[6 * b + 3 + c] + (load ? load[6 * b + 3 + c] : 0.0);
+        }
+        double wdot[3] = {0.0, 0.0, 0.0};
+        if (dof[b] & (7 << 3)) {
+            /* Euler's equations in the world frame with the orientation at t_n */
+            const double *w = twist + 6 * b + 3;
+            double Rm[3][3];
+            for (int c = 0; c < 3; ++c) {
+                double e[3] = {0.0, 0.0, 0.0}, col[3];
+                e[c] = 1.0;
+                quat_rotate(pose + 7 * b + 3, e, col);
+                for (int r = 0; r < 3; ++r) Rm[r][c] = col[r];
+            }
+            double wb[3], Lb[3], L[3], g[3], rhs[3], rb[3];
+            for (int r = 0; r < 3; ++r)   /* w in the body frame: R^T w */
+                wb[r] = Rm[0][r] * w[0] + Rm[1][r] * w[1] + Rm[2][r] * w[2];
+            for (int r = 0; r < 3; ++r) Lb[r] = inertia[3 * b + r] * wb[r];
+            for (int r = 0; r < 3; ++r) L[r] = Rm[r][0] * Lb[0] + Rm[r][1] * Lb[1] + Rm[r][2] * Lb[2];
+            cross(w, L, g);
+            for (int r = 0; r < 3; ++r) rhs[r] = T[r] - g[r];
+            for (int r = 0; r < 3; ++r)   /* I_w^-1 rhs = R diag(1/I) R^T rhs */
+                rb[r] = (Rm[0][r] * rhs[0] + Rm[1][r] * rhs[1] + Rm[2][r] * rhs[2]) / inertia[3 * b + r];
+            for (int r = 0; r < 3; ++r) wdot[r] = Rm[r][0] * rb[0] + Rm[r][1] * rb[1] + Rm[r][2] * rb[2];
+        }
         for (int c = 0; c < 3; ++c) {
             if (dof[b] & (1 << c)) {
-                const double acc = wrench[6 * b + c] / mass[b] + p->gravity[c];
+                const double acc = F[c] / mass[b] + p->gravity[c];
                 twist[6 * b + c] += dt * acc;
-                bacc[3 * b + c] = acc;
+                bacc[6 * b + c] = acc;
             } else {
-                bacc[3 * b + c] = 0.0;
+                bacc[6 * b + c] = 0.0;
+            }
+            if (dof[b] & (8 << c)) {
+                twist[6 * b + 3 + c] += dt * wdot[c];
+                bacc[6 * b + 3 + c] = wdot[c];
+            } else {
+                bacc[6 * b + 3 + c] = 0.0;
             }
             pose[7 * b + c] += dt * twist[6 * b + c];
         }

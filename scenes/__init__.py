@@ -30,6 +30,7 @@ G_EARTH = 9.81
 
 # Activity / body constants shared by the generator and its users.
 DOF_X, DOF_Y, DOF_Z = 1, 2, 4
+DOF_RX, DOF_RY, DOF_RZ = 8, 16, 32
 
 
 @dataclasses.dataclass
@@ -38,7 +39,10 @@ class Body:
     pose: np.ndarray                   # (7,) x, y, z, qw, qx, qy, qz
     twist: np.ndarray                  # (6,) vx, vy, vz, wx, wy, wz (world frame)
     mass: float
-    dof_mask: int                      # bit k set: linear DOF k integrates (x=1, y=2, z=4)
+    dof_mask: int                      # bit k set: linear DOF k integrates (x=1, y=2, z=4);
+                                       # bits 3-5: angular DOF k integrates (x=8, y=16, z=32)
+    inertia: Optional[np.ndarray] = None   # (3,) principal moments in the body frame
+    load: Optional[np.ndarray] = None      # (6,) external force, torque about the centre
 
 
 @dataclasses.dataclass
@@ -78,7 +82,9 @@ class Scene:
             self, x=self.x.copy(), u=self.u.copy(), sig=self.sig.copy(), rho=self.rho.copy(),
             fixed=self.fixed.copy(),
             bodies=[dataclasses.replace(b, markers_local=b.markers_local.copy(),
-                                        pose=b.pose.copy(), twist=b.twist.copy())
+                                        pose=b.pose.copy(), twist=b.twist.copy(),
+                                        inertia=None if b.inertia is None else b.inertia.copy(),
+                                        load=None if b.load is None else b.load.copy())
                     for b in self.bodies],
             boxes=[dataclasses.replace(bx) for bx in self.boxes],
             params=dict(self.params))

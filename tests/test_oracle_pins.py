@@ -455,6 +455,92 @@ def test_marker_kinematics_derivatives():
     assert np.allclose((xp - 2 * x0 + xm_) / e ** 2, a0, rtol=1e-4, atol=1e-4)
 
 
+# 6-DOF bodies: free angular DOFs integrate I w' = T - w x I w (world frame,
+# I_w = R diag(I) R^T) with symplectic Euler; external load added to the soil's.
+def _lone_body(pose, twist, dof, inertia, load, mass=2.0):
+    sc = scenes.lattice_only(seed=0, n=1, random_state=False)
+    wm = np.array([[0.05, 0.0, 0.0], [0.0, 0.04, 0.01]])   # far from the one SPH particle
+    sc.bodies = [scenes.Body(wm, np.asarray(pose, float), np.asarray(twist, float), mass, dof,
+                             inertia=np.asarray(inertia, float), load=np.asarray(load, float))]
+    return sc
+
+
+def test_torque_spins_up_a_spherical_body_linearly():
+    T, I, w0, dt, n = 0.3, 2.0, 0.5, 1e-3, 40
+    sc = _lone_body([5, 5, 5, 1, 0, 0, 0], [0, 0, 0, 0, 0, w0], scenes.DOF_RZ, [I, I, I],
+                    [0, 0, 0, 0, 0, T])
+    st = oracle.State(sc)
+    st.run(n, dt=dt)
+    w = [w0 + k * dt * T / I for k in range(1, n + 1)]
+    assert st.bodies.twist[0, 5] == pytest.approx(w[-1], abs=1e-14)
+    assert np.all(st.bodies.twist[0, 3:5] == 0.0)
+    th = dt * sum(w)                                   # orientation follows the updated w
+    q = st.bodies.pose[0, 3:]
+    assert abs(q[0]) == pytest.approx(math.cos(th / 2), abs=1e-12)
+    assert abs(q[3]) == pytest.approx(math.sin(th / 2), abs=1e-12)
+    assert st.bodies.acc[0, 5] == pytest.approx(T / I, abs=1e-14)
+
+
+def test_free_rotation_step_follows_euler_equations_in_the_body_frame():
+    from scipy.spatial.transform import Rotation
+    q = np.array([0.8, 0.3, -0.4, 0.2])
+    q /= np.linalg.norm(q)
+    I = np.array([1.0, 2.5, 4.0])
+    w = np.array([0.7, -1.1, 0.4])
+    dt = 1e-3
+    sc = _lone_body(np.r_[[5, 5, 5], q], np.r_[[0, 0, 0], w],
+                    scenes.DOF_RX | scenes.DOF_RY | scenes.DOF_RZ, I, np.zeros(6))
+    st = oracle.State(sc)
+    st.run(1, dt=dt)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()   # scalar-last
+    wb = R.T @ w
+    # Euler's equations, torque-free: I1 w1' = (I2 - I3) w2 w3, cyclic
+    wdb = np.array([(I[1] - I[2]) * wb[1] * wb[2] / I[0],
+                    (I[2] - I[0]) * wb[2] * wb[0] / I[1],
+                    (I[0] - I[1]) * wb[0] * wb[1] / I[2]])
+    assert np.allclose(st.bodies.twist[0, 3:], w + dt * (R @ wdb), rtol=0, atol=1e-14)
+
+
+def test_spin_about_a_principal_axis_is_steady():
+    q = np.array([0.8, 0.3, -0.4, 0.2])
+    q /= np.linalg.norm(q)
+    from scipy.spatial.transform import Rotation
+    axis = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()[:, 1]   # body y in world
+    w = 1.3 * axis
+    sc = _lone_body(np.r_[[5, 5, 5], q], np.r_[[0, 0, 0], w],
+                    scenes.DOF_RX | scenes.DOF_RY | scenes.DOF_RZ, [1.0, 2.5, 4.0], np.zeros(6))
+    st = oracle.State(sc)
+    st.run(30, dt=1e-3)
+    assert np.allclose(st.bodies.twist[0, 3:], w, atol=1e-12)
+
+
+def test_marker_acceleration_is_the_rate_of_marker_velocity():
+    # a_marker = a_c + alpha x r + w x (w x r): the velocity of the same marker a
+    # short time later (twist advanced by the accelerations, pose by the twist)
+    sc = scenes.lattice_only(seed=0, n=1, random_state=False)
+    wm = np.array([[0.1, 0.03, -0.02], [-0.04, 0.07, 0.05]])
+    pose = np.array([1.0, 2.0, 3.0, 0.9, 0.1, 0.3, -0.2])
+    pose[3:] /= np.linalg.norm(pose[3:])
+    sc.bodies = [scenes.Body(wm, pose, np.array([0.1, 0.2, -0.3, 0.5, -1.1, 0.7]), 1.0, 0)]
+    b = oracle.Bodies(sc)
+    b.acc[0] = [0.4, -0.2, 0.9, 2.0, -3.0, 1.5]
+    mb, ml = oracle.marker_arrays(sc)
+    _, u0, a0 = oracle.marker_kinematics(mb, ml, b, 0.0)
+    e = 1e-6
+    b2 = oracle.Bodies(sc)
+    b2.acc[0] = b.acc[0]
+    b2.twist[0] = b.twist[0] + e * b.acc[0]
+    b2.pose[0, :3] = b.pose[0, :3] + e * b.twist[0, :3]
+    from scipy.spatial.transform import Rotation
+    w = b.twist[0, 3:]
+    dq = Rotation.from_rotvec(e * w)
+    q0 = b.pose[0, 3:]
+    q1 = (dq * Rotation.from_quat([q0[1], q0[2], q0[3], q0[0]])).as_quat()
+    b2.pose[0, 3:] = [q1[3], q1[0], q1[1], q1[2]]
+    _, u1, _ = oracle.marker_kinematics(mb, ml, b2, 0.0)
+    assert np.allclose((u1 - u0) / e, a0, rtol=1e-5, atol=1e-5)
+
+
 # --------------------------------------------------------------------------
 # Active domains (Sec. 3.2, Alg. 3)
 
