@@ -60,6 +60,9 @@ extern "C" {
 #define CRM_KERNEL_WENDLAND 1  /* quintic Wendland, support 2h (Sec. 3.1):
                                   W = 21/(16 pi h^3) (1 - q/2)^4 (2q + 1) */
 
+#define CRM_DOF_RX 8   /* angular velocity components (world frame), integrated */
+#define CRM_DOF_RY 16  /* from I w' = T - w x I w when set (crm_set_body_inertia) */
+#define CRM_DOF_RZ 32
 #define CRM_DOF_X 1
 #define CRM_DOF_Y 2
 #define CRM_DOF_Z 4
@@ -138,9 +141,13 @@ int crm_add_fixed_bce(crm_terrain *t, int64_t n, const double *xyz);
 /* Add a rigid body carrying n_markers BCE markers given in the body frame
  * (marker_xyz_local, n*3), with pose[7], twist[6], mass (kg, > 0) and a DOF
  * mask: bit k of CRM_DOF_X/Y/Z set = that linear velocity component is
- * integrated from the soil force and gravity (symplectic Euler); otherwise it
- * is prescribed.  Angular velocity is always prescribed.  *body_id receives
- * the body index (0, 1, ... in call order). */
+ * integrated from the soil force (plus the external load) and gravity by
+ * symplectic Euler; bit k of CRM_DOF_RX/RY/RZ set = that angular velocity
+ * component is integrated from I w' = T - w x I w (needs crm_set_body_inertia);
+ * unset components are prescribed.  The body's pose is taken at its centre of
+ * mass.  *body_id receives the body index (0, 1, ... in call order).  The
+ * paper couples bodies through a multibody solver (Sec. 2.4); this built-in
+ * 6-DOF update is the library's own stand-in for it. */
 int crm_add_rigid_body(crm_terrain *t, int64_t n_markers, const double *marker_xyz_local,
                        const double pose[7], const double twist[6], double mass,
                        int32_t dof_mask, int32_t *body_id);
@@ -151,6 +158,17 @@ int crm_add_rigid_body(crm_terrain *t, int64_t n_markers, const double *marker_x
  * entry is not finite. */
 int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7],
                         const double twist[6]);
+
+/* Principal moments of inertia (kg m^2, body frame, all > 0) of a body; needed
+ * before the first step when any angular DOF of the body is free.  Host array,
+ * copied; CRM_EINVAL on a bad body or a non-positive moment. */
+int crm_set_body_inertia(crm_terrain *t, int32_t body, const double inertia[3]);
+
+/* External force (N) and torque about the centre (N m), world frame, added to
+ * the soil wrench in the body update of every following step (e.g. a drive
+ * torque); zero by default.  Host arrays, copied. */
+int crm_set_body_load(crm_terrain *t, int32_t body, const double force[3],
+                      const double torque[3]);
 
 /* Current pose and twist of a body (synchronises the stream). */
 int crm_get_body_state(crm_terrain *t, int32_t body, double pose[7], double twist[6]);

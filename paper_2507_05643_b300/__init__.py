@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcrm.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2507_05643_b300.build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2507_05643_b300/build.py` "
                       "(the CUDA library is required; there is no CPU path)")
 
 _lib = C.CDLL(LIB_PATH)
@@ -30,6 +30,7 @@ STATUS = {0: "CRM_OK", -1: "CRM_EINVAL", -2: "CRM_ENOMEM", -3: "CRM_ECAPACITY",
           -4: "CRM_EESCAPED", -5: "CRM_ENONFINITE", -6: "CRM_ETIMEOUT", -7: "CRM_ECUDA",
           -8: "CRM_ESTATE"}
 AV_NONE, AV_BILATERAL, AV_UNILATERAL = 0, 1, 2
+DOF_X, DOF_Y, DOF_Z, DOF_RX, DOF_RY, DOF_RZ = 1, 2, 4, 8, 16, 32
 KERNEL_CUBIC, KERNEL_WENDLAND = 0, 1
 
 
@@ -80,6 +81,8 @@ _sig("crm_add_rigid_body", C.c_int, [_T, _i64, _vp, _vp, _vp, C.c_double, _i32,
                                      C.POINTER(_i32)])
 _sig("crm_set_body_motion", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_get_body_state", C.c_int, [_T, _i32, _vp, _vp])
+_sig("crm_set_body_inertia", C.c_int, [_T, _i32, _vp])
+_sig("crm_set_body_load", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_add_active_box", C.c_int, [_T, _i32, _vp, _vp, C.c_double])
 _sig("crm_step", C.c_int, [_T, C.c_double, _i32])
 _sig("crm_sync", C.c_int, [_T])
@@ -110,7 +113,8 @@ KERNEL_NAMES = tuple(_lib.crm_kernel_name(k).decode() for k in range(NUM_KERNELS
 # Every symbol include/crm.h declares.
 EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create", "crm_destroy",
            "crm_last_error", "crm_add_sph", "crm_add_fixed_bce", "crm_add_rigid_body",
-           "crm_set_body_motion", "crm_get_body_state", "crm_add_active_box", "crm_step",
+           "crm_set_body_motion", "crm_get_body_state", "crm_set_body_inertia",
+           "crm_set_body_load", "crm_add_active_box", "crm_step",
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
@@ -241,6 +245,12 @@ class Terrain:
     def set_body_motion(self, body: int, pose, twist):
         self._check(_lib.crm_set_body_motion(self._h, int(body), _ptr(_c(pose)), _ptr(_c(twist))))
 
+    def set_body_inertia(self, body: int, inertia):
+        self._check(_lib.crm_set_body_inertia(self._h, int(body), _ptr(_c(inertia))))
+
+    def set_body_load(self, body: int, force, torque):
+        self._check(_lib.crm_set_body_load(self._h, int(body), _ptr(_c(force)), _ptr(_c(torque))))
+
     def body_state(self, body: int) -> Tuple[np.ndarray, np.ndarray]:
         pose, twist = np.zeros(7), np.zeros(6)
         self._check(_lib.crm_get_body_state(self._h, int(body), _ptr(pose), _ptr(twist)))
@@ -325,8 +335,12 @@ def from_scene(scene, stream=None, **param_over) -> Terrain:
     t.add_sph(scene.x, scene.u, scene.sig, scene.rho)
     if scene.fixed.shape[0]:
         t.add_fixed_bce(scene.fixed)
-    for b in scene.bodies:
+    for k, b in enumerate(scene.bodies):
         t.add_rigid_body(b.markers_local, b.pose, b.twist, b.mass, b.dof_mask)
+        if getattr(b, "inertia", None) is not None:
+            t.set_body_inertia(k, b.inertia)
+        if getattr(b, "load", None) is not None:
+            t.set_body_load(k, b.load[:3], b.load[3:])
     for bx in scene.boxes:
         t.add_active_box(bx.body, bx.half_extents, bx.offset, scene.t_delay)
     return t

@@ -435,6 +435,9 @@ int commit(crm_terrain *t)
     const int64_t nF = t->nFtot, nM = t->nMtot, N = nF + nM;
     if (N >= (int64_t)kIndexMask)
         return t->fail(CRM_EINVAL, "more than 2^26 particles and markers in one terrain");
+    for (const BodyDev &b : t->hbodies)
+        if ((b.dof & (7 << 3)) && !(b.inertia[0] > 0 && b.inertia[1] > 0 && b.inertia[2] > 0))
+            return t->fail(CRM_EINVAL, "a body with free angular DOFs needs crm_set_body_inertia");
     t->active = !t->box_body_h.empty();
     t->skin_on = !t->active && t->P.skin > 0.0;
     int rc = make_devparams(t);
@@ -1226,7 +1229,7 @@ int crm_add_rigid_body(crm_terrain *t, int64_t n, const double *xloc, const doub
     if (t->committed) return t->fail(CRM_ESTATE, "crm_add_rigid_body after the first step");
     if (n < 0 || (n > 0 && !xloc) || !pose || !twist)
         return t->fail(CRM_EINVAL, "crm_add_rigid_body: bad n or null array");
-    if (!(mass > 0) || (dof_mask & ~7)) return t->fail(CRM_EINVAL, "crm_add_rigid_body: mass > 0, dof_mask in 0..7");
+    if (!(mass > 0) || (dof_mask & ~63)) return t->fail(CRM_EINVAL, "crm_add_rigid_body: mass > 0, dof_mask in 0..63");
     if ((int)t->hbodies.size() >= kMaxBodies) return t->fail(CRM_EINVAL, "at most 16 bodies");
     if (!finite_all(xloc, 3 * n) || !finite_all(pose, 7) || !finite_all(twist, 6))
         return t->fail(CRM_EINVAL, "crm_add_rigid_body: non-finite input");
@@ -1261,6 +1264,39 @@ int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7], cons
     for (int k = 0; k < 6; ++k) b.twist[k] = twist[k];
     if (t->committed)
         CRM_CUDA(t, cudaMemcpyAsync(&t->bodies[body], &b, 13 * sizeof(double),
+                                    cudaMemcpyHostToDevice, t->st));
+    return CRM_OK;
+}
+
+int crm_set_body_inertia(crm_terrain *t, int32_t body, const double inertia[3])
+{
+    if (!t) return CRM_EINVAL;
+    if (body < 0 || body >= (int)t->hbodies.size() || !inertia)
+        return t->fail(CRM_EINVAL, "crm_set_body_inertia: bad body or null array");
+    if (!finite_all(inertia, 3) || !(inertia[0] > 0 && inertia[1] > 0 && inertia[2] > 0))
+        return t->fail(CRM_EINVAL, "crm_set_body_inertia: moments must be finite and > 0");
+    BodyDev &b = t->hbodies[body];
+    for (int k = 0; k < 3; ++k) b.inertia[k] = inertia[k];
+    if (t->committed)
+        CRM_CUDA(t, cudaMemcpyAsync(t->bodies[body].inertia, b.inertia, sizeof(b.inertia),
+                                    cudaMemcpyHostToDevice, t->st));
+    return CRM_OK;
+}
+
+int crm_set_body_load(crm_terrain *t, int32_t body, const double force[3], const double torque[3])
+{
+    if (!t) return CRM_EINVAL;
+    if (body < 0 || body >= (int)t->hbodies.size() || !force || !torque)
+        return t->fail(CRM_EINVAL, "crm_set_body_load: bad body or null array");
+    if (!finite_all(force, 3) || !finite_all(torque, 3))
+        return t->fail(CRM_EINVAL, "crm_set_body_load: non-finite load");
+    BodyDev &b = t->hbodies[body];
+    for (int k = 0; k < 3; ++k) {
+        b.load[k] = force[k];
+        b.load[3 + k] = torque[k];
+    }
+    if (t->committed)
+        CRM_CUDA(t, cudaMemcpyAsync(t->bodies[body].load, b.load, sizeof(b.load),
                                     cudaMemcpyHostToDevice, t->st));
     return CRM_OK;
 }

@@ -111,15 +111,47 @@ __device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float
             BodyDev &B = bs.bodies[b];
             for (int k = 0; k < 6; ++k) B.wrench[k] = W[k];
             if (bs.integrate) {
-                // symplectic Euler on the free linear DOFs: v += dt (F/m + g), x += dt v;
-                // prescribed DOFs move with their velocity; the orientation turns by dt w
+                // symplectic Euler on the free DOFs with the soil wrench plus the
+                // external load: v += dt (F/m + g), w += dt I_w^-1 (T - w x I_w w)
+                // (I_w = R diag(I) R^T at t_n), then x += dt v and the orientation
+                // turns by dt w; prescribed DOFs keep their velocity
+                double F[3], T[3], wdot[3] = {0.0, 0.0, 0.0};
+                for (int k = 0; k < 3; ++k) {
+                    F[k] = W[k] + B.load[k];
+                    T[k] = W[3 + k] + B.load[3 + k];
+                }
+                if (B.dof & (7 << 3)) {
+                    const double qw = B.pose[3], qx = B.pose[4], qy = B.pose[5], qz = B.pose[6];
+                    const double R[3][3] = {
+                        {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+                        {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+                        {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+                    const double *w = B.twist + 3;
+                    double L[3], rb[3];
+                    for (int r = 0; r < 3; ++r) {   // body-frame w, times I
+                        rb[r] = B.inertia[r] * (R[0][r] * w[0] + R[1][r] * w[1] + R[2][r] * w[2]);
+                    }
+                    for (int r = 0; r < 3; ++r) L[r] = R[r][0] * rb[0] + R[r][1] * rb[1] + R[r][2] * rb[2];
+                    const double rhs[3] = {T[0] - (w[1] * L[2] - w[2] * L[1]),
+                                           T[1] - (w[2] * L[0] - w[0] * L[2]),
+                                           T[2] - (w[0] * L[1] - w[1] * L[0])};
+                    for (int r = 0; r < 3; ++r)
+                        rb[r] = (R[0][r] * rhs[0] + R[1][r] * rhs[1] + R[2][r] * rhs[2]) / B.inertia[r];
+                    for (int r = 0; r < 3; ++r) wdot[r] = R[r][0] * rb[0] + R[r][1] * rb[1] + R[r][2] * rb[2];
+                }
                 for (int k = 0; k < 3; ++k) {
                     if (B.dof & (1 << k)) {
-                        const double a = W[k] / B.mass + p.g64[k];
+                        const double a = F[k] / B.mass + p.g64[k];
                         B.twist[k] += bs.dt * a;
                         B.acc[k] = a;
                     } else {
                         B.acc[k] = 0.0;
+                    }
+                    if (B.dof & (8 << k)) {
+                        B.twist[3 + k] += bs.dt * wdot[k];
+                        B.alpha[k] = wdot[k];
+                    } else {
+                        B.alpha[k] = 0.0;
                     }
                     B.pose[k] += bs.dt * B.twist[k];
                 }

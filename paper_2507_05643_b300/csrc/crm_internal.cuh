@@ -110,6 +110,9 @@ struct BodyDev {
     int pad;
     double ref_pose[7]; // pose at the last cell search (skin bookkeeping)
     double rmax;        // largest marker distance from the centre
+    double alpha[3];    // angular acceleration at the last update (free angular DOFs)
+    double inertia[3];  // principal moments of inertia in the body frame
+    double load[6];     // external force and torque about the centre, added to the soil's
 };
 
 // Stage arrays: the state every pair kernel gathers neighbours from.
@@ -211,7 +214,7 @@ __device__ __forceinline__ void qadvance(const double q[4], const double w[3], d
 struct BodyFrame {
     double c[3];
     double R[9];   // row-major rotation of the body-local marker positions
-    float v[3], w[3], acc[3];
+    float v[3], w[3], acc[3], alpha[3];
 };
 
 __device__ __forceinline__ void body_frame(const BodyDev &b, double tau, BodyFrame &F)
@@ -227,24 +230,29 @@ __device__ __forceinline__ void body_frame(const BodyDev &b, double tau, BodyFra
         F.v[k] = (float)b.twist[k];
         F.w[k] = (float)b.twist[3 + k];
         F.acc[k] = (float)b.acc[k];
+        F.alpha[k] = (float)b.alpha[k];
     }
 }
 
-// Rigid velocity and acceleration of a body marker with arm r (FP32 is enough:
-// they enter the FP32 rates), and the FP64 world position c + r.
+// Rigid velocity v + w x r and acceleration a_c + alpha x r + w x (w x r) of a
+// body marker with arm r (FP32 is enough: they enter the FP32 rates), and the
+// FP64 world position c + r.
 __device__ __forceinline__ void marker_kin(const double c[3], const double r[3], const float v[3],
-                                           const float w[3], const float acc[3], double x[3],
-                                           float u[3], float a[3], float arm[3])
+                                           const float w[3], const float acc[3],
+                                           const float alpha[3], double x[3], float u[3],
+                                           float a[3], float arm[3])
 {
     const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
     const float wr[3] = {w[1] * rf[2] - w[2] * rf[1], w[2] * rf[0] - w[0] * rf[2],
                          w[0] * rf[1] - w[1] * rf[0]};
     const float wwr[3] = {w[1] * wr[2] - w[2] * wr[1], w[2] * wr[0] - w[0] * wr[2],
                           w[0] * wr[1] - w[1] * wr[0]};
+    const float ar[3] = {alpha[1] * rf[2] - alpha[2] * rf[1], alpha[2] * rf[0] - alpha[0] * rf[2],
+                         alpha[0] * rf[1] - alpha[1] * rf[0]};
     for (int k = 0; k < 3; ++k) {
         x[k] = c[k] + r[k];
         u[k] = v[k] + wr[k];
-        a[k] = acc[k] + wwr[k];
+        a[k] = acc[k] + ar[k] + wwr[k];
         arm[k] = rf[k];
     }
 }
@@ -257,7 +265,7 @@ __device__ __forceinline__ void marker_at(const BodyFrame &F, const double *xloc
     const double r[3] = {fma(F.R[0], l0, fma(F.R[1], l1, F.R[2] * l2)),
                          fma(F.R[3], l0, fma(F.R[4], l1, F.R[5] * l2)),
                          fma(F.R[6], l0, fma(F.R[7], l1, F.R[8] * l2))};
-    marker_kin(F.c, r, F.v, F.w, F.acc, x, u, a, arm);
+    marker_kin(F.c, r, F.v, F.w, F.acc, F.alpha, x, u, a, arm);
 }
 
 // A body marker at the current pose (stage offset 0): one quaternion rotation,
@@ -270,7 +278,8 @@ __device__ __forceinline__ void marker_now(const BodyDev &b, const double *xloc,
     const float v[3] = {(float)b.twist[0], (float)b.twist[1], (float)b.twist[2]};
     const float w[3] = {(float)b.twist[3], (float)b.twist[4], (float)b.twist[5]};
     const float acc[3] = {(float)b.acc[0], (float)b.acc[1], (float)b.acc[2]};
-    marker_kin(b.pose, r, v, w, acc, x, u, a, arm);
+    const float al[3] = {(float)b.alpha[0], (float)b.alpha[1], (float)b.alpha[2]};
+    marker_kin(b.pose, r, v, w, acc, al, x, u, a, arm);
 }
 
 // Cell offsets of the neighbour codes (dx, dy, dz in {-1, 0, 1}) times the cell

@@ -250,6 +250,55 @@ def wheel_bin(seed: int = 2, nx: int = 200, ny: int = 40, nz: int = 15, d0: floa
                  [body], boxes, 0.0, dt, n_steps, lo, hi)
 
 
+def sphere_markers(radius: float, d0: float, layers: int = 3) -> np.ndarray:
+    """Body-frame markers of a sphere: `layers` shells stepping inward by d0 from
+    the surface, each covered at about d0 spacing (Fibonacci points)."""
+    pts = []
+    for L in range(layers):
+        r = radius - L * d0
+        if r <= 0.0:
+            break
+        n = max(12, int(round(4 * math.pi * r * r / (d0 * d0))))
+        k = np.arange(n) + 0.5
+        z = 1.0 - 2.0 * k / n
+        phi = math.pi * (1.0 + math.sqrt(5.0)) * k
+        rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+        pts.append(r * np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1))
+    return np.concatenate(pts, axis=0)
+
+
+def sphere_drop(seed: int = 6, nx: int = 30, ny: int = 30, nz: int = 12, d0: float = 0.01,
+                radius: float = 0.05, density: float = 7800.0, speed: float = 1.0,
+                spin: float = 3.0, phi_deg: float = 30.0, cohesion: float = 0.0,
+                dt: float = 5e-5, n_steps: int = 400, jitter: float = 1e-4) -> Scene:
+    """A solid sphere dropped onto a granular bed with all six DOFs free (the
+    paper's cratering setting of Sec. 4, small): a steel sphere of the given
+    radius hits the surface at `speed` with a spin about x, on a geostatic
+    nx x ny x nz bed with 3-layer walls.  Inertia of a solid sphere."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = default_params(d0, mu_s=math.tan(math.radians(phi_deg)), cohesion=cohesion,
+                       av_mode=2, av_gamma=0.02)
+    H = nz * d0
+    x = _jitter(rng, lattice(nx, ny, nz, d0), jitter)
+    layers = n_layers(p["h"], d0)
+    nz_wall = nz + int(round(0.05 / d0))
+    fixed = box_walls(nx, ny, nz_wall, layers, d0)
+    sig = geostatic_stress(x[:, 2], H, p["rho0"], p["nu"])
+    mass = density * 4.0 / 3.0 * math.pi * radius ** 3
+    inertia = np.full(3, 0.4 * mass * radius * radius)
+    pose = np.concatenate([[nx * d0 / 2, ny * d0 / 2, H + radius + 0.5 * d0], [1.0, 0.0, 0.0, 0.0]])
+    twist = np.array([0.0, 0.0, -speed, spin, 0.0, 0.0])
+    body = Body(sphere_markers(radius, d0, layers), pose, twist, mass,
+                DOF_X | DOF_Y | DOF_Z | DOF_RX | DOF_RY | DOF_RZ, inertia=inertia,
+                load=np.zeros(6))
+    margin = layers * d0 + 2 * p["h"]
+    lo = np.array([-margin, -margin, -margin])
+    hi = np.array([nx * d0 + margin, ny * d0 + margin, max(nz_wall * d0, H + 3 * radius) + margin])
+    m = x.shape[0]
+    return Scene("sphere_drop", p, x, np.zeros((m, 3)), sig, np.full(m, p["rho0"]), fixed,
+                 [body], [], 0.0, dt, n_steps, lo, hi)
+
+
 def lattice_only(seed: int, n: int = 12, d0: float = 0.01, jitter: float = 1e-4,
                  random_state: bool = True, **over) -> Scene:
     """An n^3 jittered lattice with random velocities and stresses and no walls

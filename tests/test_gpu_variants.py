@@ -185,3 +185,75 @@ def test_ps_freq_10_tracks_every_step_rebuild():
     print(f"ps_freq 10 vs 1 after 100 steps: max|dx|/d0 {dx:.2e}, rms dsigma/(rho0 g H) "
           f"{ds:.2e}, |dF|/|F| {dF:.2e}")
     assert dx < 1e-2 and ds < 1e-2 and dF < 5e-2
+
+
+# --------------------------------------------------------------------------
+# 6-DOF bodies: free angular DOFs, principal inertia, external load
+
+def test_drive_torque_spins_a_free_wheel_up_linearly():
+    """Wheel lifted clear of the soil, spin about its axle free, a constant drive
+    torque: w_y(n) = w0 + n dt T / I exactly (the FP64 body update)."""
+    sc = scenes.wheel_bin(seed=78, nx=40, ny=24, nz=10, wheel_radius=0.08, wheel_width=0.08,
+                          n_grousers=8, wheel_x=0.2)
+    b = sc.bodies[0]
+    b.pose[2] += 0.05
+    b.twist[:] = [0.0, 0.0, 0.0, 0.0, 0.5, 0.0]
+    b.dof_mask = scenes.DOF_RY
+    b.inertia = np.array([0.02, 0.03, 0.02])
+    b.load = np.array([0.0, 0.0, 0.0, 0.0, 0.6, 0.0])
+    t = crm.from_scene(sc)
+    n = 40
+    t.step(sc.dt, n)
+    pose, twist = t.body_state(0)
+    assert twist[4] == pytest.approx(0.5 + n * sc.dt * 0.6 / 0.03, rel=1e-12)
+    assert np.all(twist[[0, 1, 2, 3, 5]] == 0.0)
+    F, T = t.body_wrench(0)
+    assert np.all(F == 0.0) and np.all(T == 0.0)
+
+
+def _body_compare(t, st, sc, steps):
+    done = 0
+    rep = {}
+    d0 = sc.params["d0"]
+    for k in steps:
+        t.step(sc.dt, k - done)
+        st.run(k - done)
+        done = k
+        pose, twist = t.body_state(0)
+        xyz, vel, sig, rho = t.particles()
+        rep[k] = (float(np.max(np.abs(pose[:3] - st.bodies.pose[0, :3])) / d0),
+                  float(np.max(np.abs(twist - st.bodies.twist[0]))),
+                  float(np.max(np.abs(xyz - st.x)) / d0))
+    return rep
+
+
+def test_torque_driven_wheel_matches_oracle():
+    """Wheel with free spin and free sinkage driven by a drive torque into the
+    soil (N3): body state and particles follow the FP64 oracle."""
+    sc = scenes.wheel_bin(seed=79, nx=40, ny=24, nz=10, wheel_radius=0.08, wheel_width=0.08,
+                          n_grousers=8, wheel_x=0.2)
+    b = sc.bodies[0]
+    b.pose[2] -= 0.004
+    b.twist[:] = [0.05, 0.0, 0.0, 0.0, 0.8, 0.0]
+    b.dof_mask = scenes.DOF_Z | scenes.DOF_RY
+    b.inertia = np.array([0.004, 0.006, 0.004])
+    b.load = np.array([0.0, 0.0, 0.0, 0.0, 0.05, 0.0])
+    t = crm.from_scene(sc)
+    st = oracle.State(sc)
+    rep = _body_compare(t, st, sc, (1, 20, 60))
+    print("torque-driven wheel: max|dx_c|/d0, max|d twist|, max|dx|/d0:", rep)
+    assert rep[1][0] < 1e-9 and rep[1][1] < 1e-6 and rep[1][2] < 1e-6
+    assert rep[60][0] < 1e-4 and rep[60][1] < 1e-3 and rep[60][2] < 1e-3
+
+
+def test_sphere_drop_with_six_free_dofs_matches_oracle():
+    """A spinning steel sphere dropped onto the bed, all six DOFs free."""
+    sc = scenes.sphere_drop(nx=24, ny=24, nz=10, radius=0.04)
+    t = crm.from_scene(sc)
+    st = oracle.State(sc)
+    rep = _body_compare(t, st, sc, (1, 30, 100))
+    print("sphere drop: max|dx_c|/d0, max|d twist|, max|dx|/d0:", rep)
+    pose, twist = t.body_state(0)
+    assert twist[2] > -1.0 + 1e-3      # the bed has started to brake it
+    assert rep[1][0] < 1e-9 and rep[1][1] < 1e-6 and rep[1][2] < 1e-6
+    assert rep[100][0] < 1e-4 and rep[100][1] < 1e-3 and rep[100][2] < 1e-3
