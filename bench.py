@@ -207,8 +207,14 @@ def _traffic(kernel: str):
 
 def _workload(args):
     """The benchmark workload; --bin-scale S > 1 widens the bin S-fold in x and y
-    (a profiling case larger than L2, not a bench line)."""
+    (a profiling case larger than L2, not a bench line); --workload strip runs the
+    active-domain strip (a window of --strip-length m around the rover at
+    x = 5000 m; 10000 = the whole 10 km strip)."""
     import scenes
+    if args.workload == "strip":
+        half = args.strip_length / 2
+        win = None if args.strip_length >= 1.0e4 else (5000.75 - half, 5000.75 + half)
+        return scenes.strip(x_window=win)
     if args.bin_scale == 1:
         return scenes.wheel_bin()
     s = args.bin_scale
@@ -319,7 +325,7 @@ def run_crm(args):
             "pair_stage2": 56 * 3 * sc.n_fluid + 56 * sc.n_markers + 4 * fluid_pairs,
             "export": 88 * sc.n_fluid}
         if kern.startswith("pair"):
-            flop = fluid_pairs * FLOP_PER_PAIR + sc.n_fluid * FLOP_PER_PARTICLE
+            flop = fluid_pairs * FLOP_PER_PAIR + n_active * FLOP_PER_PARTICLE
             achieved = flop / (avg_ms * 1e-3) / 1e12
             roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": fp32_peak,
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
@@ -362,6 +368,11 @@ def run_crm(args):
             line["config"]["workload"] = f"profiling case: wheel_bin widened {args.bin_scale}x in x and y"
         if args.ps_freq != 1:
             line["config"]["workload"] = WORKLOAD.replace("ps_freq=1", f"ps_freq={args.ps_freq}")
+        if args.workload == "strip":
+            line["config"]["workload"] = (
+                f"strip: {args.strip_length:g} m of the 10 km x 2 m x 0.1 m strip at d0=0.025 m "
+                f"({sc.n_fluid:,} SPH stored), four-wheel rover at x=5000 m, 1 m/s, 1 m active "
+                f"boxes, dt=1e-4 s")
         line["config"]["skin"] = args.skin if args.skin is not None else 0.1
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -382,6 +393,10 @@ def main():
                     help="Verlet skin as a fraction of 2h (default: the library's 0.1)")
     ap.add_argument("--ps-freq", type=int, default=1,
                     help="neighbour-list rebuild period (Alg. 2); the workload is quoted at 1")
+    ap.add_argument("--workload", choices=["wheel_bin", "strip"], default="wheel_bin",
+                    help="strip: the 10 km active-domain strip (a parity-test configuration)")
+    ap.add_argument("--strip-length", type=float, default=20.0,
+                    help="length in m of the strip window around the rover")
     ap.add_argument("--bin-scale", type=int, default=1,
                     help="profiling only: widen the bin S-fold in x and y")
     args = ap.parse_args()

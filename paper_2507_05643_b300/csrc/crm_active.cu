@@ -51,6 +51,7 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
 {
     if (threadIdx.x != 0) return;
     if (*abort_flag) return;
+    if (p.step_ctr != nullptr) step_tag = (int64_t)*p.step_ctr;
     counts[3] = 0;
     counts[4] = 0;
     const int G[3] = {p.GX, p.GY, p.GZ};
@@ -93,6 +94,7 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
     if (hi[0] < lo[0] || hi[1] < lo[1] || hi[2] < lo[2]) {   // boxes outside the grid
         for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; }
     }
+    counts[9] = (int)min(cells, (int64_t)0x7fffffff);   // window in use (shrink policy)
     if (cells > (int64_t)p.M) {
         counts[7] = (int)min(cells, (int64_t)0x7fffffff);
         atomicCAS(abort_flag, 0, (int)(step_tag + 1));
@@ -150,6 +152,7 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
     rinfo[1] = nrange[1];
     rinfo[3] = (int)min(total, (int64_t)0x7fffffff);
     rinfo[4 + nr] = (int)total;
+    counts[10] = (int)min(total, (int64_t)0x7fffffff);   // candidates in use (shrink policy)
     if (total > cand_cap) {
         counts[8] = (int)min(total, (int64_t)0x7fffffff);
         atomicCAS(abort_flag, 0, (int)(step_tag + 1));
@@ -257,6 +260,7 @@ __global__ void k_active_sizes(DevParams p, const int *__restrict__ rinfo,
                                int64_t step_tag)
 {
     if (threadIdx.x != 0 || *abort_flag) return;
+    if (p.step_ctr != nullptr) step_tag = (int64_t)*p.step_ctr;
     const int nfc = rinfo[2], total = rinfo[3];
     const int nF = (int)slot[nfc];
     const int nfix = (int)slot[total] - nF;
@@ -315,7 +319,7 @@ __global__ void k_gather(DevParams p, const int *__restrict__ ranges, const int 
             W.vel[w] = make_float4(0.f, 0.f, 0.f, p.rho0);
             W.sA[w] = make_float4(0.f, 0.f, 0.f, 0.f);
             W.sB[w] = make_float2(0.f, 0.f);
-            wpid[w] = (uint32_t)body_markers[k];   // encoded marker pid (index | body)
+            wpid[w] = (uint32_t)body_markers[k];   // marker id
         }
     }
     (void)cand_cap;

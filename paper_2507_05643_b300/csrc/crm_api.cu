@@ -29,7 +29,8 @@ using namespace crm;
 namespace {
 enum { G_STATIC, G_WORK, G_WIN, G_CAND, G_COUNT };
 // device counters word layout
-enum { C_NF, C_NM, C_N, C_NA, C_NE, C_NEED_F, C_NEED_M, C_NEED_CELLS, C_NEED_CAND, C_WORDS = 16 };
+enum { C_NF, C_NM, C_N, C_NA, C_NE, C_NEED_F, C_NEED_M, C_NEED_CELLS, C_NEED_CAND, C_USE_CELLS,
+       C_USE_CAND, C_WORDS = 16 };
 }  // namespace
 
 struct crm_terrain {
@@ -75,6 +76,15 @@ struct crm_terrain {
     // a step with / without the Alg. 2 rebuild, one per current buffer (a graph
     // bakes in the buffer pointers; a search without a skin swaps the buffers)
     StepGraph g_search[2], g_plain[2];
+    unsigned long long *step_ctr = nullptr;   // active domains: device step index (abort tag)
+    void drop_graphs()
+    {
+        for (int b = 0; b < 2; ++b) {
+            if (g_search[b].exec) cudaGraphExecDestroy(g_search[b].exec);
+            if (g_plain[b].exec) cudaGraphExecDestroy(g_plain[b].exec);
+            g_search[b].exec = g_plain[b].exec = nullptr;
+        }
+    }
     cudaStream_t cap_st = nullptr;   // private stream the graphs are captured on
     bool graphs = true;
     // Verlet skin (non-active runs with skin > 0)
@@ -291,9 +301,12 @@ int latched_error(crm_terrain *t)
 // Working-set arrays for capF fluid + capM marker slots.
 int alloc_working(crm_terrain *t)
 {
+    t->drop_graphs();   // graphs bake in the array pointers
     t->free_group(G_WORK);
     DevParams &d = t->dp;
     const int64_t N = t->capF + t->capM;
+    if (N >= (int64_t)kIndexMask)
+        return t->fail(CRM_EINVAL, "working set beyond the 2^26 slots a neighbour entry addresses");
     d.capF = (int)t->capF;
     d.capM = (int)t->capM;
     d.capN = (int)N;
@@ -346,6 +359,7 @@ int alloc_working(crm_terrain *t)
 // Counting-sort key space: 2 Mcap + 1 cell counters and ranges.
 int alloc_window(crm_terrain *t)
 {
+    t->drop_graphs();
     t->free_group(G_WIN);
     t->dp.M = (uint32_t)t->Mcap;
     const size_t nk = 2 * (size_t)t->Mcap + 1;
@@ -364,6 +378,7 @@ int alloc_window(crm_terrain *t)
 // Candidate arrays of the activity pass (active domains).
 int alloc_cand(crm_terrain *t)
 {
+    t->drop_graphs();
     t->free_group(G_CAND);
     const size_t n = (size_t)t->cand_cap + 1;
     t->cinc = t->dalloc<uint32_t>(G_CAND, n);
@@ -433,8 +448,8 @@ int commit(crm_terrain *t)
 {
     if (t->committed) return CRM_OK;
     const int64_t nF = t->nFtot, nM = t->nMtot, N = nF + nM;
-    if (N >= (int64_t)kIndexMask)
-        return t->fail(CRM_EINVAL, "more than 2^26 particles and markers in one terrain");
+    if (N >= (int64_t)kPidIndexMask)
+        return t->fail(CRM_EINVAL, "more than 2^31 - 1 particles and markers in one terrain");
     for (const BodyDev &b : t->hbodies)
         if ((b.dof & (7 << 3)) && !(b.inertia[0] > 0 && b.inertia[1] > 0 && b.inertia[2] > 0))
             return t->fail(CRM_EINVAL, "a body with free angular DOFs needs crm_set_body_inertia");
@@ -444,6 +459,21 @@ int commit(crm_terrain *t)
     if (rc) return rc;
     DevParams &d = t->dp;
     d.n_bodies = (int)t->hbodies.size();
+    // id range of each body's markers (one contiguous range per crm_add_rigid_body)
+    {
+        std::vector<int64_t> lo(d.n_bodies, -1), hi(d.n_bodies, -1);
+        for (int64_t a = 0; a < nM; ++a) {
+            const int b = t->hmbody[a];
+            if (b < 0) continue;
+            if (lo[b] < 0) lo[b] = a;
+            else if (a != hi[b]) return t->fail(CRM_EINVAL, "body markers not contiguous");
+            hi[b] = a + 1;
+        }
+        for (int b = 0; b < d.n_bodies; ++b) {
+            d.body_lo[b] = (uint32_t)(lo[b] < 0 ? 0 : nF + lo[b]);
+            d.body_hi[b] = (uint32_t)(lo[b] < 0 ? 0 : nF + hi[b]);
+        }
+    }
     // largest marker arm of each body, and the reference pose of the skin bound
     for (size_t b = 0; b < t->hbodies.size(); ++b) {
         BodyDev &B = t->hbodies[b];
@@ -542,7 +572,7 @@ int commit(crm_terrain *t)
                 a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 b2[i] = make_float2(0.f, 0.f);
             }
-            pid[i] = i < nF ? (uint32_t)i : marker_pid(i, t->hmbody[i - nF]);
+            pid[i] = (uint32_t)i;
         }
         const int c = t->cur;
         rc = upload(t, t->A[c].pos, p4.data(), N);
@@ -592,7 +622,7 @@ int commit(crm_terrain *t)
     std::vector<int> fixed, bodym;
     for (int64_t a = 0; a < nM; ++a) {
         if (t->hmbody[a] < 0) fixed.push_back((int)a);
-        else bodym.push_back((int)marker_pid(nF + a, t->hmbody[a]));
+        else bodym.push_back((int)(nF + a));
     }
     std::vector<int64_t> fkey(fixed.size());
     for (size_t k = 0; k < fixed.size(); ++k) {
@@ -626,6 +656,8 @@ int commit(crm_terrain *t)
     t->fixed_order = t->dalloc<int>(G_STATIC, fixed.size());
     t->body_markers = t->dalloc<int>(G_STATIC, bodym.size());
     t->drift = t->dalloc<int>(G_STATIC, 1);
+    t->step_ctr = t->dalloc<unsigned long long>(G_STATIC, 1);
+    d.step_ctr = t->step_ctr;
     const size_t nbox = t->box_body_h.size();
     t->box_body = t->dalloc<int>(G_STATIC, nbox);
     t->box_half = t->dalloc<double>(G_STATIC, 3 * nbox);
@@ -673,6 +705,10 @@ int commit(crm_terrain *t)
     if (!rc) rc = alloc_cand(t);
     if (rc) return rc;
     CRM_CUDA(t, cudaStreamSynchronize(st));
+    if (cudaStreamCreateWithFlags(&t->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        t->cap_st = nullptr;   // direct launches only
+    }
     t->committed = true;
     t->have_working = false;
     return CRM_OK;
@@ -919,6 +955,7 @@ int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph 
         e = cudaStreamBeginCaptureToGraph(t->st, g, nullptr, nullptr, 0, mode);
         if (e == cudaSuccess) {
             if (search) {
+                if (t->active) activity_pass(t);
                 enqueue_search(t);
                 t->cur = 1 - t->cur;
             }
@@ -970,6 +1007,11 @@ int graph_step(crm_terrain *t, double dt)
             t->prof.launches[K_REORDER] += 1;
             t->prof.launches[K_NEIGHBORS] += 1;
             if (d.capM > 0) t->prof.launches[K_COMPACT] += 2;
+            if (t->active) {   // scatter-back, box prep, activity, scan, sizes, gather
+                t->prof.launches[K_EXPORT] += 1;
+                t->prof.launches[K_KEYS] += 4;
+                t->prof.launches[K_SCAN] += 1;
+            }
             t->cur = 1 - t->cur;
         }
         t->prof.rebuilds += 1;
@@ -1010,7 +1052,19 @@ int step_active(crm_terrain *t, double dt, int n_steps)
         const int64_t s0 = t->step_index;
         const double t0 = t->time;
         const int chunk = (int)std::min<int64_t>(remaining, SI - (s0 % SI));
-        for (int s = 0; s < chunk; ++s) one_step(t, dt);
+        const unsigned long long s0d = (unsigned long long)s0;
+        CRM_CUDA(t, cudaMemcpyAsync(t->step_ctr, &s0d, sizeof(s0d), cudaMemcpyHostToDevice, t->st));
+        for (int s = 0; s < chunk; ++s) {
+            // graph replay once the working set exists and the boxes are in force
+            // (before t_delay every particle is processed, a different launch set)
+            if (t->graphs && !t->timing && t->cap_st && t->have_working && t->lists_valid
+                && t->time > t->t_delay) {
+                int rg = graph_step(t, dt);
+                if (rg) return rg;
+            } else {
+                one_step(t, dt);
+            }
+        }
         CRM_CUDA(t, cudaGetLastError());
         int rc = read_counts(t);
         if (rc) return rc;
@@ -1055,6 +1109,20 @@ int step_active(crm_terrain *t, double dt, int n_steps)
                 t->capF = std::max<int64_t>(nF, 1);
                 t->capM = std::max<int64_t>(nM, 1);
                 rc = alloc_working(t);
+                if (rc) return rc;
+            }
+            // the cell window and the candidate ranges follow the same rule (the
+            // first step before t_delay sizes them for the whole terrain)
+            const int64_t cells = t->h_counts[C_USE_CELLS], cand = t->h_counts[C_USE_CAND];
+            if (cells > 0 && (double)cells / (double)t->Mcap < S) {
+                t->Mcap = cells;
+                rc = alloc_window(t);
+                if (rc) return rc;
+                t->lists_valid = false;
+            }
+            if (cand > 0 && (double)cand / (double)t->cand_cap < S) {
+                t->cand_cap = cand;
+                rc = alloc_cand(t);
                 if (rc) return rc;
             }
         }
@@ -1163,10 +1231,7 @@ int crm_destroy(crm_terrain *t)
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : t->ev_pool) cudaEventDestroy(e);
-    for (int b = 0; b < 2; ++b) {
-        if (t->g_search[b].exec) cudaGraphExecDestroy(t->g_search[b].exec);
-        if (t->g_plain[b].exec) cudaGraphExecDestroy(t->g_plain[b].exec);
-    }
+    t->drop_graphs();
     if (t->cap_st) cudaStreamDestroy(t->cap_st);
     if (t->side) {
         cudaStreamSynchronize(t->side);

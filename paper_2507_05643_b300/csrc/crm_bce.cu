@@ -221,7 +221,7 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
         float4 home = make_float4(0.f, 0.f, 0.f, 0.f);
         if (work) {
             const uint32_t id = pid[s];
-            body = pid_body(id);
+            body = pid_body(p, id);
             home = home_pos[s];
             if (body >= 0) {
                 const int mi = (int)pid_index(id) - n_fluid_total;
@@ -387,13 +387,13 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
 constexpr int kCompactBlock = 256;
 
 // list 0: every marker with a non-empty list; list 1: those of them on a body.
-__device__ __forceinline__ void marker_activity(const Sizes &z, const uint32_t *nnb,
-                                                const uint32_t *pid, int s, bool &valid,
-                                                bool a[2])
+__device__ __forceinline__ void marker_activity(const DevParams &p, const Sizes &z,
+                                                const uint32_t *nnb, const uint32_t *pid, int s,
+                                                bool &valid, bool a[2])
 {
     valid = s < z.N;
     a[0] = valid && nnb[s] > 0u;
-    a[1] = a[0] && pid_body(pid[s]) >= 0;
+    a[1] = a[0] && pid_body(p, pid[s]) >= 0;
 }
 
 __global__ void __launch_bounds__(kCompactBlock)
@@ -403,7 +403,7 @@ k_marker_counts(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *_
     if (*p.abort || gated_off(p)) return;
     const Sizes z = load_sizes(p);
     bool valid, a[2];
-    marker_activity(z, nnb, pid, z.nF + blockIdx.x * blockDim.x + threadIdx.x, valid, a);
+    marker_activity(p, z, nnb, pid, z.nF + blockIdx.x * blockDim.x + threadIdx.x, valid, a);
     const int c0 = __syncthreads_count(a[0]);
     const int c1 = __syncthreads_count(a[1]);
     if (threadIdx.x == 0) {
@@ -429,7 +429,7 @@ k_marker_compact(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *
     const Sizes z = load_sizes(p);
     const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
     bool valid, a[2];
-    marker_activity(z, nnb, pid, s, valid, a);
+    marker_activity(p, z, nnb, pid, s, valid, a);
     unsigned bits[2];
 #pragma unroll
     for (int l = 0; l < 2; ++l) {

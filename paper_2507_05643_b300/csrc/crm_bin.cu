@@ -242,7 +242,7 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
         seg = 1;
         const uint32_t id = pid[i];
         const int mi = (int)pid_index(id) - n_fluid_total;
-        const int body = pid_body(id);
+        const int body = pid_body(p, id);
         const double *xl = mloc + 3 * (int64_t)mi;
         double x[3] = {xl[0], xl[1], xl[2]};   // fixed marker: its world position
         if (body >= 0) {

@@ -20,15 +20,10 @@ enum : int {
 
 constexpr int kMaxBodies = 16;
 constexpr uint32_t kExtendedBit = 0x80000000u;   // pid flag: Extended-Active (read-only)
-// particle id: insertion index in bits 0..25; for a marker, bits 26..30 hold
-// its body + 1 (0 = fixed wall marker); bit 31 = Extended-Active
-constexpr uint32_t kPidIndexMask = (1u << 26) - 1u;
+// particle id: insertion index in bits 0..30 (fluid particles, then markers);
+// bit 31 = Extended-Active.  Each body's markers hold one contiguous id range.
+constexpr uint32_t kPidIndexMask = 0x7FFFFFFFu;
 __host__ __device__ __forceinline__ uint32_t pid_index(uint32_t id) { return id & kPidIndexMask; }
-__host__ __device__ __forceinline__ int pid_body(uint32_t id) { return (int)((id >> 26) & 31u) - 1; }
-__host__ __device__ __forceinline__ uint32_t marker_pid(int64_t index, int body)
-{
-    return (uint32_t)index | ((uint32_t)(body + 1) << 26);
-}
 constexpr uint32_t kIndexBits = 26;                 // neighbour entry: j | code << 26
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int kBlock = 256;
@@ -58,6 +53,9 @@ struct DevParams {
     int maxnb;
     uint32_t ell;                         // stride of the neighbour table (>= capN)
     int n_bodies;
+    uint32_t body_lo[kMaxBodies], body_hi[kMaxBodies];   // particle-id range of each body's markers
+    unsigned long long *step_ctr;         // active domains: index of the running step (the
+                                          // abort tag), advanced by pair stage 2; else null
     // device-resident sizes of the current working set: nF, nM, N, and the
     // window of the cell sort: x0, y0, z0 (global cells) and X, Y, Z
     // (X Y Z <= M).  Kept on the device so that a step needs no host sync.
@@ -114,6 +112,16 @@ struct BodyDev {
     double inertia[3];  // principal moments of inertia in the body frame
     double load[6];     // external force and torque about the centre, added to the soil's
 };
+
+// Body of the particle with id `id`: -1 for fluid particles and fixed markers.
+__device__ __forceinline__ int pid_body(const DevParams &p, uint32_t id)
+{
+    const uint32_t k = pid_index(id);
+    int b = -1;
+    for (int q = 0; q < p.n_bodies; ++q)
+        if (k >= p.body_lo[q] && k < p.body_hi[q]) b = q;
+    return b;
+}
 
 // Stage arrays: the state every pair kernel gathers neighbours from.
 struct StageArrays {

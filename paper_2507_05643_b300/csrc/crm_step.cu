@@ -144,6 +144,8 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
        const float4 *__restrict__ xref, int *__restrict__ gate)
 {
     if (*p.abort) return;
+    if (MODE == kStage2 && p.step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(p.step_ctr, 1ull);   // the step completes (no abort seen)
     __shared__ float4 lut[64];
     fill_shift_table(lut, p.cell);
     __syncthreads();

@@ -329,7 +329,9 @@ def strip(seed: int = 5, length: float = 1.0e4, width: float = 2.0, depth: float
 
     ``x_window`` = (x0, x1) keeps only the lattice columns with x0 <= x < x1 (a
     bounded sample of the strip; inactive terrain is frozen, so a window that
-    contains every box plus its 2h extension steps identically)."""
+    contains every box plus its 2h extension steps identically).  The terrain is
+    taken as settled, so the boxes are in force from the first step
+    (t_delay = -1)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     p = default_params(d0, mu_s=0.8, cohesion=5000.0, av_mode=2, av_gamma=0.02)
     nx_all, ny, nz = int(round(length / d0)), int(round(width / d0)), int(round(depth / d0))
@@ -356,7 +358,7 @@ def strip(seed: int = 5, length: float = 1.0e4, width: float = 2.0, depth: float
     hi = np.array([length + margin, width + margin, depth + 2 * wheel_radius + margin])
     m = x.shape[0]
     return Scene("strip", p, x, np.zeros((m, 3)), sig, np.full(m, p["rho0"]), fl,
-                 bodies, boxes, 0.0, dt, n_steps, lo, hi)
+                 bodies, boxes, -1.0, dt, n_steps, lo, hi)
 
 
 def workload(name: str, **kw) -> Scene:

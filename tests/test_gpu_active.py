@@ -125,3 +125,37 @@ def test_active_eval_rates_match_oracle():
     ok = ~near
     assert np.all(np.abs(got - ref)[act & ok] <= 1e-5 * scale[act & ok] + 1e-30)
     assert np.all(got[~act & ok] == 0)
+
+
+def test_strip_window_far_from_origin_matches_oracle():
+    """The large-scale active-domain case (10 km strip at 0.025 m, four-wheel
+    kinematic rover at 1 m/s, a 1 m active box per wheel) on a 20 m window
+    around the rover at x = 5000 m: active / extended counts, particle states and
+    wheel wrenches follow the oracle; terrain outside the boxes stays frozen."""
+    sc = scenes.strip(x_window=(4995.0, 5015.0))
+    sc.t_delay = -1.0          # boxes in force from the first step
+    t = crm.from_scene(sc)
+    st = oracle.State(sc)
+    t.step(sc.dt, 0)
+    x0, _, s0, _ = t.particles()
+    n = 20
+    t.step(sc.dt, n)
+    st.run(n)
+    na, ne, nb = t.counts()
+    near = _near_face(st.x, sc.boxes, st.bodies.pose, sc.params["h"])
+    oa, oe = int((st.flags == 2).sum()), int((st.flags == 1).sum())
+    assert abs(na - oa) <= near.sum() and abs(ne - oe) <= near.sum(), (na, oa, ne, oe)
+    assert na > 20000
+    xyz, vel, sig, rho = t.particles()
+    d0 = sc.params["d0"]
+    dx = np.max(np.abs(xyz - st.x)) / d0
+    ds = np.sqrt(np.mean((sig - st.sig) ** 2)) / (sc.params["rho0"] * 9.81 * 0.1)
+    print("strip window: counts", (na, ne, nb), "oracle", (oa, oe), "dx/d0", dx, "dsig", ds)
+    assert dx < 1e-4 and ds < 1e-4
+    moved = np.any(st.x != sc.x, axis=1) | np.any(st.sig != sc.sig, axis=1)
+    assert (~moved).sum() > 100000
+    assert np.array_equal(xyz[~moved], x0[~moved]) and np.array_equal(sig[~moved], s0[~moved])
+    for b in range(4):
+        F, _ = t.body_wrench(b)
+        Fo = st.bodies.wrench[b, :3]
+        assert np.linalg.norm(F - Fo) <= 1e-3 * np.linalg.norm(Fo)
