@@ -91,7 +91,9 @@ typedef struct crm_params {
     double growth;         /* active-set capacity growth factor G (Sec. 3.2), >= 1 */
     double shrink_ratio;   /* shrink threshold S (Sec. 3.2), in (0, 1] */
     int32_t shrink_interval; /* shrink check interval S_I in steps (Sec. 3.2), >= 1 */
-    int32_t reserved;
+    int32_t pair_lanes;    /* lanes per fluid particle in the pair kernels on exact lists:
+                              1, 2, or 0 = the library default (2); a pure speed knob
+                              (crm_batch_autotune picks it per terrain) */
     double skin;           /* Verlet skin as a fraction of 2h, in [0, 1): with skin > 0
                               the cell sort and the 27-cell search run with radius
                               2h (1 + skin) only when some particle has moved skin * h
@@ -236,6 +238,39 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
  * CRM_EINVAL on a null output or out-of-range argument. */
 int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
                         double shrink_ratio, int32_t shrink_interval, int64_t *new_cap);
+
+/* Lanes per fluid particle in the exact-list pair kernels (1 or 2; 0 = the
+ * default): a speed knob with no effect on the method (the sums of a particle
+ * are split between the lanes and combined, so only their order changes). */
+int crm_set_pair_lanes(crm_terrain *t, int32_t lanes);
+
+/* ------------------------------------------------------------------------
+ * Batches (an ensemble of independent terrains, e.g. many single-wheel bins of
+ * uneven size; the paper runs one terrain at a time, this is the library's own
+ * addition).  Each member runs on its own non-default CUDA stream (members
+ * that share a stream run one after the other); a batch step enqueues one step
+ * of every member on its stream (one replayed step graph each), so members on
+ * different streams run concurrently, bracketed by a fork from and a join to
+ * the batch's stream.  The batch does not own its members. */
+typedef struct crm_batch crm_batch;
+
+/* Batch of n members (distinct handles, each on a non-default stream) joined on
+ * `stream` (nullable: the legacy default stream).  CRM_EINVAL on a null or
+ * repeated member or a member on the legacy default stream. */
+int crm_batch_create(int32_t n, crm_terrain *const *members, void *stream, crm_batch **out);
+
+/* n_steps steps of every member, member i with time step dt[i]; step-major
+ * order (step k of all members is enqueued before any step k + 1).  Returns the
+ * first member error. */
+int crm_batch_step(crm_batch *b, const double *dt, int32_t n_steps);
+
+/* Per-member tuning of crm_set_pair_lanes: each member runs 1 + trial_steps
+ * steps with each choice, timed on its own stream, and keeps the faster; the
+ * trial steps are ordinary steps (the simulation advances).  choice (nullable,
+ * n entries) receives the picks.  Synchronises the members' streams. */
+int crm_batch_autotune(crm_batch *b, const double *dt, int32_t trial_steps, int32_t *choice);
+
+int crm_batch_destroy(crm_batch *b);
 
 /* Per-kernel launch counts and CUDA-event timings of one handle (for
  * measurement).  Kernel ids 0..CRM_NUM_KERNELS-1, names from crm_kernel_name:

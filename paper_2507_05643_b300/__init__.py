@@ -51,7 +51,7 @@ class Params(C.Structure):
                 ("ps_freq", C.c_int32), ("max_neighbors", C.c_int32),
                 ("domain_min", C.c_double * 3), ("domain_max", C.c_double * 3),
                 ("growth", C.c_double), ("shrink_ratio", C.c_double),
-                ("shrink_interval", C.c_int32), ("reserved", C.c_int32),
+                ("shrink_interval", C.c_int32), ("pair_lanes", C.c_int32),
                 ("skin", C.c_double)]
 
 
@@ -82,6 +82,12 @@ _sig("crm_add_rigid_body", C.c_int, [_T, _i64, _vp, _vp, _vp, C.c_double, _i32,
 _sig("crm_set_body_motion", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_get_body_state", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_set_body_inertia", C.c_int, [_T, _i32, _vp])
+_sig("crm_set_pair_lanes", C.c_int, [_T, _i32])
+_B = C.c_void_p
+_sig("crm_batch_create", C.c_int, [_i32, C.POINTER(_T), _vp, C.POINTER(_B)])
+_sig("crm_batch_step", C.c_int, [_B, _vp, _i32])
+_sig("crm_batch_autotune", C.c_int, [_B, _vp, _i32, _vp])
+_sig("crm_batch_destroy", C.c_int, [_B])
 _sig("crm_set_body_load", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_add_active_box", C.c_int, [_T, _i32, _vp, _vp, C.c_double])
 _sig("crm_step", C.c_int, [_T, C.c_double, _i32])
@@ -114,7 +120,8 @@ KERNEL_NAMES = tuple(_lib.crm_kernel_name(k).decode() for k in range(NUM_KERNELS
 EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create", "crm_destroy",
            "crm_last_error", "crm_add_sph", "crm_add_fixed_bce", "crm_add_rigid_body",
            "crm_set_body_motion", "crm_get_body_state", "crm_set_body_inertia",
-           "crm_set_body_load", "crm_add_active_box", "crm_step",
+           "crm_set_body_load", "crm_add_active_box", "crm_step", "crm_set_pair_lanes",
+           "crm_batch_create", "crm_batch_step", "crm_batch_autotune", "crm_batch_destroy",
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
@@ -245,6 +252,9 @@ class Terrain:
     def set_body_motion(self, body: int, pose, twist):
         self._check(_lib.crm_set_body_motion(self._h, int(body), _ptr(_c(pose)), _ptr(_c(twist))))
 
+    def set_pair_lanes(self, lanes: int):
+        self._check(_lib.crm_set_pair_lanes(self._h, int(lanes)))
+
     def set_body_inertia(self, body: int, inertia):
         self._check(_lib.crm_set_body_inertia(self._h, int(body), _ptr(_c(inertia))))
 
@@ -344,6 +354,47 @@ def from_scene(scene, stream=None, **param_over) -> Terrain:
     for bx in scene.boxes:
         t.add_active_box(bx.body, bx.half_extents, bx.offset, scene.t_delay)
     return t
+
+
+class Batch:
+    """``crm_batch`` over Terrain members, each created with its own stream: one
+    call steps every member concurrently (the members stay owned by the caller)."""
+
+    def __init__(self, members, stream=None):
+        self.members = list(members)
+        arr = (_T * len(self.members))(*[m._h.value for m in self.members])
+        self._b = _B()
+        rc = _lib.crm_batch_create(len(self.members), arr, _stream_handle(stream),
+                                   C.byref(self._b))
+        if rc != CRM_OK:
+            raise CrmError(rc, "crm_batch_create: members need distinct handles, each on a stream")
+
+    def _dts(self, dt):
+        return _c(np.broadcast_to(np.asarray(dt, np.float64), (len(self.members),)))
+
+    def step(self, dt, n_steps: int = 1):
+        rc = _lib.crm_batch_step(self._b, _ptr(self._dts(dt)), int(n_steps))
+        if rc != CRM_OK:
+            raise CrmError(rc, "crm_batch_step failed (see the members' last errors)")
+
+    def autotune(self, dt, trial_steps: int = 3) -> np.ndarray:
+        choice = np.zeros(len(self.members), np.int32)
+        rc = _lib.crm_batch_autotune(self._b, _ptr(self._dts(dt)), int(trial_steps),
+                                     choice.ctypes.data_as(C.c_void_p))
+        if rc != CRM_OK:
+            raise CrmError(rc, "crm_batch_autotune failed")
+        return choice
+
+    def close(self):
+        if self._b:
+            _lib.crm_batch_destroy(self._b)
+            self._b = _B()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bin_points(xyz_ptr: int, n: int, cell_size: float, dims, cell_ptr: int, perm_ptr: int,

@@ -195,6 +195,7 @@ int validate(const crm_params *p, std::string &why)
             return bad("domain_max must exceed domain_min on every axis");
     if (!(p->growth >= 1.0) || !(p->shrink_ratio > 0 && p->shrink_ratio <= 1.0) || p->shrink_interval < 1)
         return bad("growth >= 1, shrink_ratio in (0, 1], shrink_interval >= 1");
+    if (p->pair_lanes < 0 || p->pair_lanes > 2) return bad("pair_lanes must be 0, 1 or 2");
     if (!(p->skin >= 0.0 && p->skin < 1.0)) return bad("skin must lie in [0, 1)");
     return CRM_OK;
 }
@@ -250,6 +251,7 @@ int make_devparams(crm_terrain *t)
     d.dmin_y = P.domain_min[1];
     d.dmin_z = P.domain_min[2];
     d.cell_d = cell;
+    d.pair_lanes = P.pair_lanes;
     d.maxnb = P.max_neighbors;
     d.sk_r2 = (float)(cell * cell);
     d.disp_thr2 = (float)(0.95 * skin * P.h * 0.95 * skin * P.h);
@@ -1587,6 +1589,130 @@ int crm_get_neighbors(crm_terrain *t, int64_t cap, int64_t *offset, int32_t *lis
         std::sort(list + o, list + o + nnb[s]);
     }
     return CRM_OK;
+}
+
+int crm_set_pair_lanes(crm_terrain *t, int32_t lanes)
+{
+    if (!t) return CRM_EINVAL;
+    if (lanes < 0 || lanes > 2) return t->fail(CRM_EINVAL, "crm_set_pair_lanes: 0, 1 or 2");
+    t->P.pair_lanes = lanes;
+    t->dp.pair_lanes = lanes;
+    t->drop_graphs();   // the captured launches hold the old choice
+    return CRM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: several terrains stepped together, each on its own stream, so that
+// small terrains share the GPU instead of leaving it partly idle one after the
+// other.  A step of the batch is one replayed step graph per member; the
+// batch's stream forks to the members' streams and joins them again.
+struct crm_batch {
+    std::vector<crm_terrain *> m;
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    std::string msg;
+};
+
+extern "C" {
+
+int crm_batch_create(int32_t n, crm_terrain *const *members, void *stream, crm_batch **out)
+{
+    if (!out || n < 1 || !members) return CRM_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!members[i] || members[i]->st == nullptr) return CRM_EINVAL;   // not the legacy stream
+        for (int k = 0; k < i; ++k)
+            if (members[k] == members[i]) return CRM_EINVAL;
+    }
+    crm_batch *b = new crm_batch();
+    b->m.assign(members, members + n);
+    b->st = (cudaStream_t)stream;
+    b->join.assign(n, nullptr);
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < n; ++i)
+        ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        crm_batch_destroy(b);
+        return CRM_ECUDA;
+    }
+    *out = b;
+    return CRM_OK;
+}
+
+int crm_batch_destroy(crm_batch *b)
+{
+    if (!b) return CRM_OK;
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    delete b;
+    return CRM_OK;
+}
+
+int crm_batch_step(crm_batch *b, const double *dt, int32_t n_steps)
+{
+    if (!b || !dt || n_steps < 0) return CRM_EINVAL;
+    const int n = (int)b->m.size();
+    if (cudaEventRecord(b->fork, b->st) != cudaSuccess) return CRM_ECUDA;
+    for (int i = 0; i < n; ++i)
+        if (cudaStreamWaitEvent(b->m[i]->st, b->fork, 0) != cudaSuccess) return CRM_ECUDA;
+    // step-major order: every member's step k is enqueued before any step k + 1
+    for (int s = 0; s < n_steps; ++s)
+        for (int i = 0; i < n; ++i) {
+            const int rc = crm_step(b->m[i], dt[i], 1);
+            if (rc) return rc;
+        }
+    for (int i = 0; i < n; ++i) {
+        if (cudaEventRecord(b->join[i], b->m[i]->st) != cudaSuccess) return CRM_ECUDA;
+        if (cudaStreamWaitEvent(b->st, b->join[i], 0) != cudaSuccess) return CRM_ECUDA;
+    }
+    return CRM_OK;
+}
+
+int crm_batch_autotune(crm_batch *b, const double *dt, int32_t trial_steps, int32_t *choice)
+{
+    if (!b || !dt || trial_steps < 1) return CRM_EINVAL;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return CRM_ECUDA;
+    }
+    int rc = CRM_OK;
+    for (size_t i = 0; i < b->m.size() && rc == CRM_OK; ++i) {
+        crm_terrain *t = b->m[i];
+        float best = 0.f;
+        int pick = 2;
+        for (int lanes = 1; lanes <= 2 && rc == CRM_OK; ++lanes) {
+            crm_set_pair_lanes(t, lanes);
+            rc = crm_step(t, dt[i], 1);   // capture the graphs outside the timing
+            if (rc) break;
+            cudaEventRecord(e0, t->st);
+            rc = crm_step(t, dt[i], trial_steps);
+            cudaEventRecord(e1, t->st);
+            if (rc) break;
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaGetLastError();
+                rc = CRM_ECUDA;
+                break;
+            }
+            if (lanes == 1 || ms < best) {
+                best = ms;
+                pick = lanes;
+            }
+        }
+        if (rc == CRM_OK) {
+            crm_set_pair_lanes(t, pick);
+            if (choice) choice[i] = pick;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 const char *crm_kernel_name(int32_t k)

@@ -54,6 +54,8 @@ struct DevParams {
     uint32_t ell;                         // stride of the neighbour table (>= capN)
     int n_bodies;
     uint32_t body_lo[kMaxBodies], body_hi[kMaxBodies];   // particle-id range of each body's markers
+    int pair_lanes;                       // lanes per fluid particle in the exact-list pair
+                                          // kernels: 1, 2, or 0 for the default
     unsigned long long *step_ctr;         // active domains: index of the running step (the
                                           // abort tag), advanced by pair stage 2; else null
     // device-resident sizes of the current working set: nF, nM, N, and the

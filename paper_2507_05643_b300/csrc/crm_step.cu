@@ -384,8 +384,9 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
                  const uint32_t *sk_nbr, const uint32_t *sk_nnb)
 {
     // filtering kernels keep one lane per particle (the lane group's ballot per
-    // candidate costs more than the extra warps gain); the others take kPairLanes
-    constexpr int LN = kPairLanes;
+    // candidate costs more than the extra warps gain); the others take
+    // p.pair_lanes (1 or 2; 0 = kPairLanes), a per-terrain tuning knob
+    const int LN = p.pair_lanes == 1 ? 1 : (p.pair_lanes == 2 ? 2 : kPairLanes);
     const unsigned g = grid_for((int64_t)p.capF * LN, kPairBlock);
     const unsigned g1 = grid_for(p.capF, kPairBlock);
     if (mode == kStage1 && sk_nbr != nullptr) {
@@ -401,15 +402,27 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
+    if (LN == 1) {
+        if (mode == kStage1)
+            k_pair<kStage1, false, 1><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                                err, nullptr, nullptr);
+        else if (mode == kStage2)
+            k_pair<kStage2, false, 1><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                                err, xref, gate);
+        else
+            k_pair<kEval, false, 1><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                              err, nullptr, nullptr);
+        return;
+    }
     if (mode == kStage1)
-        k_pair<kStage1, false, LN><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                             err, nullptr, nullptr);
+        k_pair<kStage1, false, 2><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                            err, nullptr, nullptr);
     else if (mode == kStage2)
-        k_pair<kStage2, false, LN><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                             err, xref, gate);
+        k_pair<kStage2, false, 2><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                            err, xref, gate);
     else
-        k_pair<kEval, false, LN><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                           nullptr, nullptr);
+        k_pair<kEval, false, 2><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
+                                                          nullptr, nullptr);
 }
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,

@@ -361,6 +361,30 @@ def strip(seed: int = 5, length: float = 1.0e4, width: float = 2.0, depth: float
                  bodies, boxes, -1.0, dt, n_steps, lo, hi)
 
 
+def ensemble_bins(seed: int = 4, n: int = 64, d0: float = 0.01) -> List[Scene]:
+    """The batched ensemble: n single-wheel soil bins of uneven size.  Bin k
+    draws u_k ~ U(0, 1) from its own stream (SeedSequence(seed).spawn(n)[k]):
+    target particle count 20k + 180k u_k and bin length 0.5 + 1.5 u_k m (size
+    and length coupled, so a 0.3 m wide bin keeps a plausible depth of
+    round(N / (100 L 30)) layers), then slip U(0.1, 0.7), friction U(25, 40) deg
+    and cohesion U(0, 2000) Pa independently; the grousered wheel of wheel_bin
+    (r = 0.2 m, width 0.15 m) at 0.2 m from the bin's start."""
+    out = []
+    for k, ss in enumerate(np.random.SeedSequence(seed).spawn(n)):
+        rng = np.random.Generator(np.random.PCG64(ss))
+        u = rng.uniform()
+        target = 20000 + 180000 * u
+        length = 0.5 + 1.5 * u
+        nx, ny = int(round(length / d0)), 30
+        nz = max(4, int(round(target / (nx * ny))))
+        slip = rng.uniform(0.1, 0.7)
+        phi = rng.uniform(25.0, 40.0)
+        coh = rng.uniform(0.0, 2000.0)
+        out.append(wheel_bin(seed=int(ss.generate_state(1)[0] % (2**31)), nx=nx, ny=ny, nz=nz, d0=d0,
+                             slip=slip, phi_deg=phi, cohesion=coh, wheel_x=0.3, n_steps=1000))
+    return out
+
+
 def workload(name: str, **kw) -> Scene:
     """Named workloads: 'settling_block' (8,000-particle block), 'wheel_bin'
     (120,000-particle grousered wheel bin), 'diff_wheel_bin' (30,000-particle bin),

@@ -92,3 +92,18 @@ def test_capacity_policy_matches_oracle():
             cap_b = oracle.capacity_policy(need, cap_b, step, G, S, SI)
             assert cap_a == cap_b
             assert cap_a >= need or step % SI == 0
+
+
+def test_batch_rejects_members_without_their_own_stream():
+    import paper_2507_05643_b300 as crm
+    a = crm.Terrain(crm.default_params())
+    b = crm.Terrain(crm.default_params())
+    with pytest.raises(crm.CrmError):
+        crm.Batch([a, b])              # both on the default stream
+    with pytest.raises(crm.CrmError):
+        crm.Batch([])
+    with pytest.raises(crm.CrmError):
+        a.set_pair_lanes(3)
+    a.set_pair_lanes(1)
+    a.close()
+    b.close()

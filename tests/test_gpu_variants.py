@@ -257,3 +257,41 @@ def test_sphere_drop_with_six_free_dofs_matches_oracle():
     assert twist[2] > -1.0 + 1e-3      # the bed has started to brake it
     assert rep[1][0] < 1e-9 and rep[1][1] < 1e-6 and rep[1][2] < 1e-6
     assert rep[100][0] < 1e-4 and rep[100][1] < 1e-3 and rep[100][2] < 1e-3
+
+
+# --------------------------------------------------------------------------
+# Batched ensemble (C4 shape): members stepped concurrently on their own streams
+
+def test_batch_steps_equal_members_stepped_alone():
+    """Three bins of uneven size and material stepped as one batch give bitwise
+    the states of the same bins stepped one at a time (same lane choice), and
+    the autotuner's picks are valid."""
+    import torch
+    bins = scenes.ensemble_bins(n=3)
+    for sc in bins:                 # small versions of the ensemble's bins
+        keep = sc.x[:, 0] < 0.6
+        sc.x, sc.u, sc.sig, sc.rho = sc.x[keep], sc.u[keep], sc.sig[keep], sc.rho[keep]
+    streams = [torch.cuda.Stream() for _ in bins]
+    mem = [crm.from_scene(sc, stream=s) for sc, s in zip(bins, streams)]
+    dts = [sc.dt for sc in bins]
+    batch = crm.Batch(mem, stream=torch.cuda.current_stream())
+    picks = batch.autotune(dts, trial_steps=2)
+    assert set(picks.tolist()) <= {1, 2}
+    batch.step(dts, 20)
+    torch.cuda.synchronize()
+    # the same bins alone, with the same lane picks and the same number of steps
+    for sc, pick, m in zip(bins, picks, mem):
+        alone = crm.from_scene(sc, stream=torch.cuda.Stream())
+        alone.set_pair_lanes(1)
+        alone.step(sc.dt, 3)       # autotune ran 3 steps with 1 lane, then 3 with 2
+        alone.set_pair_lanes(2)
+        alone.step(sc.dt, 3)
+        alone.set_pair_lanes(int(pick))
+        alone.step(sc.dt, 20)
+        xa, va, sa, ra = alone.particles()
+        xb, vb, sb, rb = m.particles()
+        assert np.array_equal(xa, xb) and np.array_equal(sa, sb) and np.array_equal(ra, rb)
+        Fa, _ = alone.body_wrench(0)
+        Fb, _ = m.body_wrench(0)
+        assert np.array_equal(Fa, Fb)
+    batch.close()
