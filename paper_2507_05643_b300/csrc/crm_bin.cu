@@ -325,79 +325,131 @@ __global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restr
 // its right end) and a bottom run of the right cell (read until the x-gap alone
 // reaches the remaining radius) can hold neighbours.  (Both cut-offs carry a
 // 1e-5 relative margin, so they never drop a pair the full test would keep.)
-// The list is an ELL table
-// nbr[k * ell + s] (coalesced across a warp); each entry is j | code << 26 with
+// The list is an ELL table nbr[k * ell + s] (coalesced across a warp) in
+// ascending slot order (fluid segment first, cells in key order, each cell
+// upwards), so the k-th entries of neighbouring particles -- neighbouring lanes
+// of the pair kernels -- are close in memory; each entry is j | code << 26 with
 // code = (dx+1) | (dy+1) << 2 | (dz+1) << 4, which the pair kernels use to
 // rebuild x_s - x_j from the cell-relative offsets.
+//
+// One row (dy, dz) of the 27-cell stencil in segment seg (0 fluid, 1 markers):
+// the neighbours of particle s in cells dx = -1, 0, 1, counted and, with `nbr`,
+// written from list position `at` on (ascending slot order).
+__device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *__restrict__ pos,
+                                             const uint32_t *__restrict__ start, const Window &W,
+                                             int s, const float4 &ps, int lx, int ly, int lz,
+                                             int seg, int dy, int dz, float r2cut, float lim2,
+                                             uint32_t *__restrict__ nbr, int at, int cap)
+{
+    const int lz2 = lz + dz, ly2 = ly + dy;
+    if (lz2 < 0 || lz2 >= W.Z || ly2 < 0 || ly2 >= W.Y) return 0;
+    const float cell = p.cell;
+    const float gz = dz < 0 ? fmaxf(ps.z, 0.f) : (dz > 0 ? fmaxf(cell - ps.z, 0.f) : 0.f);
+    const float gy = dy < 0 ? fmaxf(ps.y, 0.f) : (dy > 0 ? fmaxf(cell - ps.y, 0.f) : 0.f);
+    const float d2 = gy * gy + gz * gz;
+    if (d2 >= lim2) return 0;
+    const float R = sqrtf(lim2 - d2);
+    const float sy = ps.y - (float)dy * cell, sz = ps.z - (float)dz * cell;
+    const uint32_t kb = seg * p.M + ((uint32_t)lz2 * (uint32_t)W.Y + (uint32_t)ly2) * (uint32_t)W.X;
+    const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
+    int cnt = 0;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+        const int lx2 = lx + dx;
+        if (lx2 < 0 || lx2 >= W.X) continue;
+        const int jb = (int)start[kb + lx2], je = (int)start[kb + lx2 + 1];
+        const float sx = ps.x - (float)dx * cell;
+        const uint32_t tag = ((uint32_t)(dx + 1) | codeyz) << kIndexBits;
+        // cells are x-sorted: in the left cell only a top run is within R in
+        // x (found walking down), in the right cell only a bottom run
+        int j0 = jb;
+        if (dx < 0) {
+            j0 = je;
+            while (j0 > jb && fabsf(sx - pos[j0 - 1].x) < R) --j0;
+        }
+        for (int j = j0; j < je; ++j) {
+            const float4 pj = pos[j];
+            const float rx = sx - pj.x;
+            if (dx > 0 && fabsf(rx) >= R) break;
+            const float ry = sy - pj.y, rz = sz - pj.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 < r2cut && j != s) {
+                if (nbr != nullptr && at + cnt < cap) nbr[(size_t)(at + cnt) * p.ell + s] = (uint32_t)j | tag;
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+// LANES lanes share a particle.  One lane walks the 18 rows (fluid then marker
+// segment, each dz-major) in order, writing as it goes.  With four, the rows are
+// dealt out round robin; the lanes count their rows, agree on the rows' offsets
+// by shuffles, and write their rows' entries there: the same list at about a
+// quarter of the serial latency but twice the reads, which pays only while the
+// grid is smaller than the GPU (launch_neighbors picks).
+template <int LANES>
 __global__ void __launch_bounds__(kBlock)
 k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restrict__ start,
             uint32_t *__restrict__ nbr, uint32_t *__restrict__ nnb, int cap, float r2cut,
             int *__restrict__ err)
 {
+    constexpr int kSearchLanes = LANES;
     if (*p.abort || gated_off(p)) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = t / kSearchLanes, q = t % kSearchLanes;
     const Sizes z = load_sizes(p);
-    if (s >= z.N) return;
+    const bool valid = s < z.N;
     const Window W = load_window(p);
-    const float4 ps = pos[s];
-    int ix, iy, iz;
-    decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
-    const int lx = ix - W.x0, ly = iy - W.y0, lz = iz - W.z0;
-    const int nseg = s < z.nF ? 2 : 1;
-    const float cell = p.cell;
-    const float lim2 = r2cut * (1.0f + 1e-5f);
-    // Entries come out in ascending slot order (fluid segment first, cells in
-    // key order, each cell upwards), so the k-th entries of neighbouring
-    // particles -- neighbouring lanes of the pair kernels -- are close in
-    // memory and their gathers share cache lines.
-    int cnt = 0;
-    for (int seg = 0; seg < nseg; ++seg) {
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int lz2 = lz + dz;
-            if (lz2 < 0 || lz2 >= W.Z) continue;
-            const float gz = dz < 0 ? fmaxf(ps.z, 0.f) : (dz > 0 ? fmaxf(cell - ps.z, 0.f) : 0.f);
-            const float sz = ps.z - (float)dz * cell;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int ly2 = ly + dy;
-                if (ly2 < 0 || ly2 >= W.Y) continue;
-                const float gy = dy < 0 ? fmaxf(ps.y, 0.f) : (dy > 0 ? fmaxf(cell - ps.y, 0.f) : 0.f);
-                const float d2 = gy * gy + gz * gz;
-                if (d2 >= lim2) continue;
-                const float R = sqrtf(lim2 - d2);
-                const float sy = ps.y - (float)dy * cell;
-                const uint32_t kb = seg * p.M + ((uint32_t)lz2 * (uint32_t)W.Y + (uint32_t)ly2) * (uint32_t)W.X;
-                const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int lx2 = lx + dx;
-                    if (lx2 < 0 || lx2 >= W.X) continue;
-                    const int jb = (int)start[kb + lx2], je = (int)start[kb + lx2 + 1];
-                    const float sx = ps.x - (float)dx * cell;
-                    const uint32_t tag = ((uint32_t)(dx + 1) | codeyz) << kIndexBits;
-                    // cells are x-sorted: in the left cell only a top run is within R in
-                    // x (found walking down), in the right cell only a bottom run
-                    int j0 = jb;
-                    if (dx < 0) {
-                        j0 = je;
-                        while (j0 > jb && fabsf(sx - pos[j0 - 1].x) < R) --j0;
-                    }
-                    for (int j = j0; j < je; ++j) {
-                        const float4 pj = pos[j];
-                        const float rx = sx - pj.x;
-                        if (dx > 0 && fabsf(rx) >= R) break;
-                        const float ry = sy - pj.y, rz = sz - pj.z;
-                        const float r2 = rx * rx + ry * ry + rz * rz;
-                        if (r2 < r2cut && j != s) {
-                            if (cnt < cap) nbr[(size_t)cnt * p.ell + s] = (uint32_t)j | tag;
-                            ++cnt;
-                        }
-                    }
-                }
-            }
-        }
+    float4 ps = make_float4(0.f, 0.f, 0.f, 0.f);
+    int lx = 0, ly = 0, lz = 0;
+    if (valid) {
+        ps = pos[s];
+        int ix, iy, iz;
+        decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
+        lx = ix - W.x0; ly = iy - W.y0; lz = iz - W.z0;
     }
-    if (cnt > cap) atomicOr(err, ERR_CAPACITY);
-    nnb[s] = (uint32_t)min(cnt, cap);
+    const int rows = valid ? (s < z.nF ? 18 : 9) : 0;
+    const float lim2 = r2cut * (1.0f + 1e-5f);
+    if constexpr (LANES == 1) {
+        if (!valid) return;
+        int cnt = 0;
+        for (int r = 0; r < rows; ++r)
+            cnt += row_neighbors(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
+                                 r % 3 - 1, r2cut, lim2, nbr, cnt, cap);
+        if (cnt > cap) atomicOr(err, ERR_CAPACITY);
+        nnb[s] = (uint32_t)min(cnt, cap);
+        return;
+    }
+    constexpr int kPer = (18 + kSearchLanes - 1) / kSearchLanes;
+    int c[kPer], off[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int r = k * kSearchLanes + q;
+        c[k] = r < rows ? row_neighbors(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
+                                        r % 3 - 1, r2cut, lim2, nullptr, 0, cap) : 0;
+        off[k] = 0;
+    }
+    // rows in order: row r is lane (r % 4)'s entry r / 4
+    const int base = (threadIdx.x & 31) & ~(kSearchLanes - 1);
+    int run = 0;
+#pragma unroll
+    for (int r = 0; r < 18; ++r) {
+        const int n_r = __shfl_sync(0xffffffffu, c[r / kSearchLanes], base + r % kSearchLanes);
+        if (r % kSearchLanes == q) off[r / kSearchLanes] = run;
+        run += n_r;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int r = k * kSearchLanes + q;
+        if (r < rows && c[k] > 0)
+            row_neighbors(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1, r % 3 - 1,
+                          r2cut, lim2, nbr, off[k], cap);
+    }
+    if (valid && q == 0) {
+        if (run > cap) atomicOr(err, ERR_CAPACITY);
+        nnb[s] = (uint32_t)min(run, cap);
+    }
 }
 
 // Host launchers of the terrain rebuild, one kernel each.
@@ -427,7 +479,13 @@ void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *st
 void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
                       uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st)
 {
-    k_neighbors<<<grid_for(p.capN), kBlock, 0, st>>>(p, pos, start, nbr, nnb, cap, r2cut, err);
+    // four lanes per particle while they still fit one wave of the GPU's threads
+    if ((int64_t)p.capN * 4 <= 148LL * 2048)
+        k_neighbors<4><<<grid_for((int64_t)p.capN * 4), kBlock, 0, st>>>(p, pos, start, nbr, nnb,
+                                                                         cap, r2cut, err);
+    else
+        k_neighbors<1><<<grid_for(p.capN), kBlock, 0, st>>>(p, pos, start, nbr, nnb, cap, r2cut,
+                                                            err);
 }
 
 // ---------------------------------------------------------------------------
