@@ -230,6 +230,71 @@ int crm_state_bytes(crm_terrain *t, size_t *bytes);
 int crm_save_state(crm_terrain *t, void *dev_buf, size_t cap, size_t *used);
 int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
 
+/* ---- Reverse sweep (adjoint) --------------------------------------------
+ * The paper differentiates nothing; these calls are this library's
+ * hand-derived adjoint of the discrete method of Sec. 2.1-2.4 (pair sums,
+ * Jaumann rate, artificial viscosity, BCE extrapolation, return map of Sec. 2.3
+ * with a constant friction coefficient, midpoint step, body update of Sec.
+ * 2.4), in FP32 on the device with FP64 sums of the parameter and body
+ * adjoints.  Neighbour lists are those of the forward evaluation, held fixed,
+ * and every branch is the one the forward took (the adjoint is that of the
+ * piecewise-smooth map at the evaluated point).  Rigid-body rotations are
+ * held fixed.  Not differentiated (CRM_EINVAL): active domains; in runs also
+ * a Verlet skin or ps_freq > 1, mu(I) (mu_2 != mu_s) and bodies with a free
+ * rotational DOF. */
+
+/* Indices of the parameter gradients. */
+#define CRM_GRAD_E          0
+#define CRM_GRAD_NU         1
+#define CRM_GRAD_RHO0       2   /* with the particle mass m = rho0 d0^3 and the
+                                 * marker density following rho0; the particles'
+                                 * own densities are state */
+#define CRM_GRAD_MU_S       3
+#define CRM_GRAD_COHESION   4
+#define CRM_GRAD_AV_GAMMA   5
+#define CRM_NUM_GRADS       6
+
+/* Vector-Jacobian product of crm_eval_rates at the current state.  Inputs,
+ * insertion order, each nullable (= zero): l_drho (n_sph), l_dvel (n_sph*3),
+ * l_dstress (n_sph*6), l_macc (n_markers*3, the marker accelerations that
+ * crm_eval_rates returns).  Outputs, each nullable: the adjoints of the SPH
+ * positions (g_xyz, n_sph*3), velocities (g_vel), stresses (g_stress, n_sph*6,
+ * xx yy zz xy xz yz as independent entries), densities (g_rho, n_sph); of each
+ * body's centre, linear velocity and linear acceleration (g_body, 9 per body);
+ * of the parameters (g_params, CRM_NUM_GRADS).  The output of
+ * crm_eval_rates is sum(l . rates); the returned adjoints are its gradient.
+ * Rebuilds the lists like crm_eval_rates; allocates its workspace once (kept
+ * with the terrain).  Synchronises the stream. */
+int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, const float *l_dvel,
+                       const float *l_dstress, int64_t cap_markers, const float *l_macc,
+                       double *g_xyz, double *g_vel, double *g_stress, double *g_rho,
+                       double *g_body, double *g_params);
+
+/* Differentiable run, forward half: n_steps steps of dt (as crm_step) with a
+ * checkpoint of the state every `every` steps and after the last, and the
+ * bodies after each step.  wrench_hist (n_steps*n_bodies*6: the soil force and
+ * torque of each step, as crm_get_body_wrench) and pose_hist
+ * (n_steps*n_bodies*7: the pose after each step) are nullable.  Device memory:
+ * the checkpoints (ceil(n_steps / every) + 1 states of crm_state_bytes) and the
+ * tape of one segment (`every` steps of stage arrays and lists), freed by the
+ * next call or crm_destroy.  Synchronises the stream. */
+int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t every,
+                        double *wrench_hist, double *pose_hist);
+
+/* Differentiable run, backward half: for an objective J of the recorded run
+ * with dJ / d wrench given as l_wrench (n_steps*n_bodies*6) and dJ / d centre
+ * after each step as l_center (n_steps*n_bodies*3), both nullable (= zero),
+ * returns dJ / d parameters (g_params, CRM_NUM_GRADS) and the adjoints of the
+ * run's initial state: SPH positions, velocities, stresses, densities
+ * (insertion order, as crm_eval_rates_vjp) and bodies (g_body: centre, linear
+ * velocity, linear acceleration, 9 per body); each output nullable.  Re-runs
+ * every segment from its checkpoint (with direct launches) and sweeps it in
+ * reverse; leaves the terrain in the state after the recorded run.
+ * CRM_ESTATE without a recorded run.  Synchronises the stream. */
+int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l_center,
+                         double *g_params, double *g_xyz, double *g_vel, double *g_stress,
+                         double *g_rho, double *g_body);
+
 /* Array-capacity policy of ManageArrayMemory (Sec. 3.2): the capacity that
  * follows `cap` when `need` elements are required at step `step`: grown to
  * ceil(need * growth) when need > cap; shrunk to need when step is a multiple
@@ -277,8 +342,9 @@ int crm_batch_destroy(crm_batch *b);
  * keys, scan, scatter, reorder, neighbors (cell search), compact (markers with
  * fluid in reach), bce (with the body wrench and update), pair_stage1,
  * pair_stage2 (with a skin, the first-stage kernels after a rebuild also filter
- * the exact lists), skin (search decision and copy-back), export. */
-#define CRM_NUM_KERNELS 11
+ * the exact lists), skin (search decision and copy-back), export, adjoint (the
+ * reverse-sweep kernels of crm_eval_rates_vjp and crm_adjoint_backward). */
+#define CRM_NUM_KERNELS 12
 typedef struct crm_profile {
     int64_t launches[CRM_NUM_KERNELS]; /* kernels enqueued since the last reset */
     double ms[CRM_NUM_KERNELS];        /* summed event-timed durations (timing on) */

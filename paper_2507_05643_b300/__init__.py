@@ -32,6 +32,9 @@ STATUS = {0: "CRM_OK", -1: "CRM_EINVAL", -2: "CRM_ENOMEM", -3: "CRM_ECAPACITY",
 AV_NONE, AV_BILATERAL, AV_UNILATERAL = 0, 1, 2
 DOF_X, DOF_Y, DOF_Z, DOF_RX, DOF_RY, DOF_RZ = 1, 2, 4, 8, 16, 32
 KERNEL_CUBIC, KERNEL_WENDLAND = 0, 1
+# parameter gradients of the reverse sweep, in this order
+GRAD_NAMES = ("E", "nu", "rho0", "mu_s", "cohesion", "av_gamma")
+NUM_GRADS = len(GRAD_NAMES)
 
 
 class CrmError(RuntimeError):
@@ -97,13 +100,17 @@ _sig("crm_get_body_wrench", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_get_counts", C.c_int, [_T, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)])
 _sig("crm_eval_rates", C.c_int, [_T, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp])
 _sig("crm_get_neighbors", C.c_int, [_T, _i64, _vp, _vp, C.POINTER(_i64)])
+_sig("crm_eval_rates_vjp", C.c_int, [_T, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
+                                     _vp, _vp])
+_sig("crm_adjoint_forward", C.c_int, [_T, C.c_double, _i64, _i32, _vp, _vp])
+_sig("crm_adjoint_backward", C.c_int, [_T, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp])
 _sig("crm_state_bytes", C.c_int, [_T, C.POINTER(C.c_size_t)])
 _sig("crm_save_state", C.c_int, [_T, _vp, C.c_size_t, C.POINTER(C.c_size_t)])
 _sig("crm_load_state", C.c_int, [_T, _vp, C.c_size_t])
 _sig("crm_bin_scratch_bytes", C.c_size_t, [_i64, _i64])
 _sig("crm_bin_points", C.c_int, [_vp, _i64, C.c_float, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp])
 
-NUM_KERNELS = 11
+NUM_KERNELS = 12
 
 
 class Profile(C.Structure):
@@ -126,7 +133,8 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
            "crm_profile_reset", "crm_profile_read", "crm_bin_points_noalloc",
-           "crm_capacity_policy")
+           "crm_capacity_policy", "crm_eval_rates_vjp", "crm_adjoint_forward",
+           "crm_adjoint_backward")
 
 
 _sig("crm_capacity_policy", C.c_int, [_i64, _i64, _i64, C.c_double, C.c_double, _i32,
@@ -301,6 +309,50 @@ class Terrain:
         self._check(_lib.crm_eval_rates(self._h, n, _ptr(drho), _ptr(du), _ptr(ds), m, _ptr(ma),
                                         _ptr(mv), _ptr(ms)))
         return drho, du, ds, ma, mv, ms
+
+    def _grads(self, call) -> dict:
+        n, nb = self.n_sph, self.n_bodies
+        out = {"params": np.zeros(NUM_GRADS), "xyz": np.zeros((n, 3)), "vel": np.zeros((n, 3)),
+               "stress": np.zeros((n, 6)), "rho": np.zeros(n), "body": np.zeros((max(nb, 1), 9))}
+        self._check(call(out))
+        out["body"] = out["body"][:nb]
+        out["param_grads"] = dict(zip(GRAD_NAMES, (float(v) for v in out["params"])))
+        return out
+
+    def eval_rates_vjp(self, l_drho=None, l_dvel=None, l_dstress=None, l_macc=None) -> dict:
+        """Gradient of sum(l . rates of eval_rates) at the current state (each l
+        optional): {'xyz', 'vel', 'stress', 'rho' (per SPH particle), 'body'
+        (centre, velocity, acceleration per body), 'params' (GRAD_NAMES order),
+        'param_grads' (by name)}."""
+        n, m = self.n_sph, self.n_markers
+
+        def arr(a, shape):
+            return None if a is None else np.ascontiguousarray(np.asarray(a, np.float32).reshape(shape))
+        ld, lu, ls, lm = arr(l_drho, (n,)), arr(l_dvel, (n, 3)), arr(l_dstress, (n, 6)), arr(l_macc, (m, 3))
+        return self._grads(lambda o: _lib.crm_eval_rates_vjp(
+            self._h, n, _ptr(ld), _ptr(lu), _ptr(ls), m, _ptr(lm), _ptr(o["xyz"]), _ptr(o["vel"]),
+            _ptr(o["stress"]), _ptr(o["rho"]), _ptr(o["body"]), _ptr(o["params"])))
+
+    def adjoint_forward(self, dt: float, n_steps: int, every: int) -> Tuple[np.ndarray, np.ndarray]:
+        """Run n_steps steps with checkpoints every `every` steps; returns the soil
+        wrench (n_steps, n_bodies, 6) and the pose (n_steps, n_bodies, 7) after
+        each step."""
+        nb = self.n_bodies
+        w = np.zeros((n_steps, max(nb, 1), 6))
+        q = np.zeros((n_steps, max(nb, 1), 7))
+        self._check(_lib.crm_adjoint_forward(self._h, float(dt), int(n_steps), int(every),
+                                             _ptr(w), _ptr(q)))
+        return w[:, :nb], q[:, :nb]
+
+    def adjoint_backward(self, l_wrench=None, l_center=None) -> dict:
+        """Gradient of an objective of the recorded run given dJ/d wrench
+        (n_steps, n_bodies, 6) and dJ/d centre after each step (n_steps,
+        n_bodies, 3): parameters and the initial state, as eval_rates_vjp."""
+        lw = None if l_wrench is None else np.ascontiguousarray(np.asarray(l_wrench, np.float64))
+        lc = None if l_center is None else np.ascontiguousarray(np.asarray(l_center, np.float64))
+        return self._grads(lambda o: _lib.crm_adjoint_backward(
+            self._h, _ptr(lw), _ptr(lc), _ptr(o["params"]), _ptr(o["xyz"]), _ptr(o["vel"]),
+            _ptr(o["stress"]), _ptr(o["rho"]), _ptr(o["body"])))
 
     def neighbors(self) -> Tuple[np.ndarray, np.ndarray]:
         n = self.n_sph + self.n_markers

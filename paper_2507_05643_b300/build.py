@@ -4,7 +4,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["crm_bin.cu", "crm_step.cu", "crm_bce.cu", "crm_active.cu", "crm_api.cu"]
+SOURCES = ["crm_bin.cu", "crm_step.cu", "crm_bce.cu", "crm_active.cu", "crm_adjoint.cu", "crm_api.cu"]
 LIB = os.path.join(HERE, "libcrm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,981 @@
+// crm_adjoint.cu -- reverse sweep (vector-Jacobian product) of the rate
+// evaluation and of the midpoint step (Sec. 2.1-2.4), hand-derived.
+//
+// Forward, for a target i (a fluid particle, or a marker for its acceleration)
+// and a list neighbour j: r = x_i - x_j, g = F(|r|) r with F = W'(r) / r,
+// V_j = m / rho_j, u = u_j - u_i,
+//   cont += V_j u.g,  M += V_j (sigma_i + sigma_j) g,  L += V_j u (x) g,
+//   A += f g,  f = 2 c vr / ((rho_i + rho_j)(r^2 + xi^2)),  vr = -u.r  (when the
+//   viscosity acts),  c = gamma h sqrt(K / rho0) m.
+// Fluid rates: rho' = -rho_i cont, u' = M / rho_i + g + A, sigma' = Jaumann(L, sigma_i).
+// Marker acceleration a = M / rho0 + A (rho_i = rho0), force m a.
+// Marker state (BCE, Sec. 2.4) over the fluid f in reach, W = W(|x_a - x_f|):
+//   w = sum W, su = sum u_f W, ss = sum sigma_f W, sr = sum rho_f (x_a - x_f) W,
+//   u_a = 2 u_b - su / w,  sigma_a = (ss - ((g - a_b).sr) I) / w  (w > 0), else
+//   u_a = u_b, sigma_a = 0.
+//
+// The sweep is in gather form -- every thread owns the adjoints it writes, no
+// float atomics on particle data -- in four passes per stage:
+//   fluid coefficients  adjoints of (cont, M, L, A) of every fluid target and the
+//                       local terms (Jaumann, 1/rho_i, the return map, the
+//                       integrator's identity parts);
+//   marker coefficients adjoints of (M, A) of every marker target (the rate
+//                       evaluation's marker accelerations, or a step's body wrench);
+//   marker gather       per marker: the adjoint of its BCE state (from the fluid
+//                       pairs that read it and its own acceleration pairs), the
+//                       BCE coefficients (w, su, ss, sr), the terms of its own
+//                       position, summed per body (FP64);
+//   fluid gather        per fluid particle: its own pairs (its coefficients), the
+//                       pairs of the neighbours that read it (their
+//                       coefficients), and its share of the markers' BCE sums.
+// Neighbour lists are those of the forward (frozen) and every branch (the
+// unilateral viscosity switch, the return map's cases, an empty BCE sum) is the
+// one the forward took.  Rigid-body rotations are held fixed: the body adjoints
+// are those of the centre, the linear velocity and the linear acceleration.
+#include "crm_adjoint.cuh"
+
+namespace crm {
+
+constexpr int kAdjBlock = 128;
+
+// dF/dr for F(r) = W'(r) / r: (W'' - F) / r.
+__device__ __forceinline__ float kernel_dF_dr(float q, float rinv, const DevParams &p)
+{
+    if (p.kernel == CRM_KERNEL_WENDLAND) {
+        const float t = 1.0f - 0.5f * q;
+        return -1.5f * p.kdw * t * t * p.inv_h;   // F = kdw (1 - q/2)^3
+    }
+    const float F = kernel_dw_over_r(q, rinv, p);
+    // cubic: W'' = kdw / h (4.5 q - 3) for q < 1, 1.5 kdw / h (2 - q) for 1 <= q < 2
+    const float w2 = q < 1.0f ? p.kdw * p.inv_h * (4.5f * q - 3.0f)
+                              : 1.5f * p.kdw * p.inv_h * (2.0f - q);
+    return (w2 - F) * rinv;
+}
+
+// Adjoints of one target's pair sums.
+struct Coef {
+    float lc, lM[3], lL[9], lA[3];   // cont, M, L (row-major), A
+};
+
+__device__ __forceinline__ Coef load_coef(const float *c, int64_t cs, int s)
+{
+    Coef C;
+    C.lc = c[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C.lM[k] = c[(1 + k) * cs + s];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) C.lL[k] = c[(4 + k) * cs + s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C.lA[k] = c[(13 + k) * cs + s];
+    return C;
+}
+
+__device__ __forceinline__ void store_coef(float *c, int64_t cs, int s, const Coef &C)
+{
+    c[s] = C.lc;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[(1 + k) * cs + s] = C.lM[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c[(4 + k) * cs + s] = C.lL[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[(13 + k) * cs + s] = C.lA[k];
+}
+
+// Adjoint of one particle's inputs: position, velocity, stress, density.
+struct Adj {
+    float x[3], u[3], s[6], rho;
+};
+
+__device__ __forceinline__ void adj_zero(Adj &a)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a.x[k] = a.u[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.s[k] = 0.f;
+    a.rho = 0.f;
+}
+
+__device__ __forceinline__ void adj_load(const float *a, int64_t st, int64_t s, Adj &o)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o.x[k] = a[(kAdjX + k) * st + s];
+        o.u[k] = a[(kAdjU + k) * st + s];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.s[k] = a[(kAdjS + k) * st + s];
+    o.rho = a[kAdjR * st + s];
+}
+
+__device__ __forceinline__ void adj_store(float *a, int64_t st, int64_t s, const Adj &o)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a[(kAdjX + k) * st + s] = o.x[k];
+        a[(kAdjU + k) * st + s] = o.u[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[(kAdjS + k) * st + s] = o.s[k];
+    a[kAdjR * st + s] = o.rho;
+}
+
+// Parameter adjoints of one thread (FP64).
+struct ParAcc {
+    double v[kNumGradAcc];
+};
+
+__device__ __forceinline__ void par_zero(ParAcc &a)
+{
+#pragma unroll
+    for (int k = 0; k < kNumGradAcc; ++k) a.v[k] = 0.0;
+}
+
+// Block sum of the parameter adjoints, one FP64 atomic per block and entry.
+__device__ __forceinline__ void par_flush(const ParAcc &a, double *g)
+{
+    __shared__ double red[kAdjBlock / 32][kNumGradAcc];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kNumGradAcc; ++k) {
+        double v = a.v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumGradAcc) {
+        double s = 0.0;
+        for (int w = 0; w < kAdjBlock / 32; ++w) s += red[w][threadIdx.x];
+        if (s != 0.0) atomicAdd(g + threadIdx.x, s);
+    }
+}
+
+// Particle state as the pair kernels read it.
+struct PState {
+    float4 v;    // u, rho
+    float4 a;    // sigma xx yy zz xy
+    float2 b;    // sigma xz yz
+};
+
+__device__ __forceinline__ PState load_state(const StageArrays &S, int s)
+{
+    return PState{S.vel[s], S.sA[s], S.sB[s]};
+}
+
+// Backward of one pair (target i, neighbour j, r = x_i - x_j, 0 < |r| < 2h):
+// adds the i-side input adjoints to *ai, the j-side ones to *aj (either may be
+// null), and, with `par`, the pair's parameter terms (m through V_j, the
+// viscosity constant) to *par.  rho_i of a marker target is rho0.
+__device__ __forceinline__ void pair_vjp(const DevParams &p, const Coef &C, float rx, float ry,
+                                         float rz, float r2, const PState &I, float rho_i,
+                                         const PState &J, Adj *ai, Adj *aj, ParAcc *par)
+{
+    const float rinv = rsqrtf(r2);
+    const float q = r2 * rinv * p.inv_h;
+    const float F = kernel_dw_over_r(q, rinv, p);
+    const float g[3] = {F * rx, F * ry, F * rz};
+    const float rho_j = J.v.w;
+    const float Vj = p.m / rho_j;
+    const float u[3] = {J.v.x - I.v.x, J.v.y - I.v.y, J.v.z - I.v.z};
+    // (sigma_i + sigma_j), symmetric
+    const float Sxx = I.a.x + J.a.x, Syy = I.a.y + J.a.y, Szz = I.a.z + J.a.z;
+    const float Sxy = I.a.w + J.a.w, Sxz = I.b.x + J.b.x, Syz = I.b.y + J.b.y;
+    const float Sg[3] = {Sxx * g[0] + Sxy * g[1] + Sxz * g[2], Sxy * g[0] + Syy * g[1] + Syz * g[2],
+                         Sxz * g[0] + Syz * g[1] + Szz * g[2]};
+    const float SlM[3] = {Sxx * C.lM[0] + Sxy * C.lM[1] + Sxz * C.lM[2],
+                          Sxy * C.lM[0] + Syy * C.lM[1] + Syz * C.lM[2],
+                          Sxz * C.lM[0] + Syz * C.lM[1] + Szz * C.lM[2]};
+    float Lg[3], LTu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Lg[a] = C.lL[3 * a] * g[0] + C.lL[3 * a + 1] * g[1] + C.lL[3 * a + 2] * g[2];
+        LTu[a] = C.lL[a] * u[0] + C.lL[3 + a] * u[1] + C.lL[6 + a] * u[2];
+    }
+    float gb[3], ub[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gb[k] = Vj * (C.lc * u[k] + SlM[k] + LTu[k]);
+        ub[k] = Vj * (C.lc * g[k] + Lg[k]);
+    }
+    const float Vb = C.lc * (u[0] * g[0] + u[1] * g[1] + u[2] * g[2])
+                     + C.lM[0] * Sg[0] + C.lM[1] * Sg[1] + C.lM[2] * Sg[2]
+                     + u[0] * Lg[0] + u[1] * Lg[1] + u[2] * Lg[2];
+    // both stresses: V_j sym(lM (x) g), off-diagonals counted twice
+    const float sb[6] = {Vj * C.lM[0] * g[0], Vj * C.lM[1] * g[1], Vj * C.lM[2] * g[2],
+                         Vj * (C.lM[0] * g[1] + C.lM[1] * g[0]),
+                         Vj * (C.lM[0] * g[2] + C.lM[2] * g[0]),
+                         Vj * (C.lM[1] * g[2] + C.lM[2] * g[1])};
+    float rb[3] = {0.f, 0.f, 0.f};
+    float rsum_b = 0.f;
+    if (p.av_mode != CRM_AV_NONE) {
+        const float vr = -(u[0] * rx + u[1] * ry + u[2] * rz);
+        if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+            const float rs = rho_i + rho_j, d2 = r2 + p.xi2;
+            const float inv = 1.0f / (rs * d2);
+            const float fac = 2.0f * p.av_c * vr * inv;
+            const float fb = C.lA[0] * g[0] + C.lA[1] * g[1] + C.lA[2] * g[2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gb[k] += fac * C.lA[k];
+            const float vrb = 2.0f * p.av_c * fb * inv;
+            rsum_b = -fb * fac / rs;
+            const float r2b = -fb * fac / d2;
+            if (par) par->v[kGradAvc] += (double)(2.0f * vr * fb * inv);
+            ub[0] -= vrb * rx; ub[1] -= vrb * ry; ub[2] -= vrb * rz;
+            rb[0] += 2.0f * r2b * rx - vrb * u[0];
+            rb[1] += 2.0f * r2b * ry - vrb * u[1];
+            rb[2] += 2.0f * r2b * rz - vrb * u[2];
+        }
+    }
+    // g = F(|r|) r
+    const float dF = kernel_dF_dr(q, rinv, p);
+    const float rg = (rx * gb[0] + ry * gb[1] + rz * gb[2]) * dF * rinv;
+    rb[0] += F * gb[0] + rg * rx;
+    rb[1] += F * gb[1] + rg * ry;
+    rb[2] += F * gb[2] + rg * rz;
+    if (par) par->v[kGradM] += (double)(Vb / rho_j);
+    if (ai) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ai->x[k] += rb[k];
+            ai->u[k] -= ub[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ai->s[k] += sb[k];
+        ai->rho += rsum_b;
+    }
+    if (aj) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            aj->x[k] -= rb[k];
+            aj->u[k] += ub[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) aj->s[k] += sb[k];
+        aj->rho += rsum_b - Vj / rho_j * Vb;
+    }
+}
+
+__device__ __forceinline__ float taubar6(const float s[6])
+{
+    const float p = -(s[0] + s[1] + s[2]) * (1.0f / 3.0f);
+    const float t0 = s[0] + p, t1 = s[1] + p, t2 = s[2] + p;
+    return sqrtf(0.5f * (t0 * t0 + t1 * t1 + t2 * t2) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]));
+}
+
+// Backward of the return map of Sec. 2.3 with a constant friction coefficient
+// (mu(I) off): lo = adjoint of the mapped stress, s = trial stress; returns the
+// trial stress's adjoint in ls and adds the mu_s / cohesion terms to par.
+__device__ __forceinline__ void return_map_vjp(const float s[6], const float lo[6],
+                                               const DevParams &p, float ls[6], ParAcc &par)
+{
+    const float ps = -(s[0] + s[1] + s[2]) * (1.0f / 3.0f);
+    if (p.mu_s > 0.0f && ps < -p.cohesion / p.mu_s) {   // tension cut-off: sigma = 0
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ls[k] = 0.f;
+        return;
+    }
+    const float tb = taubar6(s);
+    const float tmax = p.mu_s * ps + p.cohesion;
+    if (tb <= tmax) {                                   // admissible: identity
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ls[k] = lo[k];
+        return;
+    }
+    // out = -ps I + f D, D = deviator of s, f = tmax / tb
+    const float f = tmax / tb;
+    const float D[6] = {s[0] + ps, s[1] + ps, s[2] + ps, s[3], s[4], s[5]};
+    float lf = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) lf += lo[k] * D[k];
+    float lD[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) lD[k] = f * lo[k];
+    float lps = -(lo[0] + lo[1] + lo[2]);
+    const float ltmax = lf / tb;
+    const float ltb = -lf * f / tb;
+    par.v[kGradMu] += (double)(ltmax * ps);
+    par.v[kGradCoh] += (double)ltmax;
+    lps += ltmax * p.mu_s;
+    // tb^2 = 0.5 (D0^2 + D1^2 + D2^2) + D3^2 + D4^2 + D5^2
+    const float itb = 1.0f / tb;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lD[k] += 0.5f * ltb * D[k] * itb;
+#pragma unroll
+    for (int k = 3; k < 6; ++k) lD[k] += ltb * D[k] * itb;
+    lps += lD[0] + lD[1] + lD[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ls[k] = lD[k] - lps * (1.0f / 3.0f);
+#pragma unroll
+    for (int k = 3; k < 6; ++k) ls[k] = lD[k];
+}
+
+// Jaumann rate, forward (the pair kernels' formula) -- for the trial stress.
+__device__ __forceinline__ void jaumann(const float L[9], const float s[6], float G, float K,
+                                        float out[6])
+{
+    const float a = 0.5f * (L[1] - L[3]), b = 0.5f * (L[2] - L[6]), c = 0.5f * (L[5] - L[7]);
+    const float exx = L[0], eyy = L[4], ezz = L[8];
+    const float exy = 0.5f * (L[1] + L[3]), exz = 0.5f * (L[2] + L[6]), eyz = 0.5f * (L[5] + L[7]);
+    const float iso = (K - 2.0f * G / 3.0f) * (exx + eyy + ezz);
+    const float G2 = 2.0f * G;
+    out[0] = 2.0f * (a * s[3] + b * s[4]) + G2 * exx + iso;
+    out[1] = 2.0f * (c * s[5] - a * s[3]) + G2 * eyy + iso;
+    out[2] = -2.0f * (b * s[4] + c * s[5]) + G2 * ezz + iso;
+    out[3] = a * (s[1] - s[0]) + b * s[5] + c * s[4] + G2 * exy;
+    out[4] = b * (s[2] - s[0]) + a * s[5] - c * s[3] + G2 * exz;
+    out[5] = c * (s[2] - s[1]) - a * s[4] - b * s[3] + G2 * eyz;
+}
+
+// Backward of the Jaumann rate: l6 = adjoint of the rate (6-vector), s6 the
+// stress, L the velocity gradient.  Writes the adjoint of L to lL, adds the
+// stress's to ls and the moduli's to par.
+__device__ __forceinline__ void jaumann_vjp(const float L[9], const float s6[6], const float l6[6],
+                                            const DevParams &p, float lL[9], float ls[6],
+                                            ParAcc &par)
+{
+    // the 6-vector adjoint as a symmetric matrix (off-diagonals halved)
+    const float Lm[9] = {l6[0], 0.5f * l6[3], 0.5f * l6[4], 0.5f * l6[3], l6[1], 0.5f * l6[5],
+                         0.5f * l6[4], 0.5f * l6[5], l6[2]};
+    const float s[9] = {s6[0], s6[3], s6[4], s6[3], s6[1], s6[5], s6[4], s6[5], s6[2]};
+    float eps[9], om[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            eps[3 * a + b] = 0.5f * (L[3 * a + b] + L[3 * b + a]);
+            om[3 * a + b] = 0.5f * (L[3 * a + b] - L[3 * b + a]);
+        }
+    const float tr_e = eps[0] + eps[4] + eps[8], tr_l = Lm[0] + Lm[4] + Lm[8];
+    float omb[9], sbm[9];
+    double gG = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            float lsg = 0.f, sl = 0.f, ol = 0.f, lo = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lsg += Lm[3 * a + c] * s[3 * c + b];
+                sl += s[3 * a + c] * Lm[3 * c + b];
+                ol += om[3 * a + c] * Lm[3 * c + b];
+                lo += Lm[3 * a + c] * om[3 * c + b];
+            }
+            omb[3 * a + b] = lsg - sl;   // adjoint of Omega: Lam s - s Lam
+            sbm[3 * a + b] = lo - ol;    // adjoint of sigma: Lam Omega - Omega Lam
+            gG += 2.0 * (double)Lm[3 * a + b] * (double)(eps[3 * a + b] - (a == b ? tr_e / 3.0f : 0.0f));
+        }
+    par.v[kGradG] += gG;
+    par.v[kGradK] += (double)tr_l * (double)tr_e;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float eb = 2.0f * p.G * (Lm[3 * a + b] - (a == b ? tr_l / 3.0f : 0.0f))
+                             + (a == b ? p.K * tr_l : 0.0f);
+            lL[3 * a + b] = eb + 0.5f * (omb[3 * a + b] - omb[3 * b + a]);
+        }
+    ls[0] += sbm[0]; ls[1] += sbm[4]; ls[2] += sbm[8];
+    ls[3] += sbm[1] + sbm[3]; ls[4] += sbm[2] + sbm[6]; ls[5] += sbm[5] + sbm[7];
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: fluid coefficients.  MODE kAdjEval: the rates' adjoints come from
+// l_rate (insertion order) and the local terms are written to l_out (slot
+// order).  MODE kAdjStage2: the state is y_mid (V.S), y_n is Y0 and the
+// adjoint of y_{n+1} is read from l_next (insertion order); the local terms at
+// y_mid go to l_mid and those at y_n (the integrator's identity parts through
+// the return map) to l_y0.  MODE kAdjStage1: the state is y_n and the adjoint
+// of y_mid is l_mid (complete); everything is added to l_y0.
+template <int MODE>
+__global__ void __launch_bounds__(kAdjBlock)
+k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar)
+{
+    __shared__ float4 lut[64];
+    fill_shift_table(lut, p.cell);
+    __syncthreads();
+    const Sizes z = load_sizes(p);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    ParAcc par;
+    par_zero(par);
+    if (i < z.nF) {
+        const StageArrays &S = V.S;
+        const float4 pi = S.pos[i];
+        const PState I = load_state(S, i);
+        float cont = 0.f, M[3] = {0.f, 0.f, 0.f}, L[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) L[k] = 0.f;
+        const int nn = (int)V.nnb[i];
+        for (int k = 0; k < nn; ++k) {
+            const uint32_t e = V.nbr[(size_t)k * p.ell + i];
+            const uint32_t j = e & kIndexMask;
+            const float4 sh = lut[e >> kIndexBits];
+            const float4 pj = S.pos[j];
+            const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+            const PState J = load_state(S, j);
+            const float rinv = rsqrtf(r2);
+            const float F = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
+            const float g[3] = {F * rx, F * ry, F * rz};
+            const float Vj = p.m / J.v.w;
+            const float u[3] = {J.v.x - I.v.x, J.v.y - I.v.y, J.v.z - I.v.z};
+            cont += Vj * (u[0] * g[0] + u[1] * g[1] + u[2] * g[2]);
+            const float Sxx = I.a.x + J.a.x, Syy = I.a.y + J.a.y, Szz = I.a.z + J.a.z;
+            const float Sxy = I.a.w + J.a.w, Sxz = I.b.x + J.b.x, Syz = I.b.y + J.b.y;
+            M[0] += Vj * (Sxx * g[0] + Sxy * g[1] + Sxz * g[2]);
+            M[1] += Vj * (Sxy * g[0] + Syy * g[1] + Syz * g[2]);
+            M[2] += Vj * (Sxz * g[0] + Syz * g[1] + Szz * g[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) L[3 * a + b] += Vj * u[a] * g[b];
+        }
+        const float si[6] = {I.a.x, I.a.y, I.a.z, I.a.w, I.b.x, I.b.y};
+        const uint32_t id = pid_index(V.pid[i]);
+        const int64_t ns = io.n_fluid;          // stride of the insertion-order arrays
+        float lr[10];                           // adjoints of the rates
+        Adj y0;                                 // terms on y_n (the step's passes)
+        adj_zero(y0);
+        Adj loc;                                // local terms on this stage's state
+        adj_zero(loc);
+        if (MODE == kAdjEval) {
+            lr[0] = io.l_rate[(size_t)id];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) lr[1 + k] = io.l_rate[ns + 3 * (size_t)id + k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) lr[4 + k] = io.l_rate[4 * ns + 6 * (size_t)id + k];
+        } else if (MODE == kAdjStage2) {
+            // y_{n+1} = y_n + dt f(y_mid), x_{n+1} = x_n + dt u_mid, then the return map
+            Adj ln;
+            adj_load(io.l_next, ns, id, ln);
+            const float dt = io.dt;
+            float ds[6];
+            jaumann(L, si, p.G, p.K, ds);
+            const float4 a0 = Y0.sA[i];
+            const float2 b0 = Y0.sB[i];
+            const float sn[6] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y};
+            float trial[6], ltr[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) trial[k] = fmaf(dt, ds[k], sn[k]);
+            return_map_vjp(trial, ln.s, p, ltr, par);
+            lr[0] = dt * ln.rho;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) lr[1 + k] = dt * ln.u[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) lr[4 + k] = dt * ltr[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                y0.x[k] = ln.x[k];
+                y0.u[k] = ln.u[k];
+                loc.u[k] = dt * ln.x[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y0.s[k] = ltr[k];
+            y0.rho = ln.rho;
+        } else {
+            // y_mid = y_n + dt/2 f(y_n), x_mid = x_n + dt/2 u_n
+            Adj lm;
+            adj_load(io.l_mid, io.slot_stride, i, lm);
+            const float h = 0.5f * io.dt;
+            lr[0] = h * lm.rho;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) lr[1 + k] = h * lm.u[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) lr[4 + k] = h * lm.s[k];
+            adj_load(io.l_y0, io.slot_stride, i, y0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                y0.x[k] += lm.x[k];
+                y0.u[k] += lm.u[k] + h * lm.x[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y0.s[k] += lm.s[k];
+            y0.rho += lm.rho;
+        }
+        // rates -> coefficients and local terms at this stage's state
+        const float rho = I.v.w;
+        Coef C;
+        C.lc = -rho * lr[0];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            C.lM[k] = lr[1 + k] / rho;
+            C.lA[k] = lr[1 + k];
+        }
+        loc.rho += -cont * lr[0] - (M[0] * lr[1] + M[1] * lr[2] + M[2] * lr[3]) / (rho * rho);
+        jaumann_vjp(L, si, lr + 4, p, C.lL, loc.s, par);
+        store_coef(io.coef, io.coef_stride, i, C);
+        if (MODE == kAdjEval) {
+            adj_store(io.l_out, io.slot_stride, i, loc);
+        } else if (MODE == kAdjStage2) {
+            adj_store(io.l_mid, io.slot_stride, i, loc);
+            adj_store(io.l_y0, io.slot_stride, i, y0);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                y0.x[k] += loc.x[k];
+                y0.u[k] += loc.u[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y0.s[k] += loc.s[k];
+            y0.rho += loc.rho;
+            adj_store(io.l_y0, io.slot_stride, i, y0);
+        }
+    }
+    par_flush(par, gpar);
+}
+
+// Rigid-body kinematics of a marker slot: world arm, body velocity and
+// acceleration at the marker (FP32); returns the body index (-1: fixed marker).
+__device__ __forceinline__ int marker_body_kin(const DevParams &p, const AdjStage &V, int s,
+                                               float ub[3], float ab[3], float arm[3])
+{
+    const uint32_t id = V.pid[s];
+    const int b = pid_body(p, id);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ub[k] = ab[k] = arm[k] = 0.f;
+    if (b >= 0) {
+        const int mi = (int)pid_index(id) - V.n_fluid_total;
+        double x[3];
+        if (V.frames == nullptr) marker_now(V.bodies[b], V.mloc + 3 * (int64_t)mi, x, ub, ab, arm);
+        else marker_at(V.frames[b], V.mloc + 3 * (int64_t)mi, x, ub, ab, arm);
+    }
+    return b;
+}
+
+// Pass 2: marker coefficients.  The adjoint of a marker's acceleration
+// a = M / rho0 + A comes from l_macc (insertion order, the rate evaluation)
+// or, in a step, from the body wrench: force m a and torque arm x m a give
+// l_a = m (l_F + l_T x arm), plus the direct term of m.  Markers without an
+// adjoint get zero coefficients.
+template <int MODE>
+__global__ void __launch_bounds__(kAdjBlock)
+k_adj_marker_coef(DevParams p, AdjStage V, AdjIO io, double *gpar)
+{
+    __shared__ float4 lut[64];
+    fill_shift_table(lut, p.cell);
+    __syncthreads();
+    const Sizes z = load_sizes(p);
+    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    ParAcc par;
+    par_zero(par);
+    if (s < z.N) {
+        float la[3] = {0.f, 0.f, 0.f};
+        bool direct_m = false;
+        if (MODE == kAdjEval) {
+            if (io.l_macc != nullptr) {
+                const size_t mi = (size_t)pid_index(V.pid[s]) - (size_t)V.n_fluid_total;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) la[k] = io.l_macc[3 * mi + k];
+            }
+        } else {
+            float ub[3], ab[3], arm[3];
+            const int b = marker_body_kin(p, V, s, ub, ab, arm);
+            if (b >= 0 && V.nnb[s] > 0) {
+                const double *w = io.l_wrench + 6 * b;
+                const float lF[3] = {(float)w[0], (float)w[1], (float)w[2]};
+                const float lT[3] = {(float)w[3], (float)w[4], (float)w[5]};
+                // (arm x f) . lT = f . (lT x arm)
+                const float lf[3] = {lF[0] + lT[1] * arm[2] - lT[2] * arm[1],
+                                     lF[1] + lT[2] * arm[0] - lT[0] * arm[2],
+                                     lF[2] + lT[0] * arm[1] - lT[1] * arm[0]};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) la[k] = p.m * lf[k];
+                direct_m = true;
+            }
+        }
+        Coef C;
+        C.lc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) C.lL[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            C.lM[k] = la[k] / p.rho0;
+            C.lA[k] = la[k];
+        }
+        store_coef(io.coef, io.coef_stride, s, C);
+        if (la[0] != 0.f || la[1] != 0.f || la[2] != 0.f) {
+            // M and A again, for the terms of 1 / rho0 and of m in m a
+            const StageArrays &S = V.S;
+            const float4 pa = S.pos[s];
+            const PState A0 = load_state(S, s);
+            float M[3] = {0.f, 0.f, 0.f}, A[3] = {0.f, 0.f, 0.f};
+            const int nn = (int)V.nnb[s];
+            for (int k = 0; k < nn; ++k) {
+                const uint32_t e = V.nbr[(size_t)k * p.ell + s];
+                const uint32_t j = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pj = S.pos[j];
+                const float rx = pa.x - pj.x - sh.x, ry = pa.y - pj.y - sh.y, rz = pa.z - pj.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+                const PState J = load_state(S, j);
+                const float rinv = rsqrtf(r2);
+                const float F = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
+                const float g[3] = {F * rx, F * ry, F * rz};
+                const float Vj = p.m / J.v.w;
+                const float Sxx = A0.a.x + J.a.x, Syy = A0.a.y + J.a.y, Szz = A0.a.z + J.a.z;
+                const float Sxy = A0.a.w + J.a.w, Sxz = A0.b.x + J.b.x, Syz = A0.b.y + J.b.y;
+                M[0] += Vj * (Sxx * g[0] + Sxy * g[1] + Sxz * g[2]);
+                M[1] += Vj * (Sxy * g[0] + Syy * g[1] + Syz * g[2]);
+                M[2] += Vj * (Sxz * g[0] + Syz * g[1] + Szz * g[2]);
+                if (p.av_mode != CRM_AV_NONE) {
+                    const float vr = (A0.v.x - J.v.x) * rx + (A0.v.y - J.v.y) * ry + (A0.v.z - J.v.z) * rz;
+                    if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+                        const float fac = 2.0f * p.av_c * vr / ((p.rho0 + J.v.w) * (r2 + p.xi2));
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) A[c] += fac * g[c];
+                    }
+                }
+            }
+            const double ir = 1.0 / (double)p.rho0;
+            double drho0 = 0.0, dm = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                drho0 -= (double)la[k] * (double)M[k] * ir * ir;
+                dm += (double)la[k] * ((double)M[k] * ir + (double)A[k]);
+            }
+            par.v[kGradRho0] += drho0;
+            if (direct_m) par.v[kGradM] += dm / (double)p.m;
+        }
+    }
+    par_flush(par, gpar);
+}
+
+// Pass 3: marker gather.  ACC: the markers' own acceleration pairs carry
+// adjoints (coefficients from pass 2).  Writes the BCE coefficients of every
+// marker slot and adds the body adjoints (centre, velocity, acceleration) to
+// gbody [body][9].
+template <bool ACC>
+__global__ void __launch_bounds__(kAdjBlock)
+k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
+{
+    __shared__ float4 lut[64];
+    fill_shift_table(lut, p.cell);
+    __syncthreads();
+    const Sizes z = load_sizes(p);
+    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    ParAcc par;
+    par_zero(par);
+    int body = -1;
+    float bx[3] = {0.f, 0.f, 0.f}, bu[3] = {0.f, 0.f, 0.f}, ba[3] = {0.f, 0.f, 0.f};
+    if (s < z.N) {
+        const int mslot = s - z.nF;
+        const int64_t bs = io.coefB_stride;
+        const int nn = (int)V.nnb[s];
+        float ub[3], ab[3], arm[3];
+        body = marker_body_kin(p, V, s, ub, ab, arm);
+        if (nn == 0) {
+            for (int k = 0; k < kNumBceCoef; ++k) io.coefB[k * bs + mslot] = 0.f;
+            body = -1;
+        } else {
+            const StageArrays &S = V.S;
+            const float4 pa = S.pos[s];
+            const PState A0 = load_state(S, s);
+            Coef Ca;
+            if (ACC) Ca = load_coef(io.coef, io.coef_stride, s);
+            Adj la;
+            adj_zero(la);
+            float w = 0.f, su[3] = {0.f, 0.f, 0.f}, ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float sr[3] = {0.f, 0.f, 0.f};
+            for (int k = 0; k < nn; ++k) {
+                const uint32_t e = V.nbr[(size_t)k * p.ell + s];
+                const uint32_t f = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pf = S.pos[f];
+                const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (!(r2 < p.four_h2)) continue;
+                const PState Fs = load_state(S, f);
+                const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
+                w += W;
+                su[0] += Fs.v.x * W; su[1] += Fs.v.y * W; su[2] += Fs.v.z * W;
+                ss[0] += Fs.a.x * W; ss[1] += Fs.a.y * W; ss[2] += Fs.a.z * W;
+                ss[3] += Fs.a.w * W; ss[4] += Fs.b.x * W; ss[5] += Fs.b.y * W;
+                const float rw = Fs.v.w * W;
+                sr[0] += rw * rx; sr[1] += rw * ry; sr[2] += rw * rz;
+                if (r2 == 0.0f) continue;
+                // the fluid particle's pair that reads this marker (r_fa = -r)
+                const Coef Cf = load_coef(io.coef, io.coef_stride, (int)f);
+                pair_vjp(p, Cf, -rx, -ry, -rz, r2, Fs, Fs.v.w, A0, nullptr, &la, nullptr);
+                // the marker's own acceleration pair
+                if (ACC) pair_vjp(p, Ca, rx, ry, rz, r2, A0, p.rho0, Fs, &la, nullptr, &par);
+            }
+            // the marker density is rho0
+            par.v[kGradRho0] += (double)la.rho;
+            float cb[kNumBceCoef];
+#pragma unroll
+            for (int k = 0; k < kNumBceCoef; ++k) cb[k] = 0.f;
+            float lub[3] = {0.f, 0.f, 0.f}, lab[3] = {0.f, 0.f, 0.f};
+            if (w > 0.f) {
+                const float iw = 1.0f / w;
+                const float ua[3] = {2.f * ub[0] - su[0] * iw, 2.f * ub[1] - su[1] * iw,
+                                     2.f * ub[2] - su[2] * iw};
+                const float gp = (p.gx - ab[0]) * sr[0] + (p.gy - ab[1]) * sr[1] + (p.gz - ab[2]) * sr[2];
+                const float sa[6] = {(ss[0] - gp) * iw, (ss[1] - gp) * iw, (ss[2] - gp) * iw,
+                                     ss[3] * iw, ss[4] * iw, ss[5] * iw};
+                float lw = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    cb[kBceSu + k] = -la.u[k] * iw;
+                    lw += la.u[k] * (2.f * ub[k] - ua[k]) * iw;   // su / w^2 = (2 ub - ua) / w
+                    lub[k] = 2.f * la.u[k];
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    cb[kBceSs + k] = la.s[k] * iw;
+                    lw -= la.s[k] * sa[k] * iw;
+                }
+                const float lgp = -(la.s[0] + la.s[1] + la.s[2]) * iw;
+                cb[kBceSr + 0] = lgp * (p.gx - ab[0]);
+                cb[kBceSr + 1] = lgp * (p.gy - ab[1]);
+                cb[kBceSr + 2] = lgp * (p.gz - ab[2]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) lab[k] = -lgp * sr[k];
+                cb[kBceW] = lw;
+                // the marker position in its BCE sums
+                for (int k = 0; k < nn; ++k) {
+                    const uint32_t e = V.nbr[(size_t)k * p.ell + s];
+                    const uint32_t f = e & kIndexMask;
+                    const float4 sh = lut[e >> kIndexBits];
+                    const float4 pf = S.pos[f];
+                    const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
+                    const float r2 = rx * rx + ry * ry + rz * rz;
+                    if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+                    const PState Fs = load_state(S, f);
+                    const float rinv = rsqrtf(r2);
+                    const float q = r2 * rinv * p.inv_h;
+                    const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
+                    const float F = kernel_dw_over_r(q, rinv, p);
+                    const float lW = cb[kBceW] + cb[kBceSu] * Fs.v.x + cb[kBceSu + 1] * Fs.v.y
+                                     + cb[kBceSu + 2] * Fs.v.z + cb[kBceSs] * Fs.a.x
+                                     + cb[kBceSs + 1] * Fs.a.y + cb[kBceSs + 2] * Fs.a.z
+                                     + cb[kBceSs + 3] * Fs.a.w + cb[kBceSs + 4] * Fs.b.x
+                                     + cb[kBceSs + 5] * Fs.b.y
+                                     + Fs.v.w * (cb[kBceSr] * rx + cb[kBceSr + 1] * ry + cb[kBceSr + 2] * rz);
+                    const float rw = Fs.v.w * W, fl = lW * F;
+                    la.x[0] += rw * cb[kBceSr] + fl * rx;
+                    la.x[1] += rw * cb[kBceSr + 1] + fl * ry;
+                    la.x[2] += rw * cb[kBceSr + 2] + fl * rz;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) lub[k] = la.u[k];
+            }
+            for (int k = 0; k < kNumBceCoef; ++k) io.coefB[k * bs + mslot] = cb[k];
+            if (body >= 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    bx[k] = la.x[k];
+                    bu[k] = lub[k];
+                    ba[k] = lab[k];
+                }
+            }
+        }
+    }
+    par_flush(par, gpar);
+    // per-body sums: warp reduction, one FP64 atomic per warp and entry
+    const int lane = threadIdx.x & 31;
+    for (int b = 0; b < p.n_bodies; ++b) {
+        const bool mine = body == b;
+        if (!__any_sync(0xffffffffu, mine)) continue;
+        double v[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            v[k] = mine ? bx[k] : 0.0;
+            v[3 + k] = mine ? bu[k] : 0.0;
+            v[6 + k] = mine ? ba[k] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+            if (lane == 0 && v[k] != 0.0) atomicAdd(gbody + 9 * b + k, v[k]);
+        }
+    }
+}
+
+// Pass 4: fluid gather.  ACC: the markers in the list carry acceleration
+// coefficients.  OUT kAdjAccumulate: the sums are added to l_acc (slot order);
+// kAdjFinal: l_acc (slot order) plus the sums is written to l_final at the
+// particle's insertion index.
+template <bool ACC, int OUT>
+__global__ void __launch_bounds__(kAdjBlock)
+k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, double *gpar)
+{
+    __shared__ float4 lut[64];
+    fill_shift_table(lut, p.cell);
+    __syncthreads();
+    const Sizes z = load_sizes(p);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    ParAcc par;
+    par_zero(par);
+    if (i < z.nF) {
+        const StageArrays &S = V.S;
+        const float4 pi = S.pos[i];
+        const PState I = load_state(S, i);
+        const Coef Ci = load_coef(io.coef, io.coef_stride, i);
+        Adj a;
+        adj_load(l_acc, io.slot_stride, i, a);
+        const int nn = (int)V.nnb[i];
+        const int64_t bs = io.coefB_stride;
+        for (int k = 0; k < nn; ++k) {
+            const uint32_t e = V.nbr[(size_t)k * p.ell + i];
+            const uint32_t j = e & kIndexMask;
+            const float4 sh = lut[e >> kIndexBits];
+            const float4 pj = S.pos[j];
+            const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < p.four_h2)) continue;
+            const PState J = load_state(S, j);
+            const bool marker = (int)j >= z.nF;
+            if (r2 != 0.0f) {
+                // own pair (i target)
+                pair_vjp(p, Ci, rx, ry, rz, r2, I, I.v.w, J, &a, nullptr, &par);
+                // the neighbour's pair that reads i (j target, r_ji = -r)
+                if (!marker || ACC) {
+                    const Coef Cj = load_coef(io.coef, io.coef_stride, (int)j);
+                    pair_vjp(p, Cj, -rx, -ry, -rz, r2, J, marker ? p.rho0 : J.v.w, I, nullptr, &a,
+                             nullptr);
+                }
+            }
+            if (marker) {
+                // i in marker j's BCE sums: r_a = x_j - x_i = -r
+                const int ms = (int)j - z.nF;
+                float cb[kNumBceCoef];
+#pragma unroll
+                for (int c = 0; c < kNumBceCoef; ++c) cb[c] = io.coefB[c * bs + ms];
+                const float ax = -rx, ay = -ry, az = -rz;
+                const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
+                const float lsr = cb[kBceSr] * ax + cb[kBceSr + 1] * ay + cb[kBceSr + 2] * az;
+                const float lW = cb[kBceW] + cb[kBceSu] * I.v.x + cb[kBceSu + 1] * I.v.y
+                                 + cb[kBceSu + 2] * I.v.z + cb[kBceSs] * I.a.x + cb[kBceSs + 1] * I.a.y
+                                 + cb[kBceSs + 2] * I.a.z + cb[kBceSs + 3] * I.a.w
+                                 + cb[kBceSs + 4] * I.b.x + cb[kBceSs + 5] * I.b.y + I.v.w * lsr;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a.u[c] += cb[kBceSu + c] * W;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) a.s[c] += cb[kBceSs + c] * W;
+                a.rho += lsr * W;
+                if (r2 != 0.0f) {
+                    const float rinv = rsqrtf(r2);
+                    const float F = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
+                    const float rw = I.v.w * W, fl = lW * F;
+                    a.x[0] -= rw * cb[kBceSr] + fl * ax;
+                    a.x[1] -= rw * cb[kBceSr + 1] + fl * ay;
+                    a.x[2] -= rw * cb[kBceSr + 2] + fl * az;
+                }
+            }
+        }
+        if (OUT == kAdjAccumulate) adj_store(l_acc, io.slot_stride, i, a);
+        else adj_store(l_final, io.n_fluid, pid_index(V.pid[i]), a);
+    }
+    par_flush(par, gpar);
+}
+
+// Body adjoint of the update at the end of a step (Sec. 2.4, symplectic Euler
+// on the free linear DOFs): from the adjoints of the centre, velocity and
+// acceleration after the step (lb_next [body][9], plus the objective's terms on
+// the wrench and the centre) to the adjoint of the soil wrench (l_wrench) and
+// the partial adjoint of the body before the step (lb_cur).  One thread per body.
+__global__ void k_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double *lb_next,
+                               const double *lw_obj, const double *lc_obj, double *l_wrench,
+                               double *lb_cur)
+{
+    const int b = threadIdx.x;
+    if (b >= nb) return;
+    const BodyDev &B = bodies[b];
+    double lc[3], lv[3];
+    for (int k = 0; k < 3; ++k) {
+        lc[k] = lb_next[9 * b + k] + (lc_obj ? lc_obj[3 * b + k] : 0.0);
+        lv[k] = lb_next[9 * b + 3 + k] + dt * lc[k];           // c' = c + dt v'
+    }
+    for (int k = 0; k < 3; ++k) {
+        double lF = 0.0;
+        if (B.dof & (1 << k)) {
+            const double la = lb_next[9 * b + 6 + k] + dt * lv[k];   // v' = v + dt a, acc' = a
+            lF = la / B.mass;
+        }
+        l_wrench[6 * b + k] = lF + (lw_obj ? lw_obj[6 * b + k] : 0.0);
+        l_wrench[6 * b + 3 + k] = lw_obj ? lw_obj[6 * b + 3 + k] : 0.0;
+        lb_cur[9 * b + k] = lc[k];
+        lb_cur[9 * b + 3 + k] = lv[k];
+        lb_cur[9 * b + 6 + k] = 0.0;
+    }
+}
+
+// The stages' body adjoints into the body before the step: the midpoint
+// markers sit at c + dt/2 v with velocity v and acceleration acc (of the
+// previous update), the stage-1 markers at c.
+__global__ void k_adj_body_post(int nb, double dt, const double *g0, const double *gm, double *lb)
+{
+    const int b = threadIdx.x;
+    if (b >= nb) return;
+    for (int k = 0; k < 3; ++k) {
+        const double lcm = gm[9 * b + k];
+        lb[9 * b + k] += g0[9 * b + k] + lcm;
+        lb[9 * b + 3 + k] += g0[9 * b + 3 + k] + gm[9 * b + 3 + k] + 0.5 * dt * lcm;
+        lb[9 * b + 6 + k] += g0[9 * b + 6 + k] + gm[9 * b + 6 + k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+void launch_adj_fluid_coef(int mode, const DevParams &p, const AdjStage &V, StageArrays Y0,
+                           const AdjIO &io, double *gpar, cudaStream_t st)
+{
+    const unsigned g = grid_for(p.capF, kAdjBlock);
+    if (mode == kAdjEval) k_adj_fluid_coef<kAdjEval><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+    else if (mode == kAdjStage2) k_adj_fluid_coef<kAdjStage2><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+    else k_adj_fluid_coef<kAdjStage1><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+}
+
+void launch_adj_marker_coef(int mode, const DevParams &p, const AdjStage &V, const AdjIO &io,
+                            double *gpar, cudaStream_t st)
+{
+    if (p.capM == 0) return;
+    const unsigned g = grid_for(p.capM, kAdjBlock);
+    if (mode == kAdjEval) k_adj_marker_coef<kAdjEval><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar);
+    else k_adj_marker_coef<kAdjStage2><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar);
+}
+
+void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const AdjIO &io,
+                       double *gpar, double *gbody, cudaStream_t st)
+{
+    if (p.capM == 0) return;
+    const unsigned g = grid_for(p.capM, kAdjBlock);
+    if (acc) k_adj_marker<true><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
+    else k_adj_marker<false><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
+}
+
+void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, const AdjIO &io,
+                      float *l_acc, float *l_final, double *gpar, cudaStream_t st)
+{
+    const unsigned g = grid_for(p.capF, kAdjBlock);
+    if (acc) {
+        if (out == kAdjAccumulate)
+            k_adj_fluid<true, kAdjAccumulate><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+        else
+            k_adj_fluid<true, kAdjFinal><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+    } else {
+        if (out == kAdjAccumulate)
+            k_adj_fluid<false, kAdjAccumulate><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+        else
+            k_adj_fluid<false, kAdjFinal><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+    }
+}
+
+void launch_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double *lb_next,
+                         const double *lw_obj, const double *lc_obj, double *l_wrench,
+                         double *lb_cur, cudaStream_t st)
+{
+    if (nb == 0) return;
+    k_adj_body_pre<<<1, 32, 0, st>>>(nb, bodies, dt, lb_next, lw_obj, lc_obj, l_wrench, lb_cur);
+}
+
+void launch_adj_body_post(int nb, double dt, const double *g0, const double *gm, double *lb,
+                          cudaStream_t st)
+{
+    if (nb == 0) return;
+    k_adj_body_post<<<1, 32, 0, st>>>(nb, dt, g0, gm, lb);
+}
+
+}  // namespace crm

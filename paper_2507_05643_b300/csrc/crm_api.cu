@@ -22,12 +22,13 @@
 #include <string>
 #include <vector>
 
+#include "crm_adjoint.cuh"
 #include "crm_internal.cuh"
 
 using namespace crm;
 
 namespace {
-enum { G_STATIC, G_WORK, G_WIN, G_CAND, G_COUNT };
+enum { G_STATIC, G_WORK, G_WIN, G_CAND, G_ADJ, G_TAPE, G_COUNT };
 // device counters word layout
 enum { C_NF, C_NM, C_N, C_NA, C_NE, C_NEED_F, C_NEED_M, C_NEED_CELLS, C_NEED_CAND, C_USE_CELLS,
        C_USE_CAND, C_WORDS = 16 };
@@ -117,6 +118,31 @@ struct crm_terrain {
     uint32_t *cinc = nullptr, *cslot = nullptr;
     uint8_t *ckind = nullptr;
     SortScratch cscan{};
+
+    // reverse sweep (crm_eval_rates_vjp, crm_adjoint_*): workspace sized for the
+    // working set, and the tape of one checkpoint segment
+    struct AdjTape {
+        StageArrays Y0, YM;          // slot arrays at y_n and y_mid (markers with their state)
+        uint32_t *pid, *nbr, *nnb;   // slot order and lists of the step
+        BodyDev *bodies;             // bodies before the step
+        BodyFrame *frames;           // bodies at the step midpoint
+    };
+    struct Adjoint {
+        bool ready = false;
+        float *coef = nullptr, *coefB = nullptr, *l_mid = nullptr, *l_y0 = nullptr,
+              *l_ins = nullptr, *l_rate = nullptr, *l_macc = nullptr;
+        double *gpar = nullptr, *gbody = nullptr, *lb[2]{}, *lwrench = nullptr;
+        // trajectory: checkpoints every `every` steps (plus the final state),
+        // the bodies after each step, the objective's adjoints
+        int64_t n_steps = 0;
+        int every = 0, n_ckpt = 0;
+        double dt = 0.0;
+        size_t ckpt_bytes = 0;
+        char *ckpt = nullptr;
+        BodyDev *hist = nullptr;
+        double *lw_obj = nullptr, *lc_obj = nullptr;
+        std::vector<AdjTape> tape;
+    } adj;
 
     std::vector<void *> allocs[G_COUNT];
     bool oom = false;
@@ -305,6 +331,9 @@ int alloc_working(crm_terrain *t)
 {
     t->drop_graphs();   // graphs bake in the array pointers
     t->free_group(G_WORK);
+    t->free_group(G_ADJ);      // the sweep's workspace follows the working set
+    t->free_group(G_TAPE);
+    t->adj = crm_terrain::Adjoint{};
     DevParams &d = t->dp;
     const int64_t N = t->capF + t->capM;
     if (N >= (int64_t)kIndexMask)
@@ -717,10 +746,10 @@ int commit(crm_terrain *t)
 }
 
 enum KernelId { K_KEYS, K_SCAN, K_SCATTER, K_REORDER, K_NEIGHBORS, K_COMPACT, K_BCE, K_PAIR1,
-                K_PAIR2, K_SKIN, K_EXPORT };
+                K_PAIR2, K_SKIN, K_EXPORT, K_ADJ };
 const char *const kKernelNames[CRM_NUM_KERNELS] = {
     "keys", "scan", "scatter", "reorder", "neighbors", "compact", "bce", "pair_stage1",
-    "pair_stage2", "skin", "export"};
+    "pair_stage2", "skin", "export", "adjoint"};
 
 // Enqueue one kernel through `launch`, counting it and, when timing is on,
 // bracketing it with two events on the handle's stream.  The active-domain
@@ -1871,6 +1900,413 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used)
     }
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     return CRM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Reverse sweep: the hand-derived adjoint of one rate evaluation and of a run
+// of midpoint steps (kernels in crm_adjoint.cu).  A run is recorded as
+// checkpoints every `every` steps; the backward pass restores each segment's
+// checkpoint, re-runs its steps with direct launches while copying each step's
+// stage arrays, lists and bodies to the tape, and then sweeps the segment's
+// steps in reverse.  The adjoints of the fluid state live in insertion order
+// between steps (the cell sort re-orders the slots every step).
+namespace {
+
+int adj_workspace(crm_terrain *t)
+{
+    crm_terrain::Adjoint &A = t->adj;
+    if (A.ready) return CRM_OK;
+    const DevParams &d = t->dp;
+    const size_t nb = std::max<size_t>(t->hbodies.size(), 1);
+    const size_t nF = (size_t)std::max<int64_t>(t->nFtot, 1), nM = (size_t)std::max<int64_t>(t->nMtot, 1);
+    A.coef = t->dalloc<float>(G_ADJ, (size_t)kNumCoef * std::max(d.capN, 1));
+    A.coefB = t->dalloc<float>(G_ADJ, (size_t)kNumBceCoef * std::max(d.capM, 1));
+    A.l_mid = t->dalloc<float>(G_ADJ, (size_t)kNumAdj * std::max(d.capF, 1));
+    A.l_y0 = t->dalloc<float>(G_ADJ, (size_t)kNumAdj * std::max(d.capF, 1));
+    A.l_ins = t->dalloc<float>(G_ADJ, (size_t)kNumAdj * nF);
+    A.l_rate = t->dalloc<float>(G_ADJ, 10 * nF);
+    A.l_macc = t->dalloc<float>(G_ADJ, 3 * nM);
+    A.gpar = t->dalloc<double>(G_ADJ, kNumGradAcc);
+    A.gbody = t->dalloc<double>(G_ADJ, 2 * 9 * nb);
+    A.lb[0] = t->dalloc<double>(G_ADJ, 9 * nb);
+    A.lb[1] = t->dalloc<double>(G_ADJ, 9 * nb);
+    A.lwrench = t->dalloc<double>(G_ADJ, 6 * nb);
+    if (t->oom) {
+        t->oom = false;
+        t->free_group(G_ADJ);
+        A = crm_terrain::Adjoint{};
+        return t->fail(CRM_ENOMEM, "device allocation of the adjoint workspace failed");
+    }
+    A.ready = true;
+    return CRM_OK;
+}
+
+// What the sweep supports: no active boxes; for runs, a cell search every step
+// without a skin (so that a re-run reproduces the recorded lists), a constant
+// friction coefficient, and bodies whose rotations are prescribed.
+int adj_support(crm_terrain *t, bool run, const char *who)
+{
+    const std::string w(who);
+    if (t->active) return t->fail(CRM_EINVAL, w + ": active domains are not differentiated");
+    if (!run) return CRM_OK;
+    if (t->skin_on || t->P.ps_freq != 1)
+        return t->fail(CRM_EINVAL, w + ": needs skin = 0 and ps_freq = 1");
+    if (t->P.mu_2 != t->P.mu_s)
+        return t->fail(CRM_EINVAL, w + ": mu(I) (mu_2 != mu_s) is not differentiated");
+    for (const BodyDev &b : t->hbodies)
+        if (b.dof & (7 << 3))
+            return t->fail(CRM_EINVAL, w + ": free rotational DOFs are not differentiated");
+    return CRM_OK;
+}
+
+crm_terrain::AdjTape no_tape() { return crm_terrain::AdjTape{}; }
+
+AdjIO adj_io(crm_terrain *t, float dt)
+{
+    const DevParams &d = t->dp;
+    crm_terrain::Adjoint &A = t->adj;
+    AdjIO io{};
+    io.coef = A.coef;
+    io.coef_stride = std::max(d.capN, 1);
+    io.coefB = A.coefB;
+    io.coefB_stride = std::max(d.capM, 1);
+    io.l_rate = A.l_rate;
+    io.l_macc = nullptr;
+    io.l_wrench = A.lwrench;
+    io.l_next = A.l_ins;
+    io.l_mid = A.l_mid;
+    io.l_y0 = A.l_y0;
+    io.l_out = A.l_y0;
+    io.slot_stride = std::max(d.capF, 1);
+    io.n_fluid = std::max<int64_t>(t->nFtot, 1);
+    io.dt = dt;
+    return io;
+}
+
+// Accumulated parameter adjoints (G, K, m, viscosity constant, direct rho0,
+// mu_s, cohesion) -> the public parameters: G = E / (2 (1 + nu)),
+// K = E / (3 (1 - 2 nu)), m = rho0 d0^3, c = gamma h sqrt(K / rho0) m.
+void grads_from_acc(const crm_params &P, const double *a, double *g)
+{
+    const double Gm = P.E / (2.0 * (1.0 + P.nu)), Km = P.E / (3.0 * (1.0 - 2.0 * P.nu));
+    const double m = P.rho0 * P.d0 * P.d0 * P.d0;
+    const double c1 = P.h * std::sqrt(Km / P.rho0) * m;   // dc / dgamma
+    const double c = P.av_gamma * c1;
+    g[CRM_GRAD_E] = (a[kGradG] * Gm + a[kGradK] * Km + 0.5 * a[kGradAvc] * c) / P.E;
+    g[CRM_GRAD_NU] = -a[kGradG] * Gm / (1.0 + P.nu) + (2.0 * a[kGradK] * Km + a[kGradAvc] * c) / (1.0 - 2.0 * P.nu);
+    g[CRM_GRAD_RHO0] = a[kGradRho0] + a[kGradM] * m / P.rho0 + 0.5 * a[kGradAvc] * c / P.rho0;
+    g[CRM_GRAD_MU_S] = a[kGradMu];
+    g[CRM_GRAD_COHESION] = a[kGradCoh];
+    g[CRM_GRAD_AV_GAMMA] = a[kGradAvc] * c1;
+}
+
+// Fluid adjoints (insertion order, FP32 on the device) -> caller's FP64
+// arrays; body and parameter adjoints likewise.
+int adj_export(crm_terrain *t, const double *lb_dev, double *g_xyz, double *g_vel,
+               double *g_stress, double *g_rho, double *g_body, double *g_params)
+{
+    crm_terrain::Adjoint &A = t->adj;
+    const int64_t nF = t->nFtot;
+    const size_t nb = t->hbodies.size();
+    std::vector<float> l((size_t)kNumAdj * std::max<int64_t>(nF, 1));
+    std::vector<double> acc(kNumGradAcc), lb(9 * std::max<size_t>(nb, 1));
+    if (nF > 0 && (g_xyz || g_vel || g_stress || g_rho))
+        CRM_CUDA(t, cudaMemcpyAsync(l.data(), A.l_ins, l.size() * sizeof(float), cudaMemcpyDeviceToHost, t->st));
+    CRM_CUDA(t, cudaMemcpyAsync(acc.data(), A.gpar, kNumGradAcc * sizeof(double), cudaMemcpyDeviceToHost, t->st));
+    if (nb > 0 && g_body && lb_dev)
+        CRM_CUDA(t, cudaMemcpyAsync(lb.data(), lb_dev, 9 * nb * sizeof(double), cudaMemcpyDeviceToHost, t->st));
+    CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    int rc = latched_error(t);
+    if (rc) return rc;
+    for (int64_t i = 0; i < nF; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            if (g_xyz) g_xyz[3 * i + k] = l[(size_t)(kAdjX + k) * nF + i];
+            if (g_vel) g_vel[3 * i + k] = l[(size_t)(kAdjU + k) * nF + i];
+        }
+        if (g_stress)
+            for (int k = 0; k < 6; ++k) g_stress[6 * i + k] = l[(size_t)(kAdjS + k) * nF + i];
+        if (g_rho) g_rho[i] = l[(size_t)kAdjR * nF + i];
+    }
+    if (g_body && lb_dev) std::memcpy(g_body, lb.data(), 9 * nb * sizeof(double));
+    if (g_params) grads_from_acc(t->P, acc.data(), g_params);
+    return CRM_OK;
+}
+
+// One step of the run with direct launches, the step's stage arrays, lists and
+// bodies copied to the tape (the same kernels as the graph of a search step).
+int record_step(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
+{
+    const DevParams &d = t->dp;
+    const size_t N = (size_t)std::max(d.capN, 1), nb = t->hbodies.size();
+    auto copy = [&](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, t->st);
+    };
+    auto copy_stage = [&](StageArrays &dst, const StageArrays &src) {
+        cudaError_t e = copy(dst.pos, src.pos, N * sizeof(float4));
+        if (e == cudaSuccess) e = copy(dst.vel, src.vel, N * sizeof(float4));
+        if (e == cudaSuccess) e = copy(dst.sA, src.sA, N * sizeof(float4));
+        if (e == cudaSuccess) e = copy(dst.sB, src.sB, N * sizeof(float2));
+        return e;
+    };
+    if (nb > 0) CRM_CUDA(t, copy(T.bodies, t->bodies, nb * sizeof(BodyDev)));
+    rebuild(t);
+    const int c = t->cur;
+    RateOut none{};
+    bce(t, t->A[c], 0.0, 0, dt, 0, false);
+    pair(t, kStage1, t->A[c], t->A[c], (float)dt, none);
+    CRM_CUDA(t, copy_stage(T.Y0, t->A[c]));
+    CRM_CUDA(t, copy(T.pid, t->pid[c], N * sizeof(uint32_t)));
+    CRM_CUDA(t, copy(T.nbr, t->nbr, (size_t)d.maxnb * d.ell * sizeof(uint32_t)));
+    CRM_CUDA(t, copy(T.nnb, t->nnb, N * sizeof(uint32_t)));
+    if (nb > 0) CRM_CUDA(t, copy(T.frames, t->mid_frames, nb * sizeof(BodyFrame)));
+    bce(t, t->MID, 0.5 * dt, 0);
+    if (d.capM > 0 && d.n_bodies > 0) bce(t, t->MID, 0.5 * dt, 1, dt, 1);
+    pair(t, kStage2, t->MID, t->A[c], (float)dt, none);
+    CRM_CUDA(t, copy_stage(T.YM, t->MID));
+    t->step_index += 1;
+    t->time += dt;
+    CRM_CUDA(t, cudaGetLastError());
+    return CRM_OK;
+}
+
+// Reverse sweep of step s from its tape: the adjoint of y_{s+1} (insertion
+// order, A.l_ins) and of the bodies after the step (A.lb[0]) become those of
+// y_s and of the bodies before it.
+int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
+{
+    const DevParams &d = t->dp;
+    crm_terrain::Adjoint &A = t->adj;
+    const int nb = (int)t->hbodies.size();
+    const double dt = A.dt;
+    const AdjStage Vm{T.YM, T.nbr, T.nnb, T.pid, t->mloc, T.bodies, T.frames, (int)t->nFtot};
+    const AdjStage V0{T.Y0, T.nbr, T.nnb, T.pid, t->mloc, T.bodies, nullptr, (int)t->nFtot};
+    const AdjIO io = adj_io(t, (float)dt);
+    double *g0 = A.gbody, *gm = A.gbody + 9 * std::max(nb, 1);
+    const double *lw = A.lw_obj ? A.lw_obj + (size_t)s * nb * 6 : nullptr;
+    const double *lc = A.lc_obj ? A.lc_obj + (size_t)s * nb * 3 : nullptr;
+    if (nb > 0) {
+        launch(t, K_ADJ, [&] { launch_adj_body_pre(nb, T.bodies, dt, A.lb[0], lw, lc, A.lwrench,
+                                                   A.lb[1], t->st); });
+        CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 2 * 9 * (size_t)nb * sizeof(double), t->st));
+    }
+    // stage 2 (at y_mid, with the wrench's marker accelerations)
+    launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjStage2, d, Vm, T.Y0, io, A.gpar, t->st); });
+    const bool acc = nb > 0 && d.capM > 0;
+    if (acc) launch(t, K_ADJ, [&] { launch_adj_marker_coef(kAdjStage2, d, Vm, io, A.gpar, t->st); });
+    launch(t, K_ADJ, [&] { launch_adj_marker(acc, d, Vm, io, A.gpar, gm, t->st); });
+    launch(t, K_ADJ, [&] { launch_adj_fluid(acc, kAdjAccumulate, d, Vm, io, A.l_mid, nullptr,
+                                            A.gpar, t->st); });
+    // stage 1 (at y_n)
+    launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjStage1, d, V0, T.Y0, io, A.gpar, t->st); });
+    launch(t, K_ADJ, [&] { launch_adj_marker(false, d, V0, io, A.gpar, g0, t->st); });
+    launch(t, K_ADJ, [&] { launch_adj_fluid(false, kAdjFinal, d, V0, io, A.l_y0, A.l_ins, A.gpar,
+                                            t->st); });
+    if (nb > 0) {
+        launch(t, K_ADJ, [&] { launch_adj_body_post(nb, dt, g0, gm, A.lb[1], t->st); });
+        std::swap(A.lb[0], A.lb[1]);
+    }
+    CRM_CUDA(t, cudaGetLastError());
+    return CRM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, const float *l_dvel,
+                       const float *l_dstress, int64_t cap_markers, const float *l_macc,
+                       double *g_xyz, double *g_vel, double *g_stress, double *g_rho,
+                       double *g_body, double *g_params)
+{
+    if (!t) return CRM_EINVAL;
+    if (cap_sph < t->nFtot || (l_macc && cap_markers < t->nMtot))
+        return t->fail(CRM_EINVAL, "crm_eval_rates_vjp: adjoint capacity too small");
+    int rc = commit(t);
+    if (rc) return rc;
+    rc = adj_support(t, false, "crm_eval_rates_vjp");
+    if (rc) return rc;
+    rc = adj_workspace(t);
+    if (rc) return rc;
+    crm_terrain::Adjoint &A = t->adj;
+    const int64_t nF = t->nFtot, nM = t->nMtot;
+    // the rate adjoints, insertion order: drho [n], du [3n], dsigma [6n]
+    std::vector<float> lr((size_t)10 * std::max<int64_t>(nF, 1), 0.0f);
+    for (int64_t i = 0; i < nF; ++i) {
+        if (l_drho) lr[i] = l_drho[i];
+        for (int k = 0; k < 3; ++k) lr[nF + 3 * i + k] = l_dvel ? l_dvel[3 * i + k] : 0.0f;
+        for (int k = 0; k < 6; ++k) lr[4 * nF + 6 * i + k] = l_dstress ? l_dstress[6 * i + k] : 0.0f;
+    }
+    CRM_CUDA(t, cudaMemcpyAsync(A.l_rate, lr.data(), lr.size() * sizeof(float), cudaMemcpyHostToDevice, t->st));
+    if (l_macc && nM > 0)
+        CRM_CUDA(t, cudaMemcpyAsync(A.l_macc, l_macc, 3 * nM * sizeof(float), cudaMemcpyHostToDevice, t->st));
+    // the forward evaluation (lists, marker state) as crm_eval_rates runs it
+    rebuild(t);
+    const int c = t->cur;
+    const DevParams &d = t->dp;
+    const size_t wF = (size_t)std::max(d.capF, 1);
+    void *buf = nullptr;
+    CRM_CUDA(t, cudaMallocAsync(&buf, wF * (sizeof(float) + 2 * sizeof(float4) + sizeof(float2)) + 64, t->st));
+    RateOut r;
+    r.du = (float4 *)buf;
+    r.dsA = r.du + wF;
+    r.dsB = (float2 *)(r.dsA + wF);
+    r.drho = (float *)(r.dsB + wF);
+    if (t->skin_on) {
+        bce(t, t->A[c], 0.0, 0, 0.0, 0, true);
+        pair(t, kEval, t->A[c], t->A[c], 0.0f, r, true);
+        bce(t, t->A[c], 0.0, 2);
+    } else {
+        bce(t, t->A[c], 0.0, 2);
+        pair(t, kEval, t->A[c], t->A[c], 0.0f, r);
+    }
+    cudaFreeAsync(buf, t->st);
+    const size_t nb = t->hbodies.size();
+    CRM_CUDA(t, cudaMemsetAsync(A.gpar, 0, kNumGradAcc * sizeof(double), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 9 * std::max<size_t>(nb, 1) * sizeof(double), t->st));
+    const AdjStage V{t->A[c], t->nbr, t->nnb, t->pid[c], t->mloc, t->bodies, nullptr, (int)nF};
+    AdjIO io = adj_io(t, 0.0f);
+    io.l_macc = (l_macc && nM > 0) ? A.l_macc : nullptr;
+    const bool acc = io.l_macc != nullptr;
+    if (d.capF > 0) launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjEval, d, V, t->A[c], io, A.gpar, t->st); });
+    if (d.capM > 0) {
+        launch(t, K_ADJ, [&] { launch_adj_marker_coef(kAdjEval, d, V, io, A.gpar, t->st); });
+        launch(t, K_ADJ, [&] { launch_adj_marker(acc, d, V, io, A.gpar, A.gbody, t->st); });
+    }
+    if (nF > 0)
+        CRM_CUDA(t, cudaMemsetAsync(A.l_ins, 0, (size_t)kNumAdj * nF * sizeof(float), t->st));
+    if (d.capF > 0)
+        launch(t, K_ADJ, [&] { launch_adj_fluid(acc, kAdjFinal, d, V, io, A.l_y0, A.l_ins, A.gpar, t->st); });
+    CRM_CUDA(t, cudaGetLastError());
+    return adj_export(t, A.gbody, g_xyz, g_vel, g_stress, g_rho, g_body, g_params);
+}
+
+int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t every,
+                        double *wrench_hist, double *pose_hist)
+{
+    if (!t) return CRM_EINVAL;
+    if (!(dt > 0) || !std::isfinite(dt) || n_steps < 1 || every < 1)
+        return t->fail(CRM_EINVAL, "crm_adjoint_forward: dt > 0, n_steps >= 1, every >= 1");
+    int rc = commit(t);
+    if (rc) return rc;
+    rc = adj_support(t, true, "crm_adjoint_forward");
+    if (rc) return rc;
+    rc = adj_workspace(t);
+    if (rc) return rc;
+    crm_terrain::Adjoint &A = t->adj;
+    t->free_group(G_TAPE);
+    A.tape.clear();
+    A.n_steps = 0;
+    const DevParams &d = t->dp;
+    const size_t nb = t->hbodies.size();
+    size_t sb = 0;
+    crm_state_bytes(t, &sb);
+    A.ckpt_bytes = (sb + 255) / 256 * 256;
+    A.n_ckpt = (int)((n_steps + every - 1) / every) + 1;
+    A.ckpt = t->dalloc<char>(G_TAPE, A.ckpt_bytes * A.n_ckpt);
+    A.hist = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1) * n_steps);
+    A.lw_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 6 * n_steps);
+    A.lc_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 3 * n_steps);
+    // the tape of one segment
+    const int seg = (int)std::min<int64_t>(every, n_steps);
+    const size_t N = (size_t)std::max(d.capN, 1);
+    for (int k = 0; k < seg; ++k) {
+        crm_terrain::AdjTape T = no_tape();
+        for (StageArrays *S : {&T.Y0, &T.YM}) {
+            S->pos = t->dalloc<float4>(G_TAPE, N);
+            S->vel = t->dalloc<float4>(G_TAPE, N);
+            S->sA = t->dalloc<float4>(G_TAPE, N);
+            S->sB = t->dalloc<float2>(G_TAPE, N);
+        }
+        T.pid = t->dalloc<uint32_t>(G_TAPE, N);
+        T.nbr = t->dalloc<uint32_t>(G_TAPE, (size_t)d.maxnb * d.ell);
+        T.nnb = t->dalloc<uint32_t>(G_TAPE, N);
+        T.bodies = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1));
+        T.frames = t->dalloc<BodyFrame>(G_TAPE, std::max<size_t>(nb, 1));
+        A.tape.push_back(T);
+    }
+    if (t->oom) {
+        t->oom = false;
+        t->free_group(G_TAPE);
+        A.tape.clear();
+        return t->fail(CRM_ENOMEM, "crm_adjoint_forward: device allocation of the checkpoints and tape failed");
+    }
+    A.dt = dt;
+    A.every = every;
+    size_t used = 0;
+    for (int64_t s = 0; s < n_steps; ++s) {
+        if (s % every == 0) {
+            rc = crm_save_state(t, A.ckpt + (size_t)(s / every) * A.ckpt_bytes, A.ckpt_bytes, &used);
+            if (rc) return rc;
+        }
+        rc = crm_step(t, dt, 1);
+        if (rc) return rc;
+        if (nb > 0)
+            CRM_CUDA(t, cudaMemcpyAsync(A.hist + (size_t)s * nb, t->bodies, nb * sizeof(BodyDev),
+                                        cudaMemcpyDeviceToDevice, t->st));
+    }
+    rc = crm_save_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, A.ckpt_bytes, &used);
+    if (rc) return rc;
+    rc = latched_error(t);
+    if (rc) return rc;
+    if (nb > 0 && (wrench_hist || pose_hist)) {
+        std::vector<BodyDev> h(nb * n_steps);
+        CRM_CUDA(t, cudaMemcpyAsync(h.data(), A.hist, h.size() * sizeof(BodyDev), cudaMemcpyDeviceToHost, t->st));
+        CRM_CUDA(t, cudaStreamSynchronize(t->st));
+        for (size_t q = 0; q < h.size(); ++q) {
+            if (wrench_hist) std::memcpy(wrench_hist + 6 * q, h[q].wrench, 6 * sizeof(double));
+            if (pose_hist) std::memcpy(pose_hist + 7 * q, h[q].pose, 7 * sizeof(double));
+        }
+    }
+    A.n_steps = n_steps;
+    return CRM_OK;
+}
+
+int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l_center,
+                         double *g_params, double *g_xyz, double *g_vel, double *g_stress,
+                         double *g_rho, double *g_body)
+{
+    if (!t) return CRM_EINVAL;
+    crm_terrain::Adjoint &A = t->adj;
+    if (!A.ready || A.n_steps < 1 || A.tape.empty())
+        return t->fail(CRM_ESTATE, "crm_adjoint_backward: no run recorded by crm_adjoint_forward");
+    const int64_t n = A.n_steps;
+    const size_t nb = t->hbodies.size();
+    if (nb > 0) {
+        std::vector<double> w(nb * 6 * n, 0.0), c(nb * 3 * n, 0.0);
+        if (l_wrench) std::memcpy(w.data(), l_wrench, w.size() * sizeof(double));
+        if (l_center) std::memcpy(c.data(), l_center, c.size() * sizeof(double));
+        CRM_CUDA(t, cudaMemcpyAsync(A.lw_obj, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, t->st));
+        CRM_CUDA(t, cudaMemcpyAsync(A.lc_obj, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, t->st));
+        CRM_CUDA(t, cudaMemsetAsync(A.lb[0], 0, 9 * nb * sizeof(double), t->st));
+        // (the host copies above read pageable memory: finish them before the
+        // vectors go out of scope)
+        CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    }
+    CRM_CUDA(t, cudaMemsetAsync(A.gpar, 0, kNumGradAcc * sizeof(double), t->st));
+    if (t->nFtot > 0)
+        CRM_CUDA(t, cudaMemsetAsync(A.l_ins, 0, (size_t)kNumAdj * t->nFtot * sizeof(float), t->st));
+    size_t sb = 0;
+    crm_state_bytes(t, &sb);
+    const int64_t n_seg = (n + A.every - 1) / A.every;
+    for (int64_t g = n_seg - 1; g >= 0; --g) {
+        int rc = crm_load_state(t, A.ckpt + (size_t)g * A.ckpt_bytes, sb);
+        if (rc) return rc;
+        const int64_t s0 = g * A.every, s1 = std::min<int64_t>(n, s0 + A.every);
+        for (int64_t s = s0; s < s1; ++s) {
+            rc = record_step(t, A.dt, A.tape[(size_t)(s - s0)]);
+            if (rc) return rc;
+        }
+        for (int64_t s = s1 - 1; s >= s0; --s) {
+            rc = vjp_step(t, A.tape[(size_t)(s - s0)], s);
+            if (rc) return rc;
+        }
+    }
+    // leave the terrain as the forward run left it
+    int rc = crm_load_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, sb);
+    if (rc) return rc;
+    return adj_export(t, A.lb[0], g_xyz, g_vel, g_stress, g_rho, g_body, g_params);
 }
 
 }  // extern "C"

@@ -1,0 +1,290 @@
+"""The reverse sweep (hand-derived adjoint) against central differences of the
+FP64 oracle.
+
+Each check is a directional derivative: for a random direction d of one input
+group, <g, d> from the adjoint must match (J(y + e d) - J(y - e d)) / 2e of the
+oracle, J = sum(l . outputs) with random weights l.  The oracle's neighbour
+lists are built once at the base point (the adjoint differentiates with the
+lists held fixed), and the state is chosen so that no branch (the unilateral
+viscosity switch, the return map's cases) sits within the difference step.
+Bar: |<g, d> - FD| <= TOL * sum_i |g_i d_i| (the sum of the magnitudes of the
+dot product's terms: the adjoint is FP32 arithmetic, the difference FP64).
+"""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+crm = pytest.importorskip("paper_2507_05643_b300")
+TOL = 2e-3          # rate evaluation
+RUN_TOL = 1e-2      # a run of steps (FP32 trajectory against the FP64 one)
+
+
+def _wheel(seed=21, nx=24, ny=16, nz=8):
+    sc = scenes.wheel_bin(seed=seed, nx=nx, ny=ny, nz=nz, wheel_radius=0.06, wheel_width=0.06,
+                          n_grousers=8, wheel_x=0.12)
+    sc.bodies[0].pose[2] -= 0.004   # grousers in the soil
+    rng = np.random.default_rng(seed)
+    sc.u = rng.uniform(-0.05, 0.05, size=sc.u.shape)
+    sc.sig = sc.sig + rng.uniform(-300.0, 300.0, size=sc.sig.shape)
+    sc.rho = sc.params["rho0"] * (1 + rng.uniform(-0.01, 0.01, size=sc.rho.shape))
+    sc.bodies[0].twist[2] = -0.02
+    return sc
+
+
+class _OracleRates:
+    """J = sum(l . rates) of the oracle with the lists of the base point."""
+
+    def __init__(self, sc):
+        self.sc = sc
+        self.st = oracle.State(sc)
+        self.st.rebuild("brute" if sc.x.shape[0] < 4000 else "cells")
+
+    def J(self, lam, params=None, x=None, u=None, sig=None, rho=None, bodies=None):
+        st = self.st
+        P = st.params if params is None else params
+        x = st.x if x is None else x
+        u = st.u if u is None else u
+        sig = st.sig if sig is None else sig
+        rho = st.rho if rho is None else rho
+        b = st.bodies if bodies is None else bodies
+        xm, umb, amb = oracle.marker_kinematics(st.mbody, st.mxloc, b, 0.0)
+        um, sm = oracle.bce(P, x, u, sig, rho, xm, umb, amb, st.off, st.lst)
+        drho, du, ds, macc, _, _ = oracle.rates(P, x, u, sig, rho, xm, um, sm, st.off, st.lst)
+        return (np.sum(lam["drho"] * drho) + np.sum(lam["du"] * du) + np.sum(lam["ds"] * ds)
+                + np.sum(lam["macc"] * macc))
+
+    def J_abs(self, lam):
+        """sum |l . output| at the base point: the FP32 resolution of J is ~1e-7 of it."""
+        st = self.st
+        xm, umb, amb = oracle.marker_kinematics(st.mbody, st.mxloc, st.bodies, 0.0)
+        um, sm = oracle.bce(st.params, st.x, st.u, st.sig, st.rho, xm, umb, amb, st.off, st.lst)
+        drho, du, ds, macc, _, _ = oracle.rates(st.params, st.x, st.u, st.sig, st.rho, xm, um, sm,
+                                                st.off, st.lst)
+        return float(np.sum(np.abs(lam["drho"] * drho)) + np.sum(np.abs(lam["du"] * du))
+                     + np.sum(np.abs(lam["ds"] * ds)) + np.sum(np.abs(lam["macc"] * macc)))
+
+
+def _lam(sc, which, seed):
+    rng = np.random.default_rng(seed)
+    n, m = sc.x.shape[0], sum(b.markers_local.shape[0] for b in sc.bodies) + sc.fixed.shape[0]
+    lam = {"drho": np.zeros(n), "du": np.zeros((n, 3)), "ds": np.zeros((n, 6)), "macc": np.zeros((m, 3))}
+    # weights of comparable effect: the stress rates are ~1e6 times the others
+    scale = {"drho": 1.0, "du": 1.0, "ds": 1e-4, "macc": 1.0}
+    for k in lam:
+        if which in (k, "all"):
+            lam[k] = rng.normal(size=lam[k].shape) * scale[k]
+    return lam
+
+
+SC_EVAL = _wheel()
+INPUTS = ("x", "u", "sig", "rho", "body_c", "body_v", "body_a", "E", "nu", "rho0", "av_gamma")
+
+
+@pytest.fixture(scope="module")
+def eval_case():
+    sc = SC_EVAL.copy()
+    t = crm.from_scene(sc)
+    return sc, t, _OracleRates(sc)
+
+
+def _direction(sc, name, rng):
+    """(perturbation kwargs builder, direction, step, adjoint entry)."""
+    n = sc.x.shape[0]
+    h = sc.params["h"]
+    if name in ("x", "u", "sig", "rho"):
+        shape = {"x": (n, 3), "u": (n, 3), "sig": (n, 6), "rho": (n,)}[name]
+        d = rng.normal(size=shape)
+        eps = {"x": 1e-6 * h, "u": 1e-6, "sig": 1e-2, "rho": 1e-3}[name]
+        return d, eps
+    if name.startswith("body_"):
+        return rng.normal(size=3), {"body_c": 1e-6 * h, "body_v": 1e-6, "body_a": 1e-4}[name]
+    return np.ones(1), 1e-6 * abs(sc.params[name])
+
+
+def _perturbed(orc, name, d, e):
+    st = orc.st
+    if name in ("x", "u", "sig", "rho"):
+        return {name: getattr(st, name) + e * d}
+    if name.startswith("body_"):
+        b = copy.deepcopy(st.bodies)
+        if name == "body_c":
+            b.pose[0, :3] += e * d
+        elif name == "body_v":
+            b.twist[0, :3] += e * d
+        else:
+            b.acc[0, :3] += e * d
+        return {"bodies": b}
+    P = dict(st.params)
+    P[name] += e * d[0]
+    return {"params": P}
+
+
+def _adjoint_terms(g, name, d):
+    if name in ("x", "u", "sig", "rho"):
+        key = {"x": "xyz", "u": "vel", "sig": "stress", "rho": "rho"}[name]
+        return g[key].reshape(d.shape) * d
+    if name.startswith("body_"):
+        off = {"body_c": 0, "body_v": 3, "body_a": 6}[name]
+        return g["body"][0, off:off + 3] * d
+    return np.array([g["param_grads"][name] * d[0]])
+
+
+@pytest.mark.parametrize("which", ["drho", "du", "ds", "macc"])
+def test_rate_vjp_matches_oracle_differences(eval_case, which):
+    sc, t, orc = eval_case
+    lam = _lam(sc, which, seed=hash(which) % 1000)
+    g = t.eval_rates_vjp(lam["drho"], lam["du"], lam["ds"], lam["macc"])
+    rng = np.random.default_rng(5)
+    j_abs = orc.J_abs(lam)
+    bad = []
+    for name in INPUTS:
+        d, e = _direction(sc, name, rng)
+        jp = orc.J(lam, **_perturbed(orc, name, d, e))
+        jm = orc.J(lam, **_perturbed(orc, name, d, -e))
+        fd = (jp - jm) / (2 * e)
+        terms = _adjoint_terms(g, name, d)
+        ad, scale = float(terms.sum()), float(np.abs(terms).sum())
+        # a parameter derivative can be a small remainder of cancelling terms (the
+        # marker accelerations hardly depend on rho0): its floor is the FP32
+        # resolution of J per relative change of the parameter
+        floor = 1e-6 * j_abs / abs(sc.params[name]) if name in sc.params else 0.0
+        if abs(ad - fd) > TOL * scale + floor + 1e-9 * (abs(fd) + 1):
+            bad.append((name, ad, fd, scale))
+    assert not bad, bad
+
+
+def test_rate_vjp_of_zero_weights_is_zero(eval_case):
+    sc, t, _ = eval_case
+    g = t.eval_rates_vjp()
+    for k in ("xyz", "vel", "stress", "rho", "body", "params"):
+        assert np.all(g[k] == 0.0), k
+
+
+def test_rate_vjp_rejects_active_domains():
+    sc = scenes.wheel_bin(seed=3, nx=20, ny=12, nz=6, wheel_radius=0.05, wheel_width=0.05,
+                          n_grousers=6, wheel_x=0.1, active_box=np.array([0.1, 0.1, 0.1]))
+    t = crm.from_scene(sc)
+    with pytest.raises(crm.CrmError):
+        t.eval_rates_vjp(l_drho=np.ones(sc.x.shape[0]))
+
+
+# ---------------------------------------------------------------------------
+# A run of steps: J = sum_s lw_s . wrench_s + lc_s . centre_s
+N_RUN, EVERY = 4, 3
+
+
+def _oracle_run_J(sc, lw, lc, dt, params=None, x=None, u=None, sig=None, rho=None, bodies=None):
+    s2 = sc.copy()
+    if params is not None:
+        s2.params = params
+    for k, v in (("x", x), ("u", u), ("sig", sig), ("rho", rho)):
+        if v is not None:
+            setattr(s2, k, v)
+    st = oracle.State(s2)
+    if bodies is not None:
+        st.bodies = bodies
+    J = 0.0
+    for s in range(lw.shape[0]):
+        st.step(dt, "brute" if sc.x.shape[0] < 4000 else "cells")
+        J += float(np.sum(lw[s, 0] * st.bodies.wrench[0]) + np.sum(lc[s, 0] * st.bodies.pose[0, :3]))
+    return J
+
+
+@pytest.fixture(scope="module")
+def run_case():
+    sc = _wheel(seed=31, nx=16, ny=12, nz=6)
+    sc.params["mu_2"] = sc.params["mu_s"]
+    sc.params["skin"] = 0.0            # differentiable runs search the cells every step
+    t = crm.from_scene(sc)
+    dt = sc.dt
+    w, q = t.adjoint_forward(dt, N_RUN, EVERY)
+    rng = np.random.default_rng(7)
+    lw = rng.normal(size=(N_RUN, 1, 6))
+    lw[:, :, 3:] *= 10.0
+    lc = rng.normal(size=(N_RUN, 1, 3)) * 1e3
+    g = t.adjoint_backward(lw, lc)
+    return sc, t, dt, w, q, lw, lc, g
+
+
+def test_run_forward_matches_plain_steps(run_case):
+    sc, t, dt, w, q, *_ = run_case
+    t2 = crm.from_scene(sc.copy())
+    for s in range(N_RUN):
+        t2.step(dt, 1)
+        f, tq = t2.body_wrench(0)
+        np.testing.assert_array_equal(w[s, 0], np.concatenate([f, tq]))
+        pose, _ = t2.body_state(0)
+        np.testing.assert_array_equal(q[s, 0], pose)
+
+
+@pytest.mark.parametrize("name", ["E", "nu", "rho0", "mu_s", "cohesion", "av_gamma", "x", "u",
+                                  "sig", "rho", "body_c", "body_v"])
+def test_run_gradient_matches_oracle_differences(run_case, name):
+    sc, t, dt, w, q, lw, lc, g = run_case
+    rng = np.random.default_rng(11)
+    base = oracle.State(sc)
+    n = sc.x.shape[0]
+    h = sc.params["h"]
+    if name in ("x", "u", "sig", "rho"):
+        shape = {"x": (n, 3), "u": (n, 3), "sig": (n, 6), "rho": (n,)}[name]
+        d = rng.normal(size=shape)
+        e = {"x": 1e-6 * h, "u": 1e-6, "sig": 1e-2, "rho": 1e-3}[name]
+        arr = getattr(base, name)
+        jp = _oracle_run_J(sc, lw, lc, dt, **{name: arr + e * d})
+        jm = _oracle_run_J(sc, lw, lc, dt, **{name: arr - e * d})
+        key = {"x": "xyz", "u": "vel", "sig": "stress", "rho": "rho"}[name]
+        terms = g[key].reshape(d.shape) * d
+    elif name in ("body_c", "body_v"):
+        d = rng.normal(size=3)
+        e = 1e-6 * h if name == "body_c" else 1e-6
+        bp, bm = copy.deepcopy(base.bodies), copy.deepcopy(base.bodies)
+        if name == "body_c":
+            bp.pose[0, :3] += e * d
+            bm.pose[0, :3] -= e * d
+        else:
+            bp.twist[0, :3] += e * d
+            bm.twist[0, :3] -= e * d
+        jp = _oracle_run_J(sc, lw, lc, dt, bodies=bp)
+        jm = _oracle_run_J(sc, lw, lc, dt, bodies=bm)
+        off = 0 if name == "body_c" else 3
+        terms = g["body"][0, off:off + 3] * d
+    else:
+        e = 1e-6 * abs(sc.params[name])
+        pp, pm = dict(sc.params), dict(sc.params)
+        pp[name] += e
+        pm[name] -= e
+        if name == "mu_s":   # a constant friction coefficient: mu_2 follows mu_s
+            pp["mu_2"], pm["mu_2"] = pp["mu_s"], pm["mu_s"]
+        jp = _oracle_run_J(sc, lw, lc, dt, params=pp)
+        jm = _oracle_run_J(sc, lw, lc, dt, params=pm)
+        terms = np.array([g["param_grads"][name]])
+    fd = (jp - jm) / (2 * e)
+    ad, scale = float(terms.sum()), float(np.abs(terms).sum())
+    assert abs(ad - fd) <= RUN_TOL * max(scale, abs(fd)) + 1e-9, (name, ad, fd, scale)
+
+
+def test_run_backward_restores_the_final_state(run_case):
+    sc, t, dt, w, q, *_ = run_case
+    pose, _ = t.body_state(0)
+    np.testing.assert_array_equal(pose, q[-1, 0])
+
+
+def test_run_rejects_unsupported_configurations():
+    sc = _wheel(seed=41, nx=16, ny=12, nz=6)
+    sc.params["skin"] = 0.0
+    sc.params["mu_2"] = sc.params["mu_s"] + 0.2      # mu(I)
+    with pytest.raises(crm.CrmError):
+        crm.from_scene(sc).adjoint_forward(sc.dt, 2, 1)
+    sc.params["mu_2"] = sc.params["mu_s"]
+    sc.params["skin"] = 0.1                          # a Verlet skin
+    with pytest.raises(crm.CrmError):
+        crm.from_scene(sc).adjoint_forward(sc.dt, 2, 1)
+    t2 = crm.from_scene(_wheel(seed=42, nx=16, ny=12, nz=6))
+    with pytest.raises(crm.CrmError):                # nothing recorded
+        t2.adjoint_backward(None, None)
