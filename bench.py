@@ -221,6 +221,133 @@ def _workload(args):
     return scenes.wheel_bin(nx=200 * s, ny=40 * s, wheel_x=0.4 * s)
 
 
+ADJ_WORKLOAD = ("differentiable wheel test: 30,000 SPH particles, 1.0x0.3x0.1 m bin at d0=0.01 m, "
+                "the wheel_bin wheel and material, skin 0, ps_freq=1, 400 steps of 5e-5 s, "
+                "checkpoint every 20; J = mean over steps 201-400 of drawbar pull F_x and of "
+                "sinkage z0 - z")
+
+
+def _adjoint_scene():
+    import scenes
+    sc = scenes.wheel_bin(seed=3, nx=100, ny=30, nz=10)
+    sc.params["skin"] = 0.0
+    return sc
+
+
+def _adjoint_objectives(n_steps: int, nb: int = 1):
+    """dJ/d wrench and dJ/d centre of the two objectives (mean drawbar pull F_x and
+    mean sinkage z0 - z over the second half of the run)."""
+    import numpy as np
+    half = n_steps // 2
+    lw_dp = np.zeros((n_steps, nb, 6))
+    lw_dp[half:, 0, 0] = 1.0 / (n_steps - half)
+    lc_sink = np.zeros((n_steps, nb, 3))
+    lc_sink[half:, 0, 2] = -1.0 / (n_steps - half)
+    return {"drawbar_pull": (lw_dp, None), "sinkage": (None, lc_sink)}
+
+
+def _phi_grads(g, mu_s: float) -> dict:
+    """(phi [rad], c, E, rho0) from the library's parameter gradients, mu_s = tan phi."""
+    return {"phi": g["mu_s"] * (1.0 + mu_s * mu_s), "cohesion": g["cohesion"], "E": g["E"],
+            "rho0": g["rho0"]}
+
+
+def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = False) -> dict:
+    """Adjoint cost against the forward step on the differentiable wheel test, and
+    the gradients of both objectives (optionally against FP64 central differences
+    of the oracle, relative step 1e-4, lists rebuilt as the oracle does)."""
+    import numpy as np
+    import torch
+
+    import paper_2507_05643_b300 as crm
+    sc = _adjoint_scene()
+    dt = sc.dt
+    with torch.cuda.stream(stream):
+        # plain forward: graph-replayed steps, CUDA events on the library's stream
+        t = crm.from_scene(sc, stream=stream)
+        t.step(dt, 4)            # commit, graph capture, warm-up
+        t.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        t.step(dt, n_steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_ms = ev[0].elapsed_time(ev[1]) / n_steps
+        t.close()
+        t = crm.from_scene(sc, stream=stream)
+        w0 = time.perf_counter()
+        wr, pose = t.adjoint_forward(dt, n_steps, every)
+        rec_s = time.perf_counter() - w0
+        grads, bwd_s = {}, []
+        for name, (lw, lc) in _adjoint_objectives(n_steps).items():
+            w0 = time.perf_counter()
+            g = t.adjoint_backward(lw, lc)
+            bwd_s.append(time.perf_counter() - w0)
+            grads[name] = _phi_grads(g["param_grads"], sc.params["mu_s"])
+        prof = t.profile()
+    half = n_steps // 2
+    out = {
+        "workload": ADJ_WORKLOAD, "n_sph": sc.n_fluid, "n_bce": sc.n_markers,
+        "forward_ms_per_step": fwd_ms,
+        "recorded_forward_ms_per_step": 1e3 * rec_s / n_steps,
+        "backward_ms_per_step": 1e3 * statistics.mean(bwd_s) / n_steps,
+        "adjoint_over_forward": 1e3 * statistics.mean(bwd_s) / n_steps / fwd_ms,
+        "objectives": {"drawbar_pull_N": float(wr[half:, 0, 0].mean()),
+                       "sinkage_m": float((sc.bodies[0].pose[2] - pose[half:, 0, 2]).mean())},
+        "gradients": grads,
+        "gradient_units": "per rad (phi), per Pa (cohesion, E), per kg/m^3 (rho0)",
+        "adjoint_launches": prof["launches"].get("adjoint", 0),
+        "timing": "forward: CUDA events over the graph-replayed steps; backward: host wall "
+                  "time of crm_adjoint_backward (recompute of every segment + reverse sweep)",
+    }
+    if fd:
+        out["fd_check"] = _adjoint_fd(sc, n_steps, grads)
+    return out
+
+
+def _adjoint_fd(sc, n_steps: int, grads: dict) -> dict:
+    """FP64 central differences of both objectives with the oracle (relative step
+    1e-4; mu_2 follows mu_s)."""
+    import math
+
+    import numpy as np
+
+    import oracle
+    half = n_steps // 2
+    dt = sc.dt
+    z0 = sc.bodies[0].pose[2]
+
+    def run(params):
+        s2 = sc.copy()
+        s2.params = params
+        st = oracle.State(s2)
+        fx, z = [], []
+        for _ in range(n_steps):
+            st.step(dt)
+            fx.append(st.bodies.wrench[0, 0])
+            z.append(st.bodies.pose[0, 2])
+        return {"drawbar_pull": float(np.mean(fx[half:])), "sinkage": float(np.mean(z0 - np.array(z[half:])))}
+
+    res = {}
+    phi = math.atan(sc.params["mu_s"])
+    for name in ("phi", "cohesion", "E", "rho0"):
+        pp, pm = dict(sc.params), dict(sc.params)
+        if name == "phi":
+            e = 1e-4 * phi
+            pp["mu_s"] = pp["mu_2"] = math.tan(phi + e)
+            pm["mu_s"] = pm["mu_2"] = math.tan(phi - e)
+        else:
+            e = 1e-4 * abs(sc.params[name])
+            pp[name] += e
+            pm[name] -= e
+        jp, jm = run(pp), run(pm)
+        for obj in ("drawbar_pull", "sinkage"):
+            fdv = (jp[obj] - jm[obj]) / (2 * e)
+            res.setdefault(obj, {})[name] = {"adjoint": grads[obj][name], "fd": fdv,
+                                             "rel_err": abs(grads[obj][name] - fdv) / max(abs(fdv), 1e-300)}
+    return res
+
+
 def run_batch(args):
     """The batched ensemble (64 single-wheel bins of uneven size, each on its own
     stream, stepped by one crm_batch_step per step after a per-member autotune)
@@ -434,6 +561,8 @@ def run_crm(args):
                 f"({sc.n_fluid:,} SPH stored), four-wheel rover at x=5000 m, 1 m/s, 1 m active "
                 f"boxes, dt=1e-4 s")
         line["config"]["skin"] = args.skin if args.skin is not None else 0.1
+        if not args.no_adjoint and args.workload == "wheel_bin" and args.bin_scale == 1:
+            line["adjoint"] = adjoint_line(stream, dev, fd=args.adjoint_fd)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -459,6 +588,11 @@ def main():
     ap.add_argument("--batch-n", type=int, default=64, help="bins in the batched ensemble")
     ap.add_argument("--strip-length", type=float, default=20.0,
                     help="length in m of the strip window around the rover")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint-cost measurement on the differentiable wheel test")
+    ap.add_argument("--adjoint-fd", action="store_true",
+                    help="also check its gradients against FP64 central differences of the "
+                         "oracle (about 8 oracle runs of 400 steps)")
     ap.add_argument("--bin-scale", type=int, default=1,
                     help="profiling only: widen the bin S-fold in x and y")
     args = ap.parse_args()

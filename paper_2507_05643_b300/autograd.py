@@ -1,0 +1,58 @@
+"""``torch.autograd.Function`` over a differentiable run of the terrain.
+
+The forward records a run through ``crm_adjoint_forward`` (checkpoints every
+``every`` steps); the backward hands the incoming gradients of the per-step
+body wrench and centre to ``crm_adjoint_backward`` (recompute of each segment,
+then the hand-derived reverse sweep in the CUDA library).  Tensors here are
+FP64 host tensors: the run itself stays on the device inside the library.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import GRAD_NAMES, from_scene
+
+
+class TerrainRun(torch.autograd.Function):
+    """(wrench, centre) = TerrainRun.apply(params, x, u, sig, rho, scene, n_steps, every).
+
+    params: FP64 tensor in GRAD_NAMES order (E, nu, rho0, mu_s, cohesion,
+    av_gamma; mu_2 follows mu_s); x, u, sig, rho: the initial SPH state
+    (n, 3), (n, 3), (n, 6), (n,); scene: the ``scenes.Scene`` that supplies
+    the walls, bodies and the other constants.  Returns the soil wrench
+    (n_steps, n_bodies, 6) and the body centres (n_steps, n_bodies, 3) after
+    each step.  Every tensor input receives its gradient."""
+
+    @staticmethod
+    def forward(ctx, params, x, u, sig, rho, scene, n_steps: int, every: int):
+        sc = scene.copy()
+        p = params.detach().cpu().double().numpy()
+        for k, name in enumerate(GRAD_NAMES):
+            sc.params[name] = float(p[k])
+        sc.params["mu_2"] = sc.params["mu_s"]
+        sc.x = x.detach().cpu().double().numpy().copy()
+        sc.u = u.detach().cpu().double().numpy().copy()
+        sc.sig = sig.detach().cpu().double().numpy().copy()
+        sc.rho = rho.detach().cpu().double().numpy().copy()
+        t = from_scene(sc, skin=0.0)
+        w, q = t.adjoint_forward(sc.dt, int(n_steps), int(every))
+        ctx.terrain = t
+        return torch.from_numpy(w.copy()), torch.from_numpy(q[..., :3].copy())
+
+    @staticmethod
+    def backward(ctx, g_wrench, g_centre):
+        t = ctx.terrain
+        lw = None if g_wrench is None else g_wrench.detach().cpu().double().numpy()
+        lc = None if g_centre is None else g_centre.detach().cpu().double().numpy()
+        g = t.adjoint_backward(lw, lc)
+        ctx.terrain = None
+        t.close()
+        return (torch.from_numpy(g["params"].copy()), torch.from_numpy(g["xyz"].copy()),
+                torch.from_numpy(g["vel"].copy()), torch.from_numpy(g["stress"].copy()),
+                torch.from_numpy(g["rho"].copy()), None, None, None)
+
+
+def scene_params(scene) -> torch.Tensor:
+    """The scene's differentiable constants as a tensor in GRAD_NAMES order."""
+    return torch.tensor([float(scene.params[n]) for n in GRAD_NAMES], dtype=torch.float64)

@@ -288,3 +288,22 @@ def test_run_rejects_unsupported_configurations():
     t2 = crm.from_scene(_wheel(seed=42, nx=16, ny=12, nz=6))
     with pytest.raises(crm.CrmError):                # nothing recorded
         t2.adjoint_backward(None, None)
+
+
+def test_autograd_function_matches_the_c_abi(run_case):
+    import torch
+
+    from paper_2507_05643_b300.autograd import TerrainRun, scene_params
+    sc, t, dt, w, q, lw, lc, g = run_case
+    params = scene_params(sc).requires_grad_(True)
+    state = [torch.tensor(a, dtype=torch.float64, requires_grad=True)
+             for a in (sc.x, sc.u, sc.sig, sc.rho)]
+    W, Cc = TerrainRun.apply(params, *state, sc, N_RUN, EVERY)
+    np.testing.assert_array_equal(W.detach().numpy(), w)
+    J = (W * torch.from_numpy(lw)).sum() + (Cc * torch.from_numpy(lc)).sum()
+    J.backward()
+    # the same sweep; FP64 atomics order the parameter and body sums freely
+    np.testing.assert_allclose(params.grad.numpy(), g["params"], rtol=1e-6)
+    for a, key in zip(state, ("xyz", "vel", "stress", "rho")):
+        np.testing.assert_allclose(a.grad.numpy(), g[key], rtol=1e-4,
+                                   atol=1e-6 * np.abs(g[key]).max())
