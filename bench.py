@@ -305,9 +305,11 @@ def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = Fa
     return out
 
 
-def _adjoint_fd(sc, n_steps: int, grads: dict) -> dict:
-    """FP64 central differences of both objectives with the oracle (relative step
-    1e-4; mu_2 follows mu_s)."""
+def _adjoint_fd(sc, n_steps: int, grads: dict, rels=(1e-4, 1e-6)) -> dict:
+    """FP64 central differences of both objectives with the oracle at relative
+    steps `rels` (mu_2 follows mu_s).  The objectives are piecewise smooth (each
+    particle's return-map case can switch), so a difference converges to the
+    derivative only once the step is below the nearest switch."""
     import math
 
     import numpy as np
@@ -330,21 +332,23 @@ def _adjoint_fd(sc, n_steps: int, grads: dict) -> dict:
 
     res = {}
     phi = math.atan(sc.params["mu_s"])
-    for name in ("phi", "cohesion", "E", "rho0"):
-        pp, pm = dict(sc.params), dict(sc.params)
-        if name == "phi":
-            e = 1e-4 * phi
-            pp["mu_s"] = pp["mu_2"] = math.tan(phi + e)
-            pm["mu_s"] = pm["mu_2"] = math.tan(phi - e)
-        else:
-            e = 1e-4 * abs(sc.params[name])
-            pp[name] += e
-            pm[name] -= e
-        jp, jm = run(pp), run(pm)
-        for obj in ("drawbar_pull", "sinkage"):
-            fdv = (jp[obj] - jm[obj]) / (2 * e)
-            res.setdefault(obj, {})[name] = {"adjoint": grads[obj][name], "fd": fdv,
-                                             "rel_err": abs(grads[obj][name] - fdv) / max(abs(fdv), 1e-300)}
+    for rel in rels:
+        for name in ("phi", "cohesion", "E", "rho0"):
+            pp, pm = dict(sc.params), dict(sc.params)
+            if name == "phi":
+                e = rel * phi
+                pp["mu_s"] = pp["mu_2"] = math.tan(phi + e)
+                pm["mu_s"] = pm["mu_2"] = math.tan(phi - e)
+            else:
+                e = rel * abs(sc.params[name])
+                pp[name] += e
+                pm[name] -= e
+            jp, jm = run(pp), run(pm)
+            for obj in ("drawbar_pull", "sinkage"):
+                fdv = (jp[obj] - jm[obj]) / (2 * e)
+                res.setdefault(f"step {rel:g}", {}).setdefault(obj, {})[name] = {
+                    "adjoint": grads[obj][name], "fd": fdv,
+                    "rel_err": abs(grads[obj][name] - fdv) / max(abs(fdv), 1e-300)}
     return res
 
 

@@ -57,28 +57,54 @@ struct Coef {
     float lc, lM[3], lL[9], lA[3];   // cont, M, L (row-major), A
 };
 
-__device__ __forceinline__ Coef load_coef(const float *c, int64_t cs, int s)
+// A slot's coefficients as four float4 (64 contiguous bytes):
+// (cont, M), (L0..L3), (L4..L7), (L8, A).
+__device__ __forceinline__ Coef load_coef(const float4 *c4, int s)
 {
+    const float4 a = c4[4 * (size_t)s], b = c4[4 * (size_t)s + 1], c = c4[4 * (size_t)s + 2],
+                 d = c4[4 * (size_t)s + 3];
     Coef C;
-    C.lc = c[s];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) C.lM[k] = c[(1 + k) * cs + s];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) C.lL[k] = c[(4 + k) * cs + s];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) C.lA[k] = c[(13 + k) * cs + s];
+    C.lc = a.x; C.lM[0] = a.y; C.lM[1] = a.z; C.lM[2] = a.w;
+    C.lL[0] = b.x; C.lL[1] = b.y; C.lL[2] = b.z; C.lL[3] = b.w;
+    C.lL[4] = c.x; C.lL[5] = c.y; C.lL[6] = c.z; C.lL[7] = c.w;
+    C.lL[8] = d.x; C.lA[0] = d.y; C.lA[1] = d.z; C.lA[2] = d.w;
     return C;
 }
 
-__device__ __forceinline__ void store_coef(float *c, int64_t cs, int s, const Coef &C)
+__device__ __forceinline__ void store_coef(float4 *c4, int s, const Coef &C)
 {
-    c[s] = C.lc;
+    c4[4 * (size_t)s] = make_float4(C.lc, C.lM[0], C.lM[1], C.lM[2]);
+    c4[4 * (size_t)s + 1] = make_float4(C.lL[0], C.lL[1], C.lL[2], C.lL[3]);
+    c4[4 * (size_t)s + 2] = make_float4(C.lL[4], C.lL[5], C.lL[6], C.lL[7]);
+    c4[4 * (size_t)s + 3] = make_float4(C.lL[8], C.lA[0], C.lA[1], C.lA[2]);
+}
+
+// A marker's BCE coefficients, padded to four float4.
+__device__ __forceinline__ void load_bce(const float4 *b4, int m, float cb[kNumBceCoef])
+{
+    const float4 a = b4[4 * (size_t)m], b = b4[4 * (size_t)m + 1], c = b4[4 * (size_t)m + 2],
+                 d = b4[4 * (size_t)m + 3];
+    cb[0] = a.x; cb[1] = a.y; cb[2] = a.z; cb[3] = a.w;
+    cb[4] = b.x; cb[5] = b.y; cb[6] = b.z; cb[7] = b.w;
+    cb[8] = c.x; cb[9] = c.y; cb[10] = c.z; cb[11] = c.w;
+    cb[12] = d.x;
+}
+
+__device__ __forceinline__ void store_bce(float4 *b4, int m, const float cb[kNumBceCoef])
+{
+    b4[4 * (size_t)m] = make_float4(cb[0], cb[1], cb[2], cb[3]);
+    b4[4 * (size_t)m + 1] = make_float4(cb[4], cb[5], cb[6], cb[7]);
+    b4[4 * (size_t)m + 2] = make_float4(cb[8], cb[9], cb[10], cb[11]);
+    b4[4 * (size_t)m + 3] = make_float4(cb[12], 0.f, 0.f, 0.f);
+}
+
+// Sum over the LANES lanes that share a particle (every lane of the warp calls it).
+template <int LANES>
+__device__ __forceinline__ float lane_sum(float v)
+{
 #pragma unroll
-    for (int k = 0; k < 3; ++k) c[(1 + k) * cs + s] = C.lM[k];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) c[(4 + k) * cs + s] = C.lL[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) c[(13 + k) * cs + s] = C.lA[k];
+    for (int o = 1; o < LANES; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // Adjoint of one particle's inputs: position, velocity, stress, density.
@@ -379,6 +405,11 @@ __device__ __forceinline__ void jaumann_vjp(const float L[9], const float s6[6],
 }
 
 // ---------------------------------------------------------------------------
+// Lanes per particle of the gather passes: each lane walks every LANES-th entry
+// of the list and the sums are combined by shuffles (a 30k-particle bin would
+// otherwise leave most of the GPU's warp slots empty).
+constexpr int kAdjLanes = 4;
+
 // Pass 1: fluid coefficients.  MODE kAdjEval: the rates' adjoints come from
 // l_rate (insertion order) and the local terms are written to l_out (slot
 // order).  MODE kAdjStage2: the state is y_mid (V.S), y_n is Y0 and the
@@ -386,7 +417,7 @@ __device__ __forceinline__ void jaumann_vjp(const float L[9], const float s6[6],
 // y_mid go to l_mid and those at y_n (the integrator's identity parts through
 // the return map) to l_y0.  MODE kAdjStage1: the state is y_n and the adjoint
 // of y_mid is l_mid (complete); everything is added to l_y0.
-template <int MODE>
+template <int MODE, int LANES>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar)
 {
@@ -394,18 +425,21 @@ k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar
     fill_shift_table(lut, p.cell);
     __syncthreads();
     const Sizes z = load_sizes(p);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LANES, q = t % LANES;
+    const bool valid = i < z.nF;
     ParAcc par;
     par_zero(par);
-    if (i < z.nF) {
-        const StageArrays &S = V.S;
-        const float4 pi = S.pos[i];
-        const PState I = load_state(S, i);
-        float cont = 0.f, M[3] = {0.f, 0.f, 0.f}, L[9];
+    const StageArrays &S = V.S;
+    float cont = 0.f, M[3] = {0.f, 0.f, 0.f}, L[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) L[k] = 0.f;
+    for (int k = 0; k < 9; ++k) L[k] = 0.f;
+    PState I{};
+    if (valid) {
+        const float4 pi = S.pos[i];
+        I = load_state(S, i);
         const int nn = (int)V.nnb[i];
-        for (int k = 0; k < nn; ++k) {
+        for (int k = q; k < nn; k += LANES) {
             const uint32_t e = V.nbr[(size_t)k * p.ell + i];
             const uint32_t j = e & kIndexMask;
             const float4 sh = lut[e >> kIndexBits];
@@ -430,6 +464,13 @@ k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar
 #pragma unroll
                 for (int b = 0; b < 3; ++b) L[3 * a + b] += Vj * u[a] * g[b];
         }
+    }
+    cont = lane_sum<LANES>(cont);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) M[k] = lane_sum<LANES>(M[k]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) L[k] = lane_sum<LANES>(L[k]);
+    if (valid && q == 0) {
         const float si[6] = {I.a.x, I.a.y, I.a.z, I.a.w, I.b.x, I.b.y};
         const uint32_t id = pid_index(V.pid[i]);
         const int64_t ns = io.n_fluid;          // stride of the insertion-order arrays
@@ -503,7 +544,7 @@ k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar
         }
         loc.rho += -cont * lr[0] - (M[0] * lr[1] + M[1] * lr[2] + M[2] * lr[3]) / (rho * rho);
         jaumann_vjp(L, si, lr + 4, p, C.lL, loc.s, par);
-        store_coef(io.coef, io.coef_stride, i, C);
+        store_coef(io.coef, i, C);
         if (MODE == kAdjEval) {
             adj_store(io.l_out, io.slot_stride, i, loc);
         } else if (MODE == kAdjStage2) {
@@ -592,7 +633,7 @@ k_adj_marker_coef(DevParams p, AdjStage V, AdjIO io, double *gpar)
             C.lM[k] = la[k] / p.rho0;
             C.lA[k] = la[k];
         }
-        store_coef(io.coef, io.coef_stride, s, C);
+        store_coef(io.coef, s, C);
         if (la[0] != 0.f || la[1] != 0.f || la[2] != 0.f) {
             // M and A again, for the terms of 1 / rho0 and of m in m a
             const StageArrays &S = V.S;
@@ -645,7 +686,7 @@ k_adj_marker_coef(DevParams p, AdjStage V, AdjIO io, double *gpar)
 // adjoints (coefficients from pass 2).  Writes the BCE coefficients of every
 // marker slot and adds the body adjoints (centre, velocity, acceleration) to
 // gbody [body][9].
-template <bool ACC>
+template <bool ACC, int LANES>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
 {
@@ -653,125 +694,129 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
     fill_shift_table(lut, p.cell);
     __syncthreads();
     const Sizes z = load_sizes(p);
-    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = z.nF + t / LANES, q = t % LANES;
+    const bool valid = s < z.N;
     ParAcc par;
     par_zero(par);
+    const int nn = valid ? (int)V.nnb[s] : 0;
+    float ub[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f}, arm[3];
     int body = -1;
-    float bx[3] = {0.f, 0.f, 0.f}, bu[3] = {0.f, 0.f, 0.f}, ba[3] = {0.f, 0.f, 0.f};
-    if (s < z.N) {
-        const int mslot = s - z.nF;
-        const int64_t bs = io.coefB_stride;
-        const int nn = (int)V.nnb[s];
-        float ub[3], ab[3], arm[3];
-        body = marker_body_kin(p, V, s, ub, ab, arm);
-        if (nn == 0) {
-            for (int k = 0; k < kNumBceCoef; ++k) io.coefB[k * bs + mslot] = 0.f;
-            body = -1;
-        } else {
-            const StageArrays &S = V.S;
-            const float4 pa = S.pos[s];
-            const PState A0 = load_state(S, s);
-            Coef Ca;
-            if (ACC) Ca = load_coef(io.coef, io.coef_stride, s);
-            Adj la;
-            adj_zero(la);
-            float w = 0.f, su[3] = {0.f, 0.f, 0.f}, ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float sr[3] = {0.f, 0.f, 0.f};
-            for (int k = 0; k < nn; ++k) {
-                const uint32_t e = V.nbr[(size_t)k * p.ell + s];
-                const uint32_t f = e & kIndexMask;
-                const float4 sh = lut[e >> kIndexBits];
-                const float4 pf = S.pos[f];
-                const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
-                const float r2 = rx * rx + ry * ry + rz * rz;
-                if (!(r2 < p.four_h2)) continue;
-                const PState Fs = load_state(S, f);
-                const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
-                w += W;
-                su[0] += Fs.v.x * W; su[1] += Fs.v.y * W; su[2] += Fs.v.z * W;
-                ss[0] += Fs.a.x * W; ss[1] += Fs.a.y * W; ss[2] += Fs.a.z * W;
-                ss[3] += Fs.a.w * W; ss[4] += Fs.b.x * W; ss[5] += Fs.b.y * W;
-                const float rw = Fs.v.w * W;
-                sr[0] += rw * rx; sr[1] += rw * ry; sr[2] += rw * rz;
-                if (r2 == 0.0f) continue;
-                // the fluid particle's pair that reads this marker (r_fa = -r)
-                const Coef Cf = load_coef(io.coef, io.coef_stride, (int)f);
-                pair_vjp(p, Cf, -rx, -ry, -rz, r2, Fs, Fs.v.w, A0, nullptr, &la, nullptr);
-                // the marker's own acceleration pair
-                if (ACC) pair_vjp(p, Ca, rx, ry, rz, r2, A0, p.rho0, Fs, &la, nullptr, &par);
-            }
-            // the marker density is rho0
-            par.v[kGradRho0] += (double)la.rho;
-            float cb[kNumBceCoef];
-#pragma unroll
-            for (int k = 0; k < kNumBceCoef; ++k) cb[k] = 0.f;
-            float lub[3] = {0.f, 0.f, 0.f}, lab[3] = {0.f, 0.f, 0.f};
-            if (w > 0.f) {
-                const float iw = 1.0f / w;
-                const float ua[3] = {2.f * ub[0] - su[0] * iw, 2.f * ub[1] - su[1] * iw,
-                                     2.f * ub[2] - su[2] * iw};
-                const float gp = (p.gx - ab[0]) * sr[0] + (p.gy - ab[1]) * sr[1] + (p.gz - ab[2]) * sr[2];
-                const float sa[6] = {(ss[0] - gp) * iw, (ss[1] - gp) * iw, (ss[2] - gp) * iw,
-                                     ss[3] * iw, ss[4] * iw, ss[5] * iw};
-                float lw = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    cb[kBceSu + k] = -la.u[k] * iw;
-                    lw += la.u[k] * (2.f * ub[k] - ua[k]) * iw;   // su / w^2 = (2 ub - ua) / w
-                    lub[k] = 2.f * la.u[k];
-                }
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    cb[kBceSs + k] = la.s[k] * iw;
-                    lw -= la.s[k] * sa[k] * iw;
-                }
-                const float lgp = -(la.s[0] + la.s[1] + la.s[2]) * iw;
-                cb[kBceSr + 0] = lgp * (p.gx - ab[0]);
-                cb[kBceSr + 1] = lgp * (p.gy - ab[1]);
-                cb[kBceSr + 2] = lgp * (p.gz - ab[2]);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) lab[k] = -lgp * sr[k];
-                cb[kBceW] = lw;
-                // the marker position in its BCE sums
-                for (int k = 0; k < nn; ++k) {
-                    const uint32_t e = V.nbr[(size_t)k * p.ell + s];
-                    const uint32_t f = e & kIndexMask;
-                    const float4 sh = lut[e >> kIndexBits];
-                    const float4 pf = S.pos[f];
-                    const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
-                    const float r2 = rx * rx + ry * ry + rz * rz;
-                    if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
-                    const PState Fs = load_state(S, f);
-                    const float rinv = rsqrtf(r2);
-                    const float q = r2 * rinv * p.inv_h;
-                    const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
-                    const float F = kernel_dw_over_r(q, rinv, p);
-                    const float lW = cb[kBceW] + cb[kBceSu] * Fs.v.x + cb[kBceSu + 1] * Fs.v.y
-                                     + cb[kBceSu + 2] * Fs.v.z + cb[kBceSs] * Fs.a.x
-                                     + cb[kBceSs + 1] * Fs.a.y + cb[kBceSs + 2] * Fs.a.z
-                                     + cb[kBceSs + 3] * Fs.a.w + cb[kBceSs + 4] * Fs.b.x
-                                     + cb[kBceSs + 5] * Fs.b.y
-                                     + Fs.v.w * (cb[kBceSr] * rx + cb[kBceSr + 1] * ry + cb[kBceSr + 2] * rz);
-                    const float rw = Fs.v.w * W, fl = lW * F;
-                    la.x[0] += rw * cb[kBceSr] + fl * rx;
-                    la.x[1] += rw * cb[kBceSr + 1] + fl * ry;
-                    la.x[2] += rw * cb[kBceSr + 2] + fl * rz;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) lub[k] = la.u[k];
-            }
-            for (int k = 0; k < kNumBceCoef; ++k) io.coefB[k * bs + mslot] = cb[k];
-            if (body >= 0) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    bx[k] = la.x[k];
-                    bu[k] = lub[k];
-                    ba[k] = lab[k];
-                }
-            }
-        }
+    if (valid && nn > 0) body = marker_body_kin(p, V, s, ub, ab, arm);
+    const StageArrays &S = V.S;
+    const float4 pa = nn > 0 ? S.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+    PState A0{};
+    if (nn > 0) A0 = load_state(S, s);
+    Coef Ca{};
+    if (ACC && nn > 0) Ca = load_coef(io.coef, s);
+    Adj la;
+    adj_zero(la);
+    float w = 0.f, su[3] = {0.f, 0.f, 0.f}, ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float sr[3] = {0.f, 0.f, 0.f};
+    for (int k = q; k < nn; k += LANES) {
+        const uint32_t e = V.nbr[(size_t)k * p.ell + s];
+        const uint32_t f = e & kIndexMask;
+        const float4 sh = lut[e >> kIndexBits];
+        const float4 pf = S.pos[f];
+        const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        if (!(r2 < p.four_h2)) continue;
+        const PState Fs = load_state(S, f);
+        const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
+        w += W;
+        su[0] += Fs.v.x * W; su[1] += Fs.v.y * W; su[2] += Fs.v.z * W;
+        ss[0] += Fs.a.x * W; ss[1] += Fs.a.y * W; ss[2] += Fs.a.z * W;
+        ss[3] += Fs.a.w * W; ss[4] += Fs.b.x * W; ss[5] += Fs.b.y * W;
+        const float rw = Fs.v.w * W;
+        sr[0] += rw * rx; sr[1] += rw * ry; sr[2] += rw * rz;
+        if (r2 == 0.0f) continue;
+        // the fluid particle's pair that reads this marker (r_fa = -r)
+        const Coef Cf = load_coef(io.coef, (int)f);
+        pair_vjp(p, Cf, -rx, -ry, -rz, r2, Fs, Fs.v.w, A0, nullptr, &la, nullptr);
+        // the marker's own acceleration pair
+        if (ACC) pair_vjp(p, Ca, rx, ry, rz, r2, A0, p.rho0, Fs, &la, nullptr, &par);
     }
+    w = lane_sum<LANES>(w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        su[k] = lane_sum<LANES>(su[k]);
+        sr[k] = lane_sum<LANES>(sr[k]);
+        la.x[k] = lane_sum<LANES>(la.x[k]);
+        la.u[k] = lane_sum<LANES>(la.u[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        ss[k] = lane_sum<LANES>(ss[k]);
+        la.s[k] = lane_sum<LANES>(la.s[k]);
+    }
+    la.rho = lane_sum<LANES>(la.rho);
+    // BCE extrapolation backward (every lane of the marker, redundantly)
+    float cb[kNumBceCoef];
+#pragma unroll
+    for (int k = 0; k < kNumBceCoef; ++k) cb[k] = 0.f;
+    float lub[3] = {0.f, 0.f, 0.f}, lab[3] = {0.f, 0.f, 0.f}, px[3] = {0.f, 0.f, 0.f};
+    if (w > 0.f) {
+        const float iw = 1.0f / w;
+        const float ua[3] = {2.f * ub[0] - su[0] * iw, 2.f * ub[1] - su[1] * iw,
+                             2.f * ub[2] - su[2] * iw};
+        const float gp = (p.gx - ab[0]) * sr[0] + (p.gy - ab[1]) * sr[1] + (p.gz - ab[2]) * sr[2];
+        const float sa[6] = {(ss[0] - gp) * iw, (ss[1] - gp) * iw, (ss[2] - gp) * iw,
+                             ss[3] * iw, ss[4] * iw, ss[5] * iw};
+        float lw = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            cb[kBceSu + k] = -la.u[k] * iw;
+            lw += la.u[k] * (2.f * ub[k] - ua[k]) * iw;   // su / w^2 = (2 ub - ua) / w
+            lub[k] = 2.f * la.u[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            cb[kBceSs + k] = la.s[k] * iw;
+            lw -= la.s[k] * sa[k] * iw;
+        }
+        const float lgp = -(la.s[0] + la.s[1] + la.s[2]) * iw;
+        cb[kBceSr + 0] = lgp * (p.gx - ab[0]);
+        cb[kBceSr + 1] = lgp * (p.gy - ab[1]);
+        cb[kBceSr + 2] = lgp * (p.gz - ab[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lab[k] = -lgp * sr[k];
+        cb[kBceW] = lw;
+        // the marker position in its BCE sums
+        for (int k = q; k < nn; k += LANES) {
+            const uint32_t e = V.nbr[(size_t)k * p.ell + s];
+            const uint32_t f = e & kIndexMask;
+            const float4 sh = lut[e >> kIndexBits];
+            const float4 pf = S.pos[f];
+            const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
+            const PState Fs = load_state(S, f);
+            const float rinv = rsqrtf(r2);
+            const float qk = r2 * rinv * p.inv_h;
+            const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
+            const float F = kernel_dw_over_r(qk, rinv, p);
+            const float lW = cb[kBceW] + cb[kBceSu] * Fs.v.x + cb[kBceSu + 1] * Fs.v.y
+                             + cb[kBceSu + 2] * Fs.v.z + cb[kBceSs] * Fs.a.x
+                             + cb[kBceSs + 1] * Fs.a.y + cb[kBceSs + 2] * Fs.a.z
+                             + cb[kBceSs + 3] * Fs.a.w + cb[kBceSs + 4] * Fs.b.x
+                             + cb[kBceSs + 5] * Fs.b.y
+                             + Fs.v.w * (cb[kBceSr] * rx + cb[kBceSr + 1] * ry + cb[kBceSr + 2] * rz);
+            const float rw = Fs.v.w * W, fl = lW * F;
+            px[0] += rw * cb[kBceSr] + fl * rx;
+            px[1] += rw * cb[kBceSr + 1] + fl * ry;
+            px[2] += rw * cb[kBceSr + 2] + fl * rz;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lub[k] = la.u[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) la.x[k] += lane_sum<LANES>(px[k]);
+    if (valid && q == 0) {
+        store_bce(io.coefB, s - z.nF, cb);
+        par.v[kGradRho0] += (double)la.rho;     // the marker density is rho0
+    }
+    if (q != 0) body = -1;
     par_flush(par, gpar);
     // per-body sums: warp reduction, one FP64 atomic per warp and entry
     const int lane = threadIdx.x & 31;
@@ -781,9 +826,9 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
         double v[9];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            v[k] = mine ? bx[k] : 0.0;
-            v[3 + k] = mine ? bu[k] : 0.0;
-            v[6 + k] = mine ? ba[k] : 0.0;
+            v[k] = mine ? la.x[k] : 0.0;
+            v[3 + k] = mine ? lub[k] : 0.0;
+            v[6 + k] = mine ? lab[k] : 0.0;
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -798,7 +843,7 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
 // coefficients.  OUT kAdjAccumulate: the sums are added to l_acc (slot order);
 // kAdjFinal: l_acc (slot order) plus the sums is written to l_final at the
 // particle's insertion index.
-template <bool ACC, int OUT>
+template <bool ACC, int OUT, int LANES>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, double *gpar)
 {
@@ -806,19 +851,20 @@ k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, dou
     fill_shift_table(lut, p.cell);
     __syncthreads();
     const Sizes z = load_sizes(p);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LANES, q = t % LANES;
+    const bool valid = i < z.nF;
     ParAcc par;
     par_zero(par);
-    if (i < z.nF) {
+    Adj a;
+    adj_zero(a);
+    if (valid) {
         const StageArrays &S = V.S;
         const float4 pi = S.pos[i];
         const PState I = load_state(S, i);
-        const Coef Ci = load_coef(io.coef, io.coef_stride, i);
-        Adj a;
-        adj_load(l_acc, io.slot_stride, i, a);
+        const Coef Ci = load_coef(io.coef, i);
         const int nn = (int)V.nnb[i];
-        const int64_t bs = io.coefB_stride;
-        for (int k = 0; k < nn; ++k) {
+        for (int k = q; k < nn; k += LANES) {
             const uint32_t e = V.nbr[(size_t)k * p.ell + i];
             const uint32_t j = e & kIndexMask;
             const float4 sh = lut[e >> kIndexBits];
@@ -833,17 +879,15 @@ k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, dou
                 pair_vjp(p, Ci, rx, ry, rz, r2, I, I.v.w, J, &a, nullptr, &par);
                 // the neighbour's pair that reads i (j target, r_ji = -r)
                 if (!marker || ACC) {
-                    const Coef Cj = load_coef(io.coef, io.coef_stride, (int)j);
+                    const Coef Cj = load_coef(io.coef, (int)j);
                     pair_vjp(p, Cj, -rx, -ry, -rz, r2, J, marker ? p.rho0 : J.v.w, I, nullptr, &a,
                              nullptr);
                 }
             }
             if (marker) {
                 // i in marker j's BCE sums: r_a = x_j - x_i = -r
-                const int ms = (int)j - z.nF;
                 float cb[kNumBceCoef];
-#pragma unroll
-                for (int c = 0; c < kNumBceCoef; ++c) cb[c] = io.coefB[c * bs + ms];
+                load_bce(io.coefB, (int)j - z.nF, cb);
                 const float ax = -rx, ay = -ry, az = -rz;
                 const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
                 const float lsr = cb[kBceSr] * ax + cb[kBceSr + 1] * ay + cb[kBceSr + 2] * az;
@@ -866,6 +910,26 @@ k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, dou
                 }
             }
         }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a.x[k] = lane_sum<LANES>(a.x[k]);
+        a.u[k] = lane_sum<LANES>(a.u[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.s[k] = lane_sum<LANES>(a.s[k]);
+    a.rho = lane_sum<LANES>(a.rho);
+    if (valid && q == 0) {
+        Adj b;
+        adj_load(l_acc, io.slot_stride, i, b);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a.x[k] += b.x[k];
+            a.u[k] += b.u[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.s[k] += b.s[k];
+        a.rho += b.rho;
         if (OUT == kAdjAccumulate) adj_store(l_acc, io.slot_stride, i, a);
         else adj_store(l_final, io.n_fluid, pid_index(V.pid[i]), a);
     }
@@ -922,10 +986,14 @@ __global__ void k_adj_body_post(int nb, double dt, const double *g0, const doubl
 void launch_adj_fluid_coef(int mode, const DevParams &p, const AdjStage &V, StageArrays Y0,
                            const AdjIO &io, double *gpar, cudaStream_t st)
 {
-    const unsigned g = grid_for(p.capF, kAdjBlock);
-    if (mode == kAdjEval) k_adj_fluid_coef<kAdjEval><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
-    else if (mode == kAdjStage2) k_adj_fluid_coef<kAdjStage2><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
-    else k_adj_fluid_coef<kAdjStage1><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+    constexpr int LN = kAdjLanes;
+    const unsigned g = grid_for((int64_t)p.capF * LN, kAdjBlock);
+    if (mode == kAdjEval)
+        k_adj_fluid_coef<kAdjEval, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+    else if (mode == kAdjStage2)
+        k_adj_fluid_coef<kAdjStage2, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+    else
+        k_adj_fluid_coef<kAdjStage1, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
 }
 
 void launch_adj_marker_coef(int mode, const DevParams &p, const AdjStage &V, const AdjIO &io,
@@ -941,25 +1009,27 @@ void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const Ad
                        double *gpar, double *gbody, cudaStream_t st)
 {
     if (p.capM == 0) return;
-    const unsigned g = grid_for(p.capM, kAdjBlock);
-    if (acc) k_adj_marker<true><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
-    else k_adj_marker<false><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
+    constexpr int LN = kAdjLanes;
+    const unsigned g = grid_for((int64_t)p.capM * LN, kAdjBlock);
+    if (acc) k_adj_marker<true, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
+    else k_adj_marker<false, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
 }
 
 void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, const AdjIO &io,
                       float *l_acc, float *l_final, double *gpar, cudaStream_t st)
 {
-    const unsigned g = grid_for(p.capF, kAdjBlock);
+    constexpr int LN = kAdjLanes;
+    const unsigned g = grid_for((int64_t)p.capF * LN, kAdjBlock);
     if (acc) {
         if (out == kAdjAccumulate)
-            k_adj_fluid<true, kAdjAccumulate><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+            k_adj_fluid<true, kAdjAccumulate, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
         else
-            k_adj_fluid<true, kAdjFinal><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+            k_adj_fluid<true, kAdjFinal, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
     } else {
         if (out == kAdjAccumulate)
-            k_adj_fluid<false, kAdjAccumulate><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+            k_adj_fluid<false, kAdjAccumulate, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
         else
-            k_adj_fluid<false, kAdjFinal><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
+            k_adj_fluid<false, kAdjFinal, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, l_acc, l_final, gpar);
     }
 }
 

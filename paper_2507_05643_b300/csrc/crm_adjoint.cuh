@@ -33,10 +33,8 @@ struct AdjStage {
 };
 
 struct AdjIO {
-    float *coef;                 // kNumCoef x coef_stride (fluid and marker slots)
-    int64_t coef_stride;
-    float *coefB;                // kNumBceCoef x coefB_stride (marker slot - nF)
-    int64_t coefB_stride;
+    float4 *coef;                // 4 per slot (fluid and marker slots): kNumCoef values
+    float4 *coefB;               // 4 per marker (slot - nF): kNumBceCoef values, padded
     const float *l_rate;         // evaluation: rate adjoints, insertion order
                                  // (drho [n], du [3n], dsigma [6n])
     const float *l_macc;         // evaluation: marker acceleration adjoints [3 n_markers]

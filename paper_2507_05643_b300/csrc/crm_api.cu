@@ -129,8 +129,9 @@ struct crm_terrain {
     };
     struct Adjoint {
         bool ready = false;
-        float *coef = nullptr, *coefB = nullptr, *l_mid = nullptr, *l_y0 = nullptr,
-              *l_ins = nullptr, *l_rate = nullptr, *l_macc = nullptr;
+        float4 *coef = nullptr, *coefB = nullptr;
+        float *l_mid = nullptr, *l_y0 = nullptr, *l_ins = nullptr, *l_rate = nullptr,
+              *l_macc = nullptr;
         double *gpar = nullptr, *gbody = nullptr, *lb[2]{}, *lwrench = nullptr;
         // trajectory: checkpoints every `every` steps (plus the final state),
         // the bodies after each step, the objective's adjoints
@@ -1921,8 +1922,8 @@ int adj_workspace(crm_terrain *t)
     const DevParams &d = t->dp;
     const size_t nb = std::max<size_t>(t->hbodies.size(), 1);
     const size_t nF = (size_t)std::max<int64_t>(t->nFtot, 1), nM = (size_t)std::max<int64_t>(t->nMtot, 1);
-    A.coef = t->dalloc<float>(G_ADJ, (size_t)kNumCoef * std::max(d.capN, 1));
-    A.coefB = t->dalloc<float>(G_ADJ, (size_t)kNumBceCoef * std::max(d.capM, 1));
+    A.coef = t->dalloc<float4>(G_ADJ, 4 * (size_t)std::max(d.capN, 1));
+    A.coefB = t->dalloc<float4>(G_ADJ, 4 * (size_t)std::max(d.capM, 1));
     A.l_mid = t->dalloc<float>(G_ADJ, (size_t)kNumAdj * std::max(d.capF, 1));
     A.l_y0 = t->dalloc<float>(G_ADJ, (size_t)kNumAdj * std::max(d.capF, 1));
     A.l_ins = t->dalloc<float>(G_ADJ, (size_t)kNumAdj * nF);
@@ -1969,9 +1970,7 @@ AdjIO adj_io(crm_terrain *t, float dt)
     crm_terrain::Adjoint &A = t->adj;
     AdjIO io{};
     io.coef = A.coef;
-    io.coef_stride = std::max(d.capN, 1);
     io.coefB = A.coefB;
-    io.coefB_stride = std::max(d.capM, 1);
     io.l_rate = A.l_rate;
     io.l_macc = nullptr;
     io.l_wrench = A.lwrench;
