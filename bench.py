@@ -352,6 +352,23 @@ def _adjoint_fd(sc, n_steps: int, grads: dict, rels=(1e-4, 1e-6)) -> dict:
     return res
 
 
+def run_adjoint(args):
+    """--workload adjoint: the adjoint measurement alone (a profiling and
+    diagnostics line; the default line carries the same object)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    adj = adjoint_line(stream, dev, n_steps=args.adjoint_steps, fd=args.adjoint_fd)
+    line = {"metric": "adjoint step cost / forward step cost", "value": adj["adjoint_over_forward"],
+            "unit": "ratio", "n_gpus": 1, "steps": args.adjoint_steps, "warmup": 4,
+            "ms_per_step": adj["backward_ms_per_step"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": adj["workload"].replace("400 steps", f"{args.adjoint_steps} steps")},
+            "adjoint": adj}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """The batched ensemble (64 single-wheel bins of uneven size, each on its own
     stream, stepped by one crm_batch_step per step after a per-member autotune)
@@ -566,7 +583,8 @@ def run_crm(args):
                 f"boxes, dt=1e-4 s")
         line["config"]["skin"] = args.skin if args.skin is not None else 0.1
         if not args.no_adjoint and args.workload == "wheel_bin" and args.bin_scale == 1:
-            line["adjoint"] = adjoint_line(stream, dev, fd=args.adjoint_fd)
+            line["adjoint"] = adjoint_line(stream, dev, n_steps=args.adjoint_steps,
+                                           fd=args.adjoint_fd)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -586,14 +604,17 @@ def main():
                     help="Verlet skin as a fraction of 2h (default: the library's 0.1)")
     ap.add_argument("--ps-freq", type=int, default=1,
                     help="neighbour-list rebuild period (Alg. 2); the workload is quoted at 1")
-    ap.add_argument("--workload", choices=["wheel_bin", "strip", "batch"], default="wheel_bin",
-                    help="strip: the 10 km active-domain strip; batch: the 64-bin ensemble "
-                         "(parity-test configurations, not the headline line)")
+    ap.add_argument("--workload", choices=["wheel_bin", "strip", "batch", "adjoint"],
+                    default="wheel_bin",
+                    help="strip: the 10 km active-domain strip; batch: the 64-bin ensemble; "
+                         "adjoint: the adjoint measurement alone (not the headline line)")
     ap.add_argument("--batch-n", type=int, default=64, help="bins in the batched ensemble")
     ap.add_argument("--strip-length", type=float, default=20.0,
                     help="length in m of the strip window around the rover")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint-cost measurement on the differentiable wheel test")
+    ap.add_argument("--adjoint-steps", type=int, default=400,
+                    help="steps of the differentiable wheel test (the test is quoted at 400)")
     ap.add_argument("--adjoint-fd", action="store_true",
                     help="also check its gradients against FP64 central differences of the "
                          "oracle (about 8 oracle runs of 400 steps)")
@@ -606,6 +627,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_crm(args)
 
