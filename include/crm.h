@@ -282,18 +282,21 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
                         double *wrench_hist, double *pose_hist);
 
 /* Differentiable run, backward half: for an objective J of the recorded run
- * with dJ / d wrench given as l_wrench (n_steps*n_bodies*6) and dJ / d centre
- * after each step as l_center (n_steps*n_bodies*3), both nullable (= zero),
- * returns dJ / d parameters (g_params, CRM_NUM_GRADS) and the adjoints of the
- * run's initial state: SPH positions, velocities, stresses, densities
- * (insertion order, as crm_eval_rates_vjp) and bodies (g_body: centre, linear
- * velocity, linear acceleration, 9 per body); each output nullable.  Re-runs
- * every segment from its checkpoint (with direct launches) and sweeps it in
- * reverse; leaves the terrain in the state after the recorded run.
- * CRM_ESTATE without a recorded run.  Synchronises the stream. */
+ * with dJ / d wrench given as l_wrench (n_steps*n_bodies*6), dJ / d centre
+ * after each step as l_center (n_steps*n_bodies*3), and dJ / d final SPH state
+ * as l_xyz, l_vel (n_sph*3), l_stress (n_sph*6), l_rho (n_sph), insertion
+ * order, all nullable (= zero), returns dJ / d parameters (g_params,
+ * CRM_NUM_GRADS) and the adjoints of the run's initial state: SPH positions,
+ * velocities, stresses, densities (insertion order, as crm_eval_rates_vjp) and
+ * bodies (g_body: centre, linear velocity, linear acceleration, 9 per body);
+ * each output nullable.  Re-runs every segment from its checkpoint (with
+ * direct launches) and sweeps it in reverse; leaves the terrain in the state
+ * after the recorded run.  CRM_ESTATE without a recorded run.  Synchronises
+ * the stream. */
 int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l_center,
-                         double *g_params, double *g_xyz, double *g_vel, double *g_stress,
-                         double *g_rho, double *g_body);
+                         const double *l_xyz, const double *l_vel, const double *l_stress,
+                         const double *l_rho, double *g_params, double *g_xyz, double *g_vel,
+                         double *g_stress, double *g_rho, double *g_body);
 
 /* Array-capacity policy of ManageArrayMemory (Sec. 3.2): the capacity that
  * follows `cap` when `need` elements are required at step `step`: grown to

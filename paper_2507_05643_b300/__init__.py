@@ -103,7 +103,8 @@ _sig("crm_get_neighbors", C.c_int, [_T, _i64, _vp, _vp, C.POINTER(_i64)])
 _sig("crm_eval_rates_vjp", C.c_int, [_T, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp])
 _sig("crm_adjoint_forward", C.c_int, [_T, C.c_double, _i64, _i32, _vp, _vp])
-_sig("crm_adjoint_backward", C.c_int, [_T, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp])
+_sig("crm_adjoint_backward", C.c_int, [_T, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                       _vp, _vp])
 _sig("crm_state_bytes", C.c_int, [_T, C.POINTER(C.c_size_t)])
 _sig("crm_save_state", C.c_int, [_T, _vp, C.c_size_t, C.POINTER(C.c_size_t)])
 _sig("crm_load_state", C.c_int, [_T, _vp, C.c_size_t])
@@ -344,15 +345,18 @@ class Terrain:
                                              _ptr(w), _ptr(q)))
         return w[:, :nb], q[:, :nb]
 
-    def adjoint_backward(self, l_wrench=None, l_center=None) -> dict:
+    def adjoint_backward(self, l_wrench=None, l_center=None, l_xyz=None, l_vel=None,
+                         l_stress=None, l_rho=None) -> dict:
         """Gradient of an objective of the recorded run given dJ/d wrench
-        (n_steps, n_bodies, 6) and dJ/d centre after each step (n_steps,
-        n_bodies, 3): parameters and the initial state, as eval_rates_vjp."""
-        lw = None if l_wrench is None else np.ascontiguousarray(np.asarray(l_wrench, np.float64))
-        lc = None if l_center is None else np.ascontiguousarray(np.asarray(l_center, np.float64))
+        (n_steps, n_bodies, 6), dJ/d centre after each step (n_steps, n_bodies,
+        3) and dJ/d final SPH state (l_xyz, l_vel (n, 3), l_stress (n, 6), l_rho
+        (n,)): parameters and the initial state, as eval_rates_vjp."""
+        def arr(a):
+            return None if a is None else np.ascontiguousarray(np.asarray(a, np.float64))
+        lw, lc, lx, lu, ls, lr = (arr(a) for a in (l_wrench, l_center, l_xyz, l_vel, l_stress, l_rho))
         return self._grads(lambda o: _lib.crm_adjoint_backward(
-            self._h, _ptr(lw), _ptr(lc), _ptr(o["params"]), _ptr(o["xyz"]), _ptr(o["vel"]),
-            _ptr(o["stress"]), _ptr(o["rho"]), _ptr(o["body"])))
+            self._h, _ptr(lw), _ptr(lc), _ptr(lx), _ptr(lu), _ptr(ls), _ptr(lr), _ptr(o["params"]),
+            _ptr(o["xyz"]), _ptr(o["vel"]), _ptr(o["stress"]), _ptr(o["rho"]), _ptr(o["body"])))
 
     def neighbors(self) -> Tuple[np.ndarray, np.ndarray]:
         n = self.n_sph + self.n_markers

@@ -2263,8 +2263,9 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
 }
 
 int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l_center,
-                         double *g_params, double *g_xyz, double *g_vel, double *g_stress,
-                         double *g_rho, double *g_body)
+                         const double *l_xyz, const double *l_vel, const double *l_stress,
+                         const double *l_rho, double *g_params, double *g_xyz, double *g_vel,
+                         double *g_stress, double *g_rho, double *g_body)
 {
     if (!t) return CRM_EINVAL;
     crm_terrain::Adjoint &A = t->adj;
@@ -2284,8 +2285,22 @@ int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l
         CRM_CUDA(t, cudaStreamSynchronize(t->st));
     }
     CRM_CUDA(t, cudaMemsetAsync(A.gpar, 0, kNumGradAcc * sizeof(double), t->st));
-    if (t->nFtot > 0)
-        CRM_CUDA(t, cudaMemsetAsync(A.l_ins, 0, (size_t)kNumAdj * t->nFtot * sizeof(float), t->st));
+    const int64_t nF = t->nFtot;
+    if (nF > 0) {
+        // the objective's terms on the final SPH state (insertion order, component-major)
+        std::vector<float> l((size_t)kNumAdj * nF, 0.0f);
+        for (int64_t i = 0; i < nF; ++i) {
+            for (int k = 0; k < 3; ++k) {
+                if (l_xyz) l[(size_t)(kAdjX + k) * nF + i] = (float)l_xyz[3 * i + k];
+                if (l_vel) l[(size_t)(kAdjU + k) * nF + i] = (float)l_vel[3 * i + k];
+            }
+            if (l_stress)
+                for (int k = 0; k < 6; ++k) l[(size_t)(kAdjS + k) * nF + i] = (float)l_stress[6 * i + k];
+            if (l_rho) l[(size_t)kAdjR * nF + i] = (float)l_rho[i];
+        }
+        CRM_CUDA(t, cudaMemcpyAsync(A.l_ins, l.data(), l.size() * sizeof(float), cudaMemcpyHostToDevice, t->st));
+        CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    }
     size_t sb = 0;
     crm_state_bytes(t, &sb);
     const int64_t n_seg = (n + A.every - 1) / A.every;

@@ -179,7 +179,9 @@ def test_rate_vjp_rejects_active_domains():
 N_RUN, EVERY = 4, 3
 
 
-def _oracle_run_J(sc, lw, lc, dt, params=None, x=None, u=None, sig=None, rho=None, bodies=None):
+def _oracle_run_J(sc, lw, lc, dt, params=None, x=None, u=None, sig=None, rho=None, bodies=None,
+                  lfin=None, n_steps=None):
+    """J = sum_s lw_s . wrench_s + lc_s . centre_s + lfin . final SPH state (oracle)."""
     s2 = sc.copy()
     if params is not None:
         s2.params = params
@@ -190,10 +192,21 @@ def _oracle_run_J(sc, lw, lc, dt, params=None, x=None, u=None, sig=None, rho=Non
     if bodies is not None:
         st.bodies = bodies
     J = 0.0
-    for s in range(lw.shape[0]):
+    n = lw.shape[0] if n_steps is None else n_steps
+    for s in range(n):
         st.step(dt, "brute" if sc.x.shape[0] < 4000 else "cells")
-        J += float(np.sum(lw[s, 0] * st.bodies.wrench[0]) + np.sum(lc[s, 0] * st.bodies.pose[0, :3]))
+        if lw is not None and len(sc.bodies):
+            J += float(np.sum(lw[s, 0] * st.bodies.wrench[0]) + np.sum(lc[s, 0] * st.bodies.pose[0, :3]))
+    if lfin is not None:
+        J += float(np.sum(lfin["x"] * st.x) + np.sum(lfin["u"] * st.u) + np.sum(lfin["sig"] * st.sig)
+                   + np.sum(lfin["rho"] * st.rho))
     return J
+
+
+def _final_weights(n, seed):
+    rng = np.random.default_rng(seed)
+    return {"x": rng.normal(size=(n, 3)) * 10.0, "u": rng.normal(size=(n, 3)),
+            "sig": rng.normal(size=(n, 6)) * 1e-4, "rho": rng.normal(size=n) * 1e-2}
 
 
 @pytest.fixture(scope="module")
@@ -208,8 +221,9 @@ def run_case():
     lw = rng.normal(size=(N_RUN, 1, 6))
     lw[:, :, 3:] *= 10.0
     lc = rng.normal(size=(N_RUN, 1, 3)) * 1e3
-    g = t.adjoint_backward(lw, lc)
-    return sc, t, dt, w, q, lw, lc, g
+    lf = _final_weights(sc.x.shape[0], 8)
+    g = t.adjoint_backward(lw, lc, lf["x"], lf["u"], lf["sig"], lf["rho"])
+    return sc, t, dt, w, q, lw, lc, g, lf
 
 
 def test_run_forward_matches_plain_steps(run_case):
@@ -226,7 +240,7 @@ def test_run_forward_matches_plain_steps(run_case):
 @pytest.mark.parametrize("name", ["E", "nu", "rho0", "mu_s", "cohesion", "av_gamma", "x", "u",
                                   "sig", "rho", "body_c", "body_v"])
 def test_run_gradient_matches_oracle_differences(run_case, name):
-    sc, t, dt, w, q, lw, lc, g = run_case
+    sc, t, dt, w, q, lw, lc, g, lf = run_case
     rng = np.random.default_rng(11)
     base = oracle.State(sc)
     n = sc.x.shape[0]
@@ -236,8 +250,8 @@ def test_run_gradient_matches_oracle_differences(run_case, name):
         d = rng.normal(size=shape)
         e = {"x": 1e-6 * h, "u": 1e-6, "sig": 1e-2, "rho": 1e-3}[name]
         arr = getattr(base, name)
-        jp = _oracle_run_J(sc, lw, lc, dt, **{name: arr + e * d})
-        jm = _oracle_run_J(sc, lw, lc, dt, **{name: arr - e * d})
+        jp = _oracle_run_J(sc, lw, lc, dt, lfin=lf, **{name: arr + e * d})
+        jm = _oracle_run_J(sc, lw, lc, dt, lfin=lf, **{name: arr - e * d})
         key = {"x": "xyz", "u": "vel", "sig": "stress", "rho": "rho"}[name]
         terms = g[key].reshape(d.shape) * d
     elif name in ("body_c", "body_v"):
@@ -250,8 +264,8 @@ def test_run_gradient_matches_oracle_differences(run_case, name):
         else:
             bp.twist[0, :3] += e * d
             bm.twist[0, :3] -= e * d
-        jp = _oracle_run_J(sc, lw, lc, dt, bodies=bp)
-        jm = _oracle_run_J(sc, lw, lc, dt, bodies=bm)
+        jp = _oracle_run_J(sc, lw, lc, dt, bodies=bp, lfin=lf)
+        jm = _oracle_run_J(sc, lw, lc, dt, bodies=bm, lfin=lf)
         off = 0 if name == "body_c" else 3
         terms = g["body"][0, off:off + 3] * d
     else:
@@ -261,8 +275,8 @@ def test_run_gradient_matches_oracle_differences(run_case, name):
         pm[name] -= e
         if name == "mu_s":   # a constant friction coefficient: mu_2 follows mu_s
             pp["mu_2"], pm["mu_2"] = pp["mu_s"], pm["mu_s"]
-        jp = _oracle_run_J(sc, lw, lc, dt, params=pp)
-        jm = _oracle_run_J(sc, lw, lc, dt, params=pm)
+        jp = _oracle_run_J(sc, lw, lc, dt, params=pp, lfin=lf)
+        jm = _oracle_run_J(sc, lw, lc, dt, params=pm, lfin=lf)
         terms = np.array([g["param_grads"][name]])
     fd = (jp - jm) / (2 * e)
     ad, scale = float(terms.sum()), float(np.abs(terms).sum())
@@ -294,16 +308,94 @@ def test_autograd_function_matches_the_c_abi(run_case):
     import torch
 
     from paper_2507_05643_b300.autograd import TerrainRun, scene_params
-    sc, t, dt, w, q, lw, lc, g = run_case
+    sc, t, dt, w, q, lw, lc, g, lf = run_case
     params = scene_params(sc).requires_grad_(True)
     state = [torch.tensor(a, dtype=torch.float64, requires_grad=True)
              for a in (sc.x, sc.u, sc.sig, sc.rho)]
-    W, Cc = TerrainRun.apply(params, *state, sc, N_RUN, EVERY)
+    W, Cc, xT, uT, sT, rT = TerrainRun.apply(params, *state, sc, N_RUN, EVERY)
     np.testing.assert_array_equal(W.detach().numpy(), w)
-    J = (W * torch.from_numpy(lw)).sum() + (Cc * torch.from_numpy(lc)).sum()
+    J = ((W * torch.from_numpy(lw)).sum() + (Cc * torch.from_numpy(lc)).sum()
+         + (xT * torch.from_numpy(lf["x"])).sum() + (uT * torch.from_numpy(lf["u"])).sum()
+         + (sT * torch.from_numpy(lf["sig"])).sum() + (rT * torch.from_numpy(lf["rho"])).sum())
     J.backward()
     # the same sweep; FP64 atomics order the parameter and body sums freely
     np.testing.assert_allclose(params.grad.numpy(), g["params"], rtol=1e-6)
     for a, key in zip(state, ("xyz", "vel", "stress", "rho")):
         np.testing.assert_allclose(a.grad.numpy(), g[key], rtol=1e-4,
                                    atol=1e-6 * np.abs(g[key]).max())
+
+
+# ---------------------------------------------------------------------------
+# Variants of the rate evaluation: Wendland kernel, bilateral and no viscosity
+
+
+@pytest.mark.parametrize("variant", ["wendland", "bilateral", "no_av"])
+def test_rate_vjp_variants_match_oracle_differences(variant):
+    sc = _wheel(seed=51, nx=20, ny=14, nz=7)
+    if variant == "wendland":
+        sc.params["kernel"] = 1
+    elif variant == "bilateral":
+        sc.params["av_mode"] = 1
+    else:
+        sc.params["av_mode"] = 0
+    t = crm.from_scene(sc)
+    orc = _OracleRates(sc)
+    lam = _lam(sc, "all", seed=3)
+    g = t.eval_rates_vjp(lam["drho"], lam["du"], lam["ds"], lam["macc"])
+    rng = np.random.default_rng(9)
+    j_abs = orc.J_abs(lam)
+    bad = []
+    for name in INPUTS:
+        d, e = _direction(sc, name, rng)
+        fd = (orc.J(lam, **_perturbed(orc, name, d, e)) - orc.J(lam, **_perturbed(orc, name, d, -e))) / (2 * e)
+        terms = _adjoint_terms(g, name, d)
+        ad, scale = float(terms.sum()), float(np.abs(terms).sum())
+        floor = 1e-6 * j_abs / abs(sc.params[name]) if name in sc.params else 0.0
+        if abs(ad - fd) > TOL * scale + floor + 1e-9 * (abs(fd) + 1):
+            bad.append((name, ad, fd, scale))
+    assert not bad, bad
+
+
+def test_run_without_bodies_matches_oracle_differences():
+    """A walled block without bodies, J on the final SPH state only."""
+    sc = scenes.settling_block(seed=61, n=8, box=0.14)
+    rng = np.random.default_rng(61)
+    sc.u = rng.uniform(-0.05, 0.05, size=sc.u.shape)
+    sc.sig = np.zeros_like(sc.sig)
+    sc.sig[:, :3] = -rng.uniform(500.0, 2000.0, size=(sc.x.shape[0], 3))
+    sc.sig[:, 3:] = rng.uniform(-100.0, 100.0, size=(sc.x.shape[0], 3))
+    sc.params["skin"] = 0.0
+    sc.params["cohesion"] = 200.0
+    n_steps = 3
+    t = crm.from_scene(sc)
+    t.adjoint_forward(sc.dt, n_steps, 2)
+    lf = _final_weights(sc.x.shape[0], 62)
+    g = t.adjoint_backward(None, None, lf["x"], lf["u"], lf["sig"], lf["rho"])
+    assert g["body"].shape == (0, 9)
+    h = sc.params["h"]
+    bad = []
+    for name in ("x", "u", "sig", "rho", "E", "rho0", "mu_s", "cohesion"):
+        if name in ("x", "u", "sig", "rho"):
+            shape = {"x": (-1, 3), "u": (-1, 3), "sig": (-1, 6), "rho": (-1,)}[name]
+            arr = getattr(sc, name)
+            d = rng.normal(size=arr.shape)
+            e = {"x": 1e-6 * h, "u": 1e-6, "sig": 1e-2, "rho": 1e-3}[name]
+            jp = _oracle_run_J(sc, None, None, sc.dt, lfin=lf, n_steps=n_steps, **{name: arr + e * d})
+            jm = _oracle_run_J(sc, None, None, sc.dt, lfin=lf, n_steps=n_steps, **{name: arr - e * d})
+            key = {"x": "xyz", "u": "vel", "sig": "stress", "rho": "rho"}[name]
+            terms = g[key].reshape(d.shape) * d
+        else:
+            e = 1e-6 * abs(sc.params[name])
+            pp, pm = dict(sc.params), dict(sc.params)
+            pp[name] += e
+            pm[name] -= e
+            if name == "mu_s":
+                pp["mu_2"], pm["mu_2"] = pp["mu_s"], pm["mu_s"]
+            jp = _oracle_run_J(sc, None, None, sc.dt, params=pp, lfin=lf, n_steps=n_steps)
+            jm = _oracle_run_J(sc, None, None, sc.dt, params=pm, lfin=lf, n_steps=n_steps)
+            terms = np.array([g["param_grads"][name]])
+        fd = (jp - jm) / (2 * e)
+        ad, scale = float(terms.sum()), float(np.abs(terms).sum())
+        if abs(ad - fd) > RUN_TOL * max(scale, abs(fd)) + 1e-9:
+            bad.append((name, ad, fd, scale))
+    assert not bad, bad
