@@ -188,96 +188,146 @@ __device__ __forceinline__ PState load_state(const StageArrays &S, int s)
     return PState{S.vel[s], S.sA[s], S.sB[s]};
 }
 
-// Backward of one pair (target i, neighbour j, r = x_i - x_j, 0 < |r| < 2h):
-// adds the i-side input adjoints to *ai, the j-side ones to *aj (either may be
-// null), and, with `par`, the pair's parameter terms (m through V_j, the
-// viscosity constant) to *par.  rho_i of a marker target is rho0.
-__device__ __forceinline__ void pair_vjp(const DevParams &p, const Coef &C, float rx, float ry,
-                                         float rz, float r2, const PState &I, float rho_i,
-                                         const PState &J, Adj *ai, Adj *aj, ParAcc *par)
+// Both directed pairs of the unordered pair {i, j}, seen from i (r = x_i - x_j,
+// 0 < |r| < 2h): OWN, the pair with target i (coefficients Ci, i's own sums);
+// OTHER, the pair with target j that reads i as its neighbour (coefficients Cj;
+// in it r' = -r, g' = -g, u' = -u, V' = m / rho_i, and the viscosity factor is
+// the same).  Adds both pairs' adjoints of i's inputs to `a` and the OWN pair's
+// parameter terms to `par`.  Densities are the states' (a marker's is rho0).
+// The two share the kernel, its derivative, the stress sum and the viscosity
+// factor, which is why they are evaluated together.
+template <bool OWN, bool OTHER>
+__device__ __forceinline__ void pair_vjp_both(const DevParams &p, const Coef &Ci, const Coef &Cj,
+                                              float rx, float ry, float rz, float r2,
+                                              const PState &I, const PState &J, Adj &a,
+                                              ParAcc &par)
 {
     const float rinv = rsqrtf(r2);
     const float q = r2 * rinv * p.inv_h;
     const float F = kernel_dw_over_r(q, rinv, p);
+    const float dFr = kernel_dF_dr(q, rinv, p) * rinv;
     const float g[3] = {F * rx, F * ry, F * rz};
-    const float rho_j = J.v.w;
-    const float Vj = p.m / rho_j;
+    const float r[3] = {rx, ry, rz};
+    const float rho_i = I.v.w, rho_j = J.v.w;
     const float u[3] = {J.v.x - I.v.x, J.v.y - I.v.y, J.v.z - I.v.z};
-    // (sigma_i + sigma_j), symmetric
     const float Sxx = I.a.x + J.a.x, Syy = I.a.y + J.a.y, Szz = I.a.z + J.a.z;
     const float Sxy = I.a.w + J.a.w, Sxz = I.b.x + J.b.x, Syz = I.b.y + J.b.y;
     const float Sg[3] = {Sxx * g[0] + Sxy * g[1] + Sxz * g[2], Sxy * g[0] + Syy * g[1] + Syz * g[2],
                          Sxz * g[0] + Syz * g[1] + Szz * g[2]};
-    const float SlM[3] = {Sxx * C.lM[0] + Sxy * C.lM[1] + Sxz * C.lM[2],
-                          Sxy * C.lM[0] + Syy * C.lM[1] + Syz * C.lM[2],
-                          Sxz * C.lM[0] + Syz * C.lM[1] + Szz * C.lM[2]};
-    float Lg[3], LTu[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        Lg[a] = C.lL[3 * a] * g[0] + C.lL[3 * a + 1] * g[1] + C.lL[3 * a + 2] * g[2];
-        LTu[a] = C.lL[a] * u[0] + C.lL[3 + a] * u[1] + C.lL[6 + a] * u[2];
-    }
-    float gb[3], ub[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        gb[k] = Vj * (C.lc * u[k] + SlM[k] + LTu[k]);
-        ub[k] = Vj * (C.lc * g[k] + Lg[k]);
-    }
-    const float Vb = C.lc * (u[0] * g[0] + u[1] * g[1] + u[2] * g[2])
-                     + C.lM[0] * Sg[0] + C.lM[1] * Sg[1] + C.lM[2] * Sg[2]
-                     + u[0] * Lg[0] + u[1] * Lg[1] + u[2] * Lg[2];
-    // both stresses: V_j sym(lM (x) g), off-diagonals counted twice
-    const float sb[6] = {Vj * C.lM[0] * g[0], Vj * C.lM[1] * g[1], Vj * C.lM[2] * g[2],
-                         Vj * (C.lM[0] * g[1] + C.lM[1] * g[0]),
-                         Vj * (C.lM[0] * g[2] + C.lM[2] * g[0]),
-                         Vj * (C.lM[1] * g[2] + C.lM[2] * g[1])};
-    float rb[3] = {0.f, 0.f, 0.f};
-    float rsum_b = 0.f;
+    const float ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+    // viscosity: vr = -u.r for both directions, rho_i + rho_j, r^2 + xi^2
+    bool av = false;
+    float vr = 0.f, inv = 0.f, fac = 0.f;
+    const float rs = rho_i + rho_j, d2 = r2 + p.xi2;
     if (p.av_mode != CRM_AV_NONE) {
-        const float vr = -(u[0] * rx + u[1] * ry + u[2] * rz);
-        if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-            const float rs = rho_i + rho_j, d2 = r2 + p.xi2;
-            const float inv = 1.0f / (rs * d2);
-            const float fac = 2.0f * p.av_c * vr * inv;
+        vr = -(u[0] * rx + u[1] * ry + u[2] * rz);
+        av = p.av_mode == CRM_AV_BILATERAL || vr < 0.0f;
+        if (av) {
+            inv = 1.0f / (rs * d2);
+            fac = 2.0f * p.av_c * vr * inv;
+        }
+    }
+    if (OWN) {
+        const Coef &C = Ci;
+        const float V = p.m / rho_j;
+        float Lg[3], LTu[3], SlM[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Lg[k] = C.lL[3 * k] * g[0] + C.lL[3 * k + 1] * g[1] + C.lL[3 * k + 2] * g[2];
+            LTu[k] = C.lL[k] * u[0] + C.lL[3 + k] * u[1] + C.lL[6 + k] * u[2];
+        }
+        SlM[0] = Sxx * C.lM[0] + Sxy * C.lM[1] + Sxz * C.lM[2];
+        SlM[1] = Sxy * C.lM[0] + Syy * C.lM[1] + Syz * C.lM[2];
+        SlM[2] = Sxz * C.lM[0] + Syz * C.lM[1] + Szz * C.lM[2];
+        const float Vb = C.lc * ug + C.lM[0] * Sg[0] + C.lM[1] * Sg[1] + C.lM[2] * Sg[2]
+                         + u[0] * Lg[0] + u[1] * Lg[1] + u[2] * Lg[2];
+        float gb[3], ub[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gb[k] = V * (C.lc * u[k] + SlM[k] + LTu[k]);
+            ub[k] = V * (C.lc * g[k] + Lg[k]);
+        }
+        float rb[3] = {0.f, 0.f, 0.f};
+        if (av) {
             const float fb = C.lA[0] * g[0] + C.lA[1] * g[1] + C.lA[2] * g[2];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gb[k] += fac * C.lA[k];
             const float vrb = 2.0f * p.av_c * fb * inv;
-            rsum_b = -fb * fac / rs;
             const float r2b = -fb * fac / d2;
-            if (par) par->v[kGradAvc] += (double)(2.0f * vr * fb * inv);
-            ub[0] -= vrb * rx; ub[1] -= vrb * ry; ub[2] -= vrb * rz;
-            rb[0] += 2.0f * r2b * rx - vrb * u[0];
-            rb[1] += 2.0f * r2b * ry - vrb * u[1];
-            rb[2] += 2.0f * r2b * rz - vrb * u[2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gb[k] += fac * C.lA[k];
+                ub[k] -= vrb * r[k];
+                rb[k] = 2.0f * r2b * r[k] - vrb * u[k];
+            }
+            a.rho += -fb * fac / rs;
+            par.v[kGradAvc] += (double)(2.0f * vr * fb * inv);
         }
-    }
-    // g = F(|r|) r
-    const float dF = kernel_dF_dr(q, rinv, p);
-    const float rg = (rx * gb[0] + ry * gb[1] + rz * gb[2]) * dF * rinv;
-    rb[0] += F * gb[0] + rg * rx;
-    rb[1] += F * gb[1] + rg * ry;
-    rb[2] += F * gb[2] + rg * rz;
-    if (par) par->v[kGradM] += (double)(Vb / rho_j);
-    if (ai) {
+        const float rg = (rx * gb[0] + ry * gb[1] + rz * gb[2]) * dFr;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            ai->x[k] += rb[k];
-            ai->u[k] -= ub[k];
+            a.x[k] += rb[k] + F * gb[k] + rg * r[k];
+            a.u[k] -= ub[k];
         }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) ai->s[k] += sb[k];
-        ai->rho += rsum_b;
+        a.s[0] += V * C.lM[0] * g[0];
+        a.s[1] += V * C.lM[1] * g[1];
+        a.s[2] += V * C.lM[2] * g[2];
+        a.s[3] += V * (C.lM[0] * g[1] + C.lM[1] * g[0]);
+        a.s[4] += V * (C.lM[0] * g[2] + C.lM[2] * g[0]);
+        a.s[5] += V * (C.lM[1] * g[2] + C.lM[2] * g[1]);
+        par.v[kGradM] += (double)(Vb / rho_j);
     }
-    if (aj) {
+    if (OTHER) {
+        // target j, neighbour i: in j's frame r' = -r, g' = -g, u' = -u, V' = m / rho_i
+        const Coef &C = Cj;
+        const float V = p.m / rho_i;
+        float Lg[3], LTu[3], SlM[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            aj->x[k] -= rb[k];
-            aj->u[k] += ub[k];
+            Lg[k] = C.lL[3 * k] * g[0] + C.lL[3 * k + 1] * g[1] + C.lL[3 * k + 2] * g[2];
+            LTu[k] = C.lL[k] * u[0] + C.lL[3 + k] * u[1] + C.lL[6 + k] * u[2];
         }
+        SlM[0] = Sxx * C.lM[0] + Sxy * C.lM[1] + Sxz * C.lM[2];
+        SlM[1] = Sxy * C.lM[0] + Syy * C.lM[1] + Syz * C.lM[2];
+        SlM[2] = Sxz * C.lM[0] + Syz * C.lM[1] + Szz * C.lM[2];
+        // u'.g' = u.g, S g' = -S g, u'.(lL g') = u.(lL g)
+        const float Vb = C.lc * ug - (C.lM[0] * Sg[0] + C.lM[1] * Sg[1] + C.lM[2] * Sg[2])
+                         + u[0] * Lg[0] + u[1] * Lg[1] + u[2] * Lg[2];
+        // gb' = V (lc u' + S lM + lL^T u') + fac lA,  ub' = V (lc g' + lL g') - vrb' r'
+        float gb[3], ub[3];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) aj->s[k] += sb[k];
-        aj->rho += rsum_b - Vj / rho_j * Vb;
+        for (int k = 0; k < 3; ++k) {
+            gb[k] = V * (-C.lc * u[k] + SlM[k] - LTu[k]);
+            ub[k] = -V * (C.lc * g[k] + Lg[k]);
+        }
+        // rb' (adjoint of r') = F gb' + (r'.gb') dF/|r| r' + 2 r2b' r' - vrb' u', and
+        // x_i enters r' with a minus sign
+        float rb[3] = {0.f, 0.f, 0.f};
+        float rsum = 0.f;
+        if (av) {
+            const float fb = -(C.lA[0] * g[0] + C.lA[1] * g[1] + C.lA[2] * g[2]);   // lA . g'
+            const float vrb = 2.0f * p.av_c * fb * inv;
+            const float r2b = -fb * fac / d2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gb[k] += fac * C.lA[k];
+                ub[k] += vrb * r[k];                   // -vrb' r' = +vrb' r
+                rb[k] = -2.0f * r2b * r[k] + vrb * u[k];
+            }
+            rsum = -fb * fac / rs;
+        }
+        const float rg = (rx * gb[0] + ry * gb[1] + rz * gb[2]) * dFr;   // (r'.gb') r' = (r.gb') r
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a.x[k] -= rb[k] + F * gb[k] + rg * r[k];
+            a.u[k] += ub[k];
+        }
+        // sym(lM (x) g') = -sym(lM (x) g)
+        a.s[0] -= V * C.lM[0] * g[0];
+        a.s[1] -= V * C.lM[1] * g[1];
+        a.s[2] -= V * C.lM[2] * g[2];
+        a.s[3] -= V * (C.lM[0] * g[1] + C.lM[1] * g[0]);
+        a.s[4] -= V * (C.lM[0] * g[2] + C.lM[2] * g[0]);
+        a.s[5] -= V * (C.lM[1] * g[2] + C.lM[2] * g[1]);
+        a.rho += rsum - V / rho_i * Vb;
     }
 }
 
@@ -730,11 +780,10 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
         const float rw = Fs.v.w * W;
         sr[0] += rw * rx; sr[1] += rw * ry; sr[2] += rw * rz;
         if (r2 == 0.0f) continue;
-        // the fluid particle's pair that reads this marker (r_fa = -r)
+        // the marker's own acceleration pair (ACC) and the fluid particle's pair
+        // that reads this marker
         const Coef Cf = load_coef(io.coef, (int)f);
-        pair_vjp(p, Cf, -rx, -ry, -rz, r2, Fs, Fs.v.w, A0, nullptr, &la, nullptr);
-        // the marker's own acceleration pair
-        if (ACC) pair_vjp(p, Ca, rx, ry, rz, r2, A0, p.rho0, Fs, &la, nullptr, &par);
+        pair_vjp_both<ACC, true>(p, Ca, Cf, rx, ry, rz, r2, A0, Fs, la, par);
     }
     w = lane_sum<LANES>(w);
 #pragma unroll
@@ -875,13 +924,13 @@ k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, dou
             const PState J = load_state(S, j);
             const bool marker = (int)j >= z.nF;
             if (r2 != 0.0f) {
-                // own pair (i target)
-                pair_vjp(p, Ci, rx, ry, rz, r2, I, I.v.w, J, &a, nullptr, &par);
-                // the neighbour's pair that reads i (j target, r_ji = -r)
+                // own pair (i target) and the neighbour's pair that reads i (j
+                // target; a marker's only with acceleration adjoints)
                 if (!marker || ACC) {
                     const Coef Cj = load_coef(io.coef, (int)j);
-                    pair_vjp(p, Cj, -rx, -ry, -rz, r2, J, marker ? p.rho0 : J.v.w, I, nullptr, &a,
-                             nullptr);
+                    pair_vjp_both<true, true>(p, Ci, Cj, rx, ry, rz, r2, I, J, a, par);
+                } else {
+                    pair_vjp_both<true, false>(p, Ci, Ci, rx, ry, rz, r2, I, J, a, par);
                 }
             }
             if (marker) {
