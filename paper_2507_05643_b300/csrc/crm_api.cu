@@ -126,6 +126,8 @@ struct crm_terrain {
         uint32_t *pid, *nbr, *nnb;   // slot order and lists of the step
         BodyDev *bodies;             // bodies before the step
         BodyFrame *frames;           // bodies at the step midpoint
+        cudaGraphExec_t rec[2];      // the recording step as a graph, per current buffer
+        double rec_dt;
     };
     struct Adjoint {
         bool ready = false;
@@ -327,13 +329,26 @@ int latched_error(crm_terrain *t)
     return t->fail(CRM_ETIMEOUT, "a bounded device-side wait gave up");
 }
 
+// Free the adjoint's tape (and the recording graphs that point into it).
+void drop_tape(crm_terrain *t)
+{
+    for (crm_terrain::AdjTape &T : t->adj.tape)
+        for (cudaGraphExec_t &g : T.rec)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    t->adj.tape.clear();
+    t->free_group(G_TAPE);
+}
+
 // Working-set arrays for capF fluid + capM marker slots.
 int alloc_working(crm_terrain *t)
 {
     t->drop_graphs();   // graphs bake in the array pointers
     t->free_group(G_WORK);
-    t->free_group(G_ADJ);      // the sweep's workspace follows the working set
-    t->free_group(G_TAPE);
+    drop_tape(t);              // the sweep's workspace follows the working set
+    t->free_group(G_ADJ);
     t->adj = crm_terrain::Adjoint{};
     DevParams &d = t->dp;
     const int64_t N = t->capF + t->capM;
@@ -1271,6 +1286,7 @@ int crm_destroy(crm_terrain *t)
         cudaEventDestroy(t->ev_fork);
         cudaEventDestroy(t->ev_join);
     }
+    drop_tape(t);
     for (int g = 0; g < G_COUNT; ++g) t->free_group(g);
     if (t->h_counts) cudaFreeHost(t->h_counts);
     delete t;
@@ -2033,9 +2049,10 @@ int adj_export(crm_terrain *t, const double *lb_dev, double *g_xyz, double *g_ve
     return CRM_OK;
 }
 
-// One step of the run with direct launches, the step's stage arrays, lists and
-// bodies copied to the tape (the same kernels as the graph of a search step).
-int record_step(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
+// The device work of one recorded step: the step's kernels (those of the graph
+// of a search step) with its stage arrays, lists and bodies copied to the tape.
+// Flips t->cur as a rebuild does.
+int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
 {
     const DevParams &d = t->dp;
     const size_t N = (size_t)std::max(d.capN, 1), nb = t->hbodies.size();
@@ -2064,6 +2081,54 @@ int record_step(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
     if (d.capM > 0 && d.n_bodies > 0) bce(t, t->MID, 0.5 * dt, 1, dt, 1);
     pair(t, kStage2, t->MID, t->A[c], (float)dt, none);
     CRM_CUDA(t, copy_stage(T.YM, t->MID));
+    return CRM_OK;
+}
+
+// One step of the run recorded to tape slot T: a graph per slot and current
+// buffer, captured at its first use and replayed for every later segment (the
+// tape and working arrays it points into stay put), else direct launches.
+int record_step(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
+{
+    const int par = t->cur;
+    cudaGraphExec_t &G = T.rec[par];
+    if (G && T.rec_dt != dt) {
+        cudaGraphExecDestroy(G);
+        G = nullptr;
+    }
+    if (!G && t->graphs && t->cap_st && !t->timing) {
+        cudaStream_t user = t->st;
+        const crm_profile saved = t->prof;
+        const bool lv = t->lists_valid;
+        t->st = t->cap_st;
+        cudaGraph_t g = nullptr;
+        int rc = CRM_OK;
+        cudaError_t e = cudaStreamBeginCapture(t->st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = enqueue_record(t, dt, T);
+            e = cudaStreamEndCapture(t->st, &g);
+        }
+        t->cur = par;
+        t->st = user;
+        t->prof = saved;
+        t->lists_valid = lv;
+        if (e == cudaSuccess && rc == CRM_OK) e = cudaGraphInstantiate(&G, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || rc != CRM_OK) {
+            cudaGetLastError();
+            G = nullptr;
+            t->msg.clear();
+        }
+        T.rec_dt = dt;
+    }
+    if (G) {
+        CRM_CUDA(t, cudaGraphLaunch(G, t->st));
+        t->cur = 1 - t->cur;        // the replayed rebuild's buffer swap
+        t->lists_valid = true;
+        t->prof.rebuilds += 1;
+    } else {
+        int rc = enqueue_record(t, dt, T);
+        if (rc) return rc;
+    }
     t->step_index += 1;
     t->time += dt;
     CRM_CUDA(t, cudaGetLastError());
@@ -2194,8 +2259,7 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
     rc = adj_workspace(t);
     if (rc) return rc;
     crm_terrain::Adjoint &A = t->adj;
-    t->free_group(G_TAPE);
-    A.tape.clear();
+    drop_tape(t);
     A.n_steps = 0;
     const DevParams &d = t->dp;
     const size_t nb = t->hbodies.size();
@@ -2223,12 +2287,13 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
         T.nnb = t->dalloc<uint32_t>(G_TAPE, N);
         T.bodies = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1));
         T.frames = t->dalloc<BodyFrame>(G_TAPE, std::max<size_t>(nb, 1));
+        T.rec[0] = T.rec[1] = nullptr;
+        T.rec_dt = 0.0;
         A.tape.push_back(T);
     }
     if (t->oom) {
         t->oom = false;
-        t->free_group(G_TAPE);
-        A.tape.clear();
+        drop_tape(t);
         return t->fail(CRM_ENOMEM, "crm_adjoint_forward: device allocation of the checkpoints and tape failed");
     }
     A.dt = dt;
