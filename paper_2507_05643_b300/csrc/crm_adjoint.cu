@@ -15,13 +15,13 @@
 //   u_a = u_b, sigma_a = 0.
 //
 // The sweep is in gather form -- every thread owns the adjoints it writes, no
-// float atomics on particle data -- in four passes per stage:
+// float atomics on particle data -- in three passes per stage:
 //   fluid coefficients  adjoints of (cont, M, L, A) of every fluid target and the
 //                       local terms (Jaumann, 1/rho_i, the return map, the
 //                       integrator's identity parts);
-//   marker coefficients adjoints of (M, A) of every marker target (the rate
-//                       evaluation's marker accelerations, or a step's body wrench);
-//   marker gather       per marker: the adjoint of its BCE state (from the fluid
+//   marker gather       per marker: the adjoints of (M, A) of its acceleration
+//                       (the rate evaluation's marker accelerations, or a step's
+//                       body wrench), the adjoint of its BCE state (from the fluid
 //                       pairs that read it and its own acceleration pairs), the
 //                       BCE coefficients (w, su, ss, sr), the terms of its own
 //                       position, summed per body (FP64);
@@ -633,109 +633,10 @@ __device__ __forceinline__ int marker_body_kin(const DevParams &p, const AdjStag
     return b;
 }
 
-// Pass 2: marker coefficients.  The adjoint of a marker's acceleration
-// a = M / rho0 + A comes from l_macc (insertion order, the rate evaluation)
-// or, in a step, from the body wrench: force m a and torque arm x m a give
-// l_a = m (l_F + l_T x arm), plus the direct term of m.  Markers without an
-// adjoint get zero coefficients.
-template <int MODE>
-__global__ void __launch_bounds__(kAdjBlock)
-k_adj_marker_coef(DevParams p, AdjStage V, AdjIO io, double *gpar)
-{
-    __shared__ float4 lut[64];
-    fill_shift_table(lut, p.cell);
-    __syncthreads();
-    const Sizes z = load_sizes(p);
-    const int s = z.nF + blockIdx.x * blockDim.x + threadIdx.x;
-    ParAcc par;
-    par_zero(par);
-    if (s < z.N) {
-        float la[3] = {0.f, 0.f, 0.f};
-        bool direct_m = false;
-        if (MODE == kAdjEval) {
-            if (io.l_macc != nullptr) {
-                const size_t mi = (size_t)pid_index(V.pid[s]) - (size_t)V.n_fluid_total;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) la[k] = io.l_macc[3 * mi + k];
-            }
-        } else {
-            float ub[3], ab[3], arm[3];
-            const int b = marker_body_kin(p, V, s, ub, ab, arm);
-            if (b >= 0 && V.nnb[s] > 0) {
-                const double *w = io.l_wrench + 6 * b;
-                const float lF[3] = {(float)w[0], (float)w[1], (float)w[2]};
-                const float lT[3] = {(float)w[3], (float)w[4], (float)w[5]};
-                // (arm x f) . lT = f . (lT x arm)
-                const float lf[3] = {lF[0] + lT[1] * arm[2] - lT[2] * arm[1],
-                                     lF[1] + lT[2] * arm[0] - lT[0] * arm[2],
-                                     lF[2] + lT[0] * arm[1] - lT[1] * arm[0]};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) la[k] = p.m * lf[k];
-                direct_m = true;
-            }
-        }
-        Coef C;
-        C.lc = 0.f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) C.lL[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            C.lM[k] = la[k] / p.rho0;
-            C.lA[k] = la[k];
-        }
-        store_coef(io.coef, s, C);
-        if (la[0] != 0.f || la[1] != 0.f || la[2] != 0.f) {
-            // M and A again, for the terms of 1 / rho0 and of m in m a
-            const StageArrays &S = V.S;
-            const float4 pa = S.pos[s];
-            const PState A0 = load_state(S, s);
-            float M[3] = {0.f, 0.f, 0.f}, A[3] = {0.f, 0.f, 0.f};
-            const int nn = (int)V.nnb[s];
-            for (int k = 0; k < nn; ++k) {
-                const uint32_t e = V.nbr[(size_t)k * p.ell + s];
-                const uint32_t j = e & kIndexMask;
-                const float4 sh = lut[e >> kIndexBits];
-                const float4 pj = S.pos[j];
-                const float rx = pa.x - pj.x - sh.x, ry = pa.y - pj.y - sh.y, rz = pa.z - pj.z - sh.z;
-                const float r2 = rx * rx + ry * ry + rz * rz;
-                if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
-                const PState J = load_state(S, j);
-                const float rinv = rsqrtf(r2);
-                const float F = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
-                const float g[3] = {F * rx, F * ry, F * rz};
-                const float Vj = p.m / J.v.w;
-                const float Sxx = A0.a.x + J.a.x, Syy = A0.a.y + J.a.y, Szz = A0.a.z + J.a.z;
-                const float Sxy = A0.a.w + J.a.w, Sxz = A0.b.x + J.b.x, Syz = A0.b.y + J.b.y;
-                M[0] += Vj * (Sxx * g[0] + Sxy * g[1] + Sxz * g[2]);
-                M[1] += Vj * (Sxy * g[0] + Syy * g[1] + Syz * g[2]);
-                M[2] += Vj * (Sxz * g[0] + Syz * g[1] + Szz * g[2]);
-                if (p.av_mode != CRM_AV_NONE) {
-                    const float vr = (A0.v.x - J.v.x) * rx + (A0.v.y - J.v.y) * ry + (A0.v.z - J.v.z) * rz;
-                    if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-                        const float fac = 2.0f * p.av_c * vr / ((p.rho0 + J.v.w) * (r2 + p.xi2));
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) A[c] += fac * g[c];
-                    }
-                }
-            }
-            const double ir = 1.0 / (double)p.rho0;
-            double drho0 = 0.0, dm = 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                drho0 -= (double)la[k] * (double)M[k] * ir * ir;
-                dm += (double)la[k] * ((double)M[k] * ir + (double)A[k]);
-            }
-            par.v[kGradRho0] += drho0;
-            if (direct_m) par.v[kGradM] += dm / (double)p.m;
-        }
-    }
-    par_flush(par, gpar);
-}
-
-// Pass 3: marker gather.  ACC: the markers' own acceleration pairs carry
-// adjoints (coefficients from pass 2).  Writes the BCE coefficients of every
-// marker slot and adds the body adjoints (centre, velocity, acceleration) to
-// gbody [body][9].
+// Pass 2: marker gather.  ACC: the markers' own acceleration pairs carry
+// adjoints (their coefficients are formed here and stored for pass 3).  Writes
+// the BCE coefficients of every marker slot and adds the body adjoints (centre,
+// velocity, acceleration) to gbody [body][9].
 template <bool ACC, int LANES>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
@@ -757,12 +658,42 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
     const float4 pa = nn > 0 ? S.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
     PState A0{};
     if (nn > 0) A0 = load_state(S, s);
+    // ACC: the adjoint of the marker's acceleration a = M / rho0 + A -- from
+    // l_macc (the rate evaluation) or from its body's wrench (a step: force m a,
+    // torque arm x m a, so l_a = m (l_F + l_T x arm) plus the direct term of m) --
+    // and its pair-sum coefficients, stored for the fluid gather
     Coef Ca{};
-    if (ACC && nn > 0) Ca = load_coef(io.coef, s);
+    float la3[3] = {0.f, 0.f, 0.f};
+    bool direct_m = false;
+    if (ACC && nn > 0) {
+        if (io.l_macc != nullptr) {
+            const size_t mi = (size_t)pid_index(V.pid[s]) - (size_t)V.n_fluid_total;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) la3[k] = io.l_macc[3 * mi + k];
+        } else if (body >= 0) {
+            const double *wr = io.l_wrench + 6 * body;
+            const float lF[3] = {(float)wr[0], (float)wr[1], (float)wr[2]};
+            const float lT[3] = {(float)wr[3], (float)wr[4], (float)wr[5]};
+            // (arm x f) . lT = f . (lT x arm)
+            const float lf[3] = {lF[0] + lT[1] * arm[2] - lT[2] * arm[1],
+                                 lF[1] + lT[2] * arm[0] - lT[0] * arm[2],
+                                 lF[2] + lT[0] * arm[1] - lT[1] * arm[0]};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) la3[k] = p.m * lf[k];
+            direct_m = true;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Ca.lM[k] = la3[k] / p.rho0;
+            Ca.lA[k] = la3[k];
+        }
+        if (q == 0) store_coef(io.coef, s, Ca);
+    }
     Adj la;
     adj_zero(la);
     float w = 0.f, su[3] = {0.f, 0.f, 0.f}, ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float sr[3] = {0.f, 0.f, 0.f};
+    float Ms[3] = {0.f, 0.f, 0.f}, As[3] = {0.f, 0.f, 0.f};   // the acceleration's sums (ACC)
     for (int k = q; k < nn; k += LANES) {
         const uint32_t e = V.nbr[(size_t)k * p.ell + s];
         const uint32_t f = e & kIndexMask;
@@ -780,10 +711,48 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
         const float rw = Fs.v.w * W;
         sr[0] += rw * rx; sr[1] += rw * ry; sr[2] += rw * rz;
         if (r2 == 0.0f) continue;
+        if (ACC) {
+            // M and A of the forward, for the terms of 1 / rho0 and of m in m a
+            const float rinv = rsqrtf(r2);
+            const float F = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
+            const float g[3] = {F * rx, F * ry, F * rz};
+            const float Vf = p.m / Fs.v.w;
+            const float Sxx = A0.a.x + Fs.a.x, Syy = A0.a.y + Fs.a.y, Szz = A0.a.z + Fs.a.z;
+            const float Sxy = A0.a.w + Fs.a.w, Sxz = A0.b.x + Fs.b.x, Syz = A0.b.y + Fs.b.y;
+            Ms[0] += Vf * (Sxx * g[0] + Sxy * g[1] + Sxz * g[2]);
+            Ms[1] += Vf * (Sxy * g[0] + Syy * g[1] + Syz * g[2]);
+            Ms[2] += Vf * (Sxz * g[0] + Syz * g[1] + Szz * g[2]);
+            if (p.av_mode != CRM_AV_NONE) {
+                const float vr = (A0.v.x - Fs.v.x) * rx + (A0.v.y - Fs.v.y) * ry + (A0.v.z - Fs.v.z) * rz;
+                if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
+                    const float fac = 2.0f * p.av_c * vr / ((p.rho0 + Fs.v.w) * (r2 + p.xi2));
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) As[c] += fac * g[c];
+                }
+            }
+        }
         // the marker's own acceleration pair (ACC) and the fluid particle's pair
         // that reads this marker
         const Coef Cf = load_coef(io.coef, (int)f);
         pair_vjp_both<ACC, true>(p, Ca, Cf, rx, ry, rz, r2, A0, Fs, la, par);
+    }
+    if (ACC) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Ms[k] = lane_sum<LANES>(Ms[k]);
+            As[k] = lane_sum<LANES>(As[k]);
+        }
+        if (q == 0 && (la3[0] != 0.f || la3[1] != 0.f || la3[2] != 0.f)) {
+            const double ir = 1.0 / (double)p.rho0;
+            double drho0 = 0.0, dm = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                drho0 -= (double)la3[k] * (double)Ms[k] * ir * ir;
+                dm += (double)la3[k] * ((double)Ms[k] * ir + (double)As[k]);
+            }
+            par.v[kGradRho0] += drho0;
+            if (direct_m) par.v[kGradM] += dm / (double)p.m;
+        }
     }
     w = lane_sum<LANES>(w);
 #pragma unroll
@@ -888,7 +857,7 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
     }
 }
 
-// Pass 4: fluid gather.  ACC: the markers in the list carry acceleration
+// Pass 3: fluid gather.  ACC: the markers in the list carry acceleration
 // coefficients.  OUT kAdjAccumulate: the sums are added to l_acc (slot order);
 // kAdjFinal: l_acc (slot order) plus the sums is written to l_final at the
 // particle's insertion index.
@@ -1043,15 +1012,6 @@ void launch_adj_fluid_coef(int mode, const DevParams &p, const AdjStage &V, Stag
         k_adj_fluid_coef<kAdjStage2, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
     else
         k_adj_fluid_coef<kAdjStage1, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
-}
-
-void launch_adj_marker_coef(int mode, const DevParams &p, const AdjStage &V, const AdjIO &io,
-                            double *gpar, cudaStream_t st)
-{
-    if (p.capM == 0) return;
-    const unsigned g = grid_for(p.capM, kAdjBlock);
-    if (mode == kAdjEval) k_adj_marker_coef<kAdjEval><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar);
-    else k_adj_marker_coef<kAdjStage2><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar);
 }
 
 void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const AdjIO &io,

@@ -50,8 +50,6 @@ struct AdjIO {
 
 void launch_adj_fluid_coef(int mode, const DevParams &p, const AdjStage &V, StageArrays Y0,
                            const AdjIO &io, double *gpar, cudaStream_t st);
-void launch_adj_marker_coef(int mode, const DevParams &p, const AdjStage &V, const AdjIO &io,
-                            double *gpar, cudaStream_t st);
 void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const AdjIO &io,
                        double *gpar, double *gbody, cudaStream_t st);
 void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, const AdjIO &io,

@@ -2158,7 +2158,6 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     // stage 2 (at y_mid, with the wrench's marker accelerations)
     launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjStage2, d, Vm, T.Y0, io, A.gpar, t->st); });
     const bool acc = nb > 0 && d.capM > 0;
-    if (acc) launch(t, K_ADJ, [&] { launch_adj_marker_coef(kAdjStage2, d, Vm, io, A.gpar, t->st); });
     launch(t, K_ADJ, [&] { launch_adj_marker(acc, d, Vm, io, A.gpar, gm, t->st); });
     launch(t, K_ADJ, [&] { launch_adj_fluid(acc, kAdjAccumulate, d, Vm, io, A.l_mid, nullptr,
                                             A.gpar, t->st); });
@@ -2235,7 +2234,6 @@ int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, con
     const bool acc = io.l_macc != nullptr;
     if (d.capF > 0) launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjEval, d, V, t->A[c], io, A.gpar, t->st); });
     if (d.capM > 0) {
-        launch(t, K_ADJ, [&] { launch_adj_marker_coef(kAdjEval, d, V, io, A.gpar, t->st); });
         launch(t, K_ADJ, [&] { launch_adj_marker(acc, d, V, io, A.gpar, A.gbody, t->st); });
     }
     if (nF > 0)
