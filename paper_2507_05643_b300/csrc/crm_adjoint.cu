@@ -18,7 +18,8 @@
 // float atomics on particle data -- in three passes per stage:
 //   fluid coefficients  adjoints of (cont, M, L, A) of every fluid target and the
 //                       local terms (Jaumann, 1/rho_i, the return map, the
-//                       integrator's identity parts);
+//                       integrator's identity parts), from the pair sums that the
+//                       forward's pair kernel wrote to the tape;
 //   marker gather       per marker: the adjoints of (M, A) of its acceleration
 //                       (the rate evaluation's marker accelerations, or a step's
 //                       body wrench), the adjoint of its BCE state (from the fluid
@@ -460,67 +461,39 @@ __device__ __forceinline__ void jaumann_vjp(const float L[9], const float s6[6],
 // otherwise leave most of the GPU's warp slots empty).
 constexpr int kAdjLanes = 4;
 
-// Pass 1: fluid coefficients.  MODE kAdjEval: the rates' adjoints come from
+// Pass 1: fluid coefficients, from the pair sums the forward pair kernel wrote
+// (one thread per particle, no list walk).  MODE kAdjEval: the rates' adjoints come from
 // l_rate (insertion order) and the local terms are written to l_out (slot
 // order).  MODE kAdjStage2: the state is y_mid (V.S), y_n is Y0 and the
 // adjoint of y_{n+1} is read from l_next (insertion order); the local terms at
 // y_mid go to l_mid and those at y_n (the integrator's identity parts through
 // the return map) to l_y0.  MODE kAdjStage1: the state is y_n and the adjoint
 // of y_mid is l_mid (complete); everything is added to l_y0.
-template <int MODE, int LANES>
+template <int MODE>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar)
 {
-    __shared__ float4 lut[64];
-    fill_shift_table(lut, p.cell);
-    __syncthreads();
     const Sizes z = load_sizes(p);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / LANES, q = t % LANES;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < z.nF;
     ParAcc par;
     par_zero(par);
     const StageArrays &S = V.S;
+    // the forward's pair sums of this stage (written by the pair kernel)
     float cont = 0.f, M[3] = {0.f, 0.f, 0.f}, L[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) L[k] = 0.f;
     PState I{};
     if (valid) {
-        const float4 pi = S.pos[i];
         I = load_state(S, i);
-        const int nn = (int)V.nnb[i];
-        for (int k = q; k < nn; k += LANES) {
-            const uint32_t e = V.nbr[(size_t)k * p.ell + i];
-            const uint32_t j = e & kIndexMask;
-            const float4 sh = lut[e >> kIndexBits];
-            const float4 pj = S.pos[j];
-            const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
-            const float r2 = rx * rx + ry * ry + rz * rz;
-            if (!(r2 < p.four_h2) || r2 == 0.0f) continue;
-            const PState J = load_state(S, j);
-            const float rinv = rsqrtf(r2);
-            const float F = kernel_dw_over_r(r2 * rinv * p.inv_h, rinv, p);
-            const float g[3] = {F * rx, F * ry, F * rz};
-            const float Vj = p.m / J.v.w;
-            const float u[3] = {J.v.x - I.v.x, J.v.y - I.v.y, J.v.z - I.v.z};
-            cont += Vj * (u[0] * g[0] + u[1] * g[1] + u[2] * g[2]);
-            const float Sxx = I.a.x + J.a.x, Syy = I.a.y + J.a.y, Szz = I.a.z + J.a.z;
-            const float Sxy = I.a.w + J.a.w, Sxz = I.b.x + J.b.x, Syz = I.b.y + J.b.y;
-            M[0] += Vj * (Sxx * g[0] + Sxy * g[1] + Sxz * g[2]);
-            M[1] += Vj * (Sxy * g[0] + Syy * g[1] + Syz * g[2]);
-            M[2] += Vj * (Sxz * g[0] + Syz * g[1] + Szz * g[2]);
+        const size_t cs = (size_t)p.capF;
+        cont = V.sums[i];
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) M[k] = V.sums[(1 + k) * cs + i];
 #pragma unroll
-                for (int b = 0; b < 3; ++b) L[3 * a + b] += Vj * u[a] * g[b];
-        }
+        for (int k = 0; k < 9; ++k) L[k] = V.sums[(4 + k) * cs + i];
     }
-    cont = lane_sum<LANES>(cont);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) M[k] = lane_sum<LANES>(M[k]);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) L[k] = lane_sum<LANES>(L[k]);
-    if (valid && q == 0) {
+    if (valid) {
         const float si[6] = {I.a.x, I.a.y, I.a.z, I.a.w, I.b.x, I.b.y};
         const uint32_t id = pid_index(V.pid[i]);
         const int64_t ns = io.n_fluid;          // stride of the insertion-order arrays
@@ -1004,14 +977,13 @@ __global__ void k_adj_body_post(int nb, double dt, const double *g0, const doubl
 void launch_adj_fluid_coef(int mode, const DevParams &p, const AdjStage &V, StageArrays Y0,
                            const AdjIO &io, double *gpar, cudaStream_t st)
 {
-    constexpr int LN = kAdjLanes;
-    const unsigned g = grid_for((int64_t)p.capF * LN, kAdjBlock);
+    const unsigned g = grid_for(p.capF, kAdjBlock);
     if (mode == kAdjEval)
-        k_adj_fluid_coef<kAdjEval, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+        k_adj_fluid_coef<kAdjEval><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
     else if (mode == kAdjStage2)
-        k_adj_fluid_coef<kAdjStage2, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+        k_adj_fluid_coef<kAdjStage2><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
     else
-        k_adj_fluid_coef<kAdjStage1, LN><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
+        k_adj_fluid_coef<kAdjStage1><<<g, kAdjBlock, 0, st>>>(p, V, Y0, io, gpar);
 }
 
 void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const AdjIO &io,

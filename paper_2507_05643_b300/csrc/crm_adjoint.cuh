@@ -30,6 +30,7 @@ struct AdjStage {
     const BodyDev *bodies;
     const BodyFrame *frames;
     int n_fluid_total;
+    const float *sums;   // the forward's fluid pair sums at this stage, [13][capF]
 };
 
 struct AdjIO {

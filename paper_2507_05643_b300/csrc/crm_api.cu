@@ -126,6 +126,7 @@ struct crm_terrain {
         uint32_t *pid, *nbr, *nnb;   // slot order and lists of the step
         BodyDev *bodies;             // bodies before the step
         BodyFrame *frames;           // bodies at the step midpoint
+        float *sum0, *sumM;          // fluid pair sums of the two stages ([13][capF])
         cudaGraphExec_t rec[2];      // the recording step as a graph, per current buffer
         double rec_dt;
     };
@@ -133,7 +134,7 @@ struct crm_terrain {
         bool ready = false;
         float4 *coef = nullptr, *coefB = nullptr;
         float *l_mid = nullptr, *l_y0 = nullptr, *l_ins = nullptr, *l_rate = nullptr,
-              *l_macc = nullptr;
+              *l_macc = nullptr, *sums = nullptr;
         double *gpar = nullptr, *gbody = nullptr, *lb[2]{}, *lwrench = nullptr;
         // trajectory: checkpoints every `every` steps (plus the final state),
         // the bodies after each step, the objective's adjoints
@@ -1572,7 +1573,7 @@ int crm_eval_rates(crm_terrain *t, int64_t cap_sph, float *drho, float *dvel, fl
     void *buf = nullptr;
     CRM_CUDA(t, cudaMallocAsync(&buf, std::max<size_t>(rate_bytes + out_bytes + 64, 64), t->st));
     char *b = (char *)buf;
-    RateOut r;
+    RateOut r{};
     r.du = (float4 *)b;
     r.dsA = r.du + wF;
     r.dsB = (float2 *)(r.dsA + wF);
@@ -1945,6 +1946,7 @@ int adj_workspace(crm_terrain *t)
     A.l_ins = t->dalloc<float>(G_ADJ, (size_t)kNumAdj * nF);
     A.l_rate = t->dalloc<float>(G_ADJ, 10 * nF);
     A.l_macc = t->dalloc<float>(G_ADJ, 3 * nM);
+    A.sums = t->dalloc<float>(G_ADJ, 13 * (size_t)std::max(d.capF, 1));
     A.gpar = t->dalloc<double>(G_ADJ, kNumGradAcc);
     A.gbody = t->dalloc<double>(G_ADJ, 2 * 9 * nb);
     A.lb[0] = t->dalloc<double>(G_ADJ, 9 * nb);
@@ -2069,9 +2071,11 @@ int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
     if (nb > 0) CRM_CUDA(t, copy(T.bodies, t->bodies, nb * sizeof(BodyDev)));
     rebuild(t);
     const int c = t->cur;
-    RateOut none{};
+    RateOut r1{}, r2{};
+    r1.sums = T.sum0;
+    r2.sums = T.sumM;
     bce(t, t->A[c], 0.0, 0, dt, 0, false);
-    pair(t, kStage1, t->A[c], t->A[c], (float)dt, none);
+    pair(t, kStage1, t->A[c], t->A[c], (float)dt, r1);
     CRM_CUDA(t, copy_stage(T.Y0, t->A[c]));
     CRM_CUDA(t, copy(T.pid, t->pid[c], N * sizeof(uint32_t)));
     CRM_CUDA(t, copy(T.nbr, t->nbr, (size_t)d.maxnb * d.ell * sizeof(uint32_t)));
@@ -2079,7 +2083,7 @@ int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
     if (nb > 0) CRM_CUDA(t, copy(T.frames, t->mid_frames, nb * sizeof(BodyFrame)));
     bce(t, t->MID, 0.5 * dt, 0);
     if (d.capM > 0 && d.n_bodies > 0) bce(t, t->MID, 0.5 * dt, 1, dt, 1);
-    pair(t, kStage2, t->MID, t->A[c], (float)dt, none);
+    pair(t, kStage2, t->MID, t->A[c], (float)dt, r2);
     CRM_CUDA(t, copy_stage(T.YM, t->MID));
     return CRM_OK;
 }
@@ -2144,8 +2148,10 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     crm_terrain::Adjoint &A = t->adj;
     const int nb = (int)t->hbodies.size();
     const double dt = A.dt;
-    const AdjStage Vm{T.YM, T.nbr, T.nnb, T.pid, t->mloc, T.bodies, T.frames, (int)t->nFtot};
-    const AdjStage V0{T.Y0, T.nbr, T.nnb, T.pid, t->mloc, T.bodies, nullptr, (int)t->nFtot};
+    const AdjStage Vm{T.YM, T.nbr, T.nnb, T.pid, t->mloc, T.bodies, T.frames, (int)t->nFtot,
+                      T.sumM};
+    const AdjStage V0{T.Y0, T.nbr, T.nnb, T.pid, t->mloc, T.bodies, nullptr, (int)t->nFtot,
+                      T.sum0};
     const AdjIO io = adj_io(t, (float)dt);
     double *g0 = A.gbody, *gm = A.gbody + 9 * std::max(nb, 1);
     const double *lw = A.lw_obj ? A.lw_obj + (size_t)s * nb * 6 : nullptr;
@@ -2211,11 +2217,12 @@ int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, con
     const size_t wF = (size_t)std::max(d.capF, 1);
     void *buf = nullptr;
     CRM_CUDA(t, cudaMallocAsync(&buf, wF * (sizeof(float) + 2 * sizeof(float4) + sizeof(float2)) + 64, t->st));
-    RateOut r;
+    RateOut r{};
     r.du = (float4 *)buf;
     r.dsA = r.du + wF;
     r.dsB = (float2 *)(r.dsA + wF);
     r.drho = (float *)(r.dsB + wF);
+    r.sums = A.sums;
     if (t->skin_on) {
         bce(t, t->A[c], 0.0, 0, 0.0, 0, true);
         pair(t, kEval, t->A[c], t->A[c], 0.0f, r, true);
@@ -2228,7 +2235,8 @@ int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, con
     const size_t nb = t->hbodies.size();
     CRM_CUDA(t, cudaMemsetAsync(A.gpar, 0, kNumGradAcc * sizeof(double), t->st));
     CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 9 * std::max<size_t>(nb, 1) * sizeof(double), t->st));
-    const AdjStage V{t->A[c], t->nbr, t->nnb, t->pid[c], t->mloc, t->bodies, nullptr, (int)nF};
+    const AdjStage V{t->A[c], t->nbr, t->nnb, t->pid[c], t->mloc, t->bodies, nullptr, (int)nF,
+                     A.sums};
     AdjIO io = adj_io(t, 0.0f);
     io.l_macc = (l_macc && nM > 0) ? A.l_macc : nullptr;
     const bool acc = io.l_macc != nullptr;
@@ -2285,6 +2293,8 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
         T.nnb = t->dalloc<uint32_t>(G_TAPE, N);
         T.bodies = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1));
         T.frames = t->dalloc<BodyFrame>(G_TAPE, std::max<size_t>(nb, 1));
+        T.sum0 = t->dalloc<float>(G_TAPE, 13 * (size_t)std::max(d.capF, 1));
+        T.sumM = t->dalloc<float>(G_TAPE, 13 * (size_t)std::max(d.capF, 1));
         T.rec[0] = T.rec[1] = nullptr;
         T.rec_dt = 0.0;
         A.tape.push_back(T);

@@ -368,6 +368,8 @@ struct RateOut {
     float4 *du;     // [slot] (x, y, z, 0)
     float4 *dsA;    // [slot] xx, yy, zz, xy
     float2 *dsB;    // [slot] xz, yz
+    float *sums;    // nullable, any mode: each fluid particle's pair sums (continuity,
+                    // M (3), L (9)), component-major [13][capF] (for the adjoint's tape)
 };
 
 enum { kStage1 = 0, kStage2 = 1, kEval = 2 };

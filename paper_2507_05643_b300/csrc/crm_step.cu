@@ -263,6 +263,15 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
         if (cnt > p.maxnb) atomicOr(err, ERR_CAPACITY);
         io.out_n[i] = (uint32_t)min(cnt, p.maxnb);
     }
+    if (out.sums != nullptr) {
+        const size_t cs = (size_t)p.capF;
+        out.sums[i] = A.cont;
+        out.sums[cs + i] = A.mx;
+        out.sums[2 * cs + i] = A.my;
+        out.sums[3 * cs + i] = A.mz;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) out.sums[(4 + k) * cs + i] = A.L[k];
+    }
     const float rinv_i = 1.0f / vi.w;
     const float drho = -vi.w * A.cont;
     const float dux = A.mx * rinv_i + p.gx + A.avx;
