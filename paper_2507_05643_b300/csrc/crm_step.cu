@@ -194,20 +194,15 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
             const float4 pj = __ldg(&S.pos[j]);
             float4 vj, aj;
             float2 bj;
-            if (!FILTER) {
-                vj = __ldg(&S.vel[j]);
-                aj = __ldg(&S.sA[j]);
-                bj = __ldg(&S.sB[j]);
-            }
+            vj = __ldg(&S.vel[j]);
+            aj = __ldg(&S.sA[j]);
+            bj = __ldg(&S.sB[j]);
             const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
             const float r2 = rx * rx + ry * ry + rz * rz;
             if (!(r2 < p.four_h2)) continue;
             if (FILTER) {
                 if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
                 ++cnt;
-                vj = __ldg(&S.vel[j]);
-                aj = __ldg(&S.sA[j]);
-                bj = __ldg(&S.sB[j]);
             }
             if (r2 == 0.0f) continue;
             pair_terms(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
