@@ -569,6 +569,13 @@ def run_crm(args):
                                          for k in per},
             "cell_searches": launches["launches"]["neighbors"],
             "pair_stage2_fp32_frac": pair_fp32,
+            # the pair kernels against the other roof: DRAM bytes per launch (ncu,
+            # profiles/traffic.txt) over the event-timed launch
+            "pair_hbm": {k: {"traffic": _traffic(k), "ms_per_launch": per[k],
+                             "achieved_gbs": _traffic(k) / (per[k] * 1e-3) / 1e9,
+                             "frac": _traffic(k) / (per[k] * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+                         for k in ("pair_stage1", "pair_stage2")
+                         if per.get(k) and _traffic(k)},
             "roofline": roof,
             "clocks": clocks,
         }
