@@ -46,6 +46,7 @@ WORKLOAD = ("wheel_bin: 120,000 SPH particles, 2.0x0.4x0.15 m bin at d0=0.01 m, 
 FLOP_PER_PAIR = 99
 FLOP_PER_PARTICLE = 100
 SM_FP32_LANES = 128
+BODY_BYTES = 352   # one body's device record, copied out by the exchange
 
 
 def _peaks():
@@ -490,25 +491,21 @@ def run_crm(args):
     all_pairs = int(off[-1])
 
     # end to end through the public API: per step the co-simulation exchange of
-    # Sec. 2.4 -- body pose/twist host->device, step, wrench + body state
-    # device->host (pinned host buffers, synchronous read of the result)
+    # Sec. 2.4 -- the bodies' pose/twist host->device, step, wrench + body state
+    # device->host, one synchronous call (crm_cosim_step, pinned staging)
     pose, twist = t.body_state(0)
-    hbuf = torch.empty(13, dtype=torch.float64, pin_memory=True)
-    hbuf[:7] = torch.from_numpy(pose)
-    hbuf[7:] = torch.from_numpy(twist)
+    nb = t.n_bodies
+    hpose = np.tile(pose, (nb, 1))
+    htwist = np.tile(twist, (nb, 1))
+    for b in range(nb):
+        hpose[b], htwist[b] = t.body_state(b)
     e2e_steps = max(args.steps, 1)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     w0 = time.perf_counter()
     for _ in range(e2e_steps):
-        hb = hbuf.numpy()
-        t.set_body_motion(0, hb[:7], hb[7:])
-        t.step(dt, 1)
-        F, T = t.body_wrench(0)
-        p, tw = t.body_state(0)
-        hbuf[:7] = torch.from_numpy(p)
-        hbuf[7:] = torch.from_numpy(tw)
+        W, hpose, htwist = t.cosim_step(dt, 1, hpose, htwist)
     e2e_s = time.perf_counter() - w0
     t.sync()
 
@@ -560,8 +557,9 @@ def run_crm(args):
                        "n_bce": n_bce, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write outside the events)"},
             "e2e": {"value": units * e2e_steps / args.steps / e2e_max, "unit": UNIT,
-                    "h2d_bytes_per_step": 13 * 8, "d2h_bytes_per_step": 6 * 8 + 13 * 8 + 4,
-                    "loop": "set_body_motion -> step -> body_wrench + body_state (sync)"},
+                    "h2d_bytes_per_step": 13 * 8 * nb, "d2h_bytes_per_step": BODY_BYTES * nb + 4,
+                    "loop": "crm_cosim_step: bodies' pose/twist in, one step, every body's "
+                            "state and wrench out, one synchronisation per step"},
             "gpu_launches": sum(launches["launches"].values()),
             "kernels_us_per_step": {k: 1e3 * prof["ms"][k] / max(prof["steps"], 1)
                                     for k in per},

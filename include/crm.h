@@ -203,6 +203,17 @@ int crm_get_body_wrench(crm_terrain *t, int32_t body, double force[3], double to
  * last step (without active boxes every SPH particle is active). */
 int crm_get_counts(crm_terrain *t, int64_t *n_active, int64_t *n_extended, int64_t *n_bce);
 
+/* One co-simulation exchange with a multibody code (the FSI loop of Sec.
+ * 2.4): set every body's motion from pose_in (n_bodies*7) and twist_in
+ * (n_bodies*6) -- both or neither (nullptr: keep the current motion) -- then
+ * advance n_steps steps of dt (0: none), then return every body's soil wrench
+ * (wrench_out, n_bodies*6, as crm_get_body_wrench), pose and twist (each
+ * nullable), with a single synchronisation (the transfers go through pinned
+ * staging kept with the terrain).  Errors as crm_set_body_motion, crm_step
+ * and crm_sync. */
+int crm_cosim_step(crm_terrain *t, const double *pose_in, const double *twist_in, double dt,
+                   int32_t n_steps, double *wrench_out, double *pose_out, double *twist_out);
+
 /* Evaluate the rates f(y) at the current state without advancing it (the
  * first RK2 stage: rebuilds the lists, extrapolates the BCE state and sums the
  * pairs).  Outputs in insertion order, each nullable: drho (n_sph),

@@ -100,6 +100,7 @@ _sig("crm_get_body_wrench", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_get_counts", C.c_int, [_T, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)])
 _sig("crm_eval_rates", C.c_int, [_T, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp])
 _sig("crm_get_neighbors", C.c_int, [_T, _i64, _vp, _vp, C.POINTER(_i64)])
+_sig("crm_cosim_step", C.c_int, [_T, _vp, _vp, C.c_double, _i32, _vp, _vp, _vp])
 _sig("crm_eval_rates_vjp", C.c_int, [_T, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp])
 _sig("crm_adjoint_forward", C.c_int, [_T, C.c_double, _i64, _i32, _vp, _vp])
@@ -134,7 +135,7 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
            "crm_profile_reset", "crm_profile_read", "crm_bin_points_noalloc",
-           "crm_capacity_policy", "crm_eval_rates_vjp", "crm_adjoint_forward",
+           "crm_capacity_policy", "crm_cosim_step", "crm_eval_rates_vjp", "crm_adjoint_forward",
            "crm_adjoint_backward")
 
 
@@ -290,6 +291,18 @@ class Terrain:
         self._check(_lib.crm_get_particles(self._h, n, _ptr(xyz), _ptr(vel), _ptr(sig), _ptr(rho),
                                            C.byref(nout)))
         return xyz, vel, sig, rho
+
+    def cosim_step(self, dt: float, n_steps: int = 1, pose=None, twist=None):
+        """One co-simulation exchange: optionally set every body's motion (pose
+        (n_bodies, 7), twist (n_bodies, 6)), step, and return (wrench
+        (n_bodies, 6), pose, twist) with one synchronisation."""
+        nb = self.n_bodies
+        pin = None if pose is None else np.ascontiguousarray(np.asarray(pose, np.float64).reshape(nb, 7))
+        tin = None if twist is None else np.ascontiguousarray(np.asarray(twist, np.float64).reshape(nb, 6))
+        w, q, v = np.zeros((max(nb, 1), 6)), np.zeros((max(nb, 1), 7)), np.zeros((max(nb, 1), 6))
+        self._check(_lib.crm_cosim_step(self._h, _ptr(pin), _ptr(tin), float(dt), int(n_steps),
+                                        _ptr(w), _ptr(q), _ptr(v)))
+        return w[:nb], q[:nb], v[:nb]
 
     def body_wrench(self, body: int) -> Tuple[np.ndarray, np.ndarray]:
         f, t = np.zeros(3), np.zeros(3)

@@ -105,6 +105,8 @@ struct crm_terrain {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int *err = nullptr, *counts = nullptr, *win = nullptr, *abort_flag = nullptr;
     int *h_counts = nullptr;      // pinned mirror: counters + abort word
+    BodyDev *h_xbodies = nullptr; // pinned staging of the co-simulation exchange: the
+                                  // bodies, then one int (the error word)
     // active domains: master store and candidates
     StageArrays Mst{};
     uint32_t *mpid = nullptr, *mslot_of_pid = nullptr;
@@ -1290,6 +1292,7 @@ int crm_destroy(crm_terrain *t)
     drop_tape(t);
     for (int g = 0; g < G_COUNT; ++g) t->free_group(g);
     if (t->h_counts) cudaFreeHost(t->h_counts);
+    if (t->h_xbodies) cudaFreeHost(t->h_xbodies);
     delete t;
     return CRM_OK;
 }
@@ -1364,9 +1367,12 @@ int crm_add_rigid_body(crm_terrain *t, int64_t n, const double *xloc, const doub
     return CRM_OK;
 }
 
-int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7], const double twist[6])
+}  // extern "C"
+
+namespace {
+// The host copy of a body's motion, checked and with the quaternion normalised.
+int set_motion_host(crm_terrain *t, int32_t body, const double pose[7], const double twist[6])
 {
-    if (!t) return CRM_EINVAL;
     if (body < 0 || body >= (int)t->hbodies.size() || !pose || !twist)
         return t->fail(CRM_EINVAL, "crm_set_body_motion: bad body or null array");
     if (!finite_all(pose, 7) || !finite_all(twist, 6)) return t->fail(CRM_EINVAL, "non-finite motion");
@@ -1376,6 +1382,18 @@ int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7], cons
     for (int k = 0; k < 3; ++k) b.pose[k] = pose[k];
     for (int k = 3; k < 7; ++k) b.pose[k] = pose[k] / qn;
     for (int k = 0; k < 6; ++k) b.twist[k] = twist[k];
+    return CRM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int crm_set_body_motion(crm_terrain *t, int32_t body, const double pose[7], const double twist[6])
+{
+    if (!t) return CRM_EINVAL;
+    const int rc = set_motion_host(t, body, pose, twist);
+    if (rc) return rc;
+    BodyDev &b = t->hbodies[body];
     if (t->committed)
         CRM_CUDA(t, cudaMemcpyAsync(&t->bodies[body], &b, 13 * sizeof(double),
                                     cudaMemcpyHostToDevice, t->st));
@@ -1512,6 +1530,56 @@ int crm_get_particles(crm_terrain *t, int64_t cap, double *xyz, float *vel, floa
     cudaFreeAsync(buf, t->st);
     if (rc) return rc;
     return latched_error(t);
+}
+
+int crm_cosim_step(crm_terrain *t, const double *pose_in, const double *twist_in, double dt,
+                   int32_t n_steps, double *wrench_out, double *pose_out, double *twist_out)
+{
+    if (!t) return CRM_EINVAL;
+    const int nb = (int)t->hbodies.size();
+    if ((pose_in == nullptr) != (twist_in == nullptr))
+        return t->fail(CRM_EINVAL, "crm_cosim_step: give both pose and twist, or neither");
+    if (pose_in) {
+        for (int b = 0; b < nb; ++b) {
+            const int rc = set_motion_host(t, b, pose_in + 7 * b, twist_in + 6 * b);
+            if (rc) return rc;
+        }
+    }
+    int rc = commit(t);
+    if (rc) return rc;
+    if (!t->h_xbodies) {
+        void *h = nullptr;
+        if (cudaMallocHost(&h, std::max(nb, 1) * sizeof(BodyDev) + sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return t->fail(CRM_ENOMEM, "crm_cosim_step: pinned staging allocation failed");
+        }
+        t->h_xbodies = (BodyDev *)h;
+    }
+    int *h_err = (int *)(t->h_xbodies + std::max(nb, 1));
+    if (pose_in) {
+        // the new motions through pinned memory: truly asynchronous uploads
+        for (int b = 0; b < nb; ++b) {
+            std::memcpy(t->h_xbodies[b].pose, t->hbodies[b].pose, 13 * sizeof(double));
+            CRM_CUDA(t, cudaMemcpyAsync(&t->bodies[b], &t->h_xbodies[b], 13 * sizeof(double),
+                                        cudaMemcpyHostToDevice, t->st));
+        }
+    }
+    if (n_steps > 0) {
+        rc = crm_step(t, dt, n_steps);
+        if (rc) return rc;
+    }
+    if (nb > 0)
+        CRM_CUDA(t, cudaMemcpyAsync(t->h_xbodies, t->bodies, nb * sizeof(BodyDev), cudaMemcpyDeviceToHost, t->st));
+    CRM_CUDA(t, cudaMemcpyAsync(h_err, t->err, sizeof(int), cudaMemcpyDeviceToHost, t->st));
+    CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    if (*h_err != 0) return latched_error(t);
+    for (int b = 0; b < nb; ++b) {
+        t->hbodies[b] = t->h_xbodies[b];
+        if (wrench_out) std::memcpy(wrench_out + 6 * b, t->h_xbodies[b].wrench, 6 * sizeof(double));
+        if (pose_out) std::memcpy(pose_out + 7 * b, t->h_xbodies[b].pose, 7 * sizeof(double));
+        if (twist_out) std::memcpy(twist_out + 6 * b, t->h_xbodies[b].twist, 6 * sizeof(double));
+    }
+    return CRM_OK;
 }
 
 int crm_get_body_wrench(crm_terrain *t, int32_t body, double force[3], double torque[3])

@@ -366,3 +366,27 @@ def test_ragged_sizes_match_oracle_rates():
         # particle has no neighbours, where S = 0)
         tol = RATE_TOL * scale + 2 * np.finfo(np.float32).eps * np.abs(ref) + 1e-30
         assert np.all(np.abs(got - ref) <= tol), n
+
+
+def test_cosim_exchange_equals_the_separate_calls():
+    """crm_cosim_step (motion in, steps, wrench and state out, one synchronisation)
+    gives bitwise what set_body_motion + step + body_wrench + body_state give."""
+    sc = scenes.wheel_bin(seed=93, nx=30, ny=20, nz=8, wheel_radius=0.07, wheel_width=0.07,
+                          n_grousers=8, wheel_x=0.15)
+    t1, t2 = crm.from_scene(sc), crm.from_scene(sc)
+    dt = sc.dt
+    for k in range(4):
+        pose, twist = t1.body_state(0)
+        twist = twist.copy()
+        twist[0] += 0.01 * k           # a new prescribed forward speed each exchange
+        t1.set_body_motion(0, pose, twist)
+        t1.step(dt, 3)
+        f, tq = t1.body_wrench(0)
+        p1, v1 = t1.body_state(0)
+        W, P, V = t2.cosim_step(dt, 3, pose[None], twist[None])
+        np.testing.assert_array_equal(W[0], np.concatenate([f, tq]))
+        np.testing.assert_array_equal(P[0], p1)
+        np.testing.assert_array_equal(V[0], v1)
+    # no motion given and no steps: the state as it stands
+    W, P, V = t2.cosim_step(dt, 0)
+    np.testing.assert_array_equal(P[0], t1.body_state(0)[0])
