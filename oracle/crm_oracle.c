@@ -483,7 +483,7 @@ static double kernel_dw_condition(const orc_params *p, double r)
  * Markers use their extrapolated velocity and stress (orc_bce).
  * `scale` (nullable; 10 per fluid particle: rho, u x3, sigma x6) receives the
  * absolute sums sum_j |term_ij| of each component, the size against which a
- * single-precision evaluation is judged; `mscale` (nullable; 3 per marker) the
+ * single-precision evaluation is measured; `mscale` (nullable; 3 per marker) the
  * same for the marker accelerations. */
 void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
                const double *xf, const double *uf, const double *sf, const double *rf,

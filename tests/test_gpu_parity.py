@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Bars (the method's single-precision reading of the benchmark spec's tolerances):
+Bars (the single-precision reading of the parity tolerances):
 * integer work (cells, sort order, cell ranges) is bit-exact; neighbour sets are
   exact except pairs whose FP64 distance lies within 1e-6 h of the 2h cut-off
   (an FP32 evaluation may decide those either way);
