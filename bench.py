@@ -134,9 +134,22 @@ def cpu_baseline(budget_s: float = 15.0) -> dict:
         n += 1
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # the same oracle on one thread, a shorter sample continuing the same run
+    prev = oracle.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        n1 = 0
+        while n1 < 1 or time.perf_counter() - t1 < budget_s / 3:
+            st.step()
+            n1 += 1
+        el1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(prev)
     return {"value": sc.n_fluid * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"wheel_bin workload, first {n} whole steps ({el:.1f} s, FP64, OpenMP), "
-                      f"cpu={_cpu_model()}"}
+                      f"cpu={_cpu_model()}",
+            "single_thread": {"value": sc.n_fluid * n1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"the next {n1} whole steps ({el1:.1f} s)"}}
 
 
 def _cpu_model() -> str:

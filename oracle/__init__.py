@@ -97,6 +97,15 @@ def lib():
     return _lib
 
 
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's loops (its OpenMP runtime's setting);
+    returns the previous maximum."""
+    L = lib()
+    prev = int(L.omp_get_max_threads())
+    L.omp_set_num_threads(C.c_int(int(n)))
+    return prev
+
+
 def _c(a, dt=np.float64):
     return np.ascontiguousarray(a, dtype=dt)
 
