@@ -92,8 +92,9 @@ typedef struct crm_params {
     double shrink_ratio;   /* shrink threshold S (Sec. 3.2), in (0, 1] */
     int32_t shrink_interval; /* shrink check interval S_I in steps (Sec. 3.2), >= 1 */
     int32_t pair_lanes;    /* lanes per fluid particle in the pair kernels on exact lists:
-                              1, 2, or 0 = the library default (2); a pure speed knob
-                              (crm_batch_autotune picks it per terrain) */
+                              1, 2, 4, or 0 = the library default (4 while four threads
+                              per particle fit the GPU's resident threads, else 2); a
+                              pure speed knob (crm_batch_autotune picks it per terrain) */
     double skin;           /* Verlet skin as a fraction of 2h, in [0, 1): with skin > 0
                               the cell sort and the 27-cell search run with radius
                               2h (1 + skin) only when some particle has moved skin * h
@@ -318,7 +319,7 @@ int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l
 int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
                         double shrink_ratio, int32_t shrink_interval, int64_t *new_cap);
 
-/* Lanes per fluid particle in the exact-list pair kernels (1 or 2; 0 = the
+/* Lanes per fluid particle in the exact-list pair kernels (1, 2 or 4; 0 = the
  * default): a speed knob with no effect on the method (the sums of a particle
  * are split between the lanes and combined, so only their order changes). */
 int crm_set_pair_lanes(crm_terrain *t, int32_t lanes);

@@ -227,7 +227,8 @@ int validate(const crm_params *p, std::string &why)
             return bad("domain_max must exceed domain_min on every axis");
     if (!(p->growth >= 1.0) || !(p->shrink_ratio > 0 && p->shrink_ratio <= 1.0) || p->shrink_interval < 1)
         return bad("growth >= 1, shrink_ratio in (0, 1], shrink_interval >= 1");
-    if (p->pair_lanes < 0 || p->pair_lanes > 2) return bad("pair_lanes must be 0, 1 or 2");
+    if (p->pair_lanes < 0 || p->pair_lanes > 4 || p->pair_lanes == 3)
+        return bad("pair_lanes must be 0, 1, 2 or 4");
     if (!(p->skin >= 0.0 && p->skin < 1.0)) return bad("skin must lie in [0, 1)");
     return CRM_OK;
 }
@@ -1709,7 +1710,8 @@ int crm_get_neighbors(crm_terrain *t, int64_t cap, int64_t *offset, int32_t *lis
 int crm_set_pair_lanes(crm_terrain *t, int32_t lanes)
 {
     if (!t) return CRM_EINVAL;
-    if (lanes < 0 || lanes > 2) return t->fail(CRM_EINVAL, "crm_set_pair_lanes: 0, 1 or 2");
+    if (lanes < 0 || lanes > 4 || lanes == 3)
+        return t->fail(CRM_EINVAL, "crm_set_pair_lanes: 0, 1, 2 or 4");
     t->P.pair_lanes = lanes;
     t->dp.pair_lanes = lanes;
     t->drop_graphs();   // the captured launches hold the old choice
@@ -1801,7 +1803,7 @@ int crm_batch_autotune(crm_batch *b, const double *dt, int32_t trial_steps, int3
         crm_terrain *t = b->m[i];
         float best = 0.f;
         int pick = 2;
-        for (int lanes = 1; lanes <= 2 && rc == CRM_OK; ++lanes) {
+        for (int lanes = 1; lanes <= 4 && rc == CRM_OK; lanes *= 2) {
             crm_set_pair_lanes(t, lanes);
             rc = crm_step(t, dt[i], 1);   // capture the graphs outside the timing
             if (rc) break;

@@ -132,7 +132,7 @@ __device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi,
     }
 }
 
-// LANES lanes share particle i: each walks every LANES-th entry of its list and
+// LANES (1, 2 or 4) lanes share particle i: each walks every LANES-th entry of its list and
 // the sums are combined by shuffles (more warps in flight for the gathers of a
 // grid that would otherwise fill each SM only partly).  FILTER (stage 1 with a
 // skin): the list walked is the skin list, and the pairs closer than 2h at y_n
@@ -389,8 +389,11 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
 {
     // filtering kernels keep one lane per particle (the lane group's ballot per
     // candidate costs more than the extra warps gain); the others take
-    // p.pair_lanes (1 or 2; 0 = kPairLanes), a per-terrain tuning knob
-    const int LN = p.pair_lanes == 1 ? 1 : (p.pair_lanes == 2 ? 2 : kPairLanes);
+    // p.pair_lanes (1, 2 or 4), a per-terrain tuning knob; by default four lanes
+    // while four threads per particle still fit the GPU's resident threads (a
+    // small working set otherwise leaves most warp slots empty), else kPairLanes
+    const int LN = p.pair_lanes != 0 ? p.pair_lanes
+                                     : ((int64_t)p.capF * 4 <= 148LL * 2048 ? 4 : kPairLanes);
     const unsigned g = grid_for((int64_t)p.capF * LN, kPairBlock);
     const unsigned g1 = grid_for(p.capF, kPairBlock);
     if (mode == kStage1 && sk_nbr != nullptr) {
@@ -415,6 +418,18 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
                                                                 err, xref, gate);
         else
             k_pair<kEval, false, 1><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                              err, nullptr, nullptr);
+        return;
+    }
+    if (LN == 4) {
+        if (mode == kStage1)
+            k_pair<kStage1, false, 4><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                                err, nullptr, nullptr);
+        else if (mode == kStage2)
+            k_pair<kStage2, false, 4><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
+                                                                err, xref, gate);
+        else
+            k_pair<kEval, false, 4><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
                                                               err, nullptr, nullptr);
         return;
     }

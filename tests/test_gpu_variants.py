@@ -276,16 +276,15 @@ def test_batch_steps_equal_members_stepped_alone():
     dts = [sc.dt for sc in bins]
     batch = crm.Batch(mem, stream=torch.cuda.current_stream())
     picks = batch.autotune(dts, trial_steps=2)
-    assert set(picks.tolist()) <= {1, 2}
+    assert set(picks.tolist()) <= {1, 2, 4}
     batch.step(dts, 20)
     torch.cuda.synchronize()
     # the same bins alone, with the same lane picks and the same number of steps
     for sc, pick, m in zip(bins, picks, mem):
         alone = crm.from_scene(sc, stream=torch.cuda.Stream())
-        alone.set_pair_lanes(1)
-        alone.step(sc.dt, 3)       # autotune ran 3 steps with 1 lane, then 3 with 2
-        alone.set_pair_lanes(2)
-        alone.step(sc.dt, 3)
+        for lanes in (1, 2, 4):    # autotune ran 3 steps with each choice
+            alone.set_pair_lanes(lanes)
+            alone.step(sc.dt, 3)
         alone.set_pair_lanes(int(pick))
         alone.step(sc.dt, 20)
         xa, va, sa, ra = alone.particles()
