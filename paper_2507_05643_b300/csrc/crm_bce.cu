@@ -45,6 +45,73 @@ __device__ __forceinline__ float group_sum(float v)
     return v;
 }
 
+// The end-of-step update of body b from its summed soil wrench W (Sec. 2.4):
+// symplectic Euler on the free DOFs with the soil wrench plus the external load,
+// v += dt (F/m + g), w += dt I_w^-1 (T - w x I_w w) (I_w = R diag(I) R^T at t_n),
+// then x += dt v and the orientation turns by dt w; prescribed DOFs keep their
+// velocity.
+__device__ __forceinline__ void body_update(const DevParams &p, const BodyStep &bs, int b,
+                                            const double W[6])
+{
+    BodyDev &B = bs.bodies[b];
+    for (int k = 0; k < 6; ++k) B.wrench[k] = W[k];
+    if (!bs.integrate) return;
+    double F[3], T[3], wdot[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 3; ++k) {
+        F[k] = W[k] + B.load[k];
+        T[k] = W[3 + k] + B.load[3 + k];
+    }
+    if (B.dof & (7 << 3)) {
+        const double qw = B.pose[3], qx = B.pose[4], qy = B.pose[5], qz = B.pose[6];
+        const double R[3][3] = {
+            {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+        const double *w = B.twist + 3;
+        double L[3], rb[3];
+        for (int r = 0; r < 3; ++r)   // body-frame w, times I
+            rb[r] = B.inertia[r] * (R[0][r] * w[0] + R[1][r] * w[1] + R[2][r] * w[2]);
+        for (int r = 0; r < 3; ++r) L[r] = R[r][0] * rb[0] + R[r][1] * rb[1] + R[r][2] * rb[2];
+        const double rhs[3] = {T[0] - (w[1] * L[2] - w[2] * L[1]), T[1] - (w[2] * L[0] - w[0] * L[2]),
+                               T[2] - (w[0] * L[1] - w[1] * L[0])};
+        for (int r = 0; r < 3; ++r)
+            rb[r] = (R[0][r] * rhs[0] + R[1][r] * rhs[1] + R[2][r] * rhs[2]) / B.inertia[r];
+        for (int r = 0; r < 3; ++r) wdot[r] = R[r][0] * rb[0] + R[r][1] * rb[1] + R[r][2] * rb[2];
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (B.dof & (1 << k)) {
+            const double a = F[k] / B.mass + p.g64[k];
+            B.twist[k] += bs.dt * a;
+            B.acc[k] = a;
+        } else {
+            B.acc[k] = 0.0;
+        }
+        if (B.dof & (8 << k)) {
+            B.twist[3 + k] += bs.dt * wdot[k];
+            B.alpha[k] = wdot[k];
+        } else {
+            B.alpha[k] = 0.0;
+        }
+        B.pose[k] += bs.dt * B.twist[k];
+    }
+    double q[4];
+    qadvance(B.pose + 3, B.twist + 3, bs.dt, q);
+    for (int k = 0; k < 4; ++k) B.pose[3 + k] = q[k];
+    if (bs.gate != nullptr) {
+        // every marker of the body has moved at most |dc| + 2 sin(theta/2) rmax
+        // since the last cell search (theta: rotation since then)
+        double dc2 = 0.0, w = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double d = B.pose[k] - B.ref_pose[k];
+            dc2 += d * d;
+        }
+        for (int k = 0; k < 4; ++k) w += B.pose[3 + k] * B.ref_pose[3 + k];
+        const double sh = sqrt(fmax(0.0, 1.0 - w * w));
+        const double d = sqrt(dc2) + 2.0 * sh * B.rmax;
+        atomicMax(bs.gate + GATE_DISP, __float_as_int((float)(d * d) * 1.0001f));
+    }
+}
+
 // ACCEL == 1 tail of k_bce: FP64 per-block partial wrench of every body, then
 // the last block sums the partials in a fixed order and advances the bodies.
 __device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float f[3],
@@ -88,6 +155,7 @@ __device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    __shared__ double s_w[kMaxBodies][6];
     for (int b = 0; b < nb; ++b) {
         // L2 loads (the partials were published before the ticket): issued
         // together, not one round trip each
@@ -104,77 +172,16 @@ __device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float
 #pragma unroll
             for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double W[6] = {0, 0, 0, 0, 0, 0};
-            for (int w = 0; w < kBlock / 32; ++w)
-                for (int k = 0; k < 6; ++k) W[k] += red[w][k];
-            BodyDev &B = bs.bodies[b];
-            for (int k = 0; k < 6; ++k) B.wrench[k] = W[k];
-            if (bs.integrate) {
-                // symplectic Euler on the free DOFs with the soil wrench plus the
-                // external load: v += dt (F/m + g), w += dt I_w^-1 (T - w x I_w w)
-                // (I_w = R diag(I) R^T at t_n), then x += dt v and the orientation
-                // turns by dt w; prescribed DOFs keep their velocity
-                double F[3], T[3], wdot[3] = {0.0, 0.0, 0.0};
-                for (int k = 0; k < 3; ++k) {
-                    F[k] = W[k] + B.load[k];
-                    T[k] = W[3 + k] + B.load[3 + k];
-                }
-                if (B.dof & (7 << 3)) {
-                    const double qw = B.pose[3], qx = B.pose[4], qy = B.pose[5], qz = B.pose[6];
-                    const double R[3][3] = {
-                        {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
-                        {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
-                        {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
-                    const double *w = B.twist + 3;
-                    double L[3], rb[3];
-                    for (int r = 0; r < 3; ++r) {   // body-frame w, times I
-                        rb[r] = B.inertia[r] * (R[0][r] * w[0] + R[1][r] * w[1] + R[2][r] * w[2]);
-                    }
-                    for (int r = 0; r < 3; ++r) L[r] = R[r][0] * rb[0] + R[r][1] * rb[1] + R[r][2] * rb[2];
-                    const double rhs[3] = {T[0] - (w[1] * L[2] - w[2] * L[1]),
-                                           T[1] - (w[2] * L[0] - w[0] * L[2]),
-                                           T[2] - (w[0] * L[1] - w[1] * L[0])};
-                    for (int r = 0; r < 3; ++r)
-                        rb[r] = (R[0][r] * rhs[0] + R[1][r] * rhs[1] + R[2][r] * rhs[2]) / B.inertia[r];
-                    for (int r = 0; r < 3; ++r) wdot[r] = R[r][0] * rb[0] + R[r][1] * rb[1] + R[r][2] * rb[2];
-                }
-                for (int k = 0; k < 3; ++k) {
-                    if (B.dof & (1 << k)) {
-                        const double a = F[k] / B.mass + p.g64[k];
-                        B.twist[k] += bs.dt * a;
-                        B.acc[k] = a;
-                    } else {
-                        B.acc[k] = 0.0;
-                    }
-                    if (B.dof & (8 << k)) {
-                        B.twist[3 + k] += bs.dt * wdot[k];
-                        B.alpha[k] = wdot[k];
-                    } else {
-                        B.alpha[k] = 0.0;
-                    }
-                    B.pose[k] += bs.dt * B.twist[k];
-                }
-                double q[4];
-                qadvance(B.pose + 3, B.twist + 3, bs.dt, q);
-                for (int k = 0; k < 4; ++k) B.pose[3 + k] = q[k];
-                if (bs.gate != nullptr) {
-                    // every marker of the body has moved at most |dc| + 2 sin(theta/2) rmax
-                    // since the last cell search (theta: rotation since then)
-                    double dc2 = 0.0, w = 0.0;
-                    for (int k = 0; k < 3; ++k) {
-                        const double d = B.pose[k] - B.ref_pose[k];
-                        dc2 += d * d;
-                    }
-                    for (int k = 0; k < 4; ++k) w += B.pose[3 + k] * B.ref_pose[3 + k];
-                    const double sh = sqrt(fmax(0.0, 1.0 - w * w));
-                    const double d = sqrt(dc2) + 2.0 * sh * B.rmax;
-                    atomicMax(bs.gate + GATE_DISP, __float_as_int((float)(d * d) * 1.0001f));
-                }
-            }
+        if (threadIdx.x < 6) {
+            double W = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) W += red[w][threadIdx.x];
+            s_w[b][threadIdx.x] = W;
         }
         __syncthreads();
     }
+    // the bodies' updates, one thread each (their FP64 arithmetic is long-latency)
+    if ((int)threadIdx.x < nb) body_update(p, bs, threadIdx.x, s_w[threadIdx.x]);
+    __syncthreads();
     if (threadIdx.x == 0) *bs.ticket = 0u;
 }
 
