@@ -155,32 +155,20 @@ __device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    __shared__ double s_w[kMaxBodies][6];
-    for (int b = 0; b < nb; ++b) {
-        // L2 loads (the partials were published before the ticket): issued
-        // together, not one round trip each
+    // the final sums: warp w takes bodies w, w + 8, ...; its lanes stride over the
+    // blocks' partials (L2 loads: they were published before the ticket), then a
+    // fixed shuffle tree; lane 0 updates the body (FP64 work kept to one warp per body)
+    for (int b = warp; b < nb; b += kBlock / 32) {
         double v[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll 4
-        for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x)
+        for (unsigned q = lane; q < gridDim.x; q += 32)
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[k] += __ldcg(&bs.partial[((size_t)q * nb + b) * 6 + k]);
 #pragma unroll
         for (int k = 0; k < 6; ++k)
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-        if (lane == 0)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            double W = 0.0;
-            for (int w = 0; w < kBlock / 32; ++w) W += red[w][threadIdx.x];
-            s_w[b][threadIdx.x] = W;
-        }
-        __syncthreads();
+        if (lane == 0) body_update(p, bs, b, v);
     }
-    // the bodies' updates, one thread each (their FP64 arithmetic is long-latency)
-    if ((int)threadIdx.x < nb) body_update(p, bs, threadIdx.x, s_w[threadIdx.x]);
     __syncthreads();
     if (threadIdx.x == 0) *bs.ticket = 0u;
 }
