@@ -49,17 +49,16 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
                            int *__restrict__ counts, int *__restrict__ abort_flag,
                            int64_t step_tag)
 {
-    if (threadIdx.x != 0) return;
     if (*abort_flag) return;
-    if (p.step_ctr != nullptr) step_tag = (int64_t)*p.step_ctr;
-    counts[3] = 0;
-    counts[4] = 0;
     const int G[3] = {p.GX, p.GY, p.GZ};
     const double dmin[3] = {p.dmin_x, p.dmin_y, p.dmin_z};
-    int lo[3] = {G[0], G[1], G[2]}, hi[3] = {-1, -1, -1};
-    int xa[kMaxBodies], xb[kMaxBodies];
-    const double grow = 2.0 * (double)p.h;
-    for (int b = 0; b < nbox; ++b) {
+    const double inv_cell = 1.0 / p.cell_d;
+    // the boxes' frames and cell ranges, one thread per box (FP64 work is slow:
+    // keep it parallel); the window below pads every range by one cell
+    __shared__ int s_lo[kMaxBodies][3], s_hi[kMaxBodies][3];
+    if ((int)threadIdx.x < nbox) {
+        const int b = threadIdx.x;
+        const double grow = 2.0 * (double)p.h;
         const BodyDev &B = bodies[box_body[b]];
         BoxFrame &F = frames[b];
         const double *q = B.pose + 3;
@@ -77,14 +76,24 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
         for (int k = 0; k < 3; ++k) {
             const double ext = fabs(R[3 * k]) * F.eg[0] + fabs(R[3 * k + 1]) * F.eg[1]
                                + fabs(R[3 * k + 2]) * F.eg[2];
-            int a = (int)floor((F.c[k] - ext - dmin[k]) / p.cell_d) - 1;
-            int c = (int)floor((F.c[k] + ext - dmin[k]) / p.cell_d) + 1;
-            a = max(a, 0);
-            c = min(c, G[k] - 1);
-            lo[k] = min(lo[k], a);
-            hi[k] = max(hi[k], c);
-            if (k == 0) { xa[b] = a; xb[b] = c; }
+            s_lo[b][k] = max((int)floor((F.c[k] - ext - dmin[k]) * inv_cell) - 1, 0);
+            s_hi[b][k] = min((int)floor((F.c[k] + ext - dmin[k]) * inv_cell) + 1, G[k] - 1);
         }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (p.step_ctr != nullptr) step_tag = (int64_t)*p.step_ctr;
+    counts[3] = 0;
+    counts[4] = 0;
+    int lo[3] = {G[0], G[1], G[2]}, hi[3] = {-1, -1, -1};
+    int xa[kMaxBodies], xb[kMaxBodies];
+    for (int b = 0; b < nbox; ++b) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = min(lo[k], s_lo[b][k]);
+            hi[k] = max(hi[k], s_hi[b][k]);
+        }
+        xa[b] = s_lo[b][0];
+        xb[b] = s_hi[b][0];
     }
     if (all_active || nbox == 0) {
         for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = G[k] - 1; }
