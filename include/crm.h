@@ -284,7 +284,9 @@ int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, con
 
 /* Differentiable run, forward half: n_steps steps of dt (as crm_step) with a
  * checkpoint of the state every `every` steps and after the last, and the
- * bodies after each step.  wrench_hist (n_steps*n_bodies*6: the soil force and
+ * bodies after each step; every = 0 keeps the whole run's tape resident
+ * instead (no checkpoints, and no re-run in the backward half: about
+ * 35 MB per step for 30,000 particles -- HBM traded for time).  wrench_hist (n_steps*n_bodies*6: the soil force and
  * torque of each step, as crm_get_body_wrench) and pose_hist
  * (n_steps*n_bodies*7: the pose after each step) are nullable.  Device memory:
  * the checkpoints (ceil(n_steps / every) + 1 states of crm_state_bytes) and the

@@ -142,6 +142,8 @@ struct crm_terrain {
         // the bodies after each step, the objective's adjoints
         int64_t n_steps = 0;
         int every = 0, n_ckpt = 0;
+        int64_t alloc_steps = -1;     // shape the tape and checkpoints were allocated for
+        int alloc_every = -1;
         double dt = 0.0;
         size_t ckpt_bytes = 0;
         char *ckpt = nullptr;
@@ -2161,7 +2163,7 @@ int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
 // One step of the run recorded to tape slot T: a graph per slot and current
 // buffer, captured at its first use and replayed for every later segment (the
 // tape and working arrays it points into stay put), else direct launches.
-int record_step(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
+int record_step(crm_terrain *t, double dt, crm_terrain::AdjTape &T, bool use_graph = true)
 {
     const int par = t->cur;
     cudaGraphExec_t &G = T.rec[par];
@@ -2169,7 +2171,7 @@ int record_step(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
         cudaGraphExecDestroy(G);
         G = nullptr;
     }
-    if (!G && t->graphs && t->cap_st && !t->timing) {
+    if (!G && use_graph && t->graphs && t->cap_st && !t->timing) {
         cudaStream_t user = t->st;
         const crm_profile saved = t->prof;
         const bool lv = t->lists_valid;
@@ -2326,8 +2328,8 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
                         double *wrench_hist, double *pose_hist)
 {
     if (!t) return CRM_EINVAL;
-    if (!(dt > 0) || !std::isfinite(dt) || n_steps < 1 || every < 1)
-        return t->fail(CRM_EINVAL, "crm_adjoint_forward: dt > 0, n_steps >= 1, every >= 1");
+    if (!(dt > 0) || !std::isfinite(dt) || n_steps < 1 || every < 0)
+        return t->fail(CRM_EINVAL, "crm_adjoint_forward: dt > 0, n_steps >= 1, every >= 0");
     int rc = commit(t);
     if (rc) return rc;
     rc = adj_support(t, true, "crm_adjoint_forward");
@@ -2335,22 +2337,32 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
     rc = adj_workspace(t);
     if (rc) return rc;
     crm_terrain::Adjoint &A = t->adj;
-    drop_tape(t);
     A.n_steps = 0;
     const DevParams &d = t->dp;
     const size_t nb = t->hbodies.size();
+    // every == 0: the whole run's tape stays resident (no checkpoints, no re-run)
+    const bool resident = every == 0;
+    // a run of the same shape reuses the tape and checkpoints allocated before
+    const bool reuse = A.alloc_steps == n_steps && A.alloc_every == every && !A.tape.empty();
+    if (!reuse) {
+        drop_tape(t);
+        A.alloc_steps = -1;
+        A.alloc_every = -1;
+    }
     size_t sb = 0;
     crm_state_bytes(t, &sb);
     A.ckpt_bytes = (sb + 255) / 256 * 256;
-    A.n_ckpt = (int)((n_steps + every - 1) / every) + 1;
-    A.ckpt = t->dalloc<char>(G_TAPE, A.ckpt_bytes * A.n_ckpt);
-    A.hist = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1) * n_steps);
-    A.lw_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 6 * n_steps);
-    A.lc_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 3 * n_steps);
-    // the tape of one segment
-    const int seg = (int)std::min<int64_t>(every, n_steps);
+    A.n_ckpt = resident ? 0 : (int)((n_steps + every - 1) / every) + 1;
+    if (!reuse) {
+        A.ckpt = resident ? nullptr : t->dalloc<char>(G_TAPE, A.ckpt_bytes * A.n_ckpt);
+        A.hist = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1) * n_steps);
+        A.lw_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 6 * n_steps);
+        A.lc_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 3 * n_steps);
+    }
+    // the tape of one segment (of the whole run when resident)
+    const int64_t seg = resident ? n_steps : std::min<int64_t>(every, n_steps);
     const size_t N = (size_t)std::max(d.capN, 1);
-    for (int k = 0; k < seg; ++k) {
+    for (int64_t k = reuse ? seg : 0; k < seg && !t->oom; ++k) {
         crm_terrain::AdjTape T = no_tape();
         for (StageArrays *S : {&T.Y0, &T.YM}) {
             S->pos = t->dalloc<float4>(G_TAPE, N);
@@ -2374,22 +2386,30 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
         drop_tape(t);
         return t->fail(CRM_ENOMEM, "crm_adjoint_forward: device allocation of the checkpoints and tape failed");
     }
+    A.alloc_steps = n_steps;
+    A.alloc_every = every;
     A.dt = dt;
     A.every = every;
     size_t used = 0;
     for (int64_t s = 0; s < n_steps; ++s) {
-        if (s % every == 0) {
-            rc = crm_save_state(t, A.ckpt + (size_t)(s / every) * A.ckpt_bytes, A.ckpt_bytes, &used);
-            if (rc) return rc;
+        if (resident) {
+            rc = record_step(t, dt, A.tape[(size_t)s], false);   // each slot used once
+        } else {
+            if (s % every == 0) {
+                rc = crm_save_state(t, A.ckpt + (size_t)(s / every) * A.ckpt_bytes, A.ckpt_bytes, &used);
+                if (rc) return rc;
+            }
+            rc = crm_step(t, dt, 1);
         }
-        rc = crm_step(t, dt, 1);
         if (rc) return rc;
         if (nb > 0)
             CRM_CUDA(t, cudaMemcpyAsync(A.hist + (size_t)s * nb, t->bodies, nb * sizeof(BodyDev),
                                         cudaMemcpyDeviceToDevice, t->st));
     }
-    rc = crm_save_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, A.ckpt_bytes, &used);
-    if (rc) return rc;
+    if (!resident) {
+        rc = crm_save_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, A.ckpt_bytes, &used);
+        if (rc) return rc;
+    }
     rc = latched_error(t);
     if (rc) return rc;
     if (nb > 0 && (wrench_hist || pose_hist)) {
@@ -2443,6 +2463,14 @@ int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l
         }
         CRM_CUDA(t, cudaMemcpyAsync(A.l_ins, l.data(), l.size() * sizeof(float), cudaMemcpyHostToDevice, t->st));
         CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    }
+    if (A.every == 0) {
+        // resident tape: the reverse sweep alone
+        for (int64_t s = n - 1; s >= 0; --s) {
+            int rc = vjp_step(t, A.tape[(size_t)s], s);
+            if (rc) return rc;
+        }
+        return adj_export(t, A.lb[0], g_xyz, g_vel, g_stress, g_rho, g_body, g_params);
     }
     size_t sb = 0;
     crm_state_bytes(t, &sb);

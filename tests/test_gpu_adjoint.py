@@ -399,3 +399,17 @@ def test_run_without_bodies_matches_oracle_differences():
         if abs(ad - fd) > RUN_TOL * max(scale, abs(fd)) + 1e-9:
             bad.append((name, ad, fd, scale))
     assert not bad, bad
+
+
+def test_resident_tape_matches_the_checkpointed_run(run_case):
+    """every = 0 keeps every step's tape (no checkpoints, no re-run): the same
+    recorded run and the same sweep, so the same gradients."""
+    sc, t, dt, w, q, lw, lc, g, lf = run_case
+    t2 = crm.from_scene(sc)
+    w2, q2 = t2.adjoint_forward(dt, N_RUN, 0)
+    np.testing.assert_array_equal(w2, w)
+    np.testing.assert_array_equal(q2, q)
+    g2 = t2.adjoint_backward(lw, lc, lf["x"], lf["u"], lf["sig"], lf["rho"])
+    np.testing.assert_allclose(g2["params"], g["params"], rtol=1e-9)
+    for key in ("xyz", "vel", "stress", "rho"):
+        np.testing.assert_allclose(g2[key], g[key], rtol=1e-5, atol=1e-7 * np.abs(g[key]).max())
