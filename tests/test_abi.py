@@ -107,3 +107,26 @@ def test_batch_rejects_members_without_their_own_stream():
     a.set_pair_lanes(1)
     a.close()
     b.close()
+
+
+def test_adjoint_and_exchange_argument_checks():
+    """The argument checks of the adjoint and co-simulation calls answer before any
+    device work (no GPU needed)."""
+    import paper_2507_05643_b300 as crm
+    t = crm.Terrain(crm.default_params())
+    t.add_sph(np.array([[0.5, 0.5, 0.5]]))
+    with pytest.raises(crm.CrmError) as e:
+        t.adjoint_backward()                       # nothing recorded
+    assert e.value.code == -8                      # CRM_ESTATE
+    for dt, n, every in ((-1.0, 2, 1), (1e-4, 0, 1), (1e-4, 2, -1)):
+        with pytest.raises(crm.CrmError) as e:
+            t.adjoint_forward(dt, n, every)
+        assert e.value.code == -1                  # CRM_EINVAL
+    lib = crm.lib()
+    assert lib.crm_eval_rates_vjp(t._h, 0, None, None, None, 0, None, None, None, None, None,
+                                  None, None) == -1   # capacity below the particle count
+    assert lib.crm_cosim_step(t._h, np.zeros(7).ctypes.data, None, 1e-4, 1, None, None,
+                              None) == -1          # a pose without a twist
+    t.set_pair_lanes(4)
+    t.set_pair_lanes(0)
+    t.close()
