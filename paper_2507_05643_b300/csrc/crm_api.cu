@@ -2393,7 +2393,9 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
     size_t used = 0;
     for (int64_t s = 0; s < n_steps; ++s) {
         if (resident) {
-            rc = record_step(t, dt, A.tape[(size_t)s], false);   // each slot used once
+            // each slot's recording graph is captured at its first use and replayed
+            // by later runs of the same shape (the tape is reused)
+            rc = record_step(t, dt, A.tape[(size_t)s]);
         } else {
             if (s % every == 0) {
                 rc = crm_save_state(t, A.ckpt + (size_t)(s / every) * A.ckpt_bytes, A.ckpt_bytes, &used);
