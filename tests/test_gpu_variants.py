@@ -389,3 +389,59 @@ def test_cosim_exchange_equals_the_separate_calls():
     # no motion given and no steps: the state as it stands
     W, P, V = t2.cosim_step(dt, 0)
     np.testing.assert_array_equal(P[0], t1.body_state(0)[0])
+
+
+def test_column_settles_to_a_lithostatic_state():
+    """A confined 30 x 30 x 10 column (0.3 x 0.3 x 0.1 m, 3-layer walls and floor)
+    released from zero stress under gravity, with a strong bilateral viscosity
+    (gamma 0.5) to settle it and a cohesion of 5 kPa that keeps the loading path
+    elastic (off the cone's apex at p = 0), run for 1 s (10,000 steps).  Then the
+    kinetic energy is below 1e-8 of the potential energy; in the central column,
+    between 2h above the floor and 3h below the surface, each lattice layer's mean
+    sigma_zz equals -rho0 g (H - z) within 10 % and the layers' sigma_zz falls with
+    depth at rho0 g within 10 %; the horizontal-to-vertical stress ratio lies
+    within 20 % of the uniaxial-strain value nu / (1 - nu).  (Measured: layers
+    within 2-7 %, ratio 0.37 against 0.43 -- the SPH column with h = 1.2 d0 and
+    BCE walls is not perfectly confined laterally.  A kinetic-energy threshold
+    alone is no settling test here: the viscosity quiets the column long before
+    its stress profile has relaxed.)"""
+    import math
+    d0, nx, ny, nz = 0.01, 30, 30, 10
+    p = scenes.default_params(d0, mu_s=math.tan(math.radians(30.0)), cohesion=5000.0, av_mode=1,
+                              av_gamma=0.5)
+    rng = np.random.default_rng(97)
+    x = scenes.lattice(nx, ny, nz, d0) + rng.uniform(-1e-4, 1e-4, size=(nx * ny * nz, 3))
+    layers = scenes.n_layers(p["h"], d0)
+    fixed = scenes.box_walls(nx, ny, nz + 5, layers, d0)
+    m = x.shape[0]
+    margin = layers * d0 + 2 * p["h"]
+    sc = scenes.Scene("column", p, x, np.zeros((m, 3)), np.zeros((m, 6)), np.full(m, p["rho0"]),
+                      fixed, [], [], 0.0, 1e-4, 0, np.array([-margin] * 3),
+                      np.array([nx * d0 + margin, ny * d0 + margin, (nz + 5) * d0 + margin]))
+    t = crm.from_scene(sc)
+    g, H, h = 9.81, nz * d0, p["h"]
+    pe = p["rho0"] * d0 ** 3 * g * float(np.sum(x[:, 2]))
+    t.step(sc.dt, 10000)
+    xyz, vel, sig, rho = t.particles()
+    ke = 0.5 * p["rho0"] * d0 ** 3 * float(np.sum(vel.astype(np.float64) ** 2))
+    assert ke < 1e-8 * pe, (ke, pe)
+    c = np.array([nx * d0 / 2, ny * d0 / 2])
+    sel = ((np.abs(xyz[:, 0] - c[0]) < 0.05) & (np.abs(xyz[:, 1] - c[1]) < 0.05)
+           & (xyz[:, 2] > 2 * h) & (xyz[:, 2] < H - 3 * h))
+    z = xyz[sel, 2]
+    szz = sig[sel, 2].astype(np.float64)
+    sxy = 0.5 * (sig[sel, 0] + sig[sel, 1]).astype(np.float64)
+    layer = np.floor(z / d0).astype(int)
+    assert len(np.unique(layer)) >= 4
+    zl, sl = [], []
+    for L in np.unique(layer):
+        k = layer == L
+        zl.append(float(np.mean(z[k])))
+        sl.append(float(np.mean(szz[k])))
+        lith = -p["rho0"] * g * (H - zl[-1])
+        assert abs(sl[-1] - lith) <= 0.10 * abs(lith), (L, sl[-1], lith)
+    slope = float(np.polyfit(zl, sl, 1)[0])
+    assert abs(slope - p["rho0"] * g) <= 0.10 * p["rho0"] * g, slope
+    k0 = p["nu"] / (1 - p["nu"])
+    ratio = float(np.sum(sxy) / np.sum(szz))
+    assert abs(ratio - k0) <= 0.2 * k0, ratio
