@@ -35,6 +35,9 @@ KERNEL_CUBIC, KERNEL_WENDLAND = 0, 1
 # parameter gradients of the reverse sweep, in this order
 GRAD_NAMES = ("E", "nu", "rho0", "mu_s", "cohesion", "av_gamma")
 NUM_GRADS = len(GRAD_NAMES)
+# per-body gradient entries: centre, velocity, acceleration, orientation (world-frame
+# rotation vector), angular velocity
+BODY_GRADS = 15
 
 
 class CrmError(RuntimeError):
@@ -327,7 +330,7 @@ class Terrain:
     def _grads(self, call) -> dict:
         n, nb = self.n_sph, self.n_bodies
         out = {"params": np.zeros(NUM_GRADS), "xyz": np.zeros((n, 3)), "vel": np.zeros((n, 3)),
-               "stress": np.zeros((n, 6)), "rho": np.zeros(n), "body": np.zeros((max(nb, 1), 9))}
+               "stress": np.zeros((n, 6)), "rho": np.zeros(n), "body": np.zeros((max(nb, 1), BODY_GRADS))}
         self._check(call(out))
         out["body"] = out["body"][:nb]
         out["param_grads"] = dict(zip(GRAD_NAMES, (float(v) for v in out["params"])))
@@ -336,7 +339,8 @@ class Terrain:
     def eval_rates_vjp(self, l_drho=None, l_dvel=None, l_dstress=None, l_macc=None) -> dict:
         """Gradient of sum(l . rates of eval_rates) at the current state (each l
         optional): {'xyz', 'vel', 'stress', 'rho' (per SPH particle), 'body'
-        (centre, velocity, acceleration per body), 'params' (GRAD_NAMES order),
+        (per body: centre, velocity, acceleration, orientation as a world-frame
+        rotation vector, angular velocity), 'params' (GRAD_NAMES order),
         'param_grads' (by name)}."""
         n, m = self.n_sph, self.n_markers
 

@@ -624,7 +624,7 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
     ParAcc par;
     par_zero(par);
     const int nn = valid ? (int)V.nnb[s] : 0;
-    float ub[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f}, arm[3];
+    float ub[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f}, arm[3] = {0.f, 0.f, 0.f};
     int body = -1;
     if (valid && nn > 0) body = marker_body_kin(p, V, s, ub, ab, arm);
     const StageArrays &S = V.S;
@@ -808,24 +808,72 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
         par.v[kGradRho0] += (double)la.rho;     // the marker density is rho0
     }
     if (q != 0) body = -1;
+    // the body's rotation: the marker sits at r = R l from the centre (a world-frame
+    // turn d theta moves it by d theta x r) and moves with u_b = v + w x r and
+    // a_b = acc + w x (w x r) (+ alpha x r, held fixed); in a step's wrench the
+    // marker force f = m a also acts at the arm r (torque r x f)
+    float lth[3] = {0.f, 0.f, 0.f}, lom[3] = {0.f, 0.f, 0.f};
+    if (body >= 0) {
+        const double *tw = V.bodies[body].twist + 3;
+        const float om[3] = {(float)tw[0], (float)tw[1], (float)tw[2]};
+        float lr[3] = {la.x[0], la.x[1], la.x[2]};
+        if (ACC && io.l_macc == nullptr) {
+            const double *wr = io.l_wrench + 6 * body;
+            const float lT[3] = {(float)wr[3], (float)wr[4], (float)wr[5]};
+            float fm[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) fm[k] = p.m * (Ms[k] / p.rho0 + As[k]);
+            // (r x f) . lT = r . (f x lT)
+            lr[0] += fm[1] * lT[2] - fm[2] * lT[1];
+            lr[1] += fm[2] * lT[0] - fm[0] * lT[2];
+            lr[2] += fm[0] * lT[1] - fm[1] * lT[0];
+        }
+        // u_b = v + w x r: (w x r) . l = r . (l x w) = w . (r x l)
+        lr[0] += lub[1] * om[2] - lub[2] * om[1];
+        lr[1] += lub[2] * om[0] - lub[0] * om[2];
+        lr[2] += lub[0] * om[1] - lub[1] * om[0];
+        lom[0] += arm[1] * lub[2] - arm[2] * lub[1];
+        lom[1] += arm[2] * lub[0] - arm[0] * lub[2];
+        lom[2] += arm[0] * lub[1] - arm[1] * lub[0];
+        // a_b = acc + w x q, q = w x r
+        const float qv[3] = {om[1] * arm[2] - om[2] * arm[1], om[2] * arm[0] - om[0] * arm[2],
+                             om[0] * arm[1] - om[1] * arm[0]};
+        const float lq[3] = {lab[1] * om[2] - lab[2] * om[1], lab[2] * om[0] - lab[0] * om[2],
+                             lab[0] * om[1] - lab[1] * om[0]};   // l_q = l_a x w
+        lom[0] += qv[1] * lab[2] - qv[2] * lab[1];
+        lom[1] += qv[2] * lab[0] - qv[0] * lab[2];
+        lom[2] += qv[0] * lab[1] - qv[1] * lab[0];
+        lr[0] += lq[1] * om[2] - lq[2] * om[1];
+        lr[1] += lq[2] * om[0] - lq[0] * om[2];
+        lr[2] += lq[0] * om[1] - lq[1] * om[0];
+        lom[0] += arm[1] * lq[2] - arm[2] * lq[1];
+        lom[1] += arm[2] * lq[0] - arm[0] * lq[2];
+        lom[2] += arm[0] * lq[1] - arm[1] * lq[0];
+        // d r = d theta x r: the turn's adjoint is r x l_r
+        lth[0] = arm[1] * lr[2] - arm[2] * lr[1];
+        lth[1] = arm[2] * lr[0] - arm[0] * lr[2];
+        lth[2] = arm[0] * lr[1] - arm[1] * lr[0];
+    }
     par_flush(par, gpar);
     // per-body sums: warp reduction, one FP64 atomic per warp and entry
     const int lane = threadIdx.x & 31;
     for (int b = 0; b < p.n_bodies; ++b) {
         const bool mine = body == b;
         if (!__any_sync(0xffffffffu, mine)) continue;
-        double v[9];
+        double v[kBodyAdj];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            v[k] = mine ? la.x[k] : 0.0;
-            v[3 + k] = mine ? lub[k] : 0.0;
-            v[6 + k] = mine ? lab[k] : 0.0;
+            v[kBodyC + k] = mine ? la.x[k] : 0.0;
+            v[kBodyV + k] = mine ? lub[k] : 0.0;
+            v[kBodyA + k] = mine ? lab[k] : 0.0;
+            v[kBodyTheta + k] = mine ? lth[k] : 0.0;
+            v[kBodyW + k] = mine ? lom[k] : 0.0;
         }
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
+        for (int k = 0; k < kBodyAdj; ++k) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-            if (lane == 0 && v[k] != 0.0) atomicAdd(gbody + 9 * b + k, v[k]);
+            if (lane == 0 && v[k] != 0.0) atomicAdd(gbody + kBodyAdj * b + k, v[k]);
         }
     }
 }
@@ -927,11 +975,46 @@ k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, dou
     par_flush(par, gpar);
 }
 
+// The turn of a step: dq = exp(phi / 2) with phi = w tau (qadvance), applied in
+// the world frame, so an orientation perturbed by the world-frame rotation
+// vector d theta stays perturbed by R(dq) d theta after the turn, and a change
+// d w of the rate turns it by J(phi) tau d w, J the left Jacobian of SO(3):
+// J(phi) = I + (1 - cos t) / t^2 [phi]x + (t - sin t) / t^3 [phi]x^2, t = |phi|.
+// turn_adjoint(w, tau, l) returns R(dq)^T l in lt and adds tau J(phi)^T l to lw.
+__device__ __forceinline__ void turn_adjoint(const double w[3], double tau, const double l[3],
+                                             double lt[3], double lw[3])
+{
+    const double ph[3] = {w[0] * tau, w[1] * tau, w[2] * tau};
+    const double t2 = ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2];
+    // R(dq)^T l: rotate l by the conjugate of dq = (cos(t/2), sin(t/2) phi / t)
+    double dq[4];
+    const double zero[4] = {1.0, 0.0, 0.0, 0.0};
+    qadvance(zero, w, tau, dq);
+    const double dqc[4] = {dq[0], -dq[1], -dq[2], -dq[3]};
+    qrot(dqc, l, lt);
+    // J^T l = l - a (phi x l) + b (phi x (phi x l)); Maclaurin series of a, b for small t
+    double a, b;
+    if (t2 <= 1e-2) {
+        a = 0.5 - t2 / 24.0 * (1.0 - t2 / 30.0);
+        b = 1.0 / 6.0 - t2 / 120.0 * (1.0 - t2 / 42.0);
+    } else {
+        const double t = sqrt(t2);
+        a = (1.0 - cos(t)) / t2;
+        b = (t - sin(t)) / (t2 * t);
+    }
+    const double c1[3] = {ph[1] * l[2] - ph[2] * l[1], ph[2] * l[0] - ph[0] * l[2],
+                          ph[0] * l[1] - ph[1] * l[0]};
+    const double c2[3] = {ph[1] * c1[2] - ph[2] * c1[1], ph[2] * c1[0] - ph[0] * c1[2],
+                          ph[0] * c1[1] - ph[1] * c1[0]};
+    for (int k = 0; k < 3; ++k) lw[k] += tau * (l[k] - a * c1[k] + b * c2[k]);
+}
+
 // Body adjoint of the update at the end of a step (Sec. 2.4, symplectic Euler
-// on the free linear DOFs): from the adjoints of the centre, velocity and
-// acceleration after the step (lb_next [body][9], plus the objective's terms on
-// the wrench and the centre) to the adjoint of the soil wrench (l_wrench) and
-// the partial adjoint of the body before the step (lb_cur).  One thread per body.
+// on the free linear DOFs, the orientation turned by the prescribed w): from
+// the adjoints of the body after the step (lb_next [body][kBodyAdj], plus the
+// objective's terms on the wrench and the centre) to the adjoint of the soil
+// wrench (l_wrench) and the partial adjoint of the body before the step
+// (lb_cur).  One thread per body.
 __global__ void k_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double *lb_next,
                                const double *lw_obj, const double *lc_obj, double *l_wrench,
                                double *lb_cur)
@@ -939,38 +1022,50 @@ __global__ void k_adj_body_pre(int nb, const BodyDev *bodies, double dt, const d
     const int b = threadIdx.x;
     if (b >= nb) return;
     const BodyDev &B = bodies[b];
+    const double *ln = lb_next + kBodyAdj * b;
+    double *lc_ = lb_cur + kBodyAdj * b;
     double lc[3], lv[3];
     for (int k = 0; k < 3; ++k) {
-        lc[k] = lb_next[9 * b + k] + (lc_obj ? lc_obj[3 * b + k] : 0.0);
-        lv[k] = lb_next[9 * b + 3 + k] + dt * lc[k];           // c' = c + dt v'
+        lc[k] = ln[kBodyC + k] + (lc_obj ? lc_obj[3 * b + k] : 0.0);
+        lv[k] = ln[kBodyV + k] + dt * lc[k];           // c' = c + dt v'
     }
     for (int k = 0; k < 3; ++k) {
         double lF = 0.0;
         if (B.dof & (1 << k)) {
-            const double la = lb_next[9 * b + 6 + k] + dt * lv[k];   // v' = v + dt a, acc' = a
+            const double la = ln[kBodyA + k] + dt * lv[k];   // v' = v + dt a, acc' = a
             lF = la / B.mass;
         }
         l_wrench[6 * b + k] = lF + (lw_obj ? lw_obj[6 * b + k] : 0.0);
         l_wrench[6 * b + 3 + k] = lw_obj ? lw_obj[6 * b + 3 + k] : 0.0;
-        lb_cur[9 * b + k] = lc[k];
-        lb_cur[9 * b + 3 + k] = lv[k];
-        lb_cur[9 * b + 6 + k] = 0.0;
+        lc_[kBodyC + k] = lc[k];
+        lc_[kBodyV + k] = lv[k];
+        lc_[kBodyA + k] = 0.0;
+        lc_[kBodyW + k] = ln[kBodyW + k];            // the prescribed rate stays
     }
+    // q' = exp(w dt / 2) q
+    turn_adjoint(B.twist + 3, dt, ln + kBodyTheta, lc_ + kBodyTheta, lc_ + kBodyW);
 }
 
 // The stages' body adjoints into the body before the step: the midpoint
-// markers sit at c + dt/2 v with velocity v and acceleration acc (of the
-// previous update), the stage-1 markers at c.
-__global__ void k_adj_body_post(int nb, double dt, const double *g0, const double *gm, double *lb)
+// markers sit at c + dt/2 v, turned by exp(w dt / 4), with velocity v, rate w
+// and acceleration acc (of the previous update); the stage-1 markers at c.
+__global__ void k_adj_body_post(int nb, const BodyDev *bodies, double dt, const double *g0,
+                                const double *gm, double *lb)
 {
     const int b = threadIdx.x;
     if (b >= nb) return;
+    const double *a0 = g0 + kBodyAdj * b, *am = gm + kBodyAdj * b;
+    double *l = lb + kBodyAdj * b;
     for (int k = 0; k < 3; ++k) {
-        const double lcm = gm[9 * b + k];
-        lb[9 * b + k] += g0[9 * b + k] + lcm;
-        lb[9 * b + 3 + k] += g0[9 * b + 3 + k] + gm[9 * b + 3 + k] + 0.5 * dt * lcm;
-        lb[9 * b + 6 + k] += g0[9 * b + 6 + k] + gm[9 * b + 6 + k];
+        l[kBodyC + k] += a0[kBodyC + k] + am[kBodyC + k];
+        l[kBodyV + k] += a0[kBodyV + k] + am[kBodyV + k] + 0.5 * dt * am[kBodyC + k];
+        l[kBodyA + k] += a0[kBodyA + k] + am[kBodyA + k];
+        l[kBodyTheta + k] += a0[kBodyTheta + k];
+        l[kBodyW + k] += a0[kBodyW + k] + am[kBodyW + k];
     }
+    double lt[3];
+    turn_adjoint(bodies[b].twist + 3, 0.5 * dt, am + kBodyTheta, lt, l + kBodyW);
+    for (int k = 0; k < 3; ++k) l[kBodyTheta + k] += lt[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1022,11 +1117,11 @@ void launch_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double 
     k_adj_body_pre<<<1, 32, 0, st>>>(nb, bodies, dt, lb_next, lw_obj, lc_obj, l_wrench, lb_cur);
 }
 
-void launch_adj_body_post(int nb, double dt, const double *g0, const double *gm, double *lb,
-                          cudaStream_t st)
+void launch_adj_body_post(int nb, const BodyDev *bodies, double dt, const double *g0,
+                          const double *gm, double *lb, cudaStream_t st)
 {
     if (nb == 0) return;
-    k_adj_body_post<<<1, 32, 0, st>>>(nb, dt, g0, gm, lb);
+    k_adj_body_post<<<1, 32, 0, st>>>(nb, bodies, dt, g0, gm, lb);
 }
 
 }  // namespace crm

@@ -16,6 +16,9 @@ enum : int { kBceW = 0, kBceSu = 1, kBceSs = 4, kBceSr = 10, kNumBceCoef = 13 };
 // directly (marker density, 1 / rho0 of the marker accelerations), friction
 // coefficient, cohesion.
 enum : int { kGradG = 0, kGradK, kGradM, kGradAvc, kGradRho0, kGradMu, kGradCoh, kNumGradAcc };
+// Body adjoints, per body: centre (3), linear velocity (3), linear acceleration
+// (3), world-frame rotation vector of the orientation (3), angular velocity (3).
+enum : int { kBodyC = 0, kBodyV = 3, kBodyA = 6, kBodyTheta = 9, kBodyW = 12, kBodyAdj = 15 };
 // Stage of a sweep pass.
 enum : int { kAdjEval = 0, kAdjStage1 = 1, kAdjStage2 = 2 };
 enum : int { kAdjAccumulate = 0, kAdjFinal = 1 };
@@ -58,7 +61,7 @@ void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, 
 void launch_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double *lb_next,
                          const double *lw_obj, const double *lc_obj, double *l_wrench,
                          double *lb_cur, cudaStream_t st);
-void launch_adj_body_post(int nb, double dt, const double *g0, const double *gm, double *lb,
-                          cudaStream_t st);
+void launch_adj_body_post(int nb, const BodyDev *bodies, double dt, const double *g0,
+                          const double *gm, double *lb, cudaStream_t st);
 
 }  // namespace crm

@@ -2020,9 +2020,9 @@ int adj_workspace(crm_terrain *t)
     A.l_macc = t->dalloc<float>(G_ADJ, 3 * nM);
     A.sums = t->dalloc<float>(G_ADJ, 13 * (size_t)std::max(d.capF, 1));
     A.gpar = t->dalloc<double>(G_ADJ, kNumGradAcc);
-    A.gbody = t->dalloc<double>(G_ADJ, 2 * 9 * nb);
-    A.lb[0] = t->dalloc<double>(G_ADJ, 9 * nb);
-    A.lb[1] = t->dalloc<double>(G_ADJ, 9 * nb);
+    A.gbody = t->dalloc<double>(G_ADJ, 2 * kBodyAdj * nb);
+    A.lb[0] = t->dalloc<double>(G_ADJ, kBodyAdj * nb);
+    A.lb[1] = t->dalloc<double>(G_ADJ, kBodyAdj * nb);
     A.lwrench = t->dalloc<double>(G_ADJ, 6 * nb);
     if (t->oom) {
         t->oom = false;
@@ -2100,12 +2100,12 @@ int adj_export(crm_terrain *t, const double *lb_dev, double *g_xyz, double *g_ve
     const int64_t nF = t->nFtot;
     const size_t nb = t->hbodies.size();
     std::vector<float> l((size_t)kNumAdj * std::max<int64_t>(nF, 1));
-    std::vector<double> acc(kNumGradAcc), lb(9 * std::max<size_t>(nb, 1));
+    std::vector<double> acc(kNumGradAcc), lb(kBodyAdj * std::max<size_t>(nb, 1));
     if (nF > 0 && (g_xyz || g_vel || g_stress || g_rho))
         CRM_CUDA(t, cudaMemcpyAsync(l.data(), A.l_ins, l.size() * sizeof(float), cudaMemcpyDeviceToHost, t->st));
     CRM_CUDA(t, cudaMemcpyAsync(acc.data(), A.gpar, kNumGradAcc * sizeof(double), cudaMemcpyDeviceToHost, t->st));
     if (nb > 0 && g_body && lb_dev)
-        CRM_CUDA(t, cudaMemcpyAsync(lb.data(), lb_dev, 9 * nb * sizeof(double), cudaMemcpyDeviceToHost, t->st));
+        CRM_CUDA(t, cudaMemcpyAsync(lb.data(), lb_dev, kBodyAdj * nb * sizeof(double), cudaMemcpyDeviceToHost, t->st));
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     int rc = latched_error(t);
     if (rc) return rc;
@@ -2118,7 +2118,7 @@ int adj_export(crm_terrain *t, const double *lb_dev, double *g_xyz, double *g_ve
             for (int k = 0; k < 6; ++k) g_stress[6 * i + k] = l[(size_t)(kAdjS + k) * nF + i];
         if (g_rho) g_rho[i] = l[(size_t)kAdjR * nF + i];
     }
-    if (g_body && lb_dev) std::memcpy(g_body, lb.data(), 9 * nb * sizeof(double));
+    if (g_body && lb_dev) std::memcpy(g_body, lb.data(), kBodyAdj * nb * sizeof(double));
     if (g_params) grads_from_acc(t->P, acc.data(), g_params);
     return CRM_OK;
 }
@@ -2225,13 +2225,13 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     const AdjStage V0{T.Y0, T.nbr, T.nnb, T.pid, t->mloc, T.bodies, nullptr, (int)t->nFtot,
                       T.sum0};
     const AdjIO io = adj_io(t, (float)dt);
-    double *g0 = A.gbody, *gm = A.gbody + 9 * std::max(nb, 1);
+    double *g0 = A.gbody, *gm = A.gbody + kBodyAdj * std::max(nb, 1);
     const double *lw = A.lw_obj ? A.lw_obj + (size_t)s * nb * 6 : nullptr;
     const double *lc = A.lc_obj ? A.lc_obj + (size_t)s * nb * 3 : nullptr;
     if (nb > 0) {
         launch(t, K_ADJ, [&] { launch_adj_body_pre(nb, T.bodies, dt, A.lb[0], lw, lc, A.lwrench,
                                                    A.lb[1], t->st); });
-        CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 2 * 9 * (size_t)nb * sizeof(double), t->st));
+        CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 2 * kBodyAdj * (size_t)nb * sizeof(double), t->st));
     }
     // stage 2 (at y_mid, with the wrench's marker accelerations)
     launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjStage2, d, Vm, T.Y0, io, A.gpar, t->st); });
@@ -2245,7 +2245,7 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     launch(t, K_ADJ, [&] { launch_adj_fluid(false, kAdjFinal, d, V0, io, A.l_y0, A.l_ins, A.gpar,
                                             t->st); });
     if (nb > 0) {
-        launch(t, K_ADJ, [&] { launch_adj_body_post(nb, dt, g0, gm, A.lb[1], t->st); });
+        launch(t, K_ADJ, [&] { launch_adj_body_post(nb, T.bodies, dt, g0, gm, A.lb[1], t->st); });
         std::swap(A.lb[0], A.lb[1]);
     }
     CRM_CUDA(t, cudaGetLastError());
@@ -2306,7 +2306,7 @@ int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, con
     cudaFreeAsync(buf, t->st);
     const size_t nb = t->hbodies.size();
     CRM_CUDA(t, cudaMemsetAsync(A.gpar, 0, kNumGradAcc * sizeof(double), t->st));
-    CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 9 * std::max<size_t>(nb, 1) * sizeof(double), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, kBodyAdj * std::max<size_t>(nb, 1) * sizeof(double), t->st));
     const AdjStage V{t->A[c], t->nbr, t->nnb, t->pid[c], t->mloc, t->bodies, nullptr, (int)nF,
                      A.sums};
     AdjIO io = adj_io(t, 0.0f);
@@ -2444,7 +2444,7 @@ int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l
         if (l_center) std::memcpy(c.data(), l_center, c.size() * sizeof(double));
         CRM_CUDA(t, cudaMemcpyAsync(A.lw_obj, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, t->st));
         CRM_CUDA(t, cudaMemcpyAsync(A.lc_obj, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, t->st));
-        CRM_CUDA(t, cudaMemsetAsync(A.lb[0], 0, 9 * nb * sizeof(double), t->st));
+        CRM_CUDA(t, cudaMemsetAsync(A.lb[0], 0, kBodyAdj * nb * sizeof(double), t->st));
         // (the host copies above read pageable memory: finish them before the
         // vectors go out of scope)
         CRM_CUDA(t, cudaStreamSynchronize(t->st));

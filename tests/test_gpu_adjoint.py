@@ -83,7 +83,20 @@ def _lam(sc, which, seed):
 
 
 SC_EVAL = _wheel()
-INPUTS = ("x", "u", "sig", "rho", "body_c", "body_v", "body_a", "E", "nu", "rho0", "av_gamma")
+INPUTS = ("x", "u", "sig", "rho", "body_c", "body_v", "body_a", "body_theta", "body_w", "E", "nu",
+          "rho0", "av_gamma")
+BODY_OFF = {"body_c": 0, "body_v": 3, "body_a": 6, "body_theta": 9, "body_w": 12}
+
+
+def _turned(q, phi):
+    """The quaternion q (w, x, y, z) turned by the world-frame rotation vector phi."""
+    t = float(np.linalg.norm(phi))
+    dq = np.array([1.0, 0.0, 0.0, 0.0]) if t == 0.0 else np.concatenate(
+        [[np.cos(t / 2)], np.sin(t / 2) * np.asarray(phi) / t])
+    w1, x1, y1, z1 = dq
+    w2, x2, y2, z2 = q
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
 
 
 @pytest.fixture(scope="module")
@@ -103,7 +116,8 @@ def _direction(sc, name, rng):
         eps = {"x": 1e-6 * h, "u": 1e-6, "sig": 1e-2, "rho": 1e-3}[name]
         return d, eps
     if name.startswith("body_"):
-        return rng.normal(size=3), {"body_c": 1e-6 * h, "body_v": 1e-6, "body_a": 1e-4}[name]
+        return rng.normal(size=3), {"body_c": 1e-6 * h, "body_v": 1e-6, "body_a": 1e-4,
+                                    "body_theta": 1e-6, "body_w": 1e-6}[name]
     return np.ones(1), 1e-6 * abs(sc.params[name])
 
 
@@ -117,8 +131,12 @@ def _perturbed(orc, name, d, e):
             b.pose[0, :3] += e * d
         elif name == "body_v":
             b.twist[0, :3] += e * d
-        else:
+        elif name == "body_a":
             b.acc[0, :3] += e * d
+        elif name == "body_theta":
+            b.pose[0, 3:] = _turned(b.pose[0, 3:], e * d)
+        else:
+            b.twist[0, 3:] += e * d
         return {"bodies": b}
     P = dict(st.params)
     P[name] += e * d[0]
@@ -130,7 +148,7 @@ def _adjoint_terms(g, name, d):
         key = {"x": "xyz", "u": "vel", "sig": "stress", "rho": "rho"}[name]
         return g[key].reshape(d.shape) * d
     if name.startswith("body_"):
-        off = {"body_c": 0, "body_v": 3, "body_a": 6}[name]
+        off = BODY_OFF[name]
         return g["body"][0, off:off + 3] * d
     return np.array([g["param_grads"][name] * d[0]])
 
@@ -238,7 +256,7 @@ def test_run_forward_matches_plain_steps(run_case):
 
 
 @pytest.mark.parametrize("name", ["E", "nu", "rho0", "mu_s", "cohesion", "av_gamma", "x", "u",
-                                  "sig", "rho", "body_c", "body_v"])
+                                  "sig", "rho", "body_c", "body_v", "body_theta", "body_w"])
 def test_run_gradient_matches_oracle_differences(run_case, name):
     sc, t, dt, w, q, lw, lc, g, lf = run_case
     rng = np.random.default_rng(11)
@@ -254,19 +272,25 @@ def test_run_gradient_matches_oracle_differences(run_case, name):
         jm = _oracle_run_J(sc, lw, lc, dt, lfin=lf, **{name: arr - e * d})
         key = {"x": "xyz", "u": "vel", "sig": "stress", "rho": "rho"}[name]
         terms = g[key].reshape(d.shape) * d
-    elif name in ("body_c", "body_v"):
+    elif name.startswith("body_"):
         d = rng.normal(size=3)
         e = 1e-6 * h if name == "body_c" else 1e-6
         bp, bm = copy.deepcopy(base.bodies), copy.deepcopy(base.bodies)
         if name == "body_c":
             bp.pose[0, :3] += e * d
             bm.pose[0, :3] -= e * d
-        else:
+        elif name == "body_v":
             bp.twist[0, :3] += e * d
             bm.twist[0, :3] -= e * d
+        elif name == "body_theta":
+            bp.pose[0, 3:] = _turned(bp.pose[0, 3:], e * d)
+            bm.pose[0, 3:] = _turned(bm.pose[0, 3:], -e * d)
+        else:
+            bp.twist[0, 3:] += e * d
+            bm.twist[0, 3:] -= e * d
         jp = _oracle_run_J(sc, lw, lc, dt, bodies=bp, lfin=lf)
         jm = _oracle_run_J(sc, lw, lc, dt, bodies=bm, lfin=lf)
-        off = 0 if name == "body_c" else 3
+        off = BODY_OFF[name]
         terms = g["body"][0, off:off + 3] * d
     else:
         e = 1e-6 * abs(sc.params[name])
@@ -371,7 +395,7 @@ def test_run_without_bodies_matches_oracle_differences():
     t.adjoint_forward(sc.dt, n_steps, 2)
     lf = _final_weights(sc.x.shape[0], 62)
     g = t.adjoint_backward(None, None, lf["x"], lf["u"], lf["sig"], lf["rho"])
-    assert g["body"].shape == (0, 9)
+    assert g["body"].shape == (0, 15)
     h = sc.params["h"]
     bad = []
     for name in ("x", "u", "sig", "rho", "E", "rho0", "mu_s", "cohesion"):
