@@ -260,10 +260,15 @@ def _adjoint_objectives(n_steps: int, nb: int = 1):
     return {"drawbar_pull": (lw_dp, None), "sinkage": (None, lc_sink)}
 
 
-def _phi_grads(g, mu_s: float) -> dict:
-    """(phi [rad], c, E, rho0) from the library's parameter gradients, mu_s = tan phi."""
-    return {"phi": g["mu_s"] * (1.0 + mu_s * mu_s), "cohesion": g["cohesion"], "E": g["E"],
-            "rho0": g["rho0"]}
+def _phi_grads(g, mu_s: float, body=None) -> dict:
+    """(phi [rad], c, E, rho0) from the library's parameter gradients, mu_s = tan phi;
+    with the wheel's body gradients also its prescribed forward speed and spin."""
+    out = {"phi": g["mu_s"] * (1.0 + mu_s * mu_s), "cohesion": g["cohesion"], "E": g["E"],
+           "rho0": g["rho0"]}
+    if body is not None:
+        out["speed_x"] = float(body[3])      # d J / d v_x (prescribed forward speed)
+        out["omega_y"] = float(body[13])     # d J / d w_y (prescribed spin)
+    return out
 
 
 def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = False) -> dict:
@@ -305,7 +310,7 @@ def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = Fa
             w0 = time.perf_counter()
             g = t.adjoint_backward(lw, lc)
             bwd_s.append(time.perf_counter() - w0)
-            grads[name] = _phi_grads(g["param_grads"], sc.params["mu_s"])
+            grads[name] = _phi_grads(g["param_grads"], sc.params["mu_s"], g["body"][0])
         prof = t.profile()
         # the same run with the whole tape resident in HBM (no checkpoints, no re-run)
         t.load_state(init.data_ptr(), used)
@@ -332,7 +337,8 @@ def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = Fa
         "objectives": {"drawbar_pull_N": float(wr[half:, 0, 0].mean()),
                        "sinkage_m": float((sc.bodies[0].pose[2] - pose[half:, 0, 2]).mean())},
         "gradients": grads,
-        "gradient_units": "per rad (phi), per Pa (cohesion, E), per kg/m^3 (rho0)",
+        "gradient_units": "per rad (phi), per Pa (cohesion, E), per kg/m^3 (rho0), per m/s "
+                          "(speed_x), per rad/s (omega_y)",
         "adjoint_launches": prof["launches"].get("adjoint", 0),
         "resident_tape": {
             "recorded_forward_ms_per_step": 1e3 * rec_res / n_steps,
@@ -364,9 +370,11 @@ def _adjoint_fd(sc, n_steps: int, grads: dict, rels=(1e-4, 1e-6)) -> dict:
     dt = sc.dt
     z0 = sc.bodies[0].pose[2]
 
-    def run(params):
+    def run(params, twist=None):
         s2 = sc.copy()
         s2.params = params
+        if twist is not None:
+            s2.bodies[0].twist = twist
         st = oracle.State(s2)
         fx, z = [], []
         for _ in range(n_steps):
@@ -378,17 +386,24 @@ def _adjoint_fd(sc, n_steps: int, grads: dict, rels=(1e-4, 1e-6)) -> dict:
     res = {}
     phi = math.atan(sc.params["mu_s"])
     for rel in rels:
-        for name in ("phi", "cohesion", "E", "rho0"):
+        for name in ("phi", "cohesion", "E", "rho0", "speed_x", "omega_y"):
             pp, pm = dict(sc.params), dict(sc.params)
+            tp = tm = None
             if name == "phi":
                 e = rel * phi
                 pp["mu_s"] = pp["mu_2"] = math.tan(phi + e)
                 pm["mu_s"] = pm["mu_2"] = math.tan(phi - e)
+            elif name in ("speed_x", "omega_y"):
+                k = 0 if name == "speed_x" else 4
+                e = rel * abs(sc.bodies[0].twist[k])
+                tp, tm = sc.bodies[0].twist.copy(), sc.bodies[0].twist.copy()
+                tp[k] += e
+                tm[k] -= e
             else:
                 e = rel * abs(sc.params[name])
                 pp[name] += e
                 pm[name] -= e
-            jp, jm = run(pp), run(pm)
+            jp, jm = run(pp, tp), run(pm, tm)
             for obj in ("drawbar_pull", "sinkage"):
                 fdv = (jp[obj] - jm[obj]) / (2 * e)
                 res.setdefault(f"step {rel:g}", {}).setdefault(obj, {})[name] = {
