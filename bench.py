@@ -563,8 +563,10 @@ def run_crm(args):
     if world > 1:
         dist.barrier()
     w0 = time.perf_counter()
+    out = (np.zeros((nb, 6)), np.zeros((nb, 7)), np.zeros((nb, 6)))
     for _ in range(e2e_steps):
-        W, hpose, htwist = t.cosim_step(dt, 1, hpose, htwist)
+        W, P, V = t.cosim_step(dt, 1, hpose, htwist, out=out)
+        hpose[:], htwist[:] = P, V     # the multibody side's next motion (here: the same)
     e2e_s = time.perf_counter() - w0
     t.sync()
 

@@ -295,17 +295,28 @@ class Terrain:
                                            C.byref(nout)))
         return xyz, vel, sig, rho
 
-    def cosim_step(self, dt: float, n_steps: int = 1, pose=None, twist=None):
+    def cosim_step(self, dt: float, n_steps: int = 1, pose=None, twist=None, out=None):
         """One co-simulation exchange: optionally set every body's motion (pose
         (n_bodies, 7), twist (n_bodies, 6)), step, and return (wrench
-        (n_bodies, 6), pose, twist) with one synchronisation."""
+        (n_bodies, 6), pose, twist) with one synchronisation.  `out`: optional
+        (wrench, pose, twist) float64 arrays of those shapes to fill (no
+        allocation per call)."""
         nb = self.n_bodies
-        pin = None if pose is None else np.ascontiguousarray(np.asarray(pose, np.float64).reshape(nb, 7))
-        tin = None if twist is None else np.ascontiguousarray(np.asarray(twist, np.float64).reshape(nb, 6))
-        w, q, v = np.zeros((max(nb, 1), 6)), np.zeros((max(nb, 1), 7)), np.zeros((max(nb, 1), 6))
+
+        def arr(a, k):
+            if a is None:
+                return None
+            if isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous \
+                    and a.size == nb * k:
+                return a
+            return np.ascontiguousarray(np.asarray(a, np.float64).reshape(nb, k))
+        pin, tin = arr(pose, 7), arr(twist, 6)
+        if out is None:
+            out = (np.zeros((nb, 6)), np.zeros((nb, 7)), np.zeros((nb, 6)))
+        w, q, v = out
         self._check(_lib.crm_cosim_step(self._h, _ptr(pin), _ptr(tin), float(dt), int(n_steps),
                                         _ptr(w), _ptr(q), _ptr(v)))
-        return w[:nb], q[:nb], v[:nb]
+        return w, q, v
 
     def body_wrench(self, body: int) -> Tuple[np.ndarray, np.ndarray]:
         f, t = np.zeros(3), np.zeros(3)
