@@ -246,15 +246,15 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
  * The paper differentiates nothing; these calls are this library's
  * hand-derived adjoint of the discrete method of Sec. 2.1-2.4 (pair sums,
  * Jaumann rate, artificial viscosity, BCE extrapolation, return map of Sec. 2.3
- * with a constant friction coefficient, midpoint step, body update of Sec.
- * 2.4), in FP32 on the device with FP64 sums of the parameter and body
+ * with mu(I), midpoint step, body update of Sec. 2.4), in FP32 on the device with FP64 sums of the parameter and body
  * adjoints.  Neighbour lists are those of the forward evaluation, held fixed,
  * and every branch is the one the forward took (the adjoint is that of the
  * piecewise-smooth map at the evaluated point).  Bodies: centre, velocity,
  * acceleration, orientation and angular velocity; an angular acceleration is
  * held fixed.  Not differentiated (CRM_EINVAL): active domains; in runs also
- * a Verlet skin or ps_freq > 1, mu(I) (mu_2 != mu_s) and bodies with a free
- * rotational DOF (their angular velocity must be prescribed). */
+ * a Verlet skin or ps_freq > 1 and bodies with a free rotational DOF (their
+ * angular velocity must be prescribed).  With mu(I) off (mu_2 = mu_s) the
+ * gradient for mu_s is the one with mu_2 moving along (mu_2's is zero). */
 
 /* Indices of the parameter gradients. */
 #define CRM_GRAD_E          0
@@ -265,7 +265,10 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
 #define CRM_GRAD_MU_S       3
 #define CRM_GRAD_COHESION   4
 #define CRM_GRAD_AV_GAMMA   5
-#define CRM_NUM_GRADS       6
+#define CRM_GRAD_MU_2       6
+#define CRM_GRAD_I0         7
+#define CRM_GRAD_GRAIN_D    8
+#define CRM_NUM_GRADS       9
 #define CRM_BODY_GRADS      15  /* per body: centre 3, velocity 3, acceleration 3,
                                  * orientation 3, angular velocity 3 */
 

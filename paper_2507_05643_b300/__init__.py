@@ -33,7 +33,7 @@ AV_NONE, AV_BILATERAL, AV_UNILATERAL = 0, 1, 2
 DOF_X, DOF_Y, DOF_Z, DOF_RX, DOF_RY, DOF_RZ = 1, 2, 4, 8, 16, 32
 KERNEL_CUBIC, KERNEL_WENDLAND = 0, 1
 # parameter gradients of the reverse sweep, in this order
-GRAD_NAMES = ("E", "nu", "rho0", "mu_s", "cohesion", "av_gamma")
+GRAD_NAMES = ("E", "nu", "rho0", "mu_s", "cohesion", "av_gamma", "mu_2", "I0", "grain_d")
 NUM_GRADS = len(GRAD_NAMES)
 # per-body gradient entries: centre, velocity, acceleration, orientation (world-frame
 # rotation vector), angular velocity

@@ -20,7 +20,9 @@ class TerrainRun(torch.autograd.Function):
     scene, n_steps, every).
 
     params: FP64 tensor in GRAD_NAMES order (E, nu, rho0, mu_s, cohesion,
-    av_gamma; mu_2 follows mu_s); x0, u0, sig0, rho0: the initial SPH state
+    av_gamma, mu_2, I0, grain_d; mu_2 = mu_s turns mu(I) off, and then the
+    gradient for mu_s is the one with mu_2 moving along); x0, u0, sig0, rho0: the
+    initial SPH state
     (n, 3), (n, 3), (n, 6), (n,); scene: the ``scenes.Scene`` that supplies
     the walls, bodies and the other constants.  Returns the soil wrench
     (n_steps, n_bodies, 6) and the body centres (n_steps, n_bodies, 3) after
@@ -33,7 +35,6 @@ class TerrainRun(torch.autograd.Function):
         p = params.detach().cpu().double().numpy()
         for k, name in enumerate(GRAD_NAMES):
             sc.params[name] = float(p[k])
-        sc.params["mu_2"] = sc.params["mu_s"]
         sc.x = x.detach().cpu().double().numpy().copy()
         sc.u = u.detach().cpu().double().numpy().copy()
         sc.sig = sig.detach().cpu().double().numpy().copy()

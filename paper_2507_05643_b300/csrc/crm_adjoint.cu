@@ -339,11 +339,33 @@ __device__ __forceinline__ float taubar6(const float s[6])
     return sqrtf(0.5f * (t0 * t0 + t1 * t1 + t2 * t2) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]));
 }
 
-// Backward of the return map of Sec. 2.3 with a constant friction coefficient
-// (mu(I) off): lo = adjoint of the mapped stress, s = trial stress; returns the
-// trial stress's adjoint in ls and adds the mu_s / cohesion terms to par.
-__device__ __forceinline__ void return_map_vjp(const float s[6], const float lo[6],
-                                               const DevParams &p, float ls[6], ParAcc &par)
+// Adjoint of taubar (the norm of the deviator, shear entries counted twice):
+// adds ltb d taubar / d s to ls (as a 6-vector).
+__device__ __forceinline__ void taubar_vjp(const float s[6], float tb, float ltb, float ls[6])
+{
+    if (!(tb > 0.0f) || ltb == 0.0f) return;
+    const float ps = -(s[0] + s[1] + s[2]) * (1.0f / 3.0f);
+    const float D[3] = {s[0] + ps, s[1] + ps, s[2] + ps};
+    const float itb = 1.0f / tb;
+    // tb^2 = 0.5 (D0^2 + D1^2 + D2^2) + s3^2 + s4^2 + s5^2, D = s + ps, ps = -tr/3
+    float lD[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lD[k] = 0.5f * ltb * D[k] * itb;
+    const float lps = lD[0] + lD[1] + lD[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ls[k] += lD[k] - lps * (1.0f / 3.0f);
+#pragma unroll
+    for (int k = 3; k < 6; ++k) ls[k] += ltb * s[k] * itb;
+}
+
+// Backward of the return map of Sec. 2.3: lo = adjoint of the mapped stress, s
+// = trial stress, sn = stress at t_n (the mu(I) shear rate); writes the trial
+// stress's adjoint to ls, adds the adjoint of sn to lsn and the parameters' to
+// par.  With mu(I) off (mu_2 = mu_s) the friction coefficient's adjoint is
+// mu_s's with mu_2 moving along.
+__device__ __forceinline__ void return_map_vjp(const float s[6], const float sn[6], float dt,
+                                               const float lo[6], const DevParams &p, float ls[6],
+                                               float lsn[6], ParAcc &par)
 {
     const float ps = -(s[0] + s[1] + s[2]) * (1.0f / 3.0f);
     if (p.mu_s > 0.0f && ps < -p.cohesion / p.mu_s) {   // tension cut-off: sigma = 0
@@ -352,7 +374,19 @@ __device__ __forceinline__ void return_map_vjp(const float s[6], const float lo[
         return;
     }
     const float tb = taubar6(s);
-    const float tmax = p.mu_s * ps + p.cohesion;
+    // mu(I) as the forward takes it
+    float mu = p.mu_s, I = 0.f, gdot = 0.f, tbn = 0.f;
+    bool rate = false;
+    if (p.mu_2 != p.mu_s) {
+        tbn = taubar6(sn);
+        gdot = (tb - tbn) / (p.G * dt);
+        if (gdot > 0.0f && ps > 0.0f) {
+            I = gdot * p.grain_d * sqrtf(p.rho0 / ps);
+            mu = p.mu_s + (p.mu_2 - p.mu_s) / (1.0f + p.I0 / I);
+            rate = true;
+        }
+    }
+    const float tmax = mu * ps + p.cohesion;
     if (tb <= tmax) {                                   // admissible: identity
 #pragma unroll
         for (int k = 0; k < 6; ++k) ls[k] = lo[k];
@@ -364,15 +398,33 @@ __device__ __forceinline__ void return_map_vjp(const float s[6], const float lo[
     float lf = 0.f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) lf += lo[k] * D[k];
+    float lps = -(lo[0] + lo[1] + lo[2]);
+    const float ltmax = lf / tb;
+    float ltb = -lf * f / tb;
+    par.v[kGradCoh] += (double)ltmax;
+    lps += ltmax * mu;
+    const float lmu = ltmax * ps;
+    if (!rate) {
+        par.v[kGradMu] += (double)lmu;
+    } else {
+        // mu = mu_s + (mu_2 - mu_s) / (1 + I0 / I), I = gdot d sqrt(rho0 / ps),
+        // gdot = (tb - taubar(sn)) / (G dt)
+        const float den = I + p.I0, dmu = p.mu_2 - p.mu_s;
+        par.v[kGradMu] += (double)(lmu * p.I0 / den);
+        par.v[kGradMu2] += (double)(lmu * I / den);
+        par.v[kGradI0] += (double)(-lmu * dmu * I / (den * den));
+        const float lI = lmu * dmu * p.I0 / (den * den);
+        par.v[kGradGrain] += (double)(lI * I / p.grain_d);
+        par.v[kGradRho0] += (double)(lI * I / (2.0f * p.rho0));
+        lps -= lI * I / (2.0f * ps);
+        const float lg = lI * p.grain_d * sqrtf(p.rho0 / ps);   // lI dI/dgdot
+        ltb += lg / (p.G * dt);
+        par.v[kGradG] += (double)(-lg * gdot / p.G);
+        taubar_vjp(sn, tbn, -lg / (p.G * dt), lsn);
+    }
     float lD[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) lD[k] = f * lo[k];
-    float lps = -(lo[0] + lo[1] + lo[2]);
-    const float ltmax = lf / tb;
-    const float ltb = -lf * f / tb;
-    par.v[kGradMu] += (double)(ltmax * ps);
-    par.v[kGradCoh] += (double)ltmax;
-    lps += ltmax * p.mu_s;
     // tb^2 = 0.5 (D0^2 + D1^2 + D2^2) + D3^2 + D4^2 + D5^2
     const float itb = 1.0f / tb;
 #pragma unroll
@@ -518,10 +570,10 @@ k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar
             const float4 a0 = Y0.sA[i];
             const float2 b0 = Y0.sB[i];
             const float sn[6] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y};
-            float trial[6], ltr[6];
+            float trial[6], ltr[6], lsn[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 6; ++k) trial[k] = fmaf(dt, ds[k], sn[k]);
-            return_map_vjp(trial, ln.s, p, ltr, par);
+            return_map_vjp(trial, sn, dt, ln.s, p, ltr, lsn, par);
             lr[0] = dt * ln.rho;
 #pragma unroll
             for (int k = 0; k < 3; ++k) lr[1 + k] = dt * ln.u[k];
@@ -534,7 +586,7 @@ k_adj_fluid_coef(DevParams p, AdjStage V, StageArrays Y0, AdjIO io, double *gpar
                 loc.u[k] = dt * ln.x[k];
             }
 #pragma unroll
-            for (int k = 0; k < 6; ++k) y0.s[k] = ltr[k];
+            for (int k = 0; k < 6; ++k) y0.s[k] = ltr[k] + lsn[k];   // trial = sn + dt ds
             y0.rho = ln.rho;
         } else {
             // y_mid = y_n + dt/2 f(y_n), x_mid = x_n + dt/2 u_n

@@ -14,8 +14,9 @@ enum : int { kBceW = 0, kBceSu = 1, kBceSs = 4, kBceSr = 10, kNumBceCoef = 13 };
 // Parameter adjoints accumulated on the device (FP64): shear and bulk modulus,
 // particle mass, viscosity constant gamma h c_s m, rho0 where it enters
 // directly (marker density, 1 / rho0 of the marker accelerations), friction
-// coefficient, cohesion.
-enum : int { kGradG = 0, kGradK, kGradM, kGradAvc, kGradRho0, kGradMu, kGradCoh, kNumGradAcc };
+// coefficient, cohesion, and the mu(I) constants mu_2, I0, grain diameter.
+enum : int { kGradG = 0, kGradK, kGradM, kGradAvc, kGradRho0, kGradMu, kGradCoh, kGradMu2,
+             kGradI0, kGradGrain, kNumGradAcc };
 // Body adjoints, per body: centre (3), linear velocity (3), linear acceleration
 // (3), world-frame rotation vector of the orientation (3), angular velocity (3).
 enum : int { kBodyC = 0, kBodyV = 3, kBodyA = 6, kBodyTheta = 9, kBodyW = 12, kBodyAdj = 15 };

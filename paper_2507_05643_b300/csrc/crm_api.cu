@@ -2035,8 +2035,8 @@ int adj_workspace(crm_terrain *t)
 }
 
 // What the sweep supports: no active boxes; for runs, a cell search every step
-// without a skin (so that a re-run reproduces the recorded lists), a constant
-// friction coefficient, and bodies whose rotations are prescribed.
+// without a skin (so that a re-run reproduces the recorded lists) and bodies
+// whose rotations are prescribed.
 int adj_support(crm_terrain *t, bool run, const char *who)
 {
     const std::string w(who);
@@ -2044,8 +2044,6 @@ int adj_support(crm_terrain *t, bool run, const char *who)
     if (!run) return CRM_OK;
     if (t->skin_on || t->P.ps_freq != 1)
         return t->fail(CRM_EINVAL, w + ": needs skin = 0 and ps_freq = 1");
-    if (t->P.mu_2 != t->P.mu_s)
-        return t->fail(CRM_EINVAL, w + ": mu(I) (mu_2 != mu_s) is not differentiated");
     for (const BodyDev &b : t->hbodies)
         if (b.dof & (7 << 3))
             return t->fail(CRM_EINVAL, w + ": free rotational DOFs are not differentiated");
@@ -2075,7 +2073,7 @@ AdjIO adj_io(crm_terrain *t, float dt)
 }
 
 // Accumulated parameter adjoints (G, K, m, viscosity constant, direct rho0,
-// mu_s, cohesion) -> the public parameters: G = E / (2 (1 + nu)),
+// mu_s, cohesion, mu_2, I0, grain diameter) -> the public parameters: G = E / (2 (1 + nu)),
 // K = E / (3 (1 - 2 nu)), m = rho0 d0^3, c = gamma h sqrt(K / rho0) m.
 void grads_from_acc(const crm_params &P, const double *a, double *g)
 {
@@ -2089,6 +2087,9 @@ void grads_from_acc(const crm_params &P, const double *a, double *g)
     g[CRM_GRAD_MU_S] = a[kGradMu];
     g[CRM_GRAD_COHESION] = a[kGradCoh];
     g[CRM_GRAD_AV_GAMMA] = a[kGradAvc] * c1;
+    g[CRM_GRAD_MU_2] = a[kGradMu2];
+    g[CRM_GRAD_I0] = a[kGradI0];
+    g[CRM_GRAD_GRAIN_D] = a[kGradGrain];
 }
 
 // Fluid adjoints (insertion order, FP32 on the device) -> caller's FP64

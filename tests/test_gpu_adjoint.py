@@ -316,10 +316,10 @@ def test_run_backward_restores_the_final_state(run_case):
 def test_run_rejects_unsupported_configurations():
     sc = _wheel(seed=41, nx=16, ny=12, nz=6)
     sc.params["skin"] = 0.0
-    sc.params["mu_2"] = sc.params["mu_s"] + 0.2      # mu(I)
+    sc.bodies[0].dof_mask |= crm.DOF_RY               # a free rotational DOF
     with pytest.raises(crm.CrmError):
         crm.from_scene(sc).adjoint_forward(sc.dt, 2, 1)
-    sc.params["mu_2"] = sc.params["mu_s"]
+    sc.bodies[0].dof_mask = crm.DOF_Z
     sc.params["skin"] = 0.1                          # a Verlet skin
     with pytest.raises(crm.CrmError):
         crm.from_scene(sc).adjoint_forward(sc.dt, 2, 1)
@@ -437,3 +437,41 @@ def test_resident_tape_matches_the_checkpointed_run(run_case):
     np.testing.assert_allclose(g2["params"], g["params"], rtol=1e-9)
     for key in ("xyz", "vel", "stress", "rho"):
         np.testing.assert_allclose(g2[key], g[key], rtol=1e-5, atol=1e-7 * np.abs(g[key]).max())
+
+
+@pytest.mark.parametrize("name", ["mu_s", "mu_2", "I0", "grain_d", "E", "rho0", "sig", "x"])
+def test_run_gradient_with_mu_i_matches_oracle_differences(name):
+    """The rate-dependent friction mu(I) (mu_2 != mu_s): its constants, and the
+    stress at t_n through the shear rate."""
+    sc = _wheel(seed=71, nx=16, ny=12, nz=6)
+    sc.params["skin"] = 0.0
+    sc.params["mu_2"] = sc.params["mu_s"] + 0.3
+    sc.bodies[0].pose[2] -= 0.004                    # deeper: more of the soil yields
+    t = crm.from_scene(sc)
+    dt = sc.dt
+    t.adjoint_forward(dt, N_RUN, EVERY)
+    rng = np.random.default_rng(13)
+    lw = rng.normal(size=(N_RUN, 1, 6))
+    lc = rng.normal(size=(N_RUN, 1, 3)) * 1e3
+    lf = _final_weights(sc.x.shape[0], 14)
+    g = t.adjoint_backward(lw, lc, lf["x"], lf["u"], lf["sig"], lf["rho"])
+    if name in ("sig", "x"):
+        arr = getattr(sc, name)
+        d = rng.normal(size=arr.shape)
+        e = 1e-2 if name == "sig" else 1e-6 * sc.params["h"]
+        jp = _oracle_run_J(sc, lw, lc, dt, lfin=lf, **{name: arr + e * d})
+        jm = _oracle_run_J(sc, lw, lc, dt, lfin=lf, **{name: arr - e * d})
+        terms = g["stress" if name == "sig" else "xyz"].reshape(d.shape) * d
+    else:
+        e = 1e-6 * abs(sc.params[name])
+        pp, pm = dict(sc.params), dict(sc.params)
+        pp[name] += e
+        pm[name] -= e
+        jp = _oracle_run_J(sc, lw, lc, dt, params=pp, lfin=lf)
+        jm = _oracle_run_J(sc, lw, lc, dt, params=pm, lfin=lf)
+        terms = np.array([g["param_grads"][name]])
+    fd = (jp - jm) / (2 * e)
+    ad, scale = float(terms.sum()), float(np.abs(terms).sum())
+    if name in ("mu_2", "I0", "grain_d"):     # the rate branch is exercised
+        assert abs(fd) * abs(sc.params[name]) > 1e-6 * abs(jp), (name, fd, jp)
+    assert abs(ad - fd) <= RUN_TOL * max(scale, abs(fd)) + 1e-9, (name, ad, fd, scale)
