@@ -250,11 +250,11 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
  * adjoints.  Neighbour lists are those of the forward evaluation, held fixed,
  * and every branch is the one the forward took (the adjoint is that of the
  * piecewise-smooth map at the evaluated point).  Bodies: centre, velocity,
- * acceleration, orientation and angular velocity; an angular acceleration is
- * held fixed.  Not differentiated (CRM_EINVAL): active domains; in runs also
- * a Verlet skin or ps_freq > 1 and bodies with a free rotational DOF (their
- * angular velocity must be prescribed).  With mu(I) off (mu_2 = mu_s) the
- * gradient for mu_s is the one with mu_2 moving along (mu_2's is zero). */
+ * acceleration, orientation, angular velocity and acceleration, through the
+ * markers' kinematics, the wrench and the 6-DOF update (Euler's equations in the
+ * world frame).  Not differentiated (CRM_EINVAL): active domains; in runs also
+ * a Verlet skin or ps_freq > 1.  With mu(I) off (mu_2 = mu_s) the gradient for
+ * mu_s is the one with mu_2 moving along (mu_2's is zero). */
 
 /* Indices of the parameter gradients. */
 #define CRM_GRAD_E          0
@@ -269,8 +269,9 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
 #define CRM_GRAD_I0         7
 #define CRM_GRAD_GRAIN_D    8
 #define CRM_NUM_GRADS       9
-#define CRM_BODY_GRADS      15  /* per body: centre 3, velocity 3, acceleration 3,
-                                 * orientation 3, angular velocity 3 */
+#define CRM_BODY_GRADS      18  /* per body: centre 3, velocity 3, acceleration 3,
+                                 * orientation 3, angular velocity 3, angular
+                                 * acceleration 3 */
 
 /* Vector-Jacobian product of crm_eval_rates at the current state.  Inputs,
  * insertion order, each nullable (= zero): l_drho (n_sph), l_dvel (n_sph*3),
@@ -280,8 +281,8 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used);
  * xx yy zz xy xz yz as independent entries), densities (g_rho, n_sph); of each
  * body's centre, linear velocity, linear acceleration, orientation (as a
  * world-frame rotation vector: the gradient with respect to a small turn
- * applied to the body) and angular velocity (g_body, CRM_BODY_GRADS per body,
- * in that order);
+ * applied to the body), angular velocity and angular acceleration (g_body,
+ * CRM_BODY_GRADS per body, in that order);
  * of the parameters (g_params, CRM_NUM_GRADS).  The output of
  * crm_eval_rates is sum(l . rates); the returned adjoints are its gradient.
  * Rebuilds the lists like crm_eval_rates; allocates its workspace once (kept
@@ -311,9 +312,9 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
  * order, all nullable (= zero), returns dJ / d parameters (g_params,
  * CRM_NUM_GRADS) and the adjoints of the run's initial state: SPH positions,
  * velocities, stresses, densities (insertion order, as crm_eval_rates_vjp) and
- * bodies (g_body, CRM_BODY_GRADS per body, as crm_eval_rates_vjp; a prescribed
- * angular velocity is constant over the run, so its entry is the gradient with
- * respect to it);
+ * bodies (g_body, CRM_BODY_GRADS per body, as crm_eval_rates_vjp: their state
+ * at the start; a prescribed velocity is constant over the run, so its entry is
+ * the gradient with respect to it);
  * each output nullable.  Re-runs every segment from its checkpoint (with
  * direct launches) and sweeps it in reverse; leaves the terrain in the state
  * after the recorded run.  CRM_ESTATE without a recorded run.  Synchronises

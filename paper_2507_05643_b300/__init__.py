@@ -36,8 +36,8 @@ KERNEL_CUBIC, KERNEL_WENDLAND = 0, 1
 GRAD_NAMES = ("E", "nu", "rho0", "mu_s", "cohesion", "av_gamma", "mu_2", "I0", "grain_d")
 NUM_GRADS = len(GRAD_NAMES)
 # per-body gradient entries: centre, velocity, acceleration, orientation (world-frame
-# rotation vector), angular velocity
-BODY_GRADS = 15
+# rotation vector), angular velocity, angular acceleration
+BODY_GRADS = 18
 
 
 class CrmError(RuntimeError):
@@ -351,7 +351,8 @@ class Terrain:
         """Gradient of sum(l . rates of eval_rates) at the current state (each l
         optional): {'xyz', 'vel', 'stress', 'rho' (per SPH particle), 'body'
         (per body: centre, velocity, acceleration, orientation as a world-frame
-        rotation vector, angular velocity), 'params' (GRAD_NAMES order),
+        rotation vector, angular velocity, angular acceleration), 'params'
+        (GRAD_NAMES order),
         'param_grads' (by name)}."""
         n, m = self.n_sph, self.n_markers
 

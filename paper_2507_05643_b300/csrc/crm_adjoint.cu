@@ -862,9 +862,9 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
     if (q != 0) body = -1;
     // the body's rotation: the marker sits at r = R l from the centre (a world-frame
     // turn d theta moves it by d theta x r) and moves with u_b = v + w x r and
-    // a_b = acc + w x (w x r) (+ alpha x r, held fixed); in a step's wrench the
-    // marker force f = m a also acts at the arm r (torque r x f)
-    float lth[3] = {0.f, 0.f, 0.f}, lom[3] = {0.f, 0.f, 0.f};
+    // a_b = acc + alpha x r + w x (w x r); in a step's wrench the marker force
+    // f = m a also acts at the arm r (torque r x f)
+    float lth[3] = {0.f, 0.f, 0.f}, lom[3] = {0.f, 0.f, 0.f}, lal[3] = {0.f, 0.f, 0.f};
     if (body >= 0) {
         const double *tw = V.bodies[body].twist + 3;
         const float om[3] = {(float)tw[0], (float)tw[1], (float)tw[2]};
@@ -887,7 +887,15 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
         lom[0] += arm[1] * lub[2] - arm[2] * lub[1];
         lom[1] += arm[2] * lub[0] - arm[0] * lub[2];
         lom[2] += arm[0] * lub[1] - arm[1] * lub[0];
-        // a_b = acc + w x q, q = w x r
+        // a_b = acc + alpha x r + w x q, q = w x r
+        const double *al = V.bodies[body].alpha;
+        const float alp[3] = {(float)al[0], (float)al[1], (float)al[2]};
+        lal[0] = arm[1] * lab[2] - arm[2] * lab[1];
+        lal[1] = arm[2] * lab[0] - arm[0] * lab[2];
+        lal[2] = arm[0] * lab[1] - arm[1] * lab[0];
+        lr[0] += lab[1] * alp[2] - lab[2] * alp[1];
+        lr[1] += lab[2] * alp[0] - lab[0] * alp[2];
+        lr[2] += lab[0] * alp[1] - lab[1] * alp[0];
         const float qv[3] = {om[1] * arm[2] - om[2] * arm[1], om[2] * arm[0] - om[0] * arm[2],
                              om[0] * arm[1] - om[1] * arm[0]};
         const float lq[3] = {lab[1] * om[2] - lab[2] * om[1], lab[2] * om[0] - lab[0] * om[2],
@@ -920,6 +928,7 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
             v[kBodyA + k] = mine ? lab[k] : 0.0;
             v[kBodyTheta + k] = mine ? lth[k] : 0.0;
             v[kBodyW + k] = mine ? lom[k] : 0.0;
+            v[kBodyAlpha + k] = mine ? lal[k] : 0.0;
         }
 #pragma unroll
         for (int k = 0; k < kBodyAdj; ++k) {
@@ -1061,15 +1070,41 @@ __device__ __forceinline__ void turn_adjoint(const double w[3], double tau, cons
     for (int k = 0; k < 3; ++k) lw[k] += tau * (l[k] - a * c1[k] + b * c2[k]);
 }
 
+// I_w v = R diag(I) R^T v, and its inverse, with R the rotation of quaternion q.
+__device__ __forceinline__ void inertia_world(const double q[4], const double I[3], const double v[3],
+                                              bool inverse, double o[3])
+{
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                            {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                            {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+    double t[3];
+    for (int r = 0; r < 3; ++r) {
+        const double d = R[0][r] * v[0] + R[1][r] * v[1] + R[2][r] * v[2];
+        t[r] = inverse ? d / I[r] : d * I[r];
+    }
+    for (int r = 0; r < 3; ++r) o[r] = R[r][0] * t[0] + R[r][1] * t[1] + R[r][2] * t[2];
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
 // Body adjoint of the update at the end of a step (Sec. 2.4, symplectic Euler
-// on the free linear DOFs, the orientation turned by the prescribed w): from
-// the adjoints of the body after the step (lb_next [body][kBodyAdj], plus the
-// objective's terms on the wrench and the centre) to the adjoint of the soil
-// wrench (l_wrench) and the partial adjoint of the body before the step
-// (lb_cur).  One thread per body.
-__global__ void k_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double *lb_next,
-                               const double *lw_obj, const double *lc_obj, double *l_wrench,
-                               double *lb_cur)
+// on the free DOFs: v' = v + dt (F/m + g), w' = w + dt wd with
+// wd = I_w^-1 (T - w x I_w w), I_w = R diag(I) R^T at t_n; then c' = c + dt v'
+// and q' = exp(w' dt / 2) q; acc' and alpha' are the free components of the
+// accelerations): from the adjoints of the body after the step (lb_next
+// [body][kBodyAdj], plus the objective's terms on the wrench and the centre) to
+// the adjoint of the soil wrench (l_wrench) and the partial adjoint of the body
+// before the step (lb_cur).  bodies / after: the bodies before / after the step.
+// One thread per body.
+__global__ void k_adj_body_pre(int nb, const BodyDev *bodies, const BodyDev *after, double dt,
+                               const double *lb_next, const double *lw_obj, const double *lc_obj,
+                               double *l_wrench, double *lb_cur)
 {
     const int b = threadIdx.x;
     if (b >= nb) return;
@@ -1092,10 +1127,50 @@ __global__ void k_adj_body_pre(int nb, const BodyDev *bodies, double dt, const d
         lc_[kBodyC + k] = lc[k];
         lc_[kBodyV + k] = lv[k];
         lc_[kBodyA + k] = 0.0;
-        lc_[kBodyW + k] = ln[kBodyW + k];            // the prescribed rate stays
+        lc_[kBodyW + k] = 0.0;
+        lc_[kBodyAlpha + k] = 0.0;
     }
-    // q' = exp(w dt / 2) q
-    turn_adjoint(B.twist + 3, dt, ln + kBodyTheta, lc_ + kBodyTheta, lc_ + kBodyW);
+    // q' = exp(w' dt / 2) q
+    double lw1[3] = {ln[kBodyW], ln[kBodyW + 1], ln[kBodyW + 2]};
+    turn_adjoint(after[b].twist + 3, dt, ln + kBodyTheta, lc_ + kBodyTheta, lw1);
+    // w' = w + dt wd on the free components (w' = w on the others), alpha' = wd there
+    double lwd[3] = {0.0, 0.0, 0.0};
+    bool free_rot = false;
+    for (int k = 0; k < 3; ++k) {
+        lc_[kBodyW + k] = lw1[k];
+        if (B.dof & (8 << k)) {
+            lwd[k] = dt * lw1[k] + ln[kBodyAlpha + k];
+            free_rot = true;
+        }
+    }
+    if (free_rot) {
+        // wd = I_w^-1 rhs, rhs = T - w x h, h = I_w w, I_w = R diag(I) R^T; a world
+        // turn d theta changes I_w by [d theta]x I_w - I_w [d theta]x
+        const double *q = B.pose + 3, *w = B.twist + 3;
+        double h[3], rhs[3], wd[3], lrhs[3];
+        inertia_world(q, B.inertia, w, false, h);
+        double wxh[3];
+        cross3(w, h, wxh);
+        for (int k = 0; k < 3; ++k) rhs[k] = after[b].wrench[3 + k] + B.load[3 + k] - wxh[k];
+        inertia_world(q, B.inertia, rhs, true, wd);
+        inertia_world(q, B.inertia, lwd, true, lrhs);
+        for (int k = 0; k < 3; ++k) l_wrench[6 * b + 3 + k] += lrhs[k];   // rhs = T - ...
+        double t1[3], t2[3];
+        cross3(wd, lwd, t1);
+        cross3(rhs, lrhs, t2);
+        for (int k = 0; k < 3; ++k) lc_[kBodyTheta + k] += t1[k] - t2[k];     // through I_w^-1
+        // rhs = T - w x h: (w x h) . l = w . (h x l) = h . (l x w)
+        double hxl[3], lh[3], Ilh[3], wxIlh[3], hxlh[3];
+        cross3(h, lrhs, hxl);
+        cross3(w, lrhs, lh);                    // l_h = -(l x w) = w x l
+        inertia_world(q, B.inertia, lh, false, Ilh);
+        cross3(w, Ilh, wxIlh);
+        cross3(h, lh, hxlh);
+        for (int k = 0; k < 3; ++k) {
+            lc_[kBodyW + k] += -hxl[k] + Ilh[k];                   // h = I_w w
+            lc_[kBodyTheta + k] += hxlh[k] - wxIlh[k];            // through I_w in h
+        }
+    }
 }
 
 // The stages' body adjoints into the body before the step: the midpoint
@@ -1114,6 +1189,7 @@ __global__ void k_adj_body_post(int nb, const BodyDev *bodies, double dt, const 
         l[kBodyA + k] += a0[kBodyA + k] + am[kBodyA + k];
         l[kBodyTheta + k] += a0[kBodyTheta + k];
         l[kBodyW + k] += a0[kBodyW + k] + am[kBodyW + k];
+        l[kBodyAlpha + k] += a0[kBodyAlpha + k] + am[kBodyAlpha + k];
     }
     double lt[3];
     turn_adjoint(bodies[b].twist + 3, 0.5 * dt, am + kBodyTheta, lt, l + kBodyW);
@@ -1161,12 +1237,13 @@ void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, 
     }
 }
 
-void launch_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double *lb_next,
-                         const double *lw_obj, const double *lc_obj, double *l_wrench,
-                         double *lb_cur, cudaStream_t st)
+void launch_adj_body_pre(int nb, const BodyDev *bodies, const BodyDev *after, double dt,
+                         const double *lb_next, const double *lw_obj, const double *lc_obj,
+                         double *l_wrench, double *lb_cur, cudaStream_t st)
 {
     if (nb == 0) return;
-    k_adj_body_pre<<<1, 32, 0, st>>>(nb, bodies, dt, lb_next, lw_obj, lc_obj, l_wrench, lb_cur);
+    k_adj_body_pre<<<1, 32, 0, st>>>(nb, bodies, after, dt, lb_next, lw_obj, lc_obj, l_wrench,
+                                     lb_cur);
 }
 
 void launch_adj_body_post(int nb, const BodyDev *bodies, double dt, const double *g0,

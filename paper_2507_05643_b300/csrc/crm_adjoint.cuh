@@ -18,8 +18,10 @@ enum : int { kBceW = 0, kBceSu = 1, kBceSs = 4, kBceSr = 10, kNumBceCoef = 13 };
 enum : int { kGradG = 0, kGradK, kGradM, kGradAvc, kGradRho0, kGradMu, kGradCoh, kGradMu2,
              kGradI0, kGradGrain, kNumGradAcc };
 // Body adjoints, per body: centre (3), linear velocity (3), linear acceleration
-// (3), world-frame rotation vector of the orientation (3), angular velocity (3).
-enum : int { kBodyC = 0, kBodyV = 3, kBodyA = 6, kBodyTheta = 9, kBodyW = 12, kBodyAdj = 15 };
+// (3), world-frame rotation vector of the orientation (3), angular velocity (3),
+// angular acceleration (3).
+enum : int { kBodyC = 0, kBodyV = 3, kBodyA = 6, kBodyTheta = 9, kBodyW = 12, kBodyAlpha = 15,
+             kBodyAdj = 18 };
 // Stage of a sweep pass.
 enum : int { kAdjEval = 0, kAdjStage1 = 1, kAdjStage2 = 2 };
 enum : int { kAdjAccumulate = 0, kAdjFinal = 1 };
@@ -59,9 +61,9 @@ void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const Ad
                        double *gpar, double *gbody, cudaStream_t st);
 void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, const AdjIO &io,
                       float *l_acc, float *l_final, double *gpar, cudaStream_t st);
-void launch_adj_body_pre(int nb, const BodyDev *bodies, double dt, const double *lb_next,
-                         const double *lw_obj, const double *lc_obj, double *l_wrench,
-                         double *lb_cur, cudaStream_t st);
+void launch_adj_body_pre(int nb, const BodyDev *bodies, const BodyDev *after, double dt,
+                         const double *lb_next, const double *lw_obj, const double *lc_obj,
+                         double *l_wrench, double *lb_cur, cudaStream_t st);
 void launch_adj_body_post(int nb, const BodyDev *bodies, double dt, const double *g0,
                           const double *gm, double *lb, cudaStream_t st);
 

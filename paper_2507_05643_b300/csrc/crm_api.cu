@@ -128,6 +128,7 @@ struct crm_terrain {
         uint32_t *pid, *nbr, *nnb;   // slot order and lists of the step
         BodyDev *bodies;             // bodies before the step
         BodyFrame *frames;           // bodies at the step midpoint
+        BodyDev *after;              // bodies after the step (its wrench, the updated rates)
         float *sum0, *sumM;          // fluid pair sums of the two stages ([13][capF])
         cudaGraphExec_t rec[2];      // the recording step as a graph, per current buffer
         double rec_dt;
@@ -2035,8 +2036,7 @@ int adj_workspace(crm_terrain *t)
 }
 
 // What the sweep supports: no active boxes; for runs, a cell search every step
-// without a skin (so that a re-run reproduces the recorded lists) and bodies
-// whose rotations are prescribed.
+// without a skin (so that a re-run reproduces the recorded lists).
 int adj_support(crm_terrain *t, bool run, const char *who)
 {
     const std::string w(who);
@@ -2044,9 +2044,6 @@ int adj_support(crm_terrain *t, bool run, const char *who)
     if (!run) return CRM_OK;
     if (t->skin_on || t->P.ps_freq != 1)
         return t->fail(CRM_EINVAL, w + ": needs skin = 0 and ps_freq = 1");
-    for (const BodyDev &b : t->hbodies)
-        if (b.dof & (7 << 3))
-            return t->fail(CRM_EINVAL, w + ": free rotational DOFs are not differentiated");
     return CRM_OK;
 }
 
@@ -2158,6 +2155,7 @@ int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
     if (d.capM > 0 && d.n_bodies > 0) bce(t, t->MID, 0.5 * dt, 1, dt, 1);
     pair(t, kStage2, t->MID, t->A[c], (float)dt, r2);
     CRM_CUDA(t, copy_stage(T.YM, t->MID));
+    if (nb > 0) CRM_CUDA(t, copy(T.after, t->bodies, nb * sizeof(BodyDev)));
     return CRM_OK;
 }
 
@@ -2230,8 +2228,8 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     const double *lw = A.lw_obj ? A.lw_obj + (size_t)s * nb * 6 : nullptr;
     const double *lc = A.lc_obj ? A.lc_obj + (size_t)s * nb * 3 : nullptr;
     if (nb > 0) {
-        launch(t, K_ADJ, [&] { launch_adj_body_pre(nb, T.bodies, dt, A.lb[0], lw, lc, A.lwrench,
-                                                   A.lb[1], t->st); });
+        launch(t, K_ADJ, [&] { launch_adj_body_pre(nb, T.bodies, T.after, dt, A.lb[0], lw, lc,
+                                                   A.lwrench, A.lb[1], t->st); });
         CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 2 * kBodyAdj * (size_t)nb * sizeof(double), t->st));
     }
     // stage 2 (at y_mid, with the wrench's marker accelerations)
@@ -2376,6 +2374,7 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
         T.nnb = t->dalloc<uint32_t>(G_TAPE, N);
         T.bodies = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1));
         T.frames = t->dalloc<BodyFrame>(G_TAPE, std::max<size_t>(nb, 1));
+        T.after = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1));
         T.sum0 = t->dalloc<float>(G_TAPE, 13 * (size_t)std::max(d.capF, 1));
         T.sumM = t->dalloc<float>(G_TAPE, 13 * (size_t)std::max(d.capF, 1));
         T.rec[0] = T.rec[1] = nullptr;

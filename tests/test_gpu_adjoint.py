@@ -316,10 +316,10 @@ def test_run_backward_restores_the_final_state(run_case):
 def test_run_rejects_unsupported_configurations():
     sc = _wheel(seed=41, nx=16, ny=12, nz=6)
     sc.params["skin"] = 0.0
-    sc.bodies[0].dof_mask |= crm.DOF_RY               # a free rotational DOF
-    with pytest.raises(crm.CrmError):
+    sc.boxes.append(scenes.ActiveBox(0, np.array([0.1, 0.1, 0.1]), np.zeros(3)))
+    with pytest.raises(crm.CrmError):                # active domains
         crm.from_scene(sc).adjoint_forward(sc.dt, 2, 1)
-    sc.bodies[0].dof_mask = crm.DOF_Z
+    sc.boxes.clear()
     sc.params["skin"] = 0.1                          # a Verlet skin
     with pytest.raises(crm.CrmError):
         crm.from_scene(sc).adjoint_forward(sc.dt, 2, 1)
@@ -395,7 +395,7 @@ def test_run_without_bodies_matches_oracle_differences():
     t.adjoint_forward(sc.dt, n_steps, 2)
     lf = _final_weights(sc.x.shape[0], 62)
     g = t.adjoint_backward(None, None, lf["x"], lf["u"], lf["sig"], lf["rho"])
-    assert g["body"].shape == (0, 15)
+    assert g["body"].shape == (0, 18)
     h = sc.params["h"]
     bad = []
     for name in ("x", "u", "sig", "rho", "E", "rho0", "mu_s", "cohesion"):
@@ -474,4 +474,77 @@ def test_run_gradient_with_mu_i_matches_oracle_differences(name):
     ad, scale = float(terms.sum()), float(np.abs(terms).sum())
     if name in ("mu_2", "I0", "grain_d"):     # the rate branch is exercised
         assert abs(fd) * abs(sc.params[name]) > 1e-6 * abs(jp), (name, fd, jp)
+    assert abs(ad - fd) <= RUN_TOL * max(scale, abs(fd)) + 1e-9, (name, ad, fd, scale)
+
+
+# ---------------------------------------------------------------------------
+# A body with all six DOFs free (Euler's equations with unequal moments)
+
+
+@pytest.fixture(scope="module")
+def six_dof_case():
+    sc = scenes.sphere_drop(seed=81, nx=16, ny=16, nz=8, radius=0.04)
+    sc.params["skin"] = 0.0
+    b = sc.bodies[0]
+    b.inertia = b.inertia * np.array([1.0, 2.0, 4.0])   # unequal moments: w x I w != 0
+    b.twist[3:] = [40.0, -30.0, 25.0]                    # fast: the gyroscopic terms count
+    b.pose[2] -= 0.006                                   # in contact with the bed
+    t = crm.from_scene(sc)
+    t.adjoint_forward(sc.dt, N_RUN, EVERY)
+    rng = np.random.default_rng(17)
+    lw = rng.normal(size=(N_RUN, 1, 6))
+    lw[:, :, 3:] *= 10.0
+    lc = rng.normal(size=(N_RUN, 1, 3)) * 1e3
+    lf = _final_weights(sc.x.shape[0], 18)
+    g = t.adjoint_backward(lw, lc, lf["x"], lf["u"], lf["sig"], lf["rho"])
+    return sc, g, lw, lc, lf
+
+
+@pytest.mark.parametrize("name", ["E", "mu_s", "x", "sig", "body_c", "body_v", "body_theta",
+                                  "body_w", "body_a", "body_alpha"])
+def test_run_six_dof_gradient_matches_oracle_differences(six_dof_case, name):
+    sc, g, lw, lc, lf = six_dof_case
+    dt = sc.dt
+    rng = np.random.default_rng(19)
+    base = oracle.State(sc)
+    if name in ("x", "sig"):
+        arr = getattr(sc, name)
+        d = rng.normal(size=arr.shape)
+        e = 1e-2 if name == "sig" else 1e-6 * sc.params["h"]
+        jp = _oracle_run_J(sc, lw, lc, dt, lfin=lf, **{name: arr + e * d})
+        jm = _oracle_run_J(sc, lw, lc, dt, lfin=lf, **{name: arr - e * d})
+        terms = g["stress" if name == "sig" else "xyz"].reshape(d.shape) * d
+    elif name.startswith("body_"):
+        d = rng.normal(size=3)
+        e = 1e-6 * sc.params["h"] if name == "body_c" else 1e-6
+        bp, bm = copy.deepcopy(base.bodies), copy.deepcopy(base.bodies)
+        for bb, sgn in ((bp, 1.0), (bm, -1.0)):
+            if name == "body_c":
+                bb.pose[0, :3] += sgn * e * d
+            elif name == "body_v":
+                bb.twist[0, :3] += sgn * e * d
+            elif name == "body_theta":
+                bb.pose[0, 3:] = _turned(bb.pose[0, 3:], sgn * e * d)
+            elif name == "body_w":
+                bb.twist[0, 3:] += sgn * e * d
+            elif name == "body_a":
+                bb.acc[0, :3] += sgn * e * d
+            else:
+                bb.acc[0, 3:] += sgn * e * d
+        jp = _oracle_run_J(sc, lw, lc, dt, bodies=bp, lfin=lf)
+        jm = _oracle_run_J(sc, lw, lc, dt, bodies=bm, lfin=lf)
+        off = dict(BODY_OFF, body_alpha=15)[name]
+        terms = g["body"][0, off:off + 3] * d
+    else:
+        e = 1e-6 * abs(sc.params[name])
+        pp, pm = dict(sc.params), dict(sc.params)
+        pp[name] += e
+        pm[name] -= e
+        if name == "mu_s":
+            pp["mu_2"], pm["mu_2"] = pp["mu_s"], pm["mu_s"]
+        jp = _oracle_run_J(sc, lw, lc, dt, params=pp, lfin=lf)
+        jm = _oracle_run_J(sc, lw, lc, dt, params=pm, lfin=lf)
+        terms = np.array([g["param_grads"][name]])
+    fd = (jp - jm) / (2 * e)
+    ad, scale = float(terms.sum()), float(np.abs(terms).sum())
     assert abs(ad - fd) <= RUN_TOL * max(scale, abs(fd)) + 1e-9, (name, ad, fd, scale)
