@@ -235,10 +235,12 @@ def _workload(args):
     return scenes.wheel_bin(nx=200 * s, ny=40 * s, wheel_x=0.4 * s)
 
 
-ADJ_WORKLOAD = ("differentiable wheel test: 30,000 SPH particles, 1.0x0.3x0.1 m bin at d0=0.01 m, "
-                "the wheel_bin wheel and material, skin 0, ps_freq=1, 400 steps of 5e-5 s, "
-                "checkpoint every 20; J = mean over steps 201-400 of drawbar pull F_x and of "
-                "sinkage z0 - z")
+def adj_workload(n_steps: int = 400, every: int = 20) -> str:
+    half = n_steps // 2
+    return ("differentiable wheel test: 30,000 SPH particles, 1.0x0.3x0.1 m bin at d0=0.01 m, "
+            f"the wheel_bin wheel and material, skin 0, ps_freq=1, {n_steps} steps of 5e-5 s, "
+            f"checkpoint every {every}; J = mean over steps {half + 1}-{n_steps} of drawbar "
+            "pull F_x and of sinkage z0 - z")
 
 
 def _adjoint_scene():
@@ -328,7 +330,7 @@ def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = Fa
         t.close()
     half = n_steps // 2
     out = {
-        "workload": ADJ_WORKLOAD, "n_sph": sc.n_fluid, "n_bce": sc.n_markers,
+        "workload": adj_workload(n_steps, every), "n_sph": sc.n_fluid, "n_bce": sc.n_markers,
         "forward_ms_per_step": fwd_ms,
         "recorded_forward_ms_per_step": 1e3 * rec_s / n_steps,
         "first_recording_s": first_s,
@@ -424,7 +426,7 @@ def run_adjoint(args):
             "unit": "ratio", "n_gpus": 1, "steps": args.adjoint_steps, "warmup": 4,
             "ms_per_step": adj["backward_ms_per_step"], "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": adj["workload"].replace("400 steps", f"{args.adjoint_steps} steps")},
+            "config": {"workload": adj["workload"]},
             "adjoint": adj}
     print(json.dumps(line), flush=True)
 
