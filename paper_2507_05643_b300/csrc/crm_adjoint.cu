@@ -1056,8 +1056,8 @@ __device__ __forceinline__ void turn_adjoint(const double w[3], double tau, cons
     // J^T l = l - a (phi x l) + b (phi x (phi x l)); Maclaurin series of a, b for small t
     double a, b;
     if (t2 <= 1e-2) {
-        a = 0.5 - t2 / 24.0 * (1.0 - t2 / 30.0);
-        b = 1.0 / 6.0 - t2 / 120.0 * (1.0 - t2 / 42.0);
+        a = 0.5 - t2 * (1.0 / 24.0) * (1.0 - t2 * (1.0 / 30.0));
+        b = 1.0 / 6.0 - t2 * (1.0 / 120.0) * (1.0 - t2 * (1.0 / 42.0));
     } else {
         const double t = sqrt(t2);
         a = (1.0 - cos(t)) / t2;
@@ -1101,13 +1101,18 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 // [body][kBodyAdj], plus the objective's terms on the wrench and the centre) to
 // the adjoint of the soil wrench (l_wrench) and the partial adjoint of the body
 // before the step (lb_cur).  bodies / after: the bodies before / after the step.
-// One thread per body.
+// It also clears the body's two stage accumulators (gbody [2][nb][kBodyAdj]) for
+// the marker passes that follow.  One thread per body.
 __global__ void k_adj_body_pre(int nb, const BodyDev *bodies, const BodyDev *after, double dt,
                                const double *lb_next, const double *lw_obj, const double *lc_obj,
-                               double *l_wrench, double *lb_cur)
+                               double *l_wrench, double *lb_cur, double *gbody)
 {
     const int b = threadIdx.x;
     if (b >= nb) return;
+    for (int k = 0; k < kBodyAdj; ++k) {
+        gbody[kBodyAdj * b + k] = 0.0;
+        gbody[kBodyAdj * (nb + b) + k] = 0.0;
+    }
     const BodyDev &B = bodies[b];
     const double *ln = lb_next + kBodyAdj * b;
     double *lc_ = lb_cur + kBodyAdj * b;
@@ -1237,13 +1242,15 @@ void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, 
     }
 }
 
+static_assert(kMaxBodies <= 32, "the body kernels run one warp, one thread per body");
+
 void launch_adj_body_pre(int nb, const BodyDev *bodies, const BodyDev *after, double dt,
                          const double *lb_next, const double *lw_obj, const double *lc_obj,
-                         double *l_wrench, double *lb_cur, cudaStream_t st)
+                         double *l_wrench, double *lb_cur, double *gbody, cudaStream_t st)
 {
     if (nb == 0) return;
     k_adj_body_pre<<<1, 32, 0, st>>>(nb, bodies, after, dt, lb_next, lw_obj, lc_obj, l_wrench,
-                                     lb_cur);
+                                     lb_cur, gbody);
 }
 
 void launch_adj_body_post(int nb, const BodyDev *bodies, double dt, const double *g0,

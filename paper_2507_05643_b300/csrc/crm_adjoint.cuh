@@ -63,7 +63,7 @@ void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, 
                       float *l_acc, float *l_final, double *gpar, cudaStream_t st);
 void launch_adj_body_pre(int nb, const BodyDev *bodies, const BodyDev *after, double dt,
                          const double *lb_next, const double *lw_obj, const double *lc_obj,
-                         double *l_wrench, double *lb_cur, cudaStream_t st);
+                         double *l_wrench, double *lb_cur, double *gbody, cudaStream_t st);
 void launch_adj_body_post(int nb, const BodyDev *bodies, double dt, const double *g0,
                           const double *gm, double *lb, cudaStream_t st);
 

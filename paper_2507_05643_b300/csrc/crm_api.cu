@@ -2229,8 +2229,7 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     const double *lc = A.lc_obj ? A.lc_obj + (size_t)s * nb * 3 : nullptr;
     if (nb > 0) {
         launch(t, K_ADJ, [&] { launch_adj_body_pre(nb, T.bodies, T.after, dt, A.lb[0], lw, lc,
-                                                   A.lwrench, A.lb[1], t->st); });
-        CRM_CUDA(t, cudaMemsetAsync(A.gbody, 0, 2 * kBodyAdj * (size_t)nb * sizeof(double), t->st));
+                                                   A.lwrench, A.lb[1], A.gbody, t->st); });
     }
     // stage 2 (at y_mid, with the wrench's marker accelerations)
     launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjStage2, d, Vm, T.Y0, io, A.gpar, t->st); });

@@ -214,9 +214,12 @@ __device__ __forceinline__ void qadvance(const double q[4], const double w[3], d
     const double phi2 = 0.25 * w2 * tau * tau;
     double c, sw;   // cos(phi), sin(phi) / |w|
     if (phi2 <= 0.0025) {
+        // products with the reciprocals (an FP64 division is a long software
+        // sequence; these differ from it by at most an ulp)
         const double x = phi2;
-        c = 1.0 - x / 2.0 * (1.0 - x / 12.0 * (1.0 - x / 30.0 * (1.0 - x / 56.0)));
-        sw = 0.5 * tau * (1.0 - x / 6.0 * (1.0 - x / 20.0 * (1.0 - x / 42.0 * (1.0 - x / 72.0))));
+        c = 1.0 - x * 0.5 * (1.0 - x * (1.0 / 12.0) * (1.0 - x * (1.0 / 30.0) * (1.0 - x * (1.0 / 56.0))));
+        sw = 0.5 * tau * (1.0 - x * (1.0 / 6.0) * (1.0 - x * (1.0 / 20.0) * (1.0 - x * (1.0 / 42.0)
+                                                                     * (1.0 - x * (1.0 / 72.0)))));
     } else {
         const double wn = sqrt(w2);
         double s;
