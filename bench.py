@@ -200,14 +200,22 @@ KERNEL_SOURCE = {"pair_stage1": "crm_step.cu", "pair_stage2": "crm_step.cu", "bc
                  "neighbors": "crm_bin.cu", "export": "crm_step.cu"}
 
 
-def _traffic(kernel: str):
+def _traffic(kernel: str, captured: bool = True):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.txt: kernel, bytes per launch, sha256[:16] of the source
-    file the kernel lives in when it was captured), if it was taken on the
-    current source (else None)."""
+    file the kernel lives in followed by the shared device header, when it was
+    captured), if it was taken on the
+    current source (else None).  captured: the line's workload is the one the
+    summary was captured on (the wheel bin); on any other the figure does not
+    apply and None is returned."""
+    if not captured:
+        return None
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_2507_05643_b300", "csrc", KERNEL_SOURCE.get(kernel, "crm_step.cu"))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2507_05643_b300", "csrc")
+    h = hashlib.sha256()
+    for f in (KERNEL_SOURCE.get(kernel, "crm_step.cu"), "crm_internal.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    h = h.hexdigest()[:16]
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -583,6 +591,8 @@ def run_crm(args):
         # dominant kernel = largest share of the event-timed step
         kern = max(prof["ms"], key=lambda k: prof["ms"][k])
         avg_ms = per[kern]
+        # the ncu DRAM bytes in profiles/ were captured on the wheel bin as quoted
+        same_case = args.workload == "wheel_bin" and args.bin_scale == 1 and args.ps_freq == 1
         fp32_peak = nsm * SM_FP32_LANES * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         alg_bytes = {   # algorithmic DRAM bytes per launch (state read / written once)
             "keys": 40 * n_all, "scan": 8 * (2 * 60000 + 1), "scatter": 12 * n_all,
@@ -599,14 +609,14 @@ def run_crm(args):
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                     "peak_source": f"{nsm} SMs x {SM_FP32_LANES} FP32 lanes x 2 x "
                                    f"{peaks['sm_max_mhz']:.0f} MHz ({kind} max clock)",
-                    "traffic": _traffic(kern), "flop_per_launch": flop, "ms_per_launch": avg_ms}
+                    "traffic": _traffic(kern, same_case), "flop_per_launch": flop, "ms_per_launch": avg_ms}
         else:
             b = alg_bytes.get(kern, 0.0)
             achieved = b / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": kern, "achieved": achieved,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "peak_source": f"hbm_gbs ({kind})",
-                    "traffic": _traffic(kern), "bytes_per_launch": b, "ms_per_launch": avg_ms}
+                    "traffic": _traffic(kern, same_case), "bytes_per_launch": b, "ms_per_launch": avg_ms}
         pair_ms = per.get("pair_stage2", 0.0)
         pair_fp32 = ((fluid_pairs * FLOP_PER_PAIR + sc.n_fluid * FLOP_PER_PARTICLE)
                      / (pair_ms * 1e-3) / 1e12 / fp32_peak) if pair_ms else None
@@ -636,7 +646,7 @@ def run_crm(args):
                              "achieved_gbs": _traffic(k) / (per[k] * 1e-3) / 1e9,
                              "frac": _traffic(k) / (per[k] * 1e-3) / 1e9 / peaks["hbm_gbs"]}
                          for k in ("pair_stage1", "pair_stage2")
-                         if per.get(k) and _traffic(k)},
+                         if per.get(k) and _traffic(k, same_case)},
             "roofline": roof,
             "clocks": clocks,
         }

@@ -26,3 +26,15 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_captured_traffic_applies_only_to_its_workload_and_source():
+    """The ncu DRAM bytes in profiles/traffic.txt belong to the wheel bin on the
+    source they were captured on: no other workload, and no edited source, reports them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("pair_stage1", "pair_stage2", "bce"):
+        assert bench._traffic(k, captured=False) is None
+    v = bench._traffic("pair_stage1")
+    assert v is None or v > 1e6          # None once crm_step.cu changed since the capture
+    assert bench._traffic("no_such_kernel") is None
