@@ -548,3 +548,72 @@ def test_run_six_dof_gradient_matches_oracle_differences(six_dof_case, name):
     fd = (jp - jm) / (2 * e)
     ad, scale = float(terms.sum()), float(np.abs(terms).sum())
     assert abs(ad - fd) <= RUN_TOL * max(scale, abs(fd)) + 1e-9, (name, ad, fd, scale)
+
+
+# ---------------------------------------------------------------------------
+# Against the oracle's own FP64 adjoint (oracle/adjoint.py, pinned to the C
+# oracle by tests/test_oracle_adjoint.py): every entry of every gradient, not
+# one direction.  Bars: the relative L2 error of each array, the largest entry
+# error against the array's largest entry, each parameter gradient against its
+# own size (FP32 sweep of an FP32 trajectory against FP64 throughout).
+ORACLE_REL = 2e-3        # relative L2 error of an array / error of a parameter gradient
+ORACLE_MAX = 1e-2        # largest entry error / largest entry
+
+
+def _against_oracle_adjoint(sc, g, lw, lc, lf, n_steps, params):
+    from oracle import adjoint as oadj
+    _, _, o = oadj.run_gradients(sc, sc.dt, n_steps, lw, lc, lf, mode="brute")
+    errs, bad = {}, []
+    pairs = [("xyz", "x"), ("vel", "u"), ("stress", "sig"), ("rho", "rho")]
+    arrays = {k: (np.asarray(g[k], float).reshape(o[ko].shape), o[ko]) for k, ko in pairs}
+    if len(sc.bodies):
+        b = np.asarray(g["body"], float)[0]
+        arrays.update({"body_c": (b[0:3], o["body_c"][0]), "body_v": (b[3:6], o["body_v"][0]),
+                       "body_a": (b[6:9], o["body_acc"][0, :3]),
+                       "body_theta": (b[9:12], o["body_theta"][0]),
+                       "body_w": (b[12:15], o["body_w"][0]),
+                       "body_alpha": (b[15:18], o["body_acc"][0, 3:])})
+    for k, (a, r) in arrays.items():
+        nr = float(np.linalg.norm(r))
+        if nr == 0.0:
+            continue
+        rel = float(np.linalg.norm(a - r)) / nr
+        mx = float(np.abs(a - r).max()) / float(np.abs(r).max())
+        errs[k] = (rel, mx)
+        if rel > ORACLE_REL or mx > ORACLE_MAX:
+            bad.append(k)
+    for k in params:
+        a, r = float(g["param_grads"][k]), float(o["params"][k])
+        rel = abs(a - r) / max(abs(r), 1e-300)
+        errs[k] = rel
+        if rel > ORACLE_REL:
+            bad.append(k)
+    print("errors against the oracle adjoint:", errs)
+    assert not bad, (bad, errs)
+
+
+def test_run_gradients_match_the_oracle_adjoint(run_case):
+    sc, t, dt, w, q, lw, lc, g, lf = run_case
+    _against_oracle_adjoint(sc, g, lw, lc, lf, N_RUN, ("E", "nu", "rho0", "mu_s", "cohesion",
+                                                      "av_gamma"))
+
+
+def test_six_dof_gradients_match_the_oracle_adjoint(six_dof_case):
+    sc, g, lw, lc, lf = six_dof_case
+    _against_oracle_adjoint(sc, g, lw, lc, lf, N_RUN, ("E", "nu", "rho0", "mu_s", "av_gamma"))
+
+
+def test_mu_i_gradients_match_the_oracle_adjoint():
+    sc = _wheel(seed=71, nx=16, ny=12, nz=6)
+    sc.params["skin"] = 0.0
+    sc.params["mu_2"] = sc.params["mu_s"] + 0.3
+    sc.bodies[0].pose[2] -= 0.004
+    t = crm.from_scene(sc)
+    t.adjoint_forward(sc.dt, N_RUN, EVERY)
+    rng = np.random.default_rng(13)
+    lw = rng.normal(size=(N_RUN, 1, 6))
+    lc = rng.normal(size=(N_RUN, 1, 3)) * 1e3
+    lf = _final_weights(sc.x.shape[0], 14)
+    g = t.adjoint_backward(lw, lc, lf["x"], lf["u"], lf["sig"], lf["rho"])
+    _against_oracle_adjoint(sc, g, lw, lc, lf, N_RUN, ("E", "mu_s", "mu_2", "I0", "grain_d",
+                                                      "cohesion"))
