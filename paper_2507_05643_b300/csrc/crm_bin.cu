@@ -383,11 +383,11 @@ __device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *_
 }
 
 // LANES lanes share a particle.  One lane walks the 18 rows (fluid then marker
-// segment, each dz-major) in order, writing as it goes.  With four, the rows are
+// segment, each dz-major) in order, writing as it goes.  With more, the rows are
 // dealt out round robin; the lanes count their rows, agree on the rows' offsets
-// by shuffles, and write their rows' entries there: the same list at about a
-// quarter of the serial latency but twice the reads, which pays only while the
-// grid is smaller than the GPU (launch_neighbors picks).
+// by shuffles, and write their rows' entries there: the same list at a fraction
+// of the serial latency but twice the reads, which pays only while the grid is
+// small against the GPU (launch_neighbors picks).
 template <int LANES>
 __global__ void __launch_bounds__(kBlock)
 k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restrict__ start,
@@ -479,9 +479,11 @@ void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *st
 void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
                       uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st)
 {
-    // four lanes per particle while they still fit one wave of the GPU's threads
-    if ((int64_t)p.capN * 4 <= 148LL * 2048)
-        k_neighbors<4><<<grid_for((int64_t)p.capN * 4), kBlock, 0, st>>>(p, pos, start, nbr, nnb,
+    // lanes per particle: eight up to four waves of the GPU's threads (each lane
+    // walks at most three rows of the stencil: on the 25,600-particle active set of
+    // the rover strip 76 against 82 us with four lanes, 90 with sixteen), else one
+    if ((int64_t)p.capN * 4 <= 148LL * 2048 * 4)
+        k_neighbors<8><<<grid_for((int64_t)p.capN * 8), kBlock, 0, st>>>(p, pos, start, nbr, nnb,
                                                                          cap, r2cut, err);
     else
         k_neighbors<1><<<grid_for(p.capN), kBlock, 0, st>>>(p, pos, start, nbr, nnb, cap, r2cut,

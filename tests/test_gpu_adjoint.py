@@ -556,8 +556,9 @@ def test_run_six_dof_gradient_matches_oracle_differences(six_dof_case, name):
 # one direction.  Bars: the relative L2 error of each array, the largest entry
 # error against the array's largest entry, each parameter gradient against its
 # own size (FP32 sweep of an FP32 trajectory against FP64 throughout).
-ORACLE_REL = 2e-3        # relative L2 error of an array / error of a parameter gradient
-ORACLE_MAX = 1e-2        # largest entry error / largest entry
+# (measured on a B300: 1e-7 to 9e-7 everywhere but the six-DOF orientation, 7.5e-6)
+ORACLE_REL = 5e-5        # relative L2 error of an array / error of a parameter gradient
+ORACLE_MAX = 5e-5        # largest entry error / largest entry
 
 
 def _against_oracle_adjoint(sc, g, lw, lc, lf, n_steps, params):
