@@ -14,6 +14,11 @@ map, FP64 wrench and body update.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl crm|reference]
 
+The line also carries the adjoint measurement on the differentiable wheel test
+(30,000 SPH particles, 400 steps): recorded forward, reverse sweep, their ratio to
+the plain forward step, the gradients, and as its CPU baseline the oracle's own
+FP64 adjoint timed over a few steps on the host cores.
+
 Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
 replica of the workload ("replicas only": the method has no exchange step on
 one terrain here), so value = all ranks' particle-steps / max-over-ranks time.
@@ -281,7 +286,30 @@ def _phi_grads(g, mu_s: float, body=None) -> dict:
     return out
 
 
-def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = False) -> dict:
+def _oracle_adjoint_sample(sc, n: int) -> dict:
+    """The oracle's own FP64 adjoint (autograd over its PyTorch CPU restatement of
+    the step) timed on the host cores over the first n steps of the same test:
+    forward with the tape, then the reverse sweep of the drawbar-pull objective."""
+    import numpy as np
+    import torch
+
+    from oracle import adjoint as oadj
+    r = oadj.Run(sc, "cells")
+    t0 = time.perf_counter()
+    r.forward(sc.dt, n)
+    t1 = time.perf_counter()
+    lw = np.zeros((n, 1, 6))
+    lw[:, 0, 0] = 1.0 / n
+    r.backward(lw)
+    t2 = time.perf_counter()
+    return {"value": 1e3 * (t2 - t1) / n, "unit": "ms per step of the reverse sweep",
+            "forward_ms_per_step": 1e3 * (t1 - t0) / n, "cores": torch.get_num_threads(),
+            "kind": "oracle", "what": "the oracle's own FP64 adjoint (autograd, CPU)",
+            "sample": f"the first {n} steps of the differentiable wheel test"}
+
+
+def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = False,
+                 oracle_steps: int = 0) -> dict:
     """Adjoint cost against the forward step on the differentiable wheel test, and
     the gradients of both objectives (optionally against FP64 central differences
     of the oracle, relative step 1e-4, lists rebuilt as the oracle does)."""
@@ -361,6 +389,8 @@ def adjoint_line(stream, dev, n_steps: int = 400, every: int = 20, fd: bool = Fa
                   "host wall time of crm_adjoint_forward (its second call, tape allocated) and "
                   "crm_adjoint_backward (re-run of every segment + reverse sweep)",
     }
+    if oracle_steps > 0:
+        out["cpu_baseline"] = _oracle_adjoint_sample(sc, oracle_steps)
     if fd:
         out["fd_check"] = _adjoint_fd(sc, n_steps, grads)
     return out
@@ -429,7 +459,8 @@ def run_adjoint(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    adj = adjoint_line(stream, dev, n_steps=args.adjoint_steps, fd=args.adjoint_fd)
+    adj = adjoint_line(stream, dev, n_steps=args.adjoint_steps, fd=args.adjoint_fd,
+                       oracle_steps=args.oracle_adjoint_steps)
     line = {"metric": "adjoint step cost / forward step cost", "value": adj["adjoint_over_forward"],
             "unit": "ratio", "n_gpus": 1, "steps": args.adjoint_steps, "warmup": 4,
             "ms_per_step": adj["backward_ms_per_step"], "higher_is_better": False,
@@ -661,8 +692,9 @@ def run_crm(args):
                 f"boxes, dt=1e-4 s")
         line["config"]["skin"] = args.skin if args.skin is not None else 0.1
         if not args.no_adjoint and args.workload == "wheel_bin" and args.bin_scale == 1:
-            line["adjoint"] = adjoint_line(stream, dev, n_steps=args.adjoint_steps,
-                                           fd=args.adjoint_fd)
+            line["adjoint"] = adjoint_line(
+                stream, dev, n_steps=args.adjoint_steps, fd=args.adjoint_fd,
+                oracle_steps=0 if args.no_cpu_baseline or world > 1 else args.oracle_adjoint_steps)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -693,6 +725,9 @@ def main():
                     help="skip the adjoint-cost measurement on the differentiable wheel test")
     ap.add_argument("--adjoint-steps", type=int, default=400,
                     help="steps of the differentiable wheel test (the test is quoted at 400)")
+    ap.add_argument("--oracle-adjoint-steps", type=int, default=2,
+                    help="steps of the differentiable wheel test over which the oracle's own "
+                         "FP64 adjoint is timed on the host cores (0: skip; ~6 s per step)")
     ap.add_argument("--adjoint-fd", action="store_true",
                     help="also check its gradients against FP64 central differences of the "
                          "oracle (about 8 oracle runs of 400 steps)")
