@@ -96,6 +96,7 @@ struct PairAcc {
 };
 
 // One pair (i, j) with r = x_i - x_j, 0 < |r| < 2h, added to the sums of i.
+// V_j grad_i W_ij is formed once, so every sum is a chain of FMAs.
 __device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi, const float4 &ai,
                                            const float2 &bi, const float4 &vj, const float4 &aj,
                                            const float2 &bj, float rx, float ry, float rz,
@@ -104,30 +105,30 @@ __device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi,
     const float rinv = rsqrtf(r2);
     const float q = r2 * rinv * p.inv_h;
     const float f = kernel_dw_over_r(q, rinv, p);
-    const float gx = f * rx, gy = f * ry, gz = f * rz;          // grad_i W_ij
     const float Vj = __fdividef(p.m, vj.w);   // MUFU reciprocal: ~2 ulp
+    const float fv = f * Vj;
+    const float gx = fv * rx, gy = fv * ry, gz = fv * rz;       // V_j grad_i W_ij
     const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;   // u_ji
     // continuity (F2)
-    A.cont = fmaf(Vj, ux * gx + uy * gy + uz * gz, A.cont);
+    A.cont = fmaf(ux, gx, fmaf(uy, gy, fmaf(uz, gz, A.cont)));
     // momentum (F3): (sigma_i + sigma_j) . grad W
     const float sxx = ai.x + aj.x, syy = ai.y + aj.y, szz = ai.z + aj.z;
     const float sxy = ai.w + aj.w, sxz = bi.x + bj.x, syz = bi.y + bj.y;
-    A.mx = fmaf(Vj, sxx * gx + sxy * gy + sxz * gz, A.mx);
-    A.my = fmaf(Vj, sxy * gx + syy * gy + syz * gz, A.my);
-    A.mz = fmaf(Vj, sxz * gx + syz * gy + szz * gz, A.mz);
-    // velocity gradient (F2): L += V_j u_ji (x) grad W
-    const float vx = Vj * ux, vy = Vj * uy, vz = Vj * uz;
-    A.L[0] = fmaf(vx, gx, A.L[0]); A.L[1] = fmaf(vx, gy, A.L[1]); A.L[2] = fmaf(vx, gz, A.L[2]);
-    A.L[3] = fmaf(vy, gx, A.L[3]); A.L[4] = fmaf(vy, gy, A.L[4]); A.L[5] = fmaf(vy, gz, A.L[5]);
-    A.L[6] = fmaf(vz, gx, A.L[6]); A.L[7] = fmaf(vz, gy, A.L[7]); A.L[8] = fmaf(vz, gz, A.L[8]);
-    // artificial viscosity: v_ij . r_ij = -(u_ji . r_ij)
+    A.mx = fmaf(sxx, gx, fmaf(sxy, gy, fmaf(sxz, gz, A.mx)));
+    A.my = fmaf(sxy, gx, fmaf(syy, gy, fmaf(syz, gz, A.my)));
+    A.mz = fmaf(sxz, gx, fmaf(syz, gy, fmaf(szz, gz, A.mz)));
+    // velocity gradient (F2): L += u_ji (x) V_j grad W
+    A.L[0] = fmaf(ux, gx, A.L[0]); A.L[1] = fmaf(ux, gy, A.L[1]); A.L[2] = fmaf(ux, gz, A.L[2]);
+    A.L[3] = fmaf(uy, gx, A.L[3]); A.L[4] = fmaf(uy, gy, A.L[4]); A.L[5] = fmaf(uy, gz, A.L[5]);
+    A.L[6] = fmaf(uz, gx, A.L[6]); A.L[7] = fmaf(uz, gy, A.L[7]); A.L[8] = fmaf(uz, gz, A.L[8]);
+    // artificial viscosity: v_ij . r_ij = -(u_ji . r_ij), along grad W = f r
     if (p.av_mode != CRM_AV_NONE) {
         const float vr = -(ux * rx + uy * ry + uz * rz);
         if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-            const float fac = __fdividef(2.0f * p.av_c * vr, (vi.w + vj.w) * (r2 + p.xi2));
-            A.avx = fmaf(fac, gx, A.avx);
-            A.avy = fmaf(fac, gy, A.avy);
-            A.avz = fmaf(fac, gz, A.avz);
+            const float fa = f * __fdividef(2.0f * p.av_c * vr, (vi.w + vj.w) * (r2 + p.xi2));
+            A.avx = fmaf(fa, rx, A.avx);
+            A.avy = fmaf(fa, ry, A.avy);
+            A.avz = fmaf(fa, rz, A.avz);
         }
     }
 }
