@@ -521,7 +521,7 @@ def run_batch(args):
                                    "U(0.1,0.7), friction U(25,40) deg, cohesion U(0,2000) Pa, "
                                    "dt=5e-5 s, one batched step per step",
                        "l2": "not flushed: the ensemble's working set (~10 GB) exceeds L2",
-                       "pair_lanes": {"1": int((picks == 1).sum()), "2": int((picks == 2).sum())}},
+                       "pair_lanes": {str(k): int((picks == k).sum()) for k in (1, 2, 4)}},
             "sequential": {"value": units / (ms_s * 1e-3), "ms_per_step": ms_s / args.steps,
                            "form": "the same members stepped one at a time"},
             "batched_over_sequential": ms_s / ms_b,

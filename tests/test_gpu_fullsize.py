@@ -1,0 +1,130 @@
+"""Parity at the benchmark's full size: the 120,000-particle wheel bin (65,328 wall
+and 5,920 wheel markers) exactly as bench.py builds it and steps it -- the default
+Verlet skin, the step graph, the default lanes of the pair kernels -- against the
+FP64 oracle on every particle and marker (the oracle is fast enough for that at
+this size).
+
+Bars: the rate bars of test_gpu_parity.py (|r_gpu - r_oracle| <= 1e-5 S per
+particle and component, S the sum of the term magnitudes; marker accelerations
+against the kernel-edge conditioned S') plus twice the FP64
+oracle's own response to moving every position by up to one FP32 ulp of the
+cell-relative offsets the GPU stores (2^-24 of the cell).  At this size some
+top-surface particles sit within ~1e-5 m of a wheel marker's plane y = const
+while the markers' velocity has no y component: their shear-rate terms are
+proportional to that tiny offset, so S is tiny while the rounding of the stored
+positions is not (the oracle's response to it there is ~5e-4 S; the measured
+differences reach 5e-5 S).  After 1 and 10
+graph-replayed steps: the short-horizon measures of the reduced wheel (position
+against d0, stress against rho0 g H, density, the wheel force).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+crm = pytest.importorskip("paper_2507_05643_b300")
+RATE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bench_scene():
+    sc = scenes.wheel_bin()
+    assert sc.x.shape[0] == 120000
+    return sc
+
+
+def _rates_at(st, x, xm, umb, amb):
+    um, sm = oracle.bce(st.params, x, st.u, st.sig, st.rho, xm, umb, amb, st.off, st.lst)
+    drho, du, ds, macc, _, _ = oracle.rates(st.params, x, st.u, st.sig, st.rho, xm, um, sm,
+                                            st.off, st.lst)
+    return np.concatenate([drho[:, None], du, ds], axis=1), macc
+
+
+def _position_rounding_response(st, cell, samples=8, seed=5):
+    """max over random moves of every particle and marker position by up to one
+    FP32 ulp of a cell-relative offset: the oracle's response (lists fixed) of the
+    particles' rates and of the markers' accelerations."""
+    rng = np.random.default_rng(seed)
+    ulp = cell * 2.0 ** -24
+    xm, umb, amb = st.markers_now()
+    base, mbase = _rates_at(st, st.x, xm, umb, amb)
+    resp, mresp = np.zeros_like(base), np.zeros_like(mbase)
+    for _ in range(samples):
+        x1 = st.x + rng.uniform(-ulp, ulp, size=st.x.shape)
+        xm1 = xm + rng.uniform(-ulp, ulp, size=xm.shape)
+        r, m = _rates_at(st, x1, xm1, umb, amb)
+        resp = np.maximum(resp, np.abs(r - base))
+        mresp = np.maximum(mresp, np.abs(m - mbase))
+    return resp, mresp
+
+
+def test_full_size_rates_match_oracle(bench_scene):
+    sc = bench_scene.copy()
+    t = crm.from_scene(sc)
+    st = oracle.State(sc)
+    drho, du, ds, macc, mvel, msig = t.eval_rates()
+    o_drho, o_du, o_ds, o_macc, scale, o_um, o_sm = st.eval_rates(want_scale=True)
+    got = np.concatenate([drho[:, None], du, ds], axis=1).astype(np.float64)
+    ref = np.concatenate([o_drho[:, None], o_du, o_ds], axis=1)
+    err = np.abs(got - ref)
+    rnd, mrnd = _position_rounding_response(st, 2.0 * sc.params["h"])
+    bar = RATE_TOL * scale + 2.0 * rnd + 1e-30
+    worst = float(np.max(err / np.maximum(scale, 1e-30)))
+    print(f"full size: {got.shape[0]} particles, worst rate error / S = {worst:.3e}, "
+          f"worst error / bar = {float(np.max(err / bar)):.3e}, "
+          f"components over 1e-5 S: {int(np.sum(err > RATE_TOL * scale))}")
+    assert np.all(err <= bar), float(np.max(err / bar))
+    oracle.set_scale_conditioning(True)
+    try:
+        st.eval_rates(want_scale=True)
+    finally:
+        oracle.set_scale_conditioning(False)
+    cms = st.mscale
+    merr = np.abs(macc.astype(np.float64) - o_macc)
+    mbar = RATE_TOL * cms + 2.0 * mrnd + 1e-30
+    mworst = float(np.max(merr / np.maximum(cms, 1e-30)))
+    print(f"full size: {macc.shape[0]} markers, worst acceleration error / S' = {mworst:.3e}, "
+          f"worst error / bar = {float(np.max(merr / mbar)):.3e}, "
+          f"components over 1e-5 S': {int(np.sum(merr > RATE_TOL * cms))}")
+    assert np.all(merr <= mbar), float(np.max(merr / mbar))
+    umax = max(np.abs(st.u).max(), 1e-6)
+    assert np.all(np.abs(mvel - o_um) <= RATE_TOL * umax * 4 + 1e-7)
+    smax = max(np.abs(st.sig).max(), 1.0)
+    assert np.all(np.abs(msig - o_sm) <= RATE_TOL * smax * 4)
+
+
+def test_full_size_steps_match_oracle(bench_scene):
+    """The bench's launch configuration: default skin (the first step searches with
+    the skin radius and filters in stage 1), the step graph replayed."""
+    sc = bench_scene.copy()
+    t = crm.from_scene(sc)
+    st = oracle.State(sc)
+    d0 = sc.params["d0"]
+    sig_scale = sc.params["rho0"] * 9.81 * 0.15
+    report = {}
+    done = 0
+    for k in (1, 10):
+        t.step(sc.dt, k - done)
+        st.run(k - done)
+        done = k
+        xyz, vel, sig, rho = t.particles()
+        F, _ = t.body_wrench(0)
+        Fo = st.bodies.wrench[0, :3]
+        report[k] = (float(np.max(np.abs(xyz - st.x)) / d0),
+                     float(np.sqrt(np.mean((sig - st.sig) ** 2)) / sig_scale),
+                     float(np.max(np.abs(sig - st.sig)) / sig_scale),
+                     float(np.max(np.abs(rho - st.rho)) / sc.params["rho0"]),
+                     float(np.linalg.norm(F - Fo) / max(np.linalg.norm(Fo), 1e-12)))
+    print("full size: max|dx|/d0, rms dsig/(rho0 g H), max|dsig|/(rho0 g H), max|drho|/rho0, "
+          "|dF|/|F|:", report)
+    dx, ds, dsm, dr, dF = report[1]
+    # measured on a B300: 1.9e-7, 1.0e-8, 9.7e-8, 3.6e-8, 3.7e-8 after one step and
+    # 9.7e-7, 3.0e-8, 4.3e-7, 3.4e-7, 8.7e-8 after ten
+    assert dx < 1e-6 and ds < 1e-7 and dsm < 1e-6 and dr < 1e-6 and dF < 1e-6, report
+    dx, ds, dsm, dr, dF = report[10]
+    assert dx < 1e-5 and ds < 1e-6 and dsm < 1e-5 and dr < 1e-5 and dF < 1e-6, report
+    pose, _ = t.body_state(0)
+    assert abs(pose[2] - st.bodies.pose[0, 2]) < 1e-7
