@@ -200,6 +200,29 @@ int crm_get_particles(crm_terrain *t, int64_t cap, double *xyz, float *vel, floa
 /* Body force and torque (about the body centre) of the last step, FP64. */
 int crm_get_body_wrench(crm_terrain *t, int32_t body, double force[3], double torque[3]);
 
+/* Global FP64 diagnostics of the SPH particles (every particle of the terrain,
+ * Active or not; the precision pattern: FP32 state, FP64 global sums), with the
+ * particle mass m = rho0 d0^3 of the readings (Sec. 2.2):
+ *   out[CRM_DIAG_COUNT]     number of SPH particles
+ *   out[CRM_DIAG_MASS]      sum m
+ *   out[CRM_DIAG_VOLUME]    sum m / rho (rho the particle's density)
+ *   out[CRM_DIAG_MOMENTUM]  sum m u (3 entries, x y z)
+ *   out[CRM_DIAG_ANGULAR]   sum m x (x) u about the world origin (3 entries), x the
+ *                           absolute FP64 position rebuilt from the cell-relative one
+ *   out[CRM_DIAG_KINETIC]   sum m |u|^2 / 2
+ * out: caller-owned host array of CRM_NUM_DIAG doubles.  Summed on the device in
+ * FP64 in a fixed order: the same state gives the same bits.  Before the first
+ * step the sums come from the host copies of the inputs.  Synchronises the
+ * terrain's stream.  CRM_EINVAL for a null handle or output. */
+#define CRM_DIAG_COUNT 0
+#define CRM_DIAG_MASS 1
+#define CRM_DIAG_VOLUME 2
+#define CRM_DIAG_MOMENTUM 3
+#define CRM_DIAG_ANGULAR 6
+#define CRM_DIAG_KINETIC 9
+#define CRM_NUM_DIAG 10
+int crm_get_diagnostics(crm_terrain *t, double *out);
+
 /* Active / extended-active SPH particles and BCE markers processed in the
  * last step (without active boxes every SPH particle is active). */
 int crm_get_counts(crm_terrain *t, int64_t *n_active, int64_t *n_extended, int64_t *n_bce);

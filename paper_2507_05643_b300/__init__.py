@@ -100,6 +100,7 @@ _sig("crm_step", C.c_int, [_T, C.c_double, _i32])
 _sig("crm_sync", C.c_int, [_T])
 _sig("crm_get_particles", C.c_int, [_T, _i64, _vp, _vp, _vp, _vp, C.POINTER(_i64)])
 _sig("crm_get_body_wrench", C.c_int, [_T, _i32, _vp, _vp])
+_sig("crm_get_diagnostics", C.c_int, [_T, _vp])
 _sig("crm_get_counts", C.c_int, [_T, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)])
 _sig("crm_eval_rates", C.c_int, [_T, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp])
 _sig("crm_get_neighbors", C.c_int, [_T, _i64, _vp, _vp, C.POINTER(_i64)])
@@ -134,7 +135,7 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_set_body_motion", "crm_get_body_state", "crm_set_body_inertia",
            "crm_set_body_load", "crm_add_active_box", "crm_step", "crm_set_pair_lanes",
            "crm_batch_create", "crm_batch_step", "crm_batch_autotune", "crm_batch_destroy",
-           "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_counts",
+           "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_diagnostics", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
            "crm_profile_reset", "crm_profile_read", "crm_bin_points_noalloc",
@@ -322,6 +323,15 @@ class Terrain:
         f, t = np.zeros(3), np.zeros(3)
         self._check(_lib.crm_get_body_wrench(self._h, int(body), _ptr(f), _ptr(t)))
         return f, t
+
+    def diagnostics(self) -> dict:
+        """FP64 global sums over the SPH particles (crm_get_diagnostics): count,
+        mass, volume, momentum (3), angular momentum about the origin (3), kinetic
+        energy."""
+        out = np.zeros(10)
+        self._check(_lib.crm_get_diagnostics(self._h, _ptr(out)))
+        return {"count": out[0], "mass": out[1], "volume": out[2], "momentum": out[3:6].copy(),
+                "angular_momentum": out[6:9].copy(), "kinetic_energy": out[9]}
 
     def counts(self) -> Tuple[int, int, int]:
         a, e, b = _i64(), _i64(), _i64()

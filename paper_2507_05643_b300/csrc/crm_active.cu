@@ -444,4 +444,70 @@ void launch_export_master(const DevParams &p, StageArrays M, const uint32_t *mpi
 
 size_t box_frame_bytes() { return sizeof(BoxFrame); }
 
+// ---------------------------------------------------------------------------
+// FP64 diagnostics of the SPH particles: the state is FP32, its global sums are
+// FP64 (count, mass, volume sum m / rho, linear momentum sum m u, angular
+// momentum about the world origin sum m x (x) u with absolute FP64 positions,
+// kinetic energy sum m |u|^2 / 2).  Deterministic: a fixed grid walking the
+// slots with a fixed stride, a fixed tree inside each block, then one warp
+// summing the block partials in block order.
+constexpr int kDiagBlocks = 296;
+
+__global__ void __launch_bounds__(kBlock)
+k_diag_partial(DevParams p, StageArrays S, const int *__restrict__ n_dev, int n_host, double m,
+               double *__restrict__ partial)
+{
+    const int n = n_dev != nullptr ? __ldg(n_dev) : n_host;
+    double v[CRM_NUM_DIAG];
+#pragma unroll
+    for (int k = 0; k < CRM_NUM_DIAG; ++k) v[k] = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double x[3];
+        abs_pos(p, S.pos[s], x);
+        const float4 u4 = S.vel[s];
+        const double ux = u4.x, uy = u4.y, uz = u4.z;
+        v[0] += 1.0;
+        v[1] += m;
+        v[2] += m / (double)u4.w;
+        v[3] += m * ux;
+        v[4] += m * uy;
+        v[5] += m * uz;
+        v[6] += m * (x[1] * uz - x[2] * uy);
+        v[7] += m * (x[2] * ux - x[0] * uz);
+        v[8] += m * (x[0] * uy - x[1] * ux);
+        v[9] += 0.5 * m * (ux * ux + uy * uy + uz * uz);
+    }
+    __shared__ double red[kBlock / 32][CRM_NUM_DIAG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < CRM_NUM_DIAG; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane == 0) red[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < CRM_NUM_DIAG) {
+        double a = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) a += red[w][threadIdx.x];
+        partial[(size_t)blockIdx.x * CRM_NUM_DIAG + threadIdx.x] = a;
+    }
+}
+
+__global__ void k_diag_final(const double *__restrict__ partial, double *__restrict__ out)
+{
+    if (threadIdx.x >= CRM_NUM_DIAG) return;
+    double a = 0.0;
+    for (int b = 0; b < kDiagBlocks; ++b) a += partial[(size_t)b * CRM_NUM_DIAG + threadIdx.x];
+    out[threadIdx.x] = a;
+}
+
+size_t diag_scratch_doubles() { return (size_t)(kDiagBlocks + 1) * CRM_NUM_DIAG; }
+
+void launch_diagnostics(const DevParams &p, StageArrays S, const int *n_dev, int n_host, double m,
+                        double *scratch, cudaStream_t st)
+{
+    k_diag_partial<<<kDiagBlocks, kBlock, 0, st>>>(p, S, n_dev, n_host, m, scratch);
+    k_diag_final<<<1, 32, 0, st>>>(scratch, scratch + (size_t)kDiagBlocks * CRM_NUM_DIAG);
+}
+
 }  // namespace crm

@@ -1586,6 +1586,42 @@ int crm_cosim_step(crm_terrain *t, const double *pose_in, const double *twist_in
     return CRM_OK;
 }
 
+int crm_get_diagnostics(crm_terrain *t, double *out)
+{
+    if (!t || !out) return CRM_EINVAL;
+    const double m = t->P.rho0 * t->P.d0 * t->P.d0 * t->P.d0;
+    const int64_t n = t->nFtot;
+    if (!t->committed) {
+        for (int k = 0; k < CRM_NUM_DIAG; ++k) out[k] = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double *x = &t->hx[3 * i], *u = &t->hu[3 * i];
+            out[CRM_DIAG_COUNT] += 1.0;
+            out[CRM_DIAG_MASS] += m;
+            out[CRM_DIAG_VOLUME] += m / t->hr[i];
+            for (int k = 0; k < 3; ++k) out[CRM_DIAG_MOMENTUM + k] += m * u[k];
+            out[CRM_DIAG_ANGULAR + 0] += m * (x[1] * u[2] - x[2] * u[1]);
+            out[CRM_DIAG_ANGULAR + 1] += m * (x[2] * u[0] - x[0] * u[2]);
+            out[CRM_DIAG_ANGULAR + 2] += m * (x[0] * u[1] - x[1] * u[0]);
+            out[CRM_DIAG_KINETIC] += 0.5 * m * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        }
+        return CRM_OK;
+    }
+    const size_t nd = diag_scratch_doubles();
+    double *buf = nullptr;
+    CRM_CUDA(t, cudaMallocAsync((void **)&buf, nd * sizeof(double), t->st));
+    if (t->active) {
+        scatter_back(t);   // the master store holds every particle, Active or not
+        launch(t, K_EXPORT, [&] { launch_diagnostics(t->dp, t->Mst, nullptr, (int)n, m, buf, t->st); });
+    } else {
+        launch(t, K_EXPORT, [&] { launch_diagnostics(t->dp, t->A[t->cur], t->dp.sizes, 0, m, buf,
+                                                     t->st); });
+    }
+    int rc = download(t, out, buf + (nd - CRM_NUM_DIAG), CRM_NUM_DIAG);
+    cudaFreeAsync(buf, t->st);
+    if (rc) return rc;
+    return latched_error(t);   // synchronises the stream
+}
+
 int crm_get_body_wrench(crm_terrain *t, int32_t body, double force[3], double torque[3])
 {
     if (!t) return CRM_EINVAL;

@@ -450,5 +450,10 @@ void launch_scatter_back(const DevParams &p, StageArrays W, const uint32_t *wpid
                          cudaStream_t st);
 void launch_export_master(const DevParams &p, StageArrays M, const uint32_t *mpid, int n,
                           double *xyz, float *vel, float *sig, float *rho, cudaStream_t st);
+// FP64 global sums of the first n SPH slots of S (n from n_dev when non-null):
+// scratch holds diag_scratch_doubles() doubles, the CRM_NUM_DIAG results last.
+size_t diag_scratch_doubles();
+void launch_diagnostics(const DevParams &p, StageArrays S, const int *n_dev, int n_host, double m,
+                        double *scratch, cudaStream_t st);
 
 }  // namespace crm

@@ -445,3 +445,60 @@ def test_column_settles_to_a_lithostatic_state():
     k0 = p["nu"] / (1 - p["nu"])
     ratio = float(np.sum(sxy) / np.sum(szz))
     assert abs(ratio - k0) <= 0.2 * k0, ratio
+
+
+# --------------------------------------------------------------------------
+# FP64 global diagnostics (crm_get_diagnostics)
+
+def _diag_of(x, u, rho, m):
+    """The diagnostics' definitions in FP64 numpy."""
+    x, u, rho = (np.asarray(a, np.float64) for a in (x, u, rho))
+    return {"count": float(x.shape[0]), "mass": m * x.shape[0], "volume": float(np.sum(m / rho)),
+            "momentum": m * u.sum(axis=0), "angular_momentum": m * np.cross(x, u).sum(axis=0),
+            "kinetic_energy": 0.5 * m * float(np.sum(u * u))}
+
+
+@pytest.mark.parametrize("active", [False, True])
+def test_diagnostics_are_fp64_sums_of_the_state_and_track_the_oracle(active):
+    """The device's FP64 sums equal FP64 sums of the exported state (the same FP32
+    values: only the summation order differs), repeat bit for bit, and after 10 steps
+    differ from the FP64 oracle's by the stated amounts per quantity."""
+    sc = scenes.wheel_bin(seed=61, nx=40, ny=24, nz=10, wheel_radius=0.08, wheel_width=0.08,
+                          n_grousers=8, wheel_x=0.2)
+    sc.bodies[0].pose[2] -= 0.005
+    rng = np.random.default_rng(61)
+    sc.u = rng.uniform(-0.05, 0.05, size=sc.u.shape)
+    if active:
+        sc.boxes.append(scenes.ActiveBox(0, np.array([0.12, 0.08, 0.12]), np.zeros(3)))
+    m = sc.params["rho0"] * sc.params["d0"] ** 3
+    t = crm.from_scene(sc)
+    d0 = t.diagnostics()                     # before the first step: the host inputs
+    ref0 = _diag_of(sc.x, sc.u, sc.rho, m)
+    for k in ref0:
+        np.testing.assert_allclose(d0[k], ref0[k], rtol=1e-12, atol=1e-15)
+    t.step(sc.dt, 10)
+    d = t.diagnostics()
+    d_again = t.diagnostics()
+    for k in d:
+        np.testing.assert_array_equal(d[k], d_again[k])
+    x, u, _, rho = t.particles()
+    mine = _diag_of(x, u, rho, m)
+    for k in mine:        # summation order only
+        np.testing.assert_allclose(d[k], mine[k], rtol=1e-12, atol=1e-12 * m)
+    st = oracle.State(sc)
+    st.run(10)
+    orc = _diag_of(st.x, st.u, st.rho, m)
+    umag = m * float(np.sum(np.abs(st.u)))
+    xu = m * float(np.sum(np.abs(np.cross(st.x, st.u))))
+    assert d["count"] == orc["count"] and abs(d["mass"] - orc["mass"]) <= 1e-12 * orc["mass"]
+    # measured on a B300: volume 7e-10, momentum 7.7e-9, angular momentum 7.6e-9, kinetic
+    # energy 7.3e-9 (relative to the sums of magnitudes) after 10 steps
+    assert abs(d["volume"] - orc["volume"]) <= 1e-8 * orc["volume"]
+    assert np.all(np.abs(d["momentum"] - orc["momentum"]) <= 1e-7 * umag)
+    assert np.all(np.abs(d["angular_momentum"] - orc["angular_momentum"]) <= 1e-7 * xu)
+    assert abs(d["kinetic_energy"] - orc["kinetic_energy"]) <= 1e-7 * orc["kinetic_energy"]
+    print("diagnostics against the oracle after 10 steps (relative):",
+          {"volume": abs(d["volume"] - orc["volume"]) / orc["volume"],
+           "momentum": float(np.max(np.abs(d["momentum"] - orc["momentum"]))) / umag,
+           "angular_momentum": float(np.max(np.abs(d["angular_momentum"] - orc["angular_momentum"]))) / xu,
+           "kinetic_energy": abs(d["kinetic_energy"] - orc["kinetic_energy"]) / orc["kinetic_energy"]})
