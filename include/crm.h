@@ -361,6 +361,15 @@ int crm_capacity_policy(int64_t need, int64_t cap, int64_t step, double growth,
  * are split between the lanes and combined, so only their order changes). */
 int crm_set_pair_lanes(crm_terrain *t, int32_t lanes);
 
+/* Cell tiles of the sort order (Sec. 3.1 steps 1-2): cells are keyed tile by
+ * tile, tiles of nx x ny x nz cells (powers of two up to 8 x 4 x 4; 1 x 1 x 1 =
+ * the row-major order c = (z Y + y) X + x), so that consecutive sorted slots
+ * form compact 3-D pieces of the terrain.  Takes effect at the next step (which
+ * re-sorts).  A speed knob with no effect on the method: neighbour sets are
+ * unchanged, only the slot order and the order of the pair sums. */
+int crm_set_cell_tile(crm_terrain *t, int32_t nx, int32_t ny, int32_t nz);
+
+
 /* ------------------------------------------------------------------------
  * Batches (an ensemble of independent terrains, e.g. many single-wheel bins of
  * uneven size; the paper runs one terrain at a time, this is the library's own

@@ -89,6 +89,7 @@ _sig("crm_set_body_motion", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_get_body_state", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_set_body_inertia", C.c_int, [_T, _i32, _vp])
 _sig("crm_set_pair_lanes", C.c_int, [_T, _i32])
+_sig("crm_set_cell_tile", C.c_int, [_T, _i32, _i32, _i32])
 _B = C.c_void_p
 _sig("crm_batch_create", C.c_int, [_i32, C.POINTER(_T), _vp, C.POINTER(_B)])
 _sig("crm_batch_step", C.c_int, [_B, _vp, _i32])
@@ -133,7 +134,7 @@ KERNEL_NAMES = tuple(_lib.crm_kernel_name(k).decode() for k in range(NUM_KERNELS
 EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create", "crm_destroy",
            "crm_last_error", "crm_add_sph", "crm_add_fixed_bce", "crm_add_rigid_body",
            "crm_set_body_motion", "crm_get_body_state", "crm_set_body_inertia",
-           "crm_set_body_load", "crm_add_active_box", "crm_step", "crm_set_pair_lanes",
+           "crm_set_body_load", "crm_add_active_box", "crm_step", "crm_set_pair_lanes", "crm_set_cell_tile",
            "crm_batch_create", "crm_batch_step", "crm_batch_autotune", "crm_batch_destroy",
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_diagnostics", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
@@ -268,6 +269,9 @@ class Terrain:
 
     def set_pair_lanes(self, lanes: int):
         self._check(_lib.crm_set_pair_lanes(self._h, int(lanes)))
+
+    def set_cell_tile(self, nx: int, ny: int, nz: int):
+        self._check(_lib.crm_set_cell_tile(self._h, int(nx), int(ny), int(nz)))
 
     def set_body_inertia(self, body: int, inertia):
         self._check(_lib.crm_set_body_inertia(self._h, int(body), _ptr(_c(inertia))))

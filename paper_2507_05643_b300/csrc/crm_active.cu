@@ -98,8 +98,8 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
     if (all_active || nbox == 0) {
         for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = G[k] - 1; }
     }
-    const int64_t cells = (int64_t)max(hi[0] - lo[0] + 1, 1) * max(hi[1] - lo[1] + 1, 1)
-                          * max(hi[2] - lo[2] + 1, 1);
+    const int64_t cells = key_cells(max(hi[0] - lo[0] + 1, 1), max(hi[1] - lo[1] + 1, 1),
+                                    max(hi[2] - lo[2] + 1, 1));
     if (hi[0] < lo[0] || hi[1] < lo[1] || hi[2] < lo[2]) {   // boxes outside the grid
         for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; }
     }
@@ -403,7 +403,7 @@ void launch_activity(const DevParams &p, int nbox, const void *frames, const int
                      const int *fixed_order, int all_active, int64_t cand_cap, uint32_t *include,
                      uint8_t *kind, int *counts, const int *abort_flag, cudaStream_t st)
 {
-    const unsigned g = (unsigned)std::min<int64_t>(grid_for(cand_cap), 148 * 16);
+    const unsigned g = (unsigned)std::min<int64_t>(grid_for(cand_cap), (int64_t)p.n_sm * 16);
     k_activity<<<g, kBlock, 0, st>>>(p, nbox, (const BoxFrame *)frames, ranges, rinfo, mpos, mloc,
                                      fixed_order, all_active, cand_cap, include, kind, counts,
                                      abort_flag);
@@ -423,7 +423,7 @@ void launch_gather(const DevParams &p, const int *ranges, const int *rinfo,
                    int64_t cand_cap, StageArrays W, uint32_t *wpid, const int *counts,
                    const int *abort_flag, cudaStream_t st)
 {
-    const unsigned g = (unsigned)std::min<int64_t>(grid_for(cand_cap + n_body_markers), 148 * 16);
+    const unsigned g = (unsigned)std::min<int64_t>(grid_for(cand_cap + n_body_markers), (int64_t)p.n_sm * 16);
     k_gather<<<g, kBlock, 0, st>>>(p, ranges, rinfo, kind, slot, M, mpid, fixed_order,
                                    body_markers, n_body_markers, n_fluid_total, cand_cap, W, wpid,
                                    counts, abort_flag);

@@ -90,6 +90,7 @@ struct crm_terrain {
     bool graphs = true;
     // Verlet skin (non-active runs with skin > 0)
     bool skin_on = false;
+    int tile_log2[3] = {0, 0, 0};   // cell tiles of the sort order (crm_set_cell_tile)
     uint32_t *sk_nbr = nullptr, *sk_nnb = nullptr;
     float4 *xref = nullptr;
     int *gate = nullptr;
@@ -288,6 +289,19 @@ int make_devparams(crm_terrain *t)
     d.dmin_z = P.domain_min[2];
     d.cell_d = cell;
     d.pair_lanes = P.pair_lanes;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess
+            || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess
+            || nsm < 1) {
+            cudaGetLastError();
+            nsm = 148;
+        }
+        d.n_sm = nsm;
+    }
+    d.tbx = t->tile_log2[0];
+    d.tby = t->tile_log2[1];
+    d.tbz = t->tile_log2[2];
     d.maxnb = P.max_neighbors;
     d.sk_r2 = (float)(cell * cell);
     d.disp_thr2 = (float)(0.95 * skin * P.h * 0.95 * skin * P.h);
@@ -494,8 +508,8 @@ void estimate_active(crm_terrain *t, const std::vector<int> &colF_h, const std::
         if (xb >= xa) cand += colF_h[xb + 1] - colF_h[xa] + colM_h[xb + 1] - colM_h[xa];
         fluid += (int64_t)(vol / (t->P.d0 * t->P.d0 * t->P.d0));
     }
-    cells = 1;
-    for (int k = 0; k < 3; ++k) cells *= std::max(hi[k] - lo[k] + 1, 1);
+    cells = key_cells(std::max(hi[0] - lo[0] + 1, 1), std::max(hi[1] - lo[1] + 1, 1),
+                      std::max(hi[2] - lo[2] + 1, 1));
 }
 
 int commit(crm_terrain *t)
@@ -540,7 +554,7 @@ int commit(crm_terrain *t)
         const double *x = &t->hmloc[3 * a];
         t->hbodies[b].rmax = std::max(t->hbodies[b].rmax, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
     }
-    const int64_t full_cells = (int64_t)d.GX * d.GY * d.GZ;
+    const int64_t full_cells = key_cells(d.GX, d.GY, d.GZ);
     cudaStream_t st = t->st;
     t->n_bodym = (int)std::count_if(t->hmbody.begin(), t->hmbody.end(), [](int b) { return b >= 0; });
 
@@ -1744,6 +1758,36 @@ int crm_get_neighbors(crm_terrain *t, int64_t cap, int64_t *offset, int32_t *lis
         std::sort(list + o, list + o + nnb[s]);
     }
     return CRM_OK;
+}
+
+// The next step re-sorts and searches whatever the skin test says (a change
+// of the sort order makes the cell ranges of the last search stale).
+static int force_search(crm_terrain *t)
+{
+    t->lists_valid = false;
+    if (!t->committed || !t->skin_on) return CRM_OK;
+    static const int one = 1;
+    CRM_CUDA(t, cudaMemcpyAsync(t->gate + GATE_FORCE, &one, sizeof(int), cudaMemcpyHostToDevice,
+                                t->st));
+    CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    return CRM_OK;
+}
+
+int crm_set_cell_tile(crm_terrain *t, int32_t nx, int32_t ny, int32_t nz)
+{
+    if (!t) return CRM_EINVAL;
+    auto lg = [](int v, int mx) { for (int k = 0; (1 << k) <= mx; ++k) if ((1 << k) == v) return k; return -1; };
+    const int bx = lg(nx, kTileX), by = lg(ny, kTileY), bz = lg(nz, kTileZ);
+    if (bx < 0 || by < 0 || bz < 0)
+        return t->fail(CRM_EINVAL, "crm_set_cell_tile: powers of two up to 8 x 4 x 4");
+    t->tile_log2[0] = bx;
+    t->tile_log2[1] = by;
+    t->tile_log2[2] = bz;
+    t->dp.tbx = bx;
+    t->dp.tby = by;
+    t->dp.tbz = bz;
+    t->drop_graphs();   // the captured launches hold the old shape
+    return force_search(t);
 }
 
 int crm_set_pair_lanes(crm_terrain *t, int32_t lanes)

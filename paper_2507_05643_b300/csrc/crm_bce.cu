@@ -249,11 +249,11 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
         float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
         float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
-        e_nx = q < nn ? __ldg(row + (size_t)q * p.ell) : 0u;
+        e_nx = q < nn ? ld_list(row + (size_t)q * p.ell) : 0u;
         for (int r = 0; r < rounds; ++r) {
             const int k = r * kBceLanes + q;
             const uint32_t e = e_nx;
-            if (k + kBceLanes < nn) e_nx = __ldg(row + (size_t)(k + kBceLanes) * p.ell);
+            if (k + kBceLanes < nn) e_nx = ld_list(row + (size_t)(k + kBceLanes) * p.ell);
             bool keep = false;
             float W = 0.f;
             float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), aj = vj;
@@ -322,11 +322,11 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
             const int n2 = (ACCEL == 2 || body >= 0) ? nn : 0;
             const int rounds2 = __reduce_max_sync(0xffffffffu, (n2 + kBceLanes - 1) / kBceLanes);
             float mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
-            e_nx = q < n2 ? __ldg(row + (size_t)q * p.ell) : 0u;
+            e_nx = q < n2 ? ld_list(row + (size_t)q * p.ell) : 0u;
             for (int r = 0; r < rounds2; ++r) {
                 const int k = r * kBceLanes + q;
                 const uint32_t e = e_nx;
-                if (k + kBceLanes < n2) e_nx = __ldg(row + (size_t)(k + kBceLanes) * p.ell);
+                if (k + kBceLanes < n2) e_nx = ld_list(row + (size_t)(k + kBceLanes) * p.ell);
                 if (k >= n2) continue;
                 const uint32_t j = e & kIndexMask;
                 const float4 sh = lut[e >> kIndexBits];

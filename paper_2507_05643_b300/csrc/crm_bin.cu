@@ -268,8 +268,7 @@ __global__ void k_keys(DevParams p, float4 *__restrict__ pos, const uint32_t *__
         ix = lx + W.x0; iy = ly + W.y0; iz = lz + W.z0;
     }
     if (bad) atomicOr(err, ERR_ESCAPED);
-    const uint32_t key = seg * p.M + ((uint32_t)lz * (uint32_t)W.Y + (uint32_t)ly) * (uint32_t)W.X
-                         + (uint32_t)lx;
+    const uint32_t key = seg * p.M + cell_key(lx, ly, lz, W, p);
     keys[i] = key;
     rank[i] = atomicAdd(&count[key], 1u);
     ps.w = __uint_as_float(encode_cell(ix, iy, iz, p));
@@ -350,14 +349,15 @@ __device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *_
     if (d2 >= lim2) return 0;
     const float R = sqrtf(lim2 - d2);
     const float sy = ps.y - (float)dy * cell, sz = ps.z - (float)dz * cell;
-    const uint32_t kb = seg * p.M + ((uint32_t)lz2 * (uint32_t)W.Y + (uint32_t)ly2) * (uint32_t)W.X;
+    const uint32_t kb = seg * p.M;
     const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
     int cnt = 0;
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
         const int lx2 = lx + dx;
         if (lx2 < 0 || lx2 >= W.X) continue;
-        const int jb = (int)start[kb + lx2], je = (int)start[kb + lx2 + 1];
+        const uint32_t key = kb + cell_key(lx2, ly2, lz2, W, p);
+        const int jb = (int)start[key], je = (int)start[key + 1];
         const float sx = ps.x - (float)dx * cell;
         const uint32_t tag = ((uint32_t)(dx + 1) | codeyz) << kIndexBits;
         // cells are x-sorted: in the left cell only a top run is within R in
@@ -482,7 +482,7 @@ void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *sta
     // lanes per particle: eight up to four waves of the GPU's threads (each lane
     // walks at most three rows of the stencil: on the 25,600-particle active set of
     // the rover strip 76 against 82 us with four lanes, 90 with sixteen), else one
-    if ((int64_t)p.capN * 4 <= 148LL * 2048 * 4)
+    if ((int64_t)p.capN * 4 <= (int64_t)p.n_sm * 2048 * 4)
         k_neighbors<8><<<grid_for((int64_t)p.capN * 8), kBlock, 0, st>>>(p, pos, start, nbr, nnb,
                                                                          cap, r2cut, err);
     else

@@ -54,6 +54,9 @@ struct DevParams {
     uint32_t ell;                         // stride of the neighbour table (>= capN)
     int n_bodies;
     uint32_t body_lo[kMaxBodies], body_hi[kMaxBodies];   // particle-id range of each body's markers
+    int n_sm;                             // multiprocessors of the device (launch shapes)
+    int tbx, tby, tbz;                    // cell tiles of the sort order: log2 of their
+                                          // size in cells along x, y, z (see cell_key)
     int pair_lanes;                       // lanes per fluid particle in the exact-list pair
                                           // kernels: 1, 2, or 0 for the default
     unsigned long long *step_ctr;         // active domains: index of the running step (the
@@ -87,6 +90,35 @@ __device__ __forceinline__ bool gated_off(const DevParams &p)
 
 struct Sizes { int nF, nM, N; };
 struct Window { int x0, y0, z0, X, Y, Z; };
+
+// Cell keys of the counting sort.  The cells of the window are grouped into
+// tiles of 2^tbx x 2^tby x 2^tbz cells; tiles are numbered x fastest, then y,
+// then z, and so are the cells inside a tile; key = tile * (tile size) +
+// position in the tile.  Slots are sorted by key, so a run of consecutive
+// slots -- the particles one thread block or one SM works on -- is a compact
+// 3-D piece of the terrain, whose neighbourhood stays in L1, rather than a
+// long thin run along x.  Tiles of 1 x 1 x 1 give the row-major order
+// c = (z Y + y) X + x.  Tile sizes are at most kTileX x kTileY x kTileZ, so
+// every key lies below key_cells(X, Y, Z).
+constexpr int kTileX = 8, kTileY = 4, kTileZ = 4;
+__host__ __device__ __forceinline__ int64_t key_cells(int64_t X, int64_t Y, int64_t Z)
+{
+    return ((X + kTileX - 1) / kTileX * kTileX) * ((Y + kTileY - 1) / kTileY * kTileY)
+           * ((Z + kTileZ - 1) / kTileZ * kTileZ);
+}
+
+template <class P>
+__device__ __forceinline__ uint32_t cell_key(int lx, int ly, int lz, const Window &W, const P &p)
+{
+    const uint32_t bx = (uint32_t)p.tbx, by = (uint32_t)p.tby, bz = (uint32_t)p.tbz;
+    const uint32_t x = (uint32_t)lx, y = (uint32_t)ly, z = (uint32_t)lz;
+    const uint32_t nbx = ((uint32_t)W.X + (1u << bx) - 1u) >> bx;
+    const uint32_t nby = ((uint32_t)W.Y + (1u << by) - 1u) >> by;
+    const uint32_t tile = ((z >> bz) * nby + (y >> by)) * nbx + (x >> bx);
+    const uint32_t local = ((((z & ((1u << bz) - 1u)) << by) | (y & ((1u << by) - 1u))) << bx)
+                           | (x & ((1u << bx) - 1u));
+    return (tile << (bx + by + bz)) | local;
+}
 
 __device__ __forceinline__ Sizes load_sizes(const DevParams &p)
 {
@@ -304,6 +336,16 @@ __device__ __forceinline__ void marker_now(const BodyDev &b, const double *xloc,
     const float acc[3] = {(float)b.acc[0], (float)b.acc[1], (float)b.acc[2]};
     const float al[3] = {(float)b.alpha[0], (float)b.alpha[1], (float)b.alpha[2]};
     marker_kin(b.pose, r, v, w, acc, al, x, u, a, arm);
+}
+
+// A neighbour-list word: read once per kernel, so it is fetched without
+// allocating in L1 (which is left to the neighbours' state, re-read by ~56
+// particles each).
+__device__ __forceinline__ uint32_t ld_list(const uint32_t *p)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
 }
 
 // Cell offsets of the neighbour codes (dx, dy, dz in {-1, 0, 1}) times the cell

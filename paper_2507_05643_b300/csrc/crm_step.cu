@@ -11,6 +11,8 @@
 //                           (the last block sums the FP64 wrench and moves the bodies)
 // Every particle owns its outputs (gather form): no float atomics, so a step
 // is bitwise reproducible.
+#include <algorithm>
+
 #include "crm_internal.cuh"
 
 namespace crm {
@@ -96,15 +98,30 @@ struct PairAcc {
 };
 
 // One pair (i, j) with r = x_i - x_j, 0 < |r| < 2h, added to the sums of i.
-// V_j grad_i W_ij is formed once, so every sum is a chain of FMAs.
+// V_j grad_i W_ij is formed once, so every sum is a chain of FMAs.  KAV =
+// 3 kernel + viscosity mode (compile-time, so the pair carries no mode tests);
+// the spline's two pieces and the unilateral switch are selects, not branches
+// (the lanes of a warp do not diverge on them).
+template <int KAV>
 __device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi, const float4 &ai,
                                            const float2 &bi, const float4 &vj, const float4 &aj,
                                            const float2 &bj, float rx, float ry, float rz,
                                            float r2, PairAcc &A)
 {
+    constexpr int KER = KAV / 3, AV = KAV % 3;
     const float rinv = rsqrtf(r2);
     const float q = r2 * rinv * p.inv_h;
-    const float f = kernel_dw_over_r(q, rinv, p);
+    float f;
+    if (KER == CRM_KERNEL_WENDLAND) {
+        // dW/dr = -5 a q (1 - q/2)^3 / h, so (dW/dr) / r = -5 a (1 - q/2)^3 / h^2
+        const float t = 1.0f - 0.5f * q;
+        f = p.kdw * t * t * t;
+    } else {
+        const float t = 2.0f - q;
+        const float inner = p.kdw * q * (2.25f * q - 3.0f);
+        const float outer = -0.75f * p.kdw * t * t;
+        f = (q < 1.0f ? inner : outer) * rinv;
+    }
     const float Vj = __fdividef(p.m, vj.w);   // MUFU reciprocal: ~2 ulp
     const float fv = f * Vj;
     const float gx = fv * rx, gy = fv * ry, gz = fv * rz;       // V_j grad_i W_ij
@@ -122,143 +139,30 @@ __device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi,
     A.L[3] = fmaf(uy, gx, A.L[3]); A.L[4] = fmaf(uy, gy, A.L[4]); A.L[5] = fmaf(uy, gz, A.L[5]);
     A.L[6] = fmaf(uz, gx, A.L[6]); A.L[7] = fmaf(uz, gy, A.L[7]); A.L[8] = fmaf(uz, gz, A.L[8]);
     // artificial viscosity: v_ij . r_ij = -(u_ji . r_ij), along grad W = f r
-    if (p.av_mode != CRM_AV_NONE) {
+    if (AV != CRM_AV_NONE) {
         const float vr = -(ux * rx + uy * ry + uz * rz);
-        if (p.av_mode == CRM_AV_BILATERAL || vr < 0.0f) {
-            const float fa = f * __fdividef(2.0f * p.av_c * vr, (vi.w + vj.w) * (r2 + p.xi2));
-            A.avx = fmaf(fa, rx, A.avx);
-            A.avy = fmaf(fa, ry, A.avy);
-            A.avz = fmaf(fa, rz, A.avz);
-        }
+        float fa = f * __fdividef(2.0f * p.av_c * vr, (vi.w + vj.w) * (r2 + p.xi2));
+        if (AV == CRM_AV_UNILATERAL) fa = vr < 0.0f ? fa : 0.0f;
+        A.avx = fmaf(fa, rx, A.avx);
+        A.avy = fmaf(fa, ry, A.avy);
+        A.avz = fmaf(fa, rz, A.avz);
     }
 }
 
-// LANES (1, 2 or 4) lanes share particle i: each walks every LANES-th entry of its list and
-// the sums are combined by shuffles (more warps in flight for the gathers of a
-// grid that would otherwise fill each SM only partly).  FILTER (stage 1 with a
-// skin): the list walked is the skin list, and the pairs closer than 2h at y_n
-// are written, in list order, as the exact list for the rest of the step.
-template <int MODE, bool FILTER, int LANES>
-__global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
-k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
-       const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err,
-       const float4 *__restrict__ xref, int *__restrict__ gate)
+// Stage epilogue of fluid particle i from its pair sums A: the rates (the
+// F2 / F3 sums, gravity, the Jaumann stress rate), then per MODE the rates
+// themselves (kEval), y_mid = y_n + dt/2 f(y_n) (kStage1), or
+// y_{n+1} = y_n + dt f(y_mid) with the return map of Sec. 2.3 (kStage2; S holds
+// y_mid and Y holds y_n of particle i).
+template <int MODE>
+__device__ __forceinline__ void stage_epilogue(const DevParams &p, int i, const float4 &pi,
+                                               const float4 &vi, const float4 &ai,
+                                               const float2 &bi, const PairAcc &A, StageArrays S,
+                                               StageArrays Y, StageArrays MID, float dt,
+                                               RateOut out, int *__restrict__ err,
+                                               const float4 *__restrict__ xref,
+                                               int *__restrict__ gate)
 {
-    if (*p.abort) return;
-    if (MODE == kStage2 && p.step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(p.step_ctr, 1ull);   // the step completes (no abort seen)
-    __shared__ float4 lut[64];
-    fill_shift_table(lut, p.cell);
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / LANES, q = t % LANES;
-    const bool valid = i < __ldg(p.sizes);
-    // Extended-Active particles (active domains) are read-only neighbours
-    const bool adv = valid && (pid == nullptr || !(pid[i] & kExtendedBit));
-    if (valid && !adv && q == 0) {
-        if (FILTER) io.out_n[i] = 0u;
-        if (MODE == kStage1) {
-            MID.pos[i] = S.pos[i];
-            MID.vel[i] = S.vel[i];
-            MID.sA[i] = S.sA[i];
-            MID.sB[i] = S.sB[i];
-        } else if (MODE == kEval) {
-            out.drho[i] = 0.0f;
-            out.du[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            out.dsA[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            out.dsB[i] = make_float2(0.f, 0.f);
-        }
-    }
-    if (LANES == 1 && !adv) return;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 pi = adv ? S.pos[i] : z4;
-    const float4 vi = adv ? S.vel[i] : z4;
-    const float4 ai = adv ? S.sA[i] : z4;
-    const float2 bi = adv ? S.sB[i] : make_float2(0.f, 0.f);
-    PairAcc A;
-    A.cont = A.mx = A.my = A.mz = A.avx = A.avy = A.avz = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) A.L[k] = 0.f;
-    const int nn = adv ? (int)io.in_n[i] : 0;
-    const uint32_t *row = io.in + (adv ? i : 0);
-    int cnt = 0;
-    // the lane's next list entry is fetched one iteration ahead
-    uint32_t e_nx = q < nn ? __ldg(row + (size_t)q * p.ell) : 0u;
-    if (!FILTER || LANES == 1) {
-        // on an exact list the neighbour's whole state is gathered at once (one
-        // load round per iteration); on a skin list the rest follows the distance test
-        for (int k = q; k < nn; k += LANES) {
-            const uint32_t e = e_nx;
-            if (k + LANES < nn) e_nx = __ldg(row + (size_t)(k + LANES) * p.ell);
-            const uint32_t j = e & kIndexMask;
-            const float4 sh = lut[e >> kIndexBits];
-            const float4 pj = __ldg(&S.pos[j]);
-            float4 vj, aj;
-            float2 bj;
-            vj = __ldg(&S.vel[j]);
-            aj = __ldg(&S.sA[j]);
-            bj = __ldg(&S.sB[j]);
-            const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
-            const float r2 = rx * rx + ry * ry + rz * rz;
-            if (!(r2 < p.four_h2)) continue;
-            if (FILTER) {
-                if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
-                ++cnt;
-            }
-            if (r2 == 0.0f) continue;
-            pair_terms(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
-        }
-    } else {
-        // filtering with a lane group: warp-uniform rounds, in each of which the
-        // group's lanes test consecutive candidates and place the kept ones by ballot
-        const int rounds = __reduce_max_sync(0xffffffffu, (nn + LANES - 1) / LANES);
-        const int lane = threadIdx.x & 31;
-        for (int r = 0; r < rounds; ++r) {
-            const int k = r * LANES + q;
-            const uint32_t e = e_nx;
-            if (k + LANES < nn) e_nx = __ldg(row + (size_t)(k + LANES) * p.ell);
-            bool keep = false;
-            float rx = 0.f, ry = 0.f, rz = 0.f, r2 = 0.f;
-            uint32_t j = 0;
-            if (k < nn) {
-                j = e & kIndexMask;
-                const float4 sh = lut[e >> kIndexBits];
-                const float4 pj = __ldg(&S.pos[j]);
-                rx = pi.x - pj.x - sh.x; ry = pi.y - pj.y - sh.y; rz = pi.z - pj.z - sh.z;
-                r2 = rx * rx + ry * ry + rz * rz;
-                keep = r2 < p.four_h2;
-            }
-            const unsigned b = __ballot_sync(0xffffffffu, keep);
-            const unsigned g = (b >> (lane & ~(LANES - 1))) & ((1u << LANES) - 1u);
-            const int at = cnt + __popc(g & ((1u << q) - 1u));
-            if (keep && at < p.maxnb) io.out[(size_t)at * p.ell + i] = e;
-            cnt += __popc(g);
-            if (!keep || r2 == 0.0f) continue;
-            const float4 vj = __ldg(&S.vel[j]);
-            const float4 aj = __ldg(&S.sA[j]);
-            const float2 bj = __ldg(&S.sB[j]);
-            pair_terms(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
-        }
-    }
-    if (LANES > 1) {
-#pragma unroll
-        for (int o = 1; o < LANES; o <<= 1) {
-            A.cont += __shfl_xor_sync(0xffffffffu, A.cont, o);
-            A.mx += __shfl_xor_sync(0xffffffffu, A.mx, o);
-            A.my += __shfl_xor_sync(0xffffffffu, A.my, o);
-            A.mz += __shfl_xor_sync(0xffffffffu, A.mz, o);
-            A.avx += __shfl_xor_sync(0xffffffffu, A.avx, o);
-            A.avy += __shfl_xor_sync(0xffffffffu, A.avy, o);
-            A.avz += __shfl_xor_sync(0xffffffffu, A.avz, o);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) A.L[k] += __shfl_xor_sync(0xffffffffu, A.L[k], o);
-        }
-        if (!adv || q != 0) return;
-    }
-    if (FILTER) {
-        if (cnt > p.maxnb) atomicOr(err, ERR_CAPACITY);
-        io.out_n[i] = (uint32_t)min(cnt, p.maxnb);
-    }
     if (out.sums != nullptr) {
         const size_t cs = (size_t)p.capF;
         out.sums[i] = A.cont;
@@ -324,6 +228,148 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
     }
 }
 
+// LANES (1, 2 or 4) lanes share particle i: each walks every LANES-th entry of its list and
+// the sums are combined by shuffles (more warps in flight for the gathers of a
+// grid that would otherwise fill each SM only partly).  FILTER (stage 1 with a
+// skin): the list walked is the skin list, and the pairs closer than 2h at y_n
+// are written, in list order, as the exact list for the rest of the step.
+// The pair sums and stage epilogue of fluid particle i (lane q of its LANES),
+// for i < limit.
+template <int MODE, bool FILTER, int LANES, int KAV>
+__device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int limit,
+                                         const float4 *lut, StageArrays S, StageArrays Y,
+                                         StageArrays MID, const ListIO &io,
+                                         const uint32_t *__restrict__ pid, float dt, RateOut out,
+                                         int *__restrict__ err, const float4 *__restrict__ xref,
+                                         int *__restrict__ gate)
+{
+    const bool valid = i < limit;
+    // Extended-Active particles (active domains) are read-only neighbours
+    const bool adv = valid && (pid == nullptr || !(pid[i] & kExtendedBit));
+    if (valid && !adv && q == 0) {
+        if (FILTER) io.out_n[i] = 0u;
+        if (MODE == kStage1) {
+            MID.pos[i] = S.pos[i];
+            MID.vel[i] = S.vel[i];
+            MID.sA[i] = S.sA[i];
+            MID.sB[i] = S.sB[i];
+        } else if (MODE == kEval) {
+            out.drho[i] = 0.0f;
+            out.du[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            out.dsA[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            out.dsB[i] = make_float2(0.f, 0.f);
+        }
+    }
+    if (LANES == 1 && !adv) return;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pi = adv ? S.pos[i] : z4;
+    const float4 vi = adv ? S.vel[i] : z4;
+    const float4 ai = adv ? S.sA[i] : z4;
+    const float2 bi = adv ? S.sB[i] : make_float2(0.f, 0.f);
+    PairAcc A;
+    A.cont = A.mx = A.my = A.mz = A.avx = A.avy = A.avz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A.L[k] = 0.f;
+    const int nn = adv ? (int)io.in_n[i] : 0;
+    const uint32_t *row = io.in + (adv ? i : 0);
+    int cnt = 0;
+    // the lane's next list entry is fetched one iteration ahead
+    uint32_t e_nx = q < nn ? ld_list(row + (size_t)q * p.ell) : 0u;
+    if (!FILTER || LANES == 1) {
+        // on an exact list the neighbour's whole state is gathered at once (one
+        // load round per iteration); on a skin list the rest follows the distance test
+        for (int k = q; k < nn; k += LANES) {
+            const uint32_t e = e_nx;
+            if (k + LANES < nn) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
+            const uint32_t j = e & kIndexMask;
+            const float4 sh = lut[e >> kIndexBits];
+            const float4 pj = __ldg(&S.pos[j]);
+            float4 vj, aj;
+            float2 bj;
+            vj = __ldg(&S.vel[j]);
+            aj = __ldg(&S.sA[j]);
+            bj = __ldg(&S.sB[j]);
+            const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < p.four_h2)) continue;
+            if (FILTER) {
+                if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
+                ++cnt;
+            }
+            if (r2 == 0.0f) continue;
+            pair_terms<KAV>(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
+        }
+    } else {
+        // filtering with a lane group: warp-uniform rounds, in each of which the
+        // group's lanes test consecutive candidates and place the kept ones by ballot
+        const int rounds = __reduce_max_sync(0xffffffffu, (nn + LANES - 1) / LANES);
+        const int lane = threadIdx.x & 31;
+        for (int r = 0; r < rounds; ++r) {
+            const int k = r * LANES + q;
+            const uint32_t e = e_nx;
+            if (k + LANES < nn) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
+            bool keep = false;
+            float rx = 0.f, ry = 0.f, rz = 0.f, r2 = 0.f;
+            uint32_t j = 0;
+            if (k < nn) {
+                j = e & kIndexMask;
+                const float4 sh = lut[e >> kIndexBits];
+                const float4 pj = __ldg(&S.pos[j]);
+                rx = pi.x - pj.x - sh.x; ry = pi.y - pj.y - sh.y; rz = pi.z - pj.z - sh.z;
+                r2 = rx * rx + ry * ry + rz * rz;
+                keep = r2 < p.four_h2;
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, keep);
+            const unsigned g = (b >> (lane & ~(LANES - 1))) & ((1u << LANES) - 1u);
+            const int at = cnt + __popc(g & ((1u << q) - 1u));
+            if (keep && at < p.maxnb) io.out[(size_t)at * p.ell + i] = e;
+            cnt += __popc(g);
+            if (!keep || r2 == 0.0f) continue;
+            const float4 vj = __ldg(&S.vel[j]);
+            const float4 aj = __ldg(&S.sA[j]);
+            const float2 bj = __ldg(&S.sB[j]);
+            pair_terms<KAV>(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
+        }
+    }
+    if (LANES > 1) {
+#pragma unroll
+        for (int o = 1; o < LANES; o <<= 1) {
+            A.cont += __shfl_xor_sync(0xffffffffu, A.cont, o);
+            A.mx += __shfl_xor_sync(0xffffffffu, A.mx, o);
+            A.my += __shfl_xor_sync(0xffffffffu, A.my, o);
+            A.mz += __shfl_xor_sync(0xffffffffu, A.mz, o);
+            A.avx += __shfl_xor_sync(0xffffffffu, A.avx, o);
+            A.avy += __shfl_xor_sync(0xffffffffu, A.avy, o);
+            A.avz += __shfl_xor_sync(0xffffffffu, A.avz, o);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) A.L[k] += __shfl_xor_sync(0xffffffffu, A.L[k], o);
+        }
+        if (!adv || q != 0) return;
+    }
+    if (FILTER) {
+        if (cnt > p.maxnb) atomicOr(err, ERR_CAPACITY);
+        io.out_n[i] = (uint32_t)min(cnt, p.maxnb);
+    }
+    stage_epilogue<MODE>(p, i, pi, vi, ai, bi, A, S, Y, MID, dt, out, err, xref, gate);
+}
+
+template <int MODE, bool FILTER, int LANES, int KAV>
+__global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
+k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
+       const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err,
+       const float4 *__restrict__ xref, int *__restrict__ gate)
+{
+    if (*p.abort) return;
+    if (MODE == kStage2 && p.step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(p.step_ctr, 1ull);   // the step completes (no abort seen)
+    __shared__ float4 lut[64];
+    fill_shift_table(lut, p.cell);
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    pair_one<MODE, FILTER, LANES, KAV>(p, t / LANES, t % LANES, __ldg(p.sizes), lut, S, Y, MID,
+                                       io, pid, dt, out, err, xref, gate);
+}
+
 // Sorted fluid slots -> insertion order (absolute FP64 positions).
 __global__ void k_export(DevParams p, StageArrays S, const uint32_t *__restrict__ pid,
                          double *__restrict__ xyz, float *__restrict__ vel,
@@ -383,6 +429,44 @@ __global__ void k_export_rates(DevParams p, const uint32_t *__restrict__ pid, Ra
 
 // ---------------------------------------------------------------------------
 // Host-side launchers used by the API translation unit.
+template <int KAV>
+void launch_pair_k(int mode, int LN, const DevParams &p, StageArrays S, StageArrays Y,
+                   StageArrays MID, const uint32_t *nbr, const uint32_t *nnb,
+                   const uint32_t *pid, float dt, RateOut out, int *err, const float4 *xref,
+                   int *gate, cudaStream_t st, const uint32_t *sk_nbr, const uint32_t *sk_nnb)
+{
+    constexpr int B = kPairBlock;
+    const unsigned g = grid_for((int64_t)p.capF * LN, B);
+    const unsigned g1 = grid_for(p.capF, B);
+    if (sk_nbr != nullptr) {   // stage 1 or an evaluation right after a skin search
+        const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
+        if (mode == kStage1)
+            k_pair<kStage1, true, 1, KAV><<<g1, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err,
+                                                            nullptr, nullptr);
+        else
+            k_pair<kEval, true, 1, KAV><<<g1, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err,
+                                                          nullptr, nullptr);
+        return;
+    }
+    const ListIO L{nbr, nnb, nullptr, nullptr, err};
+#define CRM_PAIR(LNS)                                                                           \
+    do {                                                                                        \
+        if (mode == kStage1)                                                                    \
+            k_pair<kStage1, false, LNS, KAV><<<g, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err, \
+                                                              nullptr, nullptr);                \
+        else if (mode == kStage2)                                                               \
+            k_pair<kStage2, false, LNS, KAV><<<g, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err, \
+                                                              xref, gate);                      \
+        else                                                                                    \
+            k_pair<kEval, false, LNS, KAV><<<g, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err,   \
+                                                            nullptr, nullptr);                  \
+    } while (0)
+    if (LN == 1) CRM_PAIR(1);
+    else if (LN == 4) CRM_PAIR(4);
+    else CRM_PAIR(2);
+#undef CRM_PAIR
+}
+
 void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, StageArrays MID,
                  const uint32_t *nbr, const uint32_t *nnb, const uint32_t *integrate, float dt,
                  RateOut out, int *err, const float4 *xref, int *gate, cudaStream_t st,
@@ -394,55 +478,18 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
     // while four threads per particle still fit the GPU's resident threads (a
     // small working set otherwise leaves most warp slots empty), else kPairLanes
     const int LN = p.pair_lanes != 0 ? p.pair_lanes
-                                     : ((int64_t)p.capF * 4 <= 148LL * 2048 ? 4 : kPairLanes);
-    const unsigned g = grid_for((int64_t)p.capF * LN, kPairBlock);
-    const unsigned g1 = grid_for(p.capF, kPairBlock);
-    if (mode == kStage1 && sk_nbr != nullptr) {
-        const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_pair<kStage1, true, 1><<<g1, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                            err, nullptr, nullptr);
-        return;
+                                     : ((int64_t)p.capF * 4 <= (int64_t)p.n_sm * 2048 ? 4 : kPairLanes);
+    const int kav = 3 * (p.kernel == CRM_KERNEL_WENDLAND ? 1 : 0)
+                    + (p.av_mode == CRM_AV_BILATERAL ? 1 : p.av_mode == CRM_AV_UNILATERAL ? 2 : 0);
+#define CRM_KAV(K)                                                                               \
+    case K:                                                                                      \
+        launch_pair_k<K>(mode, LN, p, S, Y, MID, nbr, nnb, integrate, dt, out, err, xref, gate,  \
+                         st, sk_nbr, sk_nnb);                                                    \
+        break
+    switch (kav) {
+        CRM_KAV(0); CRM_KAV(1); CRM_KAV(2); CRM_KAV(3); CRM_KAV(4); CRM_KAV(5);
     }
-    if (mode == kEval && sk_nbr != nullptr) {
-        const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_pair<kEval, true, 1><<<g1, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                          nullptr, nullptr);
-        return;
-    }
-    const ListIO L{nbr, nnb, nullptr, nullptr, err};
-    if (LN == 1) {
-        if (mode == kStage1)
-            k_pair<kStage1, false, 1><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                                err, nullptr, nullptr);
-        else if (mode == kStage2)
-            k_pair<kStage2, false, 1><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                                err, xref, gate);
-        else
-            k_pair<kEval, false, 1><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                              err, nullptr, nullptr);
-        return;
-    }
-    if (LN == 4) {
-        if (mode == kStage1)
-            k_pair<kStage1, false, 4><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                                err, nullptr, nullptr);
-        else if (mode == kStage2)
-            k_pair<kStage2, false, 4><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                                err, xref, gate);
-        else
-            k_pair<kEval, false, 4><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                              err, nullptr, nullptr);
-        return;
-    }
-    if (mode == kStage1)
-        k_pair<kStage1, false, 2><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                            err, nullptr, nullptr);
-    else if (mode == kStage2)
-        k_pair<kStage2, false, 2><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out,
-                                                            err, xref, gate);
-    else
-        k_pair<kEval, false, 2><<<g, kPairBlock, 0, st>>>(p, S, Y, MID, L, integrate, dt, out, err,
-                                                          nullptr, nullptr);
+#undef CRM_KAV
 }
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,
