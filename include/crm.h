@@ -188,7 +188,12 @@ int crm_add_active_box(crm_terrain *t, int32_t body, const double half_extents[3
  * Sec. 2.3 at the end of each step).  Enqueues on the stream and returns. */
 int crm_step(crm_terrain *t, double dt, int32_t n_steps);
 
-/* Wait for the stream and report any latched device-side failure. */
+/* Wait for the stream and report any latched device-side failure.  After
+ * CRM_ETIMEOUT (a bounded device wait gave up) the terrain is frozen: the
+ * kernels enqueued after the failed wait returned at once, its state is
+ * unspecified, and the calls that advance or evaluate it (crm_step,
+ * crm_cosim_step, crm_eval_rates, the adjoint calls) return CRM_ESTATE until
+ * crm_load_state restores a checkpoint. */
 int crm_sync(crm_terrain *t);
 
 /* Copy the SPH state out in insertion order: xyz (double, n*3), vel (n*3),
@@ -369,6 +374,16 @@ int crm_set_pair_lanes(crm_terrain *t, int32_t lanes);
  * unchanged, only the slot order and the order of the pair sums. */
 int crm_set_cell_tile(crm_terrain *t, int32_t nx, int32_t ny, int32_t nz);
 
+/* Test hook of the failure detection for device-side waits (CRM_ETIMEOUT), on
+ * the current device: on = 1 makes every look-back scan (the cell sort of a
+ * terrain, its active-set compaction, the stateless binning) started from now
+ * on hold back the prefix of its first tile and give up each wait after 1,000
+ * polls, so the waits of its later tiles run out and report the timeout --
+ * nothing hangs and nothing faults, every wait being bounded; on = 0 restores
+ * normal operation.  Scans of a single tile (4,096 cells or fewer) have no
+ * wait.  CRM_EINVAL for other values, CRM_ECUDA if the device copy fails. */
+int crm_debug_wait_fault(int32_t on);
+
 
 /* ------------------------------------------------------------------------
  * Batches (an ensemble of independent terrains, e.g. many single-wheel bins of
@@ -440,7 +455,13 @@ int crm_profile_read(crm_terrain *t, crm_profile *out);
  *              bytes, 256-byte aligned; its contents are overwritten
  * Enqueues on `cuda_stream` (NULL = default stream) and returns without
  * synchronising.  CRM_EINVAL for null pointers, n < 0, n >= 2^31, a
- * non-positive cell size, a bad grid, or too small a scratch buffer. */
+ * non-positive cell size, a bad grid, or too small a scratch buffer.
+ * Cost: O(n + X*Y*Z) per call for any distribution of the points over the cells
+ * (the sort is a least-significant-digit radix sort, one pass per 8 bits of the
+ * largest cell index).  Device-side failure: a bounded wait of the scans that
+ * gives up leaves cell_start_out[X*Y*Z] = 0xFFFFFFFF (a successful call leaves n
+ * there) and the other outputs unspecified; the call itself has returned
+ * CRM_OK by then, so a caller that must detect it reads that entry. */
 size_t crm_bin_scratch_bytes(int64_t n, int64_t ncell);
 int crm_bin_points(const float *xyz, int64_t n, float cell_size, const int32_t dims[3],
                    uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out,
@@ -455,15 +476,18 @@ int crm_bin_points(const float *xyz, int64_t n, float cell_size, const int32_t d
  *   Limits: n <= 1,048,576 points and X*Y*Z <= 1,048,575 cells; larger
  *   inputs return CRM_EINVAL (with a message on stderr) -- use
  *   crm_bin_points with a caller buffer instead.
- *   Scratch: one built-in device array of about 12.6 MB, shared by every
- *   call on a device and held by every GPU that loads the library until the
- *   process exits.  Each call clears the parts that must start at zero, so
- *   results never depend on the previous call; but calls whose work can
- *   overlap on a GPU (different streams, or host threads) race on that array:
- *   serialise them.
- *   Set-up: the first call on each device looks up the array's device
- *   address with that device current (cudaGetSymbolAddress); make that first
- *   call before any stream capture.
+ *   Scratch: one built-in device array of 22 MiB, shared by every call on a
+ *   device and held by every GPU that loads the library until the process
+ *   exits.  Each call clears the parts that must start at zero, so results
+ *   never depend on the previous call; but calls whose work can overlap on a
+ *   GPU (different streams, or host threads) race on that array: serialise
+ *   them.
+ *   Set-up: the first call on each device -- and the first call after the
+ *   device's context was reset -- looks up the array's device address with
+ *   that device current (cudaGetSymbolAddress); make that call before any
+ *   stream capture.
+ *   Device-side failure: as crm_bin_points (cell_start_out[X*Y*Z] =
+ *   0xFFFFFFFF).
  *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
 int crm_bin_points_noalloc(const float *xyz, int64_t n, float cell_size, const int32_t dims[3],
                            uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out,

@@ -90,6 +90,7 @@ _sig("crm_get_body_state", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_set_body_inertia", C.c_int, [_T, _i32, _vp])
 _sig("crm_set_pair_lanes", C.c_int, [_T, _i32])
 _sig("crm_set_cell_tile", C.c_int, [_T, _i32, _i32, _i32])
+_sig("crm_debug_wait_fault", C.c_int, [_i32])
 _B = C.c_void_p
 _sig("crm_batch_create", C.c_int, [_i32, C.POINTER(_T), _vp, C.POINTER(_B)])
 _sig("crm_batch_step", C.c_int, [_B, _vp, _i32])
@@ -135,6 +136,7 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_last_error", "crm_add_sph", "crm_add_fixed_bce", "crm_add_rigid_body",
            "crm_set_body_motion", "crm_get_body_state", "crm_set_body_inertia",
            "crm_set_body_load", "crm_add_active_box", "crm_step", "crm_set_pair_lanes", "crm_set_cell_tile",
+           "crm_debug_wait_fault",
            "crm_batch_create", "crm_batch_step", "crm_batch_autotune", "crm_batch_destroy",
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_diagnostics", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
@@ -521,6 +523,14 @@ def bin_points_noalloc(xyz_ptr: int, n: int, cell_size: float, dims, cell_ptr: i
                                      C.c_void_p(start_ptr), _stream_handle(stream))
     if rc != CRM_OK:
         raise CrmError(rc, "crm_bin_points_noalloc rejected its arguments")
+
+
+def debug_wait_fault(on: bool):
+    """crm_debug_wait_fault: make the device waits of the look-back scans on the
+    current device run out (on) or behave normally (off) -- a test hook."""
+    rc = _lib.crm_debug_wait_fault(int(bool(on)))
+    if rc != CRM_OK:
+        raise CrmError(rc, "crm_debug_wait_fault failed")
 
 
 def bin_scratch_bytes(n: int, ncell: int) -> int:

@@ -50,6 +50,7 @@ struct crm_terrain {
 
     bool committed = false;
     bool lists_valid = false;
+    bool frozen = false;          // a device wait gave up: no stepping until crm_load_state
     bool active = false;          // any active box
     bool have_working = false;    // working set holds state not yet written back
     int64_t step_index = 0;
@@ -343,6 +344,7 @@ int latched_error(crm_terrain *t)
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     if (e == 0) return CRM_OK;
     CRM_CUDA(t, cudaMemsetAsync(t->err, 0, sizeof(int), t->st));
+    if (e & ERR_TIMEOUT) t->frozen = true;   // its kernels return at once (abort word)
     if (e & ERR_NONFINITE) return t->fail(CRM_ENONFINITE, "the particle state became non-finite");
     if (e & ERR_ESCAPED) return t->fail(CRM_EESCAPED, "a particle or marker left the grid domain");
     if (e & ERR_CAPACITY)
@@ -843,7 +845,7 @@ void activity_pass(crm_terrain *t)
                                             t->mloc, t->fixed_order, all, t->cand_cap, t->cinc,
                                             t->ckind, t->counts, t->abort_flag, t->st); });
     launch(t, K_SCAN, [&] { launch_scan_reset(t->cinc, t->cslot, t->cand_cap + 1, t->cscan, t->err,
-                                              t->st); });
+                                              t->st, nullptr, t->abort_flag); });
     launch(t, K_KEYS, [&] { launch_active_sizes(d, t->rinfo, t->cslot, t->n_bodym, t->counts,
                                                 t->abort_flag, t->step_index, t->st); });
     launch(t, K_KEYS, [&] { launch_gather(d, t->ranges, t->rinfo, t->ckind, t->cslot, t->Mst,
@@ -865,7 +867,7 @@ void enqueue_search(crm_terrain *t)
     launch(t, K_KEYS, [&] { launch_keys(d, t->A[c], t->pid[c], t->mloc, t->bodies,
                                         t->ss, t->err, (int)t->nFtot, t->st); });
     launch(t, K_SCAN, [&] { launch_scan_reset(t->ss.count, t->start, 2 * (int64_t)d.M + 1, t->ss,
-                                              t->err, t->st, d.gate); });
+                                              t->err, t->st, d.gate, t->abort_flag); });
     launch(t, K_SCATTER, [&] { launch_scatter(d, t->ss, t->start, t->st); });
     launch(t, K_REORDER, [&] { launch_reorder(d, t->ss, t->start, t->A[c], t->pid[c], t->A[n],
                                               t->pid[n], t->st); });
@@ -1137,6 +1139,7 @@ int step_active(crm_terrain *t, double dt, int n_steps)
         int rc = read_counts(t);
         if (rc) return rc;
         const int ab = t->h_counts[C_WORDS];
+        if (ab == kAbortTimeout) return latched_error(t);   // frozen until crm_load_state
         if (ab != 0) {
             if (++guard > 64) return t->fail(CRM_ENOMEM, "active-set capacity kept overflowing");
             const int64_t failed = (int64_t)ab - 1;
@@ -1488,6 +1491,8 @@ int crm_step(crm_terrain *t, double dt, int32_t n_steps)
 {
     if (!t) return CRM_EINVAL;
     if (!(dt > 0) || !std::isfinite(dt) || n_steps < 0) return t->fail(CRM_EINVAL, "crm_step: dt > 0, n_steps >= 0");
+    if (t->frozen)
+        return t->fail(CRM_ESTATE, "terrain frozen after a device wait gave up; crm_load_state a checkpoint");
     int rc = commit(t);
     if (rc) return rc;
     if (t->active) return step_active(t, dt, n_steps);
@@ -1554,6 +1559,8 @@ int crm_cosim_step(crm_terrain *t, const double *pose_in, const double *twist_in
                    int32_t n_steps, double *wrench_out, double *pose_out, double *twist_out)
 {
     if (!t) return CRM_EINVAL;
+    if (t->frozen)
+        return t->fail(CRM_ESTATE, "terrain frozen after a device wait gave up; crm_load_state a checkpoint");
     const int nb = (int)t->hbodies.size();
     if ((pose_in == nullptr) != (twist_in == nullptr))
         return t->fail(CRM_EINVAL, "crm_cosim_step: give both pose and twist, or neither");
@@ -1672,6 +1679,8 @@ int crm_eval_rates(crm_terrain *t, int64_t cap_sph, float *drho, float *dvel, fl
                    int64_t cap_markers, float *marker_acc, float *marker_vel, float *marker_stress)
 {
     if (!t) return CRM_EINVAL;
+    if (t->frozen)
+        return t->fail(CRM_ESTATE, "terrain frozen after a device wait gave up; crm_load_state a checkpoint");
     if (cap_sph < t->nFtot || cap_markers < t->nMtot)
         return t->fail(CRM_EINVAL, "crm_eval_rates: output capacity too small");
     int rc = commit(t);
@@ -1771,6 +1780,12 @@ static int force_search(crm_terrain *t)
                                 t->st));
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     return CRM_OK;
+}
+
+int crm_debug_wait_fault(int32_t on)
+{
+    if (on != 0 && on != 1) return CRM_EINVAL;
+    return set_wait_fault(on) == 0 ? CRM_OK : CRM_ECUDA;
 }
 
 int crm_set_cell_tile(crm_terrain *t, int32_t nx, int32_t ny, int32_t nz)
@@ -2065,6 +2080,10 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used)
     std::memcpy(&t->time, &hdr[1], sizeof(double));
     t->lists_valid = false;
     t->have_working = false;
+    // a terrain frozen by a device wait that gave up resumes from the checkpoint
+    CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->err, 0, sizeof(int), t->st));
+    t->frozen = false;
     if (t->skin_on) {
         const int g0[GATE_WORDS] = {1, 0, 1, 0};
         CRM_CUDA(t, cudaMemcpyAsync(t->gate, g0, sizeof(g0), cudaMemcpyHostToDevice, t->st));
@@ -2340,6 +2359,8 @@ int crm_eval_rates_vjp(crm_terrain *t, int64_t cap_sph, const float *l_drho, con
                        double *g_body, double *g_params)
 {
     if (!t) return CRM_EINVAL;
+    if (t->frozen)
+        return t->fail(CRM_ESTATE, "terrain frozen after a device wait gave up; crm_load_state a checkpoint");
     if (cap_sph < t->nFtot || (l_macc && cap_markers < t->nMtot))
         return t->fail(CRM_EINVAL, "crm_eval_rates_vjp: adjoint capacity too small");
     int rc = commit(t);
@@ -2406,6 +2427,8 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
                         double *wrench_hist, double *pose_hist)
 {
     if (!t) return CRM_EINVAL;
+    if (t->frozen)
+        return t->fail(CRM_ESTATE, "terrain frozen after a device wait gave up; crm_load_state a checkpoint");
     if (!(dt > 0) || !std::isfinite(dt) || n_steps < 1 || every < 0)
         return t->fail(CRM_EINVAL, "crm_adjoint_forward: dt > 0, n_steps >= 1, every >= 0");
     int rc = commit(t);
@@ -2512,6 +2535,8 @@ int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l
                          double *g_stress, double *g_rho, double *g_body)
 {
     if (!t) return CRM_EINVAL;
+    if (t->frozen)
+        return t->fail(CRM_ESTATE, "terrain frozen after a device wait gave up; crm_load_state a checkpoint");
     crm_terrain::Adjoint &A = t->adj;
     if (!A.ready || A.n_steps < 1 || A.tape.empty())
         return t->fail(CRM_ESTATE, "crm_adjoint_backward: no run recorded by crm_adjoint_forward");

@@ -7,6 +7,7 @@
 // The atomic ranks make the arrival order within a cell nondeterministic; a
 // fix-up pass re-ranks every element by its input index inside its cell, so
 // the result equals a stable sort by (cell, input index) on every run.
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -25,22 +26,31 @@ namespace crm {
 namespace {
 constexpr uint32_t kAgg = 1u, kIncl = 2u;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kFaultSpinLimit = 1000;
+
+// Test switch of the device-wait failure path (crm_debug_wait_fault): when
+// set, the first tile of every look-back scan publishes nothing and every wait
+// gives up after kFaultSpinLimit polls, so the waits of the later tiles run out
+// (they return with ERR_TIMEOUT; nothing hangs and nothing faults).
+__device__ int g_wait_fault = 0;
 
 __device__ __forceinline__ int pad(int k) { return k + (k >> 5); }
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(uint32_t *__restrict__ count, uint32_t *__restrict__ start, int64_t n,
        unsigned long long *status, uint32_t *ctr, int64_t n_tiles, int *err,
-       const int *__restrict__ gate)
+       const int *__restrict__ gate, int *abort_word)
 {
     if (gate != nullptr && __ldg(gate) == 0) return;   // every block: uniform
     __shared__ uint32_t s_items[kScanTile + kScanTile / 32];
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_tile, s_epoch, s_prefix;
+    __shared__ int s_fault;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) {
         s_tile = atomicAdd(&ctr[0], 1u);
         s_epoch = (((volatile uint32_t *)ctr)[1] + 1u) & 0x3FFFFFFFu;
+        s_fault = *(volatile int *)&g_wait_fault;
     }
     __syncthreads();
     const int64_t tile = s_tile;
@@ -94,16 +104,20 @@ k_scan(uint32_t *__restrict__ count, uint32_t *__restrict__ start, int64_t n,
                     if (st == kIncl) break;
                     --j;
                     spins = 0;
-                } else if (++spins > kSpinLimit) {
+                } else if (++spins > (s_fault ? kFaultSpinLimit : kSpinLimit)) {
                     atomicOr(err, ERR_TIMEOUT);
+                    // every later kernel of the terrain's enqueued work returns at
+                    // once: none of them indexes with these partial cell ranges
+                    if (abort_word != nullptr) atomicExch(abort_word, kAbortTimeout);
                     break;
                 } else {
                     __nanosleep(32);
                 }
             }
         }
-        atomicExch(&status[tile],
-                   ((unsigned long long)((epoch << 2) | kIncl) << 32) | (prefix + agg));
+        if (!(s_fault && tile == 0))
+            atomicExch(&status[tile],
+                       ((unsigned long long)((epoch << 2) | kIncl) << 32) | (prefix + agg));
         s_prefix = prefix;
     }
     __syncthreads();
@@ -134,11 +148,17 @@ k_scan(uint32_t *__restrict__ count, uint32_t *__restrict__ start, int64_t n,
 }  // namespace
 
 void launch_scan_reset(uint32_t *count, uint32_t *start, int64_t n, const SortScratch &s,
-                       int *err, cudaStream_t st, const int *gate)
+                       int *err, cudaStream_t st, const int *gate, int *abort_word)
 {
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     k_scan<<<(unsigned)tiles, kScanThreads, 0, st>>>(count, start, n, s.tile_status, s.ctr,
-                                                     tiles, err, gate);
+                                                     tiles, err, gate, abort_word);
+}
+
+int set_wait_fault(int on)
+{
+    const int v = on ? 1 : 0;
+    return cudaMemcpyToSymbol(g_wait_fault, &v, sizeof(int)) == cudaSuccess ? 0 : -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -157,33 +177,11 @@ __global__ void k_scatter(const uint32_t *__restrict__ keys, const uint32_t *__r
     tmp[start[keys[i]] + rank[i]] = (uint32_t)i;
 }
 
-// Final slot of the element that k_scatter put at slot s: its rank by input
-// index among the elements of the same key.
-__device__ __forceinline__ uint32_t stable_slot(const uint32_t *__restrict__ keys,
-                                                const uint32_t *__restrict__ start,
-                                                const uint32_t *__restrict__ tmp, uint32_t i)
-{
-    const uint32_t key = keys[i];
-    const uint32_t b = start[key], e = start[key + 1];
-    uint32_t r = 0;
-    for (uint32_t u = b; u < e; ++u) r += tmp[u] < i ? 1u : 0u;
-    return b + r;
-}
-
-__global__ void k_perm(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ start,
-                       const uint32_t *__restrict__ tmp, uint32_t *__restrict__ perm, int64_t n)
-{
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const uint32_t i = tmp[s];
-    perm[stable_slot(keys, start, tmp, i)] = i;
-}
-
-// H3 of the stateless call: cell of each point (clamped into the grid) and its
-// arrival rank within the cell.
+// H3 of the stateless call: cell of each point (clamped into the grid), and the
+// count of each cell.
 __global__ void k_hash_points(const float *__restrict__ xyz, int64_t n, float inv_cell, int X,
                               int Y, int Z, uint32_t *__restrict__ cell,
-                              uint32_t *__restrict__ rank, uint32_t *__restrict__ count)
+                              uint32_t *__restrict__ count)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -195,7 +193,90 @@ __global__ void k_hash_points(const float *__restrict__ xyz, int64_t n, float in
     iz = min(max(iz, 0), Z - 1);
     const uint32_t c = ((uint32_t)iz * (uint32_t)Y + (uint32_t)iy) * (uint32_t)X + (uint32_t)ix;
     cell[i] = c;
-    rank[i] = atomicAdd(&count[c], 1u);
+    atomicAdd(&count[c], 1u);
+}
+
+// H4 of the stateless call: a stable least-significant-digit radix sort of
+// (cell, input index) by cell, 8 bits per pass, O(n) work per pass whatever
+// the distribution of points over cells (a cell holding all n points costs no
+// more than n distinct cells).  A pass: each block counts the digits of its
+// tile of kRadixTile elements (k_radix_hist, written digit-major: hist[d *
+// tiles + b]); one exclusive scan of that array gives every (digit, tile) its
+// output offset, so tiles keep their order within a digit; k_radix_scatter
+// ranks each tile's elements by digit in input order (warp match, then the
+// warps in order) and writes them there.  Every kernel does nothing once a
+// wait of a scan has given up (*err & ERR_TIMEOUT).
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift, int64_t tiles,
+             uint32_t *__restrict__ hist, const int *__restrict__ err)
+{
+    __shared__ uint32_t h[256];
+    if (*(volatile const int *)err & ERR_TIMEOUT) return;   // uniform over the grid
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int k = threadIdx.x; k < kRadixTile; k += kRadixThreads) {
+        const int64_t i = base + k;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// vals_in == nullptr: the values are the input indices.  keys_out == nullptr:
+// the last pass (only the values are kept).
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                int64_t n, int shift, int64_t tiles, const uint32_t *__restrict__ offs,
+                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                const int *__restrict__ err)
+{
+    __shared__ uint32_t run[256];                 // elements of each digit placed so far
+    __shared__ uint32_t wcnt[kRadixWarps][256];   // this round: per warp, per digit
+    if (*(volatile const int *)err & ERR_TIMEOUT) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    run[t] = offs[(int64_t)t * tiles + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int r = 0; r < kRadixItems; ++r) {
+        for (int w = 0; w < kRadixWarps; ++w) wcnt[w][t] = 0u;
+        __syncthreads();
+        const int64_t i = base + (int64_t)r * kRadixThreads + t;   // input order within the tile
+        const bool ok = i < n;
+        const uint32_t key = ok ? keys_in[i] : 0u;
+        const uint32_t d = ok ? (key >> shift) & 255u : 256u + (uint32_t)lane;   // never matches
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t below = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+        if (ok && below == 0u) wcnt[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        // digit t: exclusive prefix over the warps, in warp order
+        uint32_t acc = run[t];
+        for (int w = 0; w < kRadixWarps; ++w) {
+            const uint32_t c = wcnt[w][t];
+            wcnt[w][t] = acc;
+            acc += c;
+        }
+        __syncthreads();
+        if (ok) {
+            const uint32_t at = wcnt[warp][d] + below;
+            vals_out[at] = vals_in ? vals_in[i] : (uint32_t)i;
+            if (keys_out) keys_out[at] = key;
+        }
+        __syncthreads();
+        run[t] = acc;
+    }
+}
+
+// After the sort: when a wait gave up, cell_start[ncell] is set to a value no
+// successful call leaves there (a successful call leaves n).
+__global__ void k_bin_status(uint32_t *__restrict__ cell_start, int64_t ncell,
+                             const int *__restrict__ err)
+{
+    if (*(volatile const int *)err & ERR_TIMEOUT) cell_start[ncell] = 0xFFFFFFFFu;
 }
 }  // namespace
 
@@ -555,27 +636,93 @@ void launch_copyback(const DevParams &p, StageArrays src, const uint32_t *pid_sr
 }  // namespace crm
 
 // ---------------------------------------------------------------------------
-// Stateless binning entry point (include/crm.h).
+// Stateless binning entry points (include/crm.h).
 namespace {
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Scratch of one stateless binning call: the radix sort's key/value buffers
+// (two pairs, ping-ponged), the digit histograms and their offsets, the cell
+// counts, the look-back words of the scans and the counters (ctr[3] collects
+// device-side failures).
 struct BinLayout {
-    size_t rank, tmp, count, status, ctr, total;
+    size_t kA, vA, kB, vB, hist, offs, count, status, ctr, total;
+    int64_t radix_tiles, scan_tiles;
 };
 
 BinLayout bin_layout(int64_t n, int64_t ncell)
 {
     BinLayout L;
-    const int64_t nk = ncell + 1;
-    const int64_t tiles = (nk + crm::kScanTile - 1) / crm::kScanTile;
+    const int64_t nn = n > 0 ? n : 1;
+    L.radix_tiles = (nn + crm::kRadixTile - 1) / crm::kRadixTile;
+    const int64_t nh = 256 * L.radix_tiles;
+    L.scan_tiles = (std::max<int64_t>(ncell + 1, nh) + crm::kScanTile - 1) / crm::kScanTile;
     size_t o = 0;
-    L.rank = o;   o += align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-    L.tmp = o;    o += align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-    L.count = o;  o += align256(sizeof(uint32_t) * (size_t)nk);
-    L.status = o; o += align256(sizeof(unsigned long long) * (size_t)tiles);
+    L.kA = o;     o += align256(sizeof(uint32_t) * (size_t)nn);
+    L.vA = o;     o += align256(sizeof(uint32_t) * (size_t)nn);
+    L.kB = o;     o += align256(sizeof(uint32_t) * (size_t)nn);
+    L.vB = o;     o += align256(sizeof(uint32_t) * (size_t)nn);
+    L.hist = o;   o += align256(sizeof(uint32_t) * (size_t)nh);
+    L.offs = o;   o += align256(sizeof(uint32_t) * (size_t)nh);
+    L.count = o;  o += align256(sizeof(uint32_t) * (size_t)(ncell + 1));
+    L.status = o; o += align256(sizeof(unsigned long long) * (size_t)L.scan_tiles);
     L.ctr = o;    o += align256(sizeof(uint32_t) * 4);
     L.total = o;
     return L;
+}
+
+bool bin_args_ok(const float *xyz, int64_t n, float cell_size, const int32_t dims[3],
+                 const uint32_t *cell_out, const uint32_t *perm_out, const uint32_t *cell_start_out)
+{
+    if (!dims || !cell_start_out || n < 0 || n >= (int64_t(1) << 31)) return false;
+    if (n > 0 && (!xyz || !cell_out || !perm_out)) return false;
+    if (!(cell_size > 0.0f) || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return false;
+    return (int64_t)dims[0] * dims[1] * dims[2] < (int64_t(1) << 31);
+}
+
+// The binning itself on a scratch area laid out by L.  The parts that must
+// start at zero (cell counts, look-back words, counters) are cleared here; the
+// rest is written before it is read.
+int bin_points_on(const float *xyz, int64_t n, float cell_size, const int32_t dims[3],
+                  uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out, char *base,
+                  const BinLayout &L, cudaStream_t st)
+{
+    const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
+    if (cudaMemsetAsync(base + L.count, 0, sizeof(uint32_t) * (size_t)(ncell + 1), st) != cudaSuccess
+        || cudaMemsetAsync(base + L.status, 0, L.total - L.status, st) != cudaSuccess)
+        return CRM_ECUDA;
+    crm::SortScratch s{};
+    s.count = (uint32_t *)(base + L.count);
+    s.tile_status = (unsigned long long *)(base + L.status);
+    s.ctr = (uint32_t *)(base + L.ctr);
+    int *err = (int *)(s.ctr + 3);
+    if (n > 0)
+        crm::k_hash_points<<<crm::grid_for(n), crm::kBlock, 0, st>>>(
+            xyz, n, 1.0f / cell_size, dims[0], dims[1], dims[2], cell_out, s.count);
+    crm::launch_scan_reset(s.count, cell_start_out, ncell + 1, s, err, st);
+    if (n > 0) {
+        int bits = 1;
+        while (bits < 31 && ((ncell - 1) >> bits) != 0) ++bits;
+        const int passes = (bits + 7) / 8;
+        const int64_t tiles = L.radix_tiles;
+        uint32_t *hist = (uint32_t *)(base + L.hist), *offs = (uint32_t *)(base + L.offs);
+        uint32_t *kbuf[2] = {(uint32_t *)(base + L.kA), (uint32_t *)(base + L.kB)};
+        uint32_t *vbuf[2] = {(uint32_t *)(base + L.vA), (uint32_t *)(base + L.vB)};
+        const uint32_t *kin = cell_out, *vin = nullptr;
+        for (int ps = 0; ps < passes; ++ps) {
+            const bool last = ps == passes - 1;
+            uint32_t *kout = last ? nullptr : kbuf[ps & 1];
+            uint32_t *vout = last ? perm_out : vbuf[ps & 1];
+            crm::k_radix_hist<<<(unsigned)tiles, crm::kRadixThreads, 0, st>>>(kin, n, 8 * ps, tiles,
+                                                                           hist, err);
+            crm::launch_scan_reset(hist, offs, 256 * tiles, s, err, st);
+            crm::k_radix_scatter<<<(unsigned)tiles, crm::kRadixThreads, 0, st>>>(
+                kin, vin, n, 8 * ps, tiles, offs, kout, vout, err);
+            kin = kout;
+            vin = vout;
+        }
+    }
+    crm::k_bin_status<<<1, 1, 0, st>>>(cell_start_out, ncell, err);
+    return cudaGetLastError() == cudaSuccess ? CRM_OK : CRM_ECUDA;
 }
 }  // namespace
 
@@ -589,39 +736,13 @@ extern "C" int crm_bin_points(const float *xyz, int64_t n, float cell_size, cons
                               uint32_t *cell_out, uint32_t *perm_out, uint32_t *cell_start_out,
                               void *scratch, size_t scratch_bytes, void *cuda_stream)
 {
-    if (!dims || !cell_start_out || !scratch || n < 0 || n >= (int64_t(1) << 31)) return CRM_EINVAL;
-    if (n > 0 && (!xyz || !cell_out || !perm_out)) return CRM_EINVAL;
-    if (!(cell_size > 0.0f) || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return CRM_EINVAL;
-    const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
-    if (ncell >= (int64_t(1) << 31)) return CRM_EINVAL;
+    if (!bin_args_ok(xyz, n, cell_size, dims, cell_out, perm_out, cell_start_out) || !scratch)
+        return CRM_EINVAL;
     if (((uintptr_t)scratch & 255u) != 0) return CRM_EINVAL;
-    const BinLayout L = bin_layout(n, ncell);
+    const BinLayout L = bin_layout(n, (int64_t)dims[0] * dims[1] * dims[2]);
     if (scratch_bytes < L.total) return CRM_EINVAL;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    char *base = (char *)scratch;
-    crm::SortScratch s;
-    s.keys = cell_out;
-    s.rank = (uint32_t *)(base + L.rank);
-    s.tmp = (uint32_t *)(base + L.tmp);
-    s.count = (uint32_t *)(base + L.count);
-    s.tile_status = (unsigned long long *)(base + L.status);
-    s.ctr = (uint32_t *)(base + L.ctr);
-    s.n_tiles = (ncell + 1 + crm::kScanTile - 1) / crm::kScanTile;
-    // counts, look-back words and counters start from zero on every call (the
-    // scratch content is the caller's); ctr[3] collects device-side failures
-    if (cudaMemsetAsync(base + L.count, 0, L.total - L.count, st) != cudaSuccess) return CRM_ECUDA;
-    int *err = (int *)(s.ctr + 3);
-    if (n > 0)
-        crm::k_hash_points<<<crm::grid_for(n), crm::kBlock, 0, st>>>(
-            xyz, n, 1.0f / cell_size, dims[0], dims[1], dims[2], s.keys, s.rank, s.count);
-    crm::launch_scan_reset(s.count, cell_start_out, ncell + 1, s, err, st);
-    if (n > 0) {
-        crm::k_scatter<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, s.rank, cell_start_out,
-                                                                 s.tmp, n, nullptr, nullptr);
-        crm::k_perm<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, cell_start_out, s.tmp,
-                                                              perm_out, n);
-    }
-    return cudaGetLastError() == cudaSuccess ? CRM_OK : CRM_ECUDA;
+    return bin_points_on(xyz, n, cell_size, dims, cell_out, perm_out, cell_start_out,
+                         (char *)scratch, L, (cudaStream_t)cuda_stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -630,28 +751,61 @@ extern "C" int crm_bin_points(const float *xyz, int64_t n, float cell_size, cons
 // For callers that cannot allocate device memory at the time they bin --
 // for example code running inside a host callback or a real-time loop where
 // cudaMalloc would stall or is forbidden, or a caller whose device memory is
-// fully reserved by its own allocator -- the scratch of the counting sort
-// lives in one file-scope device array instead of a caller buffer.  That array
-// is part of the library image: every GPU that loads the library holds
+// fully reserved by its own allocator -- the scratch of the sort lives in one
+// file-scope device array instead of a caller buffer.  That array is part of
+// the library image: every GPU that loads the library holds
 // kNoAllocScratchBytes of it until the process exits.
 namespace {
-constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 20;   // 1,048,576 points
+constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 20;        // 1,048,576 points
 constexpr int64_t kNoAllocMaxCells = (int64_t(1) << 20) - 1;   // 1,048,575 cells
-constexpr size_t kNoAllocRank = 0;
-constexpr size_t kNoAllocTmp = kNoAllocRank + sizeof(uint32_t) * kNoAllocMaxPoints;
-constexpr size_t kNoAllocCount = kNoAllocTmp + sizeof(uint32_t) * kNoAllocMaxPoints;
-constexpr int64_t kNoAllocTiles = (kNoAllocMaxCells + 1 + crm::kScanTile - 1) / crm::kScanTile;
-constexpr size_t kNoAllocStatus = kNoAllocCount + sizeof(uint32_t) * (kNoAllocMaxCells + 1);
-constexpr size_t kNoAllocCtr = kNoAllocStatus + sizeof(unsigned long long) * kNoAllocTiles;
-constexpr size_t kNoAllocScratchBytes = kNoAllocCtr + 256;
+// the layout at both limits bounds the layout of every admissible call
+// (each part grows with n or ncell)
+constexpr size_t kNoAllocScratchBytes = 22 * (size_t(1) << 20);   // 23,068,672 B
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device (host code
-// must not use the symbol itself: on the host it is only a stand-in).
+// Device address of g_noalloc_scratch for the current device and context,
+// looked up with cudaGetSymbolAddress (host code must not use the symbol
+// itself: on the host it is only a stand-in).  The lookup is repeated whenever
+// the current context differs from the one the cached address belongs to (a
+// device reset gives the device a new primary context and the module a new
+// address).
 constexpr int kMaxDevices = 64;
-void *g_noalloc_addr[kMaxDevices] = {};
+struct NoAllocAddr {
+    void *ptr = nullptr;
+    unsigned long long ctx = 0;
+};
+NoAllocAddr g_noalloc_addr[kMaxDevices];
 std::mutex g_noalloc_mutex;
+
+using CtxGetId = int (*)(void *ctx, unsigned long long *id);
+using CtxGetCurrent = int (*)(void **ctx);
+
+// Id of the current context (0 when the driver entry points are unavailable;
+// the address is then looked up on every call).
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrent get_cur = nullptr;
+    static CtxGetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess
+            && q == cudaDriverEntryPointSuccess)
+            get_cur = (CtxGetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess
+            && q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetId)f;
+        cudaGetLastError();
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 int noalloc_scratch(void **out)
 {
@@ -661,15 +815,19 @@ int noalloc_scratch(void **out)
         return CRM_ECUDA;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    const unsigned long long ctx = current_ctx_id();
+    NoAllocAddr &a = g_noalloc_addr[dev];
+    if (!a.ptr || ctx == 0 || a.ctx != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
+            a = NoAllocAddr{};
             return CRM_ECUDA;
         }
-        g_noalloc_addr[dev] = p;
+        a.ptr = p;
+        a.ctx = ctx;
     }
-    *out = g_noalloc_addr[dev];
+    *out = a.ptr;
     return CRM_OK;
 }
 }  // namespace
@@ -679,9 +837,8 @@ extern "C" int crm_bin_points_noalloc(const float *xyz, int64_t n, float cell_si
                                       uint32_t *perm_out, uint32_t *cell_start_out,
                                       void *cuda_stream)
 {
-    if (!dims || !cell_start_out || n < 0) return CRM_EINVAL;
-    if (n > 0 && (!xyz || !cell_out || !perm_out)) return CRM_EINVAL;
-    if (!(cell_size > 0.0f) || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return CRM_EINVAL;
+    if (!bin_args_ok(xyz, n, cell_size, dims, cell_out, perm_out, cell_start_out))
+        return CRM_EINVAL;
     const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
     if (n > kNoAllocMaxPoints || ncell > kNoAllocMaxCells) {
         std::fprintf(stderr,
@@ -692,36 +849,11 @@ extern "C" int crm_bin_points_noalloc(const float *xyz, int64_t n, float cell_si
                      (long long)kNoAllocMaxCells);
         return CRM_EINVAL;
     }
+    const BinLayout L = bin_layout(n, ncell);
+    if (L.total > kNoAllocScratchBytes) return CRM_EINVAL;   // cannot happen within the limits
     void *addr = nullptr;
     const int rc = noalloc_scratch(&addr);
     if (rc != CRM_OK) return rc;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    char *base = (char *)addr;
-    crm::SortScratch s;
-    s.keys = cell_out;
-    s.rank = (uint32_t *)(base + kNoAllocRank);
-    s.tmp = (uint32_t *)(base + kNoAllocTmp);
-    s.count = (uint32_t *)(base + kNoAllocCount);
-    s.tile_status = (unsigned long long *)(base + kNoAllocStatus);
-    s.ctr = (uint32_t *)(base + kNoAllocCtr);
-    s.n_tiles = (ncell + 1 + crm::kScanTile - 1) / crm::kScanTile;
-    // the array keeps whatever the previous call left: the counts, the look-back
-    // words and the counters must start from zero
-    if (cudaMemsetAsync(base + kNoAllocCount, 0, sizeof(uint32_t) * (size_t)(ncell + 1), st)
-            != cudaSuccess
-        || cudaMemsetAsync(base + kNoAllocStatus, 0, kNoAllocScratchBytes - kNoAllocStatus, st)
-               != cudaSuccess)
-        return CRM_ECUDA;
-    int *err = (int *)(s.ctr + 3);
-    if (n > 0)
-        crm::k_hash_points<<<crm::grid_for(n), crm::kBlock, 0, st>>>(
-            xyz, n, 1.0f / cell_size, dims[0], dims[1], dims[2], s.keys, s.rank, s.count);
-    crm::launch_scan_reset(s.count, cell_start_out, ncell + 1, s, err, st);
-    if (n > 0) {
-        crm::k_scatter<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, s.rank, cell_start_out,
-                                                                 s.tmp, n, nullptr, nullptr);
-        crm::k_perm<<<crm::grid_for(n), crm::kBlock, 0, st>>>(s.keys, cell_start_out, s.tmp,
-                                                              perm_out, n);
-    }
-    return cudaGetLastError() == cudaSuccess ? CRM_OK : CRM_ECUDA;
+    return bin_points_on(xyz, n, cell_size, dims, cell_out, perm_out, cell_start_out,
+                         (char *)addr, L, (cudaStream_t)cuda_stream);
 }

@@ -18,6 +18,10 @@ enum : int {
     ERR_TIMEOUT = 8,    // a bounded spin-wait gave up
 };
 
+// Abort word value of a device wait that gave up (a terrain's abort word
+// otherwise holds 0, or 1 + the step whose capacity overflowed).
+constexpr int kAbortTimeout = (int)0x80000000;
+
 constexpr int kMaxBodies = 16;
 constexpr uint32_t kExtendedBit = 0x80000000u;   // pid flag: Extended-Active (read-only)
 // particle id: insertion index in bits 0..30 (fluid particles, then markers);
@@ -393,8 +397,13 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Exclusive scan of count[0..n) into start[0..n), resetting count to zero.
 // Single pass, decoupled look-back; every wait is bounded (ERR_TIMEOUT).
+// On a timed-out wait the scan also sets *abort_word (when given) to
+// kAbortTimeout.
 void launch_scan_reset(uint32_t *count, uint32_t *start, int64_t n, const SortScratch &s,
-                       int *err, cudaStream_t st, const int *gate = nullptr);
+                       int *err, cudaStream_t st, const int *gate = nullptr,
+                       int *abort_word = nullptr);
+// Device-wait fault switch of the current device (crm_debug_wait_fault): 0 on success.
+int set_wait_fault(int on);
 
 // Rebuild (Alg. 2 "PreprocessNeighborList" + Alg. 1), one kernel per launcher:
 // keys + arrival ranks, exclusive scan of the counts (cell ranges, 2M + 1

@@ -318,14 +318,20 @@ def test_nonfinite_reported():
 # --------------------------------------------------------------------------
 # Stateless binning (Sec. 3.1 steps 1-3): bit-exact against its definition.
 
-@pytest.mark.parametrize("n, dims", [(0, (3, 2, 2)), (1, (1, 1, 1)), (4097, (9, 7, 5)),
-                                     (250_000, (88, 22, 29)), (1_000_003, (200, 40, 30))])
-def test_bin_points_exact(n, dims):
+@pytest.mark.parametrize("n, dims, spread", [
+    (0, (3, 2, 2), 1.0), (1, (1, 1, 1), 1.0), (4097, (9, 7, 5), 1.0),
+    (250_000, (88, 22, 29), 1.0), (1_000_003, (200, 40, 30), 1.0),
+    # degenerate distributions: every point in one cell; ~90 % of the points
+    # outside the grid, clamped into its boundary cells; a grid whose cell index
+    # needs all four 8-bit digits of the radix sort
+    (200_000, (1, 1, 1), 1.0), (300_000, (64, 32, 16), 10.0), (100_000, (512, 256, 200), 1.0)])
+def test_bin_points_exact(n, dims, spread):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(n)
     cell = np.float32(0.024)
     ext = np.array(dims, np.float32) * cell
-    xyz = (rng.uniform(-0.01, 1.0, size=(n, 3)) * ext).astype(np.float32)
+    xyz = ((rng.uniform(-0.01, 1.0, size=(n, 3)) - 0.5) * spread + 0.5) * ext
+    xyz = xyz.astype(np.float32)
     if n > 10:
         xyz[:5] = np.float32(cell) * np.float32(2.0)   # points exactly on cell faces
     ncell = int(np.prod(dims))

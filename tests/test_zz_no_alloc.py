@@ -14,21 +14,22 @@ pytestmark = pytest.mark.gpu
 crm = pytest.importorskip("paper_2507_05643_b300")
 
 
-def _points(seed, n, dims, cell):
+def _points(seed, n, dims, cell, spread=1.0):
     rng = np.random.default_rng(seed)
     ext = np.array(dims, np.float32) * np.float32(cell)
-    return (rng.uniform(-0.02, 1.01, size=(n, 3)) * ext).astype(np.float32)
+    u = (rng.uniform(-0.02, 1.01, size=(n, 3)) - 0.5) * spread + 0.5
+    return (u * ext).astype(np.float32)
 
 
 def _bin_both(torch, xyz, dims, cell):
     dev = torch.device("cuda")
     n = xyz.shape[0]
     ncell = int(np.prod(dims))
-    X = torch.from_numpy(xyz.reshape(-1)).to(dev)
+    X = torch.from_numpy(xyz.reshape(-1)).to(dev) if n else torch.zeros(3, device=dev)
     outs = []
     for noalloc in (False, True):
-        cells = torch.full((n,), -1, dtype=torch.int32, device=dev)
-        perm = torch.full((n,), -1, dtype=torch.int32, device=dev)
+        cells = torch.full((max(n, 1),), -1, dtype=torch.int32, device=dev)
+        perm = torch.full((max(n, 1),), -1, dtype=torch.int32, device=dev)
         start = torch.full((ncell + 1,), -1, dtype=torch.int32, device=dev)
         torch.cuda.synchronize()
         if noalloc:
@@ -44,14 +45,35 @@ def _bin_both(torch, xyz, dims, cell):
     return outs
 
 
+def _stable_reference(xyz, dims, cell):
+    """The definition: clamped cell of each point, a stable argsort by cell and
+    the start of each cell's run (NumPy on the host)."""
+    cell = np.float32(cell)
+    ijk = np.clip(np.floor(xyz * (np.float32(1.0) / cell)).astype(np.int64), 0,
+                  np.array(dims) - 1)
+    c = (ijk[:, 2] * dims[1] + ijk[:, 1]) * dims[0] + ijk[:, 0]
+    perm = np.argsort(c, kind="stable")
+    start = np.searchsorted(c[perm], np.arange(int(np.prod(dims)) + 1), side="left")
+    return c, perm, start
+
+
 def test_noalloc_matches_scratch_entry_point_two_calls_in_a_row():
     torch = pytest.importorskip("torch")
     cell = 0.024
-    # two different inputs back to back: the second call must not see the first's leftovers
-    for seed, n, dims in ((1, 191_248, (88, 22, 29)), (2, 1_000_000, (160, 80, 60))):
-        ref, got = _bin_both(torch, _points(seed, n, dims, cell), dims, cell)
+    # different inputs back to back: each call must not see the previous one's
+    # leftovers; an empty input; and one whose points lie ~90 % outside the grid,
+    # clamped into a few boundary cells
+    cases = ((1, 191_248, (88, 22, 29), 1.0), (2, 1_000_000, (160, 80, 60), 1.0),
+             (3, 0, (5, 4, 3), 1.0), (4, 20_000, (16, 8, 8), 10.0))
+    for seed, n, dims, spread in cases:
+        xyz = _points(seed, n, dims, cell, spread)
+        ref, got = _bin_both(torch, xyz, dims, cell)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b)   # integer work: bit-exact
+        c, perm, start = _stable_reference(xyz, dims, cell)
+        assert np.array_equal(got[0][:n].astype(np.int64), c)
+        assert np.array_equal(got[1][:n].astype(np.int64), perm)
+        assert np.array_equal(got[2].astype(np.int64), start)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
