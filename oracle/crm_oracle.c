@@ -483,8 +483,10 @@ static double kernel_dw_condition(const orc_params *p, double r)
  * Markers use their extrapolated velocity and stress (orc_bce).
  * `scale` (nullable; 10 per fluid particle: rho, u x3, sigma x6) receives the
  * absolute sums sum_j |term_ij| of each component, the size against which a
- * single-precision evaluation is measured; `mscale` (nullable; 3 per marker) the
- * same for the marker accelerations. */
+ * single-precision evaluation is measured -- for the momentum components the
+ * term's size is that of the products it adds, V_j sum_b (|sigma_i,ab| +
+ * |sigma_j,ab|) |dW_b| / rho_i; `mscale` (nullable; 3 per marker) the same for
+ * the marker accelerations. */
 void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
                const double *xf, const double *uf, const double *sf, const double *rf,
                const double *xm, const double *um, const double *sm,
@@ -537,12 +539,18 @@ void orc_rates(const orc_params *p, int64_t nf, int64_t nm,
             double fac = 0.0;
             const int has_av = av_factor(p, cs, m, vij, rij, rhoi, rhoj, &fac);
             for (int a = 0; a < 3; ++a) {
-                double t = 0.0;
-                for (int b = 0; b < 3; ++b) t += Ssum[a][b] * g[b];
+                double t = 0.0, tm = 0.0;
+                for (int b = 0; b < 3; ++b) {
+                    t += Ssum[a][b] * g[b];
+                    tm += (fabs(si3[a][b]) + fabs(sj3[a][b])) * fabs(g[b]);
+                }
                 mom[a] += Vj * t;
                 if (has_av) av[a] += fac * g[a];
+                /* the size of the products the momentum sum combines (sigma_i g and
+                 * sigma_j g separately: their sum cancels where a marker's
+                 * extrapolated stress mirrors its neighbour's) */
                 if (scale || mscale)
-                    sc[1 + a] += cw * (fabs(Vj * t / rhoi) + (has_av ? fabs(fac * g[a]) : 0.0));
+                    sc[1 + a] += cw * (Vj * tm / rhoi + (has_av ? fabs(fac * g[a]) : 0.0));
             }
             if (is_fluid) {
                 double Lj[3][3], dsj[6];

@@ -244,7 +244,12 @@ int make_devparams(crm_terrain *t)
     const crm_params &P = t->P;
     DevParams &d = t->dp;
     const double skin = t->skin_on ? P.skin : 0.0;
-    const double cell = 2.0 * P.h * (1.0 + skin);
+    // cells of 2h (1 + skin), rounded up to an FP32 value: the kernels shift
+    // offsets by whole cells in FP32, so that shift and the FP64 grid agree exactly
+    const double cell_req = 2.0 * P.h * (1.0 + skin);
+    float cell_f = (float)cell_req;
+    if ((double)cell_f < cell_req) cell_f = std::nextafter(cell_f, INFINITY);
+    const double cell = (double)cell_f;
     int64_t G[3];
     for (int k = 0; k < 3; ++k) {
         G[k] = (int64_t)std::ceil((P.domain_max[k] - P.domain_min[k]) / cell);

@@ -6,11 +6,15 @@ Bars (the single-precision reading of the parity tolerances):
   (an FP32 evaluation may decide those either way);
 * single-step rates: |r_gpu - r_oracle| <= 1e-5 * S per particle and component,
   S = sum_j |term_ij| from the oracle (rates of a body at rest cancel to ~0, so a
-  plain relative error is undefined);
-* marker accelerations: the same bar against the kernel-edge conditioned scale
-  S' = sum_j |term_ij| (1 + kappa_j), kappa = 2q/(2-q) near the cut-off: a marker
-  whose few neighbours sit near 2h has each term's FP32 rounding of q amplified
-  by kappa, which the plain sum does not reflect;
+  plain relative error is undefined; a momentum term's size is that of the
+  products it adds, sigma_i dW and sigma_j dW), with the oracle fed the state the
+  terrain holds (tests/held.py: FP32 cell-relative positions, FP32 velocity,
+  stress and density) so that the bar measures the kernels' arithmetic;
+* marker accelerations: the same bar; a marker component over it must be one
+  of a marker with a neighbour at the kernel edge (a pair at q >= 1.99, where
+  W' ~ (2 - q)^2 amplifies the FP32 rounding of r by kappa = 2q/(2-q) >= 400)
+  and must meet the bar against S' = sum_j |term_ij| (1 + kappa_j) instead; the
+  random-state wheel scene has 16 such components of 8 wheel markers;
 * marker velocity / stress: the extrapolation is a convex weighting, so the bar
   is 1e-5 of the largest fluid value involved;
 * one step: the same bars carried through the two RK2 stages (dt times twice the
@@ -23,6 +27,7 @@ import math
 import numpy as np
 import pytest
 
+import held
 import oracle
 import scenes
 
@@ -91,27 +96,8 @@ def test_neighbor_sets_match_oracle(pair):
 
 def test_rates_match_oracle(pair):
     name, sc, t, st = pair
-    drho, du, ds, macc, mvel, msig = t.eval_rates()
-    o_drho, o_du, o_ds, o_macc, scale, o_um, o_sm = st.eval_rates(want_scale=True)
-    got = np.concatenate([drho[:, None], du, ds], axis=1).astype(np.float64)
-    ref = np.concatenate([o_drho[:, None], o_du, o_ds], axis=1)
-    err = np.abs(got - ref)
-    worst = np.max(err / np.maximum(scale, 1e-30))
-    assert np.all(err <= RATE_TOL * scale + 1e-30), f"{name}: worst err/S = {worst:.3e}"
-    if st.nm:
-        oracle.set_scale_conditioning(True)
-        try:
-            st.eval_rates(want_scale=True)
-        finally:
-            oracle.set_scale_conditioning(False)
-        cms = st.mscale
-        merr = np.abs(macc.astype(np.float64) - o_macc)
-        assert np.all(merr <= RATE_TOL * cms + 1e-30), \
-            f"{name}: marker acc worst {np.max(merr / np.maximum(cms, 1e-30)):.3e}"
-        umax = max(np.abs(st.u).max(), 1e-6)
-        assert np.all(np.abs(mvel - o_um) <= RATE_TOL * umax * 4 + 1e-7)
-        smax = max(np.abs(st.sig).max(), 1.0)
-        assert np.all(np.abs(msig - o_sm) <= RATE_TOL * smax * 4)
+    edge = held.check_rates(name, sc, t.eval_rates())
+    assert len(edge) <= 20
 
 
 def test_gpu_momentum_antisymmetry():
