@@ -68,8 +68,7 @@ struct crm_terrain {
     SortScratch ss{};
     uint32_t *start = nullptr, *nbr = nullptr, *nnb = nullptr;
     float4 *mforce = nullptr;
-    double *partial = nullptr;
-    unsigned *ticket = nullptr;
+    double *partial = nullptr;   // FP64 wrench partials [block][body][6]
     // CUDA graphs of whole steps (runs without active boxes, timing off)
     struct StepGraph {
         cudaGraphExec_t exec = nullptr;
@@ -405,7 +404,6 @@ int alloc_working(crm_terrain *t)
     t->mforce = t->dalloc<float4>(G_WORK, t->capM);
     t->partial = t->dalloc<double>(G_WORK, (size_t)wrench_blocks(t->n_bodym)
                                                * std::max<size_t>(t->hbodies.size(), 1) * 6);
-    t->ticket = t->dalloc<unsigned>(G_WORK, 1);
     t->act = t->dalloc<uint32_t>(G_WORK, t->capM);
     t->act_body = t->dalloc<uint32_t>(G_WORK, std::max(t->n_bodym, 1));
     t->act_bcount = t->dalloc<uint32_t>(G_WORK, 2 * (size_t)compact_blocks(d));
@@ -424,7 +422,6 @@ int alloc_working(crm_terrain *t)
     }
     CRM_CUDA(t, cudaMemsetAsync(t->nnb, 0, N * sizeof(uint32_t), t->st));
     CRM_CUDA(t, cudaMemsetAsync(t->mforce, 0, std::max<int64_t>(t->capM, 1) * sizeof(float4), t->st));
-    CRM_CUDA(t, cudaMemsetAsync(t->ticket, 0, sizeof(unsigned), t->st));
     CRM_CUDA(t, cudaMemsetAsync(t->n_act, 0, 2 * sizeof(int), t->st));
     t->cur = 0;
     t->lists_valid = false;
@@ -925,8 +922,9 @@ void bce(crm_terrain *t, StageArrays S, double tau, int accel, double dt = 0.0, 
     const int *n_act = accel == 1 ? t->n_act + 1 : t->n_act;
     launch(t, K_BCE, [&] { launch_bce(d, S, t->A[c].pos, t->pid[c], t->mloc, t->bodies, t->nbr,
                                       t->nnb, tau, accel, (int)t->nFtot, t->mforce, t->partial,
-                                      t->ticket, dt, integrate, gate, st ? st : t->st, skl, skn,
-                                      t->err, t->mid_frames, act, n_act, t->n_bodym); });
+                                      dt, integrate, gate, st ? st : t->st, skl, skn,
+                                      t->err, t->mid_frames, act, n_act, t->n_bodym); },
+           accel == 1 ? 2 : 1);
 }
 
 void pair(crm_terrain *t, int mode, StageArrays S, StageArrays Y, float dt, RateOut out,
@@ -1092,7 +1090,7 @@ int graph_step(crm_terrain *t, double dt)
         t->prof.rebuilds += 1;
         t->lists_valid = true;
     }
-    if (d.capM > 0) t->prof.launches[K_BCE] += d.n_bodies > 0 ? 3 : 2;
+    if (d.capM > 0) t->prof.launches[K_BCE] += d.n_bodies > 0 ? 4 : 2;
     if (d.capF > 0) {
         t->prof.launches[K_PAIR1] += 1;
         t->prof.launches[K_PAIR2] += 1;
@@ -1383,6 +1381,7 @@ int crm_add_rigid_body(crm_terrain *t, int64_t n, const double *xloc, const doub
     for (int k = 3; k < 7; ++k) b.pose[k] = pose[k] / qn;
     for (int k = 0; k < 6; ++k) b.twist[k] = twist[k];
     b.mass = mass;
+    b.inv_mass = 1.0 / mass;
     b.dof = dof_mask;
     const int id = (int)t->hbodies.size();
     t->hbodies.push_back(b);

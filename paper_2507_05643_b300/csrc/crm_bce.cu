@@ -1,6 +1,8 @@
 // crm_bce.cu -- BCE boundary markers (Sec. 2.4): marker state extrapolated from
 // the fluid, marker accelerations, the FP64 body wrench and the body update,
 // and the compaction of the markers that have fluid in reach.
+#include <algorithm>
+
 #include "crm_internal.cuh"
 
 namespace crm {
@@ -13,12 +15,12 @@ namespace crm {
 //   Stress: sigma_a = [sum_f sigma_f W - ((g - a_body) . sum_f rho_f (x_a - x_f) W) I]
 //   / sum_f W (the pressure extrapolation of the cited scheme in stress form);
 //   without fluid in reach u_a = u_body and sigma_a = 0.
-// ACCEL: 0 = state only; 1 = the accelerations of the body markers (their
-// state already written by a state launch on the same arrays), reduced per
-// block into FP64 force / torque partials, after which the last block to
-// finish sums the partials in a fixed order and advances the bodies (the wrench
-// and body update of Sec. 2.4); 2 = state and accelerations of every marker,
-// the accelerations written to mforce (rate evaluation).  Acceleration: a_a = (1/rho0) sum_f V_f
+// ACCEL: 0 = state only; 1 = the forces of the active body markers (their
+// state already written by a state launch on the same arrays), summed per block
+// and body into FP64 force / torque partials, which k_body_reduce sums in a
+// fixed order before the body update (the wrench and body update of Sec. 2.4);
+// 2 = state and accelerations of every marker, the forces written to mforce
+// (rate evaluation).  Acceleration: a_a = (1/rho0) sum_f V_f
 // (sigma_a + sigma_f) . grad_a W_af + AV, no gravity.
 // FILTER (stage 1 with a Verlet skin): the marker walks its skin list and keeps
 // the fluid particles closer than 2h as its exact list for the rest of the step.
@@ -26,22 +28,24 @@ namespace crm {
 // without fluid neighbours is not read by anyone (the relation is symmetric),
 // so its lanes only take part in the warp and block reductions.
 struct BodyStep {
-    double *partial;      // [block][body][6]
-    unsigned *ticket;     // last-block counter (reset by the last block)
-    BodyDev *bodies;      // advanced by the last block
+    double *partial;      // [block][body][6]: FP64 wrench partials of the wrench pass
+    BodyDev *bodies;      // advanced by k_body_reduce
     double dt;
     int integrate;
     int *gate;            // skin bookkeeping (nullable): marker displacement bound
 };
 
 
-constexpr int kBceLanes = 4;   // lanes sharing one marker's neighbour list
+constexpr int kBceLanes = 4;      // lanes sharing one marker's neighbour list
+constexpr int kWrenchLanes = 16;  // the same for the wrench pass: its few body markers
+                                  // would otherwise leave the GPU nearly idle
 
-// Sum over the kBceLanes lanes of a marker's group (every lane of the warp calls it).
+// Sum over the LANES lanes of a marker's group (every lane of the warp calls it).
+template <int LANES>
 __device__ __forceinline__ float group_sum(float v)
 {
 #pragma unroll
-    for (int o = 1; o < kBceLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 1; o < LANES; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
@@ -80,7 +84,7 @@ __device__ __forceinline__ void body_update(const DevParams &p, const BodyStep &
     }
     for (int k = 0; k < 3; ++k) {
         if (B.dof & (1 << k)) {
-            const double a = F[k] / B.mass + p.g64[k];
+            const double a = F[k] * B.inv_mass + p.g64[k];
             B.twist[k] += bs.dt * a;
             B.acc[k] = a;
         } else {
@@ -100,31 +104,37 @@ __device__ __forceinline__ void body_update(const DevParams &p, const BodyStep &
     if (bs.gate != nullptr) {
         // every marker of the body has moved at most |dc| + 2 sin(theta/2) rmax
         // since the last cell search (theta: rotation since then)
+        // (a bound compared with an FP32 threshold: its square roots in FP32,
+        // the 1.0001 margin covering their rounding)
         double dc2 = 0.0, w = 0.0;
         for (int k = 0; k < 3; ++k) {
             const double d = B.pose[k] - B.ref_pose[k];
             dc2 += d * d;
         }
         for (int k = 0; k < 4; ++k) w += B.pose[3 + k] * B.ref_pose[3 + k];
-        const double sh = sqrt(fmax(0.0, 1.0 - w * w));
-        const double d = sqrt(dc2) + 2.0 * sh * B.rmax;
-        atomicMax(bs.gate + GATE_DISP, __float_as_int((float)(d * d) * 1.0001f));
+        const float sh = sqrtf((float)fmax(0.0, 1.0 - w * w));
+        const float d = sqrtf((float)dc2) + 2.0f * sh * (float)B.rmax;
+        atomicMax(bs.gate + GATE_DISP, __float_as_int(d * d * 1.0001f));
     }
 }
 
-// ACCEL == 1 tail of k_bce: FP64 per-block partial wrench of every body, then
-// the last block sums the partials in a fixed order and advances the bodies.
-__device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float f[3],
-                                                 const float arm[3], int body, bool mine,
-                                                 const BodyStep &bs, unsigned &s_bodies,
-                                                 unsigned &s_last, double (*red)[6])
+// Wrench partials of one block of the wrench pass: for every body with a
+// marker in the block, the FP64 sum of its markers' forces and torques about
+// the centre (torque = arm x f, each product exact in FP64), a fixed shuffle
+// tree per warp and the warps in order.  FP64 arithmetic is slow on this part,
+// so it is spread over the blocks (one partial each) and kept off one SM.
+__device__ __forceinline__ void block_wrench_partial(const DevParams &p, const float f[3],
+                                                     const float arm[3], int body, bool mine,
+                                                     const BodyStep &bs, unsigned &s_bodies,
+                                                     double (*red)[6])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (mine) atomicOr(&s_bodies, 1u << body);
     __syncthreads();
     const int nb = p.n_bodies;
+    const unsigned present_all = s_bodies;
     for (int b = 0; b < nb; ++b) {
-        const bool present = (s_bodies >> b) & 1u;
+        const bool present = (present_all >> b) & 1u;
         if (present) {
             double v[6] = {0, 0, 0, 0, 0, 0};
             if (mine && body == b) {
@@ -133,10 +143,13 @@ __device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float
                 v[4] = (double)arm[2] * f[0] - (double)arm[0] * f[2];
                 v[5] = (double)arm[0] * f[1] - (double)arm[1] * f[0];
             }
+            if (__any_sync(0xffffffffu, mine && body == b)) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
+                for (int k = 0; k < 6; ++k)
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+                    for (int off = 16; off > 0; off >>= 1)
+                        v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+            }
             if (lane == 0)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
@@ -150,30 +163,9 @@ __device__ __forceinline__ void body_wrench_tail(const DevParams &p, const float
         }
         __syncthreads();
     }
-    __threadfence();
-    if (threadIdx.x == 0) s_last = atomicAdd(bs.ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // the final sums: warp w takes bodies w, w + 8, ...; its lanes stride over the
-    // blocks' partials (L2 loads: they were published before the ticket), then a
-    // fixed shuffle tree; lane 0 updates the body (FP64 work kept to one warp per body)
-    for (int b = warp; b < nb; b += kBlock / 32) {
-        double v[6] = {0, 0, 0, 0, 0, 0};
-        for (unsigned q = lane; q < gridDim.x; q += 32)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] += __ldcg(&bs.partial[((size_t)q * nb + b) * 6 + k]);
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-        if (lane == 0) body_update(p, bs, b, v);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *bs.ticket = 0u;
 }
 
-template <int ACCEL, bool FILTER>
+template <int ACCEL, bool FILTER, int LANES = kBceLanes>
 __global__ void __launch_bounds__(kBlock)
 k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
       const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
@@ -185,7 +177,7 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     if (*p.abort) return;
     __shared__ float4 lut[64];
     __shared__ double red[kBlock / 32][6];
-    __shared__ unsigned s_bodies, s_last;
+    __shared__ unsigned s_bodies;
     if (tau == 0.0 && frames != nullptr && bs.dt > 0.0 && blockIdx.x == 0
         && (int)threadIdx.x < p.n_bodies) {
         // the midpoint frames of the following stage-2 launch, once per step
@@ -196,15 +188,15 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     __syncthreads();
     const Sizes z = load_sizes(p);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int q = t & (kBceLanes - 1);           // lane within the marker's group
+    const int q = t & (LANES - 1);           // lane within the marker's group
     int s;
     bool valid;
     if (act != nullptr) {                        // the markers with fluid in reach
-        const int mk = t / kBceLanes;
+        const int mk = t / LANES;
         valid = mk < __ldg(n_act);
         s = valid ? (int)__ldg(&act[mk]) : z.N;
     } else {                                     // every marker slot
-        s = z.nF + t / kBceLanes;
+        s = z.nF + t / LANES;
         valid = s < z.N;
     }
     const int nn = valid ? (int)L.in_n[s] : 0;
@@ -245,15 +237,15 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
         } else {
         // pass 1: extrapolation sums, the list strided over the group's lanes
         // (warp-uniform round count; the next entry is fetched one round ahead)
-        const int rounds = __reduce_max_sync(0xffffffffu, (nn + kBceLanes - 1) / kBceLanes);
+        const int rounds = __reduce_max_sync(0xffffffffu, (nn + LANES - 1) / LANES);
         float w = 0.f, sux = 0.f, suy = 0.f, suz = 0.f, sr[3] = {0.f, 0.f, 0.f};
         float ss[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
         e_nx = q < nn ? ld_list(row + (size_t)q * p.ell) : 0u;
         for (int r = 0; r < rounds; ++r) {
-            const int k = r * kBceLanes + q;
+            const int k = r * LANES + q;
             const uint32_t e = e_nx;
-            if (k + kBceLanes < nn) e_nx = ld_list(row + (size_t)(k + kBceLanes) * p.ell);
+            if (k + LANES < nn) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
             bool keep = false;
             float W = 0.f;
             float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), aj = vj;
@@ -274,7 +266,7 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
             if (FILTER) {
                 // the kept entries, in list order, become the exact list
                 const unsigned b = __ballot_sync(0xffffffffu, keep);
-                const unsigned g = (b >> ((threadIdx.x & 31) & ~(kBceLanes - 1))) & ((1u << kBceLanes) - 1u);
+                const unsigned g = (b >> ((threadIdx.x & 31) & ~(LANES - 1))) & ((1u << LANES) - 1u);
                 const int at = cnt + __popc(g & ((1u << q) - 1u));
                 if (keep && at < p.maxnb) L.out[(size_t)at * p.ell + s] = e;
                 cnt += __popc(g);
@@ -286,12 +278,12 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
             const float rw = vj.w * W;
             sr[0] = fmaf(rw, rx, sr[0]); sr[1] = fmaf(rw, ry, sr[1]); sr[2] = fmaf(rw, rz, sr[2]);
         }
-        w = group_sum(w);
-        sux = group_sum(sux); suy = group_sum(suy); suz = group_sum(suz);
+        w = group_sum<LANES>(w);
+        sux = group_sum<LANES>(sux); suy = group_sum<LANES>(suy); suz = group_sum<LANES>(suz);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) ss[k] = group_sum(ss[k]);
+        for (int k = 0; k < 6; ++k) ss[k] = group_sum<LANES>(ss[k]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sr[k] = group_sum(sr[k]);
+        for (int k = 0; k < 3; ++k) sr[k] = group_sum<LANES>(sr[k]);
         if (FILTER && q == 0 && valid) {
             if (cnt > p.maxnb) atomicOr(L.err, ERR_CAPACITY);
             L.out_n[s] = (uint32_t)min(cnt, p.maxnb);
@@ -320,13 +312,13 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
             // pass 2: marker accelerations (body markers for the wrench; every
             // marker for the rate evaluation)
             const int n2 = (ACCEL == 2 || body >= 0) ? nn : 0;
-            const int rounds2 = __reduce_max_sync(0xffffffffu, (n2 + kBceLanes - 1) / kBceLanes);
+            const int rounds2 = __reduce_max_sync(0xffffffffu, (n2 + LANES - 1) / LANES);
             float mx = 0.f, my = 0.f, mz = 0.f, avx = 0.f, avy = 0.f, avz = 0.f;
             e_nx = q < n2 ? ld_list(row + (size_t)q * p.ell) : 0u;
             for (int r = 0; r < rounds2; ++r) {
-                const int k = r * kBceLanes + q;
+                const int k = r * LANES + q;
                 const uint32_t e = e_nx;
-                if (k + kBceLanes < n2) e_nx = ld_list(row + (size_t)(k + kBceLanes) * p.ell);
+                if (k + LANES < n2) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
                 if (k >= n2) continue;
                 const uint32_t j = e & kIndexMask;
                 const float4 sh = lut[e >> kIndexBits];
@@ -357,8 +349,8 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
                 }
             }
             if (rounds2 > 0) {
-                mx = group_sum(mx); my = group_sum(my); mz = group_sum(mz);
-                avx = group_sum(avx); avy = group_sum(avy); avz = group_sum(avz);
+                mx = group_sum<LANES>(mx); my = group_sum<LANES>(my); mz = group_sum<LANES>(mz);
+                avx = group_sum<LANES>(avx); avy = group_sum<LANES>(avy); avz = group_sum<LANES>(avz);
             }
             const float ir = 1.0f / p.rho0;
             f[0] = p.m * (mx * ir + avx);
@@ -371,8 +363,30 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     if constexpr (ACCEL == 2) {
         if (valid && q == 0) mforce[s - z.nF] = make_float4(f[0], f[1], f[2], __int_as_float(body));
     } else if constexpr (ACCEL == 1) {
-        body_wrench_tail(p, f, arm, body, q == 0 && nn > 0 && body >= 0, bs, s_bodies, s_last, red);
+        block_wrench_partial(p, f, arm, body, valid && q == 0 && nn > 0 && body >= 0, bs, s_bodies,
+                             red);
     }
+}
+
+// The soil wrench of body b = blockIdx.x (Sec. 2.4): the sum of the wrench
+// pass's block partials in a fixed order (lane l takes blocks l, l + 32, ...,
+// then a fixed shuffle tree), then the body update -- one warp per body.
+__global__ void __launch_bounds__(32)
+k_body_reduce(DevParams p, BodyStep bs, const int *__restrict__ n_act_body)
+{
+    if (*p.abort) return;
+    const int b = blockIdx.x, lane = threadIdx.x, nb = p.n_bodies;
+    // the blocks of the wrench pass that held active body markers
+    const int n_blocks = (int)grid_for((int64_t)__ldg(n_act_body) * kWrenchLanes);
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = lane; q < n_blocks; q += 32)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += bs.partial[((size_t)q * nb + b) * 6 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0) body_update(p, bs, b, v);
 }
 
 // Markers with a non-empty list, compacted in slot order at each list rebuild
@@ -456,32 +470,35 @@ k_marker_compact(DevParams p, const uint32_t *__restrict__ nnb, const uint32_t *
 void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
                 const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
-                unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
+                double dt, int integrate, int *gate, cudaStream_t st,
                 const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames,
                 const uint32_t *act, const int *n_act, int64_t body_markers)
 {
-    BodyStep bs{partial, ticket, bodies, dt, integrate, gate};
+    BodyStep bs{partial, bodies, dt, integrate, gate};
     if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
         k_bce<0, true><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
-                                                         act, n_act, tau, n_fluid_total, mforce, bs);
+                                                         act, n_act, tau, n_fluid_total, mforce,
+                                                         bs);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
-    if (accel == 0)
+    if (accel == 0) {
         k_bce<0, false><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
                                                           act, n_act, tau, n_fluid_total, mforce, bs);
-    else if (accel == 1)
-        k_bce<1, false><<<wrench_blocks(body_markers), kBlock, 0, st>>>(
+    } else if (accel == 1) {
+        k_bce<1, false, kWrenchLanes><<<wrench_blocks(body_markers), kBlock, 0, st>>>(
             p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
-    else
+        k_body_reduce<<<(unsigned)std::max(p.n_bodies, 1), 32, 0, st>>>(p, bs, n_act);
+    } else {
         k_bce<2, false><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
                                                           act, n_act, tau, n_fluid_total, mforce, bs);
+    }
 }
 
 unsigned bce_blocks(const DevParams &p) { return grid_for((int64_t)p.capM * kBceLanes); }
 
-unsigned wrench_blocks(int64_t body_markers) { return grid_for(body_markers * kBceLanes); }
+unsigned wrench_blocks(int64_t body_markers) { return grid_for(body_markers * kWrenchLanes); }
 
 unsigned compact_blocks(const DevParams &p) { return grid_for(p.capM, kCompactBlock); }
 

@@ -149,6 +149,7 @@ struct BodyDev {
     double alpha[3];    // angular acceleration at the last update (free angular DOFs)
     double inertia[3];  // principal moments of inertia in the body frame
     double load[6];     // external force and torque about the centre, added to the soil's
+    double inv_mass;    // 1 / mass (FP64 division is a long sequence on the device)
 };
 
 // Body of the particle with id `id`: -1 for fluid particles and fixed markers.
@@ -374,7 +375,7 @@ struct ListIO {
 
 // ---------------------------------------------------------------------------
 // Launch helpers shared by the translation units.
-inline unsigned grid_for(int64_t n, int block = kBlock)
+__host__ __device__ inline unsigned grid_for(int64_t n, int block = kBlock)
 {
     const int64_t g = (n + block - 1) / block;
     return (unsigned)(g > 0 ? g : 1);
@@ -445,9 +446,11 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
                  const uint32_t *nbr, const uint32_t *nnb, const uint32_t *pid, float dt,
                  RateOut out, int *err, const float4 *xref, int *gate, cudaStream_t st,
                  const uint32_t *sk_nbr = nullptr, const uint32_t *sk_nnb = nullptr);
-// BCE state of every marker slot of S at stage offset tau; accel 1 also sums
-// the body wrench (FP64) and, in the last block, advances the bodies by dt
-// (integrate != 0); accel 2 writes every marker's force to mforce.  With
+// BCE state of every marker slot of S at stage offset tau; accel 1 instead
+// sums the active body markers' forces and torques per block into FP64
+// partials (wrench_blocks(body_markers) blocks x bodies x 6), then a second
+// kernel sums the partials per body in a fixed order and advances the bodies
+// by dt (integrate != 0); accel 2 writes every marker's force to mforce.  With
 // sk_nbr (stage 1 with a skin) the markers walk their skin lists and write
 // their exact lists to nbr / nnb.  frames (kMaxBodies entries): a launch at
 // tau = 0 with dt > 0 writes the bodies' frames at dt / 2 there, and a launch
@@ -457,7 +460,7 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
 void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const uint32_t *pid,
                 const double *mloc, BodyDev *bodies, const uint32_t *nbr, const uint32_t *nnb,
                 double tau, int accel, int n_fluid_total, float4 *mforce, double *partial,
-                unsigned *ticket, double dt, int integrate, int *gate, cudaStream_t st,
+                double dt, int integrate, int *gate, cudaStream_t st,
                 const uint32_t *sk_nbr, const uint32_t *sk_nnb, int *err, BodyFrame *frames,
                 const uint32_t *act, const int *n_act, int64_t body_markers);
 unsigned bce_blocks(const DevParams &p);
