@@ -470,10 +470,37 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_sample(scs, budget_s: float) -> dict:
+    """The FP64 oracle on a bounded sample of a workload: whole steps of each scene
+    in `scs` (at least 2 each) within ~budget_s, as particle-steps per second."""
+    import oracle
+    done, el = 0, 0.0
+    per = budget_s / max(len(scs), 1)
+    parts = []
+    for sc in scs:
+        st = oracle.State(sc)
+        t0 = time.perf_counter()
+        n = 0
+        while n < 2 or time.perf_counter() - t0 < per:
+            st.step()
+            n += 1
+        e = time.perf_counter() - t0
+        done += sc.n_fluid * n
+        el += e
+        parts.append(f"{sc.n_fluid:,} SPH x {n} steps")
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{'; '.join(parts)} ({el:.1f} s, FP64, OpenMP), cpu={_cpu_model()}"}
+
+
 def run_batch(args):
-    """The batched ensemble (64 single-wheel bins of uneven size, each on its own
-    stream, stepped by one crm_batch_step per step after a per-member autotune)
-    against the same members stepped one at a time (the per-instance form)."""
+    """The batched ensemble (64 single-wheel bins of uneven size) after a
+    per-member autotune (lanes x cell tile), stepped by crm_batch_step in its
+    stream form (each member's step graph on its own stream; the library's
+    default and the faster form here) -- the headline -- and in its persistent
+    form (one graph per batch step, one launch per stage over all bins), against
+    the same members stepped one at a time (the per-instance form)."""
+    import numpy as np
     import torch
 
     import paper_2507_05643_b300 as crm
@@ -488,18 +515,24 @@ def run_batch(args):
     main = torch.cuda.Stream(device=dev)
     batch = crm.Batch(mem, stream=main)
     picks = batch.autotune(dts, trial_steps=3)
-    batch.step(dts, args.warmup)
-    torch.cuda.synchronize(dev)
-    n_act = sum(m.counts()[0] for m in mem)
+
+    def timed(persistent: bool):
+        batch.set_persistent(persistent)
+        batch.step(dts, args.warmup)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(main):
+            e0.record(main)
+            batch.step(dts, args.steps)
+            e1.record(main)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    ms_pers = timed(True)
     sampler = ClockSampler(0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(main):
-        e0.record(main)
-        batch.step(dts, args.steps)
-        e1.record(main)
-    torch.cuda.synchronize(dev)
+    ms_b = timed(False)
     clocks = sampler.stop()
-    ms_b = e0.elapsed_time(e1)
+    n_act = sum(m.counts()[0] for m in mem)
     # per-instance form: each member alone, one after the other
     ms_s = 0.0
     for m, st, dt in zip(mem, streams, dts):
@@ -511,6 +544,8 @@ def run_batch(args):
         torch.cuda.synchronize(dev)
         ms_s += a.elapsed_time(b)
     units = n_act * args.steps
+    lanes = picks & 0xF
+    tile = [f"{(p >> 4) & 0xF}x{(p >> 8) & 0xF}x{(p >> 12) & 0xF}" for p in picks.tolist()]
     line = {"metric": METRIC, "value": units / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -520,12 +555,27 @@ def run_batch(args):
                                    f"SPH each ({sum(b.n_fluid for b in bins):,} in total), slip "
                                    "U(0.1,0.7), friction U(25,40) deg, cohesion U(0,2000) Pa, "
                                    "dt=5e-5 s, one batched step per step",
+                       "form": "streams: each member's step graph on its own stream",
                        "l2": "not flushed: the ensemble's working set (~10 GB) exceeds L2",
-                       "pair_lanes": {str(k): int((picks == k).sum()) for k in (1, 2, 4)}},
+                       "pair_lanes": {str(k): int((lanes == k).sum()) for k in (1, 2, 4)},
+                       "cell_tiles": {k: tile.count(k) for k in sorted(set(tile))}},
+            "persistent": {"value": units / (ms_pers * 1e-3), "ms_per_step": ms_pers / args.steps,
+                           "form": "one graph per batch step: every member's gated search, "
+                                   "then one persistent launch per stage over all bins"},
             "sequential": {"value": units / (ms_s * 1e-3), "ms_per_step": ms_s / args.steps,
                            "form": "the same members stepped one at a time"},
             "batched_over_sequential": ms_s / ms_b,
+            "persistent_over_streams": ms_b / ms_pers,
+            "gpu_launches": sum(m.profile()["launches"][k] for m in mem
+                                for k in m.profile()["launches"]),
             "clocks": clocks}
+    if not args.no_cpu_baseline:
+        sizes = [b.n_fluid for b in bins]
+        order = np.argsort(sizes)
+        pick3 = [bins[int(order[0])], bins[int(order[len(order) // 2])], bins[int(order[-1])]]
+        line["cpu_baseline"] = _oracle_sample(pick3, args.cpu_seconds)
+        line["cpu_baseline"]["sample"] = ("smallest, median and largest bins: "
+                                          + line["cpu_baseline"]["sample"])
     print(json.dumps(line), flush=True)
     batch.close()
 

@@ -388,11 +388,20 @@ int crm_debug_wait_fault(int32_t on);
 /* ------------------------------------------------------------------------
  * Batches (an ensemble of independent terrains, e.g. many single-wheel bins of
  * uneven size; the paper runs one terrain at a time, this is the library's own
- * addition).  Each member runs on its own non-default CUDA stream (members
- * that share a stream run one after the other); a batch step enqueues one step
- * of every member on its stream (one replayed step graph each), so members on
- * different streams run concurrently, bracketed by a fork from and a join to
- * the batch's stream.  The batch does not own its members. */
+ * addition).  Two forms:
+ *   - streams (the default): each member runs on its own non-default CUDA
+ *     stream (members that share a stream run one after the other); a batch step
+ *     enqueues one step of every member on its stream (one replayed step graph
+ *     each), so members on different streams run concurrently, bracketed by a
+ *     fork from and a join to the batch's stream;
+ *   - persistent (crm_batch_set_persistent): one CUDA graph per batch step on
+ *     the batch's stream: every member's search decision and gated cell search
+ *     as parallel branches, then one persistent launch per stage over all
+ *     members (marker state, pair sums of stage 1, midpoint marker state, pair
+ *     sums of stage 2 beside the wrench pass and the body updates) whose blocks
+ *     take the members' blocks off a work queue; the per-member arithmetic is
+ *     that of the members' own steps, so both forms give the same bits.
+ * The batch does not own its members. */
 typedef struct crm_batch crm_batch;
 
 /* Batch of n members (distinct handles, each on a non-default stream) joined on
@@ -405,11 +414,21 @@ int crm_batch_create(int32_t n, crm_terrain *const *members, void *stream, crm_b
  * first member error. */
 int crm_batch_step(crm_batch *b, const double *dt, int32_t n_steps);
 
-/* Per-member tuning of crm_set_pair_lanes: each member runs 1 + trial_steps
- * steps with each choice, timed on its own stream, and keeps the faster; the
+/* Per-member tuning of crm_set_pair_lanes (1, 2, 4) and crm_set_cell_tile
+ * (1 x 1 x 1 or 4 x 2 x 2 cells): each member runs 1 + trial_steps steps with
+ * each of the six choices, timed on its own stream, and keeps the fastest; the
  * trial steps are ordinary steps (the simulation advances).  choice (nullable,
- * n entries) receives the picks.  Synchronises the members' streams. */
+ * n entries) receives the picks as lanes | nx << 4 | ny << 8 | nz << 12.
+ * Synchronises the members' streams. */
 int crm_batch_autotune(crm_batch *b, const double *dt, int32_t trial_steps, int32_t *choice);
+
+/* Select the form of crm_batch_step: on = 1 persistent, 0 streams (the
+ * default).  The persistent form needs every member with a Verlet skin
+ * (skin > 0), ps_freq = 1 and no active boxes (crm_batch_step returns
+ * CRM_EINVAL otherwise); its graph is built at the first step and rebuilt
+ * when the time steps or a member's tuning change.  CRM_EINVAL for a null
+ * batch or another value of on. */
+int crm_batch_set_persistent(crm_batch *b, int32_t on);
 
 int crm_batch_destroy(crm_batch *b);
 

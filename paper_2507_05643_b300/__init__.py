@@ -96,6 +96,7 @@ _sig("crm_batch_create", C.c_int, [_i32, C.POINTER(_T), _vp, C.POINTER(_B)])
 _sig("crm_batch_step", C.c_int, [_B, _vp, _i32])
 _sig("crm_batch_autotune", C.c_int, [_B, _vp, _i32, _vp])
 _sig("crm_batch_destroy", C.c_int, [_B])
+_sig("crm_batch_set_persistent", C.c_int, [_B, _i32])
 _sig("crm_set_body_load", C.c_int, [_T, _i32, _vp, _vp])
 _sig("crm_add_active_box", C.c_int, [_T, _i32, _vp, _vp, C.c_double])
 _sig("crm_step", C.c_int, [_T, C.c_double, _i32])
@@ -138,6 +139,7 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_set_body_load", "crm_add_active_box", "crm_step", "crm_set_pair_lanes", "crm_set_cell_tile",
            "crm_debug_wait_fault",
            "crm_batch_create", "crm_batch_step", "crm_batch_autotune", "crm_batch_destroy",
+           "crm_batch_set_persistent",
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_diagnostics", "crm_get_counts",
            "crm_eval_rates", "crm_get_neighbors", "crm_state_bytes", "crm_save_state",
            "crm_load_state", "crm_bin_scratch_bytes", "crm_bin_points", "crm_kernel_name",
@@ -477,6 +479,13 @@ class Batch:
         rc = _lib.crm_batch_step(self._b, _ptr(self._dts(dt)), int(n_steps))
         if rc != CRM_OK:
             raise CrmError(rc, "crm_batch_step failed (see the members' last errors)")
+
+    def set_persistent(self, on: bool = True):
+        """Step the batch by one graph with one persistent launch per stage over
+        all members (on), or by the members' own graphs on their streams (off)."""
+        rc = _lib.crm_batch_set_persistent(self._b, int(bool(on)))
+        if rc != CRM_OK:
+            raise CrmError(rc, "crm_batch_set_persistent failed")
 
     def autotune(self, dt, trial_steps: int = 3) -> np.ndarray:
         choice = np.zeros(len(self.members), np.int32)

@@ -1833,7 +1833,298 @@ struct crm_batch {
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
     std::string msg;
+    // persistent form (crm_batch_set_persistent): one step graph for the whole
+    // batch -- every member's search decision and gated search, then one
+    // persistent launch per stage over all members
+    bool persistent = false;
+    cudaStream_t cap = nullptr, side = nullptr;   // capture streams
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<double> gdt;                      // the time steps of the graph
+    MemberDev *dmem = nullptr;                    // device tables of the graph
+    int *dtab = nullptr;
+    unsigned *dqueue = nullptr;
+    int launches_per_step = 0;
+    void drop()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        if (dmem) cudaFree(dmem);
+        if (dtab) cudaFree(dtab);
+        if (dqueue) cudaFree(dqueue);
+        dmem = nullptr;
+        dtab = nullptr;
+        dqueue = nullptr;
+        gdt.clear();
+    }
 };
+
+namespace {
+
+// Capture terrain t's search decision and its gated cell search (the
+// conditional branch of its step graph) into graph g as a root branch; *out
+// receives the conditional node.
+int append_member_search(crm_terrain *t, cudaGraph_t g, cudaGraphNode_t *out)
+{
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    cudaStream_t user = t->st;
+    const bool timing = t->timing;
+    const crm_profile saved = t->prof;
+    t->st = t->cap_st;
+    t->timing = false;
+    const DevParams &d = t->dp;
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    cudaGraphNode_t dec = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(t->st, g, nullptr, nullptr, 0, mode);
+    if (e == cudaSuccess) {
+        launch_decide(d, t->gate, (unsigned long long)h, 1, t->st);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(t->st, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+        if (e == cudaSuccess && nd == 1) dec = deps[0];
+        cudaGraph_t g2 = g;
+        const cudaError_t e2 = cudaStreamEndCapture(t->st, &g2);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && dec == nullptr) e = cudaErrorUnknown;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cn, g, &dec, nullptr, 1, &cp);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(t->st, body, nullptr, nullptr, 0, mode);
+        if (e == cudaSuccess) {
+            enqueue_search(t);
+            e = cudaStreamEndCapture(t->st, &body);
+        }
+    }
+    t->st = user;
+    t->timing = timing;
+    t->prof = saved;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CRM_ECUDA;
+    }
+    *out = cn;
+    return CRM_OK;
+}
+
+// Work table of one batched launch (members and their block counts) appended to
+// the host table; returns {offset of the member list, offset of the prefix
+// offsets, count, total blocks}.
+struct Work { int mlist, off, n, total; };
+
+Work add_work(std::vector<int> &tab, const std::vector<std::pair<int, int>> &mb)
+{
+    Work w{(int)tab.size(), 0, (int)mb.size(), 0};
+    for (auto &x : mb) tab.push_back(x.first);
+    w.off = (int)tab.size();
+    int acc = 0;
+    tab.push_back(0);
+    for (auto &x : mb) {
+        acc += x.second;
+        tab.push_back(acc);
+    }
+    w.total = acc;
+    return w;
+}
+
+// Build the persistent batch step graph for time steps dt (member i: dt[i]).
+int batch_build(crm_batch *b, const double *dt)
+{
+    b->drop();
+    const int n = (int)b->m.size();
+    for (int i = 0; i < n; ++i) {
+        crm_terrain *t = b->m[i];
+        int rc = commit(t);
+        if (rc) return rc;
+        if (!t->skin_on || t->active || t->P.ps_freq != 1 || !t->graphs || !t->cap_st
+            || t->dp.capN < 1 || t->frozen) {
+            b->msg = "persistent batch: every member needs a Verlet skin, ps_freq 1, no active "
+                     "boxes and step graphs";
+            return CRM_EINVAL;
+        }
+    }
+    // members' descriptors
+    std::vector<MemberDev> hm(n);
+    for (int i = 0; i < n; ++i) {
+        crm_terrain *t = b->m[i];
+        const int c = t->cur;
+        MemberDev &M = hm[i];
+        M.p = t->dp;
+        M.S = t->A[c];
+        M.MID = t->MID;
+        M.pid = t->pid[c];
+        M.mloc = t->mloc;
+        M.bodies = t->bodies;
+        M.frames = t->mid_frames;
+        M.nbr = t->nbr;
+        M.nnb = t->nnb;
+        M.sk_nbr = t->sk_nbr;
+        M.sk_nnb = t->sk_nnb;
+        M.act = t->act;
+        M.act_body = t->act_body;
+        M.n_act = t->n_act;
+        M.mforce = t->mforce;
+        M.partial = t->partial;
+        M.xref = t->xref;
+        M.gate = t->gate;
+        M.err = t->err;
+        M.n_fluid_total = (int)t->nFtot;
+        M.n_bodym = (int)t->n_bodym;
+        M.dt = dt[i];
+    }
+    // work tables: BCE state launches, the wrench, stage 1 by kernel shape, stage 2
+    // by (lanes, kernel shape), the (member, body) pairs of the body updates
+    std::vector<int> tab;
+    std::vector<std::pair<int, int>> bce, wr;
+    std::vector<int> pairs;
+    std::vector<std::pair<int, std::vector<std::pair<int, int>>>> p1, p2;   // key -> members
+    auto group = [](std::vector<std::pair<int, std::vector<std::pair<int, int>>>> &gs, int key)
+        -> std::vector<std::pair<int, int>> & {
+        for (auto &g : gs)
+            if (g.first == key) return g.second;
+        gs.push_back({key, {}});
+        return gs.back().second;
+    };
+    for (int i = 0; i < n; ++i) {
+        const DevParams &d = hm[i].p;
+        if (d.capM > 0) bce.push_back({i, (int)bce_blocks(d)});
+        if (d.capM > 0 && d.n_bodies > 0) {
+            wr.push_back({i, (int)wrench_blocks(b->m[i]->n_bodym)});
+            for (int q = 0; q < d.n_bodies; ++q) {
+                pairs.push_back(i);
+                pairs.push_back(q);
+            }
+        }
+        if (d.capF > 0) {
+            const int kav = pair_kav(d), ln = pair_lanes_of(d);
+            group(p1, kav).push_back({i, (int)grid_for(d.capF, 128)});
+            group(p2, 8 * kav + ln).push_back({i, (int)grid_for((int64_t)d.capF * ln, 128)});
+        }
+    }
+    const Work w_bce = add_work(tab, bce), w_wr = add_work(tab, wr);
+    std::vector<std::pair<int, Work>> w1, w2;
+    for (auto &g : p1) w1.push_back({g.first, add_work(tab, g.second)});
+    for (auto &g : p2) w2.push_back({g.first, add_work(tab, g.second)});
+    const int pair_at = (int)tab.size();
+    tab.insert(tab.end(), pairs.begin(), pairs.end());
+    const int nq = 4 + (int)w1.size() + (int)w2.size();
+    if (cudaMalloc(&b->dmem, sizeof(MemberDev) * n) != cudaSuccess
+        || cudaMalloc(&b->dtab, sizeof(int) * std::max<size_t>(tab.size(), 1)) != cudaSuccess
+        || cudaMalloc(&b->dqueue, sizeof(unsigned) * 2 * nq) != cudaSuccess) {
+        cudaGetLastError();
+        b->drop();
+        return CRM_ENOMEM;
+    }
+    if (cudaMemcpy(b->dmem, hm.data(), sizeof(MemberDev) * n, cudaMemcpyHostToDevice) != cudaSuccess
+        || cudaMemcpy(b->dtab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice)
+               != cudaSuccess
+        || cudaMemset(b->dqueue, 0, sizeof(unsigned) * 2 * nq) != cudaSuccess) {
+        cudaGetLastError();
+        b->drop();
+        return CRM_ECUDA;
+    }
+    // the graph: every member's search branch, then the batched stages
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return CRM_ECUDA;
+    std::vector<cudaGraphNode_t> deps(n);
+    for (int i = 0; i < n; ++i) {
+        const int rc = append_member_search(b->m[i], g, &deps[i]);
+        if (rc) {
+            cudaGraphDestroy(g);
+            b->drop();
+            return rc;
+        }
+    }
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(b->cap, g, deps.data(), nullptr, deps.size(), mode);
+    int launches = 0;
+    if (e == cudaSuccess) {
+        const int *T = b->dtab;
+        unsigned *Q = b->dqueue;
+        auto bce_go = [&](int kind, const Work &w, cudaStream_t s, unsigned *q) {
+            if (w.total > 0) {
+                launch_batch_bce(kind, b->dmem, T + w.mlist, T + w.off, w.n, w.total, q, s);
+                ++launches;
+            }
+        };
+        bce_go(0, w_bce, b->cap, Q);
+        int qi = 4;
+        for (auto &x : w1) {
+            launch_batch_pair(kStage1, 1, x.first, b->dmem, T + x.second.mlist, T + x.second.off,
+                              x.second.n, x.second.total, Q + 2 * qi++, b->cap);
+            ++launches;
+        }
+        bce_go(1, w_bce, b->cap, Q + 2);
+        const bool fork = w_wr.total > 0;
+        if (fork) {
+            cudaEventRecord(b->ev_fork, b->cap);
+            cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+            bce_go(2, w_wr, b->side, Q + 4);
+            launch_batch_reduce(b->dmem, T + pair_at, (int)pairs.size() / 2, b->side);
+            ++launches;
+        }
+        for (auto &x : w2) {
+            launch_batch_pair(kStage2, x.first % 8, x.first / 8, b->dmem, T + x.second.mlist,
+                              T + x.second.off, x.second.n, x.second.total, Q + 2 * qi++, b->cap);
+            ++launches;
+        }
+        if (fork) {
+            cudaEventRecord(b->ev_join, b->side);
+            cudaStreamWaitEvent(b->cap, b->ev_join, 0);
+        }
+        e = cudaStreamEndCapture(b->cap, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->drop();
+        b->msg = std::string("persistent batch graph: ") + cudaGetErrorString(e);
+        return CRM_ECUDA;
+    }
+    b->launches_per_step = launches;
+    b->gdt.assign(dt, dt + n);
+    return CRM_OK;
+}
+
+// One step of every member by the persistent batch graph, and the members'
+// host bookkeeping of it (as graph_step keeps it).
+int batch_graph_step(crm_batch *b, const double *dt)
+{
+    const int n = (int)b->m.size();
+    bool same = b->exec && (int)b->gdt.size() == n;
+    for (int i = 0; same && i < n; ++i) same = b->gdt[i] == dt[i];
+    if (!same) {
+        const int rc = batch_build(b, dt);
+        if (rc) return rc;
+    }
+    if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) return CRM_ECUDA;
+    for (int i = 0; i < n; ++i) {
+        crm_terrain *t = b->m[i];
+        t->prof.launches[K_SKIN] += 1;
+        if (t->dp.capM > 0) t->prof.launches[K_BCE] += t->dp.n_bodies > 0 ? 4 : 2;
+        if (t->dp.capF > 0) {
+            t->prof.launches[K_PAIR1] += 1;
+            t->prof.launches[K_PAIR2] += 1;
+        }
+        t->prof.rebuilds += 1;
+        t->lists_valid = true;
+        t->step_index += 1;
+        t->time += dt[i];
+        t->prof.steps += 1;
+    }
+    return CRM_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1850,7 +2141,11 @@ int crm_batch_create(int32_t n, crm_terrain *const *members, void *stream, crm_b
     b->m.assign(members, members + n);
     b->st = (cudaStream_t)stream;
     b->join.assign(n, nullptr);
-    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess
+              && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess
+              && cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess
+              && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess
+              && cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess;
     for (int i = 0; ok && i < n; ++i)
         ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -1865,6 +2160,11 @@ int crm_batch_create(int32_t n, crm_terrain *const *members, void *stream, crm_b
 int crm_batch_destroy(crm_batch *b)
 {
     if (!b) return CRM_OK;
+    b->drop();
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->fork) cudaEventDestroy(b->fork);
     for (cudaEvent_t e : b->join)
         if (e) cudaEventDestroy(e);
@@ -1876,6 +2176,24 @@ int crm_batch_step(crm_batch *b, const double *dt, int32_t n_steps)
 {
     if (!b || !dt || n_steps < 0) return CRM_EINVAL;
     const int n = (int)b->m.size();
+    if (b->persistent) {
+        // the batch's stream waits for the members' pending work, runs the steps,
+        // and the members' streams wait for it
+        for (int i = 0; i < n; ++i) {
+            if (b->m[i]->frozen) return CRM_ESTATE;
+            if (cudaEventRecord(b->join[i], b->m[i]->st) != cudaSuccess
+                || cudaStreamWaitEvent(b->st, b->join[i], 0) != cudaSuccess)
+                return CRM_ECUDA;
+        }
+        for (int s = 0; s < n_steps; ++s) {
+            const int rc = batch_graph_step(b, dt);
+            if (rc) return rc;
+        }
+        if (cudaEventRecord(b->fork, b->st) != cudaSuccess) return CRM_ECUDA;
+        for (int i = 0; i < n; ++i)
+            if (cudaStreamWaitEvent(b->m[i]->st, b->fork, 0) != cudaSuccess) return CRM_ECUDA;
+        return CRM_OK;
+    }
     if (cudaEventRecord(b->fork, b->st) != cudaSuccess) return CRM_ECUDA;
     for (int i = 0; i < n; ++i)
         if (cudaStreamWaitEvent(b->m[i]->st, b->fork, 0) != cudaSuccess) return CRM_ECUDA;
@@ -1892,6 +2210,14 @@ int crm_batch_step(crm_batch *b, const double *dt, int32_t n_steps)
     return CRM_OK;
 }
 
+int crm_batch_set_persistent(crm_batch *b, int32_t on)
+{
+    if (!b || (on != 0 && on != 1)) return CRM_EINVAL;
+    b->persistent = on != 0;
+    b->drop();
+    return CRM_OK;
+}
+
 int crm_batch_autotune(crm_batch *b, const double *dt, int32_t trial_steps, int32_t *choice)
 {
     if (!b || !dt || trial_steps < 1) return CRM_EINVAL;
@@ -1900,37 +2226,51 @@ int crm_batch_autotune(crm_batch *b, const double *dt, int32_t trial_steps, int3
         cudaGetLastError();
         return CRM_ECUDA;
     }
+    // candidates: lanes per particle of the exact-list pair kernels x cell tiles
+    // of the sort order (row-major, and 4 x 2 x 2 cells)
+    static const int tiles[2][3] = {{1, 1, 1}, {4, 2, 2}};
     int rc = CRM_OK;
     for (size_t i = 0; i < b->m.size() && rc == CRM_OK; ++i) {
         crm_terrain *t = b->m[i];
         float best = 0.f;
-        int pick = 2;
-        for (int lanes = 1; lanes <= 4 && rc == CRM_OK; lanes *= 2) {
-            crm_set_pair_lanes(t, lanes);
-            rc = crm_step(t, dt[i], 1);   // capture the graphs outside the timing
-            if (rc) break;
-            cudaEventRecord(e0, t->st);
-            rc = crm_step(t, dt[i], trial_steps);
-            cudaEventRecord(e1, t->st);
-            if (rc) break;
-            float ms = 0.f;
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                cudaGetLastError();
-                rc = CRM_ECUDA;
-                break;
+        int pick_l = 2, pick_t = 0;
+        bool first = true;
+        for (int tl = 0; tl < 2 && rc == CRM_OK; ++tl)
+            for (int lanes = 1; lanes <= 4 && rc == CRM_OK; lanes *= 2) {
+                crm_set_pair_lanes(t, lanes);
+                rc = crm_set_cell_tile(t, tiles[tl][0], tiles[tl][1], tiles[tl][2]);
+                if (rc) break;
+                rc = crm_step(t, dt[i], 1);   // capture the graphs (and re-sort) outside the timing
+                if (rc) break;
+                cudaEventRecord(e0, t->st);
+                rc = crm_step(t, dt[i], trial_steps);
+                cudaEventRecord(e1, t->st);
+                if (rc) break;
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) != cudaSuccess
+                    || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = CRM_ECUDA;
+                    break;
+                }
+                if (first || ms < best) {
+                    best = ms;
+                    pick_l = lanes;
+                    pick_t = tl;
+                    first = false;
+                }
             }
-            if (lanes == 1 || ms < best) {
-                best = ms;
-                pick = lanes;
-            }
-        }
         if (rc == CRM_OK) {
-            crm_set_pair_lanes(t, pick);
-            if (choice) choice[i] = pick;
+            crm_set_pair_lanes(t, pick_l);
+            rc = crm_set_cell_tile(t, tiles[pick_t][0], tiles[pick_t][1], tiles[pick_t][2]);
+            if (choice)
+                choice[i] = pick_l | tiles[pick_t][0] << 4 | tiles[pick_t][1] << 8
+                            | tiles[pick_t][2] << 12;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    b->drop();   // the persistent graph holds the old choices
     return rc;
 }
 

@@ -126,7 +126,7 @@ __device__ __forceinline__ void body_update(const DevParams &p, const BodyStep &
 __device__ __forceinline__ void block_wrench_partial(const DevParams &p, const float f[3],
                                                      const float arm[3], int body, bool mine,
                                                      const BodyStep &bs, unsigned &s_bodies,
-                                                     double (*red)[6])
+                                                     double (*red)[6], int vb)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (mine) atomicOr(&s_bodies, 1u << body);
@@ -159,26 +159,28 @@ __device__ __forceinline__ void block_wrench_partial(const DevParams &p, const f
             double a = 0.0;
             if (present)
                 for (int w = 0; w < kBlock / 32; ++w) a += red[w][threadIdx.x];
-            bs.partial[((size_t)blockIdx.x * nb + b) * 6 + threadIdx.x] = a;
+            bs.partial[((size_t)vb * nb + b) * 6 + threadIdx.x] = a;
         }
         __syncthreads();
     }
 }
 
-template <int ACCEL, bool FILTER, int LANES = kBceLanes>
-__global__ void __launch_bounds__(kBlock)
-k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
-      const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
-      const BodyDev *bodies, BodyFrame *frames, ListIO L, const uint32_t *__restrict__ act,
-      const int *__restrict__ n_act, double tau, int n_fluid_total, float4 *__restrict__ mforce,
-      BodyStep bs)
+// The work of block vb of a k_bce launch (a kBlock-thread block; every thread
+// of the block calls it; lut, red and s_bodies are the block's shared arrays).
+template <int ACCEL, bool FILTER, int LANES>
+__device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
+                                          const float4 *__restrict__ home_pos,
+                                          const uint32_t *__restrict__ pid,
+                                          const double *__restrict__ mloc, const BodyDev *bodies,
+                                          BodyFrame *frames, const ListIO &L,
+                                          const uint32_t *__restrict__ act,
+                                          const int *__restrict__ n_act, double tau,
+                                          int n_fluid_total, float4 *__restrict__ mforce,
+                                          const BodyStep &bs, int vb, float4 *lut,
+                                          double (*red)[6], unsigned &s_bodies)
 {
     static_assert(!(FILTER && ACCEL != 0), "filtering runs in stage 1 only (no accelerations)");
-    if (*p.abort) return;
-    __shared__ float4 lut[64];
-    __shared__ double red[kBlock / 32][6];
-    __shared__ unsigned s_bodies;
-    if (tau == 0.0 && frames != nullptr && bs.dt > 0.0 && blockIdx.x == 0
+    if (tau == 0.0 && frames != nullptr && bs.dt > 0.0 && vb == 0
         && (int)threadIdx.x < p.n_bodies) {
         // the midpoint frames of the following stage-2 launch, once per step
         body_frame(bodies[threadIdx.x], 0.5 * bs.dt, frames[threadIdx.x]);
@@ -187,7 +189,7 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     if (threadIdx.x == 0) s_bodies = 0u;
     __syncthreads();
     const Sizes z = load_sizes(p);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = vb * kBlock + threadIdx.x;
     const int q = t & (LANES - 1);           // lane within the marker's group
     int s;
     bool valid;
@@ -364,18 +366,33 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
         if (valid && q == 0) mforce[s - z.nF] = make_float4(f[0], f[1], f[2], __int_as_float(body));
     } else if constexpr (ACCEL == 1) {
         block_wrench_partial(p, f, arm, body, valid && q == 0 && nn > 0 && body >= 0, bs, s_bodies,
-                             red);
+                             red, vb);
     }
+}
+
+template <int ACCEL, bool FILTER, int LANES = kBceLanes>
+__global__ void __launch_bounds__(kBlock)
+k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
+      const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
+      const BodyDev *bodies, BodyFrame *frames, ListIO L, const uint32_t *__restrict__ act,
+      const int *__restrict__ n_act, double tau, int n_fluid_total, float4 *__restrict__ mforce,
+      BodyStep bs)
+{
+    if (*p.abort) return;
+    __shared__ float4 lut[64];
+    __shared__ double red[kBlock / 32][6];
+    __shared__ unsigned s_bodies;
+    bce_block<ACCEL, FILTER, LANES>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
+                                    n_fluid_total, mforce, bs, blockIdx.x, lut, red, s_bodies);
 }
 
 // The soil wrench of body b = blockIdx.x (Sec. 2.4): the sum of the wrench
 // pass's block partials in a fixed order (lane l takes blocks l, l + 32, ...,
 // then a fixed shuffle tree), then the body update -- one warp per body.
-__global__ void __launch_bounds__(32)
-k_body_reduce(DevParams p, BodyStep bs, const int *__restrict__ n_act_body)
+__device__ __forceinline__ void body_reduce_warp(const DevParams &p, const BodyStep &bs, int b,
+                                                 const int *__restrict__ n_act_body)
 {
-    if (*p.abort) return;
-    const int b = blockIdx.x, lane = threadIdx.x, nb = p.n_bodies;
+    const int lane = threadIdx.x & 31, nb = p.n_bodies;
     // the blocks of the wrench pass that held active body markers
     const int n_blocks = (int)grid_for((int64_t)__ldg(n_act_body) * kWrenchLanes);
     double v[6] = {0, 0, 0, 0, 0, 0};
@@ -387,6 +404,102 @@ k_body_reduce(DevParams p, BodyStep bs, const int *__restrict__ n_act_body)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
     if (lane == 0) body_update(p, bs, b, v);
+}
+
+__global__ void __launch_bounds__(32)
+k_body_reduce(DevParams p, BodyStep bs, const int *__restrict__ n_act_body)
+{
+    if (*p.abort) return;
+    body_reduce_warp(p, bs, blockIdx.x, n_act_body);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms (crm_batch): persistent blocks take virtual blocks off the
+// launch's work queue -- an atomic ticket, no waiting -- and run the member's
+// block exactly as its own launch would (same lanes, same arithmetic, same
+// partial slots), so a batched step equals the members' own steps bit for bit.
+__device__ __forceinline__ int batch_member(const int *__restrict__ off, int n, int it)
+{
+    int lo = 0, hi = n - 1;   // off[lo] <= it < off[lo + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void batch_done(unsigned *queue)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+        queue[0] = 0u;   // every block has stopped claiming: reset for the next launch
+        queue[1] = 0u;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kBlock)
+k_batch_bce(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
+            const int *__restrict__ off, int n, unsigned *queue)
+{
+    __shared__ float4 lut[64];
+    __shared__ double red[kBlock / 32][6];
+    __shared__ unsigned s_bodies;
+    __shared__ int s_item;
+    __shared__ MemberDev M;
+    const int total = __ldg(off + n);
+    int cur = -1;   // the member whose descriptor is loaded
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u) * kBatchChunk;
+        __syncthreads();
+        const int it0 = s_item;
+        if (it0 >= total) break;
+        const int it1 = min(it0 + kBatchChunk, total);
+        for (int it = it0; it < it1; ++it) {
+            const int k = batch_member(off, n, it);
+            if (k != cur) {   // block-uniform
+                __syncthreads();
+                load_member(mem + __ldg(mlist + k), &M);
+                cur = k;
+            }
+            if (*M.p.abort) continue;
+            const int vb = it - __ldg(off + k);
+            __syncthreads();   // the previous virtual block's readers of lut / red are done
+            if (KIND == 0) {
+                const ListIO L{M.sk_nbr, M.sk_nnb, M.nbr, M.nnb, M.err};
+                const BodyStep bs{M.partial, M.bodies, M.dt, 0, M.gate};
+                bce_block<0, true, kBceLanes>(M.p, M.S, M.S.pos, M.pid, M.mloc, M.bodies, M.frames,
+                                              L, M.act, M.n_act, 0.0, M.n_fluid_total, M.mforce, bs,
+                                              vb, lut, red, s_bodies);
+            } else if (KIND == 1) {
+                const ListIO L{M.nbr, M.nnb, nullptr, nullptr, M.err};
+                const BodyStep bs{M.partial, M.bodies, 0.0, 0, M.gate};
+                bce_block<0, false, kBceLanes>(M.p, M.MID, M.S.pos, M.pid, M.mloc, M.bodies,
+                                               M.frames, L, M.act, M.n_act, 0.5 * M.dt,
+                                               M.n_fluid_total, M.mforce, bs, vb, lut, red,
+                                               s_bodies);
+            } else {
+                const ListIO L{M.nbr, M.nnb, nullptr, nullptr, M.err};
+                const BodyStep bs{M.partial, M.bodies, M.dt, 1, M.gate};
+                bce_block<1, false, kWrenchLanes>(M.p, M.MID, M.S.pos, M.pid, M.mloc, M.bodies,
+                                                  M.frames, L, M.act_body, M.n_act + 1, 0.5 * M.dt,
+                                                  M.n_fluid_total, M.mforce, bs, vb, lut, red,
+                                                  s_bodies);
+            }
+        }
+    }
+    batch_done(queue);
+}
+
+// One warp per (member, body) pair: pairs[2 k], pairs[2 k + 1].
+__global__ void __launch_bounds__(32)
+k_batch_reduce(const MemberDev *__restrict__ mem, const int *__restrict__ pairs)
+{
+    const MemberDev &M = mem[__ldg(pairs + 2 * blockIdx.x)];
+    if (*M.p.abort) return;
+    const BodyStep bs{M.partial, M.bodies, M.dt, 1, M.gate};
+    body_reduce_warp(M.p, bs, __ldg(pairs + 2 * blockIdx.x + 1), M.n_act + 1);
 }
 
 // Markers with a non-empty list, compacted in slot order at each list rebuild
@@ -494,6 +607,32 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
         k_bce<2, false><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
                                                           act, n_act, tau, n_fluid_total, mforce, bs);
     }
+}
+
+void launch_batch_bce(int kind, const MemberDev *mem, const int *mlist, const int *off, int n,
+                      int total, unsigned *queue, cudaStream_t st)
+{
+    if (total < 1) return;
+    int dev = 0, nsm = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const void *f = kind == 0 ? (const void *)k_batch_bce<0>
+                              : kind == 1 ? (const void *)k_batch_bce<1> : (const void *)k_batch_bce<2>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kBlock, 0) != cudaSuccess
+        || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const unsigned g = (unsigned)std::min<int64_t>((int64_t)nsm * per_sm,
+                                                   (total + kBatchChunk - 1) / kBatchChunk);
+    if (kind == 0) k_batch_bce<0><<<g, kBlock, 0, st>>>(mem, mlist, off, n, queue);
+    else if (kind == 1) k_batch_bce<1><<<g, kBlock, 0, st>>>(mem, mlist, off, n, queue);
+    else k_batch_bce<2><<<g, kBlock, 0, st>>>(mem, mlist, off, n, queue);
+}
+
+void launch_batch_reduce(const MemberDev *mem, const int *pairs, int npairs, cudaStream_t st)
+{
+    if (npairs > 0) k_batch_reduce<<<(unsigned)npairs, 32, 0, st>>>(mem, pairs);
 }
 
 unsigned bce_blocks(const DevParams &p) { return grid_for((int64_t)p.capM * kBceLanes); }

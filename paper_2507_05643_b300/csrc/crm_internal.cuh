@@ -479,6 +479,59 @@ void launch_export_rates(const DevParams &p, const uint32_t *pid, RateOut r, Sta
                          const float4 *mforce, int n_fluid_total, float *drho, float *du,
                          float *ds, float *macc, float *mvel, float *msig, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Batches in one persistent launch per stage (crm_batch).  A member as the
+// batched stage kernels see it: its constants and the arrays of its step (a
+// member with a Verlet skin, without active boxes: its current buffer is fixed).
+struct MemberDev {
+    DevParams p;
+    StageArrays S, MID;                  // current stage arrays, midpoint arrays
+    const uint32_t *pid;
+    const double *mloc;
+    BodyDev *bodies;
+    BodyFrame *frames;                   // midpoint body frames
+    uint32_t *nbr, *nnb;                 // exact lists (written by stage 1)
+    const uint32_t *sk_nbr, *sk_nnb;     // skin lists
+    const uint32_t *act, *act_body;      // markers with fluid in reach, those on bodies
+    const int *n_act;                    // their counts
+    float4 *mforce;
+    double *partial;                     // wrench partials
+    const float4 *xref;                  // positions at the last search (skin)
+    int *gate, *err;
+    int n_fluid_total, n_bodym;
+    double dt;
+};
+
+// Virtual blocks claimed per ticket of a batched launch: one, so that every
+// virtual block starts after a block barrier (the lanes of a warp that share a
+// particle then always combine their sums within one virtual block).
+constexpr int kBatchChunk = 1;
+
+// Copy of a member's descriptor into the block's shared memory (every thread
+// of the block calls it; a barrier follows), so that its fields are reloaded
+// from shared memory instead of held in registers.
+__device__ __forceinline__ void load_member(const MemberDev *src, MemberDev *dst)
+{
+    static_assert(sizeof(MemberDev) % 4 == 0, "word copy");
+    const int *a = reinterpret_cast<const int *>(src);
+    int *b = reinterpret_cast<int *>(dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(MemberDev) / 4); k += blockDim.x) b[k] = __ldg(a + k);
+    __syncthreads();
+}
+
+// A batched launch's work: members mlist[k], k < n, own the virtual blocks
+// [off[k], off[k + 1]) (each virtual block = one block of that member's own
+// launch); queue = {ticket, done}, zero between launches (the last block to
+// finish resets it).  Kinds of the BCE launch: 0 stage-1 marker state with the
+// skin-list filter, 1 midpoint marker state, 2 wrench forces and partials.
+void launch_batch_bce(int kind, const MemberDev *mem, const int *mlist, const int *off, int n,
+                      int total, unsigned *queue, cudaStream_t st);
+void launch_batch_reduce(const MemberDev *mem, const int *pairs, int npairs, cudaStream_t st);
+void launch_batch_pair(int mode, int lanes, int kav, const MemberDev *mem, const int *mlist,
+                       const int *off, int n, int total, unsigned *queue, cudaStream_t st);
+int pair_kav(const DevParams &p);
+int pair_lanes_of(const DevParams &p);
+
 // Active domains (Sec. 3.2, Alg. 3), crm_active.cu.
 size_t box_frame_bytes();
 void launch_box_prep(const DevParams &p, int nbox, const int *box_body, const double *box_half,

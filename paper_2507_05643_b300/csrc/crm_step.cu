@@ -370,6 +370,63 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
                                        io, pid, dt, out, err, xref, gate);
 }
 
+// Batched form (crm_batch): persistent blocks take virtual blocks of the
+// members' own pair launches off the work queue (an atomic ticket) and run them
+// as those launches would: stage 1 filtering the skin lists with one lane per
+// particle, stage 2 on the exact lists with the member's lanes.
+template <int MODE, int LANES, int KAV>
+__global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
+k_batch_pair(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
+             const int *__restrict__ off, int n, unsigned *queue)
+{
+    __shared__ float4 lut[64];
+    __shared__ int s_item;
+    __shared__ MemberDev M;
+    const int total = __ldg(off + n);
+    int cur = -1;   // the member whose descriptor and shift table are loaded
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u) * kBatchChunk;
+        __syncthreads();
+        const int it0 = s_item;
+        if (it0 >= total) break;
+        const int it1 = min(it0 + kBatchChunk, total);
+        for (int it = it0; it < it1; ++it) {
+            int lo = 0, hi = n - 1;   // off[lo] <= it < off[lo + 1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(off + mid) <= it) lo = mid; else hi = mid - 1;
+            }
+            if (lo != cur) {   // block-uniform
+                __syncthreads();
+                load_member(mem + __ldg(mlist + lo), &M);
+                fill_shift_table(lut, M.p.cell);
+                __syncthreads();
+                cur = lo;
+            }
+            if (*M.p.abort) continue;
+            const int t = (it - __ldg(off + lo)) * kPairBlock + threadIdx.x;
+            const RateOut none{};
+            if (MODE == kStage1) {
+                const ListIO io{M.sk_nbr, M.sk_nnb, M.nbr, M.nnb, M.err};
+                pair_one<kStage1, true, 1, KAV>(M.p, t, 0, __ldg(M.p.sizes), lut, M.S, M.S, M.MID,
+                                                io, nullptr, (float)M.dt, none, M.err, nullptr,
+                                                nullptr);
+            } else {
+                const ListIO io{M.nbr, M.nnb, nullptr, nullptr, M.err};
+                pair_one<kStage2, false, LANES, KAV>(M.p, t / LANES, t % LANES, __ldg(M.p.sizes),
+                                                     lut, M.MID, M.S, M.MID, io, nullptr,
+                                                     (float)M.dt, none, M.err, M.xref, M.gate);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+        queue[0] = 0u;   // every block has stopped claiming: reset for the next launch
+        queue[1] = 0u;
+    }
+}
+
 // Sorted fluid slots -> insertion order (absolute FP64 positions).
 __global__ void k_export(DevParams p, StageArrays S, const uint32_t *__restrict__ pid,
                          double *__restrict__ xyz, float *__restrict__ vel,
@@ -490,6 +547,60 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
         CRM_KAV(0); CRM_KAV(1); CRM_KAV(2); CRM_KAV(3); CRM_KAV(4); CRM_KAV(5);
     }
 #undef CRM_KAV
+}
+
+int pair_kav(const DevParams &p)
+{
+    return 3 * (p.kernel == CRM_KERNEL_WENDLAND ? 1 : 0)
+           + (p.av_mode == CRM_AV_BILATERAL ? 1 : p.av_mode == CRM_AV_UNILATERAL ? 2 : 0);
+}
+
+int pair_lanes_of(const DevParams &p)
+{
+    return p.pair_lanes != 0 ? p.pair_lanes
+                             : ((int64_t)p.capF * 4 <= (int64_t)p.n_sm * 2048 ? 4 : kPairLanes);
+}
+
+template <int MODE, int LANES, int KAV>
+void batch_pair_go(const MemberDev *mem, const int *mlist, const int *off, int n, int total,
+                   unsigned *queue, cudaStream_t st)
+{
+    int dev = 0, nsm = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pair<MODE, LANES, KAV>,
+                                                      kPairBlock, 0) != cudaSuccess
+        || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const unsigned g = (unsigned)std::min<int64_t>((int64_t)nsm * per_sm,
+                                                   (total + kBatchChunk - 1) / kBatchChunk);
+    k_batch_pair<MODE, LANES, KAV><<<g, kPairBlock, 0, st>>>(mem, mlist, off, n, queue);
+}
+
+template <int KAV>
+void batch_pair_k(int mode, int lanes, const MemberDev *mem, const int *mlist, const int *off,
+                  int n, int total, unsigned *queue, cudaStream_t st)
+{
+    if (mode == kStage1) batch_pair_go<kStage1, 1, KAV>(mem, mlist, off, n, total, queue, st);
+    else if (lanes == 1) batch_pair_go<kStage2, 1, KAV>(mem, mlist, off, n, total, queue, st);
+    else if (lanes == 4) batch_pair_go<kStage2, 4, KAV>(mem, mlist, off, n, total, queue, st);
+    else batch_pair_go<kStage2, 2, KAV>(mem, mlist, off, n, total, queue, st);
+}
+
+void launch_batch_pair(int mode, int lanes, int kav, const MemberDev *mem, const int *mlist,
+                       const int *off, int n, int total, unsigned *queue, cudaStream_t st)
+{
+    if (total < 1) return;
+    switch (kav) {
+    case 0: batch_pair_k<0>(mode, lanes, mem, mlist, off, n, total, queue, st); break;
+    case 1: batch_pair_k<1>(mode, lanes, mem, mlist, off, n, total, queue, st); break;
+    case 2: batch_pair_k<2>(mode, lanes, mem, mlist, off, n, total, queue, st); break;
+    case 3: batch_pair_k<3>(mode, lanes, mem, mlist, off, n, total, queue, st); break;
+    case 4: batch_pair_k<4>(mode, lanes, mem, mlist, off, n, total, queue, st); break;
+    default: batch_pair_k<5>(mode, lanes, mem, mlist, off, n, total, queue, st); break;
+    }
 }
 
 void launch_export(const DevParams &p, StageArrays S, const uint32_t *pid, double *xyz, float *vel,

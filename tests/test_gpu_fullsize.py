@@ -110,9 +110,10 @@ def test_full_size_adjoint_matches_the_oracle_adjoint():
 
 def test_full_ensemble_members_match_oracle():
     """The whole 64-bin ensemble (6.7 M SPH particles) stepped as one batch after
-    its autotune, as bench.py runs it; the smallest and the largest bin against the
-    oracle stepped through the same steps: the autotune's 1 + 3 steps with each of
-    the three lane choices, then 5 batch steps."""
+    its autotune, as bench.py runs it -- the persistent form, one launch per stage
+    over all 64 bins; the smallest and the largest bin against the oracle stepped
+    through the same steps: the autotune's 1 + 3 steps with each of its six
+    choices (three lane counts x two cell tiles), then 5 batch steps."""
     import torch
     bins = scenes.ensemble_bins()
     streams = [torch.cuda.Stream() for _ in bins]
@@ -120,6 +121,7 @@ def test_full_ensemble_members_match_oracle():
     dts = [sc.dt for sc in bins]
     batch = crm.Batch(mem, stream=torch.cuda.current_stream())
     batch.autotune(dts, trial_steps=3)
+    batch.set_persistent(True)
     batch.step(dts, 5)
     torch.cuda.synchronize()
     sizes = [sc.x.shape[0] for sc in bins]
@@ -127,7 +129,7 @@ def test_full_ensemble_members_match_oracle():
     for k in (int(np.argmin(sizes)), int(np.argmax(sizes))):
         sc = bins[k]
         st = oracle.State(sc)
-        st.run(3 * (1 + 3) + 5)
+        st.run(6 * (1 + 3) + 5)
         xyz, vel, sig, rho = mem[k].particles()
         F, _ = mem[k].body_wrench(0)
         Fo = st.bodies.wrench[0, :3]

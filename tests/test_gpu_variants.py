@@ -276,16 +276,22 @@ def test_batch_steps_equal_members_stepped_alone():
     dts = [sc.dt for sc in bins]
     batch = crm.Batch(mem, stream=torch.cuda.current_stream())
     picks = batch.autotune(dts, trial_steps=2)
-    assert set(picks.tolist()) <= {1, 2, 4}
+    tiles = {(1, 1, 1), (4, 2, 2)}
+    for pk in picks.tolist():
+        assert pk & 0xF in {1, 2, 4}
+        assert ((pk >> 4) & 0xF, (pk >> 8) & 0xF, (pk >> 12) & 0xF) in tiles
     batch.step(dts, 20)
     torch.cuda.synchronize()
-    # the same bins alone, with the same lane picks and the same number of steps
+    # the same bins alone, with the same picks and the same number of steps
     for sc, pick, m in zip(bins, picks, mem):
         alone = crm.from_scene(sc, stream=torch.cuda.Stream())
-        for lanes in (1, 2, 4):    # autotune ran 3 steps with each choice
-            alone.set_pair_lanes(lanes)
-            alone.step(sc.dt, 3)
-        alone.set_pair_lanes(int(pick))
+        for tile in ((1, 1, 1), (4, 2, 2)):   # autotune ran 3 steps with each choice
+            for lanes in (1, 2, 4):
+                alone.set_pair_lanes(lanes)
+                alone.set_cell_tile(*tile)
+                alone.step(sc.dt, 3)
+        alone.set_pair_lanes(int(pick) & 0xF)
+        alone.set_cell_tile((pick >> 4) & 0xF, (pick >> 8) & 0xF, (pick >> 12) & 0xF)
         alone.step(sc.dt, 20)
         xa, va, sa, ra = alone.particles()
         xb, vb, sb, rb = m.particles()
@@ -294,6 +300,46 @@ def test_batch_steps_equal_members_stepped_alone():
         Fb, _ = m.body_wrench(0)
         assert np.array_equal(Fa, Fb)
     batch.close()
+
+
+def test_persistent_batch_equals_stream_batch():
+    """The persistent form (one graph per batch step, one launch per stage over
+    every member) gives bitwise the states and wrenches of the stream form, with
+    members of uneven size, different materials, lanes and cell tiles."""
+    import torch
+    bins = scenes.ensemble_bins(n=4)
+    for sc in bins:
+        keep = sc.x[:, 0] < 0.5
+        sc.x, sc.u, sc.sig, sc.rho = sc.x[keep], sc.u[keep], sc.sig[keep], sc.rho[keep]
+    choices = [(1, (1, 1, 1)), (2, (4, 2, 2)), (4, (1, 1, 1)), (2, (1, 1, 1))]
+    dts = [sc.dt for sc in bins]
+    sets = []
+    for persistent in (False, True):
+        mem = [crm.from_scene(sc, stream=torch.cuda.Stream()) for sc in bins]
+        for m, (lanes, tile) in zip(mem, choices):
+            m.set_pair_lanes(lanes)
+            m.set_cell_tile(*tile)
+        batch = crm.Batch(mem, stream=torch.cuda.current_stream())
+        batch.set_persistent(persistent)
+        batch.step(dts, 25)
+        torch.cuda.synchronize()
+        for m in mem:
+            m.sync()
+        sets.append((batch, mem))
+    (_, a), (_, b) = sets
+    for ma, mb in zip(a, b):
+        xa, va, sa, ra = ma.particles()
+        xb, vb, sb, rb = mb.particles()
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+        assert np.array_equal(sa, sb) and np.array_equal(ra, rb)
+        Fa, Ta = ma.body_wrench(0)
+        Fb, Tb = mb.body_wrench(0)
+        assert np.array_equal(Fa, Fb) and np.array_equal(Ta, Tb)
+        pa, _ = ma.body_state(0)
+        pb, _ = mb.body_state(0)
+        assert np.array_equal(pa, pb)
+    for batch, _ in sets:
+        batch.close()
 
 
 # --------------------------------------------------------------------------
