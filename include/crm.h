@@ -374,6 +374,15 @@ int crm_set_pair_lanes(crm_terrain *t, int32_t lanes);
  * unchanged, only the slot order and the order of the pair sums. */
 int crm_set_cell_tile(crm_terrain *t, int32_t nx, int32_t ny, int32_t nz);
 
+/* Comparison layout for the precision pattern (a test hook): on = 1 stores
+ * every position as an absolute FP32 coordinate would be stored -- the inputs
+ * and, after every stage, each SPH particle's and BCE marker's position are
+ * rounded to the nearest FP32 value of the absolute coordinate -- so that a run
+ * shows what the cell-relative FP32 layout (the default) avoids: the spacing
+ * of FP32 values grows with the distance from the origin (4.9e-4 m at 5 km).
+ * Before the first step only (CRM_ESTATE after); CRM_EINVAL for other values. */
+int crm_debug_absolute_fp32(crm_terrain *t, int32_t on);
+
 /* Test hook of the failure detection for device-side waits (CRM_ETIMEOUT), on
  * the current device: on = 1 makes every look-back scan (the cell sort of a
  * terrain, its active-set compaction, the stateless binning) started from now

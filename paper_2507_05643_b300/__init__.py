@@ -91,6 +91,7 @@ _sig("crm_set_body_inertia", C.c_int, [_T, _i32, _vp])
 _sig("crm_set_pair_lanes", C.c_int, [_T, _i32])
 _sig("crm_set_cell_tile", C.c_int, [_T, _i32, _i32, _i32])
 _sig("crm_debug_wait_fault", C.c_int, [_i32])
+_sig("crm_debug_absolute_fp32", C.c_int, [_T, _i32])
 _B = C.c_void_p
 _sig("crm_batch_create", C.c_int, [_i32, C.POINTER(_T), _vp, C.POINTER(_B)])
 _sig("crm_batch_step", C.c_int, [_B, _vp, _i32])
@@ -137,7 +138,7 @@ EXPORTS = ("crm_version", "crm_status_string", "crm_default_params", "crm_create
            "crm_last_error", "crm_add_sph", "crm_add_fixed_bce", "crm_add_rigid_body",
            "crm_set_body_motion", "crm_get_body_state", "crm_set_body_inertia",
            "crm_set_body_load", "crm_add_active_box", "crm_step", "crm_set_pair_lanes", "crm_set_cell_tile",
-           "crm_debug_wait_fault",
+           "crm_debug_wait_fault", "crm_debug_absolute_fp32",
            "crm_batch_create", "crm_batch_step", "crm_batch_autotune", "crm_batch_destroy",
            "crm_batch_set_persistent",
            "crm_sync", "crm_get_particles", "crm_get_body_wrench", "crm_get_diagnostics", "crm_get_counts",
@@ -273,6 +274,11 @@ class Terrain:
 
     def set_pair_lanes(self, lanes: int):
         self._check(_lib.crm_set_pair_lanes(self._h, int(lanes)))
+
+    def debug_absolute_fp32(self, on: bool = True):
+        """Store positions as absolute FP32 coordinates would be (the comparison
+        layout of the precision tests); before the first step."""
+        self._check(_lib.crm_debug_absolute_fp32(self._h, int(bool(on))))
 
     def set_cell_tile(self, nx: int, ny: int, nz: int):
         self._check(_lib.crm_set_cell_tile(self._h, int(nx), int(ny), int(nz)))

@@ -91,6 +91,7 @@ struct crm_terrain {
     // Verlet skin (non-active runs with skin > 0)
     bool skin_on = false;
     int tile_log2[3] = {0, 0, 0};   // cell tiles of the sort order (crm_set_cell_tile)
+    int abs32 = 0;                  // test-only absolute FP32 positions (crm_debug_absolute_fp32)
     uint32_t *sk_nbr = nullptr, *sk_nnb = nullptr;
     float4 *xref = nullptr;
     int *gate = nullptr;
@@ -304,6 +305,7 @@ int make_devparams(crm_terrain *t)
         }
         d.n_sm = nsm;
     }
+    d.abs32 = t->abs32;
     d.tbx = t->tile_log2[0];
     d.tby = t->tile_log2[1];
     d.tbz = t->tile_log2[2];
@@ -605,6 +607,13 @@ int commit(crm_terrain *t)
         if (rc) return rc;
     }
 
+    // test-only absolute FP32 layout: the inputs as FP32 coordinates
+    if (t->abs32) {
+        for (double &v : t->hx) v = (double)(float)v;
+        for (int64_t a = 0; a < nM; ++a)
+            if (t->hmbody[a] < 0)
+                for (int k = 0; k < 3; ++k) t->hmloc[3 * a + k] = (double)(float)t->hmloc[3 * a + k];
+    }
     // initial state, converted to cell-relative form on the host
     std::vector<float4> pos(nF), vel(nF), sA(nF);
     std::vector<float2> sB(nF);
@@ -1783,6 +1792,14 @@ static int force_search(crm_terrain *t)
     CRM_CUDA(t, cudaMemcpyAsync(t->gate + GATE_FORCE, &one, sizeof(int), cudaMemcpyHostToDevice,
                                 t->st));
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
+    return CRM_OK;
+}
+
+int crm_debug_absolute_fp32(crm_terrain *t, int32_t on)
+{
+    if (!t || (on != 0 && on != 1)) return CRM_EINVAL;
+    if (t->committed) return t->fail(CRM_ESTATE, "crm_debug_absolute_fp32: before the first step");
+    t->abs32 = on;
     return CRM_OK;
 }
 

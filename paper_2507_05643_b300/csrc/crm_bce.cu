@@ -304,7 +304,8 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
             for (int k = 0; k < 6; ++k) sa[k] = 0.f;
         }
         if (work && q == 0) {
-            S.pos[s] = make_float4(o[0], o[1], o[2], home.w);
+            const float4 mp = make_float4(o[0], o[1], o[2], home.w);
+            S.pos[s] = p.abs32 ? round_absolute(p, mp) : mp;
             S.vel[s] = make_float4(ua[0], ua[1], ua[2], p.rho0);
             S.sA[s] = make_float4(sa[0], sa[1], sa[2], sa[3]);
             S.sB[s] = make_float2(sa[4], sa[5]);

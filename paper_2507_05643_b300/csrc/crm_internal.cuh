@@ -59,6 +59,8 @@ struct DevParams {
     int n_bodies;
     uint32_t body_lo[kMaxBodies], body_hi[kMaxBodies];   // particle-id range of each body's markers
     int n_sm;                             // multiprocessors of the device (launch shapes)
+    int abs32;                            // test-only: every stored position rounded to an
+                                          // absolute FP32 coordinate (crm_debug_absolute_fp32)
     int tbx, tby, tbz;                    // cell tiles of the sort order: log2 of their
                                           // size in cells along x, y, z (see cell_key)
     int pair_lanes;                       // lanes per fluid particle in the exact-list pair
@@ -351,6 +353,21 @@ __device__ __forceinline__ uint32_t ld_list(const uint32_t *p)
     uint32_t v;
     asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
+}
+
+// A cell-relative position rounded as an absolute FP32 coordinate would be
+// (the test-only comparison layout of crm_debug_absolute_fp32): the offset
+// becomes fp32(corner + offset) - corner.
+__device__ __forceinline__ float4 round_absolute(const DevParams &p, float4 ps)
+{
+    int ix, iy, iz;
+    decode_cell(__float_as_uint(ps.w), p, ix, iy, iz);
+    const double cx = p.dmin_x + ix * p.cell_d, cy = p.dmin_y + iy * p.cell_d,
+                 cz = p.dmin_z + iz * p.cell_d;
+    ps.x = (float)((double)(float)(cx + (double)ps.x) - cx);
+    ps.y = (float)((double)(float)(cy + (double)ps.y) - cy);
+    ps.z = (float)((double)(float)(cz + (double)ps.z) - cz);
+    return ps;
 }
 
 // Cell offsets of the neighbour codes (dx, dy, dz in {-1, 0, 1}) times the cell

@@ -187,7 +187,9 @@ __device__ __forceinline__ void stage_epilogue(const DevParams &p, int i, const 
         out.dsB[i] = make_float2(ds[4], ds[5]);
     } else if (MODE == kStage1) {
         const float h = 0.5f * dt;
-        MID.pos[i] = make_float4(fmaf(h, vi.x, pi.x), fmaf(h, vi.y, pi.y), fmaf(h, vi.z, pi.z), pi.w);
+        const float4 mp = make_float4(fmaf(h, vi.x, pi.x), fmaf(h, vi.y, pi.y), fmaf(h, vi.z, pi.z),
+                                      pi.w);
+        MID.pos[i] = p.abs32 ? round_absolute(p, mp) : mp;
         MID.vel[i] = make_float4(fmaf(h, dux, vi.x), fmaf(h, duy, vi.y), fmaf(h, duz, vi.z),
                                  fmaf(h, drho, vi.w));
         MID.sA[i] = make_float4(fmaf(h, ds[0], si[0]), fmaf(h, ds[1], si[1]), fmaf(h, ds[2], si[2]),
@@ -221,7 +223,7 @@ __device__ __forceinline__ void stage_epilogue(const DevParams &p, int i, const 
             const int mx = __reduce_max_sync(am, d2);
             if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMax(gate + GATE_DISP, mx);
         }
-        Y.pos[i] = np;
+        Y.pos[i] = p.abs32 ? round_absolute(p, np) : np;
         Y.vel[i] = nv;
         Y.sA[i] = make_float4(s1[0], s1[1], s1[2], s1[3]);
         Y.sB[i] = make_float2(s1[4], s1[5]);

@@ -299,6 +299,43 @@ def sphere_drop(seed: int = 6, nx: int = 30, ny: int = 30, nz: int = 12, d0: flo
                  [body], [], 0.0, dt, n_steps, lo, hi)
 
 
+def sphere_crater(rho_sphere: float, H: float, seed: int = 8, bed=(0.14, 0.1, 0.1),
+                  d0: float = 0.0025, radius: float = 0.0125, dt: float = 5e-5,
+                  n_steps: int = 3000, jitter: float = 1e-5) -> Scene:
+    """The paper's sphere cratering test (Sec. 4, Sphere Cratering): a sphere of
+    radius 0.0125 m and density rho_sphere dropped from height H onto a granular
+    bed of density 1510 kg/m^3 and friction mu_s = 0.3 in a 0.14 x 0.1 m
+    container, SPH parameters of its table (d0 = 2.5 mm, h = 3.25 mm, bilateral
+    artificial viscosity 0.01, cubic spline, dt = 5e-5 s).  Readings where the
+    paper is silent: a bed 0.1 m deep at rest under geostatic stress; E = 1e6 Pa,
+    nu = 0.3 (the workloads' defaults); mu_2 = mu_s (the rate term needs mu_2,
+    which is not given); no cohesion.  The fall itself is not simulated: the
+    sphere starts with its lowest point at the surface and the speed sqrt(2 g H)
+    it reaches by falling H, its centre free to move vertically only."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = default_params(d0, rho0=1510.0, mu_s=0.3, mu_2=0.3, grain_d=0.001, cohesion=0.0,
+                       av_mode=1, av_gamma=0.01)
+    p["h"] = 0.00325
+    nx, ny, nz = (int(round(b / d0)) for b in bed)
+    Hb = nz * d0
+    x = _jitter(rng, lattice(nx, ny, nz, d0), jitter)
+    layers = n_layers(p["h"], d0)
+    nz_wall = nz + 4
+    fixed = box_walls(nx, ny, nz_wall, layers, d0)
+    sig = geostatic_stress(x[:, 2], Hb, p["rho0"], p["nu"])
+    mass = rho_sphere * 4.0 / 3.0 * math.pi * radius ** 3
+    pose = np.array([nx * d0 / 2, ny * d0 / 2, Hb + radius + 0.5 * d0, 1.0, 0.0, 0.0, 0.0])
+    twist = np.array([0.0, 0.0, -math.sqrt(2.0 * G_EARTH * H), 0.0, 0.0, 0.0])
+    body = Body(sphere_markers(radius, d0, layers), pose, twist, mass, DOF_Z)
+    margin = layers * d0 + 2 * p["h"]
+    lo = np.array([-margin, -margin, -margin])
+    hi = np.array([nx * d0 + margin, ny * d0 + margin, Hb + 4 * radius + margin])
+    m = x.shape[0]
+    sc = Scene("sphere_crater", p, x, np.zeros((m, 3)), sig, np.full(m, p["rho0"]), fixed,
+               [body], [], 0.0, dt, n_steps, lo, hi)
+    return sc
+
+
 def lattice_only(seed: int, n: int = 12, d0: float = 0.01, jitter: float = 1e-4,
                  random_state: bool = True, **over) -> Scene:
     """An n^3 jittered lattice with random velocities and stresses and no walls

@@ -120,6 +120,47 @@ def test_far_from_origin_keeps_precision():
     assert np.linalg.norm(Fb - Fa) <= 1e-3 * np.linalg.norm(Fa)
 
 
+def test_precision_pattern_against_absolute_fp32():
+    """The precision pattern, quantified (the wheel-bin comparison of plain
+    against cell-relative FP32): the reduced wheel bin at x = 0 and moved to
+    x = 5000 m, 20 steps, each run against the FP64 oracle at the same place,
+    with positions stored cell-relative (the library's layout) and as absolute
+    FP32 coordinates (crm_debug_absolute_fp32, the comparison layout).  Per
+    quantity: max |dx| / d0, RMS dsigma / (rho0 g H), max |drho| / rho0 and the
+    wheel force |dF| / |F|.  Cell-relative stays at FP32 rounding at both places;
+    the absolute layout loses three orders of magnitude at 5 km (its FP32
+    spacing there is 4.9e-4 m = 0.05 d0)."""
+    base = scenes.wheel_bin(seed=73, nx=40, ny=24, nz=10, wheel_radius=0.08, wheel_width=0.08,
+                            n_grousers=8, wheel_x=0.2)
+    base.bodies[0].pose[2] -= 0.004
+    d0, n = base.params["d0"], 20
+    sig_scale = base.params["rho0"] * 9.81 * 0.1
+    report = {}
+    for where, shift in (("x=0", 0.0), ("x=5000m", 5000.0)):
+        sc = _shift(base, shift)
+        st = oracle.State(sc)
+        st.run(n)
+        Fo = st.bodies.wrench[0, :3]
+        for layout in ("cell-relative", "absolute"):
+            t = crm.from_scene(sc)
+            if layout == "absolute":
+                t.debug_absolute_fp32(True)
+            t.step(sc.dt, n)
+            x, u, sig, rho = t.particles()
+            F, _ = t.body_wrench(0)
+            report[(where, layout)] = (float(np.max(np.abs(x - st.x)) / d0),
+                                       float(np.sqrt(np.mean((sig - st.sig) ** 2)) / sig_scale),
+                                       float(np.max(np.abs(rho - st.rho)) / base.params["rho0"]),
+                                       float(np.linalg.norm(F - Fo) / np.linalg.norm(Fo)))
+            t.close()
+    print("precision (max|dx|/d0, rms dsig/(rho0 g H), max|drho|/rho0, |dF|/|F|):", report)
+    for where in ("x=0", "x=5000m"):
+        dx, ds, dr, dF = report[(where, "cell-relative")]
+        assert dx < 1e-5 and ds < 1e-5 and dr < 1e-5 and dF < 1e-4, report
+    near, far = report[("x=0", "cell-relative")], report[("x=5000m", "absolute")]
+    assert far[0] > 100 * near[0] and far[3] > 100 * near[3], report
+
+
 @pytest.mark.parametrize("scene", ["lattice", "wheel"])
 def test_wendland_rates_match_oracle(scene):
     """Quintic Wendland kernel (Sec. 3.1): single-step rates of the fluid and the
