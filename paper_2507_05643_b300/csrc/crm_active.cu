@@ -26,8 +26,31 @@ struct BoxFrame {
     double c[3];
     double R[9];
     double e[3];
-    double eg[3];
+    double eg[3];   // grown by 2h
+    double em[3];   // grown by 2h and the working-set margin (act_margin)
 };
+
+// Frame of box b at the bodies' current poses (FP64).
+__device__ __forceinline__ void box_frame(const DevParams &p, int b, const int *box_body,
+                                          const double *box_half, const double *box_off,
+                                          const BodyDev *bodies, BoxFrame &F)
+{
+    const double grow = 2.0 * (double)p.h;
+    const BodyDev &B = bodies[box_body[b]];
+    const double *q = B.pose + 3;
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                         2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                         2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    for (int k = 0; k < 9; ++k) F.R[k] = R[k];
+    for (int k = 0; k < 3; ++k) {
+        F.c[k] = B.pose[k] + R[3 * k] * box_off[3 * b] + R[3 * k + 1] * box_off[3 * b + 1]
+                 + R[3 * k + 2] * box_off[3 * b + 2];
+        F.e[k] = box_half[3 * b + k];
+        F.eg[k] = box_half[3 * b + k] + grow;
+        F.em[k] = F.eg[k] + p.act_margin;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // k_box_prep: one block.  Box frames at the start of the step, the working
@@ -49,7 +72,7 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
                            int *__restrict__ counts, int *__restrict__ abort_flag,
                            int64_t step_tag)
 {
-    if (*abort_flag) return;
+    if (*abort_flag || gated_off(p)) return;
     const int G[3] = {p.GX, p.GY, p.GZ};
     const double dmin[3] = {p.dmin_x, p.dmin_y, p.dmin_z};
     const double inv_cell = 1.0 / p.cell_d;
@@ -58,24 +81,12 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
     __shared__ int s_lo[kMaxBodies][3], s_hi[kMaxBodies][3];
     if ((int)threadIdx.x < nbox) {
         const int b = threadIdx.x;
-        const double grow = 2.0 * (double)p.h;
-        const BodyDev &B = bodies[box_body[b]];
         BoxFrame &F = frames[b];
-        const double *q = B.pose + 3;
-        const double w = q[0], x = q[1], y = q[2], z = q[3];
-        const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
-                             2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
-                             2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
-        for (int k = 0; k < 9; ++k) F.R[k] = R[k];
+        box_frame(p, b, box_body, box_half, box_off, bodies, F);
+        const double *R = F.R;
         for (int k = 0; k < 3; ++k) {
-            F.c[k] = B.pose[k] + R[3 * k] * box_off[3 * b] + R[3 * k + 1] * box_off[3 * b + 1]
-                     + R[3 * k + 2] * box_off[3 * b + 2];
-            F.e[k] = box_half[3 * b + k];
-            F.eg[k] = box_half[3 * b + k] + grow;
-        }
-        for (int k = 0; k < 3; ++k) {
-            const double ext = fabs(R[3 * k]) * F.eg[0] + fabs(R[3 * k + 1]) * F.eg[1]
-                               + fabs(R[3 * k + 2]) * F.eg[2];
+            const double ext = fabs(R[3 * k]) * F.em[0] + fabs(R[3 * k + 1]) * F.em[1]
+                               + fabs(R[3 * k + 2]) * F.em[2];
             s_lo[b][k] = max((int)floor((F.c[k] - ext - dmin[k]) * inv_cell) - 1, 0);
             s_hi[b][k] = min((int)floor((F.c[k] + ext - dmin[k]) * inv_cell) + 1, G[k] - 1);
         }
@@ -83,8 +94,10 @@ __global__ void k_box_prep(DevParams p, int nbox, const int *__restrict__ box_bo
     __syncthreads();
     if (threadIdx.x != 0) return;
     if (p.step_ctr != nullptr) step_tag = (int64_t)*p.step_ctr;
-    counts[3] = 0;
-    counts[4] = 0;
+    if (!p.act_skin) {   // (with the skin the step's flag pass counts, after k_decide's reset)
+        counts[3] = 0;
+        counts[4] = 0;
+    }
     int lo[3] = {G[0], G[1], G[2]}, hi[3] = {-1, -1, -1};
     int xa[kMaxBodies], xb[kMaxBodies];
     for (int b = 0; b < nbox; ++b) {
@@ -181,19 +194,22 @@ __device__ __forceinline__ void abs_pos(const DevParams &p, float4 ps, double x[
 // Activity of a point against the step's boxes: 2 inside a box (Active), 1
 // inside a box grown by 2h (Extended-Active), else 0 -- the box-frame test of
 // UpdateActivity, in FP64.
+// With a working-set margin, 3: inside a box grown by 2h and the margin only.
 __device__ __forceinline__ int activity(const double x[3], int nbox, const BoxFrame *F)
 {
     int best = 0;
     for (int b = 0; b < nbox; ++b) {
         const double d[3] = {x[0] - F[b].c[0], x[1] - F[b].c[1], x[2] - F[b].c[2]};
-        int in = 1, ext = 1;
+        int in = 1, ext = 1, mar = 1;
         for (int k = 0; k < 3; ++k) {
             const double l = F[b].R[k] * d[0] + F[b].R[3 + k] * d[1] + F[b].R[6 + k] * d[2];
             if (fabs(l) > F[b].e[k]) in = 0;
             if (fabs(l) > F[b].eg[k]) ext = 0;
+            if (fabs(l) > F[b].em[k]) mar = 0;
         }
         if (in) return 2;
         if (ext) best = 1;
+        else if (mar && best == 0) best = 3;
     }
     return best;
 }
@@ -218,7 +234,7 @@ __global__ void k_activity(DevParams p, int nbox, const BoxFrame *__restrict__ f
                            uint32_t *__restrict__ include, uint8_t *__restrict__ kind,
                            int *__restrict__ counts, const int *__restrict__ abort_flag)
 {
-    if (*abort_flag) return;
+    if (*abort_flag || gated_off(p)) return;
     __shared__ BoxFrame F[kMaxBodies];
     for (int b = threadIdx.x; b < nbox; b += blockDim.x) F[b] = frames[b];
     __syncthreads();
@@ -242,7 +258,7 @@ __global__ void k_activity(DevParams p, int nbox, const BoxFrame *__restrict__ f
             const int f = all_active ? 2 : activity(x, nbox, F);
             inc = f > 0 ? 1u : 0u;
             k = (uint8_t)f;
-            if (c < nfc) {
+            if (c < nfc && !p.act_skin) {
                 na += f == 2;
                 ne += f == 1;
             }
@@ -268,7 +284,7 @@ __global__ void k_active_sizes(DevParams p, const int *__restrict__ rinfo,
                                int *__restrict__ counts, int *__restrict__ abort_flag,
                                int64_t step_tag)
 {
-    if (threadIdx.x != 0 || *abort_flag) return;
+    if (threadIdx.x != 0 || *abort_flag || gated_off(p)) return;
     if (p.step_ctr != nullptr) step_tag = (int64_t)*p.step_ctr;
     const int nfc = rinfo[2], total = rinfo[3];
     const int nF = (int)slot[nfc];
@@ -296,7 +312,7 @@ __global__ void k_gather(DevParams p, const int *__restrict__ ranges, const int 
                          uint32_t *__restrict__ wpid, const int *__restrict__ counts,
                          const int *__restrict__ abort_flag)
 {
-    if (*abort_flag) return;
+    if (*abort_flag || gated_off(p)) return;
     const int nr = rinfo[0] + rinfo[1];
     const int nfc = rinfo[2], total = rinfo[3];
     const int nF = counts[0];
@@ -313,7 +329,9 @@ __global__ void k_gather(DevParams p, const int *__restrict__ ranges, const int 
                 W.vel[w] = M.vel[m];
                 W.sA[w] = M.sA[m];
                 W.sB[w] = M.sB[m];
-                wpid[w] = mpid[m] | (kind[c] == 1 ? kExtendedBit : 0u);
+                const uint8_t kd = kind[c];
+                wpid[w] = mpid[m] | (kd == 2 ? 0u
+                                             : kd == 1 ? kExtendedBit : kExtendedBit | kOutsideBit);
             } else {
                 W.pos[w] = make_float4(0.f, 0.f, 0.f, 0.f);
                 W.vel[w] = make_float4(0.f, 0.f, 0.f, p.rho0);
@@ -338,17 +356,21 @@ __global__ void k_gather(DevParams p, const int *__restrict__ ranges, const int 
 // Write the Active particles of the (sorted) working set back to their master
 // slots and track how far, in x-columns, any of them has drifted from the
 // column its master slot is filed under.
+// (With the skin the working set persists across steps: the particles written
+// back are those integrated at some step since it was gathered.)  gated: part
+// of a step's gated rebuild (skipped unless the cell search is due).
 __global__ void k_scatter_back(DevParams p, StageArrays W, const uint32_t *__restrict__ wpid,
                                const uint32_t *__restrict__ mslot_of_pid,
-                               const int *__restrict__ mcol, StageArrays M, int *__restrict__ drift)
+                               const int *__restrict__ mcol, StageArrays M, int *__restrict__ drift,
+                               int gated)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     int dmax = 0;
-    if (*p.abort) return;
+    if (*p.abort || (gated && gated_off(p))) return;
     if (s < __ldg(p.sizes)) {
         const uint32_t id = wpid[s];
-        if (!(id & kExtendedBit)) {
-            const uint32_t m = mslot_of_pid[id];
+        if (p.act_skin ? (id & kTouchedBit) != 0u : !(id & kExtendedBit)) {
+            const uint32_t m = mslot_of_pid[pid_index(id)];
             const float4 ps = W.pos[s];
             M.pos[m] = ps;
             M.vel[m] = W.vel[s];
@@ -431,9 +453,58 @@ void launch_gather(const DevParams &p, const int *ranges, const int *rinfo,
 
 void launch_scatter_back(const DevParams &p, StageArrays W, const uint32_t *wpid,
                          const uint32_t *mslot_of_pid, const int *mcol, StageArrays M, int *drift,
-                         cudaStream_t st)
+                         int gated, cudaStream_t st)
 {
-    k_scatter_back<<<grid_for(p.capF), kBlock, 0, st>>>(p, W, wpid, mslot_of_pid, mcol, M, drift);
+    k_scatter_back<<<grid_for(p.capF), kBlock, 0, st>>>(p, W, wpid, mslot_of_pid, mcol, M, drift,
+                                                        gated);
+}
+
+// The activity of every working-set fluid particle against this step's boxes
+// (Alg. 3 UpdateActivity at every step, on the persisting working set): the
+// pid bits and the Active / Extended counts.  Each block computes the frames
+// of the step's boxes (FP64) for itself.
+__global__ void __launch_bounds__(kBlock)
+k_flags(DevParams p, int nbox, const int *__restrict__ box_body,
+        const double *__restrict__ box_half, const double *__restrict__ box_off,
+        const BodyDev *__restrict__ bodies, int all_active, uint32_t *__restrict__ pid,
+        const float4 *__restrict__ pos, int *__restrict__ counts)
+{
+    __shared__ BoxFrame F[kMaxBodies];
+    if (*p.abort) return;
+    if ((int)threadIdx.x < nbox) box_frame(p, threadIdx.x, box_body, box_half, box_off, bodies,
+                                           F[threadIdx.x]);
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int na = 0, ne = 0;
+    if (s < __ldg(p.sizes)) {
+        double x[3];
+        abs_pos(p, pos[s], x);
+        const int f = all_active ? 2 : activity(x, nbox, F);
+        const uint32_t id = pid[s];
+        uint32_t out = id & (kPidIndexMask | kTouchedBit);
+        if (f == 2) out |= kTouchedBit;
+        else if (f == 1) out |= kExtendedBit;
+        else out |= kExtendedBit | kOutsideBit;
+        if (out != id) pid[s] = out;
+        na = f == 2;
+        ne = f == 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        na += __shfl_down_sync(0xffffffffu, na, o);
+        ne += __shfl_down_sync(0xffffffffu, ne, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (na | ne)) {
+        atomicAdd(&counts[3], na);
+        atomicAdd(&counts[4], ne);
+    }
+}
+
+void launch_flags(const DevParams &p, int nbox, const int *box_body, const double *box_half,
+                  const double *box_off, const BodyDev *bodies, int all_active, uint32_t *pid,
+                  const float4 *pos, int *counts, cudaStream_t st)
+{
+    k_flags<<<grid_for(p.capF), kBlock, 0, st>>>(p, nbox, box_body, box_half, box_off, bodies,
+                                                 all_active, pid, pos, counts);
 }
 
 void launch_export_master(const DevParams &p, StageArrays M, const uint32_t *mpid, int n,

@@ -53,6 +53,7 @@ struct crm_terrain {
     bool frozen = false;          // a device wait gave up: no stepping until crm_load_state
     bool active = false;          // any active box
     bool have_working = false;    // working set holds state not yet written back
+    bool boxes_in_force = false;  // the last active step was after t_delay
     int64_t step_index = 0;
     double time = 0.0;
     int64_t nFtot = 0, nMtot = 0;
@@ -306,6 +307,13 @@ int make_devparams(crm_terrain *t)
         d.n_sm = nsm;
     }
     d.abs32 = t->abs32;
+    d.act_skin = t->active && t->skin_on ? 1 : 0;
+    // the gathered working set reaches a margin beyond the grown boxes; the skin
+    // test also calls for a new gather once a point of a grown box may have moved
+    // 0.95 of it (a margin of four times the particles' displacement bound: the
+    // boxes of turning wheels reach far from their centres)
+    d.act_margin = d.act_skin ? 4.0 * P.h * skin : 0.0;
+    d.box_thr2 = (float)(0.95 * d.act_margin * 0.95 * d.act_margin);
     d.tbx = t->tile_log2[0];
     d.tby = t->tile_log2[1];
     d.tbz = t->tile_log2[2];
@@ -418,7 +426,9 @@ int alloc_working(crm_terrain *t)
     if (t->oom) return t->fail(CRM_ENOMEM, "device allocation of the working set failed");
     if (t->skin_on) {
         CRM_CUDA(t, cudaMemsetAsync(t->sk_nnb, 0, N * sizeof(uint32_t), t->st));
-        const int g0[GATE_WORDS] = {1, 0, 1, 0};   // the first rebuild searches
+        // the first rebuild searches (the count of searches runs on: the launch
+        // counters read differences of it)
+        const int g0[GATE_SEARCHES] = {1, 0, 1, 0};
         CRM_CUDA(t, cudaMemcpyAsync(t->gate, g0, sizeof(g0), cudaMemcpyHostToDevice, t->st));
         CRM_CUDA(t, cudaStreamSynchronize(t->st));
     }
@@ -495,7 +505,7 @@ void estimate_active(crm_terrain *t, const std::vector<int> &colF_h, const std::
                              2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
         double eg[3], c[3], vol = 1.0;
         for (int k = 0; k < 3; ++k) {
-            eg[k] = t->box_half_h[3 * b + k] + 2.0 * t->P.h;
+            eg[k] = t->box_half_h[3 * b + k] + 2.0 * t->P.h + d.act_margin;
             vol *= 2.0 * eg[k];
         }
         for (int k = 0; k < 3; ++k)
@@ -528,7 +538,7 @@ int commit(crm_terrain *t)
         if ((b.dof & (7 << 3)) && !(b.inertia[0] > 0 && b.inertia[1] > 0 && b.inertia[2] > 0))
             return t->fail(CRM_EINVAL, "a body with free angular DOFs needs crm_set_body_inertia");
     t->active = !t->box_body_h.empty();
-    t->skin_on = !t->active && t->P.skin > 0.0;
+    t->skin_on = t->P.skin > 0.0;
     int rc = make_devparams(t);
     if (rc) return rc;
     DevParams &d = t->dp;
@@ -560,6 +570,18 @@ int commit(crm_terrain *t)
         const double *x = &t->hmloc[3 * a];
         t->hbodies[b].rmax = std::max(t->hbodies[b].rmax, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
     }
+    for (BodyDev &B : t->hbodies) B.box_reach = 0.0;
+    if (d.act_skin) {
+        // bound on the distance of a grown box's points from the body's centre
+        for (size_t k = 0; k < t->box_body_h.size(); ++k) {
+            const double *o = &t->box_off_h[3 * k], *e = &t->box_half_h[3 * k];
+            double e2 = 0.0;
+            for (int a = 0; a < 3; ++a) e2 += (e[a] + 2.0 * t->P.h) * (e[a] + 2.0 * t->P.h);
+            const double reach = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) + std::sqrt(e2);
+            BodyDev &B = t->hbodies[t->box_body_h[k]];
+            B.box_reach = std::max(B.box_reach, reach);
+        }
+    }
     const int64_t full_cells = key_cells(d.GX, d.GY, d.GZ);
     cudaStream_t st = t->st;
     t->n_bodym = (int)std::count_if(t->hmbody.begin(), t->hmbody.end(), [](int b) { return b >= 0; });
@@ -574,6 +596,7 @@ int commit(crm_terrain *t)
     t->abort_flag = t->dalloc<int>(G_STATIC, 1);
     t->gate = t->dalloc<int>(G_STATIC, GATE_WORDS);
     if (t->oom) return t->fail(CRM_ENOMEM, "device allocation failed");
+    CRM_CUDA(t, cudaMemsetAsync(t->gate, 0, GATE_WORDS * sizeof(int), t->st));
     if (t->skin_on) d.gate = t->gate;
     if (!t->h_counts && cudaMallocHost(&t->h_counts, (C_WORDS + 2) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -830,13 +853,30 @@ template <class F> void launch(crm_terrain *t, int k, F &&f, int kernels = 1)
     }
 }
 
+// The next rebuild gathers and searches (with the skin, whatever the
+// displacement test says): the working set or the lists are gone.
+int invalidate_lists(crm_terrain *t)
+{
+    t->lists_valid = false;
+    if (t->committed && t->skin_on)
+        CRM_CUDA(t, cudaMemsetAsync(t->gate + GATE_FORCE, 1, sizeof(int), t->st));   // nonzero
+    return CRM_OK;
+}
+
+// Launch count of a kernel of the gated rebuild: with the skin (and no event
+// timing) the searches the decision actually ran are counted at profile_read.
+int gated_count(const crm_terrain *t, int gated) { return gated && t->skin_on && !t->timing ? 0 : 1; }
+
 // Write the Active particles of the working set back to the master store.
-void scatter_back(crm_terrain *t)
+// gated: as part of a step's rebuild (with the skin, run only when the search
+// is due); else unconditionally (before reading the master store).
+void scatter_back(crm_terrain *t, int gated = 0)
 {
     if (!t->active || !t->have_working) return;
     const int c = t->cur;
     launch(t, K_EXPORT, [&] { launch_scatter_back(t->dp, t->A[c], t->pid[c], t->mslot_of_pid,
-                                                  t->mcol, t->Mst, t->drift, t->st); });
+                                                  t->mcol, t->Mst, t->drift, gated, t->st); },
+           gated_count(t, gated));
 }
 
 // Activity flags, counts and the gather of the working set (Alg. 3 items 1-3).
@@ -845,24 +885,26 @@ void activity_pass(crm_terrain *t)
     const DevParams &d = t->dp;
     const int all = !(t->time > t->t_delay);
     const int c = t->cur;
-    scatter_back(t);
+    scatter_back(t, t->skin_on ? 1 : 0);
     const int nbox = (int)t->box_body_h.size();
+    const int n1 = gated_count(t, 1);
     launch(t, K_KEYS, [&] { launch_box_prep(d, nbox, t->box_body, t->box_half, t->box_off,
                                             t->bodies, t->colF, t->colM, t->drift, all,
                                             (int)t->nFtot, t->n_fixed, t->cand_cap, t->frames,
                                             t->win, t->ranges, t->rinfo, t->counts, t->abort_flag,
-                                            t->step_index, t->st); });
+                                            t->step_index, t->st); }, n1);
     launch(t, K_KEYS, [&] { launch_activity(d, nbox, t->frames, t->ranges, t->rinfo, t->Mst.pos,
                                             t->mloc, t->fixed_order, all, t->cand_cap, t->cinc,
-                                            t->ckind, t->counts, t->abort_flag, t->st); });
+                                            t->ckind, t->counts, t->abort_flag, t->st); }, n1);
     launch(t, K_SCAN, [&] { launch_scan_reset(t->cinc, t->cslot, t->cand_cap + 1, t->cscan, t->err,
-                                              t->st, nullptr, t->abort_flag); });
+                                              t->st, t->skin_on ? t->gate : nullptr,
+                                              t->abort_flag); }, n1);
     launch(t, K_KEYS, [&] { launch_active_sizes(d, t->rinfo, t->cslot, t->n_bodym, t->counts,
-                                                t->abort_flag, t->step_index, t->st); });
+                                                t->abort_flag, t->step_index, t->st); }, n1);
     launch(t, K_KEYS, [&] { launch_gather(d, t->ranges, t->rinfo, t->ckind, t->cslot, t->Mst,
                                           t->mpid, t->fixed_order, t->body_markers, t->n_bodym,
                                           (int)t->nFtot, t->cand_cap, t->A[c], t->pid[c],
-                                          t->counts, t->abort_flag, t->st); });
+                                          t->counts, t->abort_flag, t->st); }, n1);
     t->have_working = true;
 }
 
@@ -904,12 +946,13 @@ void enqueue_search(crm_terrain *t)
 
 void rebuild(crm_terrain *t)
 {
-    if (t->active) activity_pass(t);
     const DevParams &d = t->dp;
-    if (d.capN > 0) {
-        if (t->skin_on) launch(t, K_SKIN, [&] { launch_decide(d, t->gate, 0ull, 0, t->st); });
-        enqueue_search(t);
-    }
+    // with the skin, the decision gates the gather of the working set too
+    if (t->skin_on && (d.capN > 0 || t->active))
+        launch(t, K_SKIN, [&] { launch_decide(d, t->gate, 0ull, 0, t->st,
+                                              t->active ? t->counts : nullptr); });
+    if (t->active) activity_pass(t);
+    if (d.capN > 0) enqueue_search(t);
     if (!t->skin_on) t->cur = 1 - t->cur;
     t->lists_valid = true;
     t->prof.rebuilds += 1;
@@ -957,6 +1000,15 @@ void enqueue_stages(crm_terrain *t, double dt, bool filter)
 {
     const int c = t->cur;
     RateOut none{};
+    if (t->active && t->skin_on && t->dp.capF > 0) {
+        // the step's Active / Extended counts start from zero (the skin decision
+        // resets them in a step that runs it)
+        if (!filter) cudaMemsetAsync(t->counts + C_NA, 0, 2 * sizeof(int), t->st);
+        const int all = !(t->time > t->t_delay);
+        launch(t, K_SKIN, [&] { launch_flags(t->dp, (int)t->box_body_h.size(), t->box_body,
+                                             t->box_half, t->box_off, t->bodies, all, t->pid[c],
+                                             t->A[c].pos, t->counts, t->st); });
+    }
     bce(t, t->A[c], 0.0, 0, dt, 0, filter);   // also the bodies' midpoint frames
     pair(t, kStage1, t->A[c], t->A[c], (float)dt, none, filter);
     bce(t, t->MID, 0.5 * dt, 0);               // marker state at the midpoint
@@ -1008,7 +1060,8 @@ int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph 
         e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(t->st, g, nullptr, nullptr, 0, mode);
         if (e == cudaSuccess) {
-            launch_decide(d, t->gate, (unsigned long long)h, 1, t->st);
+            launch_decide(d, t->gate, (unsigned long long)h, 1, t->st,
+                          t->active ? t->counts : nullptr);
             e = cudaStreamEndCapture(t->st, &g);
         }
         cudaGraphNode_t dec = nullptr, cn = nullptr;
@@ -1024,7 +1077,8 @@ int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph 
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             e = cudaStreamBeginCaptureToGraph(t->st, body, nullptr, nullptr, 0, mode);
             if (e == cudaSuccess) {
-                enqueue_search(t);
+                if (t->active) activity_pass(t);
+                if (d.capN > 0) enqueue_search(t);
                 e = cudaStreamEndCapture(t->st, &body);
             }
         }
@@ -1082,6 +1136,7 @@ int graph_step(crm_terrain *t, double dt)
     if (search) {
         if (t->skin_on) {
             t->prof.launches[K_SKIN] += 1;
+            if (t->active && d.capF > 0) t->prof.launches[K_SKIN] += 1;   // the step's flags
         } else {
             t->prof.launches[K_KEYS] += 1;
             t->prof.launches[K_SCAN] += 1;
@@ -1129,7 +1184,7 @@ int step_active(crm_terrain *t, double dt, int n_steps)
 {
     const int SI = t->P.shrink_interval;
     int remaining = n_steps;
-    int guard = 0;
+    int guard = 0, rc0 = CRM_OK;
     while (remaining > 0) {
         const int64_t s0 = t->step_index;
         const double t0 = t->time;
@@ -1137,6 +1192,14 @@ int step_active(crm_terrain *t, double dt, int n_steps)
         const unsigned long long s0d = (unsigned long long)s0;
         CRM_CUDA(t, cudaMemcpyAsync(t->step_ctr, &s0d, sizeof(s0d), cudaMemcpyHostToDevice, t->st));
         for (int s = 0; s < chunk; ++s) {
+            // with the skin, the working set gathered while every particle was
+            // processed is replaced by the boxes' one at the first step after t_delay
+            const bool boxes = t->time > t->t_delay;
+            if (t->skin_on && boxes && !t->boxes_in_force) {
+                rc0 = invalidate_lists(t);
+                if (rc0) return rc0;
+            }
+            t->boxes_in_force = boxes;
             // graph replay once the working set exists and the boxes are in force
             // (before t_delay every particle is processed, a different launch set)
             if (t->graphs && !t->timing && t->cap_st && t->have_working && t->lists_valid
@@ -1174,7 +1237,8 @@ int step_active(crm_terrain *t, double dt, int n_steps)
             if (work) { rc = alloc_working(t); if (rc) return rc; }
             if (win) { rc = alloc_window(t); if (rc) return rc; }
             if (cand) { rc = alloc_cand(t); if (rc) return rc; }
-            t->lists_valid = false;
+            rc = invalidate_lists(t);
+            if (rc) return rc;
             CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), t->st));
             CRM_CUDA(t, cudaMemsetAsync(t->counts + C_NEED_F, 0, 4 * sizeof(int), t->st));
             continue;
@@ -1192,6 +1256,7 @@ int step_active(crm_terrain *t, double dt, int n_steps)
                 t->capF = std::max<int64_t>(nF, 1);
                 t->capM = std::max<int64_t>(nM, 1);
                 rc = alloc_working(t);
+                if (!rc) rc = invalidate_lists(t);
                 if (rc) return rc;
             }
             // the cell window and the candidate ranges follow the same rule (the
@@ -1200,8 +1265,8 @@ int step_active(crm_terrain *t, double dt, int n_steps)
             if (cells > 0 && (double)cells / (double)t->Mcap < S) {
                 t->Mcap = cells;
                 rc = alloc_window(t);
+                if (!rc) rc = invalidate_lists(t);
                 if (rc) return rc;
-                t->lists_valid = false;
             }
             if (cand > 0 && (double)cand / (double)t->cand_cap < S) {
                 t->cand_cap = cand;
@@ -1704,7 +1769,9 @@ int crm_eval_rates(crm_terrain *t, int64_t cap_sph, float *drho, float *dvel, fl
         if (rc) return rc;
         if (t->h_counts[C_WORDS] != 0) {
             CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), t->st));
-            t->lists_valid = false;
+            t->have_working = false;   // the abandoned rebuild wrote it back
+            rc = invalidate_lists(t);
+            if (rc) return rc;
             return t->fail(CRM_ENOMEM, "crm_eval_rates: active set exceeds its capacity; step once first");
         }
     }
@@ -1726,6 +1793,12 @@ int crm_eval_rates(crm_terrain *t, int64_t cap_sph, float *drho, float *dvel, fl
     float *odrho = o, *odu = o + nF, *ods = odu + 3 * nF, *omacc = ods + 6 * nF,
           *omvel = omacc + 3 * nM, *omsig = omvel + 3 * nM;
     CRM_CUDA(t, cudaMemsetAsync(o, 0, out_bytes, t->st));
+    if (t->active && t->skin_on && d.capF > 0) {
+        const int all = !(t->time > t->t_delay);
+        launch(t, K_SKIN, [&] { launch_flags(d, (int)t->box_body_h.size(), t->box_body,
+                                             t->box_half, t->box_off, t->bodies, all, t->pid[c],
+                                             t->A[c].pos, t->counts, t->st); });
+    }
     if (t->skin_on) {
         // exact lists from the skin lists first (marker and fluid rows)
         bce(t, t->A[c], 0.0, 0, 0.0, 0, true);
@@ -2021,8 +2094,8 @@ int batch_build(crm_batch *b, const double *dt)
             }
         }
         if (d.capF > 0) {
-            const int kav = pair_kav(d), ln = pair_lanes_of(d);
-            group(p1, kav).push_back({i, (int)grid_for(d.capF, 128)});
+            const int kav = pair_kav(d), ln = pair_lanes_of(d), fl = pair_filter_lanes(ln);
+            group(p1, 8 * kav + fl).push_back({i, (int)grid_for((int64_t)d.capF * fl, 128)});
             group(p2, 8 * kav + ln).push_back({i, (int)grid_for((int64_t)d.capF * ln, 128)});
         }
     }
@@ -2075,8 +2148,8 @@ int batch_build(crm_batch *b, const double *dt)
         bce_go(0, w_bce, b->cap, Q);
         int qi = 4;
         for (auto &x : w1) {
-            launch_batch_pair(kStage1, 1, x.first, b->dmem, T + x.second.mlist, T + x.second.off,
-                              x.second.n, x.second.total, Q + 2 * qi++, b->cap);
+            launch_batch_pair(kStage1, x.first % 8, x.first / 8, b->dmem, T + x.second.mlist,
+                              T + x.second.off, x.second.n, x.second.total, Q + 2 * qi++, b->cap);
             ++launches;
         }
         bce_go(1, w_bce, b->cap, Q + 2);
@@ -2343,6 +2416,11 @@ int crm_profile_read(crm_terrain *t, crm_profile *out)
             t->prof.launches[K_NEIGHBORS] += t->searched;
             t->prof.launches[K_SKIN] += t->searched;
             if (t->dp.capM > 0) t->prof.launches[K_COMPACT] += 2 * t->searched;
+            if (t->active) {   // the gated gather: write-back, box prep, activity, scan, sizes, gather
+                t->prof.launches[K_EXPORT] += n;
+                t->prof.launches[K_KEYS] += 4 * t->searched;
+                t->prof.launches[K_SCAN] += t->searched;
+            }
         }
     }
     for (auto &r : t->pending) {
@@ -2446,7 +2524,7 @@ int crm_load_state(crm_terrain *t, const void *dev_buf, size_t used)
     CRM_CUDA(t, cudaMemsetAsync(t->err, 0, sizeof(int), t->st));
     t->frozen = false;
     if (t->skin_on) {
-        const int g0[GATE_WORDS] = {1, 0, 1, 0};
+        const int g0[GATE_SEARCHES] = {1, 0, 1, 0};
         CRM_CUDA(t, cudaMemcpyAsync(t->gate, g0, sizeof(g0), cudaMemcpyHostToDevice, t->st));
     }
     CRM_CUDA(t, cudaStreamSynchronize(t->st));

@@ -112,9 +112,13 @@ __device__ __forceinline__ void body_update(const DevParams &p, const BodyStep &
             dc2 += d * d;
         }
         for (int k = 0; k < 4; ++k) w += B.pose[3 + k] * B.ref_pose[3 + k];
-        const float sh = sqrtf((float)fmax(0.0, 1.0 - w * w));
-        const float d = sqrtf((float)dc2) + 2.0f * sh * (float)B.rmax;
+        const float sh = sqrtf((float)fmax(0.0, 1.0 - w * w)), dc = sqrtf((float)dc2);
+        const float d = dc + 2.0f * sh * (float)B.rmax;
         atomicMax(bs.gate + GATE_DISP, __float_as_int(d * d * 1.0001f));
+        if (p.act_skin) {   // the same bound for the body's grown active boxes
+            const float db = dc + 2.0f * sh * (float)B.box_reach;
+            atomicMax(bs.gate + GATE_BOX, __float_as_int(db * db * 1.0001f));
+        }
     }
 }
 
@@ -263,6 +267,9 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
                 rx = o[0] - pj.x - sh.x; ry = o[1] - pj.y - sh.y; rz = o[2] - pj.z - sh.z;
                 const float r2 = rx * rx + ry * ry + rz * rz;
                 keep = r2 < p.four_h2;
+                // (active domains with a skin: fluid outside every grown box is in the
+                // working set's margin only, and no marker reads it)
+                if (FILTER && p.act_skin && keep && (__ldg(pid + j) & kOutsideBit)) keep = false;
                 if (keep) W = kernel_w(sqrtf(r2) * p.inv_h, p);
             }
             if (FILTER) {

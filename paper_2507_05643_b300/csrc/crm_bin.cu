@@ -583,17 +583,24 @@ void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *sta
 // displacement since the last search reached disp_thr2.  With a graph
 // conditional handle, it also switches the graph's rebuild branch.
 __global__ void k_decide(DevParams p, int *__restrict__ gate,
-                         cudaGraphConditionalHandle h, int use_handle)
+                         cudaGraphConditionalHandle h, int use_handle, int *__restrict__ counts)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (counts != nullptr) {   // the step's Active / Extended counts start from zero
+        counts[3] = 0;
+        counts[4] = 0;
+    }
     int due = 0;
     if (!*p.abort) {
         const float d2 = __int_as_float(gate[GATE_DISP]);
         due = (gate[GATE_FORCE] != 0 || !(d2 < p.disp_thr2)) ? 1 : 0;
+        // with active boxes: also when a box may have left the working set's margin
+        if (p.act_skin && !(__int_as_float(gate[GATE_BOX]) < p.box_thr2)) due = 1;
     }
     gate[GATE_REBUILD] = due;
     if (due) {
         gate[GATE_DISP] = 0;
+        gate[GATE_BOX] = 0;
         gate[GATE_FORCE] = 0;
         gate[GATE_SEARCHES] += 1;
     }
@@ -622,9 +629,10 @@ __global__ void k_copyback(DevParams p, StageArrays src, const uint32_t *__restr
 }
 
 void launch_decide(const DevParams &p, int *gate, unsigned long long cond_handle, int use_handle,
-                   cudaStream_t st)
+                   cudaStream_t st, int *counts)
 {
-    k_decide<<<1, 32, 0, st>>>(p, gate, (cudaGraphConditionalHandle)cond_handle, use_handle);
+    k_decide<<<1, 32, 0, st>>>(p, gate, (cudaGraphConditionalHandle)cond_handle, use_handle,
+                               counts);
 }
 
 void launch_copyback(const DevParams &p, StageArrays src, const uint32_t *pid_src, StageArrays dst,

@@ -24,9 +24,15 @@ constexpr int kAbortTimeout = (int)0x80000000;
 
 constexpr int kMaxBodies = 16;
 constexpr uint32_t kExtendedBit = 0x80000000u;   // pid flag: Extended-Active (read-only)
-// particle id: insertion index in bits 0..30 (fluid particles, then markers);
-// bit 31 = Extended-Active.  Each body's markers hold one contiguous id range.
-constexpr uint32_t kPidIndexMask = 0x7FFFFFFFu;
+// particle id: insertion index in bits 0..28 (fluid particles, then markers);
+// bit 31 = not integrated this step (Extended-Active, or outside); with active
+// domains and a Verlet skin, bit 30 = outside every box grown by 2h (in the
+// working set's margin: read by nobody) and bit 29 = integrated at some step
+// since the working set was gathered (written back to the master store).  Each
+// body's markers hold one contiguous id range.
+constexpr uint32_t kOutsideBit = 0x40000000u;
+constexpr uint32_t kTouchedBit = 0x20000000u;
+constexpr uint32_t kPidIndexMask = 0x1FFFFFFFu;
 __host__ __device__ __forceinline__ uint32_t pid_index(uint32_t id) { return id & kPidIndexMask; }
 constexpr uint32_t kIndexBits = 26;                 // neighbour entry: j | code << 26
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
@@ -59,6 +65,10 @@ struct DevParams {
     int n_bodies;
     uint32_t body_lo[kMaxBodies], body_hi[kMaxBodies];   // particle-id range of each body's markers
     int n_sm;                             // multiprocessors of the device (launch shapes)
+    int act_skin;                         // active domains with a Verlet skin: the working
+    double act_margin;                    // set is gathered act_margin beyond the boxes
+                                          // grown by 2h and kept across steps, until a
+    float box_thr2;                       // box may have moved sqrt(box_thr2) < act_margin
     int abs32;                            // test-only: every stored position rounded to an
                                           // absolute FP32 coordinate (crm_debug_absolute_fp32)
     int tbx, tby, tbz;                    // cell tiles of the sort order: log2 of their
@@ -87,7 +97,7 @@ struct DevParams {
 // gate word layout: [0] rebuild due this step, [1] max squared displacement
 // since the last search (float bits, compared as int), [2] forced rebuild
 // [3] cell searches done (counter, for the launch bookkeeping)
-enum { GATE_REBUILD = 0, GATE_DISP = 1, GATE_FORCE = 2, GATE_SEARCHES = 3, GATE_WORDS = 4 };
+enum { GATE_REBUILD = 0, GATE_DISP = 1, GATE_FORCE = 2, GATE_BOX = 3, GATE_SEARCHES = 4, GATE_WORDS = 5 };
 
 __device__ __forceinline__ bool gated_off(const DevParams &p)
 {
@@ -152,6 +162,8 @@ struct BodyDev {
     double inertia[3];  // principal moments of inertia in the body frame
     double load[6];     // external force and torque about the centre, added to the soil's
     double inv_mass;    // 1 / mass (FP64 division is a long sequence on the device)
+    double box_reach;   // largest distance from the centre of a point of the body's active
+                        // boxes grown by 2h (active domains with a skin; else 0)
 };
 
 // Body of the particle with id `id`: -1 for fluid particles and fixed markers.
@@ -441,7 +453,13 @@ void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *sta
 // copy the re-sorted arrays back (the stage-1 kernels filter the skin lists
 // down to the exact 2h lists).
 void launch_decide(const DevParams &p, int *gate, unsigned long long cond_handle, int use_handle,
-                   cudaStream_t st);
+                   cudaStream_t st, int *counts = nullptr);
+// Active domains with a Verlet skin: the activity of every working-set fluid
+// particle against this step's boxes (Active / Extended-Active / outside bits
+// of its pid) and the Active and Extended counts (counts[3], counts[4]).
+void launch_flags(const DevParams &p, int nbox, const int *box_body, const double *box_half,
+                  const double *box_off, const BodyDev *bodies, int all_active, uint32_t *pid,
+                  const float4 *pos, int *counts, cudaStream_t st);
 void launch_copyback(const DevParams &p, StageArrays src, const uint32_t *pid_src, StageArrays dst,
                      uint32_t *pid_dst, float4 *xref, BodyDev *bodies, cudaStream_t st);
 
@@ -548,6 +566,8 @@ void launch_batch_pair(int mode, int lanes, int kav, const MemberDev *mem, const
                        const int *off, int n, int total, unsigned *queue, cudaStream_t st);
 int pair_kav(const DevParams &p);
 int pair_lanes_of(const DevParams &p);
+// Lanes per particle of the filtering pair kernels, given the other kernels' lanes.
+inline int pair_filter_lanes(int lanes) { return lanes == 4 ? 4 : 1; }
 
 // Active domains (Sec. 3.2, Alg. 3), crm_active.cu.
 size_t box_frame_bytes();
@@ -570,7 +590,7 @@ void launch_gather(const DevParams &p, const int *ranges, const int *rinfo,
                    int64_t cand_cap, StageArrays W, uint32_t *wpid, const int *counts,
                    const int *abort_flag, cudaStream_t st);
 void launch_scatter_back(const DevParams &p, StageArrays W, const uint32_t *wpid,
-                         const uint32_t *mslot_of_pid, const int *mcol, StageArrays M, int *drift,
+                         const uint32_t *mslot_of_pid, const int *mcol, StageArrays M, int *drift, int gated,
                          cudaStream_t st);
 void launch_export_master(const DevParams &p, StageArrays M, const uint32_t *mpid, int n,
                           double *xyz, float *vel, float *sig, float *rho, cudaStream_t st);

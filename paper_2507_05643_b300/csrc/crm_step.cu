@@ -374,8 +374,8 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
 
 // Batched form (crm_batch): persistent blocks take virtual blocks of the
 // members' own pair launches off the work queue (an atomic ticket) and run them
-// as those launches would: stage 1 filtering the skin lists with one lane per
-// particle, stage 2 on the exact lists with the member's lanes.
+// as those launches would: stage 1 filtering the skin lists, stage 2 on the
+// exact lists, each with the member's lanes.
 template <int MODE, int LANES, int KAV>
 __global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
 k_batch_pair(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
@@ -411,9 +411,9 @@ k_batch_pair(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
             const RateOut none{};
             if (MODE == kStage1) {
                 const ListIO io{M.sk_nbr, M.sk_nnb, M.nbr, M.nnb, M.err};
-                pair_one<kStage1, true, 1, KAV>(M.p, t, 0, __ldg(M.p.sizes), lut, M.S, M.S, M.MID,
-                                                io, nullptr, (float)M.dt, none, M.err, nullptr,
-                                                nullptr);
+                pair_one<kStage1, true, LANES, KAV>(M.p, t / LANES, t % LANES, __ldg(M.p.sizes),
+                                                    lut, M.S, M.S, M.MID, io, nullptr,
+                                                    (float)M.dt, none, M.err, nullptr, nullptr);
             } else {
                 const ListIO io{M.nbr, M.nnb, nullptr, nullptr, M.err};
                 pair_one<kStage2, false, LANES, KAV>(M.p, t / LANES, t % LANES, __ldg(M.p.sizes),
@@ -499,12 +499,20 @@ void launch_pair_k(int mode, int LN, const DevParams &p, StageArrays S, StageArr
     const unsigned g1 = grid_for(p.capF, B);
     if (sk_nbr != nullptr) {   // stage 1 or an evaluation right after a skin search
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        if (mode == kStage1)
+        if (pair_filter_lanes(LN) == 4) {
+            if (mode == kStage1)
+                k_pair<kStage1, true, 4, KAV><<<g, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err,
+                                                               nullptr, nullptr);
+            else
+                k_pair<kEval, true, 4, KAV><<<g, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err,
+                                                             nullptr, nullptr);
+        } else if (mode == kStage1) {
             k_pair<kStage1, true, 1, KAV><<<g1, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err,
                                                             nullptr, nullptr);
-        else
+        } else {
             k_pair<kEval, true, 1, KAV><<<g1, B, 0, st>>>(p, S, Y, MID, L, pid, dt, out, err,
                                                           nullptr, nullptr);
+        }
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
@@ -531,11 +539,12 @@ void launch_pair(int mode, const DevParams &p, StageArrays S, StageArrays Y, Sta
                  RateOut out, int *err, const float4 *xref, int *gate, cudaStream_t st,
                  const uint32_t *sk_nbr, const uint32_t *sk_nnb)
 {
-    // filtering kernels keep one lane per particle (the lane group's ballot per
-    // candidate costs more than the extra warps gain); the others take
-    // p.pair_lanes (1, 2 or 4), a per-terrain tuning knob; by default four lanes
-    // while four threads per particle still fit the GPU's resident threads (a
-    // small working set otherwise leaves most warp slots empty), else kPairLanes
+    // the kernels on exact lists take p.pair_lanes (1, 2 or 4), a per-terrain
+    // tuning knob; by default four lanes while four threads per particle still
+    // fit the GPU's resident threads (a small working set otherwise leaves most
+    // warp slots empty), else kPairLanes.  The filtering kernels follow with four
+    // lanes, else one (on a large working set the lane group's ballot per
+    // candidate costs more than the extra warps gain).
     const int LN = p.pair_lanes != 0 ? p.pair_lanes
                                      : ((int64_t)p.capF * 4 <= (int64_t)p.n_sm * 2048 ? 4 : kPairLanes);
     const int kav = 3 * (p.kernel == CRM_KERNEL_WENDLAND ? 1 : 0)
@@ -585,8 +594,10 @@ template <int KAV>
 void batch_pair_k(int mode, int lanes, const MemberDev *mem, const int *mlist, const int *off,
                   int n, int total, unsigned *queue, cudaStream_t st)
 {
-    if (mode == kStage1) batch_pair_go<kStage1, 1, KAV>(mem, mlist, off, n, total, queue, st);
-    else if (lanes == 1) batch_pair_go<kStage2, 1, KAV>(mem, mlist, off, n, total, queue, st);
+    if (mode == kStage1) {
+        if (lanes == 4) batch_pair_go<kStage1, 4, KAV>(mem, mlist, off, n, total, queue, st);
+        else batch_pair_go<kStage1, 1, KAV>(mem, mlist, off, n, total, queue, st);
+    } else if (lanes == 1) batch_pair_go<kStage2, 1, KAV>(mem, mlist, off, n, total, queue, st);
     else if (lanes == 4) batch_pair_go<kStage2, 4, KAV>(mem, mlist, off, n, total, queue, st);
     else batch_pair_go<kStage2, 2, KAV>(mem, mlist, off, n, total, queue, st);
 }

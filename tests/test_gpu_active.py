@@ -159,3 +159,46 @@ def test_strip_window_far_from_origin_matches_oracle():
         F, _ = t.body_wrench(b)
         Fo = st.bodies.wrench[b, :3]
         assert np.linalg.norm(F - Fo) <= 1e-3 * np.linalg.norm(Fo)
+
+
+@pytest.mark.parametrize("t_delay", [-1.0, 0.00045])
+def test_active_skin_agrees_with_per_step_gather(t_delay):
+    """Active domains with a Verlet skin keep the working set (gathered with a
+    margin beyond the grown boxes) across steps and re-flag it every step; the
+    trajectory matches the per-step gather without the skin up to FP32 rounding,
+    the flags agree but for particles at a face, terrain never integrated stays
+    at its FP32 inputs, and most steps skip the gather and the search."""
+    sc = _scene(seed=54, carrier_v=(2.0, 0.0, 0.0), t_delay=t_delay)
+    a = crm.from_scene(sc, skin=0.1)
+    b = crm.from_scene(sc, skin=0.0)
+    a.step(sc.dt, 0)
+    b.step(sc.dt, 0)
+    x0, _, s0, _ = a.particles()
+    xb0, _, sb0, _ = b.particles()
+    a.profile_reset()
+    n = 60
+    a.step(sc.dt, n)
+    b.step(sc.dt, n)
+    prof = a.profile()
+    xa, va, sa, ra = a.particles()
+    xb, vb, sb, rb = b.particles()
+    d0 = sc.params["d0"]
+    assert np.max(np.abs(xa - xb)) < 2e-5 * d0
+    assert np.sqrt(np.mean((sa - sb) ** 2)) < 2e-5 * sc.params["rho0"] * 9.81 * 0.1
+    na, ne, nb = a.counts()
+    ma, me, mb = b.counts()
+    st = oracle.State(sc)
+    st.run(n)
+    near = _near_face(st.x, sc.boxes, st.bodies.pose, sc.params["h"], tol=1e-6)
+    assert abs(na - ma) <= near.sum() and abs(ne - me) <= near.sum(), (na, ma, ne, me)
+    assert na > 500 and ne > 200
+    if t_delay < 0:   # (before t_delay every particle is integrated)
+        never = np.all(xb == xb0, axis=1) & np.all(sb == sb0, axis=1)
+        assert never.sum() > 1000
+        assert np.array_equal(xa[never], x0[never]) and np.array_equal(sa[never], s0[never])
+    gathers = prof["launches"]["neighbors"]
+    print("active skin: gathers", gathers, "of", n, "steps; counts", (na, ne), (ma, me))
+    assert 1 <= gathers < n // 2, prof
+    Fa, _ = a.body_wrench(0)
+    Fb, _ = b.body_wrench(0)
+    assert np.linalg.norm(Fa - Fb) <= 1e-3 * np.linalg.norm(Fb) + 1e-9
