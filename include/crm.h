@@ -102,7 +102,11 @@ typedef struct crm_params {
                               first-stage kernels filter those lists down to the exact
                               2h sets (the same sets a fresh search gives) while they
                               compute the stage.  0 = a fresh 2h search every rebuild.
-                              Ignored with active boxes. */
+                              With active boxes the Alg. 3 working set is gathered
+                              4 skin h beyond the boxes grown by 2h and kept until the
+                              search is due (also when a point of a grown box may
+                              have moved 0.95 of that margin); every step re-flags it
+                              against the current boxes. */
 } crm_params;
 
 typedef struct crm_terrain crm_terrain;
@@ -446,7 +450,8 @@ int crm_batch_destroy(crm_batch *b);
  * keys, scan, scatter, reorder, neighbors (cell search), compact (markers with
  * fluid in reach), bce (with the body wrench and update), pair_stage1,
  * pair_stage2 (with a skin, the first-stage kernels after a rebuild also filter
- * the exact lists), skin (search decision and copy-back), export, adjoint (the
+ * the exact lists), skin (search decision, copy-back and, with active boxes, the
+ * per-step activity flags), export, adjoint (the
  * reverse-sweep kernels of crm_eval_rates_vjp and crm_adjoint_backward). */
 #define CRM_NUM_KERNELS 12
 typedef struct crm_profile {
