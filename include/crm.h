@@ -138,7 +138,9 @@ const char *crm_last_error(const crm_terrain *t);
 /* Add n SPH particles (Sec. 2.2).  xyz: n*3 positions (required); vel: n*3
  * velocities, stress6: n*6 stresses, rho: n densities -- each nullable
  * (zero velocity, zero stress, rho0).  Host arrays, copied.  Only before the
- * first crm_step / crm_eval_rates (else CRM_ESTATE). */
+ * first crm_step / crm_eval_rates (else CRM_ESTATE).  A terrain holds fewer than
+ * 2^29 SPH particles and markers together (the first step returns CRM_EINVAL
+ * otherwise: a slot's id keeps three flag bits). */
 int crm_add_sph(crm_terrain *t, int64_t n, const double *xyz, const double *vel,
                 const double *stress6, const double *rho);
 

@@ -533,7 +533,7 @@ int commit(crm_terrain *t)
     if (t->committed) return CRM_OK;
     const int64_t nF = t->nFtot, nM = t->nMtot, N = nF + nM;
     if (N >= (int64_t)kPidIndexMask)
-        return t->fail(CRM_EINVAL, "more than 2^31 - 1 particles and markers in one terrain");
+        return t->fail(CRM_EINVAL, "more than 2^29 - 1 particles and markers in one terrain");
     for (const BodyDev &b : t->hbodies)
         if ((b.dof & (7 << 3)) && !(b.inertia[0] > 0 && b.inertia[1] > 0 && b.inertia[2] > 0))
             return t->fail(CRM_EINVAL, "a body with free angular DOFs needs crm_set_body_inertia");
