@@ -666,8 +666,6 @@ template <bool ACC, int LANES>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
 {
-    __shared__ float4 lut[64];
-    fill_shift_table(lut, p.cell);
     __syncthreads();
     const Sizes z = load_sizes(p);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -722,7 +720,7 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
     for (int k = q; k < nn; k += LANES) {
         const uint32_t e = V.nbr[(size_t)k * p.ell + s];
         const uint32_t f = e & kIndexMask;
-        const float4 sh = lut[e >> kIndexBits];
+        const float3 sh = entry_shift(e, p.cell);
         const float4 pf = S.pos[f];
         const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
         const float r2 = rx * rx + ry * ry + rz * rz;
@@ -828,7 +826,7 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
         for (int k = q; k < nn; k += LANES) {
             const uint32_t e = V.nbr[(size_t)k * p.ell + s];
             const uint32_t f = e & kIndexMask;
-            const float4 sh = lut[e >> kIndexBits];
+            const float3 sh = entry_shift(e, p.cell);
             const float4 pf = S.pos[f];
             const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
             const float r2 = rx * rx + ry * ry + rz * rz;
@@ -947,8 +945,6 @@ template <bool ACC, int OUT, int LANES>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, double *gpar)
 {
-    __shared__ float4 lut[64];
-    fill_shift_table(lut, p.cell);
     __syncthreads();
     const Sizes z = load_sizes(p);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -967,7 +963,7 @@ k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, dou
         for (int k = q; k < nn; k += LANES) {
             const uint32_t e = V.nbr[(size_t)k * p.ell + i];
             const uint32_t j = e & kIndexMask;
-            const float4 sh = lut[e >> kIndexBits];
+            const float3 sh = entry_shift(e, p.cell);
             const float4 pj = S.pos[j];
             const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
             const float r2 = rx * rx + ry * ry + rz * rz;

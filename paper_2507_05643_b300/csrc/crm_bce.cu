@@ -170,7 +170,7 @@ __device__ __forceinline__ void block_wrench_partial(const DevParams &p, const f
 }
 
 // The work of block vb of a k_bce launch (a kBlock-thread block; every thread
-// of the block calls it; lut, red and s_bodies are the block's shared arrays).
+// of the block calls it; red and s_bodies are the block's shared arrays).
 template <int ACCEL, bool FILTER, int LANES>
 __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
                                           const float4 *__restrict__ home_pos,
@@ -180,7 +180,7 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
                                           const uint32_t *__restrict__ act,
                                           const int *__restrict__ n_act, double tau,
                                           int n_fluid_total, float4 *__restrict__ mforce,
-                                          const BodyStep &bs, int vb, float4 *lut,
+                                          const BodyStep &bs, int vb,
                                           double (*red)[6], unsigned &s_bodies)
 {
     static_assert(!(FILTER && ACCEL != 0), "filtering runs in stage 1 only (no accelerations)");
@@ -189,7 +189,6 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
         // the midpoint frames of the following stage-2 launch, once per step
         body_frame(bodies[threadIdx.x], 0.5 * bs.dt, frames[threadIdx.x]);
     }
-    fill_shift_table(lut, p.cell);
     if (threadIdx.x == 0) s_bodies = 0u;
     __syncthreads();
     const Sizes z = load_sizes(p);
@@ -259,7 +258,7 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
             float rx = 0.f, ry = 0.f, rz = 0.f;
             if (k < nn) {
                 const uint32_t j = e & kIndexMask;
-                const float4 sh = lut[e >> kIndexBits];
+                const float3 sh = entry_shift(e, p.cell);
                 const float4 pj = __ldg(&S.pos[j]);
                 vj = __ldg(&S.vel[j]);
                 aj = __ldg(&S.sA[j]);
@@ -331,7 +330,7 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
                 if (k + LANES < n2) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
                 if (k >= n2) continue;
                 const uint32_t j = e & kIndexMask;
-                const float4 sh = lut[e >> kIndexBits];
+                const float3 sh = entry_shift(e, p.cell);
                 const float4 pj = __ldg(&S.pos[j]);
                 const float4 vj = __ldg(&S.vel[j]);
                 const float4 aj = __ldg(&S.sA[j]);
@@ -387,11 +386,10 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
       BodyStep bs)
 {
     if (*p.abort) return;
-    __shared__ float4 lut[64];
     __shared__ double red[kBlock / 32][6];
     __shared__ unsigned s_bodies;
     bce_block<ACCEL, FILTER, LANES>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
-                                    n_fluid_total, mforce, bs, blockIdx.x, lut, red, s_bodies);
+                                    n_fluid_total, mforce, bs, blockIdx.x, red, s_bodies);
 }
 
 // The soil wrench of body b = blockIdx.x (Sec. 2.4): the sum of the wrench
@@ -450,7 +448,6 @@ __global__ void __launch_bounds__(kBlock)
 k_batch_bce(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
             const int *__restrict__ off, int n, unsigned *queue)
 {
-    __shared__ float4 lut[64];
     __shared__ double red[kBlock / 32][6];
     __shared__ unsigned s_bodies;
     __shared__ int s_item;
@@ -473,26 +470,26 @@ k_batch_bce(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
             }
             if (*M.p.abort) continue;
             const int vb = it - __ldg(off + k);
-            __syncthreads();   // the previous virtual block's readers of lut / red are done
+            __syncthreads();   // the previous virtual block's readers of red are done
             if (KIND == 0) {
                 const ListIO L{M.sk_nbr, M.sk_nnb, M.nbr, M.nnb, M.err};
                 const BodyStep bs{M.partial, M.bodies, M.dt, 0, M.gate};
                 bce_block<0, true, kBceLanes>(M.p, M.S, M.S.pos, M.pid, M.mloc, M.bodies, M.frames,
                                               L, M.act, M.n_act, 0.0, M.n_fluid_total, M.mforce, bs,
-                                              vb, lut, red, s_bodies);
+                                              vb, red, s_bodies);
             } else if (KIND == 1) {
                 const ListIO L{M.nbr, M.nnb, nullptr, nullptr, M.err};
                 const BodyStep bs{M.partial, M.bodies, 0.0, 0, M.gate};
                 bce_block<0, false, kBceLanes>(M.p, M.MID, M.S.pos, M.pid, M.mloc, M.bodies,
                                                M.frames, L, M.act, M.n_act, 0.5 * M.dt,
-                                               M.n_fluid_total, M.mforce, bs, vb, lut, red,
+                                               M.n_fluid_total, M.mforce, bs, vb, red,
                                                s_bodies);
             } else {
                 const ListIO L{M.nbr, M.nnb, nullptr, nullptr, M.err};
                 const BodyStep bs{M.partial, M.bodies, M.dt, 1, M.gate};
                 bce_block<1, false, kWrenchLanes>(M.p, M.MID, M.S.pos, M.pid, M.mloc, M.bodies,
                                                   M.frames, L, M.act_body, M.n_act + 1, 0.5 * M.dt,
-                                                  M.n_fluid_total, M.mforce, bs, vb, lut, red,
+                                                  M.n_fluid_total, M.mforce, bs, vb, red,
                                                   s_bodies);
             }
         }

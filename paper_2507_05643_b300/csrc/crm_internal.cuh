@@ -382,15 +382,18 @@ __device__ __forceinline__ float4 round_absolute(const DevParams &p, float4 ps)
     return ps;
 }
 
-// Cell offsets of the neighbour codes (dx, dy, dz in {-1, 0, 1}) times the cell
-// size, built once per block in shared memory.
-__device__ __forceinline__ void fill_shift_table(float4 *lut, float cell)
+// Cell offset of a neighbour entry e = j | code << 26 (code = (dx+1) | (dy+1)
+// << 2 | (dz+1) << 4, dx, dy, dz in {-1, 0, 1}) times the cell size, in
+// registers: 2^23 + c has the bit pattern 0x4B000000 | c for small c, so
+// (2^23 + c) - (2^23 + 1) = c - 1 exactly, with no integer-to-float
+// conversion, and the products with the cell size are exact.
+__device__ __forceinline__ float3 entry_shift(uint32_t e, float cell)
 {
-    const int t = threadIdx.x;
-    if (t < 64) {
-        const int dx = (t & 3) - 1, dy = ((t >> 2) & 3) - 1, dz = (t >> 4) - 1;
-        lut[t] = make_float4((float)dx * cell, (float)dy * cell, (float)dz * cell, 0.0f);
-    }
+    const uint32_t c = e >> kIndexBits;
+    const float fx = __uint_as_float(0x4B000000u | (c & 3u)) - 8388609.0f;
+    const float fy = __uint_as_float(0x4B000000u | ((c >> 2) & 3u)) - 8388609.0f;
+    const float fz = __uint_as_float(0x4B000000u | (c >> 4)) - 8388609.0f;
+    return make_float3(fx * cell, fy * cell, fz * cell);
 }
 
 // Neighbour lists a kernel walks (and, when filtering, writes).

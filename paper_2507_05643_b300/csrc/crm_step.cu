@@ -239,7 +239,7 @@ __device__ __forceinline__ void stage_epilogue(const DevParams &p, int i, const 
 // for i < limit.
 template <int MODE, bool FILTER, int LANES, int KAV>
 __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int limit,
-                                         const float4 *lut, StageArrays S, StageArrays Y,
+                                         StageArrays S, StageArrays Y,
                                          StageArrays MID, const ListIO &io,
                                          const uint32_t *__restrict__ pid, float dt, RateOut out,
                                          int *__restrict__ err, const float4 *__restrict__ xref,
@@ -284,7 +284,7 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
             const uint32_t e = e_nx;
             if (k + LANES < nn) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
             const uint32_t j = e & kIndexMask;
-            const float4 sh = lut[e >> kIndexBits];
+            const float3 sh = entry_shift(e, p.cell);
             const float4 pj = __ldg(&S.pos[j]);
             float4 vj, aj;
             float2 bj;
@@ -315,7 +315,7 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
             uint32_t j = 0;
             if (k < nn) {
                 j = e & kIndexMask;
-                const float4 sh = lut[e >> kIndexBits];
+                const float3 sh = entry_shift(e, p.cell);
                 const float4 pj = __ldg(&S.pos[j]);
                 rx = pi.x - pj.x - sh.x; ry = pi.y - pj.y - sh.y; rz = pi.z - pj.z - sh.z;
                 r2 = rx * rx + ry * ry + rz * rz;
@@ -364,11 +364,8 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
     if (*p.abort) return;
     if (MODE == kStage2 && p.step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(p.step_ctr, 1ull);   // the step completes (no abort seen)
-    __shared__ float4 lut[64];
-    fill_shift_table(lut, p.cell);
-    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    pair_one<MODE, FILTER, LANES, KAV>(p, t / LANES, t % LANES, __ldg(p.sizes), lut, S, Y, MID,
+    pair_one<MODE, FILTER, LANES, KAV>(p, t / LANES, t % LANES, __ldg(p.sizes), S, Y, MID,
                                        io, pid, dt, out, err, xref, gate);
 }
 
@@ -381,11 +378,10 @@ __global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
 k_batch_pair(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
              const int *__restrict__ off, int n, unsigned *queue)
 {
-    __shared__ float4 lut[64];
     __shared__ int s_item;
     __shared__ MemberDev M;
     const int total = __ldg(off + n);
-    int cur = -1;   // the member whose descriptor and shift table are loaded
+    int cur = -1;   // the member whose descriptor is loaded
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u) * kBatchChunk;
@@ -402,7 +398,6 @@ k_batch_pair(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
             if (lo != cur) {   // block-uniform
                 __syncthreads();
                 load_member(mem + __ldg(mlist + lo), &M);
-                fill_shift_table(lut, M.p.cell);
                 __syncthreads();
                 cur = lo;
             }
@@ -412,12 +407,12 @@ k_batch_pair(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
             if (MODE == kStage1) {
                 const ListIO io{M.sk_nbr, M.sk_nnb, M.nbr, M.nnb, M.err};
                 pair_one<kStage1, true, LANES, KAV>(M.p, t / LANES, t % LANES, __ldg(M.p.sizes),
-                                                    lut, M.S, M.S, M.MID, io, nullptr,
+                                                    M.S, M.S, M.MID, io, nullptr,
                                                     (float)M.dt, none, M.err, nullptr, nullptr);
             } else {
                 const ListIO io{M.nbr, M.nnb, nullptr, nullptr, M.err};
                 pair_one<kStage2, false, LANES, KAV>(M.p, t / LANES, t % LANES, __ldg(M.p.sizes),
-                                                     lut, M.MID, M.S, M.MID, io, nullptr,
+                                                     M.MID, M.S, M.MID, io, nullptr,
                                                      (float)M.dt, none, M.err, M.xref, M.gate);
             }
         }
