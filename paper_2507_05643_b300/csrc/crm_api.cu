@@ -105,6 +105,11 @@ struct crm_terrain {
     uint32_t *act_bcount = nullptr;
     int *n_act = nullptr;                          // [2]: sizes of act, act_body
     cudaStream_t side = nullptr;                   // the wrench pass beside pair stage 2
+    // the checkpointed backward: the reverse sweep runs on its own stream while
+    // the handle's stream re-runs the previous segment (events: re-run done and
+    // sweep done, per tape set)
+    cudaStream_t adj_st = nullptr;
+    cudaEvent_t adj_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int *err = nullptr, *counts = nullptr, *win = nullptr, *abort_flag = nullptr;
     int *h_counts = nullptr;      // pinned mirror: counters + abort word
@@ -153,7 +158,11 @@ struct crm_terrain {
         char *ckpt = nullptr;
         BodyDev *hist = nullptr;
         double *lw_obj = nullptr, *lc_obj = nullptr;
+        // checkpointed runs: two tape sets of one segment each (a re-run fills one
+        // while the sweep reads the other); the step index and time of each
+        // checkpoint, for the stream-ordered restore
         std::vector<AdjTape> tape;
+        std::vector<std::pair<int64_t, double>> ckpt_at;
     } adj;
 
     std::vector<void *> allocs[G_COUNT];
@@ -1386,6 +1395,11 @@ int crm_destroy(crm_terrain *t)
         cudaStreamDestroy(t->side);
         cudaEventDestroy(t->ev_fork);
         cudaEventDestroy(t->ev_join);
+    }
+    if (t->adj_st) {
+        cudaStreamSynchronize(t->adj_st);
+        cudaStreamDestroy(t->adj_st);
+        for (cudaEvent_t e : t->adj_ev) cudaEventDestroy(e);
     }
     drop_tape(t);
     for (int g = 0; g < G_COUNT; ++g) t->free_group(g);
@@ -2788,6 +2802,49 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     return CRM_OK;
 }
 
+// Restore checkpoint g of the recorded run into the working arrays, in stream
+// order on the handle's stream: no host synchronisation, and no header read
+// back (the checkpoint was written by crm_adjoint_forward on this terrain, in
+// crm_save_state's layout, and the host kept its step index and time).
+int restore_ckpt(crm_terrain *t, int64_t g)
+{
+    crm_terrain::Adjoint &A = t->adj;
+    const int64_t n = t->nFtot + t->nMtot;
+    const StageArrays S = t->A[t->cur];
+    const char *b = A.ckpt + (size_t)g * A.ckpt_bytes;
+    size_t o = 64;
+    auto get = [&](void *dst, size_t nb) {
+        cudaError_t e = cudaMemcpyAsync(dst, b + o, nb, cudaMemcpyDeviceToDevice, t->st);
+        o += nb;
+        return e;
+    };
+    CRM_CUDA(t, get(S.pos, n * sizeof(float4)));
+    CRM_CUDA(t, get(S.vel, n * sizeof(float4)));
+    CRM_CUDA(t, get(S.sA, n * sizeof(float4)));
+    CRM_CUDA(t, get(S.sB, n * sizeof(float2)));
+    CRM_CUDA(t, get(t->pid[t->cur], n * sizeof(uint32_t)));
+    if (!t->hbodies.empty()) CRM_CUDA(t, get(t->bodies, t->hbodies.size() * sizeof(BodyDev)));
+    t->step_index = A.ckpt_at[(size_t)g].first;
+    t->time = A.ckpt_at[(size_t)g].second;
+    t->lists_valid = false;
+    t->have_working = false;
+    CRM_CUDA(t, cudaMemsetAsync(t->abort_flag, 0, sizeof(int), t->st));
+    CRM_CUDA(t, cudaMemsetAsync(t->err, 0, sizeof(int), t->st));
+    t->frozen = false;
+    return CRM_OK;
+}
+
+// Re-run segment g (from its checkpoint) into tape set `set` on the handle's stream.
+int rerun_segment(crm_terrain *t, int64_t g, int set)
+{
+    crm_terrain::Adjoint &A = t->adj;
+    const int64_t seg = A.every, s0 = g * A.every, s1 = std::min<int64_t>(A.n_steps, s0 + A.every);
+    int rc = restore_ckpt(t, g);
+    for (int64_t s = s0; s < s1 && rc == CRM_OK; ++s)
+        rc = record_step(t, A.dt, A.tape[(size_t)(set * seg + (s - s0))]);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2899,10 +2956,12 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
         A.lw_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 6 * n_steps);
         A.lc_obj = t->dalloc<double>(G_TAPE, std::max<size_t>(nb, 1) * 3 * n_steps);
     }
-    // the tape of one segment (of the whole run when resident)
+    // the tape of the whole run when resident, else two tape sets of one segment
+    // each (the backward re-runs one segment into a set while it sweeps the other)
     const int64_t seg = resident ? n_steps : std::min<int64_t>(every, n_steps);
+    const int64_t slots = resident ? seg : 2 * seg;
     const size_t N = (size_t)std::max(d.capN, 1);
-    for (int64_t k = reuse ? seg : 0; k < seg && !t->oom; ++k) {
+    for (int64_t k = reuse ? slots : 0; k < slots && !t->oom; ++k) {
         crm_terrain::AdjTape T = no_tape();
         for (StageArrays *S : {&T.Y0, &T.YM}) {
             S->pos = t->dalloc<float4>(G_TAPE, N);
@@ -2931,6 +2990,7 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
     A.alloc_every = every;
     A.dt = dt;
     A.every = every;
+    A.ckpt_at.assign(A.n_ckpt, {0, 0.0});
     size_t used = 0;
     for (int64_t s = 0; s < n_steps; ++s) {
         if (resident) {
@@ -2939,6 +2999,7 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
             rc = record_step(t, dt, A.tape[(size_t)s]);
         } else {
             if (s % every == 0) {
+                A.ckpt_at[(size_t)(s / every)] = {t->step_index, t->time};
                 rc = crm_save_state(t, A.ckpt + (size_t)(s / every) * A.ckpt_bytes, A.ckpt_bytes, &used);
                 if (rc) return rc;
             }
@@ -2950,6 +3011,7 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
                                         cudaMemcpyDeviceToDevice, t->st));
     }
     if (!resident) {
+        A.ckpt_at[(size_t)(A.n_ckpt - 1)] = {t->step_index, t->time};
         rc = crm_save_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, A.ckpt_bytes, &used);
         if (rc) return rc;
     }
@@ -3017,24 +3079,51 @@ int crm_adjoint_backward(crm_terrain *t, const double *l_wrench, const double *l
         }
         return adj_export(t, A.lb[0], g_xyz, g_vel, g_stress, g_rho, g_body, g_params);
     }
-    size_t sb = 0;
-    crm_state_bytes(t, &sb);
-    const int64_t n_seg = (n + A.every - 1) / A.every;
-    for (int64_t g = n_seg - 1; g >= 0; --g) {
-        int rc = crm_load_state(t, A.ckpt + (size_t)g * A.ckpt_bytes, sb);
-        if (rc) return rc;
-        const int64_t s0 = g * A.every, s1 = std::min<int64_t>(n, s0 + A.every);
-        for (int64_t s = s0; s < s1; ++s) {
-            rc = record_step(t, A.dt, A.tape[(size_t)(s - s0)]);
-            if (rc) return rc;
-        }
-        for (int64_t s = s1 - 1; s >= s0; --s) {
-            rc = vjp_step(t, A.tape[(size_t)(s - s0)], s);
-            if (rc) return rc;
+    // Segments in reverse.  The handle's stream re-runs segment g - 1 into one
+    // tape set while the sweep stream sweeps segment g from the other: the
+    // sweep of g waits for its re-run, and the re-run of g - 1 waits for the
+    // sweep of g + 1, which read the set it overwrites.
+    if (!t->adj_st) {
+        bool ok = cudaStreamCreateWithFlags(&t->adj_st, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t &e : t->adj_ev)
+            ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return t->fail(CRM_ECUDA, "crm_adjoint_backward: stream or event creation failed");
         }
     }
+    cudaStream_t R = t->st, S = t->adj_st;
+    cudaEvent_t *rerun_done = t->adj_ev, *swept = t->adj_ev + 2;
+    const int64_t seg = A.every, n_seg = (n + A.every - 1) / A.every;
+    // the sweep starts after the objective's adjoints and the accumulators are set
+    CRM_CUDA(t, cudaEventRecord(swept[0], R));
+    CRM_CUDA(t, cudaStreamWaitEvent(S, swept[0], 0));
+    int rc = rerun_segment(t, n_seg - 1, (int)((n_seg - 1) % 2));
+    if (rc) return rc;
+    CRM_CUDA(t, cudaEventRecord(rerun_done[(n_seg - 1) % 2], R));
+    for (int64_t g = n_seg - 1; g >= 0; --g) {
+        const int set = (int)(g % 2);
+        const int64_t s0 = g * A.every, s1 = std::min<int64_t>(n, s0 + A.every);
+        CRM_CUDA(t, cudaStreamWaitEvent(S, rerun_done[set], 0));
+        t->st = S;
+        for (int64_t s = s1 - 1; s >= s0 && rc == CRM_OK; --s)
+            rc = vjp_step(t, A.tape[(size_t)(set * seg + (s - s0))], s);
+        t->st = R;
+        if (rc) return rc;
+        CRM_CUDA(t, cudaEventRecord(swept[set], S));
+        if (g > 0) {
+            CRM_CUDA(t, cudaStreamWaitEvent(R, swept[1 - set], 0));   // (the sweep of g + 1)
+            rc = rerun_segment(t, g - 1, 1 - set);
+            if (rc) return rc;
+            CRM_CUDA(t, cudaEventRecord(rerun_done[1 - set], R));
+        }
+    }
+    CRM_CUDA(t, cudaEventRecord(swept[0], S));
+    CRM_CUDA(t, cudaStreamWaitEvent(R, swept[0], 0));
     // leave the terrain as the forward run left it
-    int rc = crm_load_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, sb);
+    size_t sb = 0;
+    crm_state_bytes(t, &sb);
+    rc = crm_load_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, sb);
     if (rc) return rc;
     return adj_export(t, A.lb[0], g_xyz, g_vel, g_stress, g_rho, g_body, g_params);
 }
