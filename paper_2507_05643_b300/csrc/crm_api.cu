@@ -2691,6 +2691,15 @@ int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
         return e;
     };
     if (nb > 0) CRM_CUDA(t, copy(T.bodies, t->bodies, nb * sizeof(BodyDev)));
+    // the step's cell search writes its lists into the tape slot, and the stages
+    // read them there (no copy of the list table)
+    struct ListsIn {   // the terrain's own table again on every way out
+        crm_terrain *t;
+        uint32_t *nbr, *nnb;
+        ~ListsIn() { t->nbr = nbr; t->nnb = nnb; }
+    } own{t, t->nbr, t->nnb};
+    t->nbr = T.nbr;
+    t->nnb = T.nnb;
     rebuild(t);
     const int c = t->cur;
     RateOut r1{}, r2{};
@@ -2700,8 +2709,6 @@ int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
     pair(t, kStage1, t->A[c], t->A[c], (float)dt, r1);
     CRM_CUDA(t, copy_stage(T.Y0, t->A[c]));
     CRM_CUDA(t, copy(T.pid, t->pid[c], N * sizeof(uint32_t)));
-    CRM_CUDA(t, copy(T.nbr, t->nbr, (size_t)d.maxnb * d.ell * sizeof(uint32_t)));
-    CRM_CUDA(t, copy(T.nnb, t->nnb, N * sizeof(uint32_t)));
     if (nb > 0) CRM_CUDA(t, copy(T.frames, t->mid_frames, nb * sizeof(BodyFrame)));
     bce(t, t->MID, 0.5 * dt, 0);
     if (d.capM > 0 && d.n_bodies > 0) bce(t, t->MID, 0.5 * dt, 1, dt, 1);
@@ -3010,6 +3017,8 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
             CRM_CUDA(t, cudaMemcpyAsync(A.hist + (size_t)s * nb, t->bodies, nb * sizeof(BodyDev),
                                         cudaMemcpyDeviceToDevice, t->st));
     }
+    // the recorded steps' lists are in the tape, not in the terrain's own table
+    if (resident) t->lists_valid = false;
     if (!resident) {
         A.ckpt_at[(size_t)(A.n_ckpt - 1)] = {t->step_index, t->time};
         rc = crm_save_state(t, A.ckpt + (size_t)(A.n_ckpt - 1) * A.ckpt_bytes, A.ckpt_bytes, &used);
