@@ -50,11 +50,12 @@ WORKLOAD = ("wheel_bin: 120,000 SPH particles, 2.0x0.4x0.15 m bin at d0=0.01 m, 
             "phi=33 deg, c=500 Pa, dt=5e-5 s, ps_freq=1")
 # Arithmetic of one fluid-fluid or fluid-marker pair in the pair kernel, counted
 # from its source (FMA = 2): offsets 6, r^2 5, rsqrt/scale 3, dW/dr 5, V_j 1,
-# f V_j 1, V_j grad W 3, u_ji 3, continuity 6, stress sums 6, momentum 18,
-# velocity gradient 18, artificial viscosity 18 => 93; per particle: stress
-# rate, update and return map ~100.
-FLOP_PER_PAIR = 93
-FLOP_PER_PARTICLE = 100
+# f V_j 1, V_j grad W 3, u_ji 3, sum of V_j grad W 3, sigma_j . V_j grad W 18,
+# velocity gradient 18 (continuity is its trace), artificial viscosity 18 => 84;
+# per particle: sigma_i . sum V_j grad W and the trace 20, stress rate, update
+# and return map ~100 => 120.
+FLOP_PER_PAIR = 84
+FLOP_PER_PARTICLE = 120
 SM_FP32_LANES = 128
 BODY_BYTES = 352   # one body's device record, copied out by the exchange
 

@@ -388,8 +388,35 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     if (*p.abort) return;
     __shared__ double red[kBlock / 32][6];
     __shared__ unsigned s_bodies;
-    bce_block<ACCEL, FILTER, LANES>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau,
-                                    n_fluid_total, mforce, bs, blockIdx.x, red, s_bodies);
+    if constexpr (ACCEL == 1) {   // one partial per block: one block per virtual block
+        bce_block<ACCEL, FILTER, LANES>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act,
+                                        tau, n_fluid_total, mforce, bs, blockIdx.x, red, s_bodies);
+        return;
+    }
+    // the state passes: a grid of at most one wave takes the virtual blocks that
+    // hold markers in turn (block 0 always runs: it writes the midpoint frames)
+    const int live = act != nullptr ? __ldg(n_act) : __ldg(p.sizes + 2) - __ldg(p.sizes);
+    const int nvb = max(1, (int)(((int64_t)live * LANES + kBlock - 1) / kBlock));
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
+        bce_block<ACCEL, FILTER, LANES>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act,
+                                        tau, n_fluid_total, mforce, bs, vb, red, s_bodies);
+}
+
+// Grid of a state pass: the blocks the markers need, at most one wave of the
+// kernel's resident blocks.
+template <int ACCEL, bool FILTER>
+unsigned bce_state_grid(const DevParams &p)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bce<ACCEL, FILTER>, kBlock, 0)
+                != cudaSuccess
+            || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+    }
+    return (unsigned)std::min<int64_t>(bce_blocks(p), (int64_t)std::max(p.n_sm, 1) * per_sm);
 }
 
 // The soil wrench of body b = blockIdx.x (Sec. 2.4): the sum of the wrench
@@ -595,22 +622,21 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
     BodyStep bs{partial, bodies, dt, integrate, gate};
     if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_bce<0, true><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
-                                                         act, n_act, tau, n_fluid_total, mforce,
-                                                         bs);
+        k_bce<0, true><<<bce_state_grid<0, true>(p), kBlock, 0, st>>>(
+            p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (accel == 0) {
-        k_bce<0, false><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
-                                                          act, n_act, tau, n_fluid_total, mforce, bs);
+        k_bce<0, false><<<bce_state_grid<0, false>(p), kBlock, 0, st>>>(
+            p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
     } else if (accel == 1) {
         k_bce<1, false, kWrenchLanes><<<wrench_blocks(body_markers), kBlock, 0, st>>>(
             p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
         k_body_reduce<<<(unsigned)std::max(p.n_bodies, 1), 32, 0, st>>>(p, bs, n_act);
     } else {
-        k_bce<2, false><<<bce_blocks(p), kBlock, 0, st>>>(p, S, home_pos, pid, mloc, bodies, frames, L,
-                                                          act, n_act, tau, n_fluid_total, mforce, bs);
+        k_bce<2, false><<<bce_state_grid<2, false>(p), kBlock, 0, st>>>(
+            p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
     }
 }
 

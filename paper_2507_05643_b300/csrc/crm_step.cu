@@ -91,9 +91,13 @@ __device__ __forceinline__ void return_map(float s[6], const float sn[6], const 
 constexpr int kPairBlock = 128;   // pair kernels: blocks of 128 threads
 constexpr int kPairLanes = 2;     // lanes per fluid particle in the pair kernels
 
-// Running sums of one particle's pairs.
+// Running sums of one particle's pairs.  The momentum sum of Eq. momentum_dis,
+// sum_j V_j (sigma_i + sigma_j) . grad_i W_ij, is kept as sum_j sigma_j . (V_j
+// grad_i W_ij) (mx, my, mz) and G = sum_j V_j grad_i W_ij, so that sigma_i . G is
+// added once per particle; the continuity sum sum_j V_j u_ji . grad_i W_ij is the
+// trace of the velocity-gradient sum L.
 struct PairAcc {
-    float cont, mx, my, mz, avx, avy, avz;
+    float mx, my, mz, Gx, Gy, Gz, avx, avy, avz;
     float L[9];
 };
 
@@ -126,15 +130,12 @@ __device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi,
     const float fv = f * Vj;
     const float gx = fv * rx, gy = fv * ry, gz = fv * rz;       // V_j grad_i W_ij
     const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;   // u_ji
-    // continuity (F2)
-    A.cont = fmaf(ux, gx, fmaf(uy, gy, fmaf(uz, gz, A.cont)));
-    // momentum (F3): (sigma_i + sigma_j) . grad W
-    const float sxx = ai.x + aj.x, syy = ai.y + aj.y, szz = ai.z + aj.z;
-    const float sxy = ai.w + aj.w, sxz = bi.x + bj.x, syz = bi.y + bj.y;
-    A.mx = fmaf(sxx, gx, fmaf(sxy, gy, fmaf(sxz, gz, A.mx)));
-    A.my = fmaf(sxy, gx, fmaf(syy, gy, fmaf(syz, gz, A.my)));
-    A.mz = fmaf(sxz, gx, fmaf(syz, gy, fmaf(szz, gz, A.mz)));
-    // velocity gradient (F2): L += u_ji (x) V_j grad W
+    // momentum (F3): sigma_j . grad W here, sigma_i . sum grad W in the epilogue
+    A.Gx += gx; A.Gy += gy; A.Gz += gz;
+    A.mx = fmaf(aj.x, gx, fmaf(aj.w, gy, fmaf(bj.x, gz, A.mx)));
+    A.my = fmaf(aj.w, gx, fmaf(aj.y, gy, fmaf(bj.y, gz, A.my)));
+    A.mz = fmaf(bj.x, gx, fmaf(bj.y, gy, fmaf(aj.z, gz, A.mz)));
+    // velocity gradient (F2): L += u_ji (x) V_j grad W; continuity (F2) is its trace
     A.L[0] = fmaf(ux, gx, A.L[0]); A.L[1] = fmaf(ux, gy, A.L[1]); A.L[2] = fmaf(ux, gz, A.L[2]);
     A.L[3] = fmaf(uy, gx, A.L[3]); A.L[4] = fmaf(uy, gy, A.L[4]); A.L[5] = fmaf(uy, gz, A.L[5]);
     A.L[6] = fmaf(uz, gx, A.L[6]); A.L[7] = fmaf(uz, gy, A.L[7]); A.L[8] = fmaf(uz, gz, A.L[8]);
@@ -163,21 +164,25 @@ __device__ __forceinline__ void stage_epilogue(const DevParams &p, int i, const 
                                                const float4 *__restrict__ xref,
                                                int *__restrict__ gate)
 {
+    const float si[6] = {ai.x, ai.y, ai.z, ai.w, bi.x, bi.y};
+    const float cont = A.L[0] + A.L[4] + A.L[8];
+    const float mx = fmaf(si[0], A.Gx, fmaf(si[3], A.Gy, fmaf(si[4], A.Gz, A.mx)));
+    const float my = fmaf(si[3], A.Gx, fmaf(si[1], A.Gy, fmaf(si[5], A.Gz, A.my)));
+    const float mz = fmaf(si[4], A.Gx, fmaf(si[5], A.Gy, fmaf(si[2], A.Gz, A.mz)));
     if (out.sums != nullptr) {
         const size_t cs = (size_t)p.capF;
-        out.sums[i] = A.cont;
-        out.sums[cs + i] = A.mx;
-        out.sums[2 * cs + i] = A.my;
-        out.sums[3 * cs + i] = A.mz;
+        out.sums[i] = cont;
+        out.sums[cs + i] = mx;
+        out.sums[2 * cs + i] = my;
+        out.sums[3 * cs + i] = mz;
 #pragma unroll
         for (int k = 0; k < 9; ++k) out.sums[(4 + k) * cs + i] = A.L[k];
     }
     const float rinv_i = 1.0f / vi.w;
-    const float drho = -vi.w * A.cont;
-    const float dux = A.mx * rinv_i + p.gx + A.avx;
-    const float duy = A.my * rinv_i + p.gy + A.avy;
-    const float duz = A.mz * rinv_i + p.gz + A.avz;
-    const float si[6] = {ai.x, ai.y, ai.z, ai.w, bi.x, bi.y};
+    const float drho = -vi.w * cont;
+    const float dux = mx * rinv_i + p.gx + A.avx;
+    const float duy = my * rinv_i + p.gy + A.avy;
+    const float duz = mz * rinv_i + p.gz + A.avz;
     float ds[6];
     stress_rate(A.L, si, p.G, p.K, ds);
     if (MODE == kEval) {
@@ -269,7 +274,7 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
     const float4 ai = adv ? S.sA[i] : z4;
     const float2 bi = adv ? S.sB[i] : make_float2(0.f, 0.f);
     PairAcc A;
-    A.cont = A.mx = A.my = A.mz = A.avx = A.avy = A.avz = 0.f;
+    A.mx = A.my = A.mz = A.Gx = A.Gy = A.Gz = A.avx = A.avy = A.avz = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) A.L[k] = 0.f;
     const int nn = adv ? (int)io.in_n[i] : 0;
@@ -336,8 +341,10 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
     if (LANES > 1) {
 #pragma unroll
         for (int o = 1; o < LANES; o <<= 1) {
-            A.cont += __shfl_xor_sync(0xffffffffu, A.cont, o);
             A.mx += __shfl_xor_sync(0xffffffffu, A.mx, o);
+            A.Gx += __shfl_xor_sync(0xffffffffu, A.Gx, o);
+            A.Gy += __shfl_xor_sync(0xffffffffu, A.Gy, o);
+            A.Gz += __shfl_xor_sync(0xffffffffu, A.Gz, o);
             A.my += __shfl_xor_sync(0xffffffffu, A.my, o);
             A.mz += __shfl_xor_sync(0xffffffffu, A.mz, o);
             A.avx += __shfl_xor_sync(0xffffffffu, A.avx, o);
