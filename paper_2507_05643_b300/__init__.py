@@ -176,6 +176,15 @@ def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
+def _f64_rows(a, n: int, k: int):
+    """a as a C-contiguous float64 (n, k) array (itself when it already is one)."""
+    if a is None:
+        return None
+    if type(a) is np.ndarray and a.dtype == np.float64 and a.flags.c_contiguous and a.size == n * k:
+        return a
+    return np.ascontiguousarray(np.asarray(a, np.float64).reshape(n, k))
+
+
 def _c(a, dtype=np.float64):
     return np.ascontiguousarray(a, dtype=dtype)
 
@@ -224,6 +233,7 @@ class Terrain:
         self.n_sph = 0
         self.n_markers = 0
         self.n_bodies = 0
+        self._addrs = {}
 
     # ------------------------------------------------------------------
     def _check(self, rc: int):
@@ -317,21 +327,34 @@ class Terrain:
         (wrench, pose, twist) float64 arrays of those shapes to fill (no
         allocation per call)."""
         nb = self.n_bodies
-
-        def arr(a, k):
-            if a is None:
-                return None
-            if isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous \
-                    and a.size == nb * k:
-                return a
-            return np.ascontiguousarray(np.asarray(a, np.float64).reshape(nb, k))
-        pin, tin = arr(pose, 7), arr(twist, 6)
+        pin, tin = _f64_rows(pose, nb, 7), _f64_rows(twist, nb, 6)
         if out is None:
             out = (np.zeros((nb, 6)), np.zeros((nb, 7)), np.zeros((nb, 6)))
         w, q, v = out
-        self._check(_lib.crm_cosim_step(self._h, _ptr(pin), _ptr(tin), float(dt), int(n_steps),
-                                        _ptr(w), _ptr(q), _ptr(v)))
+        for a, k in ((w, 6), (q, 7), (v, 6)):
+            if not (type(a) is np.ndarray and a.dtype == np.float64 and a.flags.c_contiguous
+                    and a.size == nb * k):
+                raise ValueError("cosim_step: out holds C-contiguous float64 arrays of "
+                                 "(n_bodies, 6), (n_bodies, 7), (n_bodies, 6)")
+        ad = self._addr
+        rc = _lib.crm_cosim_step(self._h, ad(pin), ad(tin), dt, n_steps, ad(w), ad(q), ad(v))
+        if rc != CRM_OK:
+            self._check(rc)
         return w, q, v
+
+    def _addr(self, a):
+        """Data address of array a (None for None), remembered for the arrays a
+        caller passes at every exchange."""
+        if a is None:
+            return None
+        c = self._addrs.get(id(a))
+        if c is not None and c[0] is a:
+            return c[1]
+        if len(self._addrs) > 16:
+            self._addrs.clear()
+        addr = a.ctypes.data
+        self._addrs[id(a)] = (a, addr)
+        return addr
 
     def body_wrench(self, body: int) -> Tuple[np.ndarray, np.ndarray]:
         f, t = np.zeros(3), np.zeros(3)

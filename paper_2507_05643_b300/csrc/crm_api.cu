@@ -78,13 +78,18 @@ struct crm_terrain {
     // a step with / without the Alg. 2 rebuild, one per current buffer (a graph
     // bakes in the buffer pointers; a search without a skin swaps the buffers)
     StepGraph g_search[2], g_plain[2];
+    // the same steps with the co-simulation exchange (crm_cosim_step) inside the
+    // graph: the bodies' new motion from pinned staging before, their state and
+    // the error word back to it after
+    StepGraph x_search[2], x_plain[2];
     unsigned long long *step_ctr = nullptr;   // active domains: device step index (abort tag)
     void drop_graphs()
     {
         for (int b = 0; b < 2; ++b) {
-            if (g_search[b].exec) cudaGraphExecDestroy(g_search[b].exec);
-            if (g_plain[b].exec) cudaGraphExecDestroy(g_plain[b].exec);
-            g_search[b].exec = g_plain[b].exec = nullptr;
+            for (StepGraph *G : {&g_search[b], &g_plain[b], &x_search[b], &x_plain[b]}) {
+                if (G->exec) cudaGraphExecDestroy(G->exec);
+                G->exec = nullptr;
+            }
         }
     }
     cudaStream_t cap_st = nullptr;   // private stream the graphs are captured on
@@ -1046,9 +1051,30 @@ void one_step(crm_terrain *t, double dt)
     t->prof.steps += 1;
 }
 
+// The co-simulation exchange of crm_cosim_step as stream work: the bodies' new
+// pose and twist from the pinned staging (before a step), or every body's state
+// and the error word back to it (after).
+void exchange_in(crm_terrain *t)
+{
+    for (size_t b = 0; b < t->hbodies.size(); ++b)
+        cudaMemcpyAsync(&t->bodies[b], &t->h_xbodies[b], 13 * sizeof(double), cudaMemcpyHostToDevice,
+                        t->st);
+}
+
+void exchange_out(crm_terrain *t)
+{
+    const size_t nb = t->hbodies.size();
+    if (nb > 0)
+        cudaMemcpyAsync(t->h_xbodies, t->bodies, nb * sizeof(BodyDev), cudaMemcpyDeviceToHost, t->st);
+    cudaMemcpyAsync((int *)(t->h_xbodies + std::max<size_t>(nb, 1)), t->err, sizeof(int),
+                    cudaMemcpyDeviceToHost, t->st);
+}
+
 // Capture one step into an executable graph: with the skin, the decision
-// kernel switches a conditional node around the cell sort and search.
-int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph &G)
+// kernel switches a conditional node around the cell sort and search.  With
+// `exchange` the graph also holds the co-simulation exchange around the step.
+int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph &G,
+                 bool exchange = false)
 {
     if (G.exec) {
         cudaGraphExecDestroy(G.exec);
@@ -1067,15 +1093,21 @@ int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph 
     if (e == cudaSuccess && search && t->skin_on) {
         cudaGraphConditionalHandle h;
         e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        cudaGraphNode_t dec = nullptr, cn = nullptr;
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(t->st, g, nullptr, nullptr, 0, mode);
         if (e == cudaSuccess) {
+            if (exchange) exchange_in(t);
             launch_decide(d, t->gate, (unsigned long long)h, 1, t->st,
                           t->active ? t->counts : nullptr);
-            e = cudaStreamEndCapture(t->st, &g);
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            e = cudaStreamGetCaptureInfo(t->st, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+            if (e == cudaSuccess && nd == 1) dec = deps[0];   // the decision kernel
+            const cudaError_t e2 = cudaStreamEndCapture(t->st, &g);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess && dec == nullptr) e = cudaErrorUnknown;
         }
-        cudaGraphNode_t dec = nullptr, cn = nullptr;
-        size_t nn = 1;
-        if (e == cudaSuccess) e = cudaGraphGetNodes(g, &dec, &nn);
         cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = h;
@@ -1094,17 +1126,20 @@ int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph 
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(t->st, g, &cn, nullptr, 1, mode);
         if (e == cudaSuccess) {
             enqueue_stages(t, dt, true);
+            if (exchange) exchange_out(t);
             e = cudaStreamEndCapture(t->st, &g);
         }
     } else if (e == cudaSuccess) {
         e = cudaStreamBeginCaptureToGraph(t->st, g, nullptr, nullptr, 0, mode);
         if (e == cudaSuccess) {
+            if (exchange) exchange_in(t);
             if (search) {
                 if (t->active) activity_pass(t);
                 enqueue_search(t);
                 t->cur = 1 - t->cur;
             }
             enqueue_stages(t, dt, false);
+            if (exchange) exchange_out(t);
             e = cudaStreamEndCapture(t->st, &g);
         }
     }
@@ -1123,17 +1158,21 @@ int capture_step(crm_terrain *t, double dt, bool search, crm_terrain::StepGraph 
     return CRM_OK;
 }
 
-// One step by graph replay (same kernels as one_step).
-int graph_step(crm_terrain *t, double dt)
+// One step by graph replay (same kernels as one_step); with `exchange` the
+// graph that holds the co-simulation exchange too (crm_cosim_step).
+int graph_step(crm_terrain *t, double dt, bool exchange = false)
 {
     const bool search = !t->lists_valid || t->step_index % t->P.ps_freq == 0;
-    crm_terrain::StepGraph &G = search ? t->g_search[t->cur] : t->g_plain[t->cur];
+    crm_terrain::StepGraph &G = exchange ? (search ? t->x_search[t->cur] : t->x_plain[t->cur])
+                                         : (search ? t->g_search[t->cur] : t->g_plain[t->cur]);
     if (!G.exec || G.dt != dt) {
-        if (capture_step(t, dt, search, G) != CRM_OK) {
+        if (capture_step(t, dt, search, G, exchange) != CRM_OK) {
             // no graph on this device / driver: direct launches from now on
             t->graphs = false;
             t->msg.clear();
+            if (exchange) exchange_in(t);
             one_step(t, dt);
+            if (exchange) exchange_out(t);
             CRM_CUDA(t, cudaGetLastError());
             return CRM_OK;
         }
@@ -1673,21 +1712,24 @@ int crm_cosim_step(crm_terrain *t, const double *pose_in, const double *twist_in
         t->h_xbodies = (BodyDev *)h;
     }
     int *h_err = (int *)(t->h_xbodies + std::max(nb, 1));
-    if (pose_in) {
-        // the new motions through pinned memory: truly asynchronous uploads
-        for (int b = 0; b < nb; ++b) {
+    if (pose_in)   // the new motions through pinned memory: truly asynchronous uploads
+        for (int b = 0; b < nb; ++b)
             std::memcpy(t->h_xbodies[b].pose, t->hbodies[b].pose, 13 * sizeof(double));
-            CRM_CUDA(t, cudaMemcpyAsync(&t->bodies[b], &t->h_xbodies[b], 13 * sizeof(double),
-                                        cudaMemcpyHostToDevice, t->st));
-        }
-    }
-    if (n_steps > 0) {
-        rc = crm_step(t, dt, n_steps);
+    if (n_steps == 1 && pose_in && !t->active && t->graphs && !t->timing && t->cap_st
+        && t->dp.capN > 0) {
+        // one exchange step: upload, step and read-back replayed as one graph
+        if (!(dt > 0) || !std::isfinite(dt)) return t->fail(CRM_EINVAL, "crm_cosim_step: dt > 0");
+        rc = graph_step(t, dt, true);
         if (rc) return rc;
+    } else {
+        if (pose_in) exchange_in(t);
+        if (n_steps > 0) {
+            rc = crm_step(t, dt, n_steps);
+            if (rc) return rc;
+        }
+        exchange_out(t);
     }
-    if (nb > 0)
-        CRM_CUDA(t, cudaMemcpyAsync(t->h_xbodies, t->bodies, nb * sizeof(BodyDev), cudaMemcpyDeviceToHost, t->st));
-    CRM_CUDA(t, cudaMemcpyAsync(h_err, t->err, sizeof(int), cudaMemcpyDeviceToHost, t->st));
+    CRM_CUDA(t, cudaGetLastError());
     CRM_CUDA(t, cudaStreamSynchronize(t->st));
     if (*h_err != 0) return latched_error(t);
     for (int b = 0; b < nb; ++b) {

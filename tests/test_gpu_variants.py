@@ -473,6 +473,22 @@ def test_cosim_exchange_equals_the_separate_calls():
         np.testing.assert_array_equal(W[0], np.concatenate([f, tq]))
         np.testing.assert_array_equal(P[0], p1)
         np.testing.assert_array_equal(V[0], v1)
+    # one step per exchange: upload, step and read-back replayed as one graph
+    out = (np.zeros((1, 6)), np.zeros((1, 7)), np.zeros((1, 6)))
+    for k in range(6):
+        pose, twist = t1.body_state(0)
+        twist = twist.copy()
+        twist[5] += 0.02 * k           # a new prescribed spin each exchange
+        t1.set_body_motion(0, pose, twist)
+        t1.step(dt, 1)
+        f, tq = t1.body_wrench(0)
+        p1, v1 = t1.body_state(0)
+        W, P, V = t2.cosim_step(dt, 1, pose[None], twist[None], out=out)
+        np.testing.assert_array_equal(W[0], np.concatenate([f, tq]))
+        np.testing.assert_array_equal(P[0], p1)
+        np.testing.assert_array_equal(V[0], v1)
+    for a, b in zip(t1.particles(), t2.particles()):
+        np.testing.assert_array_equal(a, b)
     # no motion given and no steps: the state as it stands
     W, P, V = t2.cosim_step(dt, 0)
     np.testing.assert_array_equal(P[0], t1.body_state(0)[0])
