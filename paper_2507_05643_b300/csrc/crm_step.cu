@@ -113,7 +113,9 @@ __device__ __forceinline__ void pair_terms(const DevParams &p, const float4 &vi,
                                            float r2, PairAcc &A)
 {
     constexpr int KER = KAV / 3, AV = KAV % 3;
-    const float rinv = rsqrtf(r2);
+    // (a pair at r = 0 -- two particles at one point -- adds nothing: r = 0 makes
+    // every term vanish once 1/r is kept finite)
+    const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
     const float q = r2 * rinv * p.inv_h;
     float f;
     if (KER == CRM_KERNEL_WENDLAND) {
@@ -285,9 +287,12 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
     if (!FILTER || LANES == 1) {
         // on an exact list the neighbour's whole state is gathered at once (one
         // load round per iteration); on a skin list the rest follows the distance test
-        for (int k = q; k < nn; k += LANES) {
+        const size_t step = (size_t)LANES * p.ell;
+        const uint32_t *nxt = row + (size_t)(q + LANES) * p.ell;   // entry k + LANES
+        uint32_t *out = FILTER ? io.out + i : nullptr;                // exact entry cnt
+        for (int k = q; k < nn; k += LANES, nxt += step) {
             const uint32_t e = e_nx;
-            if (k + LANES < nn) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
+            if (k + LANES < nn) e_nx = ld_list(nxt);
             const uint32_t j = e & kIndexMask;
             const float3 sh = entry_shift(e, p.cell);
             const float4 pj = __ldg(&S.pos[j]);
@@ -300,10 +305,12 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
             const float r2 = rx * rx + ry * ry + rz * rz;
             if (!(r2 < p.four_h2)) continue;
             if (FILTER) {
-                if (cnt < p.maxnb) io.out[(size_t)cnt * p.ell + i] = e;
+                if (cnt < p.maxnb) {
+                    *out = e;
+                    out += p.ell;
+                }
                 ++cnt;
             }
-            if (r2 == 0.0f) continue;
             pair_terms<KAV>(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
         }
     } else {
@@ -331,7 +338,7 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
             const int at = cnt + __popc(g & ((1u << q) - 1u));
             if (keep && at < p.maxnb) io.out[(size_t)at * p.ell + i] = e;
             cnt += __popc(g);
-            if (!keep || r2 == 0.0f) continue;
+            if (!keep) continue;
             const float4 vj = __ldg(&S.vel[j]);
             const float4 aj = __ldg(&S.sA[j]);
             const float2 bj = __ldg(&S.sB[j]);
