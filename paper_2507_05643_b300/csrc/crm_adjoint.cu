@@ -662,15 +662,29 @@ __device__ __forceinline__ int marker_body_kin(const DevParams &p, const AdjStag
 // adjoints (their coefficients are formed here and stored for pass 3).  Writes
 // the BCE coefficients of every marker slot and adds the body adjoints (centre,
 // velocity, acceleration) to gbody [body][9].
+// act (nullable): the marker slots that have fluid in reach, n_act[0] of them;
+// the others add nothing and their coefficients are never read (a fluid
+// particle lists a marker exactly when the marker lists it), so a launch given
+// act serves those markers only.
 template <bool ACC, int LANES>
 __global__ void __launch_bounds__(kAdjBlock)
-k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody)
+k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody,
+             const uint32_t *__restrict__ act, const int *__restrict__ n_act)
 {
-    __syncthreads();
     const Sizes z = load_sizes(p);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = z.nF + t / LANES, q = t % LANES;
-    const bool valid = s < z.N;
+    int s;
+    bool valid;
+    if (act != nullptr) {
+        const int na = __ldg(n_act);
+        if ((int)(blockIdx.x * blockDim.x / LANES) >= na) return;   // block-uniform
+        valid = t / LANES < na;
+        s = valid ? (int)__ldg(act + t / LANES) : z.N;
+    } else {
+        s = z.nF + t / LANES;
+        valid = s < z.N;
+    }
+    const int q = t % LANES;
     ParAcc par;
     par_zero(par);
     const int nn = valid ? (int)V.nnb[s] : 0;
@@ -1211,13 +1225,14 @@ void launch_adj_fluid_coef(int mode, const DevParams &p, const AdjStage &V, Stag
 }
 
 void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const AdjIO &io,
-                       double *gpar, double *gbody, cudaStream_t st)
+                       double *gpar, double *gbody, cudaStream_t st, const uint32_t *act,
+                       const int *n_act)
 {
     if (p.capM == 0) return;
     constexpr int LN = kAdjLanes;
     const unsigned g = grid_for((int64_t)p.capM * LN, kAdjBlock);
-    if (acc) k_adj_marker<true, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
-    else k_adj_marker<false, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody);
+    if (acc) k_adj_marker<true, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody, act, n_act);
+    else k_adj_marker<false, LN><<<g, kAdjBlock, 0, st>>>(p, V, io, gpar, gbody, act, n_act);
 }
 
 void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, const AdjIO &io,

@@ -57,8 +57,10 @@ struct AdjIO {
 
 void launch_adj_fluid_coef(int mode, const DevParams &p, const AdjStage &V, StageArrays Y0,
                            const AdjIO &io, double *gpar, cudaStream_t st);
+// act / n_act (nullable): the markers with fluid in reach (every marker slot when null)
 void launch_adj_marker(bool acc, const DevParams &p, const AdjStage &V, const AdjIO &io,
-                       double *gpar, double *gbody, cudaStream_t st);
+                       double *gpar, double *gbody, cudaStream_t st,
+                       const uint32_t *act = nullptr, const int *n_act = nullptr);
 void launch_adj_fluid(bool acc, int out, const DevParams &p, const AdjStage &V, const AdjIO &io,
                       float *l_acc, float *l_final, double *gpar, cudaStream_t st);
 void launch_adj_body_pre(int nb, const BodyDev *bodies, const BodyDev *after, double dt,

@@ -139,6 +139,8 @@ struct crm_terrain {
     struct AdjTape {
         StageArrays Y0, YM;          // slot arrays at y_n and y_mid (markers with their state)
         uint32_t *pid, *nbr, *nnb;   // slot order and lists of the step
+        uint32_t *act, *act_body;    // the step's markers with fluid in reach (all, on bodies)
+        int *n_act;                  // [2]: their counts
         BodyDev *bodies;             // bodies before the step
         BodyFrame *frames;           // bodies at the step midpoint
         BodyDev *after;              // bodies after the step (its wrench, the updated rates)
@@ -2733,15 +2735,24 @@ int enqueue_record(crm_terrain *t, double dt, crm_terrain::AdjTape &T)
         return e;
     };
     if (nb > 0) CRM_CUDA(t, copy(T.bodies, t->bodies, nb * sizeof(BodyDev)));
-    // the step's cell search writes its lists into the tape slot, and the stages
-    // read them there (no copy of the list table)
-    struct ListsIn {   // the terrain's own table again on every way out
+    // the step's cell search writes its lists and its compaction of the markers
+    // with fluid in reach into the tape slot, and the stages read them there (no
+    // copy of the list table)
+    struct ListsIn {   // the terrain's own tables again on every way out
         crm_terrain *t;
-        uint32_t *nbr, *nnb;
-        ~ListsIn() { t->nbr = nbr; t->nnb = nnb; }
-    } own{t, t->nbr, t->nnb};
+        uint32_t *nbr, *nnb, *act, *act_body;
+        int *n_act;
+        ~ListsIn()
+        {
+            t->nbr = nbr; t->nnb = nnb;
+            t->act = act; t->act_body = act_body; t->n_act = n_act;
+        }
+    } own{t, t->nbr, t->nnb, t->act, t->act_body, t->n_act};
     t->nbr = T.nbr;
     t->nnb = T.nnb;
+    t->act = T.act;
+    t->act_body = T.act_body;
+    t->n_act = T.n_act;
     rebuild(t);
     const int c = t->cur;
     RateOut r1{}, r2{};
@@ -2835,12 +2846,12 @@ int vjp_step(crm_terrain *t, const crm_terrain::AdjTape &T, int64_t s)
     // stage 2 (at y_mid, with the wrench's marker accelerations)
     launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjStage2, d, Vm, T.Y0, io, A.gpar, t->st); });
     const bool acc = nb > 0 && d.capM > 0;
-    launch(t, K_ADJ, [&] { launch_adj_marker(acc, d, Vm, io, A.gpar, gm, t->st); });
+    launch(t, K_ADJ, [&] { launch_adj_marker(acc, d, Vm, io, A.gpar, gm, t->st, T.act, T.n_act); });
     launch(t, K_ADJ, [&] { launch_adj_fluid(acc, kAdjAccumulate, d, Vm, io, A.l_mid, nullptr,
                                             A.gpar, t->st); });
     // stage 1 (at y_n)
     launch(t, K_ADJ, [&] { launch_adj_fluid_coef(kAdjStage1, d, V0, T.Y0, io, A.gpar, t->st); });
-    launch(t, K_ADJ, [&] { launch_adj_marker(false, d, V0, io, A.gpar, g0, t->st); });
+    launch(t, K_ADJ, [&] { launch_adj_marker(false, d, V0, io, A.gpar, g0, t->st, T.act, T.n_act); });
     launch(t, K_ADJ, [&] { launch_adj_fluid(false, kAdjFinal, d, V0, io, A.l_y0, A.l_ins, A.gpar,
                                             t->st); });
     if (nb > 0) {
@@ -3021,6 +3032,9 @@ int crm_adjoint_forward(crm_terrain *t, double dt, int64_t n_steps, int32_t ever
         T.pid = t->dalloc<uint32_t>(G_TAPE, N);
         T.nbr = t->dalloc<uint32_t>(G_TAPE, (size_t)d.maxnb * d.ell);
         T.nnb = t->dalloc<uint32_t>(G_TAPE, N);
+        T.act = t->dalloc<uint32_t>(G_TAPE, std::max<size_t>(d.capM, 1));
+        T.act_body = t->dalloc<uint32_t>(G_TAPE, std::max(t->n_bodym, 1));
+        T.n_act = t->dalloc<int>(G_TAPE, 2);
         T.bodies = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1));
         T.frames = t->dalloc<BodyFrame>(G_TAPE, std::max<size_t>(nb, 1));
         T.after = t->dalloc<BodyDev>(G_TAPE, std::max<size_t>(nb, 1));
