@@ -497,6 +497,10 @@ k_batch_bce(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
             }
             if (*M.p.abort) continue;
             const int vb = it - __ldg(off + k);
+            // the state passes: virtual blocks past the member's markers with fluid in
+            // reach hold none (block 0 still runs: it writes the midpoint frames)
+            if (KIND != 2 && vb > 0 && (int64_t)vb * kBlock >= (int64_t)*M.n_act * kBceLanes)
+                continue;
             __syncthreads();   // the previous virtual block's readers of red are done
             if (KIND == 0) {
                 const ListIO L{M.sk_nbr, M.sk_nnb, M.nbr, M.nnb, M.err};
