@@ -735,11 +735,13 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody,
         const uint32_t e = V.nbr[(size_t)k * p.ell + s];
         const uint32_t f = e & kIndexMask;
         const float3 sh = entry_shift(e, p.cell);
+        // the fluid particle's position, state and pair coefficients in one load round
         const float4 pf = S.pos[f];
+        const PState Fs = load_state(S, f);
+        const Coef Cf = load_coef(io.coef, (int)f);
         const float rx = pa.x - pf.x - sh.x, ry = pa.y - pf.y - sh.y, rz = pa.z - pf.z - sh.z;
         const float r2 = rx * rx + ry * ry + rz * rz;
         if (!(r2 < p.four_h2)) continue;
-        const PState Fs = load_state(S, f);
         const float W = kernel_w(sqrtf(r2) * p.inv_h, p);
         w += W;
         su[0] += Fs.v.x * W; su[1] += Fs.v.y * W; su[2] += Fs.v.z * W;
@@ -770,7 +772,6 @@ k_adj_marker(DevParams p, AdjStage V, AdjIO io, double *gpar, double *gbody,
         }
         // the marker's own acceleration pair (ACC) and the fluid particle's pair
         // that reads this marker
-        const Coef Cf = load_coef(io.coef, (int)f);
         pair_vjp_both<ACC, true>(p, Ca, Cf, rx, ry, rz, r2, A0, Fs, la, par);
     }
     if (ACC) {
@@ -978,17 +979,20 @@ k_adj_fluid(DevParams p, AdjStage V, AdjIO io, float *l_acc, float *l_final, dou
             const uint32_t e = V.nbr[(size_t)k * p.ell + i];
             const uint32_t j = e & kIndexMask;
             const float3 sh = entry_shift(e, p.cell);
+            // the neighbour's position, state and pair coefficients in one load round
+            // (the list holds the pairs within 2h at y_n: nearly all pass the test)
             const float4 pj = S.pos[j];
+            const PState J = load_state(S, j);
+            const bool marker = (int)j >= z.nF;
+            Coef Cj;
+            if (!marker || ACC) Cj = load_coef(io.coef, (int)j);
             const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
             const float r2 = rx * rx + ry * ry + rz * rz;
             if (!(r2 < p.four_h2)) continue;
-            const PState J = load_state(S, j);
-            const bool marker = (int)j >= z.nF;
             if (r2 != 0.0f) {
                 // own pair (i target) and the neighbour's pair that reads i (j
                 // target; a marker's only with acceleration adjoints)
                 if (!marker || ACC) {
-                    const Coef Cj = load_coef(io.coef, (int)j);
                     pair_vjp_both<true, true>(p, Ci, Cj, rx, ry, rz, r2, I, J, a, par);
                 } else {
                     pair_vjp_both<true, false>(p, Ci, Ci, rx, ry, rz, r2, I, J, a, par);
