@@ -171,7 +171,7 @@ __device__ __forceinline__ void block_wrench_partial(const DevParams &p, const f
 
 // The work of block vb of a k_bce launch (a kBlock-thread block; every thread
 // of the block calls it; red and s_bodies are the block's shared arrays).
-template <int ACCEL, bool FILTER, int LANES>
+template <int ACCEL, bool FILTER, int LANES, int BS = kBlock>
 __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
                                           const float4 *__restrict__ home_pos,
                                           const uint32_t *__restrict__ pid,
@@ -192,7 +192,7 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
     if (threadIdx.x == 0) s_bodies = 0u;
     __syncthreads();
     const Sizes z = load_sizes(p);
-    const int t = vb * kBlock + threadIdx.x;
+    const int t = vb * BS + threadIdx.x;
     const int q = t & (LANES - 1);           // lane within the marker's group
     int s;
     bool valid;
@@ -377,8 +377,8 @@ __device__ __forceinline__ void bce_block(const DevParams &p, StageArrays S,
     }
 }
 
-template <int ACCEL, bool FILTER, int LANES = kBceLanes>
-__global__ void __launch_bounds__(kBlock)
+template <int ACCEL, bool FILTER, int LANES = kBceLanes, int BS = kBlock>
+__global__ void __launch_bounds__(BS)
 k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
       const uint32_t *__restrict__ pid, const double *__restrict__ mloc,
       const BodyDev *bodies, BodyFrame *frames, ListIO L, const uint32_t *__restrict__ act,
@@ -396,11 +396,15 @@ k_bce(DevParams p, StageArrays S, const float4 *__restrict__ home_pos,
     // the state passes: a grid of at most one wave takes the virtual blocks that
     // hold markers in turn (block 0 always runs: it writes the midpoint frames)
     const int live = act != nullptr ? __ldg(n_act) : __ldg(p.sizes + 2) - __ldg(p.sizes);
-    const int nvb = max(1, (int)(((int64_t)live * LANES + kBlock - 1) / kBlock));
+    const int nvb = max(1, (int)(((int64_t)live * LANES + BS - 1) / BS));
     for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x)
-        bce_block<ACCEL, FILTER, LANES>(p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act,
-                                        tau, n_fluid_total, mforce, bs, vb, red, s_bodies);
+        bce_block<ACCEL, FILTER, LANES, BS>(p, S, home_pos, pid, mloc, bodies, frames, L, act,
+                                            n_act, tau, n_fluid_total, mforce, bs, vb, red, s_bodies);
 }
+
+// The state passes run in blocks of kBceStateBlock threads: smaller blocks even
+// out the uneven marker work (list lengths, body kinematics) over the SMs.
+constexpr int kBceStateBlock = 128;
 
 // Grid of a state pass: the blocks the markers need, at most one wave of the
 // kernel's resident blocks.
@@ -409,14 +413,16 @@ unsigned bce_state_grid(const DevParams &p)
 {
     static int per_sm = 0;
     if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bce<ACCEL, FILTER>, kBlock, 0)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_bce<ACCEL, FILTER, kBceLanes, kBceStateBlock>, kBceStateBlock, 0)
                 != cudaSuccess
             || per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
         }
     }
-    return (unsigned)std::min<int64_t>(bce_blocks(p), (int64_t)std::max(p.n_sm, 1) * per_sm);
+    return (unsigned)std::min<int64_t>(grid_for((int64_t)p.capM * kBceLanes, kBceStateBlock),
+                                       (int64_t)std::max(p.n_sm, 1) * per_sm);
 }
 
 // The soil wrench of body b = blockIdx.x (Sec. 2.4): the sum of the wrench
@@ -626,20 +632,22 @@ void launch_bce(const DevParams &p, StageArrays S, const float4 *home_pos, const
     BodyStep bs{partial, bodies, dt, integrate, gate};
     if (sk_nbr != nullptr) {   // stage 1 with a skin (no accelerations)
         const ListIO L{sk_nbr, sk_nnb, const_cast<uint32_t *>(nbr), const_cast<uint32_t *>(nnb), err};
-        k_bce<0, true><<<bce_state_grid<0, true>(p), kBlock, 0, st>>>(
+        k_bce<0, true, kBceLanes, kBceStateBlock><<<bce_state_grid<0, true>(p), kBceStateBlock, 0, st>>>(
             p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
         return;
     }
     const ListIO L{nbr, nnb, nullptr, nullptr, err};
     if (accel == 0) {
-        k_bce<0, false><<<bce_state_grid<0, false>(p), kBlock, 0, st>>>(
+        k_bce<0, false, kBceLanes, kBceStateBlock><<<bce_state_grid<0, false>(p), kBceStateBlock, 0,
+                                                    st>>>(
             p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
     } else if (accel == 1) {
         k_bce<1, false, kWrenchLanes><<<wrench_blocks(body_markers), kBlock, 0, st>>>(
             p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
         k_body_reduce<<<(unsigned)std::max(p.n_bodies, 1), 32, 0, st>>>(p, bs, n_act);
     } else {
-        k_bce<2, false><<<bce_state_grid<2, false>(p), kBlock, 0, st>>>(
+        k_bce<2, false, kBceLanes, kBceStateBlock><<<bce_state_grid<2, false>(p), kBceStateBlock, 0,
+                                                    st>>>(
             p, S, home_pos, pid, mloc, bodies, frames, L, act, n_act, tau, n_fluid_total, mforce, bs);
     }
 }
