@@ -563,7 +563,9 @@ void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *sta
     // lanes per particle: eight up to four waves of the GPU's threads (each lane
     // walks at most three rows of the stencil: on the 25,600-particle active set of
     // the rover strip 76 against 82 us with four lanes, 90 with sixteen), else one
-    if ((int64_t)p.capN * 4 <= (int64_t)p.n_sm * 2048 * 4)
+    // (the 191,000 slots of the 120,000-particle wheel bin: 146 us with one lane
+    // against 233 us with eight, whose 1.5 M threads made eight waves)
+    if ((int64_t)p.capN * 8 <= (int64_t)p.n_sm * 2048 * 4)
         k_neighbors<8><<<grid_for((int64_t)p.capN * 8), kBlock, 0, st>>>(p, pos, start, nbr, nnb,
                                                                          cap, r2cut, err);
     else
