@@ -414,7 +414,12 @@ __global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restr
 //
 // One row (dy, dz) of the 27-cell stencil in segment seg (0 fluid, 1 markers):
 // the neighbours of particle s in cells dx = -1, 0, 1, counted and, with `nbr`,
-// written from list position `at` on (ascending slot order).
+// written from list position `at` on (ascending slot order).  The candidates are
+// fetched BATCH at a time (their loads in flight together) and then taken in
+// order, as a one-by-one walk would.
+constexpr int kSearchBatch = 4;   // candidates in flight per row walk of a one-lane search
+
+template <int BATCH>
 __device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *__restrict__ pos,
                                              const uint32_t *__restrict__ start, const Window &W,
                                              int s, const float4 &ps, int lx, int ly, int lz,
@@ -446,17 +451,39 @@ __device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *_
         int j0 = jb;
         if (dx < 0) {
             j0 = je;
-            while (j0 > jb && fabsf(sx - pos[j0 - 1].x) < R) --j0;
+            bool more = true;
+            while (more && j0 > jb) {
+                float xs[BATCH];
+#pragma unroll
+                for (int u = 0; u < BATCH; ++u) xs[u] = j0 - 1 - u >= jb ? pos[j0 - 1 - u].x : 0.f;
+#pragma unroll
+                for (int u = 0; u < BATCH; ++u) {
+                    if (more && j0 > jb && fabsf(sx - xs[u]) < R) --j0;
+                    else more = false;
+                }
+            }
         }
-        for (int j = j0; j < je; ++j) {
-            const float4 pj = pos[j];
-            const float rx = sx - pj.x;
-            if (dx > 0 && fabsf(rx) >= R) break;
-            const float ry = sy - pj.y, rz = sz - pj.z;
-            const float r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 < r2cut && j != s) {
-                if (nbr != nullptr && at + cnt < cap) nbr[(size_t)(at + cnt) * p.ell + s] = (uint32_t)j | tag;
-                ++cnt;
+        bool more = true;
+        for (int j = j0; more && j < je; j += BATCH) {
+            float4 pb[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u)
+                pb[u] = j + u < je ? pos[j + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                if (!more || j + u >= je) break;
+                const float rx = sx - pb[u].x;
+                if (dx > 0 && fabsf(rx) >= R) {
+                    more = false;
+                    break;
+                }
+                const float ry = sy - pb[u].y, rz = sz - pb[u].z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 < r2cut && j + u != s) {
+                    if (nbr != nullptr && at + cnt < cap)
+                        nbr[(size_t)(at + cnt) * p.ell + s] = (uint32_t)(j + u) | tag;
+                    ++cnt;
+                }
             }
         }
     }
@@ -496,7 +523,7 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
         if (!valid) return;
         int cnt = 0;
         for (int r = 0; r < rows; ++r)
-            cnt += row_neighbors(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
+            cnt += row_neighbors<kSearchBatch>(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
                                  r % 3 - 1, r2cut, lim2, nbr, cnt, cap);
         if (cnt > cap) atomicOr(err, ERR_CAPACITY);
         nnb[s] = (uint32_t)min(cnt, cap);
@@ -507,7 +534,7 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
         const int r = k * kSearchLanes + q;
-        c[k] = r < rows ? row_neighbors(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
+        c[k] = r < rows ? row_neighbors<1>(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
                                         r % 3 - 1, r2cut, lim2, nullptr, 0, cap) : 0;
         off[k] = 0;
     }
@@ -524,7 +551,7 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
     for (int k = 0; k < kPer; ++k) {
         const int r = k * kSearchLanes + q;
         if (r < rows && c[k] > 0)
-            row_neighbors(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1, r % 3 - 1,
+            row_neighbors<1>(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1, r % 3 - 1,
                           r2cut, lim2, nbr, off[k], cap);
     }
     if (valid && q == 0) {
