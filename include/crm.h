@@ -244,8 +244,9 @@ int crm_get_counts(crm_terrain *t, int64_t *n_active, int64_t *n_extended, int64
  * advance n_steps steps of dt (0: none), then return every body's soil wrench
  * (wrench_out, n_bodies*6, as crm_get_body_wrench), pose and twist (each
  * nullable), with a single synchronisation (the transfers go through pinned
- * staging kept with the terrain).  Errors as crm_set_body_motion, crm_step
- * and crm_sync. */
+ * staging kept with the terrain; an exchange of one step with a new motion
+ * replays one graph holding the upload, the step and the read-back).  Errors as
+ * crm_set_body_motion, crm_step and crm_sync. */
 int crm_cosim_step(crm_terrain *t, const double *pose_in, const double *twist_in, double dt,
                    int32_t n_steps, double *wrench_out, double *pose_out, double *twist_out);
 
