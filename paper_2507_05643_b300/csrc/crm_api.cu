@@ -943,7 +943,7 @@ void enqueue_search(crm_terrain *t)
     if (t->skin_on) {
         launch(t, K_NEIGHBORS, [&] { launch_neighbors(d, t->A[n].pos, t->start, t->sk_nbr,
                                                       t->sk_nnb, d.skin_cap, d.sk_r2, t->err,
-                                                      t->st); });
+                                                      t->st, d.four_h2); });
         launch(t, K_SKIN, [&] { launch_copyback(d, t->A[n], t->pid[n], t->A[c], t->pid[c], t->xref,
                                                 t->bodies, t->st); });
         if (d.capM > 0)

@@ -414,30 +414,33 @@ __global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restr
 //
 // One row (dy, dz) of the 27-cell stencil in segment seg (0 fluid, 1 markers):
 // the neighbours of particle s in cells dx = -1, 0, 1, counted and, with `nbr`,
-// written from list position `at` on (ascending slot order).  The candidates are
-// fetched BATCH at a time (their loads in flight together) and then taken in
-// order, as a one-by-one walk would.
+// written in ascending slot order: those closer than sqrt(r2in) (the inner part)
+// from list position at_in on, the others (the shell between sqrt(r2in) and the
+// search radius) from position cap - 1 - at_sh downward.  Returns the two counts.
+// The candidates are fetched BATCH at a time (their loads in flight together)
+// and then taken in order, as a one-by-one walk would.
 constexpr int kSearchBatch = 4;   // candidates in flight per row walk of a one-lane search
 
 template <int BATCH>
-__device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *__restrict__ pos,
+__device__ __forceinline__ int2 row_neighbors(const DevParams &p, const float4 *__restrict__ pos,
                                              const uint32_t *__restrict__ start, const Window &W,
                                              int s, const float4 &ps, int lx, int ly, int lz,
                                              int seg, int dy, int dz, float r2cut, float lim2,
-                                             uint32_t *__restrict__ nbr, int at, int cap)
+                                             float r2in, uint32_t *__restrict__ nbr, int at_in,
+                                             int at_sh, int cap)
 {
     const int lz2 = lz + dz, ly2 = ly + dy;
-    if (lz2 < 0 || lz2 >= W.Z || ly2 < 0 || ly2 >= W.Y) return 0;
+    if (lz2 < 0 || lz2 >= W.Z || ly2 < 0 || ly2 >= W.Y) return make_int2(0, 0);
     const float cell = p.cell;
     const float gz = dz < 0 ? fmaxf(ps.z, 0.f) : (dz > 0 ? fmaxf(cell - ps.z, 0.f) : 0.f);
     const float gy = dy < 0 ? fmaxf(ps.y, 0.f) : (dy > 0 ? fmaxf(cell - ps.y, 0.f) : 0.f);
     const float d2 = gy * gy + gz * gz;
-    if (d2 >= lim2) return 0;
+    if (d2 >= lim2) return make_int2(0, 0);
     const float R = sqrtf(lim2 - d2);
     const float sy = ps.y - (float)dy * cell, sz = ps.z - (float)dz * cell;
     const uint32_t kb = seg * p.M;
     const uint32_t codeyz = (uint32_t)(dy + 1) << 2 | (uint32_t)(dz + 1) << 4;
-    int cnt = 0;
+    int cnt = 0, csh = 0;
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
         const int lx2 = lx + dx;
@@ -480,14 +483,20 @@ __device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *_
                 const float ry = sy - pb[u].y, rz = sz - pb[u].z;
                 const float r2 = rx * rx + ry * ry + rz * rz;
                 if (r2 < r2cut && j + u != s) {
-                    if (nbr != nullptr && at + cnt < cap)
-                        nbr[(size_t)(at + cnt) * p.ell + s] = (uint32_t)(j + u) | tag;
-                    ++cnt;
+                    const uint32_t e = (uint32_t)(j + u) | tag;
+                    if (r2 < r2in) {
+                        if (nbr != nullptr && at_in + cnt < cap) nbr[(size_t)(at_in + cnt) * p.ell + s] = e;
+                        ++cnt;
+                    } else {
+                        const int k = cap - 1 - (at_sh + csh);
+                        if (nbr != nullptr && k >= 0) nbr[(size_t)k * p.ell + s] = e;
+                        ++csh;
+                    }
                 }
             }
         }
     }
-    return cnt;
+    return make_int2(cnt, csh);
 }
 
 // LANES lanes share a particle.  One lane walks the 18 rows (fluid then marker
@@ -496,11 +505,15 @@ __device__ __forceinline__ int row_neighbors(const DevParams &p, const float4 *_
 // by shuffles, and write their rows' entries there: the same list at a fraction
 // of the serial latency but twice the reads, which pays only while the grid is
 // small against the GPU (launch_neighbors picks).
+// r2in > 0 (the skin search): a fluid particle's list holds the pairs closer than
+// sqrt(r2in) at the list's front and the rest of the search radius at the back of
+// its cap entries, nnb = inner count | shell count << 16 (the filtering stage 1
+// tests the shell's candidates apart); markers' lists are one front part.
 template <int LANES>
 __global__ void __launch_bounds__(kBlock)
 k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restrict__ start,
             uint32_t *__restrict__ nbr, uint32_t *__restrict__ nnb, int cap, float r2cut,
-            int *__restrict__ err)
+            float r2in, int *__restrict__ err)
 {
     constexpr int kSearchLanes = LANES;
     if (*p.abort || gated_off(p)) return;
@@ -519,44 +532,57 @@ k_neighbors(DevParams p, const float4 *__restrict__ pos, const uint32_t *__restr
     }
     const int rows = valid ? (s < z.nF ? 18 : 9) : 0;
     const float lim2 = r2cut * (1.0f + 1e-5f);
+    const float rin = (r2in > 0.0f && s < z.nF) ? r2in : 3.0e38f;   // the inner part's radius^2
     if constexpr (LANES == 1) {
         if (!valid) return;
-        int cnt = 0;
-        for (int r = 0; r < rows; ++r)
-            cnt += row_neighbors<kSearchBatch>(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
-                                 r % 3 - 1, r2cut, lim2, nbr, cnt, cap);
-        if (cnt > cap) atomicOr(err, ERR_CAPACITY);
-        nnb[s] = (uint32_t)min(cnt, cap);
+        int cin = 0, csh = 0;
+        for (int r = 0; r < rows; ++r) {
+            const int2 c = row_neighbors<kSearchBatch>(p, pos, start, W, s, ps, lx, ly, lz, r / 9,
+                                                       (r / 3) % 3 - 1, r % 3 - 1, r2cut, lim2, rin,
+                                                       nbr, cin, csh, cap);
+            cin += c.x;
+            csh += c.y;
+        }
+        if (cin + csh > cap) atomicOr(err, ERR_CAPACITY);
+        nnb[s] = (uint32_t)min(cin, cap) | (uint32_t)min(csh, cap) << 16;
         return;
     }
     constexpr int kPer = (18 + kSearchLanes - 1) / kSearchLanes;
-    int c[kPer], off[kPer];
+    int2 c[kPer];
+    int off[kPer], offs[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
         const int r = k * kSearchLanes + q;
-        c[k] = r < rows ? row_neighbors<1>(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1,
-                                        r % 3 - 1, r2cut, lim2, nullptr, 0, cap) : 0;
-        off[k] = 0;
+        c[k] = r < rows ? row_neighbors<1>(p, pos, start, W, s, ps, lx, ly, lz, r / 9,
+                                           (r / 3) % 3 - 1, r % 3 - 1, r2cut, lim2, rin, nullptr,
+                                           0, 0, cap)
+                        : make_int2(0, 0);
+        off[k] = offs[k] = 0;
     }
-    // rows in order: row r is lane (r % 4)'s entry r / 4
+    // rows in order: row r is lane (r % kSearchLanes)'s entry r / kSearchLanes
     const int base = (threadIdx.x & 31) & ~(kSearchLanes - 1);
-    int run = 0;
+    int run = 0, runs = 0;
 #pragma unroll
     for (int r = 0; r < 18; ++r) {
-        const int n_r = __shfl_sync(0xffffffffu, c[r / kSearchLanes], base + r % kSearchLanes);
-        if (r % kSearchLanes == q) off[r / kSearchLanes] = run;
+        const int n_r = __shfl_sync(0xffffffffu, c[r / kSearchLanes].x, base + r % kSearchLanes);
+        const int s_r = __shfl_sync(0xffffffffu, c[r / kSearchLanes].y, base + r % kSearchLanes);
+        if (r % kSearchLanes == q) {
+            off[r / kSearchLanes] = run;
+            offs[r / kSearchLanes] = runs;
+        }
         run += n_r;
+        runs += s_r;
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
         const int r = k * kSearchLanes + q;
-        if (r < rows && c[k] > 0)
+        if (r < rows && (c[k].x > 0 || c[k].y > 0))
             row_neighbors<1>(p, pos, start, W, s, ps, lx, ly, lz, r / 9, (r / 3) % 3 - 1, r % 3 - 1,
-                          r2cut, lim2, nbr, off[k], cap);
+                             r2cut, lim2, rin, nbr, off[k], offs[k], cap);
     }
     if (valid && q == 0) {
-        if (run > cap) atomicOr(err, ERR_CAPACITY);
-        nnb[s] = (uint32_t)min(run, cap);
+        if (run + runs > cap) atomicOr(err, ERR_CAPACITY);
+        nnb[s] = (uint32_t)min(run, cap) | (uint32_t)min(runs, cap) << 16;
     }
 }
 
@@ -585,7 +611,7 @@ void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *st
 }
 
 void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
-                      uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st)
+                      uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st, float r2in)
 {
     // lanes per particle: eight up to four waves of the GPU's threads (each lane
     // walks at most three rows of the stencil: on the 25,600-particle active set of
@@ -594,10 +620,10 @@ void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *sta
     // against 233 us with eight, whose 1.5 M threads made eight waves)
     if ((int64_t)p.capN * 8 <= (int64_t)p.n_sm * 2048 * 4)
         k_neighbors<8><<<grid_for((int64_t)p.capN * 8), kBlock, 0, st>>>(p, pos, start, nbr, nnb,
-                                                                         cap, r2cut, err);
+                                                                         cap, r2cut, r2in, err);
     else
         k_neighbors<1><<<grid_for(p.capN), kBlock, 0, st>>>(p, pos, start, nbr, nnb, cap, r2cut,
-                                                            err);
+                                                            r2in, err);
 }
 
 // ---------------------------------------------------------------------------

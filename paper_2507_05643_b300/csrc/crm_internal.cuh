@@ -450,8 +450,11 @@ void launch_scatter(const DevParams &p, const SortScratch &s, const uint32_t *st
 void launch_reorder(const DevParams &p, const SortScratch &s, const uint32_t *start,
                     StageArrays cur, const uint32_t *pid_cur, StageArrays nxt, uint32_t *pid_nxt,
                     cudaStream_t st);
+// r2in > 0: fluid lists split into the pairs closer than sqrt(r2in) (front) and
+// the rest of the radius (back of the cap entries), nnb = inner | shell << 16.
 void launch_neighbors(const DevParams &p, const float4 *pos, const uint32_t *start, uint32_t *nbr,
-                      uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st);
+                      uint32_t *nnb, int cap, float r2cut, int *err, cudaStream_t st,
+                      float r2in = 0.0f);
 // Verlet skin (Alg. 2 with a skin): decide whether the cell search is due and
 // copy the re-sorted arrays back (the stage-1 kernels filter the skin lists
 // down to the exact 2h lists).

@@ -279,14 +279,19 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
     A.mx = A.my = A.mz = A.Gx = A.Gy = A.Gz = A.avx = A.avy = A.avz = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) A.L[k] = 0.f;
-    const int nn = adv ? (int)io.in_n[i] : 0;
+    // a skin list (FILTER) holds the pairs within 2h at its search at the front
+    // (count: the low half of its count word) and the rest of the skin radius at the
+    // back of its skin_cap entries (the high half); an exact list is one front part
+    const uint32_t nw = adv ? io.in_n[i] : 0u;
+    const int nn = FILTER ? (int)(nw & 0xFFFFu) : (int)nw;
+    const int ns = FILTER ? (int)(nw >> 16) : 0;
     const uint32_t *row = io.in + (adv ? i : 0);
     int cnt = 0;
     // the lane's next list entry is fetched one iteration ahead
     uint32_t e_nx = q < nn ? ld_list(row + (size_t)q * p.ell) : 0u;
     if (!FILTER || LANES == 1) {
-        // on an exact list the neighbour's whole state is gathered at once (one
-        // load round per iteration); on a skin list the rest follows the distance test
+        // on an exact list, and on a skin list's front, the neighbour's whole state
+        // is gathered at once (one load round per iteration)
         const size_t step = (size_t)LANES * p.ell;
         const uint32_t *nxt = row + (size_t)(q + LANES) * p.ell;   // entry k + LANES
         uint32_t *out = FILTER ? io.out + i : nullptr;                // exact entry cnt
@@ -313,36 +318,91 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
             }
             pair_terms<KAV>(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
         }
-    } else {
-        // filtering with a lane group: warp-uniform rounds, in each of which the
-        // group's lanes test consecutive candidates and place the kept ones by ballot
-        const int rounds = __reduce_max_sync(0xffffffffu, (nn + LANES - 1) / LANES);
-        const int lane = threadIdx.x & 31;
-        for (int r = 0; r < rounds; ++r) {
-            const int k = r * LANES + q;
-            const uint32_t e = e_nx;
-            if (k + LANES < nn) e_nx = ld_list(row + (size_t)(k + LANES) * p.ell);
-            bool keep = false;
-            float rx = 0.f, ry = 0.f, rz = 0.f, r2 = 0.f;
-            uint32_t j = 0;
-            if (k < nn) {
-                j = e & kIndexMask;
+        if (FILTER && ns > 0) {
+            // the skin list's back: few of its candidates have come within 2h, so
+            // each is tested on its position alone, and the kept ones wait in a
+            // short queue so that the lanes of a warp sum them together afterwards
+            // (one pair evaluation per queued entry rather than one per candidate
+            // some lane keeps); a full queue sums at once
+            uint32_t q0 = 0u, q1 = 0u, q2 = 0u, q3 = 0u;
+            int nq = 0;
+            const uint32_t *sp = row + (size_t)(p.skin_cap - 1) * p.ell;
+            uint32_t s_nx = ld_list(sp);
+            for (int m = 0; m < ns; ++m, sp -= p.ell) {
+                const uint32_t e = s_nx;
+                if (m + 1 < ns) s_nx = ld_list(sp - p.ell);
+                const uint32_t j = e & kIndexMask;
                 const float3 sh = entry_shift(e, p.cell);
                 const float4 pj = __ldg(&S.pos[j]);
-                rx = pi.x - pj.x - sh.x; ry = pi.y - pj.y - sh.y; rz = pi.z - pj.z - sh.z;
-                r2 = rx * rx + ry * ry + rz * rz;
-                keep = r2 < p.four_h2;
+                const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (!(r2 < p.four_h2)) continue;
+                if (cnt < p.maxnb) {
+                    *out = e;
+                    out += p.ell;
+                }
+                ++cnt;
+                if (nq < 4) {
+                    q0 = nq == 0 ? e : q0;
+                    q1 = nq == 1 ? e : q1;
+                    q2 = nq == 2 ? e : q2;
+                    q3 = nq == 3 ? e : q3;
+                    ++nq;
+                } else {
+                    pair_terms<KAV>(p, vi, ai, bi, __ldg(&S.vel[j]), __ldg(&S.sA[j]),
+                                    __ldg(&S.sB[j]), rx, ry, rz, r2, A);
+                }
             }
-            const unsigned b = __ballot_sync(0xffffffffu, keep);
-            const unsigned g = (b >> (lane & ~(LANES - 1))) & ((1u << LANES) - 1u);
-            const int at = cnt + __popc(g & ((1u << q) - 1u));
-            if (keep && at < p.maxnb) io.out[(size_t)at * p.ell + i] = e;
-            cnt += __popc(g);
-            if (!keep) continue;
-            const float4 vj = __ldg(&S.vel[j]);
-            const float4 aj = __ldg(&S.sA[j]);
-            const float2 bj = __ldg(&S.sB[j]);
-            pair_terms<KAV>(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
+            for (int m = 0; m < nq; ++m) {
+                const uint32_t e = m == 0 ? q0 : (m == 1 ? q1 : (m == 2 ? q2 : q3));
+                const uint32_t j = e & kIndexMask;
+                const float3 sh = entry_shift(e, p.cell);
+                const float4 pj = __ldg(&S.pos[j]);
+                const float4 vj = __ldg(&S.vel[j]);
+                const float4 aj = __ldg(&S.sA[j]);
+                const float2 bj = __ldg(&S.sB[j]);
+                const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
+                pair_terms<KAV>(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, rx * rx + ry * ry + rz * rz, A);
+            }
+        }
+    } else {
+        // filtering with a lane group: the skin list's front, then its back, in
+        // warp-uniform rounds, in each of which the group's lanes test consecutive
+        // candidates and place the kept ones by ballot
+        const int lane = threadIdx.x & 31;
+        for (int part = 0; part < 2; ++part) {
+            const int len = part == 0 ? nn : ns;
+            // the part's k-th entry sits at first + k * stride
+            const ptrdiff_t stride = part == 0 ? (ptrdiff_t)p.ell : -(ptrdiff_t)p.ell;
+            const uint32_t *first = part == 0 ? row : row + (size_t)(p.skin_cap - 1) * p.ell;
+            if (part == 1) e_nx = q < len ? ld_list(first + q * stride) : 0u;
+            const int rounds = __reduce_max_sync(0xffffffffu, (len + LANES - 1) / LANES);
+            for (int r = 0; r < rounds; ++r) {
+                const int k = r * LANES + q;
+                const uint32_t e = e_nx;
+                if (k + LANES < len) e_nx = ld_list(first + (k + LANES) * stride);
+                bool keep = false;
+                float rx = 0.f, ry = 0.f, rz = 0.f, r2 = 0.f;
+                uint32_t j = 0;
+                if (k < len) {
+                    j = e & kIndexMask;
+                    const float3 sh = entry_shift(e, p.cell);
+                    const float4 pj = __ldg(&S.pos[j]);
+                    rx = pi.x - pj.x - sh.x; ry = pi.y - pj.y - sh.y; rz = pi.z - pj.z - sh.z;
+                    r2 = rx * rx + ry * ry + rz * rz;
+                    keep = r2 < p.four_h2;
+                }
+                const unsigned b = __ballot_sync(0xffffffffu, keep);
+                const unsigned g = (b >> (lane & ~(LANES - 1))) & ((1u << LANES) - 1u);
+                const int at = cnt + __popc(g & ((1u << q) - 1u));
+                if (keep && at < p.maxnb) io.out[(size_t)at * p.ell + i] = e;
+                cnt += __popc(g);
+                if (!keep) continue;
+                const float4 vj = __ldg(&S.vel[j]);
+                const float4 aj = __ldg(&S.sA[j]);
+                const float2 bj = __ldg(&S.sB[j]);
+                pair_terms<KAV>(p, vi, ai, bi, vj, aj, bj, rx, ry, rz, r2, A);
+            }
         }
     }
     if (LANES > 1) {
@@ -370,7 +430,7 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
 }
 
 template <int MODE, bool FILTER, int LANES, int KAV>
-__global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
+__global__ void __launch_bounds__(kPairBlock, LANES == 2 ? 8 : 7)
 k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
        const uint32_t *__restrict__ pid, float dt, RateOut out, int *__restrict__ err,
        const float4 *__restrict__ xref, int *__restrict__ gate)
@@ -388,7 +448,7 @@ k_pair(DevParams p, StageArrays S, StageArrays Y, StageArrays MID, ListIO io,
 // as those launches would: stage 1 filtering the skin lists, stage 2 on the
 // exact lists, each with the member's lanes.
 template <int MODE, int LANES, int KAV>
-__global__ void __launch_bounds__(kPairBlock, LANES == 1 ? 7 : 8)
+__global__ void __launch_bounds__(kPairBlock, LANES == 2 ? 8 : 7)
 k_batch_pair(const MemberDev *__restrict__ mem, const int *__restrict__ mlist,
              const int *__restrict__ off, int n, unsigned *queue)
 {
