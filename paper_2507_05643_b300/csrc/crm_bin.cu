@@ -410,7 +410,9 @@ __global__ void k_reorder(const int *__restrict__ n_dev, const uint32_t *__restr
 // upwards), so the k-th entries of neighbouring particles -- neighbouring lanes
 // of the pair kernels -- are close in memory; each entry is j | code << 26 with
 // code = (dx+1) | (dy+1) << 2 | (dz+1) << 4, which the pair kernels use to
-// rebuild x_s - x_j from the cell-relative offsets.
+// rebuild x_s - x_j from the cell-relative offsets.  (A skin search splits each
+// fluid particle's list: the pairs within 2h in that order at the front, the rest
+// of the skin radius in that order at the back, from the last entry down.)
 //
 // One row (dy, dz) of the 27-cell stencil in segment seg (0 fluid, 1 markers):
 // the neighbours of particle s in cells dx = -1, 0, 1, counted and, with `nbr`,
