@@ -326,17 +326,9 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
             // some lane keeps); a full queue sums at once
             uint32_t q0 = 0u, q1 = 0u, q2 = 0u, q3 = 0u;
             int nq = 0;
-            const uint32_t *sp = row + (size_t)(p.skin_cap - 1) * p.ell;
-            uint32_t s_nx = ld_list(sp);
-            for (int m = 0; m < ns; ++m, sp -= p.ell) {
-                const uint32_t e = s_nx;
-                if (m + 1 < ns) s_nx = ld_list(sp - p.ell);
-                const uint32_t j = e & kIndexMask;
-                const float3 sh = entry_shift(e, p.cell);
-                const float4 pj = __ldg(&S.pos[j]);
-                const float rx = pi.x - pj.x - sh.x, ry = pi.y - pj.y - sh.y, rz = pi.z - pj.z - sh.z;
-                const float r2 = rx * rx + ry * ry + rz * rz;
-                if (!(r2 < p.four_h2)) continue;
+            // a kept candidate: written to the exact list, queued (or summed at once
+            // when the queue is full)
+            auto keep = [&](uint32_t e, float rx, float ry, float rz, float r2) {
                 if (cnt < p.maxnb) {
                     *out = e;
                     out += p.ell;
@@ -349,9 +341,29 @@ __device__ __forceinline__ void pair_one(const DevParams &p, int i, int q, int l
                     q3 = nq == 3 ? e : q3;
                     ++nq;
                 } else {
+                    const uint32_t j = e & kIndexMask;
                     pair_terms<KAV>(p, vi, ai, bi, __ldg(&S.vel[j]), __ldg(&S.sA[j]),
                                     __ldg(&S.sB[j]), rx, ry, rz, r2, A);
                 }
+            };
+            // two candidates per iteration, their positions fetched together (the
+            // next two list words one iteration ahead)
+            const uint32_t *sp = row + (size_t)(p.skin_cap - 1) * p.ell;
+            uint32_t na = ld_list(sp), nb = ns > 1 ? ld_list(sp - p.ell) : 0u;
+            for (int m = 0; m < ns; m += 2, sp -= 2 * p.ell) {
+                const uint32_t ea = na, eb = nb;
+                const bool two = m + 1 < ns;
+                if (m + 2 < ns) na = ld_list(sp - 2 * p.ell);
+                if (m + 3 < ns) nb = ld_list(sp - 3 * p.ell);
+                const float3 sha = entry_shift(ea, p.cell), shb = entry_shift(eb, p.cell);
+                const float4 pa = __ldg(&S.pos[ea & kIndexMask]);
+                const float4 pb = two ? __ldg(&S.pos[eb & kIndexMask]) : pa;
+                const float ax = pi.x - pa.x - sha.x, ay = pi.y - pa.y - sha.y, az = pi.z - pa.z - sha.z;
+                const float a2 = ax * ax + ay * ay + az * az;
+                if (a2 < p.four_h2) keep(ea, ax, ay, az, a2);
+                const float bx = pi.x - pb.x - shb.x, by = pi.y - pb.y - shb.y, bz = pi.z - pb.z - shb.z;
+                const float b2 = bx * bx + by * by + bz * bz;
+                if (two && b2 < p.four_h2) keep(eb, bx, by, bz, b2);
             }
             for (int m = 0; m < nq; ++m) {
                 const uint32_t e = m == 0 ? q0 : (m == 1 ? q1 : (m == 2 ? q2 : q3));
