@@ -259,6 +259,18 @@ def _traffic(kernel: str, captured: bool = True):
     return None
 
 
+def dominant_kernel(per_launch_ms: dict, workload: str) -> str:
+    """The kernel id the roofline is quoted for: the single kernel with the largest
+    share of the event-timed step, taken as the largest time per launch -- an id
+    that counts several kernels (bce: the two marker-state passes, the wrench pass
+    and the body update) is not one kernel, and its per-step total is a sum of four.
+    With active domains and the skin (the strip), only the kernels that work at
+    every step compete: the gated gather and search kernels are launched every step
+    in the direct-launch pass but mostly return at once."""
+    every = ("pair_stage1", "pair_stage2", "bce") if workload == "strip" else tuple(per_launch_ms)
+    return max((k for k in per_launch_ms if k in every), key=lambda k: per_launch_ms[k])
+
+
 def _workload(args):
     """The benchmark workload; --bin-scale S > 1 widens the bin S-fold in x and y
     (a profiling case larger than L2, not a bench line); --workload strip runs the
@@ -701,15 +713,7 @@ def run_crm(args):
         n_all = sc.n_fluid + sc.n_markers
         per = {k: prof["ms"][k] / max(prof["launches"][k], 1) for k in prof["ms"]
                if prof["launches"][k]}
-        # dominant kernel = the single kernel with the largest share of the event-
-        # timed step, taken as the largest time per launch: an id that counts
-        # several kernels (bce: the two marker-state passes, the wrench pass and the
-        # body update) is not one kernel, and its total is a sum of four (with
-        # active domains and the skin: among the kernels that work at every step --
-        # the gated gather and search kernels are launched every step in this
-        # direct-launch pass but mostly return at once)
-        every = ("pair_stage1", "pair_stage2", "bce") if args.workload == "strip" else tuple(prof["ms"])
-        kern = max((k for k in per if k in every), key=lambda k: per[k])
+        kern = dominant_kernel(per, args.workload)
         avg_ms = per[kern]
         # the ncu DRAM bytes in profiles/ were captured on the wheel bin as quoted
         same_case = args.workload == "wheel_bin" and args.bin_scale == 1 and args.ps_freq == 1

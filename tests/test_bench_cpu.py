@@ -38,3 +38,16 @@ def test_captured_traffic_applies_only_to_its_workload_and_source():
     v = bench._traffic("pair_stage1")
     assert v is None or v > 1e6          # None once crm_step.cu changed since the capture
     assert bench._traffic("no_such_kernel") is None
+
+
+def test_dominant_kernel_is_one_kernel():
+    """The roofline's kernel: the largest time per launch, not the largest per-step
+    total of an id that counts several kernels (the four BCE launches)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    per = {"pair_stage1": 0.061, "pair_stage2": 0.047, "bce": 0.016, "neighbors": 0.003}
+    assert bench.dominant_kernel(per, "wheel_bin") == "pair_stage1"
+    per_skin0 = dict(per, neighbors=0.11)   # a search at every step dominates
+    assert bench.dominant_kernel(per_skin0, "wheel_bin") == "neighbors"
+    # the strip: gated search kernels do not compete
+    assert bench.dominant_kernel(dict(per, keys=0.5), "strip") == "pair_stage1"
