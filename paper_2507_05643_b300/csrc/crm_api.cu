@@ -604,9 +604,11 @@ int commit(crm_terrain *t)
 
     // static device state
     t->mloc = t->dalloc<double>(G_STATIC, 3 * nM);
-    t->bodies = t->dalloc<BodyDev>(G_STATIC, t->hbodies.size());
+    // the error word right after the bodies: the co-simulation exchange reads both
+    // back with one copy
+    t->bodies = t->dalloc<BodyDev>(G_STATIC, t->hbodies.size() + 1);
     t->mid_frames = t->dalloc<BodyFrame>(G_STATIC, kMaxBodies);
-    t->err = t->dalloc<int>(G_STATIC, 1);
+    t->err = t->bodies ? reinterpret_cast<int *>(t->bodies + t->hbodies.size()) : nullptr;
     t->counts = t->dalloc<int>(G_STATIC, C_WORDS);
     t->win = t->dalloc<int>(G_STATIC, 8);
     t->abort_flag = t->dalloc<int>(G_STATIC, 1);
@@ -1066,10 +1068,11 @@ void exchange_in(crm_terrain *t)
 void exchange_out(crm_terrain *t)
 {
     const size_t nb = t->hbodies.size();
-    if (nb > 0)
-        cudaMemcpyAsync(t->h_xbodies, t->bodies, nb * sizeof(BodyDev), cudaMemcpyDeviceToHost, t->st);
-    cudaMemcpyAsync((int *)(t->h_xbodies + std::max<size_t>(nb, 1)), t->err, sizeof(int),
-                    cudaMemcpyDeviceToHost, t->st);
+    if (nb > 0)   // the bodies and the error word behind them (the staging's layout too)
+        cudaMemcpyAsync(t->h_xbodies, t->bodies, nb * sizeof(BodyDev) + sizeof(int),
+                        cudaMemcpyDeviceToHost, t->st);
+    else
+        cudaMemcpyAsync((int *)(t->h_xbodies + 1), t->err, sizeof(int), cudaMemcpyDeviceToHost, t->st);
 }
 
 // Capture one step into an executable graph: with the skin, the decision
